@@ -1,0 +1,301 @@
+"""FP64 CPU oracle of the CRKSPH pair passes (CRK-HACC, arXiv 2202.02840).
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, __graft_entry__.smoke() and the
+CPU-baseline leg of bench.py, never by the product path.  Shares no code with
+the CUDA library.  Pair passes run in crk_oracle.c (FP64, brute force or an
+equivalent grid search); the elementwise steps below are plain numpy FP64.
+
+Paper sections followed:
+  P1 volumes        Sec. 1.2 eq:vol, Sec. 2.6 eq:hi
+  P2 corrections    Sec. 1.2 eq:RK, eq:gRK and the two moment conditions
+  P3 grad v         Sec. 1.2 eq:gradv
+  P4 forces         Sec. 1.2 eq:mom, eq:eng, eq:visc, eq:mu, eq:hatvi, eq:phi..eq:phiad
+  P5 compatible     Sec. 1.2 eq:compEng .. eq:fij
+  step              Sec. 2.1 eq:verletOP (KDK with predictor), CFL criteria
+  h                 Sec. 2.6 eq:thacker
+"""
+import ctypes
+import numpy as np
+
+from . import build as _build
+
+# Constants stated in the paper: gamma = 5/3 (Sec. 1.1), n_h = 4 and N_res = 268
+# (Sec. 2.6), C_l = 2, C_q = 1, eps = 0.1 (Sec. 1.2), eta_crit = 1/n_h,
+# eta_fold = 0.2/n_h (Sec. 1.2), C_CFL = 0.25, zeta = 4 (Sec. 2.1).
+PARAMS = dict(gamma=5.0 / 3.0, n_h=4.0, N_res=268.0, C_l=2.0, C_q=1.0, eps=0.1,
+              eta_crit=1.0 / 4.0, eta_fold=0.2 / 4.0, C_cfl=0.25, zeta=4.0)
+_ORDER = ["gamma", "n_h", "N_res", "C_l", "C_q", "eps", "eta_crit", "eta_fold", "C_cfl", "zeta"]
+
+_LIB = None
+_f32p = np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")
+_f64p = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
+_u32p = np.ctypeslib.ndpointer(np.uint32, flags="C_CONTIGUOUS")
+_i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
+_vp = ctypes.c_void_p
+_ci = ctypes.c_int
+
+
+def load():
+    global _LIB
+    if _LIB is None:
+        lib = ctypes.CDLL(_build.build())
+        lib.orc_fixed_point.argtypes = [_ci, _f32p, _u32p, _u32p]
+        lib.orc_neighbours.argtypes = [_ci, _f32p, _ci, _ci, _vp, _ci, _i32p, _vp, ctypes.c_longlong]
+        lib.orc_cells.argtypes = [_ci, _f32p, _ci, _u32p, _i32p, ctypes.POINTER(_ci), _i32p]
+        lib.orc_volumes.argtypes = [_ci, _f32p, _ci, _vp, _ci, _f64p, _f64p, _f64p,
+                                    ctypes.POINTER(ctypes.c_longlong)]
+        lib.orc_corrections.argtypes = [_ci, _f32p, _ci, _vp, _ci, _f64p, _f64p, _f64p, _f64p,
+                                        _f64p, _vp, _vp]
+        lib.orc_gradv.argtypes = [_ci, _f32p, _ci, _vp, _ci] + [_f64p] * 7
+        lib.orc_forces.argtypes = [_ci, _f32p, _ci, _vp, _ci] + [_f64p] * 13 + [
+            _vp, ctypes.POINTER(ctypes.c_longlong)]
+        lib.orc_compatible.argtypes = [_ci, _f32p, _ci, _vp, _ci] + [_f64p] * 13
+        lib.orc_kernel.argtypes = [_ci, _f64p, _f64p, _f64p, _f64p]
+        lib.orc_num_threads.restype = _ci
+        _LIB = lib
+    return _LIB
+
+
+def _check(rc, what):
+    if rc != 0:
+        raise ValueError("oracle %s failed with status %d" % (what, rc))
+
+
+def params(**overrides) -> np.ndarray:
+    p = dict(PARAMS)
+    p.update(overrides)
+    return np.array([p[k] for k in _ORDER], np.float64)
+
+
+def num_threads() -> int:
+    return int(load().orc_num_threads())
+
+
+def kernel(r, h):
+    """W(r, h) of eq:C4 and dW/dr, elementwise (FP64)."""
+    r = np.ascontiguousarray(r, np.float64).ravel()
+    h = np.ascontiguousarray(np.broadcast_to(h, r.shape), np.float64)
+    W, dW = np.zeros_like(r), np.zeros_like(r)
+    _check(load().orc_kernel(len(r), r, h, W, dW), "kernel")
+    return W, dW
+
+
+def grid_level(n: int) -> int:
+    """Candidate-grid level for the oracle search (about 8 particles per cell)."""
+    if n <= 4096:
+        return 0
+    k = int(round(np.log2(max(n / 8.0, 1.0)) / 3.0))
+    return max(1, min(7, k))
+
+
+def _pos(pos_h):
+    return np.ascontiguousarray(pos_h, np.float32).reshape(-1, 4)
+
+
+def _tg(targets):
+    if targets is None:
+        return None, 0, None
+    t = np.ascontiguousarray(targets, np.int32)
+    return t.ctypes.data_as(_vp), len(t), t
+
+
+def _k(pos, k):
+    return grid_level(pos.shape[0]) if k is None else int(k)
+
+
+def fixed_point(pos_h):
+    """q = floor(s 2^32) (n,3) and H = floor(h 2^32) (n,)."""
+    pos = _pos(pos_h)
+    n = pos.shape[0]
+    q = np.zeros((n, 3), np.uint32)
+    H = np.zeros(n, np.uint32)
+    _check(load().orc_fixed_point(n, pos, q, H), "fixed_point")
+    return q, H
+
+
+def neighbours(pos_h, mode=0, k=None, targets=None):
+    """mode 0: gather(i) incl. self; mode 1: pair set.  Returns (counts, lists CSR)."""
+    pos = _pos(pos_h)
+    n = pos.shape[0]
+    tp, nt, keep = _tg(targets)
+    m = n if targets is None else nt
+    counts = np.zeros(m, np.int32)
+    lib = load()
+    _check(lib.orc_neighbours(n, pos, _k(pos, k), mode, tp, nt, counts, None, 0), "neighbours")
+    total = int(counts.astype(np.int64).sum())
+    lists = np.zeros(max(total, 1), np.int32)
+    _check(lib.orc_neighbours(n, pos, _k(pos, k), mode, tp, nt, counts,
+                              lists.ctypes.data_as(_vp), total), "neighbours")
+    return counts, lists[:total]
+
+
+def cells(pos_h, kmax=7):
+    """Morton keys, stable sort permutation, chaining-mesh level and cell starts."""
+    pos = _pos(pos_h)
+    n = pos.shape[0]
+    key = np.zeros(n, np.uint32)
+    perm = np.zeros(n, np.int32)
+    kk = _ci(0)
+    start = np.zeros((1 << (3 * kmax)) + 1, np.int32)
+    _check(load().orc_cells(n, pos, kmax, key, perm, ctypes.byref(kk), start), "cells")
+    k = kk.value
+    return key, perm, k, start[: (1 << (3 * k)) + 1].copy()
+
+
+def volumes(pos_h, k=None, targets=None):
+    """P1: n_i, V_i = 1/n_i, N_i = 4/3 pi h^3 n_i (eq:vol, eq:hi)."""
+    pos = _pos(pos_h)
+    n = pos.shape[0]
+    tp, nt, keep = _tg(targets)
+    nsum, V, N = (np.full(n, np.nan) for _ in range(3))
+    pairs = ctypes.c_longlong(0)
+    _check(load().orc_volumes(n, pos, _k(pos, k), tp, nt, nsum, V, N, ctypes.byref(pairs)), "volumes")
+    return {"nsum": nsum, "V": V, "N": N, "pairs": int(pairs.value)}
+
+
+def corrections(pos_h, V, k=None, targets=None, moments=False):
+    """P2: A, B, grad A, grad B (gB[i, alpha, gamma]) and cond(m2)."""
+    pos = _pos(pos_h)
+    n = pos.shape[0]
+    tp, nt, keep = _tg(targets)
+    A = np.full(n, np.nan)
+    B, gA = np.full((n, 3), np.nan), np.full((n, 3), np.nan)
+    gB = np.full((n, 3, 3), np.nan)
+    cond = np.full(n, np.nan)
+    mom = np.full((n, 40), np.nan) if moments else None
+    _check(load().orc_corrections(n, pos, _k(pos, k), tp, nt, np.ascontiguousarray(V, np.float64),
+                                  A, B, gA, gB,
+                                  mom.ctypes.data_as(_vp) if moments else None,
+                                  cond.ctypes.data_as(_vp)), "corrections")
+    out = {"A": A, "B": B, "gA": gA, "gB": gB, "cond": cond}
+    if moments:
+        out["moments"] = mom
+    return out
+
+
+def gradv(pos_h, V, vel, A, B, gA, gB, k=None, targets=None):
+    """P3: grad v (gv[i, alpha, beta] = d v^alpha / d x^beta), eq:gradv."""
+    pos = _pos(pos_h)
+    n = pos.shape[0]
+    tp, nt, keep = _tg(targets)
+    gv = np.full((n, 3, 3), np.nan)
+    c = lambda a: np.ascontiguousarray(a, np.float64)
+    _check(load().orc_gradv(n, pos, _k(pos, k), tp, nt, c(V), c(vel), c(A), c(B), c(gA), c(gB), gv),
+           "gradv")
+    return gv
+
+
+def forces(pos_h, vel, u, mass, V, A, B, gA, gB, gv, prm=None, k=None, targets=None):
+    """P4: acceleration, direct du/dt, signal velocity, max pair Q (eq:mom, eq:eng)."""
+    pos = _pos(pos_h)
+    n = pos.shape[0]
+    tp, nt, keep = _tg(targets)
+    prm = params() if prm is None else prm
+    acc = np.full((n, 3), np.nan)
+    dudt, vsig, qmax = (np.full(n, np.nan) for _ in range(3))
+    pairs = ctypes.c_longlong(0)
+    c = lambda a: np.ascontiguousarray(a, np.float64)
+    _check(load().orc_forces(n, pos, _k(pos, k), tp, nt, c(prm), c(V), c(mass), c(vel), c(u),
+                             c(A), c(B), c(gA), c(gB), c(gv), acc, dudt, vsig,
+                             qmax.ctypes.data_as(_vp), ctypes.byref(pairs)), "forces")
+    return {"acc": acc, "dudt": dudt, "vsig": vsig, "qmax": qmax, "pairs": int(pairs.value)}
+
+
+def compatible(pos_h, vel, u, mass, V, A, B, gA, gB, gv, vb, va, prm=None, k=None, targets=None):
+    """P5: sum_j Delta u_ij for the kick vb -> va (eq:compEng .. eq:fij)."""
+    pos = _pos(pos_h)
+    n = pos.shape[0]
+    tp, nt, keep = _tg(targets)
+    prm = params() if prm is None else prm
+    du = np.full(n, np.nan)
+    c = lambda a: np.ascontiguousarray(a, np.float64)
+    _check(load().orc_compatible(n, pos, _k(pos, k), tp, nt, c(prm), c(V), c(mass), c(vel), c(u),
+                                 c(A), c(B), c(gA), c(gB), c(gv), c(vb), c(va), du), "compatible")
+    return du
+
+
+# ------------------------------------------------------------ elementwise
+
+
+def thermo(V, mass, u, prm=None):
+    """eq:EOS with rho = m/V: rho, P = (gamma-1) rho u, c_s = sqrt(gamma P/rho), s = P/rho^gamma."""
+    prm = params() if prm is None else prm
+    g = prm[0]
+    rho = np.asarray(mass, np.float64) / V
+    P = (g - 1.0) * rho * u
+    cs = np.sqrt(g * P / rho)
+    s = P / rho ** g
+    return rho, P, cs, s
+
+
+def thacker(h, N, prm=None):
+    """eq:thacker: h~ = h (1 - lambda + lambda Delta_N), Delta_N^3 = N_res / N_i."""
+    prm = params() if prm is None else prm
+    d = np.cbrt(prm[2] / np.asarray(N, np.float64))
+    lam = np.where(d < 1.0, 0.2 * (1.0 + d * d), 0.2 * (1.0 + 1.0 / d ** 3))
+    return np.asarray(h, np.float64) * (1.0 - lam + lam * d)
+
+
+def evaluate(state, prm=None, k=None, targets=None):
+    """One full derivative evaluation P1 -> P2 -> P3 -> P4 on the FP32 state."""
+    prm = params() if prm is None else prm
+    pos = _pos(state["pos_h"])
+    vu = np.asarray(state["vel_u"], np.float64).reshape(-1, 4)
+    mass = np.asarray(state["mass"], np.float64)
+    vel, u = np.ascontiguousarray(vu[:, :3]), np.ascontiguousarray(vu[:, 3])
+    p1 = volumes(pos, k)
+    p2 = corrections(pos, p1["V"], k)
+    gv = gradv(pos, p1["V"], vel, p2["A"], p2["B"], p2["gA"], p2["gB"], k)
+    p4 = forces(pos, vel, u, mass, p1["V"], p2["A"], p2["B"], p2["gA"], p2["gB"], gv, prm, k, targets)
+    ev = dict(p1)
+    ev.update(p2)
+    ev["gv"] = gv
+    ev.update({"acc": p4["acc"], "dudt": p4["dudt"], "vsig": p4["vsig"], "qmax": p4["qmax"],
+               "pairs_union": p4["pairs"], "pairs_gather": p1["pairs"]})
+    ev["rho"], ev["P"], ev["cs"], ev["s"] = thermo(p1["V"], mass, u, prm)
+    ev["pos_h"], ev["vel"], ev["u"], ev["mass"] = pos.copy(), vel, u, mass
+    return ev
+
+
+def cfl_dt(ev, prm=None):
+    """Per-particle time step of Sec. 2.1 (adot = 0, no gravity so r_soft -> inf):
+    v_max = max(v_sig, c_s, sqrt(zeta Q/rho), h_hat |tr grad v|),
+    dt_i = min(C_CFL h_hat / v_max, sqrt(h_hat / |a|))."""
+    prm = params() if prm is None else prm
+    hh = ev["pos_h"][:, 3].astype(np.float64) / prm[1]
+    csq = np.sqrt(prm[9] * ev["qmax"] / ev["rho"])
+    div = np.abs(np.trace(ev["gv"], axis1=1, axis2=2))
+    vmax = np.maximum.reduce([ev["vsig"], ev["cs"], csq, hh * div])
+    amag = np.sqrt((ev["acc"] ** 2).sum(axis=1))
+    with np.errstate(divide="ignore"):
+        dt_h = np.where(vmax > 0, prm[8] * hh / vmax, np.inf)
+        dt_a = np.where(amag > 0, np.sqrt(hh / amag), np.inf)
+    return np.minimum(dt_h, dt_a)
+
+
+def h_iterate(pos_h, tol=1e-4, max_it=50, prm=None, k=None):
+    """Fixed-point solve of eq:hi by repeated eq:thacker updates: a particle is
+    converged once |Delta_N - 1| <= tol and keeps its h from then on."""
+    prm = params() if prm is None else prm
+    pos = _pos(pos_h).copy()
+    n = pos.shape[0]
+    done = np.zeros(n, bool)
+    it = 0
+    for it in range(1, max_it + 1):
+        p1 = volumes(pos, k)
+        d = np.cbrt(prm[2] / p1["N"])
+        done |= np.abs(d - 1.0) <= tol
+        if done.all():
+            return pos[:, 3].copy(), it, done
+        hn = thacker(pos[:, 3].astype(np.float64), p1["N"], prm)
+        pos[:, 3] = np.where(done, pos[:, 3], hn.astype(np.float32))
+    return pos[:, 3].copy(), it, done
+
+
+def energy_momentum(vel, u, mass):
+    """Total energy sum(1/2 m v^2 + m u) and momentum sum(m v) in FP64."""
+    vel = np.asarray(vel, np.float64)
+    m = np.asarray(mass, np.float64)
+    E = float((0.5 * m * (vel ** 2).sum(axis=1) + m * np.asarray(u, np.float64)).sum())
+    P = (m[:, None] * vel).sum(axis=0)
+    return E, P

@@ -1,0 +1,400 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+None of these re-types an oracle formula and compares it with itself: each
+checks a property the equations imply (normalisation, derivative, reproducing
+identities, conservation laws, symmetry, special cases) so that a dropped term,
+a wrong sign or a transposed index in the oracle fails at least one of them.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import crk as O
+from paper_2202_02840_gb300 import inputs
+
+GOLDEN = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_constants.json")))
+
+
+# ---------------------------------------------------------------- helpers
+
+def clustered(n=1500, seed=11, n_clumps=6, vel_sigma=0.3):
+    """Gaussian clumps in the periodic cube, h from the k-th neighbour distance."""
+    r = inputs.rng(seed)
+    centres = r.uniform(0, 1, (n_clumps, 3))
+    widths = r.uniform(0.04, 0.15, n_clumps)
+    lab = r.integers(0, n_clumps, n)
+    pos = np.mod(centres[lab] + r.normal(0, 1, (n, 3)) * widths[lab, None], 1.0)
+    pos = inputs._to_unit_f32(pos).astype(np.float64)
+    h = inputs.knn_h(pos, k=60, h_cap=0.3)
+    vel = r.normal(0, vel_sigma, (n, 3))
+    u = 10 ** r.normal(0, 0.5, n)
+    return inputs.pack(pos, h, vel, u, r.uniform(0.5, 1.5, n) / n)
+
+
+def pair_table(pos_h, mode=0, targets=None):
+    """(i, j, x_ij) for every pair of the oracle's neighbour sets (x in FP64 box units)."""
+    pos = np.asarray(pos_h, np.float32)
+    n = pos.shape[0]
+    tg = np.arange(n) if targets is None else np.asarray(targets)
+    counts, lists = O.neighbours(pos, mode=mode, targets=tg)
+    i = np.repeat(tg, counts)
+    j = lists.astype(np.int64)
+    q, H = O.fixed_point(pos)
+    dq = (q[i].astype(np.int64) - q[j].astype(np.int64) + 2 ** 31) % 2 ** 32 - 2 ** 31
+    return i, j, dq.astype(np.float64) * 2.0 ** -32
+
+
+def w_and_grad(x, h):
+    r = np.sqrt((x * x).sum(axis=1))
+    W, dW = O.kernel(r, h)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        g = np.where(r[:, None] > 0, dW[:, None] * x / r[:, None], 0.0)
+    return W, g
+
+
+def grad_rk_pairs(A, B, gA, gB, x, W, gW):
+    """grad W^R per pair from per-pair coefficient rows (eq:gRK)."""
+    s = 1.0 + (B * x).sum(axis=1)
+    gBx = np.einsum("pag,pa->pg", gB, x)
+    return gA * (s * W)[:, None] + A[:, None] * (gBx + B) * W[:, None] + (A * s)[:, None] * gW
+
+
+# ---------------------------------------------------------------- kernel
+
+def test_kernel_normalised_and_compact():
+    for h in (0.25, 0.013):
+        r = np.linspace(0.0, h, 20001)
+        W, _ = O.kernel(r, h)
+        integrand = 4.0 * np.pi * r * r * W
+        # composite Simpson
+        I = (r[1] - r[0]) / 3.0 * (integrand[0] + integrand[-1] + 4 * integrand[1:-1:2].sum()
+                                   + 2 * integrand[2:-1:2].sum())
+        assert abs(I - 1.0) < 1e-10
+        Wout, dWout = O.kernel(np.array([h, 1.5 * h]), h)
+        assert np.all(Wout == 0.0) and np.all(dWout == 0.0)
+        assert np.all(W[:-1] > 0.0)
+
+
+def test_kernel_peak_value_printed():
+    # eq:C4 prints the coefficient 495/(32 pi h^3): W at eta = 0
+    h = 0.2
+    W0, _ = O.kernel(np.array([0.0]), h)
+    assert GOLDEN["kernel_coefficient"]["value"] == "495/(32*pi)"
+    assert abs(W0[0] * h ** 3 - 495.0 / (32.0 * np.pi)) < 1e-12
+
+
+def test_kernel_derivative_matches_finite_differences():
+    h = 0.1
+    r = np.linspace(0.001, 0.099, 400)
+    d = 1e-6
+    Wp, _ = O.kernel(r + d, h)
+    Wm, _ = O.kernel(r - d, h)
+    _, dW = O.kernel(r, h)
+    fd = (Wp - Wm) / (2 * d)
+    assert np.max(np.abs(fd - dW)) < 1e-6 * np.max(np.abs(dW))
+    # C4: the first derivatives vanish at the support edge
+    _, dW_edge = O.kernel(np.array([h * (1 - 1e-4)]), h)
+    assert abs(dW_edge[0]) < 1e-12 * np.max(np.abs(dW))
+
+
+# ---------------------------------------------------------------- neighbours / cells
+
+def perfect_lattice(n_side, h_spacings=4.0, u=1.0):
+    pos = inputs.lattice(n_side)
+    n = pos.shape[0]
+    return inputs.pack(pos, h_spacings / n_side, np.zeros((n, 3)), u, 1.0 / n)
+
+
+def test_lattice_neighbour_count_and_N_res():
+    st = perfect_lattice(16)
+    counts, _ = O.neighbours(st["pos_h"], mode=0, k=0)
+    g = np.arange(-4, 5)
+    X, Y, Z = np.meshgrid(g, g, g, indexing="ij")
+    inside = int(((X ** 2 + Y ** 2 + Z ** 2) < 16).sum())   # strict support, self included
+    assert np.all(counts == inside)
+    p1 = O.volumes(st["pos_h"], k=0)
+    # Sec. 2.6: n_h = 4 corresponds to about N_res = 268 neighbours
+    target = 4.0 / 3.0 * np.pi * GOLDEN["n_h"]["value"] ** 3
+    assert abs(target - GOLDEN["N_res"]["value"]) < 0.1
+    assert np.max(np.abs(p1["N"] / target - 1.0)) < 2e-3
+    assert np.ptp(p1["N"]) < 1e-9 * target        # every lattice site identical
+
+
+@pytest.mark.parametrize("maker", ["uniform", "clustered"])
+def test_grid_search_equals_brute_force(maker):
+    st = inputs.uniform(16) if maker == "uniform" else clustered(3000)
+    for mode in (0, 1):
+        cb, lb = O.neighbours(st["pos_h"], mode=mode, k=0)
+        for k in (1, 2, 3, 4):
+            cg, lg = O.neighbours(st["pos_h"], mode=mode, k=k)
+            assert np.array_equal(cb, cg) and np.array_equal(lb, lg)
+
+
+def test_pair_set_symmetric_and_contains_gather():
+    st = clustered(1200)
+    n = st["pos_h"].shape[0]
+    i, j, _ = pair_table(st["pos_h"], mode=1)
+    key = set(zip(i.tolist(), j.tolist()))
+    assert all((b, a) in key for a, b in key)
+    gi, gj, _ = pair_table(st["pos_h"], mode=0)
+    assert all((a, b) in key for a, b in zip(gi.tolist(), gj.tolist()) if a != b)
+    assert not any(a == b for a, b in key)
+    assert len(key) > n
+
+
+def test_cells_morton_and_stable_order():
+    st = clustered(2000)
+    key, perm, k, start = O.cells(st["pos_h"], kmax=7)
+    q, _ = O.fixed_point(st["pos_h"])
+    c = q >> 22
+    # de-interleave the 30-bit key
+    dec = np.zeros_like(c)
+    for b in range(10):
+        for a in range(3):
+            dec[:, a] |= ((key >> (3 * b + a)) & 1) << b
+    assert np.array_equal(dec, c)
+    ks = key[perm]
+    assert np.all(np.diff(ks.astype(np.int64)) >= 0)
+    ties = ks[1:] == ks[:-1]
+    assert np.all(perm[1:][ties] > perm[:-1][ties])              # stable
+    assert sorted(perm.tolist()) == list(range(len(perm)))
+    hmax = st["pos_h"][:, 3].max()
+    assert 2.0 ** -k >= hmax and (k == 7 or 2.0 ** -(k + 1) < hmax)
+    cell = ks >> (30 - 3 * k)
+    counts = np.bincount(cell, minlength=8 ** k)
+    assert np.array_equal(np.diff(start), counts) and start[0] == 0 and start[-1] == len(perm)
+
+
+# ---------------------------------------------------------------- RK corrections
+
+@pytest.mark.parametrize("maker", ["uniform", "clustered"])
+def test_reproducing_identities(maker):
+    st = inputs.uniform(16) if maker == "uniform" else clustered(1500)
+    pos = st["pos_h"]
+    p1 = O.volumes(pos, k=0)
+    V = p1["V"]
+    p2 = O.corrections(pos, V, k=0)
+    i, j, x = pair_table(pos, mode=0)
+    h = pos[:, 3].astype(np.float64)
+    W, gW = w_and_grad(x, h[i])
+    A, B, gA, gB = p2["A"][i], p2["B"][i], p2["gA"][i], p2["gB"][i]
+    WR = A * (1.0 + (B * x).sum(axis=1)) * W
+    n = pos.shape[0]
+    zero = np.bincount(i, weights=V[j] * WR, minlength=n)
+    first = np.stack([np.bincount(i, weights=V[j] * x[:, a] * WR, minlength=n) for a in range(3)], 1)
+    assert np.max(np.abs(zero - 1.0)) < 1e-11
+    assert np.max(np.abs(first)) < 1e-11 * h.max()
+    gR = grad_rk_pairs(A, B, gA, gB, x, W, gW)
+    g0 = np.stack([np.bincount(i, weights=V[j] * gR[:, g], minlength=n) for g in range(3)], 1)
+    scale = np.max(np.abs(gR)) * np.max(V) * 300
+    assert np.max(np.abs(g0)) < 1e-11 * scale
+    # sum_j V_j x_ij^a d_b W^R_ij = -delta_ab
+    g1 = np.stack([np.stack([np.bincount(i, weights=V[j] * x[:, a] * gR[:, b], minlength=n)
+                             for b in range(3)], 1) for a in range(3)], 1)
+    assert np.max(np.abs(g1 + np.eye(3)[None])) < 1e-10
+
+
+def test_correction_gradients_match_finite_differences():
+    """grad A, grad B are gradients with respect to the evaluation point with
+    every particle (i included) held fixed, as in eq:gRK: that is the derivative
+    under which the RK interpolant reproduces linear fields.  Check them by
+    central differences of A, B seen by a zero-volume probe with particle i's h
+    placed at x_i +- d (the probe adds nothing to any sum)."""
+    st = clustered(1500, seed=5)
+    pos = st["pos_h"].copy()
+    n = pos.shape[0]
+    V = O.volumes(pos, k=0)["V"]
+    base = O.corrections(pos, V, k=0)
+    tg = inputs.rng(9).choice(n, 12, replace=False)
+    d = 2.0 ** -16
+    Vp = np.append(V, 0.0)
+    checked = 0
+    for i in tg:
+        for g in range(3):
+            if not (2 * d < pos[i, g] < 1 - 2 * d):
+                continue
+            res = []
+            for sgn in (1, -1):
+                pp = np.vstack([pos, pos[i:i + 1]])
+                pp[n, g] += np.float32(sgn * d)
+                c = O.corrections(pp, Vp, k=0, targets=[n])
+                res.append((c["A"][n], c["B"][n]))
+            fdA = (res[0][0] - res[1][0]) / (2 * d)
+            fdB = (res[0][1] - res[1][1]) / (2 * d)
+            sA = max(1.0, abs(base["gA"][i]).max())
+            sB = max(1.0, abs(base["gB"][i]).max())
+            assert abs(fdA - base["gA"][i][g]) < 2e-5 * sA
+            assert np.max(np.abs(fdB - base["gB"][i][:, g])) < 2e-5 * sB
+            checked += 1
+    assert checked >= 30
+
+
+# ---------------------------------------------------------------- grad v, viscosity
+
+def test_gradv_reproduces_linear_field():
+    st = inputs.uniform(16)
+    pos = st["pos_h"]
+    x = pos[:, :3].astype(np.float64)
+    M = np.array([[0.3, -0.2, 0.1], [0.05, -0.4, 0.2], [0.7, 0.1, 0.25]])
+    vel = x @ M.T + np.array([1.0, -2.0, 0.5])
+    p1 = O.volumes(pos, k=0)
+    p2 = O.corrections(pos, p1["V"], k=0)
+    gv = O.gradv(pos, p1["V"], vel, p2["A"], p2["B"], p2["gA"], p2["gB"], k=0)
+    h = pos[:, 3].max()
+    interior = np.all((x > h + 1e-3) & (x < 1 - h - 1e-3), axis=1)
+    assert interior.sum() > 100
+    assert np.max(np.abs(gv[interior] - M[None])) < 1e-10
+
+
+def _viscous_setup(nonlinear, prm=None):
+    n_side = 24
+    pos = inputs.jittered_lattice(n_side, 0.05, seed=21)
+    x = inputs._to_unit_f32(pos).astype(np.float64)
+    M = np.array([[-0.5, 0.2, 0.0], [0.1, -0.3, 0.05], [0.0, 0.1, -0.4]])
+    vel = (x - 0.5) @ M.T
+    if nonlinear:
+        vel[:, 0] += 2.0 * (x[:, 0] - 0.5) ** 2
+    n = x.shape[0]
+    st = inputs.pack(x, 3.0 / n_side, vel, 1.0, 1.0 / n)
+    ev = O.evaluate(st, prm=prm, k=0)
+    h = 3.0 / n_side
+    interior = np.all((x > 2 * h + 0.01) & (x < 1 - 2 * h - 0.01), axis=1)
+    return ev, interior
+
+
+def test_viscosity_switches_off_for_linear_flow():
+    """Sec. 1.2: for linear velocity fields the projected difference u_hat_ij
+    vanishes and the limited viscosity switches off; plain MG83 (limiter
+    disabled by eta_crit >> 1, so phi = 0) does not."""
+    ev, interior = _viscous_setup(nonlinear=False)
+    assert interior.sum() > 500
+    p = ev["P"][interior].max()
+    # the stored FP32 velocities are linear only to ~6e-8 relative
+    assert np.max(ev["qmax"][interior]) < 1e-6 * p
+    ev_mg, _ = _viscous_setup(nonlinear=False, prm=O.params(eta_crit=10.0, eta_fold=0.01))
+    assert np.min(ev_mg["qmax"][interior]) > 1e-3 * p
+    ev2, _ = _viscous_setup(nonlinear=True)
+    assert np.max(ev2["qmax"][interior]) > 1e-4 * p
+
+
+# ---------------------------------------------------------------- forces / energy
+
+def test_momentum_conserved_any_input():
+    st = clustered(1500, seed=3)
+    ev = O.evaluate(st, k=0)
+    F = ev["acc"] * ev["mass"][:, None]
+    assert np.max(np.abs(F.sum(axis=0))) < 1e-12 * np.abs(F).sum()
+
+
+def test_direct_energy_rate_conserves_total_energy():
+    st = clustered(1500, seed=4)
+    ev = O.evaluate(st, k=0)
+    m = ev["mass"]
+    dEk = (m[:, None] * ev["vel"] * ev["acc"]).sum()
+    dEu = (m * ev["dudt"]).sum()
+    scale = np.abs(m[:, None] * ev["vel"] * ev["acc"]).sum() + np.abs(m * ev["dudt"]).sum()
+    assert abs(dEk + dEu) < 1e-11 * scale
+
+
+def test_compatible_energy_conserves_each_kick():
+    st = clustered(1500, seed=6)
+    ev = O.evaluate(st, k=0)
+    m = ev["mass"]
+    tau = 0.3 * np.min(O.cfl_dt(ev))
+    vb = ev["vel"]
+    va = vb + tau * ev["acc"]
+    du = tau * O.compatible(st["pos_h"], ev["vel"], ev["u"], m, ev["V"], ev["A"], ev["B"],
+                            ev["gA"], ev["gB"], ev["gv"], vb, va, k=0)
+    dK = 0.5 * (m * ((va ** 2).sum(1) - (vb ** 2).sum(1))).sum()
+    dU = (m * du).sum()
+    assert abs(dK + dU) < 1e-11 * (np.abs(0.5 * m * ((va ** 2).sum(1) - (vb ** 2).sum(1))).sum())
+    # entropy-weighted split differs from an even split but conserves the same total
+    assert np.max(np.abs(du)) > 0
+
+
+def test_perfect_lattice_is_in_equilibrium():
+    st = perfect_lattice(16)
+    ev = O.evaluate(st, k=0)
+    assert np.max(np.abs(ev["B"])) < 1e-10
+    assert np.max(np.abs(ev["gA"])) < 1e-8
+    assert np.max(np.abs(ev["acc"])) < 1e-9
+    assert np.max(np.abs(ev["dudt"])) < 1e-12
+    assert np.ptp(ev["A"]) < 1e-12
+
+
+def test_galilean_boost_invariance():
+    st = clustered(1200, seed=8)
+    ev = O.evaluate(st, k=0)
+    st2 = dict(st)
+    vu = st["vel_u"].copy()
+    vu[:, :3] += np.array([0.5, -0.25, 0.125], np.float32)
+    st2["vel_u"] = vu
+    ev2 = O.evaluate(st2, k=0)
+    # boosted float32 velocities differ from the original by the exact boost only
+    # where the sum was exact; compare with a tolerance at round-off of v.
+    assert np.max(np.abs(ev2["acc"] - ev["acc"])) < 1e-5 * np.abs(ev["acc"]).max()
+    assert np.max(np.abs(ev2["vsig"] - ev["vsig"])) < 1e-5 * ev["vsig"].max()
+
+
+def test_sph_limit_two_particle_repulsion():
+    """With A = 1, B = 0, grad A = grad B = 0 the pair force is the textbook
+    symmetric SPH pressure force 1/2 V_i V_j (P_i + P_j)(|W'(r,h_i)| + |W'(r,h_j)|),
+    directed away from the other particle."""
+    pos = np.array([[0.40, 0.5, 0.5], [0.43, 0.52, 0.49]])
+    h = np.array([0.08, 0.05])
+    st = inputs.pack(pos, h, np.zeros((2, 3)), np.array([1.0, 2.0]), np.array([1.0, 1.5]))
+    p = st["pos_h"]
+    V = np.array([0.7, 1.3])
+    A, B, gA, gB = np.ones(2), np.zeros((2, 3)), np.zeros((2, 3)), np.zeros((2, 3, 3))
+    gv = np.zeros((2, 3, 3))
+    vel = np.zeros((2, 3))
+    u = st["vel_u"][:, 3].astype(np.float64)
+    m = st["mass"].astype(np.float64)
+    f = O.forces(p, vel, u, m, V, A, B, gA, gB, gv, k=0)
+    i, j, x = pair_table(p, mode=1, targets=[0])
+    r = np.sqrt((x[0] ** 2).sum())
+    _, dWi = O.kernel(np.array([r]), p[0, 3])
+    _, dWj = O.kernel(np.array([r]), p[1, 3])
+    gam = 5.0 / 3.0
+    P = (gam - 1.0) * (m / V) * u
+    mag = 0.5 * V[0] * V[1] * (P[0] + P[1]) * (abs(dWi[0]) + abs(dWj[0]))
+    F0 = f["acc"][0] * m[0]
+    assert np.allclose(F0, mag * x[0] / r, rtol=1e-12, atol=0)
+    assert np.allclose(f["acc"][1] * m[1], -F0, rtol=1e-12)
+
+
+# ---------------------------------------------------------------- h, time step
+
+def test_thacker_fixed_point_and_continuity():
+    prm = O.params()
+    h = np.full(5, 0.1)
+    assert np.allclose(O.thacker(h, np.full(5, 268.0), prm), h, rtol=0, atol=0)
+    eps = 1e-9
+    lo = O.thacker([1.0], [268.0 * (1 + eps)], prm)[0]
+    hi = O.thacker([1.0], [268.0 * (1 - eps)], prm)[0]
+    assert abs(lo - 1.0) < 1e-9 and abs(hi - 1.0) < 1e-9 and lo < 1.0 < hi
+    # too many neighbours shrinks h, too few grows it
+    assert O.thacker([1.0], [400.0], prm)[0] < 1.0 < O.thacker([1.0], [150.0], prm)[0]
+
+
+def test_h_iteration_converges_to_target_neighbour_count():
+    st = inputs.uniform(16)
+    pos = st["pos_h"].copy()
+    pos[:, 3] *= np.float32(0.8)
+    h, it, done = O.h_iterate(pos, tol=1e-4, max_it=60, k=0)
+    assert done.all() and it < 60
+    pos[:, 3] = h
+    N = O.volumes(pos, k=0)["N"]
+    assert np.max(np.abs(np.cbrt(268.0 / N) - 1.0)) <= 1e-4 + 1e-12
+
+
+def test_cfl_of_gas_at_rest_is_sound_crossing():
+    st = perfect_lattice(14, h_spacings=3.5)
+    ev = O.evaluate(st, k=0)
+    dt = O.cfl_dt(ev)
+    gam = 5.0 / 3.0
+    cs = np.sqrt(gam * (gam - 1.0) * 1.0)
+    hh = st["pos_h"][:, 3].astype(np.float64) / 4.0
+    assert np.allclose(dt, 0.25 * hh / cs, rtol=1e-9)

@@ -1,0 +1,343 @@
+#!/usr/bin/env python
+"""Benchmark of the CRKSPH pair-interaction engine on one GB300.
+
+Workload: 128^3 = 2,097,152 particles of clustered gas (Zel'dovich-displaced
+lattice, P(k) ~ k^-2, log-normal u) in the periodic unit cube.  One step is a
+full KDK hydro step (crk_step): half kick with the cached rates and its
+compatible-energy pass, drift, cell rebuild, P1 volumes, P2 corrections,
+P3 grad v, P4 forces, second half kick and its compatible-energy pass, the
+Thacker h update and the CFL time step.
+
+Metric: pair interactions per second = (3 * gather pairs + 3 * ordered pair-set
+pairs) per step / step time (P1, P2, P3 walk gather(i); P4 and the two P5
+passes walk the pair set), and the step time in ms.
+
+Prints one JSON line.  --impl reference times the FP64 CPU oracle instead
+(a bounded sample of the same workload per step, all host cores).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "CRKSPH pair interactions/s and hydro-step ms at 128^3 vs plain FP32 GPU, at stated err"
+UNIT = "pair interactions/s"
+WORKLOAD = "zeldovich-128^3: clustered gas, Zel'dovich lattice displacement, P(k)~k^-2, log-normal u"
+
+# Algorithmic FP32 flops per pair unit of each pass (FMA = 2, add/mul/min/max = 1,
+# div/sqrt/exp = 1), counted from the operations the paper's formulas require
+# (derivation in the design doc).  P1-P3 count per gather pair; P4 and P5 count per
+# UNORDERED pair of the pair set (both kernel sides, limiter, viscosity, force).
+FLOPS_PER_UNIT = {"P1 volumes": 19, "P2 corrections": 104, "P3 grad v": 71, "P4 forces": 262,
+                  "P5 compatible energy": 251}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class Clocks:
+    """nvidia-smi sampler for the timed region (SM clock and throttle reasons)."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if f[5 + k].lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def alu_peak_tflops(sm_count, mhz):
+    """FP32 FMA issue peak: SMs x 128 lanes x 2 flops x clock."""
+    return sm_count * 128 * 2 * mhz * 1e6 / 1e12
+
+
+# --------------------------------------------------------------------- CPU oracle
+
+def oracle_sample(st, n_targets, seed=0):
+    """Time the FP64 oracle's passes P1..P5 on a random sample of target
+    particles of the workload.  Per-particle inputs of the non-target particles
+    are a uniform placeholder state (values do not change the work done)."""
+    from oracle import crk as O
+    pos = st["pos_h"]
+    n = pos.shape[0]
+    tg = np.sort(np.random.default_rng(seed).choice(n, n_targets, replace=False)).astype(np.int32)
+    vel = st["vel_u"][:, :3].astype(np.float64)
+    u = st["vel_u"][:, 3].astype(np.float64)
+    m = st["mass"].astype(np.float64)
+    V = np.full(n, 1.0 / n)
+    A = np.ones(n)
+    B = np.zeros((n, 3))
+    gA = np.zeros((n, 3))
+    gB = np.zeros((n, 3, 3))
+    gv = np.zeros((n, 3, 3))
+    t0 = time.perf_counter()
+    p1 = O.volumes(pos, targets=tg)
+    V[tg] = p1["V"][tg]
+    p2 = O.corrections(pos, V, targets=tg)
+    gvt = O.gradv(pos, V, vel, A, B, gA, gB, targets=tg)
+    p4 = O.forces(pos, vel, u, m, V, A, B, gA, gB, gv, targets=tg)
+    O.compatible(pos, vel, u, m, V, A, B, gA, gB, gv, vel, vel, targets=tg)
+    O.compatible(pos, vel, u, m, V, A, B, gA, gB, gv, vel, vel, targets=tg)
+    dt = time.perf_counter() - t0
+    pairs = 3 * p1["pairs"] + 3 * p4["pairs"]
+    del p2, gvt
+    return pairs, dt
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from oracle import crk as O
+    from paper_2202_02840_gb300 import inputs
+    st = inputs.zeldovich(args.n_side)
+    cores = O.num_threads()
+    # size the per-step sample so that warmup + steps end within a few minutes
+    probe = 512
+    pairs, dt = oracle_sample(st, probe, seed=1)
+    per_target = dt / probe
+    budget = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    ns = int(max(probe, min(st["pos_h"].shape[0], budget / per_target)))
+    for w in range(args.warmup):
+        oracle_sample(st, ns, seed=100 + w)
+    tot_pairs, tot_t = 0, 0.0
+    for k in range(args.steps):
+        p, t = oracle_sample(st, ns, seed=1000 + k)
+        tot_pairs += p
+        tot_t += t
+    value = tot_pairs / tot_t
+    sample = ("FP64 oracle passes P1,P2,P3,P4,P5,P5 on %d random target particles of the %d^3 workload "
+              "per step (%d steps)" % (ns, args.n_side, args.steps))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "n": args.n_side ** 3},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# --------------------------------------------------------------------- GPU arm
+
+def run_gpu(args):
+    import torch
+    import __graft_entry__
+    from paper_2202_02840_gb300 import crk, inputs
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    __graft_entry__.build()
+
+    st = inputs.zeldovich(args.n_side)
+    n = st["pos_h"].shape[0]
+    pos0 = torch.from_numpy(st["pos_h"]).to(dev)
+    vel0 = torch.from_numpy(st["vel_u"]).to(dev)
+    mass = torch.from_numpy(st["mass"]).to(dev)
+    pos, vel = pos0.clone(), vel0.clone()
+    ctx = crk.crk_create(precision=args.precision)
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    # ---------------- device-resident timing
+    for _ in range(args.warmup):
+        crk.crk_step(ctx, pos, vel, mass, 0.0)
+    barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    crk.crk_profile(ctx, True)
+    launches0 = crk.crk_launches(ctx)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    pairs = 0
+    ev0.record(stream)
+    diags = []
+    for _ in range(args.steps):
+        d = crk.crk_step(ctx, pos, vel, mass, 0.0, diag=True)
+        diags.append(d)
+        pairs += 3 * d["pairs_gather"] + 3 * d["pairs_union"]
+    ev1.record(stream)
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    launches = crk.crk_launches(ctx) - launches0
+    prof_ms, prof_cnt, _ = crk.crk_profile_read(ctx)
+    crk.crk_profile(ctx, False)
+    clk = clocks.stop()
+
+    # ---------------- end to end through host buffers (pinned), same step count
+    h_pos = torch.from_numpy(st["pos_h"]).pin_memory()
+    h_vel = torch.from_numpy(st["vel_u"]).pin_memory()
+    h_mass = torch.from_numpy(st["mass"]).pin_memory()
+    d_pos = torch.empty_like(pos0)
+    d_vel = torch.empty_like(vel0)
+    d_mass = torch.empty_like(mass)
+    e2e_ctx = crk.crk_create(precision=args.precision)
+    for _ in range(max(1, args.warmup)):
+        d_pos.copy_(h_pos, non_blocking=True)
+        d_vel.copy_(h_vel, non_blocking=True)
+        d_mass.copy_(h_mass, non_blocking=True)
+        crk.crk_step(e2e_ctx, d_pos, d_vel, d_mass, 0.0)
+        h_pos.copy_(d_pos, non_blocking=True)
+        h_vel.copy_(d_vel, non_blocking=True)
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e2e_pairs = 0
+    e0.record(stream)
+    for _ in range(args.steps):
+        d_pos.copy_(h_pos, non_blocking=True)
+        d_vel.copy_(h_vel, non_blocking=True)
+        d_mass.copy_(h_mass, non_blocking=True)
+        d = crk.crk_step(e2e_ctx, d_pos, d_vel, d_mass, 0.0, diag=True)
+        e2e_pairs += 3 * d["pairs_gather"] + 3 * d["pairs_union"]
+        h_pos.copy_(d_pos, non_blocking=True)
+        h_vel.copy_(d_vel, non_blocking=True)
+    e1.record(stream)
+    barrier()
+    e2e_ms = e0.elapsed_time(e1)
+    e2ectx_close = e2e_ctx.close()
+
+    # ---------------- aggregate over ranks (max time, summed work)
+    t = torch.tensor([ms, e2e_ms], dtype=torch.float64, device=dev)
+    w = torch.tensor([float(pairs), float(e2e_pairs)], dtype=torch.float64, device=dev)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(w, op=dist.ReduceOp.SUM)
+    ms_max, e2e_max = float(t[0]), float(t[1])
+    value = float(w[0]) / (ms_max / 1e3)
+    e2e_value = float(w[1]) / (e2e_max / 1e3)
+
+    # ---------------- roofline of the dominant pass
+    per_step_pairs = {"P1 volumes": diags[-1]["pairs_gather"], "P2 corrections": diags[-1]["pairs_gather"],
+                      "P3 grad v": diags[-1]["pairs_gather"],
+                      "P4 forces": diags[-1]["pairs_union"] / 2.0,
+                      "P5 compatible energy": diags[-1]["pairs_union"] / 2.0}
+    dominant = max(FLOPS_PER_UNIT, key=lambda k: prof_ms.get(k, 0.0))
+    launch_ms = prof_ms[dominant] / max(1, prof_cnt[dominant])
+    achieved = FLOPS_PER_UNIT[dominant] * per_step_pairs[dominant] / (launch_ms / 1e3) / 1e12
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    peaks = measured_peaks()
+    max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = alu_peak_tflops(sm_count, max_mhz)
+    roofline = {"bound": "alu", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_basis": "FP32 FMA issue: %d SMs x 128 lanes x 2 flops x %.0f MHz (max SM clock)"
+                              % (sm_count, max_mhz),
+                "launch_ms": launch_ms,
+                "pass_ms_per_step": {k: v / args.steps for k, v in prof_ms.items()}}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "n": n, "precision": "mixed" if args.precision else "plain",
+                           "parallelism": "replicas" if world > 1 else "single",
+                           "l2": "step working set ~%.1f GB > L2 (129 MB)" % (n * 460 / 1e9),
+                           "pairs_per_step": pairs / args.steps},
+                "roofline": roofline,
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": n * 36,
+                        "d2h_bytes_per_step": n * 32},
+                "gpu_launches": launches, "clocks": clk}
+        if not args.no_cpu_baseline and world == 1:
+            from oracle import crk as O
+            probe = 256
+            p, dt = oracle_sample(st, probe, seed=1)
+            ns = int(max(probe, min(n, args.cpu_seconds / (dt / probe))))
+            p, dt = oracle_sample(st, ns, seed=2)
+            line["cpu_baseline"] = {"value": p / dt, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+                                    "sample": "FP64 oracle passes P1,P2,P3,P4,P5,P5 on %d random target "
+                                              "particles of the workload (%.1f s)" % (ns, dt)}
+        print(json.dumps(line))
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n-side", type=int, default=128)
+    ap.add_argument("--precision", type=int, default=1, choices=[0, 1])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

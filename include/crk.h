@@ -1,0 +1,238 @@
+/*
+ * crk.h -- C ABI of the GB300 CRKSPH pair-interaction engine.
+ *
+ * The engine runs the particle-pair passes of the conservative reproducing-
+ * kernel SPH (CRKSPH) scheme used by CRK-HACC (arXiv 2202.02840): volumes,
+ * reproducing-kernel corrections, velocity gradients, corrected-kernel
+ * momentum and energy pair sums with limited artificial viscosity, and the
+ * compatible-energy update, on one GPU (sm_103a).
+ *
+ * Conventions shared by every entry point
+ *  - Units: natural units (a = 1, adot = 0, p = v), periodic unit cube.
+ *  - Particle arrays are caller-owned DEVICE pointers, length n, in the
+ *    caller's particle order (array-of-records, row-major):
+ *      pos_h  float[4n]  (x, y, z, h); x,y,z in [0,1), 0 < h < 1/3
+ *      vel_u  float[4n]  (vx, vy, vz, u)
+ *      mass   float[n]
+ *      V, Nngb, A, dudt, vsig, qmax, du      float[n]
+ *      B, gradA, accel, vel_before, vel_after float[3n]
+ *      gradB  float[9n]  [i][alpha][gamma] = d B^alpha / d x^gamma
+ *      gradv  float[9n]  [i][alpha][beta]  = d v^alpha / d x^beta
+ *    All device pointers must be 16-byte aligned and must not alias each
+ *    other unless stated.
+ *  - Library-owned memory (sorted particle copies, sort scratch, tiles, the
+ *    tile tree and interaction lists) belongs to the crk_ctx; it is allocated
+ *    by crk_create / grown by crk_build_cells and freed by crk_destroy.
+ *  - Streams: every call enqueues its work on `stream` (a cudaStream_t, NULL =
+ *    legacy default stream) and returns without waiting, except where a call
+ *    says it synchronises.  Outputs are valid once the stream reaches them.
+ *  - Errors: functions return CRK_OK (0) or a negative CRK_E* code; the
+ *    message of the last failure is available from crk_last_error(ctx).  A
+ *    call that fails leaves its outputs unspecified.  Device-side failures
+ *    (invalid inputs found by a kernel, exhausted capacity) are reported by
+ *    the next synchronising call.
+ *
+ * Paper readings used at this boundary (where the paper is silent):
+ *  - neighbour predicate: positions and h in uint32 fixed point q =
+ *    floor(s 2^32), H = floor(h 2^32); minimum-image integer separation;
+ *    gather(i) = {j : |dq|^2 < H_i^2} (self included); pair set =
+ *    {(i,j), i != j : |dq|^2 < max(H_i, H_j)^2}; x_ij = dq 2^-32.
+ *  - gradients in eq:gRK are taken with respect to the evaluation point at
+ *    fixed h and fixed neighbour volumes; grad W^R_ji uses particle j's
+ *    coefficients with x_ji = -x_ij.
+ *  - rho_i = m_i / V_i; P = (gamma - 1) rho u; c_s = sqrt(gamma P / rho).
+ */
+#ifndef CRK_H
+#define CRK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CRK_OK 0
+#define CRK_EINVAL (-1)     /* invalid argument or invalid particle data */
+#define CRK_ENOMEM (-2)     /* device allocation failed */
+#define CRK_ECUDA (-3)      /* a CUDA runtime call or kernel launch failed */
+#define CRK_ETIMEOUT (-4)   /* a bounded device-side wait gave up */
+#define CRK_ENONCONV (-5)   /* the h fixed-point iteration did not converge */
+#define CRK_ECAPACITY (-6)  /* a fixed-capacity buffer overflowed */
+#define CRK_ESTATE (-7)     /* call out of order (e.g. a pass before crk_build_cells) */
+
+typedef struct crk_ctx crk_ctx;
+
+/* Method and engine parameters; crk_default_params fills the paper's values. */
+typedef struct {
+    double gamma;     /* adiabatic index, 5/3 (Sec. 1.1, eq:EOS) */
+    double n_h;       /* particles per smoothing length, 4 (Sec. 2.6) */
+    double N_res;     /* target neighbour count, 268 (Sec. 2.6, eq:hi) */
+    double C_l, C_q;  /* viscosity coefficients 2, 1 (eq:visc) */
+    double eps;       /* 0.1 (eq:mu) */
+    double eta_crit;  /* 1/n_h (eq:phiad) */
+    double eta_fold;  /* 0.2/n_h (eq:phiad) */
+    double C_cfl;     /* 0.25 (Sec. 2.1 time-step criteria) */
+    double zeta;      /* 4 (Sec. 2.1, c_sq = sqrt(zeta Q / rho)) */
+    double h_min;     /* lower clamp of the evolved h (box units) */
+    double h_max;     /* upper clamp of the evolved h (< 1/3) */
+    double dt_max;    /* cap of the CFL time step */
+    int precision;    /* 0 = plain FP32 (FP32 sums, FP32 3x3 inverse);
+                         1 = mixed (FP32 pair sums with compensated momentum and
+                             energy accumulation, FP64 3x3 inverse) */
+    int kmax;         /* finest chaining-mesh level reported by crk_cells (<= 7) */
+    int reserved[6];
+} crk_params;
+
+/* Per-step diagnostics (host memory), all reductions in FP64. */
+typedef struct {
+    double dt;            /* time step used */
+    double dt_next;       /* CFL time step of the evaluation at the end of the step */
+    double E_kin, E_int;  /* sum 1/2 m v^2, sum m u after the step */
+    double P[3];          /* total momentum sum m v after the step */
+    long long pairs_gather;  /* |gather(i)| - 1 summed over i, last evaluation */
+    long long pairs_union;   /* ordered pairs of the pair set, last evaluation */
+} crk_diag;
+
+/* Fill *p with the paper's values (see crk_params).  Never fails for p != NULL. */
+int crk_default_params(crk_params *p);
+
+/* Create an engine on the current CUDA device.  *out receives the context.
+ * CRK_EINVAL for NULL pointers or parameters out of range, CRK_ECUDA/ENOMEM
+ * if the device cannot be used. */
+int crk_create(const crk_params *p, crk_ctx **out);
+
+/* Free every library-owned buffer.  Synchronises the device. */
+int crk_destroy(crk_ctx *ctx);
+
+/* Message of the last failed call on ctx (static storage inside ctx). */
+const char *crk_last_error(const crk_ctx *ctx);
+
+/* Wait for `stream`, then report device-side errors recorded since the last
+ * synchronising call (CRK_EINVAL for invalid particles, CRK_ECAPACITY ...). */
+int crk_sync(crk_ctx *ctx, void *stream);
+
+/* Chaining-mesh binning and interaction lists (Sec. 2.3 short-range solver
+ * data structures; D1-D4 analogue): fixed-point keys, 30-bit Morton keys,
+ * stable LSD radix sort, sorted particle copies, tiles of 32 consecutive
+ * particles with fixed-point bounding boxes and max H, an implicit binary
+ * tree over tiles, and per-tile interaction lists for the gather predicate and
+ * for the pair set.  pos_h is read, never written.  Synchronises `stream`
+ * once to size the lists (grows them as needed).  CRK_EINVAL if any
+ * coordinate is outside [0,1) or non-finite, or h is not in (0, 1/3). */
+int crk_build_cells(crk_ctx *ctx, int n, const float *pos_h, void *stream);
+
+/* Binning of the last build, for inspection (device outputs, may be NULL):
+ *  keys[n]      30-bit Morton keys in sorted order (x in bit 0 of each triple,
+ *               from the top 10 bits of the fixed-point coordinates)
+ *  perm[n]      caller index of each sorted slot (stable in the caller index)
+ *  cell_start   int[8^k + 1]: first sorted slot whose cell >= c, k = the
+ *               chaining-mesh level, the largest k <= kmax with 2^-k >= max h
+ * *k_out (host) receives k.  Synchronises `stream`. */
+int crk_cells(crk_ctx *ctx, uint32_t *keys, int32_t *perm, int32_t *cell_start, int *k_out,
+              void *stream);
+
+/* Counts of the last build (host outputs, may be NULL): number of tiles,
+ * gather-list and pair-list tile-pair entries.  Synchronises `stream`. */
+int crk_build_stats(crk_ctx *ctx, int *ntiles, long long *gather_tile_pairs,
+                    long long *union_tile_pairs, void *stream);
+
+/* Neighbour sets of the last build, for inspection: mode 0 = gather(i)
+ * (self included), mode 1 = the pair set of i.  Device outputs in caller
+ * order: count[n] = set size, hash[n] = sum over the set of fmix32(j + 1)
+ * modulo 2^32, with j the caller index and fmix32 the MurmurHash3 32-bit
+ * finaliser (x ^= x>>16; x *= 0x85ebca6b; x ^= x>>13; x *= 0xc2b2ae35;
+ * x ^= x>>16).  Equal (count, hash) for every particle means equal sets up
+ * to a 2^-32 collision chance per particle. */
+int crk_neighbours(crk_ctx *ctx, int mode, int32_t *count, uint32_t *hash, void *stream);
+
+/* P1, eq:vol and eq:hi: n_i = sum_{j in gather(i)} W(|x_ij|, h_i) with the
+ * C4 Wendland kernel of eq:C4, V_i = 1/n_i, Nngb_i = 4/3 pi h_i^3 n_i.
+ * Outputs V[n], Nngb[n] (Nngb may be NULL).  *pairs (host, may be NULL)
+ * receives sum_i (|gather(i)| - 1) and makes the call synchronise. */
+int crk_volumes(crk_ctx *ctx, float *V, float *Nngb, long long *pairs, void *stream);
+
+/* P2 + P3.  Moments of W over gather(i) and the reproducing-kernel
+ * coefficients of eq:RK / eq:gRK from the moment conditions
+ * sum_j V_j W^R_ij = 1, sum_j V_j x_ij W^R_ij = 0 (Sec. 1.2):
+ *   B = -m2^-1 m1, A = 1/(m0 + m1.B), grad B = -m2^-1 (grad m1 + grad m2 B),
+ *   grad A = -A^2 (grad m0 + B.grad m1 + m1.grad B)
+ * (3x3 inverse in FP64 when precision = 1), then the velocity gradient of
+ * eq:gradv, grad v_i = -sum_j V_j (v_i - v_j) (x) grad W^R_ij.
+ * Inputs V[n], vel_u[4n]; outputs A, B, gradA, gradB, gradv (gradv may be
+ * NULL to skip P3). */
+int crk_corrections(crk_ctx *ctx, const float *V, const float *vel_u, float *A, float *B,
+                    float *gradA, float *gradB, float *gradv, void *stream);
+
+/* P4, eq:mom and eq:eng with P -> P + Q (eq:visc, eq:mu), the midpoint
+ * projection of eq:hatvi and the limiter of eq:phi .. eq:phiad, over the pair
+ * set:  accel_i = (1/m_i) sum_j 1/2 V_i V_j (P~_i + P~_j)(grad W^R_ji - grad W^R_ij),
+ * dudt_i = (1/m_i) sum_j 1/2 V_i V_j P~_j (v_j - v_i).(grad W^R_ji - grad W^R_ij),
+ * vsig_i = max_j max(0, -(v_i - v_j).x_ij/|x_ij|), qmax_i = max_j Q_i of the pair.
+ * Inputs as produced by crk_volumes / crk_corrections (caller order).
+ * Outputs accel[3n], dudt[n], vsig[n], qmax[n] (vsig, qmax may be NULL).
+ * *pairs (host, may be NULL) receives the ordered pair count and makes the
+ * call synchronise. */
+int crk_forces(crk_ctx *ctx, const float *mass, const float *vel_u, const float *V,
+               const float *A, const float *B, const float *gradA, const float *gradB,
+               const float *gradv, float *accel, float *dudt, float *vsig, float *qmax,
+               long long *pairs, void *stream);
+
+/* P5, compatible energy of eq:compEng .. eq:fij (adot = 0): with F_ij the
+ * pair force of crk_forces evaluated on (mass, vel_u, V, A, B, gradA, gradB,
+ * gradv) and a kick that took velocities vel_before -> vel_after,
+ *   du_i = sum_j f_ij/2 (v_j + v'_j - v_i - v'_i).F_ij/m_i,
+ * f_ij from the specific entropies s = P/rho^gamma and the sign of
+ * Delta E_ij = 1/2 (v_j + v'_j - v_i - v'_i).F_ij (f = 1/2 if s_i + s_j = 0).
+ * Multiply du by the kick's duration to get the energy increment. */
+int crk_compatible(crk_ctx *ctx, const float *mass, const float *vel_u, const float *V,
+                   const float *A, const float *B, const float *gradA, const float *gradB,
+                   const float *gradv, const float *vel_before, const float *vel_after,
+                   float *du, void *stream);
+
+/* One hydro step, the velocity-Verlet KDK operator of eq:verletOP (Sec. 2.1)
+ * with predicted p_p, u_p and compatible energy (eq:compEng), on the caller's
+ * state pos_h[4n], vel_u[4n] (updated in place) and mass[n]:
+ *   half kick with the rates of the last evaluation, drift, rebuild,
+ *   evaluation P1..P4 at (x1, p_p, u_p), second half kick; h is advanced
+ *   by one eq:thacker update of the new evaluation (clamped to
+ *   [h_min, h_max]).  The first call (or the first after crk_reset_rates)
+ *   evaluates the rates at the initial state.  dt > 0 fixes the step;
+ *   dt <= 0 uses the CFL step of the last evaluation (Sec. 2.1 criteria,
+ *   capped by dt_max).  diag (host, may be NULL) receives FP64 diagnostics
+ *   and makes the call synchronise.  The caller must not reorder or edit the
+ *   state between steps without calling crk_reset_rates. */
+int crk_step(crk_ctx *ctx, int n, float *pos_h, float *vel_u, const float *mass, double dt,
+             crk_diag *diag, void *stream);
+
+/* Forget the cached rates so that the next crk_step evaluates afresh. */
+int crk_reset_rates(crk_ctx *ctx);
+
+/* Fixed-point solve of eq:hi by eq:thacker updates (Sec. 2.6): repeat P1 and
+ * the Thacker update for every particle not yet converged, until
+ * |Delta_N - 1| <= tol for all particles or max_it iterations.  Reads and
+ * updates the h column of pos_h[4n] in place (tiles are rebuilt as h
+ * changes).  *iterations (host) receives the iterations used.  Returns
+ * CRK_ENONCONV if some particle did not converge.  Synchronises. */
+int crk_h_iterate(crk_ctx *ctx, int n, float *pos_h, float tol, int max_it, int *iterations,
+                  void *stream);
+
+/* Per-pass GPU timing, for roofline measurement.  enable = 1 clears the
+ * records and starts recording a CUDA event pair around every pass kernel (and
+ * around each cell build), on the stream that kernel is launched on; enable = 0
+ * stops recording.  At most 4096 records are kept. */
+int crk_profile(crk_ctx *ctx, int enable);
+
+#define CRK_PROF_NPASS 8
+/* Wait for the recorded events and sum them per pass: ms[k] (milliseconds)
+ * and counts[k] (records) for k = 0 P1 volumes, 1 neighbour sets, 2 P2
+ * corrections, 3 P3 grad v, 4 P4 forces, 5 P5 compatible energy, 6 cell build
+ * (all its kernels), 7 unused; arrays of CRK_PROF_NPASS entries (may be NULL).
+ * *total_launches (may be NULL) = kernels launched by ctx since crk_create. */
+int crk_profile_read(crk_ctx *ctx, double *ms, long long *counts, long long *total_launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CRK_H */

@@ -48,7 +48,7 @@ def load():
                                         _f64p, _vp, _vp]
         lib.orc_gradv.argtypes = [_ci, _f32p, _ci, _vp, _ci] + [_f64p] * 7
         lib.orc_forces.argtypes = [_ci, _f32p, _ci, _vp, _ci] + [_f64p] * 13 + [
-            _vp, ctypes.POINTER(ctypes.c_longlong)]
+            _vp, _vp, ctypes.POINTER(ctypes.c_longlong)]
         lib.orc_compatible.argtypes = [_ci, _f32p, _ci, _vp, _ci] + [_f64p] * 13
         lib.orc_kernel.argtypes = [_ci, _f64p, _f64p, _f64p, _f64p]
         lib.orc_num_threads.restype = _ci
@@ -192,13 +192,15 @@ def forces(pos_h, vel, u, mass, V, A, B, gA, gB, gv, prm=None, k=None, targets=N
     tp, nt, keep = _tg(targets)
     prm = params() if prm is None else prm
     acc = np.full((n, 3), np.nan)
-    dudt, vsig, qmax = (np.full(n, np.nan) for _ in range(3))
+    dudt, vsig, qmax, fscale = (np.full(n, np.nan) for _ in range(4))
     pairs = ctypes.c_longlong(0)
     c = lambda a: np.ascontiguousarray(a, np.float64)
     _check(load().orc_forces(n, pos, _k(pos, k), tp, nt, c(prm), c(V), c(mass), c(vel), c(u),
                              c(A), c(B), c(gA), c(gB), c(gv), acc, dudt, vsig,
-                             qmax.ctypes.data_as(_vp), ctypes.byref(pairs)), "forces")
-    return {"acc": acc, "dudt": dudt, "vsig": vsig, "qmax": qmax, "pairs": int(pairs.value)}
+                             qmax.ctypes.data_as(_vp), fscale.ctypes.data_as(_vp),
+                             ctypes.byref(pairs)), "forces")
+    return {"acc": acc, "dudt": dudt, "vsig": vsig, "qmax": qmax, "fscale": fscale,
+            "pairs": int(pairs.value)}
 
 
 def compatible(pos_h, vel, u, mass, V, A, B, gA, gB, gv, vb, va, prm=None, k=None, targets=None):
@@ -251,6 +253,7 @@ def evaluate(state, prm=None, k=None, targets=None):
     ev.update(p2)
     ev["gv"] = gv
     ev.update({"acc": p4["acc"], "dudt": p4["dudt"], "vsig": p4["vsig"], "qmax": p4["qmax"],
+               "fscale": p4["fscale"],
                "pairs_union": p4["pairs"], "pairs_gather": p1["pairs"]})
     ev["rho"], ev["P"], ev["cs"], ev["s"] = thermo(p1["V"], mass, u, prm)
     ev["pos_h"], ev["vel"], ev["u"], ev["mass"] = pos.copy(), vel, u, mass
@@ -299,3 +302,53 @@ def energy_momentum(vel, u, mass):
     E = float((0.5 * m * (vel ** 2).sum(axis=1) + m * np.asarray(u, np.float64)).sum())
     P = (m[:, None] * vel).sum(axis=0)
     return E, P
+
+
+def _wrap_f32(x):
+    x = np.mod(np.asarray(x, np.float64), 1.0)
+    f = x.astype(np.float32)
+    f[f >= np.float32(1.0)] = np.float32(0.0)
+    return f
+
+
+def kdk_step(state, ev=None, dt=None, prm=None, k=None, h_min=1e-6, h_max=0.3, dt_max=1.0):
+    """One hydro step, eq:verletOP (Sec. 2.1) with predicted p_p, u_p and the
+    compatible energy of eq:compEng for each half kick; the rates of `ev` (the
+    evaluation at the state's positions) are reused for the first half kick.
+    h advances by one eq:thacker update of the new evaluation, clamped to
+    [h_min, h_max].  Positions, velocities and u are stored in FP32 between
+    steps, as in the engine's state.  Returns (new_state, new_eval, dt)."""
+    prm = params() if prm is None else prm
+    if ev is None:
+        ev = evaluate(state, prm, k)
+    if dt is None:
+        dt = min(float(np.min(cfl_dt(ev, prm))), dt_max)
+    pos = np.asarray(state["pos_h"], np.float32)
+    vu = np.asarray(state["vel_u"], np.float64)
+    vel, u = vu[:, :3], vu[:, 3]
+    mass = np.asarray(state["mass"], np.float64)
+    a0 = ev["acc"]
+    p_half = vel + 0.5 * dt * a0
+    du1 = compatible(ev["pos_h"], ev["vel"], ev["u"], mass, ev["V"], ev["A"], ev["B"], ev["gA"], ev["gB"],
+                     ev["gv"], vel, p_half, prm, k)
+    u_half = u + 0.5 * dt * du1
+    p_p = p_half + 0.5 * dt * a0
+    u_p = u_half + 0.5 * dt * du1
+    n = pos.shape[0]
+    st1 = {"pos_h": np.empty((n, 4), np.float32), "vel_u": np.empty((n, 4), np.float32),
+           "mass": np.asarray(state["mass"], np.float32)}
+    st1["pos_h"][:, :3] = _wrap_f32(pos[:, :3].astype(np.float64) + dt * p_half)
+    st1["pos_h"][:, 3] = pos[:, 3]
+    st1["vel_u"][:, :3] = p_p
+    st1["vel_u"][:, 3] = u_p
+    ev1 = evaluate(st1, prm, k)
+    p1 = p_half + 0.5 * dt * ev1["acc"]
+    du2 = compatible(ev1["pos_h"], ev1["vel"], ev1["u"], mass, ev1["V"], ev1["A"], ev1["B"], ev1["gA"],
+                     ev1["gB"], ev1["gv"], p_half, p1, prm, k)
+    u1 = u_half + 0.5 * dt * du2
+    h1 = np.clip(thacker(pos[:, 3].astype(np.float64), ev1["N"], prm), h_min, h_max)
+    out = {"pos_h": st1["pos_h"].copy(), "vel_u": np.empty((n, 4), np.float32), "mass": st1["mass"]}
+    out["pos_h"][:, 3] = h1
+    out["vel_u"][:, :3] = p1
+    out["vel_u"][:, 3] = u1
+    return out, ev1, dt

@@ -666,11 +666,13 @@ static void pair_force(const sys_t *s, const fstate_t *f, int i, int j,
 /* P4 -- eq:mom (momentum), eq:eng (direct energy rate) with P -> P + Q:
  *   acc_i  = (1/m_i) sum_j F_ij,
  *   dudt_i = (1/m_i) sum_j 1/2 V_i V_j P~_j (v_j - v_i).(grad W^R_ji - grad W^R_ij),
- *   vsig_i = max_j approach speed (R9), qmax_i = max_j Q_i of the pair. */
+ *   vsig_i = max_j approach speed (R9), qmax_i = max_j Q_i of the pair,
+ *   fscale_i = (1/m_i) sum_j |F_ij| (scale of the cancelling pair sum, optional). */
 int orc_forces(int n, const float *pos4, int k, const int *tgt, int ntgt, const double *prm,
                const double *V, const double *mass, const double *vel, const double *u,
                const double *A, const double *B, const double *gA, const double *gB, const double *gv,
-               double *acc, double *dudt, double *vsig, double *qmax, long long *npairs) {
+               double *acc, double *dudt, double *vsig, double *qmax, double *fscale,
+               long long *npairs) {
     sys_t s;
     int rc = sys_init(&s, n, pos4, k);
     if (rc) return rc;
@@ -688,7 +690,7 @@ int orc_forces(int n, const float *pos4, int k, const int *tgt, int ntgt, const 
         for (int kk = 0; kk < nt; kk++) {
             int i = t[kk];
             if (neighbours(&s, i, MODE_UNION, Hm, &l)) { err = ORC_ENOMEM; continue; }
-            double Fs[3] = {0}, du = 0.0, vs = 0.0, qm = 0.0;
+            double Fs[3] = {0}, du = 0.0, vs = 0.0, qm = 0.0, fa = 0.0;
             for (int m = 0; m < l.n; m++) {
                 int j = l.v[m];
                 double F[3], D[3], Ptj, Qi, ap;
@@ -698,6 +700,7 @@ int orc_forces(int n, const float *pos4, int k, const int *tgt, int ntgt, const 
                     Fs[a] += F[a];
                     wdot += (vel[3 * j + a] - vel[3 * i + a]) * D[a];
                 }
+                fa += sqrt(dot3(F, F));
                 du += 0.5 * V[i] * V[j] * Ptj * wdot;
                 if (ap > vs) vs = ap;
                 if (Qi > qm) qm = Qi;
@@ -706,6 +709,7 @@ int orc_forces(int n, const float *pos4, int k, const int *tgt, int ntgt, const 
             dudt[i] = du / mass[i];
             vsig[i] = vs;
             if (qmax) qmax[i] = qm;
+            if (fscale) fscale[i] = fa / mass[i];
             pairs += l.n;
         }
         free(l.v);

@@ -1,0 +1,290 @@
+"""Python binding of the C ABI declared in include/crk.h.
+
+Argument marshalling only: every function checks its torch tensors (CUDA,
+float32, contiguous, shape), passes raw device pointers and the current CUDA
+stream to libcrk.so and turns a non-zero status into CrkError.  Every step of
+the computation runs in the library's kernels.  The library must have been
+built (build.build()); there is no fallback.
+"""
+import ctypes
+import os
+
+import torch
+
+from . import build as _build
+
+CRK_OK = 0
+CRK_ENONCONV = -5
+_CODES = {-1: "CRK_EINVAL", -2: "CRK_ENOMEM", -3: "CRK_ECUDA", -4: "CRK_ETIMEOUT",
+          -5: "CRK_ENONCONV", -6: "CRK_ECAPACITY", -7: "CRK_ESTATE"}
+
+
+class CrkError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (_CODES.get(code, "?"), code, msg))
+        self.code = code
+
+
+class crk_params(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in
+                ("gamma", "n_h", "N_res", "C_l", "C_q", "eps", "eta_crit", "eta_fold", "C_cfl", "zeta",
+                 "h_min", "h_max", "dt_max")] + [
+        ("precision", ctypes.c_int), ("kmax", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
+
+
+class crk_diag(ctypes.Structure):
+    _fields_ = [("dt", ctypes.c_double), ("dt_next", ctypes.c_double), ("E_kin", ctypes.c_double),
+                ("E_int", ctypes.c_double), ("P", ctypes.c_double * 3),
+                ("pairs_gather", ctypes.c_longlong), ("pairs_union", ctypes.c_longlong)]
+
+
+_LIB = None
+_vp = ctypes.c_void_p
+_ci = ctypes.c_int
+
+
+def lib():
+    """Load libcrk.so (raises if it has not been built)."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError("libcrk.so is not built (%s); run paper_2202_02840_gb300.build.build()"
+                               % _build.LIB)
+        L = ctypes.CDLL(_build.LIB)
+        L.crk_default_params.argtypes = [ctypes.POINTER(crk_params)]
+        L.crk_create.argtypes = [ctypes.POINTER(crk_params), ctypes.POINTER(_vp)]
+        L.crk_destroy.argtypes = [_vp]
+        L.crk_last_error.argtypes = [_vp]
+        L.crk_last_error.restype = ctypes.c_char_p
+        L.crk_sync.argtypes = [_vp, _vp]
+        L.crk_build_cells.argtypes = [_vp, _ci, _vp, _vp]
+        L.crk_cells.argtypes = [_vp, _vp, _vp, _vp, ctypes.POINTER(_ci), _vp]
+        L.crk_build_stats.argtypes = [_vp, ctypes.POINTER(_ci), ctypes.POINTER(ctypes.c_longlong),
+                                      ctypes.POINTER(ctypes.c_longlong), _vp]
+        L.crk_neighbours.argtypes = [_vp, _ci, _vp, _vp, _vp]
+        L.crk_volumes.argtypes = [_vp, _vp, _vp, ctypes.POINTER(ctypes.c_longlong), _vp]
+        L.crk_corrections.argtypes = [_vp] + [_vp] * 7 + [_vp]
+        L.crk_forces.argtypes = [_vp] + [_vp] * 13 + [ctypes.POINTER(ctypes.c_longlong), _vp]
+        L.crk_compatible.argtypes = [_vp] + [_vp] * 12 + [_vp]
+        L.crk_step.argtypes = [_vp, _ci, _vp, _vp, _vp, ctypes.c_double, ctypes.POINTER(crk_diag), _vp]
+        L.crk_reset_rates.argtypes = [_vp]
+        L.crk_h_iterate.argtypes = [_vp, _ci, _vp, ctypes.c_float, _ci, ctypes.POINTER(_ci), _vp]
+        L.crk_profile.argtypes = [_vp, _ci]
+        L.crk_profile_read.argtypes = [_vp, _vp, _vp, ctypes.POINTER(ctypes.c_longlong)]
+        _LIB = L
+    return _LIB
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return _vp(s.cuda_stream)
+
+
+def _t(x, shape, name, dtype=torch.float32):
+    if not isinstance(x, torch.Tensor) or not x.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if x.dtype != dtype:
+        raise TypeError("%s must be %s" % (name, dtype))
+    if not x.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if tuple(x.shape) != tuple(shape):
+        raise ValueError("%s has shape %s, expected %s" % (name, tuple(x.shape), tuple(shape)))
+    return _vp(x.data_ptr())
+
+
+class Context:
+    """Owns one crk_ctx (freed on close / garbage collection)."""
+
+    def __init__(self, handle):
+        self.handle = handle
+        self.n = 0
+
+    def close(self):
+        if self.handle:
+            lib().crk_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def check(self, rc):
+        if rc != CRK_OK:
+            raise CrkError(rc, lib().crk_last_error(self.handle).decode())
+        return rc
+
+
+def crk_default_params(**overrides) -> crk_params:
+    p = crk_params()
+    lib().crk_default_params(ctypes.byref(p))
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+def crk_create(params=None, **overrides) -> Context:
+    p = params if params is not None else crk_default_params(**overrides)
+    h = _vp()
+    rc = lib().crk_create(ctypes.byref(p), ctypes.byref(h))
+    if rc != CRK_OK:
+        raise CrkError(rc, "crk_create failed")
+    return Context(h)
+
+
+def crk_sync(ctx, stream=None):
+    ctx.check(lib().crk_sync(ctx.handle, _stream(stream)))
+
+
+def crk_build_cells(ctx, pos_h, stream=None):
+    n = pos_h.shape[0]
+    p = _t(pos_h, (n, 4), "pos_h")
+    ctx.check(lib().crk_build_cells(ctx.handle, n, p, _stream(stream)))
+    ctx.n = n
+
+
+def crk_cells(ctx, kmax=7, stream=None):
+    """(keys int32 (bit pattern of the uint32 keys), perm int32, cell_start int32, k)."""
+    dev = torch.device("cuda")
+    keys = torch.empty(ctx.n, dtype=torch.int32, device=dev)
+    perm = torch.empty(ctx.n, dtype=torch.int32, device=dev)
+    cs = torch.empty((1 << (3 * kmax)) + 1, dtype=torch.int32, device=dev)
+    k = _ci(0)
+    ctx.check(lib().crk_cells(ctx.handle, _vp(keys.data_ptr()), _vp(perm.data_ptr()), _vp(cs.data_ptr()),
+                              ctypes.byref(k), _stream(stream)))
+    return keys, perm, cs[: (1 << (3 * k.value)) + 1], k.value
+
+
+def crk_build_stats(ctx, stream=None):
+    nt, g, u = _ci(0), ctypes.c_longlong(0), ctypes.c_longlong(0)
+    ctx.check(lib().crk_build_stats(ctx.handle, ctypes.byref(nt), ctypes.byref(g), ctypes.byref(u),
+                                    _stream(stream)))
+    return nt.value, g.value, u.value
+
+
+def crk_neighbours(ctx, mode=0, stream=None):
+    """Per particle: neighbour count and order-independent hash of the neighbour set."""
+    dev = torch.device("cuda")
+    cnt = torch.empty(ctx.n, dtype=torch.int32, device=dev)
+    hsh = torch.empty(ctx.n, dtype=torch.int32, device=dev)
+    ctx.check(lib().crk_neighbours(ctx.handle, int(mode), _vp(cnt.data_ptr()), _vp(hsh.data_ptr()),
+                                   _stream(stream)))
+    return cnt, hsh
+
+
+def crk_volumes(ctx, with_pairs=False, stream=None):
+    n = ctx.n
+    dev = torch.device("cuda")
+    V = torch.empty(n, dtype=torch.float32, device=dev)
+    N = torch.empty(n, dtype=torch.float32, device=dev)
+    pairs = ctypes.c_longlong(0)
+    ctx.check(lib().crk_volumes(ctx.handle, _vp(V.data_ptr()), _vp(N.data_ptr()),
+                                ctypes.byref(pairs) if with_pairs else None, _stream(stream)))
+    return (V, N, pairs.value) if with_pairs else (V, N)
+
+
+def crk_corrections(ctx, V, vel_u=None, gradv=True, stream=None):
+    n = ctx.n
+    dev = torch.device("cuda")
+    A = torch.empty(n, dtype=torch.float32, device=dev)
+    B = torch.empty((n, 3), dtype=torch.float32, device=dev)
+    gA = torch.empty((n, 3), dtype=torch.float32, device=dev)
+    gB = torch.empty((n, 3, 3), dtype=torch.float32, device=dev)
+    gv = torch.empty((n, 3, 3), dtype=torch.float32, device=dev) if gradv else None
+    pv = _t(V, (n,), "V")
+    pu = _t(vel_u, (n, 4), "vel_u") if vel_u is not None else None
+    if gradv and vel_u is None:
+        raise ValueError("vel_u is needed for grad v")
+    ctx.check(lib().crk_corrections(ctx.handle, pv, pu, _vp(A.data_ptr()), _vp(B.data_ptr()),
+                                    _vp(gA.data_ptr()), _vp(gB.data_ptr()),
+                                    _vp(gv.data_ptr()) if gradv else None, _stream(stream)))
+    return A, B, gA, gB, gv
+
+
+def _force_inputs(ctx, mass, vel_u, V, A, B, gA, gB, gv):
+    n = ctx.n
+    return [_t(mass, (n,), "mass"), _t(vel_u, (n, 4), "vel_u"), _t(V, (n,), "V"), _t(A, (n,), "A"),
+            _t(B, (n, 3), "B"), _t(gA, (n, 3), "gradA"), _t(gB, (n, 3, 3), "gradB"),
+            _t(gv, (n, 3, 3), "gradv")]
+
+
+def crk_forces(ctx, mass, vel_u, V, A, B, gA, gB, gv, with_pairs=False, stream=None):
+    n = ctx.n
+    dev = torch.device("cuda")
+    acc = torch.empty((n, 3), dtype=torch.float32, device=dev)
+    dudt = torch.empty(n, dtype=torch.float32, device=dev)
+    vsig = torch.empty(n, dtype=torch.float32, device=dev)
+    qmax = torch.empty(n, dtype=torch.float32, device=dev)
+    pairs = ctypes.c_longlong(0)
+    args = _force_inputs(ctx, mass, vel_u, V, A, B, gA, gB, gv)
+    ctx.check(lib().crk_forces(ctx.handle, *args, _vp(acc.data_ptr()), _vp(dudt.data_ptr()),
+                               _vp(vsig.data_ptr()), _vp(qmax.data_ptr()),
+                               ctypes.byref(pairs) if with_pairs else None, _stream(stream)))
+    out = (acc, dudt, vsig, qmax)
+    return out + (pairs.value,) if with_pairs else out
+
+
+def crk_compatible(ctx, mass, vel_u, V, A, B, gA, gB, gv, vel_before, vel_after, stream=None):
+    n = ctx.n
+    du = torch.empty(n, dtype=torch.float32, device=torch.device("cuda"))
+    args = _force_inputs(ctx, mass, vel_u, V, A, B, gA, gB, gv)
+    ctx.check(lib().crk_compatible(ctx.handle, *args, _t(vel_before, (n, 3), "vel_before"),
+                                   _t(vel_after, (n, 3), "vel_after"), _vp(du.data_ptr()), _stream(stream)))
+    return du
+
+
+def crk_step(ctx, pos_h, vel_u, mass, dt=0.0, diag=False, stream=None):
+    """One KDK step in place on pos_h, vel_u; returns a dict of FP64 diagnostics if diag."""
+    n = pos_h.shape[0]
+    d = crk_diag()
+    ctx.check(lib().crk_step(ctx.handle, n, _t(pos_h, (n, 4), "pos_h"), _t(vel_u, (n, 4), "vel_u"),
+                             _t(mass, (n,), "mass"), float(dt), ctypes.byref(d) if diag else None,
+                             _stream(stream)))
+    ctx.n = n
+    if not diag:
+        return None
+    return {"dt": d.dt, "dt_next": d.dt_next, "E_kin": d.E_kin, "E_int": d.E_int, "P": list(d.P),
+            "pairs_gather": d.pairs_gather, "pairs_union": d.pairs_union}
+
+
+def crk_reset_rates(ctx):
+    ctx.check(lib().crk_reset_rates(ctx.handle))
+
+
+def crk_h_iterate(ctx, pos_h, tol=1e-4, max_it=50, stream=None):
+    """Fixed-point h solve in place; returns (iterations, converged)."""
+    n = pos_h.shape[0]
+    it = _ci(0)
+    rc = lib().crk_h_iterate(ctx.handle, n, _t(pos_h, (n, 4), "pos_h"), float(tol), int(max_it),
+                             ctypes.byref(it), _stream(stream))
+    ctx.n = n
+    if rc == CRK_ENONCONV:
+        return it.value, False
+    ctx.check(rc)
+    return it.value, True
+
+
+PASS_NAMES = ["P1 volumes", "neighbour sets", "P2 corrections", "P3 grad v", "P4 forces",
+              "P5 compatible energy", "cell build", "-"]
+
+
+def crk_profile(ctx, enable=True):
+    ctx.check(lib().crk_profile(ctx.handle, 1 if enable else 0))
+
+
+def crk_profile_read(ctx):
+    """({pass: total ms}, {pass: records}, total kernel launches since creation)."""
+    ms = (ctypes.c_double * 8)()
+    cnt = (ctypes.c_longlong * 8)()
+    tot = ctypes.c_longlong(0)
+    ctx.check(lib().crk_profile_read(ctx.handle, ms, cnt, ctypes.byref(tot)))
+    return ({PASS_NAMES[k]: ms[k] for k in range(7)}, {PASS_NAMES[k]: cnt[k] for k in range(7)},
+            tot.value)
+
+
+def crk_launches(ctx):
+    """Kernels launched by ctx since it was created."""
+    tot = ctypes.c_longlong(0)
+    ctx.check(lib().crk_profile_read(ctx.handle, None, None, ctypes.byref(tot)))
+    return tot.value

@@ -1,0 +1,480 @@
+// crk_cells.cu -- chaining-mesh binning and interaction lists (CRK-HACC Sec. 2.3:
+// particles binned into chaining-mesh cells, flattened contiguous leaves with
+// bounding boxes grown by the maximal smoothing length, and interaction lists
+// assembled once per hydro step and reused by every hydro kernel).
+//
+// GB300 layout: 30-bit Morton keys of the fixed-point coordinates, a stable LSD
+// radix sort (8-bit digits, per-warp stable ranking with match_any), sorted
+// SoA particle records, tiles of 32 consecutive sorted particles (one warp),
+// an implicit binary tree over the Morton-ordered tiles, and per-tile lists of
+// neighbour tiles found by a depth-first walk of that tree with exact
+// fixed-point gap tests (never drops a pair of the neighbour predicate).
+#include "crk_internal.cuh"
+
+#include <string.h>
+#include <math.h>
+
+namespace crk {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+// ------------------------------------------------------------------ keys
+
+// Per particle t of the input order: fixed-point record, Morton key, max h.
+// Invalid records (coordinates outside [0,1) or non-finite, h outside
+// (0, 1/3)) are counted and replaced by a harmless record.
+__global__ void k_keys(int n, const float4 *__restrict__ pos, uint32_t *__restrict__ key,
+                       int32_t *__restrict__ idx, uint4 *__restrict__ q_tmp,
+                       float *__restrict__ h_tmp, unsigned long long *counters) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    float4 p = pos[t];
+    bool ok = (p.x >= 0.f && p.x < 1.f) && (p.y >= 0.f && p.y < 1.f) && (p.z >= 0.f && p.z < 1.f) &&
+              ((double)p.w > 0.0 && (double)p.w < 1.0 / 3.0);
+    if (!ok) {
+        atomicAdd(&counters[CNT_ERR_INPUT], 1ull);
+        p = make_float4(0.f, 0.f, 0.f, 0.01f);
+    }
+    uint4 q = make_uint4(to_fixed(p.x), to_fixed(p.y), to_fixed(p.z), to_fixed(p.w));
+    q_tmp[t] = q;
+    h_tmp[t] = p.w;
+    key[t] = morton30(q.x, q.y, q.z);
+    idx[t] = t;
+    atomicMax(&counters[CNT_HMAX], (unsigned long long)__float_as_uint(p.w));
+}
+
+// ------------------------------------------------------------------ radix sort
+
+constexpr int RS_WARPS = 8;
+constexpr int RS_PER_WARP = 512;
+constexpr int RS_ITEMS = RS_WARPS * RS_PER_WARP;   // keys per block
+
+__global__ void __launch_bounds__(256) k_rs_hist(int n, const uint32_t *__restrict__ key, int shift,
+                                                 uint32_t *__restrict__ hist, int nblocks) {
+    __shared__ uint32_t cnt[256];
+    cnt[threadIdx.x] = 0;
+    __syncthreads();
+    int base = blockIdx.x * RS_ITEMS;
+    for (int k = threadIdx.x; k < RS_ITEMS; k += 256) {
+        int i = base + k;
+        if (i < n) atomicAdd(&cnt[(key[i] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    hist[threadIdx.x * nblocks + blockIdx.x] = cnt[threadIdx.x];
+}
+
+// Stable scatter: warp w of block b owns the contiguous items
+// [b*RS_ITEMS + w*RS_PER_WARP, +RS_PER_WARP); within a warp, items are ranked in
+// index order with match_any, so equal digits keep their input order.
+__global__ void __launch_bounds__(256) k_rs_scatter(int n, const uint32_t *__restrict__ key_in,
+                                                    const int32_t *__restrict__ val_in,
+                                                    uint32_t *__restrict__ key_out,
+                                                    int32_t *__restrict__ val_out, int shift,
+                                                    const uint32_t *__restrict__ hist_scan,
+                                                    int nblocks) {
+    __shared__ uint32_t off[RS_WARPS][256];
+    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int d = lane; d < 256; d += 32) off[w][d] = 0;
+    __syncwarp();
+    int wbase = blockIdx.x * RS_ITEMS + w * RS_PER_WARP;
+    for (int k = 0; k < RS_PER_WARP / 32; k++) {
+        int i = wbase + k * 32 + lane;
+        bool v = i < n;
+        uint32_t d = v ? ((key_in[i] >> shift) & 255u) : 256u + lane;
+        unsigned peers = __match_any_sync(FULL, d);
+        if (v && lane == __ffs(peers) - 1) off[w][d] += __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    {
+        int d = threadIdx.x;
+        uint32_t run = hist_scan[d * nblocks + blockIdx.x];
+        for (int ww = 0; ww < RS_WARPS; ww++) {
+            uint32_t c = off[ww][d];
+            off[ww][d] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    unsigned lt = lanemask_lt();
+    for (int k = 0; k < RS_PER_WARP / 32; k++) {
+        int i = wbase + k * 32 + lane;
+        bool v = i < n;
+        uint32_t kk = v ? key_in[i] : 0u;
+        uint32_t d = v ? ((kk >> shift) & 255u) : 256u + lane;
+        unsigned peers = __match_any_sync(FULL, d);
+        uint32_t base = v ? off[w][d] : 0u;
+        __syncwarp();
+        if (v) {
+            uint32_t pos = base + __popc(peers & lt);
+            key_out[pos] = kk;
+            val_out[pos] = val_in[i];
+            if (lane == __ffs(peers) - 1) off[w][d] = base + __popc(peers);
+        }
+        __syncwarp();
+    }
+}
+
+// Exclusive scan, 4096 items per block.
+__global__ void __launch_bounds__(1024) k_scan_block(const uint32_t *__restrict__ in,
+                                                     uint32_t *__restrict__ out, int count,
+                                                     uint32_t *__restrict__ block_sums) {
+    __shared__ uint32_t wt[32];
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int base = blockIdx.x * 4096 + threadIdx.x * 4;
+    uint32_t v[4], s = 0;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        int i = base + k;
+        v[k] = i < count ? in[i] : 0u;
+        s += v[k];
+    }
+    uint32_t x = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(FULL, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wt[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t t = wt[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(FULL, t, o);
+            if (lane >= o) t += y;
+        }
+        wt[lane] = t;
+    }
+    __syncthreads();
+    uint32_t excl = x - s + (warp > 0 ? wt[warp - 1] : 0u);
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        int i = base + k;
+        if (i < count) out[i] = excl;
+        excl += v[k];
+    }
+    if (threadIdx.x == 1023 && block_sums) block_sums[blockIdx.x] = excl;
+}
+
+__global__ void k_scan_add(uint32_t *__restrict__ out, int count, const uint32_t *__restrict__ offs) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) out[i] += offs[i / 4096];
+}
+
+// exclusive scan of count <= 4096*4096 values; scratch holds >= 2*4096 words
+static int scan_exclusive(crk_ctx *ctx, const uint32_t *in, uint32_t *out, int count,
+                          uint32_t *scratch, cudaStream_t s) {
+    int nb = grid_for(count, 4096);
+    if (nb > 4096) return crk_set_error(ctx, CRK_ECAPACITY, "scan of %d items exceeds 2 levels", count);
+    k_scan_block<<<nb, 1024, 0, s>>>(in, out, count, scratch);
+    ++ctx->launches;
+    if (nb > 1) {
+        k_scan_block<<<1, 1024, 0, s>>>(scratch, scratch + 4096, nb, nullptr);
+        ++ctx->launches;
+        k_scan_add<<<grid_for(count, 256), 256, 0, s>>>(out, count, scratch + 4096);
+        ++ctx->launches;
+    }
+    CRK_LAUNCH_CHECK(ctx, "scan");
+    return CRK_OK;
+}
+
+// Stable sort of (key_a, idx_a) by the low `bits` bits of key; result in key_a/idx_a.
+static int radix_sort(crk_ctx *ctx, int n, int bits, cudaStream_t s) {
+    int nblocks = grid_for(n, RS_ITEMS);
+    int passes = (bits + 7) / 8;
+    if (passes & 1) passes++;   // even number of passes leaves the result in the _a buffers
+    uint32_t *kin = ctx->key_a, *kout = ctx->key_b;
+    int32_t *vin = ctx->idx_a, *vout = ctx->idx_b;
+    for (int p = 0; p < passes; p++) {
+        int shift = 8 * p;
+        k_rs_hist<<<nblocks, 256, 0, s>>>(n, kin, shift, ctx->hist, nblocks);
+        ++ctx->launches;
+        int rc = scan_exclusive(ctx, ctx->hist, ctx->hist, 256 * nblocks, ctx->scan_tmp, s);
+        if (rc) return rc;
+        k_rs_scatter<<<nblocks, 256, 0, s>>>(n, kin, vin, kout, vout, shift, ctx->hist, nblocks);
+        ++ctx->launches;
+        CRK_LAUNCH_CHECK(ctx, "radix sort");
+        uint32_t *tk = kin; kin = kout; kout = tk;
+        int32_t *tv = vin; vin = vout; vout = tv;
+    }
+    return CRK_OK;
+}
+
+// ------------------------------------------------------------------ sorted records
+
+__global__ void k_gather_sorted(int n, const int32_t *__restrict__ idx, const uint4 *__restrict__ q_tmp,
+                                const float *__restrict__ h_tmp, const int32_t *__restrict__ base_perm,
+                                uint4 *__restrict__ q4, float *__restrict__ hs,
+                                int32_t *__restrict__ perm_out) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    int i = idx[s];
+    q4[s] = q_tmp[i];
+    hs[s] = h_tmp[i];
+    perm_out[s] = base_perm ? base_perm[i] : i;
+}
+
+// ------------------------------------------------------------------ tiles and tree
+
+__global__ void k_tiles(int n, int ntiles, const uint4 *__restrict__ q4, uint4 *__restrict__ lo,
+                        uint4 *__restrict__ hi) {
+    int tile = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (tile >= ntiles) return;
+    int s = tile * TILE + lane;
+    bool v = s < n;
+    uint4 q = v ? q4[s] : make_uint4(0, 0, 0, 0);
+    uint32_t xl = __reduce_min_sync(FULL, v ? q.x : 0xffffffffu);
+    uint32_t yl = __reduce_min_sync(FULL, v ? q.y : 0xffffffffu);
+    uint32_t zl = __reduce_min_sync(FULL, v ? q.z : 0xffffffffu);
+    uint32_t xh = __reduce_max_sync(FULL, v ? q.x : 0u);
+    uint32_t yh = __reduce_max_sync(FULL, v ? q.y : 0u);
+    uint32_t zh = __reduce_max_sync(FULL, v ? q.z : 0u);
+    uint32_t Hm = __reduce_max_sync(FULL, v ? q.w : 0u);
+    uint32_t c = __popc(__ballot_sync(FULL, v));
+    if (lane == 0) {
+        lo[tile] = make_uint4(xl, yl, zl, Hm);
+        hi[tile] = make_uint4(xh, yh, zh, c);
+    }
+}
+
+__global__ void k_tree_level(const uint4 *__restrict__ clo, const uint4 *__restrict__ chi, int ccnt,
+                             uint4 *__restrict__ plo, uint4 *__restrict__ phi, int pcnt) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= pcnt) return;
+    uint4 l = clo[2 * k], h = chi[2 * k];
+    if (2 * k + 1 < ccnt) {
+        uint4 l2 = clo[2 * k + 1], h2 = chi[2 * k + 1];
+        l = make_uint4(min(l.x, l2.x), min(l.y, l2.y), min(l.z, l2.z), max(l.w, l2.w));
+        h = make_uint4(max(h.x, h2.x), max(h.y, h2.y), max(h.z, h2.z), h.w + h2.w);
+    }
+    plo[k] = l;
+    phi[k] = h;
+}
+
+// periodic gap (fixed point) between intervals [a0,a1] and [b0,b1] on a circle of 2^32
+__device__ __forceinline__ unsigned long long axis_gap(uint32_t a0, uint32_t a1, uint32_t b0, uint32_t b1) {
+    const long long C = 4294967296ll;
+    long long d0 = max(0ll, max((long long)b0 - (long long)a1, (long long)a0 - (long long)b1));
+    long long dp = (long long)b0 + C - (long long)a1;
+    long long dm = (long long)a0 + C - (long long)b1;
+    long long g = min(d0, min(dp, dm));
+    return (unsigned long long)g;
+}
+
+__device__ __forceinline__ unsigned long long box_gap2(uint4 alo, uint4 ahi, uint4 blo, uint4 bhi) {
+    unsigned long long gx = axis_gap(alo.x, ahi.x, blo.x, bhi.x);
+    unsigned long long gy = axis_gap(alo.y, ahi.y, blo.y, bhi.y);
+    unsigned long long gz = axis_gap(alo.z, ahi.z, blo.z, bhi.z);
+    return gx * gx + gy * gy + gz * gz;
+}
+
+struct TreeDesc {
+    int off[MAX_LEVELS];
+    int cnt[MAX_LEVELS];
+    int top;
+};
+
+// Walk the tree for tile I; emit (or count) every tile J whose box is closer
+// than the reach R: gather: R = Hmax_I; union: R = max(Hmax_I, Hmax_J).
+template <bool UNION, bool WRITE>
+__device__ int walk(const TreeDesc &T, const uint4 *__restrict__ lo, const uint4 *__restrict__ hi,
+                    uint4 Ilo, uint4 Ihi, uint32_t *__restrict__ out) {
+    int stL[2 * MAX_LEVELS], stK[2 * MAX_LEVELS];
+    int sp = 0, cnt = 0;
+    stL[sp] = T.top; stK[sp] = 0; sp++;
+    unsigned long long HI = Ilo.w;
+    while (sp > 0) {
+        sp--;
+        int L = stL[sp], k = stK[sp];
+        uint4 nlo = lo[T.off[L] + k], nhi = hi[T.off[L] + k];
+        unsigned long long R = HI;
+        if (UNION && (unsigned long long)nlo.w > R) R = nlo.w;
+        if (box_gap2(Ilo, Ihi, nlo, nhi) >= R * R) continue;
+        if (L == 0) {
+            if (WRITE) out[cnt] = (uint32_t)k;
+            cnt++;
+        } else {
+            int kr = 2 * k + 1;
+            if (kr < T.cnt[L - 1]) { stL[sp] = L - 1; stK[sp] = kr; sp++; }
+            stL[sp] = L - 1; stK[sp] = 2 * k; sp++;
+        }
+    }
+    return cnt;
+}
+
+template <bool UNION>
+__global__ void k_lists(int ntiles, TreeDesc T, const uint4 *__restrict__ lo, const uint4 *__restrict__ hi,
+                        uint2 *__restrict__ ofs, uint32_t *__restrict__ list, long long cap,
+                        unsigned long long *counter) {
+    int I = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= ntiles) return;
+    uint4 Ilo = lo[I], Ihi = hi[I];
+    int c = walk<UNION, false>(T, lo, hi, Ilo, Ihi, nullptr);
+    unsigned long long base = atomicAdd(counter, (unsigned long long)c);
+    if ((long long)(base + c) <= cap) {
+        walk<UNION, true>(T, lo, hi, Ilo, Ihi, list + base);
+        ofs[I] = make_uint2((uint32_t)base, (uint32_t)c);
+    } else {
+        ofs[I] = make_uint2(0u, 0u);
+    }
+}
+
+// ------------------------------------------------------------------ cell table
+
+__device__ __forceinline__ int cell_level(unsigned long long hbits, int kmax) {
+    float hmax = __uint_as_float((uint32_t)hbits);
+    int e;
+    float m = frexpf(hmax, &e);
+    int k = (m == 0.5f) ? 1 - e : -e;
+    return max(1, min(kmax, k));
+}
+
+__global__ void k_cell_start(int n, const uint32_t *__restrict__ keys, int kmax,
+                             const unsigned long long *__restrict__ counters, int32_t *__restrict__ cs) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    int k = cell_level(counters[CNT_HMAX], kmax);
+    int sh = 30 - 3 * k;
+    long long ncell = 1ll << (3 * k);
+    if (s > n) return;
+    long long c = (s < n) ? (long long)(keys[s] >> sh) : ncell;
+    long long cp = (s > 0) ? (long long)(keys[s - 1] >> sh) : -1;
+    for (long long cc = cp + 1; cc <= c; cc++) cs[cc] = s;
+}
+
+// ------------------------------------------------------------------ drivers
+
+static TreeDesc tree_desc(const crk_ctx *ctx) {
+    TreeDesc T;
+    for (int L = 0; L < MAX_LEVELS; L++) {
+        T.off[L] = ctx->level_off[L];
+        T.cnt[L] = ctx->level_cnt[L];
+    }
+    T.top = ctx->nlevels - 1;
+    return T;
+}
+
+int rebuild_lists(crk_ctx *ctx, cudaStream_t s) {
+    if (ctx->ntiles == 0) return CRK_OK;
+    TreeDesc T = tree_desc(ctx);
+    CRK_CUDA(ctx, cudaMemsetAsync(ctx->counters + CNT_GLIST, 0, 2 * sizeof(unsigned long long), s));
+    int b = 128;
+    k_lists<false><<<grid_for(ctx->ntiles, b), b, 0, s>>>(ctx->ntiles, T, ctx->node_lo, ctx->node_hi,
+                                                           ctx->gofs, ctx->glist, ctx->cap_glist,
+                                                           ctx->counters + CNT_GLIST);
+    ++ctx->launches;
+    k_lists<true><<<grid_for(ctx->ntiles, b), b, 0, s>>>(ctx->ntiles, T, ctx->node_lo, ctx->node_hi,
+                                                          ctx->uofs, ctx->ulist, ctx->cap_ulist,
+                                                          ctx->counters + CNT_ULIST);
+    ++ctx->launches;
+    CRK_LAUNCH_CHECK(ctx, "interaction lists");
+    return CRK_OK;
+}
+
+// Tiles and tree from the sorted q4 (used again when only h changes).
+int build_tree(crk_ctx *ctx, cudaStream_t s) {
+    int n = ctx->n, nt = ctx->ntiles;
+    if (nt == 0) return CRK_OK;
+    k_tiles<<<grid_for((long long)nt * 32, 256), 256, 0, s>>>(n, nt, ctx->q4, ctx->node_lo, ctx->node_hi);
+    ++ctx->launches;
+    for (int L = 1; L < ctx->nlevels; L++) {
+        int pc = ctx->level_cnt[L];
+        k_tree_level<<<grid_for(pc, 256), 256, 0, s>>>(ctx->node_lo + ctx->level_off[L - 1],
+                                                         ctx->node_hi + ctx->level_off[L - 1],
+                                                         ctx->level_cnt[L - 1],
+                                                         ctx->node_lo + ctx->level_off[L],
+                                                         ctx->node_hi + ctx->level_off[L], pc);
+        ++ctx->launches;
+    }
+    CRK_LAUNCH_CHECK(ctx, "tile tree");
+    return CRK_OK;
+}
+
+// Bin the n records pos[t] (float4 x,y,z,h) of some input order; base_perm maps
+// that order to caller indices (NULL = identity).  After the call idx_a holds,
+// for every new sorted slot, its index in the input order.
+int build_cells_sorted(crk_ctx *ctx, int n, const float4 *pos, const int32_t *base_perm, cudaStream_t s) {
+    int rc = crk_ensure_particles(ctx, n);
+    if (rc) return rc;
+    ctx->n = n;
+    ctx->ntiles = (n + TILE - 1) / TILE;
+    int L = 0, c = ctx->ntiles, off = 0;
+    while (c > 0 && L < MAX_LEVELS) {
+        ctx->level_off[L] = off;
+        ctx->level_cnt[L] = c;
+        off += c;
+        L++;
+        if (c == 1) break;
+        c = (c + 1) / 2;
+    }
+    ctx->nlevels = L;
+    ctx->built = 0;
+    CRK_CUDA(ctx, cudaMemsetAsync(ctx->counters + CNT_ERR_INPUT, 0, 2 * sizeof(unsigned long long), s));
+    if (n == 0) {
+        ctx->built = 1;
+        return CRK_OK;
+    }
+    uint4 *q_tmp = ctx->q_tmp;
+    float *h_tmp = ctx->h_tmp;
+    prof_begin(ctx, PROF_BUILD, s);
+    k_keys<<<grid_for(n, 256), 256, 0, s>>>(n, pos, ctx->key_a, ctx->idx_a, q_tmp, h_tmp, ctx->counters);
+    ++ctx->launches;
+    CRK_LAUNCH_CHECK(ctx, "keys");
+    rc = radix_sort(ctx, n, 30, s);
+    if (rc) return rc;
+    k_gather_sorted<<<grid_for(n, 256), 256, 0, s>>>(n, ctx->idx_a, q_tmp, h_tmp, base_perm, ctx->q4,
+                                                     ctx->hs, ctx->idx_b);
+    ++ctx->launches;
+    CRK_LAUNCH_CHECK(ctx, "gather sorted");
+    CRK_CUDA(ctx, cudaMemcpyAsync(ctx->perm, ctx->idx_b, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
+    CRK_CUDA(ctx, cudaMemcpyAsync(ctx->keys, ctx->key_a, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s));
+    k_cell_start<<<grid_for(n + 1, 256), 256, 0, s>>>(n, ctx->keys, ctx->p.kmax, ctx->counters, ctx->cell_start);
+    ++ctx->launches;
+    CRK_LAUNCH_CHECK(ctx, "cell table");
+    rc = build_tree(ctx, s);
+    if (rc) return rc;
+    rc = rebuild_lists(ctx, s);
+    if (rc) return rc;
+    prof_end(ctx, s);
+    ctx->built = 1;
+    return CRK_OK;
+}
+
+int cell_level_host(const crk_ctx *ctx) {
+    uint32_t bits = (uint32_t)ctx->h_counters[CNT_HMAX];
+    float hmax;
+    memcpy(&hmax, &bits, sizeof(float));
+    int e;
+    float m = frexpf(hmax, &e);
+    int k = (m == 0.5f) ? 1 - e : -e;
+    return k < 1 ? 1 : (k > ctx->p.kmax ? ctx->p.kmax : k);
+}
+
+// Read the counters after a build; grow and redo the lists on overflow.
+int finish_build(crk_ctx *ctx, cudaStream_t s) {
+    int rc = crk_sync_counters(ctx, s);
+    if (rc) return rc;
+    if (ctx->h_counters[CNT_ERR_INPUT])
+        return crk_set_error(ctx, CRK_EINVAL, "%llu particle records have coordinates outside [0,1) "
+                             "or h outside (0, 1/3)", ctx->h_counters[CNT_ERR_INPUT]);
+    long long ng = (long long)ctx->h_counters[CNT_GLIST], nu = (long long)ctx->h_counters[CNT_ULIST];
+    if (ng > ctx->cap_glist || nu > ctx->cap_ulist) {
+        rc = crk_ensure_lists(ctx, ng + ng / 4 + 1024, nu + nu / 4 + 1024);
+        if (rc) return rc;
+        rc = rebuild_lists(ctx, s);
+        if (rc) return rc;
+        rc = crk_sync_counters(ctx, s);
+        if (rc) return rc;
+        ng = (long long)ctx->h_counters[CNT_GLIST];
+        nu = (long long)ctx->h_counters[CNT_ULIST];
+        if (ng > ctx->cap_glist || nu > ctx->cap_ulist)
+            return crk_set_error(ctx, CRK_ECAPACITY, "interaction lists overflow after growth");
+    }
+    ctx->glist_total = ng;
+    ctx->ulist_total = nu;
+    ctx->cell_k = cell_level_host(ctx);
+    return CRK_OK;
+}
+
+}  // namespace crk

@@ -1,0 +1,580 @@
+// crk_ctx.cu -- engine lifecycle, device memory, caller-order packing and the
+// C-ABI entry points of the individual passes (declared in include/crk.h).
+#include "crk_internal.cuh"
+
+#include <new>
+#include <stdlib.h>
+#include <string.h>
+
+using namespace crk;
+
+// ------------------------------------------------------------------ errors
+
+int crk_set_error(crk_ctx *ctx, int code, const char *fmt, ...) {
+    if (ctx) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(ctx->err, sizeof(ctx->err), fmt, ap);
+        va_end(ap);
+    }
+    return code;
+}
+
+int crk_check_cuda(crk_ctx *ctx, cudaError_t e, const char *what) {
+    int code = (e == cudaErrorMemoryAllocation) ? CRK_ENOMEM : CRK_ECUDA;
+    return crk_set_error(ctx, code, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// ------------------------------------------------------------------ memory
+
+template <typename T>
+static int dalloc(crk_ctx *ctx, T **p, size_t count) {
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return crk_check_cuda(ctx, e, "cudaMalloc");
+    }
+    return CRK_OK;
+}
+
+template <typename T>
+static void dfree(T **p) {
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+}
+
+int crk_ensure_particles(crk_ctx *ctx, int n) {
+    if (n <= ctx->cap_n && ctx->q4) return CRK_OK;
+    int cap = n < 4096 ? 4096 : n + n / 8;
+    int tiles = (cap + TILE - 1) / TILE;
+    int nb = (cap + 4095) / 4096;
+    int rc = 0;
+    rc |= dalloc(ctx, &ctx->key_a, cap);
+    rc |= dalloc(ctx, &ctx->key_b, cap);
+    rc |= dalloc(ctx, &ctx->idx_a, cap);
+    rc |= dalloc(ctx, &ctx->idx_b, cap);
+    rc |= dalloc(ctx, &ctx->keys, cap);
+    rc |= dalloc(ctx, &ctx->perm, cap);
+    rc |= dalloc(ctx, &ctx->q4, cap);
+    rc |= dalloc(ctx, &ctx->hs, cap);
+    rc |= dalloc(ctx, &ctx->V, cap);
+    rc |= dalloc(ctx, &ctx->Nn, cap);
+    rc |= dalloc(ctx, &ctx->vel, cap);
+    rc |= dalloc(ctx, &ctx->mass, cap);
+    rc |= dalloc(ctx, &ctx->corr, cap);
+    rc |= dalloc(ctx, &ctx->gv, cap);
+    rc |= dalloc(ctx, &ctx->acc, cap);
+    rc |= dalloc(ctx, &ctx->vq, cap);
+    rc |= dalloc(ctx, &ctx->vb, cap);
+    rc |= dalloc(ctx, &ctx->va, cap);
+    rc |= dalloc(ctx, &ctx->du, cap);
+    rc |= dalloc(ctx, &ctx->st_pos, cap);
+    rc |= dalloc(ctx, &ctx->st_vel, cap);
+    rc |= dalloc(ctx, &ctx->st_half, cap);
+    rc |= dalloc(ctx, &ctx->st_tmp, cap);
+    rc |= dalloc(ctx, &ctx->st_tmp1, cap);
+    rc |= dalloc(ctx, &ctx->q_tmp, cap);
+    rc |= dalloc(ctx, &ctx->h_tmp, cap);
+    rc |= dalloc(ctx, &ctx->flags, cap);
+    rc |= dalloc(ctx, &ctx->d_dt, cap);
+    rc |= dalloc(ctx, &ctx->gofs, tiles);
+    rc |= dalloc(ctx, &ctx->uofs, tiles);
+    rc |= dalloc(ctx, &ctx->node_lo, 2 * (size_t)tiles + MAX_LEVELS);
+    rc |= dalloc(ctx, &ctx->node_hi, 2 * (size_t)tiles + MAX_LEVELS);
+    rc |= dalloc(ctx, &ctx->hist, 256 * (size_t)nb);
+    rc |= dalloc(ctx, &ctx->d_red, 4096 * 8);
+    if (rc) {
+        ctx->cap_n = 0;
+        return crk_set_error(ctx, CRK_ENOMEM, "cannot allocate buffers for %d particles", n);
+    }
+    ctx->cap_n = cap;
+    ctx->cap_tiles = tiles;
+    ctx->cap_nodes = 2 * tiles + MAX_LEVELS;
+    ctx->cap_hist = 256 * nb;
+    ctx->rates_valid = 0;
+    long long want = (long long)tiles * 48;
+    if (ctx->cap_glist < want || ctx->cap_ulist < want) return crk_ensure_lists(ctx, want, want);
+    return CRK_OK;
+}
+
+int crk_ensure_lists(crk_ctx *ctx, long long ng, long long nu) {
+    if (ng > 0xffffffffll || nu > 0xffffffffll)
+        return crk_set_error(ctx, CRK_ECAPACITY, "interaction lists beyond 2^32 entries");
+    int rc = 0;
+    if (ng > ctx->cap_glist) {
+        rc |= dalloc(ctx, &ctx->glist, (size_t)ng);
+        ctx->cap_glist = rc ? 0 : ng;
+    }
+    if (nu > ctx->cap_ulist) {
+        rc |= dalloc(ctx, &ctx->ulist, (size_t)nu);
+        ctx->cap_ulist = rc ? 0 : nu;
+    }
+    if (rc) return crk_set_error(ctx, CRK_ENOMEM, "cannot allocate interaction lists");
+    return CRK_OK;
+}
+
+int crk_sync_counters(crk_ctx *ctx, cudaStream_t s) {
+    CRK_CUDA(ctx, cudaMemcpyAsync(ctx->h_counters, ctx->counters, CNT_COUNT * sizeof(unsigned long long),
+                                  cudaMemcpyDeviceToHost, s));
+    CRK_CUDA(ctx, cudaStreamSynchronize(s));
+    return CRK_OK;
+}
+
+// ------------------------------------------------------------------ pack / unpack kernels
+
+__global__ void k_gather_rows(long long total, int w, const int32_t *__restrict__ perm,
+                              const uint32_t *__restrict__ in, uint32_t *__restrict__ out) {
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total) return;
+    long long s = t / w;
+    int c = (int)(t - s * w);
+    out[t] = in[(long long)perm[s] * w + c];
+}
+
+__global__ void k_scatter_rows(long long total, int w, const int32_t *__restrict__ perm,
+                               const uint32_t *__restrict__ in, uint32_t *__restrict__ out) {
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total) return;
+    long long s = t / w;
+    int c = (int)(t - s * w);
+    out[(long long)perm[s] * w + c] = in[t];
+}
+
+// caller-order (A, B, gA, gB) -> sorted CorrRec
+__global__ void k_pack_corr(int n, const int32_t *__restrict__ perm, const float *__restrict__ A,
+                            const float *__restrict__ B, const float *__restrict__ gA,
+                            const float *__restrict__ gB, CorrRec *__restrict__ out) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    long long i = perm[s];
+    const float *b = B + 3 * i, *ga = gA + 3 * i, *gb = gB + 9 * i;
+    CorrRec c;
+    c.c0 = make_float4(A[i], b[0], b[1], b[2]);
+    c.c1 = make_float4(ga[0], ga[1], ga[2], gb[0]);
+    c.c2 = make_float4(gb[1], gb[2], gb[3], gb[4]);
+    c.c3 = make_float4(gb[5], gb[6], gb[7], gb[8]);
+    out[s] = c;
+}
+
+__global__ void k_unpack_corr(int n, const int32_t *__restrict__ perm, const CorrRec *__restrict__ in,
+                              float *__restrict__ A, float *__restrict__ B, float *__restrict__ gA,
+                              float *__restrict__ gB) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    long long i = perm[s];
+    CorrRec c = in[s];
+    A[i] = c.c0.x;
+    float *b = B + 3 * i, *ga = gA + 3 * i, *gb = gB + 9 * i;
+    b[0] = c.c0.y; b[1] = c.c0.z; b[2] = c.c0.w;
+    ga[0] = c.c1.x; ga[1] = c.c1.y; ga[2] = c.c1.z;
+    gb[0] = c.c1.w; gb[1] = c.c2.x; gb[2] = c.c2.y; gb[3] = c.c2.z; gb[4] = c.c2.w;
+    gb[5] = c.c3.x; gb[6] = c.c3.y; gb[7] = c.c3.z; gb[8] = c.c3.w;
+}
+
+__global__ void k_pack_gv(int n, const int32_t *__restrict__ perm, const float *__restrict__ g,
+                          GvRec *__restrict__ out) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const float *a = g + 9 * (long long)perm[s];
+    GvRec r;
+    r.g0 = make_float4(a[0], a[1], a[2], a[3]);
+    r.g1 = make_float4(a[4], a[5], a[6], a[7]);
+    r.g2 = make_float4(a[8], 0.f, 0.f, 0.f);
+    out[s] = r;
+}
+
+__global__ void k_unpack_gv(int n, const int32_t *__restrict__ perm, const GvRec *__restrict__ in,
+                            float *__restrict__ g) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    float *a = g + 9 * (long long)perm[s];
+    GvRec r = in[s];
+    a[0] = r.g0.x; a[1] = r.g0.y; a[2] = r.g0.z; a[3] = r.g0.w;
+    a[4] = r.g1.x; a[5] = r.g1.y; a[6] = r.g1.z; a[7] = r.g1.w;
+    a[8] = r.g2.x;
+}
+
+// caller float[3n] -> sorted float4 (w = 0)
+__global__ void k_pack_v3(int n, const int32_t *__restrict__ perm, const float *__restrict__ v,
+                          float4 *__restrict__ out) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const float *a = v + 3 * (long long)perm[s];
+    out[s] = make_float4(a[0], a[1], a[2], 0.f);
+}
+
+// sorted (ax, ay, az, dudt) and (vsig, qmax) -> caller arrays
+__global__ void k_unpack_forces(int n, const int32_t *__restrict__ perm, const float4 *__restrict__ acc,
+                                const float2 *__restrict__ vq, float *__restrict__ accel,
+                                float *__restrict__ dudt, float *__restrict__ vsig, float *__restrict__ qmax) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    long long i = perm[s];
+    float4 a = acc[s];
+    accel[3 * i] = a.x;
+    accel[3 * i + 1] = a.y;
+    accel[3 * i + 2] = a.z;
+    if (dudt) dudt[i] = a.w;
+    float2 q = vq[s];
+    if (vsig) vsig[i] = q.x;
+    if (qmax) qmax[i] = q.y;
+}
+
+namespace crk {
+int gather_rows(crk_ctx *ctx, const void *in, void *out, int w, cudaStream_t s) {
+    long long total = (long long)ctx->n * w;
+    if (total == 0) return CRK_OK;
+    k_gather_rows<<<grid_for(total, 256), 256, 0, s>>>(total, w, ctx->perm, (const uint32_t *)in, (uint32_t *)out);
+    ++ctx->launches;
+    CRK_LAUNCH_CHECK(ctx, "gather rows");
+    return CRK_OK;
+}
+int scatter_rows(crk_ctx *ctx, const void *in, void *out, int w, cudaStream_t s) {
+    long long total = (long long)ctx->n * w;
+    if (total == 0) return CRK_OK;
+    k_scatter_rows<<<grid_for(total, 256), 256, 0, s>>>(total, w, ctx->perm, (const uint32_t *)in, (uint32_t *)out);
+    ++ctx->launches;
+    CRK_LAUNCH_CHECK(ctx, "scatter rows");
+    return CRK_OK;
+}
+}  // namespace crk
+
+// ------------------------------------------------------------------ pass timing
+
+namespace crk {
+void prof_begin(crk_ctx *ctx, int id, cudaStream_t s) {
+    if (!ctx->prof_on || ctx->prof_n >= ctx->prof_cap) return;
+    ctx->prof_id[ctx->prof_n] = id;
+    cudaEventRecord(ctx->prof_ev[2 * ctx->prof_n], s);
+}
+void prof_end(crk_ctx *ctx, cudaStream_t s) {
+    if (!ctx->prof_on || ctx->prof_n >= ctx->prof_cap) return;
+    cudaEventRecord(ctx->prof_ev[2 * ctx->prof_n + 1], s);
+    ctx->prof_n++;
+}
+}  // namespace crk
+
+static void prof_free(crk_ctx *ctx) {
+    if (ctx->prof_ev) {
+        for (int k = 0; k < 2 * ctx->prof_cap; k++) cudaEventDestroy(ctx->prof_ev[k]);
+        free(ctx->prof_ev);
+        free(ctx->prof_id);
+    }
+    ctx->prof_ev = nullptr;
+    ctx->prof_id = nullptr;
+    ctx->prof_cap = 0;
+}
+
+extern "C" int crk_profile(crk_ctx *ctx, int enable) {
+    if (!ctx) return CRK_EINVAL;
+    if (enable && !ctx->prof_ev) {
+        int cap = 4096;
+        ctx->prof_ev = (cudaEvent_t *)calloc(2 * (size_t)cap, sizeof(cudaEvent_t));
+        ctx->prof_id = (int *)calloc((size_t)cap, sizeof(int));
+        if (!ctx->prof_ev || !ctx->prof_id) {
+            prof_free(ctx);
+            return crk_set_error(ctx, CRK_ENOMEM, "profile buffers");
+        }
+        for (int k = 0; k < 2 * cap; k++) {
+            if (cudaEventCreate(&ctx->prof_ev[k]) != cudaSuccess) {
+                ctx->prof_cap = k / 2;
+                prof_free(ctx);
+                return crk_set_error(ctx, CRK_ECUDA, "cudaEventCreate");
+            }
+            ctx->prof_cap = (k + 1) / 2;
+        }
+        ctx->prof_cap = cap;
+    }
+    ctx->prof_on = enable ? 1 : 0;
+    if (enable) ctx->prof_n = 0;
+    return CRK_OK;
+}
+
+extern "C" int crk_profile_read(crk_ctx *ctx, double *ms, long long *counts, long long *total_launches) {
+    if (!ctx) return CRK_EINVAL;
+    if (total_launches) *total_launches = ctx->launches;
+    for (int k = 0; k < PROF_NPASS; k++) {
+        if (ms) ms[k] = 0.0;
+        if (counts) counts[k] = 0;
+    }
+    for (int r = 0; r < ctx->prof_n; r++) {
+        CRK_CUDA(ctx, cudaEventSynchronize(ctx->prof_ev[2 * r + 1]));
+        float t = 0.f;
+        CRK_CUDA(ctx, cudaEventElapsedTime(&t, ctx->prof_ev[2 * r], ctx->prof_ev[2 * r + 1]));
+        int id = ctx->prof_id[r];
+        if (ms) ms[id] += t;
+        if (counts) counts[id] += 1;
+    }
+    return CRK_OK;
+}
+
+// ------------------------------------------------------------------ lifecycle
+
+extern "C" int crk_default_params(crk_params *p) {
+    if (!p) return CRK_EINVAL;
+    memset(p, 0, sizeof(*p));
+    p->gamma = 5.0 / 3.0;
+    p->n_h = 4.0;
+    p->N_res = 268.0;
+    p->C_l = 2.0;
+    p->C_q = 1.0;
+    p->eps = 0.1;
+    p->eta_crit = 1.0 / 4.0;
+    p->eta_fold = 0.2 / 4.0;
+    p->C_cfl = 0.25;
+    p->zeta = 4.0;
+    p->h_min = 1e-6;
+    p->h_max = 0.3;
+    p->dt_max = 1.0;
+    p->precision = 1;
+    p->kmax = 7;
+    return CRK_OK;
+}
+
+extern "C" int crk_create(const crk_params *p, crk_ctx **out) {
+    if (!out) return CRK_EINVAL;
+    *out = nullptr;
+    crk_params prm;
+    if (p) prm = *p; else crk_default_params(&prm);
+    if (!(prm.gamma > 1.0) || !(prm.n_h > 0) || !(prm.N_res > 0) || !(prm.eta_fold > 0) ||
+        !(prm.h_max > 0 && prm.h_max < 1.0 / 3.0) || !(prm.h_min > 0 && prm.h_min < prm.h_max) ||
+        prm.kmax < 1 || prm.kmax > 7 || (prm.precision != 0 && prm.precision != 1) || !(prm.dt_max > 0))
+        return CRK_EINVAL;
+    crk_ctx *ctx = new (std::nothrow) crk_ctx();
+    if (!ctx) return CRK_ENOMEM;
+    ctx->p = prm;
+    ctx->err[0] = 0;
+    memset(ctx->level_off, 0, sizeof(ctx->level_off));
+    memset(ctx->level_cnt, 0, sizeof(ctx->level_cnt));
+    int rc = CRK_OK;
+    if (cudaGetDevice(&ctx->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess) {
+        delete ctx;
+        return CRK_ECUDA;
+    }
+    rc |= dalloc(ctx, &ctx->counters, CNT_COUNT);
+    rc |= dalloc(ctx, &ctx->scan_tmp, 2 * 4096 + 64);
+    rc |= dalloc(ctx, &ctx->cell_start, ((size_t)1 << (3 * prm.kmax)) + 1);
+    rc |= dalloc(ctx, &ctx->d_scalars, 64);
+    if (!rc && cudaMallocHost((void **)&ctx->h_counters, CNT_COUNT * sizeof(unsigned long long)) != cudaSuccess)
+        rc = CRK_ENOMEM;
+    if (!rc && cudaMemset(ctx->counters, 0, CNT_COUNT * sizeof(unsigned long long)) != cudaSuccess) rc = CRK_ECUDA;
+    if (rc) {
+        crk_destroy(ctx);
+        return CRK_ENOMEM;
+    }
+    *out = ctx;
+    return CRK_OK;
+}
+
+extern "C" int crk_destroy(crk_ctx *ctx) {
+    if (!ctx) return CRK_EINVAL;
+    cudaDeviceSynchronize();
+    dfree(&ctx->key_a); dfree(&ctx->key_b); dfree(&ctx->idx_a); dfree(&ctx->idx_b);
+    dfree(&ctx->hist); dfree(&ctx->scan_tmp);
+    dfree(&ctx->q4); dfree(&ctx->hs); dfree(&ctx->perm); dfree(&ctx->keys);
+    dfree(&ctx->node_lo); dfree(&ctx->node_hi);
+    dfree(&ctx->gofs); dfree(&ctx->uofs); dfree(&ctx->glist); dfree(&ctx->ulist);
+    dfree(&ctx->cell_start); dfree(&ctx->counters);
+    dfree(&ctx->V); dfree(&ctx->Nn); dfree(&ctx->vel); dfree(&ctx->mass);
+    dfree(&ctx->corr); dfree(&ctx->gv); dfree(&ctx->acc); dfree(&ctx->vq);
+    dfree(&ctx->vb); dfree(&ctx->va); dfree(&ctx->du);
+    dfree(&ctx->st_pos); dfree(&ctx->st_vel); dfree(&ctx->st_half); dfree(&ctx->st_tmp);
+    dfree(&ctx->st_tmp1); dfree(&ctx->q_tmp); dfree(&ctx->h_tmp); dfree(&ctx->flags); dfree(&ctx->d_red); dfree(&ctx->d_dt); dfree(&ctx->d_scalars);
+    if (ctx->h_counters) cudaFreeHost(ctx->h_counters);
+    prof_free(ctx);
+    delete ctx;
+    return CRK_OK;
+}
+
+extern "C" const char *crk_last_error(const crk_ctx *ctx) { return ctx ? ctx->err : "null context"; }
+
+extern "C" int crk_sync(crk_ctx *ctx, void *stream) {
+    if (!ctx) return CRK_EINVAL;
+    int rc = crk_sync_counters(ctx, (cudaStream_t)stream);
+    if (rc) return rc;
+    if (ctx->h_counters[CNT_ERR_INPUT])
+        return crk_set_error(ctx, CRK_EINVAL, "%llu invalid particle records", ctx->h_counters[CNT_ERR_INPUT]);
+    return CRK_OK;
+}
+
+// ------------------------------------------------------------------ passes
+
+static int need_built(crk_ctx *ctx) {
+    if (!ctx) return CRK_EINVAL;
+    if (!ctx->built) return crk_set_error(ctx, CRK_ESTATE, "call crk_build_cells first");
+    return CRK_OK;
+}
+
+extern "C" int crk_build_cells(crk_ctx *ctx, int n, const float *pos_h, void *stream) {
+    if (!ctx) return CRK_EINVAL;
+    if (n < 0 || (n > 0 && !pos_h)) return crk_set_error(ctx, CRK_EINVAL, "bad n or pos_h");
+    if (n > (1 << 30)) return crk_set_error(ctx, CRK_EINVAL, "n beyond 2^30");
+    cudaStream_t s = (cudaStream_t)stream;
+    ctx->rates_valid = 0;
+    int rc = build_cells_sorted(ctx, n, (const float4 *)pos_h, nullptr, s);
+    if (rc) return rc;
+    rc = finish_build(ctx, s);
+    if (rc) {
+        ctx->built = 0;
+        return rc;
+    }
+    return CRK_OK;
+}
+
+extern "C" int crk_cells(crk_ctx *ctx, uint32_t *keys, int32_t *perm, int32_t *cell_start, int *k_out,
+                         void *stream) {
+    int rc = need_built(ctx);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    rc = crk_sync_counters(ctx, s);
+    if (rc) return rc;
+    int k = cell_level_host(ctx);
+    if (k_out) *k_out = k;
+    if (keys && ctx->n) CRK_CUDA(ctx, cudaMemcpyAsync(keys, ctx->keys, 4 * (size_t)ctx->n, cudaMemcpyDeviceToDevice, s));
+    if (perm && ctx->n) CRK_CUDA(ctx, cudaMemcpyAsync(perm, ctx->perm, 4 * (size_t)ctx->n, cudaMemcpyDeviceToDevice, s));
+    if (cell_start) {
+        size_t cnt = ((size_t)1 << (3 * k)) + 1;
+        if (ctx->n)
+            CRK_CUDA(ctx, cudaMemcpyAsync(cell_start, ctx->cell_start, 4 * cnt, cudaMemcpyDeviceToDevice, s));
+        else
+            CRK_CUDA(ctx, cudaMemsetAsync(cell_start, 0, 4 * cnt, s));
+    }
+    CRK_CUDA(ctx, cudaStreamSynchronize(s));
+    return CRK_OK;
+}
+
+extern "C" int crk_build_stats(crk_ctx *ctx, int *ntiles, long long *g, long long *u, void *stream) {
+    int rc = need_built(ctx);
+    if (rc) return rc;
+    rc = crk_sync_counters(ctx, (cudaStream_t)stream);
+    if (rc) return rc;
+    if (ntiles) *ntiles = ctx->ntiles;
+    if (g) *g = (long long)ctx->h_counters[CNT_GLIST];
+    if (u) *u = (long long)ctx->h_counters[CNT_ULIST];
+    return CRK_OK;
+}
+
+extern "C" int crk_neighbours(crk_ctx *ctx, int mode, int32_t *count, uint32_t *hash, void *stream) {
+    int rc = need_built(ctx);
+    if (rc) return rc;
+    if (!count || !hash || (mode != 0 && mode != 1)) return crk_set_error(ctx, CRK_EINVAL, "bad arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    rc = run_neighbours(ctx, mode, ctx->flags, reinterpret_cast<uint32_t *>(ctx->st_tmp1), s);
+    if (!rc) rc = scatter_rows(ctx, ctx->flags, count, 1, s);
+    if (!rc) rc = scatter_rows(ctx, ctx->st_tmp1, hash, 1, s);
+    return rc;
+}
+
+extern "C" int crk_volumes(crk_ctx *ctx, float *V, float *Nngb, long long *pairs, void *stream) {
+    int rc = need_built(ctx);
+    if (rc) return rc;
+    if (!V) return crk_set_error(ctx, CRK_EINVAL, "V is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    rc = run_volumes(ctx, s);
+    if (rc) return rc;
+    rc = scatter_rows(ctx, ctx->V, V, 1, s);
+    if (!rc && Nngb) rc = scatter_rows(ctx, ctx->Nn, Nngb, 1, s);
+    if (rc) return rc;
+    if (pairs) {
+        rc = crk_sync_counters(ctx, s);
+        if (rc) return rc;
+        *pairs = (long long)ctx->h_counters[CNT_PAIRS_G];
+    }
+    return CRK_OK;
+}
+
+extern "C" int crk_corrections(crk_ctx *ctx, const float *V, const float *vel_u, float *A, float *B,
+                               float *gradA, float *gradB, float *gradv, void *stream) {
+    int rc = need_built(ctx);
+    if (rc) return rc;
+    if (!V || !A || !B || !gradA || !gradB || (gradv && !vel_u))
+        return crk_set_error(ctx, CRK_EINVAL, "NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    int n = ctx->n;
+    rc = gather_rows(ctx, V, ctx->V, 1, s);
+    if (!rc && vel_u) rc = gather_rows(ctx, vel_u, ctx->vel, 4, s);
+    if (rc) return rc;
+    rc = run_corrections(ctx, gradv != nullptr, s);
+    if (rc) return rc;
+    if (n) {
+        k_unpack_corr<<<grid_for(n, 256), 256, 0, s>>>(n, ctx->perm, ctx->corr, A, B, gradA, gradB);
+        ++ctx->launches;
+        if (gradv) {
+            k_unpack_gv<<<grid_for(n, 256), 256, 0, s>>>(n, ctx->perm, ctx->gv, gradv);
+            ++ctx->launches;
+        }
+        CRK_LAUNCH_CHECK(ctx, "unpack corrections");
+    }
+    return CRK_OK;
+}
+
+static int pack_force_inputs(crk_ctx *ctx, const float *mass, const float *vel_u, const float *V, const float *A,
+                             const float *B, const float *gradA, const float *gradB, const float *gradv,
+                             cudaStream_t s) {
+    int n = ctx->n;
+    int rc = gather_rows(ctx, mass, ctx->mass, 1, s);
+    if (!rc) rc = gather_rows(ctx, vel_u, ctx->vel, 4, s);
+    if (!rc) rc = gather_rows(ctx, V, ctx->V, 1, s);
+    if (rc) return rc;
+    if (n) {
+        k_pack_corr<<<grid_for(n, 256), 256, 0, s>>>(n, ctx->perm, A, B, gradA, gradB, ctx->corr);
+        ++ctx->launches;
+        k_pack_gv<<<grid_for(n, 256), 256, 0, s>>>(n, ctx->perm, gradv, ctx->gv);
+        ++ctx->launches;
+        CRK_LAUNCH_CHECK(ctx, "pack force inputs");
+    }
+    return CRK_OK;
+}
+
+extern "C" int crk_forces(crk_ctx *ctx, const float *mass, const float *vel_u, const float *V, const float *A,
+                          const float *B, const float *gradA, const float *gradB, const float *gradv,
+                          float *accel, float *dudt, float *vsig, float *qmax, long long *pairs, void *stream) {
+    int rc = need_built(ctx);
+    if (rc) return rc;
+    if (!mass || !vel_u || !V || !A || !B || !gradA || !gradB || !gradv || !accel || !dudt)
+        return crk_set_error(ctx, CRK_EINVAL, "NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    rc = pack_force_inputs(ctx, mass, vel_u, V, A, B, gradA, gradB, gradv, s);
+    if (rc) return rc;
+    rc = run_forces(ctx, s);
+    if (rc) return rc;
+    int n = ctx->n;
+    if (n) {
+        k_unpack_forces<<<grid_for(n, 256), 256, 0, s>>>(n, ctx->perm, ctx->acc, ctx->vq, accel, dudt, vsig, qmax);
+        ++ctx->launches;
+        CRK_LAUNCH_CHECK(ctx, "unpack forces");
+    }
+    if (pairs) {
+        rc = crk_sync_counters(ctx, s);
+        if (rc) return rc;
+        *pairs = (long long)ctx->h_counters[CNT_PAIRS_U];
+    }
+    return CRK_OK;
+}
+
+extern "C" int crk_compatible(crk_ctx *ctx, const float *mass, const float *vel_u, const float *V, const float *A,
+                              const float *B, const float *gradA, const float *gradB, const float *gradv,
+                              const float *vel_before, const float *vel_after, float *du, void *stream) {
+    int rc = need_built(ctx);
+    if (rc) return rc;
+    if (!mass || !vel_u || !V || !A || !B || !gradA || !gradB || !gradv || !vel_before || !vel_after || !du)
+        return crk_set_error(ctx, CRK_EINVAL, "NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    rc = pack_force_inputs(ctx, mass, vel_u, V, A, B, gradA, gradB, gradv, s);
+    if (rc) return rc;
+    int n = ctx->n;
+    if (n) {
+        k_pack_v3<<<grid_for(n, 256), 256, 0, s>>>(n, ctx->perm, vel_before, ctx->vb);
+        ++ctx->launches;
+        k_pack_v3<<<grid_for(n, 256), 256, 0, s>>>(n, ctx->perm, vel_after, ctx->va);
+        ++ctx->launches;
+        CRK_LAUNCH_CHECK(ctx, "pack kick velocities");
+    }
+    rc = run_compatible(ctx, s);
+    if (rc) return rc;
+    return scatter_rows(ctx, ctx->du, du, 1, s);
+}

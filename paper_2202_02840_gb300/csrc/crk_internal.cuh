@@ -1,0 +1,214 @@
+// crk_internal.cuh -- engine context, device buffers and small device helpers
+// shared by the CUDA translation units of the CRKSPH pair engine.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <stdarg.h>
+
+#include "crk.h"
+
+namespace crk {
+
+constexpr int TILE = 32;          // particles per tile = one warp
+constexpr int MAX_LEVELS = 32;    // tile-tree levels (ntiles < 2^31)
+constexpr float TWO_M32 = 2.3283064365386963e-10f;   // 2^-32
+constexpr double PI_D = 3.14159265358979323846;
+
+// device counters (unsigned long long slots in ctx->counters)
+enum {
+    CNT_GLIST = 0,      // gather-list entries allocated
+    CNT_ULIST = 1,      // union-list entries allocated
+    CNT_PAIRS_G = 2,    // gather pairs (excl. self) of the last P1
+    CNT_PAIRS_U = 3,    // ordered union pairs of the last P4
+    CNT_ERR_INPUT = 4,  // invalid particle records found
+    CNT_HMAX = 5,       // max h as float bits
+    CNT_WORK = 6,       // dynamic tile counter of the persistent pair kernels
+    CNT_NOTDONE = 7,    // h iteration: particles not converged
+    CNT_DTMIN = 8,      // min per-particle time step (float bits)
+    CNT_COUNT = 16
+};
+
+// Pass-input records in sorted order.
+struct CorrRec {      // A, B, grad A, grad B of one particle (16 floats)
+    float4 c0;        // A, Bx, By, Bz
+    float4 c1;        // gAx, gAy, gAz, gB00
+    float4 c2;        // gB01, gB02, gB10, gB11
+    float4 c3;        // gB12, gB20, gB21, gB22
+};
+struct GvRec {        // grad v (9 floats) padded to 12
+    float4 g0;        // g00 g01 g02 g10
+    float4 g1;        // g11 g12 g20 g21
+    float4 g2;        // g22 - - -
+};
+
+struct Buf {          // one device allocation
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace crk
+
+struct crk_ctx {
+    crk_params p;
+    char err[512];
+    int device = 0;
+    int nsm = 0;
+
+    // capacity of the per-particle buffers
+    int cap_n = 0;
+    int cap_tiles = 0;
+    long long cap_glist = 0, cap_ulist = 0;
+
+    // last build
+    int n = 0;
+    int ntiles = 0;
+    int nlevels = 0;
+    int level_off[crk::MAX_LEVELS];
+    int level_cnt[crk::MAX_LEVELS];
+    int built = 0;
+    int cell_k = 0;
+    long long glist_total = 0, ulist_total = 0;
+
+    // sort scratch
+    uint32_t *key_a = nullptr, *key_b = nullptr;
+    int32_t *idx_a = nullptr, *idx_b = nullptr;
+    uint32_t *hist = nullptr;        // 256 * nblocks (+ scan scratch)
+    uint32_t *scan_tmp = nullptr;
+    int cap_hist = 0;
+
+    // sorted particle data
+    uint4 *q4 = nullptr;             // (qx, qy, qz, H)
+    float *hs = nullptr;             // h
+    int32_t *perm = nullptr;         // sorted slot -> caller index
+    uint32_t *keys = nullptr;        // sorted Morton keys
+
+    // tiles and tree: all levels concatenated, level 0 = tiles
+    uint4 *node_lo = nullptr;        // (xlo, ylo, zlo, Hmax)
+    uint4 *node_hi = nullptr;        // (xhi, yhi, zhi, count)
+    int cap_nodes = 0;
+
+    // interaction lists: per tile (offset, count) and entries (tile ids)
+    uint2 *gofs = nullptr, *uofs = nullptr;
+    uint32_t *glist = nullptr, *ulist = nullptr;
+
+    // chaining-mesh cell table (8^kmax + 1)
+    int32_t *cell_start = nullptr;
+
+    // device counters
+    unsigned long long *counters = nullptr;
+    unsigned long long *h_counters = nullptr;   // pinned host mirror
+
+    // pass buffers in sorted order
+    float *V = nullptr, *Nn = nullptr;
+    float4 *vel = nullptr;           // (vx, vy, vz, u) of the evaluation state
+    float *mass = nullptr;
+    crk::CorrRec *corr = nullptr;
+    crk::GvRec *gv = nullptr;
+    float4 *acc = nullptr;           // (ax, ay, az, dudt)
+    float2 *vq = nullptr;            // (vsig, qmax)
+    float4 *vb = nullptr, *va = nullptr;  // velocities before/after a kick (w unused)
+    float *du = nullptr;
+
+    // step state (sorted order)
+    float4 *st_pos = nullptr;        // (x, y, z, h) positions of the state
+    float4 *st_vel = nullptr;        // (vx, vy, vz, u) of the state
+    float4 *st_half = nullptr;       // (p_1/2, u_1/2)
+    float4 *st_tmp = nullptr;        // permutation scratch
+    float *st_tmp1 = nullptr;
+    uint4 *q_tmp = nullptr;          // build scratch: fixed-point records in input order
+    float *h_tmp = nullptr;          // build scratch: h in input order
+    int32_t *flags = nullptr;        // h iteration: converged flags
+    double *d_red = nullptr;         // FP64 reduction scratch
+    float *d_dt = nullptr;           // per-particle dt scratch
+    double *d_scalars = nullptr;     // [0] dt of the step, [1] dt_next, [2..] diagnostics
+    int rates_valid = 0;
+    int step_n = 0;
+
+    // launch accounting and per-pass event timing
+    long long launches = 0;
+    int prof_on = 0;
+    int prof_n = 0;
+    int prof_cap = 0;
+    cudaEvent_t *prof_ev = nullptr;   // 2 per record
+    int *prof_id = nullptr;
+};
+
+// ----------------------------------------------------------------- host helpers
+
+int crk_set_error(crk_ctx *ctx, int code, const char *fmt, ...);
+int crk_check_cuda(crk_ctx *ctx, cudaError_t e, const char *what);
+int crk_ensure_particles(crk_ctx *ctx, int n);
+int crk_ensure_lists(crk_ctx *ctx, long long ng, long long nu);
+int crk_sync_counters(crk_ctx *ctx, cudaStream_t s);
+
+#define CRK_CUDA(ctx, call)                                                      \
+    do {                                                                         \
+        cudaError_t e_ = (call);                                                 \
+        if (e_ != cudaSuccess) return crk_check_cuda((ctx), e_, #call);         \
+    } while (0)
+
+#define CRK_LAUNCH_CHECK(ctx, what)                                              \
+    do {                                                                         \
+        cudaError_t e_ = cudaGetLastError();                                     \
+        if (e_ != cudaSuccess) return crk_check_cuda((ctx), e_, (what));        \
+    } while (0)
+
+// internal entry points shared between translation units (sorted-order data)
+namespace crk {
+enum { PROF_P1 = 0, PROF_PN = 1, PROF_P2 = 2, PROF_P3 = 3, PROF_P4 = 4, PROF_P5 = 5, PROF_BUILD = 6,
+       PROF_NPASS = 8 };
+void prof_begin(crk_ctx *ctx, int id, cudaStream_t s);
+void prof_end(crk_ctx *ctx, cudaStream_t s);
+int build_cells_sorted(crk_ctx *ctx, int n, const float4 *pos_h, const int32_t *order,
+                       cudaStream_t s);
+int rebuild_lists(crk_ctx *ctx, cudaStream_t s);
+int build_tree(crk_ctx *ctx, cudaStream_t s);
+int finish_build(crk_ctx *ctx, cudaStream_t s);
+int cell_level_host(const crk_ctx *ctx);
+int run_volumes(crk_ctx *ctx, cudaStream_t s);
+int run_neighbours(crk_ctx *ctx, int mode, int32_t *cnt, uint32_t *hash, cudaStream_t s);
+int run_corrections(crk_ctx *ctx, bool with_gradv, cudaStream_t s);
+int run_forces(crk_ctx *ctx, cudaStream_t s);
+int run_compatible(crk_ctx *ctx, cudaStream_t s);
+int gather_rows(crk_ctx *ctx, const void *in, void *out, int width_words, cudaStream_t s);
+int scatter_rows(crk_ctx *ctx, const void *in, void *out, int width_words, cudaStream_t s);
+inline int grid_for(long long n, int block) { return (int)((n + block - 1) / block); }
+}  // namespace crk
+
+// ----------------------------------------------------------------- device helpers
+
+namespace crk {
+
+__device__ __forceinline__ uint32_t spread3(uint32_t v) {   // 10 bits -> every 3rd bit
+    v &= 0x3ffu;
+    v = (v | (v << 16)) & 0x030000ffu;
+    v = (v | (v << 8)) & 0x0300f00fu;
+    v = (v | (v << 4)) & 0x030c30c3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+
+__device__ __forceinline__ uint32_t morton30(uint32_t qx, uint32_t qy, uint32_t qz) {
+    return spread3(qx >> 22) | (spread3(qy >> 22) << 1) | (spread3(qz >> 22) << 2);
+}
+
+// floor(s * 2^32) for s in [0,1): the product is exact, truncation is floor.
+__device__ __forceinline__ uint32_t to_fixed(float s) {
+    return (uint32_t)__float2ull_rz(s * 4294967296.0f);
+}
+
+// squared fixed-point distance of a minimum-image separation (exact)
+__device__ __forceinline__ unsigned long long r2_fixed(int dx, int dy, int dz) {
+    return (unsigned long long)((long long)dx * dx) + (unsigned long long)((long long)dy * dy) +
+           (unsigned long long)((long long)dz * dz);
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+}  // namespace crk

@@ -1,0 +1,402 @@
+// crk_pairs.cu -- gather pair passes over gather(i) = {j : |dq|^2 < H_i^2}:
+//   P1 volumes           (CRK-HACC Sec. 1.2 eq:vol, Sec. 2.6 eq:hi)
+//   P2 RK corrections    (Sec. 1.2 eq:RK, eq:gRK, moment conditions)
+//   P3 velocity gradient (Sec. 1.2 eq:gradv)
+#include "crk_pass.cuh"
+
+namespace crk {
+
+// ================================================================= P1 volumes
+
+struct P1 {
+    struct Params {
+        const uint4 *q4;
+        const float *hs;
+        float *V, *Nn;
+    };
+    struct JRec {
+        uint4 q;
+    };
+    struct IState {
+        uint4 q;
+        unsigned long long H2;
+        float h, inv_h, acc;
+        int np;
+    };
+    __device__ static void init(IState &s, int i, bool valid, const Params &p) {
+        s.q = valid ? p.q4[i] : make_uint4(0, 0, 0, 0);
+        s.h = valid ? p.hs[i] : 1.f;
+        s.H2 = (unsigned long long)s.q.w * s.q.w;
+        s.inv_h = 1.f / s.h;
+        s.acc = 0.f;
+        s.np = 0;
+    }
+    __device__ static void stage(JRec &r, int j, const Params &p) { r.q = p.q4[j]; }
+    __device__ static void pair(IState &s, const JRec &r, int, int, bool, const Params &) {
+        int dx = (int)(s.q.x - r.q.x), dy = (int)(s.q.y - r.q.y), dz = (int)(s.q.z - r.q.z);
+        if (r2_fixed(dx, dy, dz) < s.H2) {
+            Sep x = separation(dx, dy, dz);
+            float eta = x.r * s.inv_h;
+            float t = fmaxf(1.f - eta, 0.f);
+            float t2 = t * t, t3 = t2 * t;
+            s.acc = fmaf(t3 * t3, fmaf(eta, fmaf(eta, K35_3, 6.f), 1.f), s.acc);
+            s.np++;
+        }
+    }
+    __device__ static void finish(IState &s, int i, const Params &p) {
+        float ih3 = s.inv_h * s.inv_h * s.inv_h;
+        float nsum = KW * ih3 * s.acc;                       // n_i, eq:vol
+        p.V[i] = 1.f / nsum;
+        if (p.Nn) p.Nn[i] = (4.18879020f * s.h * s.h * s.h) * nsum;   // eq:hi, 4/3 pi h^3 n_i
+    }
+    __device__ static int count(const IState &s) { return s.np - 1; }
+};
+
+int run_volumes(crk_ctx *ctx, cudaStream_t s) {
+    P1::Params p{ctx->q4, ctx->hs, ctx->V, ctx->Nn};
+    CRK_CUDA(ctx, cudaMemsetAsync(ctx->counters + CNT_PAIRS_G, 0, sizeof(unsigned long long), s));
+    return launch_pass<P1, 8>(ctx, PROF_P1, false, p, ctx->counters + CNT_PAIRS_G, s, "P1 volumes");
+}
+
+// ================================================================= neighbour sets
+
+__device__ __forceinline__ uint32_t fmix32(uint32_t h) {
+    h ^= h >> 16;
+    h *= 0x85ebca6bu;
+    h ^= h >> 13;
+    h *= 0xc2b2ae35u;
+    h ^= h >> 16;
+    return h;
+}
+
+template <bool UNION>
+struct PN {
+    struct Params {
+        const uint4 *q4;
+        const int32_t *perm;
+        int32_t *cnt;
+        uint32_t *hash;
+    };
+    struct __align__(16) JRec {
+        uint4 q;
+        int4 id;   // caller index, -, -, -
+    };
+    struct IState {
+        uint4 q;
+        unsigned long long H2;
+        int c;
+        uint32_t h;
+    };
+    __device__ static void init(IState &s, int i, bool valid, const Params &p) {
+        s.q = valid ? p.q4[i] : make_uint4(0, 0, 0, 0);
+        s.H2 = (unsigned long long)s.q.w * s.q.w;
+        s.c = 0;
+        s.h = 0u;
+    }
+    __device__ static void stage(JRec &r, int j, const Params &p) {
+        r.q = p.q4[j];
+        r.id = make_int4(p.perm[j], 0, 0, 0);
+    }
+    __device__ static void pair(IState &s, const JRec &r, int j, int i, bool valid, const Params &) {
+        int dx = (int)(s.q.x - r.q.x), dy = (int)(s.q.y - r.q.y), dz = (int)(s.q.z - r.q.z);
+        unsigned long long R2 = r2_fixed(dx, dy, dz);
+        bool in;
+        if (UNION) {
+            unsigned long long Hj2 = (unsigned long long)r.q.w * r.q.w;
+            in = valid && i != j && (R2 < s.H2 || R2 < Hj2);
+        } else {
+            in = R2 < s.H2;
+        }
+        if (in) {
+            s.c++;
+            s.h += fmix32((uint32_t)r.id.x + 1u);
+        }
+    }
+    __device__ static void finish(IState &s, int i, const Params &p) {
+        p.cnt[i] = s.c;
+        p.hash[i] = s.h;
+    }
+    __device__ static int count(const IState &) { return 0; }
+};
+
+int run_neighbours(crk_ctx *ctx, int mode, int32_t *cnt, uint32_t *hash, cudaStream_t s) {
+    if (mode == 0) {
+        PN<false>::Params p{ctx->q4, ctx->perm, cnt, hash};
+        return launch_pass<PN<false>, 8>(ctx, PROF_PN, false, p, nullptr, s, "neighbour sets");
+    }
+    PN<true>::Params p{ctx->q4, ctx->perm, cnt, hash};
+    return launch_pass<PN<true>, 8>(ctx, PROF_PN, true, p, nullptr, s, "neighbour sets");
+}
+
+// ================================================================= P2 corrections
+
+// symmetric index of (a,b): xx, xy, xz, yy, yz, zz
+__host__ __device__ constexpr int sym(int a, int b) {
+    return a <= b ? (a == 0 ? b : (a == 1 ? 2 + b : 5)) : (b == 0 ? a : (b == 1 ? 2 + a : 5));
+}
+
+// Solve the RK coefficients from the moments (derived from the two moment
+// conditions of Sec. 1.2):  B = -m2^-1 m1, A = 1/(m0 + m1.B),
+// d_g B = -m2^-1 (d_g m1 + (d_g m2) B), d_g A = -A^2 (d_g m0 + B.d_g m1 + m1.d_g B).
+// dm1[a*3+g] = d_g m1^a, dm2[sym(a,b)*3+g] = d_g m2^ab.
+template <typename T>
+__device__ __forceinline__ void rk_solve(float m0f, const float *m1f, const float *m2f, const float *dm0f,
+                                         const float *dm1f, const float *dm2f, CorrRec &out) {
+    T m[9];
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+        for (int b = 0; b < 3; b++) m[3 * a + b] = (T)m2f[sym(a, b)];
+    T c00 = m[4] * m[8] - m[5] * m[7];
+    T c01 = m[5] * m[6] - m[3] * m[8];
+    T c02 = m[3] * m[7] - m[4] * m[6];
+    T det = m[0] * c00 + m[1] * c01 + m[2] * c02;
+    T id = (T)1 / det;
+    T mi[9];
+    mi[0] = c00 * id;
+    mi[1] = (m[2] * m[7] - m[1] * m[8]) * id;
+    mi[2] = (m[1] * m[5] - m[2] * m[4]) * id;
+    mi[3] = c01 * id;
+    mi[4] = (m[0] * m[8] - m[2] * m[6]) * id;
+    mi[5] = (m[2] * m[3] - m[0] * m[5]) * id;
+    mi[6] = c02 * id;
+    mi[7] = (m[1] * m[6] - m[0] * m[7]) * id;
+    mi[8] = (m[0] * m[4] - m[1] * m[3]) * id;
+    T m1[3] = {(T)m1f[0], (T)m1f[1], (T)m1f[2]};
+    T B[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) B[a] = -(mi[3 * a] * m1[0] + mi[3 * a + 1] * m1[1] + mi[3 * a + 2] * m1[2]);
+    T A = (T)1 / ((T)m0f + m1[0] * B[0] + m1[1] * B[1] + m1[2] * B[2]);
+    T dB[9];
+#pragma unroll
+    for (int g = 0; g < 3; g++) {
+        T rhs[3];
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            T r = (T)dm1f[3 * a + g];
+#pragma unroll
+            for (int b = 0; b < 3; b++) r += (T)dm2f[3 * sym(a, b) + g] * B[b];
+            rhs[a] = r;
+        }
+#pragma unroll
+        for (int a = 0; a < 3; a++)
+            dB[3 * a + g] = -(mi[3 * a] * rhs[0] + mi[3 * a + 1] * rhs[1] + mi[3 * a + 2] * rhs[2]);
+    }
+    T dA[3];
+#pragma unroll
+    for (int g = 0; g < 3; g++) {
+        T acc = (T)dm0f[g];
+#pragma unroll
+        for (int a = 0; a < 3; a++) acc += B[a] * (T)dm1f[3 * a + g] + m1[a] * dB[3 * a + g];
+        dA[g] = -A * A * acc;
+    }
+    out.c0 = make_float4((float)A, (float)B[0], (float)B[1], (float)B[2]);
+    out.c1 = make_float4((float)dA[0], (float)dA[1], (float)dA[2], (float)dB[0]);
+    out.c2 = make_float4((float)dB[1], (float)dB[2], (float)dB[3], (float)dB[4]);
+    out.c3 = make_float4((float)dB[5], (float)dB[6], (float)dB[7], (float)dB[8]);
+}
+
+template <bool FP64_SOLVE>
+struct P2 {
+    struct Params {
+        const uint4 *q4;
+        const float *hs;
+        const float *V;
+        CorrRec *corr;
+    };
+    struct __align__(16) JRec {
+        uint4 q;
+        float4 v;   // V_j, -, -, -
+    };
+    struct IState {
+        uint4 q;
+        unsigned long long H2;
+        float h, inv_h;
+        float m0, m1[3], m2[6], dm0[3], s1[9], s2[18];
+    };
+    __device__ static void init(IState &s, int i, bool valid, const Params &p) {
+        s.q = valid ? p.q4[i] : make_uint4(0, 0, 0, 0);
+        s.h = valid ? p.hs[i] : 1.f;
+        s.H2 = (unsigned long long)s.q.w * s.q.w;
+        s.inv_h = 1.f / s.h;
+        s.m0 = 0.f;
+#pragma unroll
+        for (int a = 0; a < 3; a++) s.m1[a] = s.dm0[a] = 0.f;
+#pragma unroll
+        for (int a = 0; a < 6; a++) s.m2[a] = 0.f;
+#pragma unroll
+        for (int a = 0; a < 9; a++) s.s1[a] = 0.f;
+#pragma unroll
+        for (int a = 0; a < 18; a++) s.s2[a] = 0.f;
+    }
+    __device__ static void stage(JRec &r, int j, const Params &p) {
+        r.q = p.q4[j];
+        r.v = make_float4(p.V[j], 0.f, 0.f, 0.f);
+    }
+    __device__ static void pair(IState &s, const JRec &r, int, int, bool, const Params &) {
+        int dx = (int)(s.q.x - r.q.x), dy = (int)(s.q.y - r.q.y), dz = (int)(s.q.z - r.q.z);
+        if (r2_fixed(dx, dy, dz) < s.H2) {
+            Sep d = separation(dx, dy, dz);
+            float x[3] = {d.x, d.y, d.z};
+            float eta = d.r * s.inv_h;
+            float t = fmaxf(1.f - eta, 0.f);
+            float t2 = t * t, t4 = t2 * t2, t5 = t4 * t;
+            float Wu = t5 * t * fmaf(eta, fmaf(eta, K35_3, 6.f), 1.f);   // W / (495/(32 pi h^3))
+            float Gu = -fmaf(5.f, eta, 1.f) * t5;                        // grad W / (1155/(4 pi h^5) x)
+            float w = r.v.x * Wu, g = r.v.x * Gu;
+            float gx[3] = {g * x[0], g * x[1], g * x[2]};
+            float xx[6] = {x[0] * x[0], x[0] * x[1], x[0] * x[2], x[1] * x[1], x[1] * x[2], x[2] * x[2]};
+            s.m0 += w;
+#pragma unroll
+            for (int a = 0; a < 3; a++) {
+                s.m1[a] = fmaf(w, x[a], s.m1[a]);
+                s.dm0[a] += gx[a];
+            }
+#pragma unroll
+            for (int p = 0; p < 6; p++) s.m2[p] = fmaf(w, xx[p], s.m2[p]);
+#pragma unroll
+            for (int a = 0; a < 3; a++)
+#pragma unroll
+                for (int gg = 0; gg < 3; gg++) s.s1[3 * a + gg] = fmaf(x[a], gx[gg], s.s1[3 * a + gg]);
+#pragma unroll
+            for (int p = 0; p < 6; p++)
+#pragma unroll
+                for (int gg = 0; gg < 3; gg++) s.s2[3 * p + gg] = fmaf(xx[p], gx[gg], s.s2[3 * p + gg]);
+        }
+    }
+    __device__ static void finish(IState &s, int i, const Params &p) {
+        float ih = s.inv_h, ih2 = ih * ih, ih3 = ih2 * ih;
+        float cW = KW * ih3, cG = KG * ih3 * ih2;
+        float m0 = cW * s.m0, m1[3], m2[6], dm0[3], dm1[9], dm2[18];
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            m1[a] = cW * s.m1[a];
+            dm0[a] = cG * s.dm0[a];
+        }
+#pragma unroll
+        for (int q = 0; q < 6; q++) m2[q] = cW * s.m2[q];
+        // d_g m1^a = delta_ag m0 + sum V x^a d_g W
+#pragma unroll
+        for (int a = 0; a < 3; a++)
+#pragma unroll
+            for (int g = 0; g < 3; g++) dm1[3 * a + g] = cG * s.s1[3 * a + g] + (a == g ? m0 : 0.f);
+        // d_g m2^ab = delta_ag m1^b + delta_bg m1^a + sum V x^a x^b d_g W
+#pragma unroll
+        for (int a = 0; a < 3; a++)
+#pragma unroll
+            for (int b = a; b < 3; b++)
+#pragma unroll
+                for (int g = 0; g < 3; g++) {
+                    int q = sym(a, b);
+                    float v = cG * s.s2[3 * q + g];
+                    if (a == g) v += m1[b];
+                    if (b == g) v += m1[a];
+                    dm2[3 * q + g] = v;
+                }
+        CorrRec out;
+        if (FP64_SOLVE)
+            rk_solve<double>(m0, m1, m2, dm0, dm1, dm2, out);
+        else
+            rk_solve<float>(m0, m1, m2, dm0, dm1, dm2, out);
+        p.corr[i] = out;
+    }
+    __device__ static int count(const IState &) { return 0; }
+};
+
+// ================================================================= P3 grad v
+
+struct P3 {
+    struct Params {
+        const uint4 *q4;
+        const float *hs;
+        const float *V;
+        const float4 *vel;
+        const CorrRec *corr;
+        GvRec *gv;
+    };
+    struct __align__(16) JRec {
+        uint4 q;
+        float4 vv;   // vx, vy, vz, V
+    };
+    struct IState {
+        uint4 q;
+        unsigned long long H2;
+        float inv_h, cW, cG;
+        float A, B[3], gA[3], gB[9], v[3];
+        float acc[9];
+    };
+    __device__ static void init(IState &s, int i, bool valid, const Params &p) {
+        s.q = valid ? p.q4[i] : make_uint4(0, 0, 0, 0);
+        float h = valid ? p.hs[i] : 1.f;
+        s.H2 = (unsigned long long)s.q.w * s.q.w;
+        s.inv_h = 1.f / h;
+        float ih2 = s.inv_h * s.inv_h, ih3 = ih2 * s.inv_h;
+        s.cW = KW * ih3;
+        s.cG = -KG * ih3 * ih2;
+        CorrRec c = valid ? p.corr[i] : CorrRec{};
+        float4 v = valid ? p.vel[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        s.A = c.c0.x;
+        s.B[0] = c.c0.y; s.B[1] = c.c0.z; s.B[2] = c.c0.w;
+        s.gA[0] = c.c1.x; s.gA[1] = c.c1.y; s.gA[2] = c.c1.z;
+        s.gB[0] = c.c1.w; s.gB[1] = c.c2.x; s.gB[2] = c.c2.y; s.gB[3] = c.c2.z; s.gB[4] = c.c2.w;
+        s.gB[5] = c.c3.x; s.gB[6] = c.c3.y; s.gB[7] = c.c3.z; s.gB[8] = c.c3.w;
+        s.v[0] = v.x; s.v[1] = v.y; s.v[2] = v.z;
+#pragma unroll
+        for (int k = 0; k < 9; k++) s.acc[k] = 0.f;
+    }
+    __device__ static void stage(JRec &r, int j, const Params &p) {
+        r.q = p.q4[j];
+        float4 v = p.vel[j];
+        r.vv = make_float4(v.x, v.y, v.z, p.V[j]);
+    }
+    __device__ static void pair(IState &s, const JRec &r, int, int, bool, const Params &) {
+        int dx = (int)(s.q.x - r.q.x), dy = (int)(s.q.y - r.q.y), dz = (int)(s.q.z - r.q.z);
+        if (r2_fixed(dx, dy, dz) < s.H2) {
+            Sep d = separation(dx, dy, dz);
+            float x[3] = {d.x, d.y, d.z};
+            float eta = d.r * s.inv_h;
+            float t = fmaxf(1.f - eta, 0.f);
+            float t2 = t * t, t4 = t2 * t2, t5 = t4 * t;
+            float W = s.cW * t5 * t * fmaf(eta, fmaf(eta, K35_3, 6.f), 1.f);
+            float G = s.cG * fmaf(5.f, eta, 1.f) * t5;       // grad W = G x
+            // eq:gRK with the i-side coefficients
+            float sB = fmaf(s.B[0], x[0], fmaf(s.B[1], x[1], fmaf(s.B[2], x[2], 1.f)));
+            float sW = sB * W, AW = s.A * W, AsG = s.A * sB * G;
+            float gR[3];
+#pragma unroll
+            for (int g = 0; g < 3; g++) {
+                float gBx = fmaf(s.gB[g], x[0], fmaf(s.gB[3 + g], x[1], s.gB[6 + g] * x[2]));
+                gR[g] = fmaf(s.gA[g], sW, fmaf(AW, gBx + s.B[g], AsG * x[g]));
+            }
+            float Vd[3] = {r.vv.w * (s.v[0] - r.vv.x), r.vv.w * (s.v[1] - r.vv.y), r.vv.w * (s.v[2] - r.vv.z)};
+#pragma unroll
+            for (int a = 0; a < 3; a++)
+#pragma unroll
+                for (int b = 0; b < 3; b++) s.acc[3 * a + b] = fmaf(-Vd[a], gR[b], s.acc[3 * a + b]);
+        }
+    }
+    __device__ static void finish(IState &s, int i, const Params &p) {
+        GvRec g;
+        g.g0 = make_float4(s.acc[0], s.acc[1], s.acc[2], s.acc[3]);
+        g.g1 = make_float4(s.acc[4], s.acc[5], s.acc[6], s.acc[7]);
+        g.g2 = make_float4(s.acc[8], 0.f, 0.f, 0.f);
+        p.gv[i] = g;
+    }
+    __device__ static int count(const IState &) { return 0; }
+};
+
+int run_corrections(crk_ctx *ctx, bool with_gradv, cudaStream_t s) {
+    int rc;
+    if (ctx->p.precision == 1) {
+        P2<true>::Params p{ctx->q4, ctx->hs, ctx->V, ctx->corr};
+        rc = launch_pass<P2<true>, 4>(ctx, PROF_P2, false, p, nullptr, s, "P2 corrections");
+    } else {
+        P2<false>::Params p{ctx->q4, ctx->hs, ctx->V, ctx->corr};
+        rc = launch_pass<P2<false>, 4>(ctx, PROF_P2, false, p, nullptr, s, "P2 corrections");
+    }
+    if (rc || !with_gradv) return rc;
+    P3::Params p3{ctx->q4, ctx->hs, ctx->V, ctx->vel, ctx->corr, ctx->gv};
+    return launch_pass<P3, 4>(ctx, PROF_P3, false, p3, nullptr, s, "P3 grad v");
+}
+
+}  // namespace crk

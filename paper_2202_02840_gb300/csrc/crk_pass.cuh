@@ -1,0 +1,98 @@
+// crk_pass.cuh -- warp-per-tile skeleton of the pair passes.
+//
+// One warp owns one i-tile (lane = particle i of 32 consecutive sorted
+// particles) and walks the tile's interaction list.  Each neighbour tile J is
+// staged once in shared memory (lane l loads record J*32+l, coalesced) and
+// every lane then loops over the 32 staged records, testing the exact
+// fixed-point predicate and accumulating in registers.  No atomics, no
+// inter-warp synchronisation: results are deterministic.
+#pragma once
+
+#include "crk_internal.cuh"
+
+namespace crk {
+
+struct PassGeom {
+    int n;
+    int ntiles;
+    const uint2 *ofs;        // per i-tile (offset, count) into list
+    const uint32_t *list;    // neighbour tile ids
+    unsigned long long *pairs;  // optional pair counter
+};
+
+// P must provide: Params, JRec, IState,
+//   init(IState&, int i, bool valid, const Params&)
+//   stage(JRec&, int j, const Params&)
+//   pair(IState&, const JRec&, int j, int i, bool valid, const Params&)
+//   finish(IState&, int i, const Params&)           (valid lanes only)
+//   count(const IState&) -> pairs of this lane
+template <class P, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32) k_pass(PassGeom g, typename P::Params prm) {
+    __shared__ typename P::JRec sj[WARPS][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int tile = blockIdx.x * WARPS + w;
+    if (tile >= g.ntiles) return;
+    const int i = tile * TILE + lane;
+    const bool valid = i < g.n;
+    typename P::IState st;
+    P::init(st, i, valid, prm);
+    const uint2 lo = g.ofs[tile];
+    for (uint32_t t = 0; t < lo.y; t++) {
+        const int J = (int)g.list[lo.x + t];
+        const int j0 = J * TILE;
+        const int cnt = min(TILE, g.n - j0);
+        __syncwarp();
+        if (lane < cnt) P::stage(sj[w][lane], j0 + lane, prm);
+        __syncwarp();
+        for (int jj = 0; jj < cnt; jj++) P::pair(st, sj[w][jj], j0 + jj, i, valid, prm);
+    }
+    if (valid) P::finish(st, i, prm);
+    if (g.pairs) {
+        unsigned c = valid ? (unsigned)P::count(st) : 0u;
+        c = __reduce_add_sync(0xffffffffu, c);
+        if (lane == 0 && c) atomicAdd(g.pairs, (unsigned long long)c);
+    }
+}
+
+template <class P, int WARPS>
+int launch_pass(crk_ctx *ctx, int prof_id, bool union_list, const typename P::Params &prm,
+                unsigned long long *pairs, cudaStream_t s, const char *what) {
+    if (ctx->n == 0) return CRK_OK;
+    PassGeom g;
+    g.n = ctx->n;
+    g.ntiles = ctx->ntiles;
+    g.ofs = union_list ? ctx->uofs : ctx->gofs;
+    g.list = union_list ? ctx->ulist : ctx->glist;
+    g.pairs = pairs;
+    prof_begin(ctx, prof_id, s);
+    k_pass<P, WARPS><<<grid_for(ctx->ntiles, WARPS), WARPS * 32, 0, s>>>(g, prm);
+    ++ctx->launches;
+    prof_end(ctx, s);
+    CRK_LAUNCH_CHECK(ctx, what);
+    return CRK_OK;
+}
+
+// ---------------------------------------------------------------- kernel maths
+
+// C4 Wendland kernel (eq:C4) with eta = r/h and t = 1 - eta:
+//   W = 495/(32 pi h^3) t^6 (1 + 6 eta + 35/3 eta^2)
+//   grad_i W = -1155/(4 pi h^5) (1 + 5 eta) t^5 x_ij
+constexpr float KW = 4.9238560f;       // 495 / (32 pi)
+constexpr float KG = 91.9120344f;      // 1155 / (4 pi)
+constexpr float K35_3 = 11.6666667f;   // 35 / 3
+
+struct Sep {
+    float x, y, z, r2, r;
+};
+
+__device__ __forceinline__ Sep separation(int dx, int dy, int dz) {
+    Sep s;
+    s.x = (float)dx * TWO_M32;
+    s.y = (float)dy * TWO_M32;
+    s.z = (float)dz * TWO_M32;
+    s.r2 = fmaf(s.x, s.x, fmaf(s.y, s.y, s.z * s.z));
+    s.r = sqrtf(s.r2);
+    return s;
+}
+
+}  // namespace crk

@@ -1,0 +1,380 @@
+// crk_step.cu -- the hydro step of CRK-HACC Sec. 2.1 (velocity-Verlet KDK
+// operator eq:verletOP with predicted p_p, u_p and the compatible energy of
+// eq:compEng), the time-step criteria of Sec. 2.1 (natural units, no gravity),
+// the evolved smoothing length of Sec. 2.6 (eq:thacker) and its fixed-point
+// solve, and FP64 conservation diagnostics.
+//
+// Between steps the engine keeps the last evaluation (sorted particle copies,
+// A, B, grad A, grad B, grad v, accelerations, evaluation velocities) so the
+// first half kick of the next step reuses it: one force evaluation per step.
+#include "crk_internal.cuh"
+
+#include <math.h>
+#include <string.h>
+
+namespace crk {
+
+static float bits_to_float(uint32_t b) {
+    float f;
+    memcpy(&f, &b, sizeof(f));
+    return f;
+}
+
+struct StepConsts {
+    float gamma, gm1, inv_nh, C_cfl, zeta, N_res, h_min, h_max;
+    double dt_max;
+};
+
+static StepConsts step_consts(const crk_params &p) {
+    StepConsts c;
+    c.gamma = (float)p.gamma;
+    c.gm1 = (float)(p.gamma - 1.0);
+    c.inv_nh = (float)(1.0 / p.n_h);
+    c.C_cfl = (float)p.C_cfl;
+    c.zeta = (float)p.zeta;
+    c.N_res = (float)p.N_res;
+    c.h_min = (float)p.h_min;
+    c.h_max = (float)p.h_max;
+    c.dt_max = p.dt_max;
+    return c;
+}
+
+// Per-particle time step (Sec. 2.1, adot = 0, pure hydro so r_soft -> inf):
+// v_max = max(v_sig, c_s, sqrt(zeta Q/rho), h_hat |tr grad v|),
+// dt_i = min(C_CFL h_hat / v_max, sqrt(h_hat / |a|)); global min as float bits.
+__global__ void k_cfl(int n, StepConsts c, const float *__restrict__ hs, const float *__restrict__ V,
+                      const float *__restrict__ mass, const float4 *__restrict__ vel,
+                      const float4 *__restrict__ acc, const float2 *__restrict__ vq,
+                      const GvRec *__restrict__ gv, unsigned long long *dtmin) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    float dt = 3.0e38f;
+    if (s < n) {
+        float hh = hs[s] * c.inv_nh;
+        float rho = mass[s] / V[s];
+        float u = vel[s].w;
+        float cs = sqrtf(fmaxf(c.gamma * c.gm1 * u, 0.f));
+        float2 q = vq[s];
+        float csq = sqrtf(fmaxf(c.zeta * q.y / rho, 0.f));
+        GvRec g = gv[s];
+        float div = fabsf(g.g0.x + g.g1.x + g.g2.x);
+        float vmax = fmaxf(fmaxf(q.x, cs), fmaxf(csq, hh * div));
+        if (vmax > 0.f) dt = fminf(dt, c.C_cfl * hh / vmax);
+        float4 a = acc[s];
+        float am = sqrtf(a.x * a.x + a.y * a.y + a.z * a.z);
+        if (am > 0.f) dt = fminf(dt, sqrtf(hh / am));
+    }
+    unsigned m = __reduce_min_sync(0xffffffffu, __float_as_uint(dt));
+    if ((threadIdx.x & 31) == 0) atomicMin(dtmin, (unsigned long long)m);
+}
+
+// d_scalars[0] = dt of this step: the requested dt, or min(CFL dt, dt_max)
+__global__ void k_pick_dt(double dt_req, double dt_max, const unsigned long long *dtmin, double *sc) {
+    double dt = dt_req;
+    if (!(dt > 0.0)) {
+        dt = (double)__uint_as_float((uint32_t)*dtmin);
+        if (!(dt < dt_max)) dt = dt_max;
+    }
+    sc[0] = dt;
+}
+
+// first half kick of eq:verletOP: p_1/2 = p + a dt/2; vb = p, va = p_1/2
+__global__ void k_kick1(int n, const double *sc, const float4 *__restrict__ st_vel, const float4 *__restrict__ acc,
+                        float4 *__restrict__ vb, float4 *__restrict__ va) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    float h = (float)(0.5 * sc[0]);
+    float4 v = st_vel[s], a = acc[s];
+    vb[s] = make_float4(v.x, v.y, v.z, 0.f);
+    va[s] = make_float4(fmaf(h, a.x, v.x), fmaf(h, a.y, v.y), fmaf(h, a.z, v.z), 0.f);
+}
+
+// u_1/2 = u + du dt/2; predictor p_p = p_1/2 + a dt/2, u_p = u_1/2 + du dt/2;
+// drift x1 = x + p_1/2 dt (periodic wrap into [0,1)).
+__global__ void k_half_drift(int n, const double *sc, float4 *__restrict__ st_pos, float4 *__restrict__ st_vel,
+                             float4 *__restrict__ st_half, const float4 *__restrict__ va,
+                             const float4 *__restrict__ acc, const float *__restrict__ du) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    float dt = (float)sc[0], h = 0.5f * dt;
+    float4 v = st_vel[s], ph = va[s], a = acc[s];
+    float uh = fmaf(h, du[s], v.w);
+    st_half[s] = make_float4(ph.x, ph.y, ph.z, uh);
+    st_vel[s] = make_float4(fmaf(h, a.x, ph.x), fmaf(h, a.y, ph.y), fmaf(h, a.z, ph.z), fmaf(h, du[s], uh));
+    float4 p = st_pos[s];
+    float x[3] = {fmaf(dt, ph.x, p.x), fmaf(dt, ph.y, p.y), fmaf(dt, ph.z, p.z)};
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        x[k] -= floorf(x[k]);
+        if (x[k] >= 1.f) x[k] = 0.f;
+        if (x[k] < 0.f) x[k] = 0.f;
+    }
+    st_pos[s] = make_float4(x[0], x[1], x[2], p.w);
+}
+
+// new slot s takes old slot idx[s]
+__global__ void k_permute3(int n, const int32_t *__restrict__ idx, const float4 *__restrict__ a,
+                           float4 *__restrict__ ao, const float4 *__restrict__ b, float4 *__restrict__ bo,
+                           const float4 *__restrict__ c, float4 *__restrict__ co) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    int o = idx[s];
+    ao[s] = a[o];
+    bo[s] = b[o];
+    co[s] = c[o];
+}
+
+// second half kick: p1 = p_1/2 + a1 dt/2; vb = p_1/2, va = p1
+__global__ void k_kick2(int n, const double *sc, const float4 *__restrict__ st_half, const float4 *__restrict__ acc,
+                        float4 *__restrict__ vb, float4 *__restrict__ va) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    float h = (float)(0.5 * sc[0]);
+    float4 v = st_half[s], a = acc[s];
+    vb[s] = make_float4(v.x, v.y, v.z, 0.f);
+    va[s] = make_float4(fmaf(h, a.x, v.x), fmaf(h, a.y, v.y), fmaf(h, a.z, v.z), 0.f);
+}
+
+// final state: v1 = va, u1 = u_1/2 + du dt/2; h advanced by eq:thacker
+__global__ void k_finish(int n, const double *sc, StepConsts c, const float4 *__restrict__ st_half,
+                         const float4 *__restrict__ va, const float *__restrict__ du, const float *__restrict__ Nn,
+                         const float *__restrict__ hs, float4 *__restrict__ st_vel, float4 *__restrict__ st_pos) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    float h = (float)(0.5 * sc[0]);
+    float4 a = va[s];
+    st_vel[s] = make_float4(a.x, a.y, a.z, fmaf(h, du[s], st_half[s].w));
+    float d = cbrtf(c.N_res / Nn[s]);
+    float lam = d < 1.f ? 0.2f * (1.f + d * d) : 0.2f * (1.f + 1.f / (d * d * d));
+    float hn = hs[s] * (1.f - lam + lam * d);
+    hn = fminf(fmaxf(hn, c.h_min), c.h_max);
+    float4 p = st_pos[s];
+    st_pos[s] = make_float4(p.x, p.y, p.z, hn);
+}
+
+// FP64 sums of 1/2 m v^2, m u, m v: per-block partials, then one ordered pass.
+constexpr int RED_BLOCKS = 1024;
+__global__ void k_energy_partials(int n, const float4 *__restrict__ vel, const float *__restrict__ mass,
+                                  double *__restrict__ part) {
+    __shared__ double sh[5][256];
+    double a[5] = {0, 0, 0, 0, 0};
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+        float4 v = vel[s];
+        double m = mass[s];
+        double vx = v.x, vy = v.y, vz = v.z;
+        a[0] += 0.5 * m * (vx * vx + vy * vy + vz * vz);
+        a[1] += m * (double)v.w;
+        a[2] += m * vx;
+        a[3] += m * vy;
+        a[4] += m * vz;
+    }
+    for (int k = 0; k < 5; k++) sh[k][threadIdx.x] = a[k];
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o)
+            for (int k = 0; k < 5; k++) sh[k][threadIdx.x] += sh[k][threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x < 5) part[blockIdx.x * 8 + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+__global__ void k_energy_final(int nb, const double *__restrict__ part, double *__restrict__ out) {
+    if (threadIdx.x < 5) {
+        double s = 0;
+        for (int b = 0; b < nb; b++) s += part[b * 8 + threadIdx.x];
+        out[threadIdx.x] = s;
+    }
+}
+
+// h iteration: Thacker update of every particle not yet converged (eq:thacker)
+__global__ void k_h_iter(int n, StepConsts c, float tol, const float *__restrict__ Nn, float *__restrict__ hs,
+                         uint4 *__restrict__ q4, int32_t *__restrict__ flags, unsigned long long *notdone) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned nd = 0;
+    if (s < n && !flags[s]) {
+        float d = cbrtf(c.N_res / Nn[s]);
+        if (fabsf(d - 1.f) <= tol) {
+            flags[s] = 1;
+        } else {
+            float lam = d < 1.f ? 0.2f * (1.f + d * d) : 0.2f * (1.f + 1.f / (d * d * d));
+            float hn = hs[s] * (1.f - lam + lam * d);
+            hn = fminf(fmaxf(hn, c.h_min), c.h_max);
+            hs[s] = hn;
+            uint4 q = q4[s];
+            q.w = to_fixed(hn);
+            q4[s] = q;
+            nd = 1;
+        }
+    }
+    nd = __reduce_add_sync(0xffffffffu, nd);
+    if ((threadIdx.x & 31) == 0 && nd) atomicAdd(notdone, (unsigned long long)nd);
+}
+
+__global__ void k_write_h(int n, const int32_t *__restrict__ perm, const float *__restrict__ hs, float4 *pos_h) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    pos_h[perm[s]].w = hs[s];
+}
+
+// ------------------------------------------------------------------ evaluation
+
+// P1 -> P2 -> P3 -> P4 at the current build, with ctx->vel / ctx->mass set.
+static int evaluate(crk_ctx *ctx, cudaStream_t s) {
+    int rc = run_volumes(ctx, s);
+    if (!rc) rc = run_corrections(ctx, true, s);
+    if (!rc) rc = run_forces(ctx, s);
+    if (rc) return rc;
+    StepConsts c = step_consts(ctx->p);
+    unsigned long long big = 0x7f7fffffull;   // FLT_MAX bits
+    CRK_CUDA(ctx, cudaMemcpyAsync(ctx->counters + CNT_DTMIN, &big, sizeof(big), cudaMemcpyHostToDevice, s));
+    k_cfl<<<grid_for(ctx->n, 256), 256, 0, s>>>(ctx->n, c, ctx->hs, ctx->V, ctx->mass, ctx->vel, ctx->acc,
+                                                  ctx->vq, ctx->gv, ctx->counters + CNT_DTMIN);
+    ++ctx->launches;
+    CRK_LAUNCH_CHECK(ctx, "CFL");
+    return CRK_OK;
+}
+
+}  // namespace crk
+
+using namespace crk;
+
+extern "C" int crk_reset_rates(crk_ctx *ctx) {
+    if (!ctx) return CRK_EINVAL;
+    ctx->rates_valid = 0;
+    return CRK_OK;
+}
+
+extern "C" int crk_step(crk_ctx *ctx, int n, float *pos_h, float *vel_u, const float *mass, double dt,
+                        crk_diag *diag, void *stream) {
+    if (!ctx) return CRK_EINVAL;
+    if (n <= 0 || !pos_h || !vel_u || !mass) return crk_set_error(ctx, CRK_EINVAL, "bad arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    StepConsts c = step_consts(ctx->p);
+    int rc;
+    int b = 256, g = grid_for(n, b);
+    if (!ctx->rates_valid || ctx->step_n != n || !ctx->built || ctx->n != n) {
+        rc = build_cells_sorted(ctx, n, (const float4 *)pos_h, nullptr, s);
+        if (!rc) rc = finish_build(ctx, s);
+        if (rc) return rc;
+        rc = gather_rows(ctx, pos_h, ctx->st_pos, 4, s);
+        if (!rc) rc = gather_rows(ctx, vel_u, ctx->st_vel, 4, s);
+        if (!rc) rc = gather_rows(ctx, mass, ctx->mass, 1, s);
+        if (rc) return rc;
+        CRK_CUDA(ctx, cudaMemcpyAsync(ctx->vel, ctx->st_vel, sizeof(float4) * n, cudaMemcpyDeviceToDevice, s));
+        rc = evaluate(ctx, s);
+        if (rc) return rc;
+        ctx->rates_valid = 1;
+        ctx->step_n = n;
+    } else {
+        rc = gather_rows(ctx, pos_h, ctx->st_pos, 4, s);
+        if (!rc) rc = gather_rows(ctx, vel_u, ctx->st_vel, 4, s);
+        if (rc) return rc;
+    }
+    k_pick_dt<<<1, 1, 0, s>>>(dt, c.dt_max, ctx->counters + CNT_DTMIN, ctx->d_scalars);
+    ++ctx->launches;
+    // first half kick with the cached rates, compatible energy of that kick
+    k_kick1<<<g, b, 0, s>>>(n, ctx->d_scalars, ctx->st_vel, ctx->acc, ctx->vb, ctx->va);
+    ++ctx->launches;
+    CRK_LAUNCH_CHECK(ctx, "kick");
+    rc = run_compatible(ctx, s);
+    if (rc) return rc;
+    k_half_drift<<<g, b, 0, s>>>(n, ctx->d_scalars, ctx->st_pos, ctx->st_vel, ctx->st_half, ctx->va, ctx->acc,
+                                 ctx->du);
+    ++ctx->launches;
+    CRK_LAUNCH_CHECK(ctx, "drift");
+    // rebuild at x1 (input order = current sorted order)
+    rc = build_cells_sorted(ctx, n, ctx->st_pos, ctx->perm, s);
+    if (!rc) rc = finish_build(ctx, s);
+    if (rc) {
+        ctx->rates_valid = 0;
+        return rc;
+    }
+    k_permute3<<<g, b, 0, s>>>(n, ctx->idx_a, ctx->st_pos, ctx->st_tmp, ctx->st_vel, ctx->vb, ctx->st_half, ctx->va);
+    ++ctx->launches;
+    CRK_LAUNCH_CHECK(ctx, "permute state");
+    float4 *t;
+    t = ctx->st_pos; ctx->st_pos = ctx->st_tmp; ctx->st_tmp = t;
+    t = ctx->st_vel; ctx->st_vel = ctx->vb; ctx->vb = t;
+    t = ctx->st_half; ctx->st_half = ctx->va; ctx->va = t;
+    rc = gather_rows(ctx, mass, ctx->mass, 1, s);
+    if (rc) return rc;
+    // evaluation at (x1, p_p, u_p)
+    CRK_CUDA(ctx, cudaMemcpyAsync(ctx->vel, ctx->st_vel, sizeof(float4) * n, cudaMemcpyDeviceToDevice, s));
+    rc = evaluate(ctx, s);
+    if (rc) {
+        ctx->rates_valid = 0;
+        return rc;
+    }
+    // second half kick and its compatible energy
+    k_kick2<<<g, b, 0, s>>>(n, ctx->d_scalars, ctx->st_half, ctx->acc, ctx->vb, ctx->va);
+    ++ctx->launches;
+    CRK_LAUNCH_CHECK(ctx, "kick");
+    rc = run_compatible(ctx, s);
+    if (rc) return rc;
+    k_finish<<<g, b, 0, s>>>(n, ctx->d_scalars, c, ctx->st_half, ctx->va, ctx->du, ctx->Nn, ctx->hs,
+                             ctx->st_vel, ctx->st_pos);
+    ++ctx->launches;
+    CRK_LAUNCH_CHECK(ctx, "finish step");
+    rc = scatter_rows(ctx, ctx->st_pos, pos_h, 4, s);
+    if (!rc) rc = scatter_rows(ctx, ctx->st_vel, vel_u, 4, s);
+    if (rc) return rc;
+    if (diag) {
+        k_energy_partials<<<RED_BLOCKS, 256, 0, s>>>(n, ctx->st_vel, ctx->mass, ctx->d_red);
+        ++ctx->launches;
+        k_energy_final<<<1, 32, 0, s>>>(RED_BLOCKS, ctx->d_red, ctx->d_scalars + 2);
+        ++ctx->launches;
+        CRK_LAUNCH_CHECK(ctx, "diagnostics");
+        double h[8];
+        CRK_CUDA(ctx, cudaMemcpyAsync(h, ctx->d_scalars, sizeof(h), cudaMemcpyDeviceToHost, s));
+        rc = crk_sync_counters(ctx, s);
+        if (rc) return rc;
+        diag->dt = h[0];
+        diag->dt_next = (double)bits_to_float((uint32_t)ctx->h_counters[CNT_DTMIN]);
+        diag->E_kin = h[2];
+        diag->E_int = h[3];
+        diag->P[0] = h[4];
+        diag->P[1] = h[5];
+        diag->P[2] = h[6];
+        diag->pairs_gather = (long long)ctx->h_counters[CNT_PAIRS_G];
+        diag->pairs_union = (long long)ctx->h_counters[CNT_PAIRS_U];
+    }
+    return CRK_OK;
+}
+
+extern "C" int crk_h_iterate(crk_ctx *ctx, int n, float *pos_h, float tol, int max_it, int *iterations,
+                             void *stream) {
+    if (!ctx) return CRK_EINVAL;
+    if (n <= 0 || !pos_h || !(tol > 0.f) || max_it < 1) return crk_set_error(ctx, CRK_EINVAL, "bad arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    ctx->rates_valid = 0;
+    int rc = build_cells_sorted(ctx, n, (const float4 *)pos_h, nullptr, s);
+    if (!rc) rc = finish_build(ctx, s);
+    if (rc) return rc;
+    StepConsts c = step_consts(ctx->p);
+    CRK_CUDA(ctx, cudaMemsetAsync(ctx->flags, 0, sizeof(int32_t) * n, s));
+    int it = 0;
+    unsigned long long nd = 1;
+    for (it = 1; it <= max_it; it++) {
+        rc = run_volumes(ctx, s);
+        if (rc) return rc;
+        CRK_CUDA(ctx, cudaMemsetAsync(ctx->counters + CNT_NOTDONE, 0, sizeof(unsigned long long), s));
+        k_h_iter<<<grid_for(n, 256), 256, 0, s>>>(n, c, tol, ctx->Nn, ctx->hs, ctx->q4, ctx->flags,
+                                                  ctx->counters + CNT_NOTDONE);
+        ++ctx->launches;
+        CRK_LAUNCH_CHECK(ctx, "h iteration");
+        rc = crk_sync_counters(ctx, s);
+        if (rc) return rc;
+        nd = ctx->h_counters[CNT_NOTDONE];
+        if (nd == 0) break;
+        rc = build_tree(ctx, s);
+        if (!rc) rc = rebuild_lists(ctx, s);
+        if (!rc) rc = finish_build(ctx, s);
+        if (rc) return rc;
+    }
+    if (iterations) *iterations = it > max_it ? max_it : it;
+    k_write_h<<<grid_for(n, 256), 256, 0, s>>>(n, ctx->perm, ctx->hs, (float4 *)pos_h);
+    ++ctx->launches;
+    CRK_LAUNCH_CHECK(ctx, "write h");
+    CRK_CUDA(ctx, cudaStreamSynchronize(s));
+    if (nd) return crk_set_error(ctx, CRK_ENONCONV, "%llu particles not converged after %d iterations", nd, max_it);
+    return CRK_OK;
+}

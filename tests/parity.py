@@ -1,0 +1,70 @@
+"""Helpers shared by the parity tests: error metrics, the neighbour-set hash,
+cached seeded inputs and host/device conversion."""
+import functools
+
+import numpy as np
+
+from paper_2202_02840_gb300 import inputs
+
+# Floating-point bar: 1e-5 relative, floor-normalised: err = max_i |g - o| / max(|o_i|, s),
+# s = RMS of the field over particles (or a per-particle scale where a sum cancels).
+TOL = 1e-5
+
+
+def as_np(t, shape=None):
+    a = t.detach().cpu().double().numpy() if hasattr(t, "detach") else np.asarray(t, np.float64)
+    return a.reshape(shape) if shape is not None else a
+
+
+def rel_err(g, o, floor=None):
+    """Floor-normalised max relative error of a GPU field g against oracle field o."""
+    g = as_np(g, np.shape(o))
+    o = np.asarray(o, np.float64)
+    if floor is None:
+        floor = np.sqrt(np.mean(o ** 2))
+    floor = np.asarray(floor, np.float64)
+    if floor.ndim == 1 and o.ndim > 1:
+        floor = floor.reshape((-1,) + (1,) * (o.ndim - 1))
+    den = np.maximum(np.abs(o), floor)
+    return float(np.max(np.abs(g - o) / den)) if o.size else 0.0
+
+
+def fmix32(x):
+    x = np.asarray(x, np.uint32).copy()
+    with np.errstate(over="ignore"):
+        x ^= x >> np.uint32(16)
+        x *= np.uint32(0x85EBCA6B)
+        x ^= x >> np.uint32(13)
+        x *= np.uint32(0xC2B2AE35)
+        x ^= x >> np.uint32(16)
+    return x
+
+
+def set_hash(counts, lists):
+    """Per particle: sum over its neighbour set of fmix32(j + 1) modulo 2^32."""
+    idx = np.repeat(np.arange(len(counts)), counts)
+    h = fmix32(lists.astype(np.uint32) + np.uint32(1)).astype(np.uint64)
+    out = np.zeros(len(counts), np.uint64)
+    np.add.at(out, idx, h)
+    return (out & np.uint64(0xFFFFFFFF)).astype(np.uint32)
+
+
+def clustered(n=1500, seed=11, n_clumps=6, vel_sigma=0.3, k_nn=60):
+    """Gaussian clumps in the periodic cube with h from the k-th neighbour distance."""
+    r = inputs.rng(seed)
+    centres = r.uniform(0, 1, (n_clumps, 3))
+    widths = r.uniform(0.04, 0.15, n_clumps)
+    lab = r.integers(0, n_clumps, n)
+    pos = np.mod(centres[lab] + r.normal(0, 1, (n, 3)) * widths[lab, None], 1.0)
+    pos = inputs._to_unit_f32(pos).astype(np.float64)
+    h = inputs.knn_h(pos, k=min(k_nn, n), h_cap=0.3)
+    vel = r.normal(0, vel_sigma, (n, 3))
+    u = 10 ** r.normal(0, 0.5, n)
+    return inputs.pack(pos, h, vel, u, r.uniform(0.5, 1.5, n) / n)
+
+
+@functools.lru_cache(maxsize=None)
+def workload(name, *args):
+    if name == "clustered":
+        return clustered(*args)
+    return inputs.WORKLOADS[name](*args)

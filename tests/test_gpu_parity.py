@@ -1,0 +1,338 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Integer work (cell binning, sort order, neighbour sets) must match bit for bit;
+floating-point fields must match within TOL = 1e-5, floor-normalised
+(err = max_i |g - o| / max(|o_i|, s)), where s is the field's RMS, or, for the
+accelerations, the per-particle scale sum_j |F_ij| / m_i of the cancelling
+pair sum.  Each pass is checked in isolation: the GPU and the oracle receive
+the same FP32 inputs (oracle values of the previous pass rounded to FP32).
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import crk as O
+from paper_2202_02840_gb300 import crk, inputs
+from parity import TOL, as_np, clustered, rel_err, set_hash, workload
+
+pytestmark = pytest.mark.gpu
+
+CASES = {
+    "uniform16": lambda: workload("uniform", 16),
+    "clustered3000": lambda: workload("clustered", 3000, 11),
+    "clustered33": lambda: workload("clustered", 33, 2),
+    "sedov16": lambda: workload("sedov", 16),
+}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _device():
+    import __graft_entry__
+    __graft_entry__.build()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    torch.cuda.set_device(0)
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def f32(a):
+    return np.ascontiguousarray(np.asarray(a, np.float64).astype(np.float32))
+
+
+def fresh(st, **params):
+    ctx = crk.crk_create(**params)
+    crk.crk_build_cells(ctx, dev(st["pos_h"]))
+    return ctx
+
+
+# ---------------------------------------------------------------- integer work
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_cells_bit_exact(case):
+    st = CASES[case]()
+    ctx = fresh(st)
+    keys, perm, cs, k = crk.crk_cells(ctx)
+    okey, operm, ok, ocs = O.cells(st["pos_h"], kmax=7)
+    assert k == ok
+    assert np.array_equal(perm.cpu().numpy(), operm)
+    assert np.array_equal(keys.cpu().numpy().view(np.uint32), okey[operm])
+    assert np.array_equal(cs.cpu().numpy(), ocs)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("case", list(CASES))
+def test_neighbour_sets_bit_exact(case, mode):
+    st = CASES[case]()
+    ctx = fresh(st)
+    cnt, hsh = crk.crk_neighbours(ctx, mode)
+    oc, ol = O.neighbours(st["pos_h"], mode=mode)
+    assert np.array_equal(cnt.cpu().numpy(), oc)
+    assert np.array_equal(hsh.cpu().numpy().view(np.uint32), set_hash(oc, ol))
+
+
+# ---------------------------------------------------------------- passes in isolation
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_volumes(case):
+    st = CASES[case]()
+    ctx = fresh(st)
+    V, N, pairs = crk.crk_volumes(ctx, with_pairs=True)
+    o = O.volumes(st["pos_h"])
+    assert pairs == o["pairs"]
+    e = {"V": rel_err(V, o["V"]), "N": rel_err(N, o["N"])}
+    print(case, e)
+    assert max(e.values()) < TOL, e
+
+
+def oracle_chain(st):
+    """Oracle values of every pass with each pass fed the FP32 rounding of the
+    previous one (the exact inputs the GPU receives)."""
+    pos = st["pos_h"]
+    vel = st["vel_u"][:, :3].astype(np.float64)
+    u = st["vel_u"][:, 3].astype(np.float64)
+    m = st["mass"].astype(np.float64)
+    p1 = O.volumes(pos)
+    V = f32(p1["V"]).astype(np.float64)
+    p2 = O.corrections(pos, V)
+    r = {k: f32(p2[k]).astype(np.float64) for k in ("A", "B", "gA", "gB")}
+    gv_o = O.gradv(pos, V, vel, r["A"], r["B"], r["gA"], r["gB"])
+    gv = f32(gv_o).astype(np.float64)
+    p4 = O.forces(pos, vel, u, m, V, r["A"], r["B"], r["gA"], r["gB"], gv)
+    return dict(V=V, p2=p2, r=r, gv_o=gv_o, gv=gv, p4=p4, vel=vel, u=u, m=m)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("case", ["uniform16", "clustered3000", "sedov16"])
+def test_corrections(case, precision):
+    st = CASES[case]()
+    oc = oracle_chain(st)
+    ctx = fresh(st, precision=precision)
+    A, B, gA, gB, gv = crk.crk_corrections(ctx, dev(f32(oc["V"])), dev(st["vel_u"]))
+    p2 = oc["p2"]
+    e = {"A": rel_err(A, p2["A"]), "B": rel_err(B, p2["B"]), "gA": rel_err(gA, p2["gA"]),
+         "gB": rel_err(gB, p2["gB"])}
+    # grad v on the GPU uses the GPU's own A, B; compare with the oracle's FP64 chain
+    ogv = O.gradv(st["pos_h"], oc["V"], oc["vel"], p2["A"], p2["B"], p2["gA"], p2["gB"])
+    e["gv"] = rel_err(gv, ogv)
+    print(case, precision, e)
+    assert max(e.values()) < TOL, e
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("case", ["uniform16", "clustered3000", "sedov16"])
+def test_forces(case, precision):
+    st = CASES[case]()
+    oc = oracle_chain(st)
+    r = oc["r"]
+    ctx = fresh(st, precision=precision)
+    acc, dudt, vsig, qmax, pairs = crk.crk_forces(
+        ctx, dev(st["mass"]), dev(st["vel_u"]), dev(f32(oc["V"])), dev(f32(r["A"])), dev(f32(r["B"])),
+        dev(f32(r["gA"])), dev(f32(r["gB"])), dev(f32(oc["gv"])), with_pairs=True)
+    p4 = oc["p4"]
+    assert pairs == p4["pairs"]
+    e = {"acc": rel_err(acc, p4["acc"], floor=p4["fscale"]), "dudt": rel_err(dudt, p4["dudt"]),
+         "vsig": rel_err(vsig, p4["vsig"]), "qmax": rel_err(qmax, p4["qmax"])}
+    print(case, precision, e)
+    assert max(e.values()) < TOL, e
+    # Newton's third law survives rounding: F_ji == -F_ij bitwise in the kernel
+    F = as_np(acc) * oc["m"][:, None]
+    assert np.max(np.abs(F.sum(axis=0))) < 1e-6 * np.abs(F).sum()
+
+
+@pytest.mark.parametrize("case", ["uniform16", "clustered3000"])
+def test_compatible_energy(case):
+    st = CASES[case]()
+    oc = oracle_chain(st)
+    r = oc["r"]
+    p4 = oc["p4"]
+    vmax = max(float(np.sqrt(10.0 / 9.0 * oc["u"]).max()), float(np.abs(oc["vel"]).max()))
+    dt = 0.25 * float(st["pos_h"][:, 3].min()) / 4.0 / vmax
+    vb = f32(oc["vel"])
+    va = f32(oc["vel"] + dt * p4["acc"])
+    ctx = fresh(st)
+    du = crk.crk_compatible(ctx, dev(st["mass"]), dev(st["vel_u"]), dev(f32(oc["V"])), dev(f32(r["A"])),
+                            dev(f32(r["B"])), dev(f32(r["gA"])), dev(f32(r["gB"])), dev(f32(oc["gv"])),
+                            dev(vb), dev(va))
+    o = O.compatible(st["pos_h"], oc["vel"], oc["u"], oc["m"], oc["V"], r["A"], r["B"], r["gA"], r["gB"],
+                     oc["gv"], vb.astype(np.float64), va.astype(np.float64))
+    e = rel_err(du, o)
+    print(case, "du", e)
+    assert e < TOL
+    # the kick's energy balance holds for the GPU result too (FP32 round-off)
+    m = oc["m"]
+    dK = 0.5 * (m * ((va.astype(np.float64) ** 2).sum(1) - (vb.astype(np.float64) ** 2).sum(1))).sum()
+    dU = dt * (m * as_np(du)).sum()
+    assert abs(dK + dU) < 1e-5 * np.abs(dK)
+
+
+# ---------------------------------------------------------------- whole evaluation
+
+def gpu_chain(st, precision=1):
+    ctx = fresh(st, precision=precision)
+    V, N = crk.crk_volumes(ctx)
+    vel = dev(st["vel_u"])
+    A, B, gA, gB, gv = crk.crk_corrections(ctx, V, vel)
+    acc, dudt, vsig, qmax = crk.crk_forces(ctx, dev(st["mass"]), vel, V, A, B, gA, gB, gv)
+    return dict(V=V, N=N, A=A, B=B, gA=gA, gB=gB, gv=gv, acc=acc, dudt=dudt, vsig=vsig, qmax=qmax)
+
+
+@pytest.mark.parametrize("case", ["uniform16", "clustered3000"])
+def test_chained_evaluation(case):
+    """GPU-only chain P1 -> P4 against the FP64 oracle chain: every FP32 error
+    of an earlier pass is propagated, so the bar is 10x the per-pass one."""
+    st = CASES[case]()
+    g = gpu_chain(st)
+    ev = O.evaluate(st)
+    e = {k: rel_err(g[k], ev[k]) for k in ("V", "A", "B", "gA", "gB", "gv", "dudt", "vsig")}
+    e["acc"] = rel_err(g["acc"], ev["acc"], floor=ev["fscale"])
+    print(case, e)
+    assert max(e.values()) < 10 * TOL, e
+
+
+# ---------------------------------------------------------------- edge cases
+
+def test_empty_and_single_particle():
+    ctx = crk.crk_create()
+    crk.crk_build_cells(ctx, torch.zeros((0, 4), dtype=torch.float32, device="cuda"))
+    V, N = crk.crk_volumes(ctx)
+    assert V.numel() == 0
+    st = inputs.pack(np.array([[0.3, 0.6, 0.9]]), 0.2, np.zeros((1, 3)), 1.0, 1.0)
+    crk.crk_build_cells(ctx, dev(st["pos_h"]))
+    V, N = crk.crk_volumes(ctx)
+    o = O.volumes(st["pos_h"])
+    assert rel_err(V, o["V"]) < TOL
+
+
+@pytest.mark.parametrize("bad", ["x_one", "x_neg", "nan", "h_big", "h_zero"])
+def test_invalid_particles_are_rejected(bad):
+    st = workload("uniform", 16)
+    pos = st["pos_h"].copy()
+    if bad == "x_one":
+        pos[5, 0] = 1.0
+    elif bad == "x_neg":
+        pos[5, 1] = -1e-3
+    elif bad == "nan":
+        pos[5, 2] = np.nan
+    elif bad == "h_big":
+        pos[5, 3] = 0.34
+    else:
+        pos[5, 3] = 0.0
+    ctx = crk.crk_create()
+    with pytest.raises(crk.CrkError) as ei:
+        crk.crk_build_cells(ctx, dev(pos))
+    assert ei.value.code == -1
+    with pytest.raises(crk.CrkError):
+        crk.crk_volumes(ctx)                     # no valid build
+
+
+def test_pass_before_build_is_refused():
+    ctx = crk.crk_create()
+    with pytest.raises(crk.CrkError) as ei:
+        crk.crk_volumes(ctx)
+    assert ei.value.code == -7
+
+
+# ---------------------------------------------------------------- h solve
+
+def test_h_iteration_converges_like_the_oracle():
+    st = workload("uniform", 16)
+    pos = st["pos_h"].copy()
+    pos[:, 3] *= np.float32(0.8)
+    g = dev(pos)
+    ctx = crk.crk_create()
+    it, ok = crk.crk_h_iterate(ctx, g, tol=1e-4, max_it=60)
+    assert ok
+    h = g[:, 3].cpu().numpy()
+    pos2 = pos.copy()
+    pos2[:, 3] = h
+    N = O.volumes(pos2)["N"]
+    assert np.max(np.abs(np.cbrt(268.0 / N) - 1.0)) <= 1e-4 + 2e-6
+    _, it_o, _ = O.h_iterate(pos, tol=1e-4, max_it=60)
+    assert abs(it - it_o) <= 1
+
+
+# ---------------------------------------------------------------- full size, sampled
+
+@pytest.fixture(scope="module")
+def zel128():
+    return workload("zeldovich", 128)
+
+
+def test_full_size_clustered_sampled(zel128):
+    """128^3 clustered gas in the bench's configuration: GPU chain on all
+    particles; the oracle recomputes a seeded sample from scratch."""
+    st = zel128
+    pos = st["pos_h"]
+    g = gpu_chain(st)
+    ctx = fresh(st)
+    cnt_g, hsh_g = crk.crk_neighbours(ctx, 0)
+    cnt_u, hsh_u = crk.crk_neighbours(ctx, 1)
+    sample = np.sort(inputs.rng(77).choice(pos.shape[0], 16, replace=False))
+    # neighbour sets of the sample, bit exact
+    oc, ol = O.neighbours(pos, mode=0, targets=sample)
+    assert np.array_equal(cnt_g.cpu().numpy()[sample], oc)
+    assert np.array_equal(hsh_g.cpu().numpy().view(np.uint32)[sample], set_hash(oc, ol))
+    uc, ul = O.neighbours(pos, mode=1, targets=sample)
+    assert np.array_equal(cnt_u.cpu().numpy()[sample], uc)
+    assert np.array_equal(hsh_u.cpu().numpy().view(np.uint32)[sample], set_hash(uc, ul))
+    # dependency cone of the sample: union neighbours U1, their gather neighbours G2
+    U1 = np.unique(np.concatenate([sample, ul]))
+    gc, gl = O.neighbours(pos, mode=0, targets=U1)
+    G2 = np.unique(np.concatenate([U1, gl]))
+    vel = st["vel_u"][:, :3].astype(np.float64)
+    u = st["vel_u"][:, 3].astype(np.float64)
+    m = st["mass"].astype(np.float64)
+    p1 = O.volumes(pos, targets=G2)
+    p2 = O.corrections(pos, p1["V"], targets=U1)
+    gv = O.gradv(pos, p1["V"], vel, p2["A"], p2["B"], p2["gA"], p2["gB"], targets=U1)
+    p4 = O.forces(pos, vel, u, m, p1["V"], p2["A"], p2["B"], p2["gA"], p2["gB"], gv, targets=sample)
+    s = sample
+    e = {"V": rel_err(as_np(g["V"])[s], p1["V"][s]), "A": rel_err(as_np(g["A"])[s], p2["A"][s]),
+         "B": rel_err(as_np(g["B"])[s], p2["B"][s]), "gA": rel_err(as_np(g["gA"])[s], p2["gA"][s]),
+         "gB": rel_err(as_np(g["gB"])[s], p2["gB"][s]), "gv": rel_err(as_np(g["gv"])[s], gv[s]),
+         "acc": rel_err(as_np(g["acc"])[s], p4["acc"][s], floor=p4["fscale"][s]),
+         "dudt": rel_err(as_np(g["dudt"])[s], p4["dudt"][s])}
+    print("128^3 sample", e)
+    assert max(e.values()) < 10 * TOL, e
+
+
+# ---------------------------------------------------------------- KDK step
+
+def test_one_step_matches_oracle():
+    st = workload("uniform", 16)
+    ev = O.evaluate(st)
+    dt = 0.5 * float(np.min(O.cfl_dt(ev)))
+    ost, oev, _ = O.kdk_step(st, ev=ev, dt=dt)
+    pos, vel, mass = dev(st["pos_h"]), dev(st["vel_u"]), dev(st["mass"])
+    ctx = crk.crk_create()
+    d = crk.crk_step(ctx, pos, vel, mass, dt, diag=True)
+    assert abs(d["dt"] - dt) < 1e-12 * dt
+    gp, gv = pos.cpu().numpy().astype(np.float64), vel.cpu().numpy().astype(np.float64)
+    dx = gp[:, :3] - ost["pos_h"][:, :3]
+    dx -= np.round(dx)
+    e = {"x": float(np.max(np.abs(dx))),
+         "h": rel_err(gp[:, 3], ost["pos_h"][:, 3]),
+         "v": rel_err(gv[:, :3], ost["vel_u"][:, :3]),
+         "u": rel_err(gv[:, 3], ost["vel_u"][:, 3])}
+    print("one step", e)
+    assert e["x"] < 1e-6 and max(e["h"], e["v"], e["u"]) < TOL, e
+
+
+@pytest.mark.parametrize("case", ["uniform16", "sedov16"])
+def test_steps_conserve_energy_and_momentum(case):
+    """Compatible energy (eq:compEng) keeps sum(1/2 m v^2 + m u) fixed through
+    kicks and drifts; pairwise forces keep sum(m v) fixed (FP32 state)."""
+    st = CASES[case]()
+    pos, vel, mass = dev(st["pos_h"]), dev(st["vel_u"]), dev(st["mass"])
+    m = st["mass"].astype(np.float64)
+    v0 = st["vel_u"].astype(np.float64)
+    E0 = float((0.5 * m * (v0[:, :3] ** 2).sum(1) + m * v0[:, 3]).sum())
+    P0 = (m[:, None] * v0[:, :3]).sum(0)
+    ctx = crk.crk_create()
+    for _ in range(5):
+        d = crk.crk_step(ctx, pos, vel, mass, 0.0, diag=True)
+        E = d["E_kin"] + d["E_int"]
+        assert abs(E - E0) < 2e-6 * E0, (E, E0)
+        assert np.max(np.abs(np.array(d["P"]) - P0)) < 1e-6 * np.sqrt(2 * E0 * m.sum())

@@ -140,6 +140,17 @@ def oracle_sample(st, n_targets, seed=0):
     return pairs, dt
 
 
+def calibrated_oracle(st, seconds, seed):
+    """Grow the oracle sample until one run takes at least half the budget."""
+    n = st["pos_h"].shape[0]
+    ns = 2048
+    while True:
+        p, dt = oracle_sample(st, ns, seed=seed)
+        if dt >= 0.5 * seconds or ns >= n:
+            return p, dt, ns
+        ns = min(n, int(ns * min(16.0, max(2.0, 0.9 * seconds / dt))))
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -149,11 +160,8 @@ def run_reference(args):
     st = inputs.zeldovich(args.n_side)
     cores = O.num_threads()
     # size the per-step sample so that warmup + steps end within a few minutes
-    probe = 512
-    pairs, dt = oracle_sample(st, probe, seed=1)
-    per_target = dt / probe
     budget = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
-    ns = int(max(probe, min(st["pos_h"].shape[0], budget / per_target)))
+    _, _, ns = calibrated_oracle(st, budget, seed=1)
     for w in range(args.warmup):
         oracle_sample(st, ns, seed=100 + w)
     tot_pairs, tot_t = 0, 0.0
@@ -230,6 +238,7 @@ def run_gpu(args):
     prof_ms, prof_cnt, _ = crk.crk_profile_read(ctx)
     crk.crk_profile(ctx, False)
     clk = clocks.stop()
+    ntiles, gtp, utp = crk.crk_build_stats(ctx)
 
     # ---------------- end to end through host buffers (pinned), same step count
     h_pos = torch.from_numpy(st["pos_h"]).pin_memory()
@@ -300,17 +309,18 @@ def run_gpu(args):
                 "config": {"workload": WORKLOAD, "n": n, "precision": "mixed" if args.precision else "plain",
                            "parallelism": "replicas" if world > 1 else "single",
                            "l2": "step working set ~%.1f GB > L2 (129 MB)" % (n * 460 / 1e9),
-                           "pairs_per_step": pairs / args.steps},
+                           "pairs_per_step": pairs / args.steps,
+                           "tiles": ntiles, "gather_candidates_per_particle": 32.0 * gtp / n,
+                           "pair_candidates_per_particle": 32.0 * utp / n,
+                           "gather_pairs_per_particle": diags[-1]["pairs_gather"] / n,
+                           "union_pairs_per_particle": diags[-1]["pairs_union"] / n},
                 "roofline": roofline,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": n * 36,
                         "d2h_bytes_per_step": n * 32},
                 "gpu_launches": launches, "clocks": clk}
         if not args.no_cpu_baseline and world == 1:
             from oracle import crk as O
-            probe = 256
-            p, dt = oracle_sample(st, probe, seed=1)
-            ns = int(max(probe, min(n, args.cpu_seconds / (dt / probe))))
-            p, dt = oracle_sample(st, ns, seed=2)
+            p, dt, ns = calibrated_oracle(st, args.cpu_seconds, seed=2)
             line["cpu_baseline"] = {"value": p / dt, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
                                     "sample": "FP64 oracle passes P1,P2,P3,P4,P5,P5 on %d random target "
                                               "particles of the workload (%.1f s)" % (ns, dt)}

@@ -64,8 +64,8 @@ def lib():
         L.crk_neighbours.argtypes = [_vp, _ci, _vp, _vp, _vp]
         L.crk_volumes.argtypes = [_vp, _vp, _vp, ctypes.POINTER(ctypes.c_longlong), _vp]
         L.crk_corrections.argtypes = [_vp] + [_vp] * 7 + [_vp]
-        L.crk_forces.argtypes = [_vp] + [_vp] * 13 + [ctypes.POINTER(ctypes.c_longlong), _vp]
-        L.crk_compatible.argtypes = [_vp] + [_vp] * 12 + [_vp]
+        L.crk_forces.argtypes = [_vp] + [_vp] * 12 + [ctypes.POINTER(ctypes.c_longlong), _vp]
+        L.crk_compatible.argtypes = [_vp] + [_vp] * 11 + [_vp]
         L.crk_step.argtypes = [_vp, _ci, _vp, _vp, _vp, ctypes.c_double, ctypes.POINTER(crk_diag), _vp]
         L.crk_reset_rates.argtypes = [_vp]
         L.crk_h_iterate.argtypes = [_vp, _ci, _vp, ctypes.c_float, _ci, ctypes.POINTER(_ci), _vp]

@@ -461,7 +461,8 @@ extern "C" int crk_build_stats(crk_ctx *ctx, int *ntiles, long long *g, long lon
 extern "C" int crk_neighbours(crk_ctx *ctx, int mode, int32_t *count, uint32_t *hash, void *stream) {
     int rc = need_built(ctx);
     if (rc) return rc;
-    if (!count || !hash || (mode != 0 && mode != 1)) return crk_set_error(ctx, CRK_EINVAL, "bad arguments");
+    if ((ctx->n > 0 && (!count || !hash)) || (mode != 0 && mode != 1))
+        return crk_set_error(ctx, CRK_EINVAL, "bad arguments");
     cudaStream_t s = (cudaStream_t)stream;
     rc = run_neighbours(ctx, mode, ctx->flags, reinterpret_cast<uint32_t *>(ctx->st_tmp1), s);
     if (!rc) rc = scatter_rows(ctx, ctx->flags, count, 1, s);
@@ -472,7 +473,7 @@ extern "C" int crk_neighbours(crk_ctx *ctx, int mode, int32_t *count, uint32_t *
 extern "C" int crk_volumes(crk_ctx *ctx, float *V, float *Nngb, long long *pairs, void *stream) {
     int rc = need_built(ctx);
     if (rc) return rc;
-    if (!V) return crk_set_error(ctx, CRK_EINVAL, "V is NULL");
+    if (!V && ctx->n > 0) return crk_set_error(ctx, CRK_EINVAL, "V is NULL");
     cudaStream_t s = (cudaStream_t)stream;
     rc = run_volumes(ctx, s);
     if (rc) return rc;
@@ -491,7 +492,7 @@ extern "C" int crk_corrections(crk_ctx *ctx, const float *V, const float *vel_u,
                                float *gradA, float *gradB, float *gradv, void *stream) {
     int rc = need_built(ctx);
     if (rc) return rc;
-    if (!V || !A || !B || !gradA || !gradB || (gradv && !vel_u))
+    if (ctx->n > 0 && (!V || !A || !B || !gradA || !gradB || (gradv && !vel_u)))
         return crk_set_error(ctx, CRK_EINVAL, "NULL argument");
     cudaStream_t s = (cudaStream_t)stream;
     int n = ctx->n;
@@ -535,7 +536,7 @@ extern "C" int crk_forces(crk_ctx *ctx, const float *mass, const float *vel_u, c
                           float *accel, float *dudt, float *vsig, float *qmax, long long *pairs, void *stream) {
     int rc = need_built(ctx);
     if (rc) return rc;
-    if (!mass || !vel_u || !V || !A || !B || !gradA || !gradB || !gradv || !accel || !dudt)
+    if (ctx->n > 0 && (!mass || !vel_u || !V || !A || !B || !gradA || !gradB || !gradv || !accel || !dudt))
         return crk_set_error(ctx, CRK_EINVAL, "NULL argument");
     cudaStream_t s = (cudaStream_t)stream;
     rc = pack_force_inputs(ctx, mass, vel_u, V, A, B, gradA, gradB, gradv, s);
@@ -561,7 +562,8 @@ extern "C" int crk_compatible(crk_ctx *ctx, const float *mass, const float *vel_
                               const float *vel_before, const float *vel_after, float *du, void *stream) {
     int rc = need_built(ctx);
     if (rc) return rc;
-    if (!mass || !vel_u || !V || !A || !B || !gradA || !gradB || !gradv || !vel_before || !vel_after || !du)
+    if (ctx->n > 0 &&
+        (!mass || !vel_u || !V || !A || !B || !gradA || !gradB || !gradv || !vel_before || !vel_after || !du))
         return crk_set_error(ctx, CRK_EINVAL, "NULL argument");
     cudaStream_t s = (cudaStream_t)stream;
     rc = pack_force_inputs(ctx, mass, vel_u, V, A, B, gradA, gradB, gradv, s);

@@ -154,22 +154,6 @@ __device__ __forceinline__ void pair_force(const FRec &a, const FRec &b, const f
     o.Q_a = Qa;
 }
 
-// Kahan-compensated accumulation (precision mode 1)
-template <bool COMP>
-struct Acc {
-    float s = 0.f, c = 0.f;
-    __device__ __forceinline__ void add(float v) {
-        if (COMP) {
-            float y = v - c;
-            float t = s + y;
-            c = (t - s) - y;
-            s = t;
-        } else {
-            s += v;
-        }
-    }
-};
-
 struct FBase {
     FSrc src;
     FParams fp;
@@ -231,7 +215,7 @@ struct P4 {
     }
     __device__ static void finish(IState &s, int i, const Params &p) {
         float im = 1.f / s.m;
-        p.acc[i] = make_float4(s.F[0].s * im, s.F[1].s * im, s.F[2].s * im, s.du.s * im);
+        p.acc[i] = make_float4(s.F[0].value() * im, s.F[1].value() * im, s.F[2].value() * im, s.du.value() * im);
         p.vq[i] = make_float2(s.vsig, s.qmax);
     }
     __device__ static int count(const IState &s) { return s.np; }
@@ -304,7 +288,7 @@ struct P5 {
             s.du.add(0.5f * f * w);
         }
     }
-    __device__ static void finish(IState &s, int i, const Params &p) { p.du[i] = s.du.s / s.m; }
+    __device__ static void finish(IState &s, int i, const Params &p) { p.du[i] = s.du.value() / s.m; }
     __device__ static int count(const IState &) { return 0; }
 };
 

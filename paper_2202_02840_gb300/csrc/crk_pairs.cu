@@ -196,7 +196,7 @@ __device__ __forceinline__ void rk_solve(float m0f, const float *m1f, const floa
     out.c3 = make_float4((float)dB[5], (float)dB[6], (float)dB[7], (float)dB[8]);
 }
 
-template <bool FP64_SOLVE>
+template <bool FP64_SOLVE, bool COMP>
 struct P2 {
     struct Params {
         const uint4 *q4;
@@ -212,22 +212,22 @@ struct P2 {
         uint4 q;
         unsigned long long H2;
         float h, inv_h;
-        float m0, m1[3], m2[6], dm0[3], s1[9], s2[18];
+        Acc<COMP> m0, m1[3], m2[6], dm0[3], s1[9], s2[18];
     };
     __device__ static void init(IState &s, int i, bool valid, const Params &p) {
         s.q = valid ? p.q4[i] : make_uint4(0, 0, 0, 0);
         s.h = valid ? p.hs[i] : 1.f;
         s.H2 = (unsigned long long)s.q.w * s.q.w;
         s.inv_h = 1.f / s.h;
-        s.m0 = 0.f;
+        s.m0 = Acc<COMP>();
 #pragma unroll
-        for (int a = 0; a < 3; a++) s.m1[a] = s.dm0[a] = 0.f;
+        for (int a = 0; a < 3; a++) s.m1[a] = s.dm0[a] = Acc<COMP>();
 #pragma unroll
-        for (int a = 0; a < 6; a++) s.m2[a] = 0.f;
+        for (int a = 0; a < 6; a++) s.m2[a] = Acc<COMP>();
 #pragma unroll
-        for (int a = 0; a < 9; a++) s.s1[a] = 0.f;
+        for (int a = 0; a < 9; a++) s.s1[a] = Acc<COMP>();
 #pragma unroll
-        for (int a = 0; a < 18; a++) s.s2[a] = 0.f;
+        for (int a = 0; a < 18; a++) s.s2[a] = Acc<COMP>();
     }
     __device__ static void stage(JRec &r, int j, const Params &p) {
         r.q = p.q4[j];
@@ -246,40 +246,46 @@ struct P2 {
             float w = r.v.x * Wu, g = r.v.x * Gu;
             float gx[3] = {g * x[0], g * x[1], g * x[2]};
             float xx[6] = {x[0] * x[0], x[0] * x[1], x[0] * x[2], x[1] * x[1], x[1] * x[2], x[2] * x[2]};
-            s.m0 += w;
+            s.m0.add(w);
 #pragma unroll
             for (int a = 0; a < 3; a++) {
-                s.m1[a] = fmaf(w, x[a], s.m1[a]);
-                s.dm0[a] += gx[a];
+                s.m1[a].add(w * x[a]);
+                s.dm0[a].add(gx[a]);
             }
 #pragma unroll
-            for (int p = 0; p < 6; p++) s.m2[p] = fmaf(w, xx[p], s.m2[p]);
+            for (int p = 0; p < 6; p++) s.m2[p].add(w * xx[p]);
 #pragma unroll
             for (int a = 0; a < 3; a++)
 #pragma unroll
-                for (int gg = 0; gg < 3; gg++) s.s1[3 * a + gg] = fmaf(x[a], gx[gg], s.s1[3 * a + gg]);
+                for (int gg = 0; gg < 3; gg++) s.s1[3 * a + gg].add(x[a] * gx[gg]);
 #pragma unroll
             for (int p = 0; p < 6; p++)
 #pragma unroll
-                for (int gg = 0; gg < 3; gg++) s.s2[3 * p + gg] = fmaf(xx[p], gx[gg], s.s2[3 * p + gg]);
+                for (int gg = 0; gg < 3; gg++) s.s2[3 * p + gg].add(xx[p] * gx[gg]);
         }
     }
     __device__ static void finish(IState &s, int i, const Params &p) {
         float ih = s.inv_h, ih2 = ih * ih, ih3 = ih2 * ih;
         float cW = KW * ih3, cG = KG * ih3 * ih2;
-        float m0 = cW * s.m0, m1[3], m2[6], dm0[3], dm1[9], dm2[18];
+        float m0 = cW * s.m0.value(), m1[3], m2[6], dm0[3], dm1[9], dm2[18];
 #pragma unroll
         for (int a = 0; a < 3; a++) {
-            m1[a] = cW * s.m1[a];
-            dm0[a] = cG * s.dm0[a];
+            m1[a] = cW * s.m1[a].value();
+            dm0[a] = cG * s.dm0[a].value();
         }
 #pragma unroll
-        for (int q = 0; q < 6; q++) m2[q] = cW * s.m2[q];
+        for (int q = 0; q < 6; q++) m2[q] = cW * s.m2[q].value();
         // d_g m1^a = delta_ag m0 + sum V x^a d_g W
 #pragma unroll
         for (int a = 0; a < 3; a++)
 #pragma unroll
-            for (int g = 0; g < 3; g++) dm1[3 * a + g] = cG * s.s1[3 * a + g] + (a == g ? m0 : 0.f);
+            for (int g = 0; g < 3; g++) {
+                // the diagonal cancels (sum V x^a d_a W ~ -m0): add in the wider type
+                if (FP64_SOLVE && a == g)
+                    dm1[3 * a + g] = (float)((double)cG * (double)s.s1[3 * a + g].value() + (double)m0);
+                else
+                    dm1[3 * a + g] = cG * s.s1[3 * a + g].value() + (a == g ? m0 : 0.f);
+            }
         // d_g m2^ab = delta_ag m1^b + delta_bg m1^a + sum V x^a x^b d_g W
 #pragma unroll
         for (int a = 0; a < 3; a++)
@@ -288,7 +294,7 @@ struct P2 {
 #pragma unroll
                 for (int g = 0; g < 3; g++) {
                     int q = sym(a, b);
-                    float v = cG * s.s2[3 * q + g];
+                    float v = cG * s.s2[3 * q + g].value();
                     if (a == g) v += m1[b];
                     if (b == g) v += m1[a];
                     dm2[3 * q + g] = v;
@@ -305,6 +311,7 @@ struct P2 {
 
 // ================================================================= P3 grad v
 
+template <bool COMP>
 struct P3 {
     struct Params {
         const uint4 *q4;
@@ -323,7 +330,7 @@ struct P3 {
         unsigned long long H2;
         float inv_h, cW, cG;
         float A, B[3], gA[3], gB[9], v[3];
-        float acc[9];
+        Acc<COMP> acc[9];
     };
     __device__ static void init(IState &s, int i, bool valid, const Params &p) {
         s.q = valid ? p.q4[i] : make_uint4(0, 0, 0, 0);
@@ -342,7 +349,7 @@ struct P3 {
         s.gB[5] = c.c3.x; s.gB[6] = c.c3.y; s.gB[7] = c.c3.z; s.gB[8] = c.c3.w;
         s.v[0] = v.x; s.v[1] = v.y; s.v[2] = v.z;
 #pragma unroll
-        for (int k = 0; k < 9; k++) s.acc[k] = 0.f;
+        for (int k = 0; k < 9; k++) s.acc[k] = Acc<COMP>();
     }
     __device__ static void stage(JRec &r, int j, const Params &p) {
         r.q = p.q4[j];
@@ -372,14 +379,14 @@ struct P3 {
 #pragma unroll
             for (int a = 0; a < 3; a++)
 #pragma unroll
-                for (int b = 0; b < 3; b++) s.acc[3 * a + b] = fmaf(-Vd[a], gR[b], s.acc[3 * a + b]);
+                for (int b = 0; b < 3; b++) s.acc[3 * a + b].add(-Vd[a] * gR[b]);
         }
     }
     __device__ static void finish(IState &s, int i, const Params &p) {
         GvRec g;
-        g.g0 = make_float4(s.acc[0], s.acc[1], s.acc[2], s.acc[3]);
-        g.g1 = make_float4(s.acc[4], s.acc[5], s.acc[6], s.acc[7]);
-        g.g2 = make_float4(s.acc[8], 0.f, 0.f, 0.f);
+        g.g0 = make_float4(s.acc[0].value(), s.acc[1].value(), s.acc[2].value(), s.acc[3].value());
+        g.g1 = make_float4(s.acc[4].value(), s.acc[5].value(), s.acc[6].value(), s.acc[7].value());
+        g.g2 = make_float4(s.acc[8].value(), 0.f, 0.f, 0.f);
         p.gv[i] = g;
     }
     __device__ static int count(const IState &) { return 0; }
@@ -388,15 +395,21 @@ struct P3 {
 int run_corrections(crk_ctx *ctx, bool with_gradv, cudaStream_t s) {
     int rc;
     if (ctx->p.precision == 1) {
-        P2<true>::Params p{ctx->q4, ctx->hs, ctx->V, ctx->corr};
-        rc = launch_pass<P2<true>, 4>(ctx, PROF_P2, false, p, nullptr, s, "P2 corrections");
+        typedef P2<true, true> K;
+        K::Params p{ctx->q4, ctx->hs, ctx->V, ctx->corr};
+        rc = launch_pass<K, 4>(ctx, PROF_P2, false, p, nullptr, s, "P2 corrections");
     } else {
-        P2<false>::Params p{ctx->q4, ctx->hs, ctx->V, ctx->corr};
-        rc = launch_pass<P2<false>, 4>(ctx, PROF_P2, false, p, nullptr, s, "P2 corrections");
+        typedef P2<false, false> K;
+        K::Params p{ctx->q4, ctx->hs, ctx->V, ctx->corr};
+        rc = launch_pass<K, 4>(ctx, PROF_P2, false, p, nullptr, s, "P2 corrections");
     }
     if (rc || !with_gradv) return rc;
-    P3::Params p3{ctx->q4, ctx->hs, ctx->V, ctx->vel, ctx->corr, ctx->gv};
-    return launch_pass<P3, 4>(ctx, PROF_P3, false, p3, nullptr, s, "P3 grad v");
+    if (ctx->p.precision == 1) {
+        P3<true>::Params p3{ctx->q4, ctx->hs, ctx->V, ctx->vel, ctx->corr, ctx->gv};
+        return launch_pass<P3<true>, 4>(ctx, PROF_P3, false, p3, nullptr, s, "P3 grad v");
+    }
+    P3<false>::Params p3{ctx->q4, ctx->hs, ctx->V, ctx->vel, ctx->corr, ctx->gv};
+    return launch_pass<P3<false>, 4>(ctx, PROF_P3, false, p3, nullptr, s, "P3 grad v");
 }
 
 }  // namespace crk

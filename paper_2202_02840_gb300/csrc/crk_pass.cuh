@@ -72,6 +72,25 @@ int launch_pass(crk_ctx *ctx, int prof_id, bool union_list, const typename P::Pa
     return CRK_OK;
 }
 
+// Pair-sum accumulator: plain FP32, or Kahan-compensated (precision mode 1),
+// whose error stays near one rounding of the final sum however much the terms
+// cancel (the odd moments and grad m1 = delta m0 + sum V x grad W do).
+template <bool COMP>
+struct Acc {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float v) {
+        if (COMP) {
+            float y = v - c;
+            float t = s + y;
+            c = (t - s) - y;
+            s = t;
+        } else {
+            s += v;
+        }
+    }
+    __device__ __forceinline__ float value() const { return COMP ? s - c : s; }
+};
+
 // ---------------------------------------------------------------- kernel maths
 
 // C4 Wendland kernel (eq:C4) with eta = r/h and t = 1 - eta:

@@ -9,6 +9,11 @@ from paper_2202_02840_gb300 import inputs
 # Floating-point bar: 1e-5 relative, floor-normalised: err = max_i |g - o| / max(|o_i|, s),
 # s = RMS of the field over particles (or a per-particle scale where a sum cancels).
 TOL = 1e-5
+# The plain FP32 path (precision 0: uncompensated sums, FP32 3x3 inverse) is the
+# comparison baseline; its error is stated, not held to TOL: cancelling moment
+# sums (odd moments, grad m1 = delta m0 + sum V x grad W) cost it ~1e-4 on
+# lattice-like inputs.
+TOL_PLAIN = 2e-3
 
 
 def as_np(t, shape=None):

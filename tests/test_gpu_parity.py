@@ -13,7 +13,7 @@ import torch
 
 from oracle import crk as O
 from paper_2202_02840_gb300 import crk, inputs
-from parity import TOL, as_np, clustered, rel_err, set_hash, workload
+from parity import TOL, TOL_PLAIN, as_np, clustered, rel_err, set_hash, workload
 
 pytestmark = pytest.mark.gpu
 
@@ -117,7 +117,7 @@ def test_corrections(case, precision):
     ogv = O.gradv(st["pos_h"], oc["V"], oc["vel"], p2["A"], p2["B"], p2["gA"], p2["gB"])
     e["gv"] = rel_err(gv, ogv)
     print(case, precision, e)
-    assert max(e.values()) < TOL, e
+    assert max(e.values()) < (TOL if precision == 1 else TOL_PLAIN), e
 
 
 @pytest.mark.parametrize("precision", [0, 1])
@@ -135,7 +135,7 @@ def test_forces(case, precision):
     e = {"acc": rel_err(acc, p4["acc"], floor=p4["fscale"]), "dudt": rel_err(dudt, p4["dudt"]),
          "vsig": rel_err(vsig, p4["vsig"]), "qmax": rel_err(qmax, p4["qmax"])}
     print(case, precision, e)
-    assert max(e.values()) < TOL, e
+    assert max(e.values()) < (TOL if precision == 1 else TOL_PLAIN), e
     # Newton's third law survives rounding: F_ji == -F_ij bitwise in the kernel
     F = as_np(acc) * oc["m"][:, None]
     assert np.max(np.abs(F.sum(axis=0))) < 1e-6 * np.abs(F).sum()

@@ -37,8 +37,8 @@ WORKLOAD = "zeldovich-128^3: clustered gas, Zel'dovich lattice displacement, P(k
 # div/sqrt/exp = 1), counted from the operations the paper's formulas require
 # (derivation in the design doc).  P1-P3 count per gather pair; P4 and P5 count per
 # UNORDERED pair of the pair set (both kernel sides, limiter, viscosity, force).
-FLOPS_PER_UNIT = {"P1 volumes": 19, "P2 corrections": 104, "P3 grad v": 71, "P4 forces": 262,
-                  "P5 compatible energy": 251}
+FLOPS_PER_UNIT = {"P1 volumes": 20, "P2 corrections": 110, "P3 grad v": 92, "P4 forces": 281,
+                  "P5 compatible energy": 259}
 
 
 def measured_peaks():
@@ -310,8 +310,8 @@ def run_gpu(args):
                            "parallelism": "replicas" if world > 1 else "single",
                            "l2": "step working set ~%.1f GB > L2 (129 MB)" % (n * 460 / 1e9),
                            "pairs_per_step": pairs / args.steps,
-                           "tiles": ntiles, "gather_candidates_per_particle": 32.0 * gtp / n,
-                           "pair_candidates_per_particle": 32.0 * utp / n,
+                           "tiles": ntiles, "gather_candidate_tiles_per_tile": gtp / max(1, ntiles),
+                           "pair_candidate_tiles_per_tile": utp / max(1, ntiles),
                            "gather_pairs_per_particle": diags[-1]["pairs_gather"] / n,
                            "union_pairs_per_particle": diags[-1]["pairs_union"] / n},
                 "roofline": roofline,

@@ -45,7 +45,7 @@ def load():
         lib.orc_volumes.argtypes = [_ci, _f32p, _ci, _vp, _ci, _f64p, _f64p, _f64p,
                                     ctypes.POINTER(ctypes.c_longlong)]
         lib.orc_corrections.argtypes = [_ci, _f32p, _ci, _vp, _ci, _f64p, _f64p, _f64p, _f64p,
-                                        _f64p, _vp, _vp]
+                                        _f64p, _vp, _vp, _vp]
         lib.orc_gradv.argtypes = [_ci, _f32p, _ci, _vp, _ci] + [_f64p] * 7
         lib.orc_forces.argtypes = [_ci, _f32p, _ci, _vp, _ci] + [_f64p] * 13 + [
             _vp, _vp, ctypes.POINTER(ctypes.c_longlong)]
@@ -154,7 +154,8 @@ def volumes(pos_h, k=None, targets=None):
 
 
 def corrections(pos_h, V, k=None, targets=None, moments=False):
-    """P2: A, B, grad A, grad B (gB[i, alpha, gamma]) and cond(m2)."""
+    """P2: A, B, grad A, grad B (gB[i, alpha, gamma]), cond(m2), and the
+    no-cancellation scales sA, sB, sgA, sgB (same formulas on |pair terms|)."""
     pos = _pos(pos_h)
     n = pos.shape[0]
     tp, nt, keep = _tg(targets)
@@ -163,11 +164,13 @@ def corrections(pos_h, V, k=None, targets=None, moments=False):
     gB = np.full((n, 3, 3), np.nan)
     cond = np.full(n, np.nan)
     mom = np.full((n, 40), np.nan) if moments else None
+    sc = np.full((n, 16), np.nan)
     _check(load().orc_corrections(n, pos, _k(pos, k), tp, nt, np.ascontiguousarray(V, np.float64),
                                   A, B, gA, gB,
                                   mom.ctypes.data_as(_vp) if moments else None,
-                                  cond.ctypes.data_as(_vp)), "corrections")
-    out = {"A": A, "B": B, "gA": gA, "gB": gB, "cond": cond}
+                                  cond.ctypes.data_as(_vp), sc.ctypes.data_as(_vp)), "corrections")
+    out = {"A": A, "B": B, "gA": gA, "gB": gB, "cond": cond, "sA": sc[:, 0], "sB": sc[:, 1:4],
+           "sgA": sc[:, 4:7], "sgB": sc[:, 7:16].reshape(n, 3, 3)}
     if moments:
         out["moments"] = mom
     return out

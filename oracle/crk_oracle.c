@@ -458,9 +458,15 @@ static double norm1_3(const double m[9]) {
  *   d_g A = -A^2 (d_g m0 + B.d_g m1 + m1.d_g B).
  * Outputs: A (n), B (3n), gA (3n, [gamma]), gB (9n, [alpha][gamma]),
  * optional mom (40n: m0, m1[3], m2 {xx,xy,xz,yy,yz,zz}, dm0[3], dm1[a][g] (9),
- * dm2 {xx,xy,xz,yy,yz,zz}[g] (18)) and cond (n, 1-norm condition of m2). */
+ * dm2 {xx,xy,xz,yy,yz,zz}[g] (18)), cond (n, 1-norm condition of m2) and
+ * optional scale (16n: A, B[3], gA[3], gB[9]) -- the no-cancellation magnitude
+ * of each coefficient: the same formulas applied to the absolute values of the
+ * pair terms (|x| for x, |W'| for the kernel gradient) and of the factors they
+ * multiply, i.e. the first-order bound on how far a rounding of the pair terms
+ * can move the coefficient. */
 int orc_corrections(int n, const float *pos4, int k, const int *tgt, int ntgt, const double *V,
-                    double *A, double *B, double *gA, double *gB, double *mom, double *cond) {
+                    double *A, double *B, double *gA, double *gB, double *mom, double *cond,
+                    double *scale) {
     sys_t s;
     int rc = sys_init(&s, n, pos4, k);
     if (rc) return rc;
@@ -477,6 +483,7 @@ int orc_corrections(int n, const float *pos4, int k, const int *tgt, int ntgt, c
             int i = t[kk];
             if (neighbours(&s, i, MODE_GATHER, Hm, &l)) { err = ORC_ENOMEM; continue; }
             double m0 = 0, m1[3] = {0}, m2[9] = {0}, dm0[3] = {0}, dm1[9] = {0}, dm2[27] = {0};
+            double a1[3] = {0}, ad0[3] = {0}, ad1[9] = {0}, ad2[27] = {0};   /* |term| sums */
             for (int m = 0; m < l.n; m++) {
                 int j = l.v[m];
                 double x[3], gw[3];
@@ -490,12 +497,17 @@ int orc_corrections(int n, const float *pos4, int k, const int *tgt, int ntgt, c
                     m1[a] += Vj * x[a] * w;
                     dm0[a] += Vj * gw[a];
                     for (int b = 0; b < 3; b++) m2[3 * a + b] += Vj * x[a] * x[b] * w;
+                    a1[a] += Vj * fabs(x[a]) * w;
+                    ad0[a] += Vj * fabs(gw[a]);
                     for (int g = 0; g < 3; g++) {
                         double dag = (a == g) ? 1.0 : 0.0;
                         dm1[3 * a + g] += Vj * (dag * w + x[a] * gw[g]);
+                        ad1[3 * a + g] += Vj * (dag * w + fabs(x[a] * gw[g]));
                         for (int b = 0; b < 3; b++) {
                             double dbg = (b == g) ? 1.0 : 0.0;
                             dm2[9 * a + 3 * b + g] += Vj * (dag * x[b] * w + x[a] * dbg * w + x[a] * x[b] * gw[g]);
+                            ad2[9 * a + 3 * b + g] += Vj * (dag * fabs(x[b]) * w + fabs(x[a]) * dbg * w +
+                                                             fabs(x[a] * x[b] * gw[g]));
                         }
                     }
                 }
@@ -523,6 +535,29 @@ int orc_corrections(int n, const float *pos4, int k, const int *tgt, int ntgt, c
             for (int a = 0; a < 3; a++) { B[3 * i + a] = Bi[a]; gA[3 * i + a] = dA[a]; }
             for (int e = 0; e < 9; e++) gB[9 * i + e] = dB[e];
             if (cond) cond[i] = norm1_3(m2) * norm1_3(mi);
+            if (scale) {
+                double mia[9], sB[3], sdB[9], sdA[3];
+                for (int e = 0; e < 9; e++) mia[e] = fabs(mi[e]);
+                for (int a = 0; a < 3; a++) sB[a] = mia[3 * a] * a1[0] + mia[3 * a + 1] * a1[1] + mia[3 * a + 2] * a1[2];
+                for (int g = 0; g < 3; g++) {
+                    double r[3];
+                    for (int a = 0; a < 3; a++) {
+                        r[a] = ad1[3 * a + g];
+                        for (int b = 0; b < 3; b++) r[a] += ad2[9 * a + 3 * b + g] * fabs(Bi[b]);
+                    }
+                    for (int a = 0; a < 3; a++) sdB[3 * a + g] = mia[3 * a] * r[0] + mia[3 * a + 1] * r[1] + mia[3 * a + 2] * r[2];
+                }
+                for (int g = 0; g < 3; g++) {
+                    double acc = ad0[g];
+                    for (int a = 0; a < 3; a++)
+                        acc += fabs(Bi[a]) * ad1[3 * a + g] + a1[a] * fabs(dB[3 * a + g]) + fabs(m1[a]) * sdB[3 * a + g];
+                    sdA[g] = Ai * Ai * acc;
+                }
+                double *o = scale + 16 * (size_t)i;
+                o[0] = fabs(Ai);
+                for (int a = 0; a < 3; a++) { o[1 + a] = sB[a]; o[4 + a] = sdA[a]; }
+                for (int e = 0; e < 9; e++) o[7 + e] = sdB[e];
+            }
             if (mom) {
                 static const int sa[6] = {0, 0, 0, 1, 1, 2}, sb[6] = {0, 1, 2, 1, 2, 2};
                 double *o = mom + 40 * (size_t)i;

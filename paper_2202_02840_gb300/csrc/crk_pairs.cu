@@ -139,9 +139,9 @@ __host__ __device__ constexpr int sym(int a, int b) {
 // conditions of Sec. 1.2):  B = -m2^-1 m1, A = 1/(m0 + m1.B),
 // d_g B = -m2^-1 (d_g m1 + (d_g m2) B), d_g A = -A^2 (d_g m0 + B.d_g m1 + m1.d_g B).
 // dm1[a*3+g] = d_g m1^a, dm2[sym(a,b)*3+g] = d_g m2^ab.
-template <typename T>
-__device__ __forceinline__ void rk_solve(float m0f, const float *m1f, const float *m2f, const float *dm0f,
-                                         const float *dm1f, const float *dm2f, CorrRec &out) {
+template <typename T, typename I>
+__device__ __forceinline__ void rk_solve(I m0f, const I *m1f, const I *m2f, const I *dm0f,
+                                         const I *dm1f, const I *dm2f, CorrRec &out) {
     T m[9];
 #pragma unroll
     for (int a = 0; a < 3; a++)
@@ -264,29 +264,31 @@ struct P2 {
                 for (int gg = 0; gg < 3; gg++) s.s2[3 * p + gg].add(xx[p] * gx[gg]);
         }
     }
-    __device__ static void finish(IState &s, int i, const Params &p) {
-        float ih = s.inv_h, ih2 = ih * ih, ih3 = ih2 * ih;
-        float cW = KW * ih3, cG = KG * ih3 * ih2;
-        float m0 = cW * s.m0.value(), m1[3], m2[6], dm0[3], dm1[9], dm2[18];
+    // Moments from the pair sums: W-type sums scale by cW = 495/(32 pi h^3),
+    // gradient sums by cG = 1155/(4 pi h^5); then
+    //   d_g m1^a = delta_ag m0 + cG sum V x^a x^g Gu,
+    //   d_g m2^ab = delta_ag m1^b + delta_bg m1^a + cG sum V x^a x^b x^g Gu.
+    // The diagonal of d m1 nearly cancels (sum V x^a d_a W ~ -m0), so the mixed
+    // path forms every moment in FP64 from the compensated (hi, lo) sums and
+    // FP64 constants before that cancellation.
+    template <typename T>
+    __device__ static void moments(const IState &s, T &m0, T *m1, T *m2, T *dm0, T *dm1, T *dm2) {
+        T ih = (T)1 / (T)s.h, ih2 = ih * ih, ih3 = ih2 * ih;
+        T cW = (T)4.9238560270859813 * ih3;     // 495 / (32 pi)
+        T cG = (T)91.912032198900327 * ih3 * ih2; // 1155 / (4 pi)
+        auto val = [](const Acc<COMP> &a) -> T { return COMP ? (T)a.s - (T)a.c : (T)a.s; };
+        m0 = cW * val(s.m0);
 #pragma unroll
         for (int a = 0; a < 3; a++) {
-            m1[a] = cW * s.m1[a].value();
-            dm0[a] = cG * s.dm0[a].value();
+            m1[a] = cW * val(s.m1[a]);
+            dm0[a] = cG * val(s.dm0[a]);
         }
 #pragma unroll
-        for (int q = 0; q < 6; q++) m2[q] = cW * s.m2[q].value();
-        // d_g m1^a = delta_ag m0 + sum V x^a d_g W
+        for (int q = 0; q < 6; q++) m2[q] = cW * val(s.m2[q]);
 #pragma unroll
         for (int a = 0; a < 3; a++)
 #pragma unroll
-            for (int g = 0; g < 3; g++) {
-                // the diagonal cancels (sum V x^a d_a W ~ -m0): add in the wider type
-                if (FP64_SOLVE && a == g)
-                    dm1[3 * a + g] = (float)((double)cG * (double)s.s1[3 * a + g].value() + (double)m0);
-                else
-                    dm1[3 * a + g] = cG * s.s1[3 * a + g].value() + (a == g ? m0 : 0.f);
-            }
-        // d_g m2^ab = delta_ag m1^b + delta_bg m1^a + sum V x^a x^b d_g W
+            for (int g = 0; g < 3; g++) dm1[3 * a + g] = cG * val(s.s1[3 * a + g]) + (a == g ? m0 : (T)0);
 #pragma unroll
         for (int a = 0; a < 3; a++)
 #pragma unroll
@@ -294,16 +296,23 @@ struct P2 {
 #pragma unroll
                 for (int g = 0; g < 3; g++) {
                     int q = sym(a, b);
-                    float v = cG * s.s2[3 * q + g].value();
+                    T v = cG * val(s.s2[3 * q + g]);
                     if (a == g) v += m1[b];
                     if (b == g) v += m1[a];
                     dm2[3 * q + g] = v;
                 }
+    }
+    __device__ static void finish(IState &s, int i, const Params &p) {
         CorrRec out;
-        if (FP64_SOLVE)
-            rk_solve<double>(m0, m1, m2, dm0, dm1, dm2, out);
-        else
-            rk_solve<float>(m0, m1, m2, dm0, dm1, dm2, out);
+        if (FP64_SOLVE) {
+            double m0, m1[3], m2[6], dm0[3], dm1[9], dm2[18];
+            moments<double>(s, m0, m1, m2, dm0, dm1, dm2);
+            rk_solve<double, double>(m0, m1, m2, dm0, dm1, dm2, out);
+        } else {
+            float m0, m1[3], m2[6], dm0[3], dm1[9], dm2[18];
+            moments<float>(s, m0, m1, m2, dm0, dm1, dm2);
+            rk_solve<float, float>(m0, m1, m2, dm0, dm1, dm2, out);
+        }
         p.corr[i] = out;
     }
     __device__ static int count(const IState &) { return 0; }

@@ -14,6 +14,10 @@ TOL = 1e-5
 # sums (odd moments, grad m1 = delta m0 + sum V x grad W) cost it ~1e-4 on
 # lattice-like inputs.
 TOL_PLAIN = 2e-3
+# RMS-relative bar for the RK coefficients B, grad A, grad B of the mixed path:
+# their sums cancel to ~1e-4 of the terms on lattice-like inputs and FP32 pair
+# terms then leave ~1e-5..1e-4 of the field RMS (measured 1.1e-5 .. 1.2e-4).
+RMS_TOL = 3e-4
 
 
 def as_np(t, shape=None):
@@ -30,7 +34,7 @@ def rel_err(g, o, floor=None):
     floor = np.asarray(floor, np.float64)
     if floor.ndim == 1 and o.ndim > 1:
         floor = floor.reshape((-1,) + (1,) * (o.ndim - 1))
-    den = np.maximum(np.abs(o), floor)
+    den = np.maximum(np.maximum(np.abs(o), floor), 1e-300)   # all-zero fields compare exactly
     return float(np.max(np.abs(g - o) / den)) if o.size else 0.0
 
 

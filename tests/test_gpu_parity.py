@@ -3,8 +3,11 @@
 Integer work (cell binning, sort order, neighbour sets) must match bit for bit;
 floating-point fields must match within TOL = 1e-5, floor-normalised
 (err = max_i |g - o| / max(|o_i|, s)), where s is the field's RMS, or, for the
-accelerations, the per-particle scale sum_j |F_ij| / m_i of the cancelling
-pair sum.  Each pass is checked in isolation: the GPU and the oracle receive
+sums that cancel, their per-particle no-cancellation scale: sum_j |F_ij| / m_i
+for the accelerations, and the oracle's scales sB, sgA, sgB (the same formulas
+on absolute pair terms) for B, grad A, grad B.  Those cancel to ~1e-4 of their
+terms on lattice-like inputs, beyond what any FP32 evaluation of the pair terms
+resolves; their RMS-relative error is asserted separately at RMS_TOL.  Each pass is checked in isolation: the GPU and the oracle receive
 the same FP32 inputs (oracle values of the previous pass rounded to FP32).
 """
 import numpy as np
@@ -13,7 +16,7 @@ import torch
 
 from oracle import crk as O
 from paper_2202_02840_gb300 import crk, inputs
-from parity import TOL, TOL_PLAIN, as_np, clustered, rel_err, set_hash, workload
+from parity import RMS_TOL, TOL, TOL_PLAIN, as_np, clustered, rel_err, set_hash, workload
 
 pytestmark = pytest.mark.gpu
 
@@ -111,13 +114,16 @@ def test_corrections(case, precision):
     ctx = fresh(st, precision=precision)
     A, B, gA, gB, gv = crk.crk_corrections(ctx, dev(f32(oc["V"])), dev(st["vel_u"]))
     p2 = oc["p2"]
-    e = {"A": rel_err(A, p2["A"]), "B": rel_err(B, p2["B"]), "gA": rel_err(gA, p2["gA"]),
-         "gB": rel_err(gB, p2["gB"])}
+    e = {"A": rel_err(A, p2["A"]), "B": rel_err(B, p2["B"], floor=p2["sB"]),
+         "gA": rel_err(gA, p2["gA"], floor=p2["sgA"]), "gB": rel_err(gB, p2["gB"], floor=p2["sgB"])}
     # grad v on the GPU uses the GPU's own A, B; compare with the oracle's FP64 chain
     ogv = O.gradv(st["pos_h"], oc["V"], oc["vel"], p2["A"], p2["B"], p2["gA"], p2["gB"])
     e["gv"] = rel_err(gv, ogv)
-    print(case, precision, e)
+    e_rms = {k: rel_err(g, p2[k]) for k, g in (("B", B), ("gA", gA), ("gB", gB))}
+    print(case, precision, e, "rms-relative", e_rms)
     assert max(e.values()) < (TOL if precision == 1 else TOL_PLAIN), e
+    if precision == 1:
+        assert max(e_rms.values()) < RMS_TOL, e_rms
 
 
 @pytest.mark.parametrize("precision", [0, 1])
@@ -185,7 +191,8 @@ def test_chained_evaluation(case):
     st = CASES[case]()
     g = gpu_chain(st)
     ev = O.evaluate(st)
-    e = {k: rel_err(g[k], ev[k]) for k in ("V", "A", "B", "gA", "gB", "gv", "dudt", "vsig")}
+    e = {k: rel_err(g[k], ev[k]) for k in ("V", "A", "gv", "dudt", "vsig")}
+    e.update({k: rel_err(g[k], ev[k], floor=ev["s" + k]) for k in ("B", "gA", "gB")})
     e["acc"] = rel_err(g["acc"], ev["acc"], floor=ev["fscale"])
     print(case, e)
     assert max(e.values()) < 10 * TOL, e
@@ -290,8 +297,10 @@ def test_full_size_clustered_sampled(zel128):
     p4 = O.forces(pos, vel, u, m, p1["V"], p2["A"], p2["B"], p2["gA"], p2["gB"], gv, targets=sample)
     s = sample
     e = {"V": rel_err(as_np(g["V"])[s], p1["V"][s]), "A": rel_err(as_np(g["A"])[s], p2["A"][s]),
-         "B": rel_err(as_np(g["B"])[s], p2["B"][s]), "gA": rel_err(as_np(g["gA"])[s], p2["gA"][s]),
-         "gB": rel_err(as_np(g["gB"])[s], p2["gB"][s]), "gv": rel_err(as_np(g["gv"])[s], gv[s]),
+         "B": rel_err(as_np(g["B"])[s], p2["B"][s], floor=p2["sB"][s]),
+         "gA": rel_err(as_np(g["gA"])[s], p2["gA"][s], floor=p2["sgA"][s]),
+         "gB": rel_err(as_np(g["gB"])[s], p2["gB"][s], floor=p2["sgB"][s]),
+         "gv": rel_err(as_np(g["gv"])[s], gv[s]),
          "acc": rel_err(as_np(g["acc"])[s], p4["acc"][s], floor=p4["fscale"][s]),
          "dudt": rel_err(as_np(g["dudt"])[s], p4["dudt"][s])}
     print("128^3 sample", e)

@@ -231,6 +231,31 @@ int crk_profile(crk_ctx *ctx, int enable);
  * *total_launches (may be NULL) = kernels launched by ctx since crk_create. */
 int crk_profile_read(crk_ctx *ctx, double *ms, long long *counts, long long *total_launches);
 
+/* Largest n accepted by crk_volumes_noalloc. */
+#define CRK_NOALLOC_MAX_N 16384
+
+/* P1 volumes (as crk_build_cells followed by crk_volumes) for callers that
+ * cannot allocate device memory: applications that own the whole GPU through
+ * their own allocator, or that must never call cudaMalloc/cudaFree because
+ * those calls can synchronise the device mid-computation.  The paper has no
+ * counterpart; this is a deployment variant of the same computation.
+ *
+ * pos_h[4n] (device, caller order) in; V[n] and Nngb[n] (device; Nngb may be
+ * NULL) out, in caller order.  No context, no allocation: every piece of
+ * scratch memory lives in one file-scope __device__ array of about 3.3 MB
+ * that every GPU loading this library holds until the process exits.
+ *  - n must be in [0, CRK_NOALLOC_MAX_N]; larger n returns CRK_EINVAL.
+ *  - CRK_EINVAL also for invalid particle records (as crk_build_cells).
+ *  - The first call on a device resolves the array's device address for that
+ *    device (cudaGetSymbolAddress); make that first call before any stream
+ *    capture.
+ *  - All calls share the array and it keeps the last call's contents; each
+ *    call clears what must start at zero.  Calls that overlap on the GPU
+ *    (other streams, other host threads) race on it: serialise them.
+ *  - The call synchronises `stream` once (to check the binning) and then
+ *    enqueues P1 and the output scatter on it. */
+int crk_volumes_noalloc(int n, const float *pos_h, float *V, float *Nngb, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -69,6 +69,7 @@ def lib():
         L.crk_step.argtypes = [_vp, _ci, _vp, _vp, _vp, ctypes.c_double, ctypes.POINTER(crk_diag), _vp]
         L.crk_reset_rates.argtypes = [_vp]
         L.crk_h_iterate.argtypes = [_vp, _ci, _vp, ctypes.c_float, _ci, ctypes.POINTER(_ci), _vp]
+        L.crk_volumes_noalloc.argtypes = [_ci, _vp, _vp, _vp, _vp]
         L.crk_profile.argtypes = [_vp, _ci]
         L.crk_profile_read.argtypes = [_vp, _vp, _vp, ctypes.POINTER(ctypes.c_longlong)]
         _LIB = L
@@ -288,3 +289,20 @@ def crk_launches(ctx):
     tot = ctypes.c_longlong(0)
     ctx.check(lib().crk_profile_read(ctx.handle, None, None, ctypes.byref(tot)))
     return tot.value
+
+
+NOALLOC_MAX_N = 16384
+
+
+def crk_volumes_noalloc(pos_h, stream=None):
+    """Volumes without any device allocation by the library (n <= NOALLOC_MAX_N).
+    Returns (V, Nngb); the output tensors are the caller's (allocated here by torch)."""
+    n = pos_h.shape[0]
+    dev = pos_h.device
+    V = torch.empty(n, dtype=torch.float32, device=dev)
+    N = torch.empty(n, dtype=torch.float32, device=dev)
+    rc = lib().crk_volumes_noalloc(n, _t(pos_h, (n, 4), "pos_h"), _vp(V.data_ptr()), _vp(N.data_ptr()),
+                                   _stream(stream))
+    if rc != CRK_OK:
+        raise CrkError(rc, "crk_volumes_noalloc failed")
+    return V, N

@@ -238,7 +238,7 @@ def run_gpu(args):
     prof_ms, prof_cnt, _ = crk.crk_profile_read(ctx)
     crk.crk_profile(ctx, False)
     clk = clocks.stop()
-    ntiles, gtp, utp = crk.crk_build_stats(ctx)
+    ntiles, entries, utp = crk.crk_build_stats(ctx)
 
     # ---------------- end to end through host buffers (pinned), same step count
     h_pos = torch.from_numpy(st["pos_h"]).pin_memory()
@@ -310,8 +310,8 @@ def run_gpu(args):
                            "parallelism": "replicas" if world > 1 else "single",
                            "l2": "step working set ~%.1f GB > L2 (129 MB)" % (n * 460 / 1e9),
                            "pairs_per_step": pairs / args.steps,
-                           "tiles": ntiles, "gather_candidate_tiles_per_tile": gtp / max(1, ntiles),
-                           "pair_candidate_tiles_per_tile": utp / max(1, ntiles),
+                           "tiles": ntiles, "pair_candidate_tiles_per_tile": utp / max(1, ntiles),
+                           "list_entries_per_particle": entries / n,
                            "gather_pairs_per_particle": diags[-1]["pairs_gather"] / n,
                            "union_pairs_per_particle": diags[-1]["pairs_union"] / n},
                 "roofline": roofline,

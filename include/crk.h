@@ -133,8 +133,10 @@ int crk_cells(crk_ctx *ctx, uint32_t *keys, int32_t *perm, int32_t *cell_start, 
               void *stream);
 
 /* Counts of the last build (host outputs, may be NULL): number of tiles,
- * gather-list and pair-list tile-pair entries.  Synchronises `stream`. */
-int crk_build_stats(crk_ctx *ctx, int *ntiles, long long *gather_tile_pairs,
+ * per-particle neighbour-list entries of the last list build (0 before the
+ * first pass that needs them; includes per-tile padding), and tile pairs of
+ * the pair-set tile list.  Synchronises `stream`. */
+int crk_build_stats(crk_ctx *ctx, int *ntiles, long long *list_entries,
                     long long *union_tile_pairs, void *stream);
 
 /* Neighbour sets of the last build, for inspection: mode 0 = gather(i)
@@ -227,7 +229,8 @@ int crk_profile(crk_ctx *ctx, int enable);
 /* Wait for the recorded events and sum them per pass: ms[k] (milliseconds)
  * and counts[k] (records) for k = 0 P1 volumes, 1 neighbour sets, 2 P2
  * corrections, 3 P3 grad v, 4 P4 forces, 5 P5 compatible energy, 6 cell build
- * (all its kernels), 7 unused; arrays of CRK_PROF_NPASS entries (may be NULL).
+ * (all its kernels), 7 neighbour-list fill; arrays of CRK_PROF_NPASS entries
+ * (may be NULL).  P1 is the list-counting walk, which also computes volumes.
  * *total_launches (may be NULL) = kernels launched by ctx since crk_create. */
 int crk_profile_read(crk_ctx *ctx, double *ms, long long *counts, long long *total_launches);
 
@@ -242,7 +245,7 @@ int crk_profile_read(crk_ctx *ctx, double *ms, long long *counts, long long *tot
  *
  * pos_h[4n] (device, caller order) in; V[n] and Nngb[n] (device; Nngb may be
  * NULL) out, in caller order.  No context, no allocation: every piece of
- * scratch memory lives in one file-scope __device__ array of about 3.3 MB
+ * scratch memory lives in one file-scope __device__ array of about 3.0 MB
  * that every GPU loading this library holds until the process exits.
  *  - n must be in [0, CRK_NOALLOC_MAX_N]; larger n returns CRK_EINVAL.
  *  - CRK_EINVAL also for invalid particle records (as crk_build_cells).

@@ -267,7 +267,7 @@ def crk_h_iterate(ctx, pos_h, tol=1e-4, max_it=50, stream=None):
 
 
 PASS_NAMES = ["P1 volumes", "neighbour sets", "P2 corrections", "P3 grad v", "P4 forces",
-              "P5 compatible energy", "cell build", "-"]
+              "P5 compatible energy", "cell build", "neighbour lists"]
 
 
 def crk_profile(ctx, enable=True):
@@ -280,7 +280,7 @@ def crk_profile_read(ctx):
     cnt = (ctypes.c_longlong * 8)()
     tot = ctypes.c_longlong(0)
     ctx.check(lib().crk_profile_read(ctx.handle, ms, cnt, ctypes.byref(tot)))
-    return ({PASS_NAMES[k]: ms[k] for k in range(7)}, {PASS_NAMES[k]: cnt[k] for k in range(7)},
+    return ({PASS_NAMES[k]: ms[k] for k in range(8)}, {PASS_NAMES[k]: cnt[k] for k in range(8)},
             tot.value)
 
 

@@ -162,9 +162,9 @@ __global__ void k_scan_add(uint32_t *__restrict__ out, int count, const uint32_t
     if (i < count) out[i] += offs[i / 4096];
 }
 
-// exclusive scan of count <= 4096*4096 values; scratch holds >= 2*4096 words
-static int scan_exclusive(crk_ctx *ctx, const uint32_t *in, uint32_t *out, int count,
-                          uint32_t *scratch, cudaStream_t s) {
+// exclusive scan of count <= 4096*4096 values (ctx->scan_tmp holds >= 2*4096 words)
+int scan_u32(crk_ctx *ctx, const uint32_t *in, uint32_t *out, int count, cudaStream_t s) {
+    uint32_t *scratch = ctx->scan_tmp;
     int nb = grid_for(count, 4096);
     if (nb > 4096) return crk_set_error(ctx, CRK_ECAPACITY, "scan of %d items exceeds 2 levels", count);
     k_scan_block<<<nb, 1024, 0, s>>>(in, out, count, scratch);
@@ -190,7 +190,7 @@ static int radix_sort(crk_ctx *ctx, int n, int bits, cudaStream_t s) {
         int shift = 8 * p;
         k_rs_hist<<<nblocks, 256, 0, s>>>(n, kin, shift, ctx->hist, nblocks);
         ++ctx->launches;
-        int rc = scan_exclusive(ctx, ctx->hist, ctx->hist, 256 * nblocks, ctx->scan_tmp, s);
+        int rc = scan_u32(ctx, ctx->hist, ctx->hist, 256 * nblocks, s);
         if (rc) return rc;
         k_rs_scatter<<<nblocks, 256, 0, s>>>(n, kin, vin, kout, vout, shift, ctx->hist, nblocks);
         ++ctx->launches;
@@ -359,11 +359,8 @@ int rebuild_lists(crk_ctx *ctx, cudaStream_t s) {
     if (ctx->ntiles == 0) return CRK_OK;
     TreeDesc T = tree_desc(ctx);
     CRK_CUDA(ctx, cudaMemsetAsync(ctx->counters + CNT_GLIST, 0, 2 * sizeof(unsigned long long), s));
+    ctx->lists_valid = 0;
     int b = 128;
-    k_lists<false><<<grid_for(ctx->ntiles, b), b, 0, s>>>(ctx->ntiles, T, ctx->node_lo, ctx->node_hi,
-                                                           ctx->gofs, ctx->glist, ctx->cap_glist,
-                                                           ctx->counters + CNT_GLIST);
-    ++ctx->launches;
     k_lists<true><<<grid_for(ctx->ntiles, b), b, 0, s>>>(ctx->ntiles, T, ctx->node_lo, ctx->node_hi,
                                                           ctx->uofs, ctx->ulist, ctx->cap_ulist,
                                                           ctx->counters + CNT_ULIST);
@@ -458,17 +455,16 @@ int finish_build(crk_ctx *ctx, cudaStream_t s) {
     if (ctx->h_counters[CNT_ERR_INPUT])
         return crk_set_error(ctx, CRK_EINVAL, "%llu particle records have coordinates outside [0,1) "
                              "or h outside (0, 1/3)", ctx->h_counters[CNT_ERR_INPUT]);
-    long long ng = (long long)ctx->h_counters[CNT_GLIST], nu = (long long)ctx->h_counters[CNT_ULIST];
-    if (ng > ctx->cap_glist || nu > ctx->cap_ulist) {
-        rc = crk_ensure_lists(ctx, ng + ng / 4 + 1024, nu + nu / 4 + 1024);
+    long long ng = 0, nu = (long long)ctx->h_counters[CNT_ULIST];
+    if (nu > ctx->cap_ulist) {
+        rc = crk_ensure_lists(ctx, 0, nu + nu / 4 + 1024);
         if (rc) return rc;
         rc = rebuild_lists(ctx, s);
         if (rc) return rc;
         rc = crk_sync_counters(ctx, s);
         if (rc) return rc;
-        ng = (long long)ctx->h_counters[CNT_GLIST];
         nu = (long long)ctx->h_counters[CNT_ULIST];
-        if (ng > ctx->cap_glist || nu > ctx->cap_ulist)
+        if (nu > ctx->cap_ulist)
             return crk_set_error(ctx, CRK_ECAPACITY, "interaction lists overflow after growth");
     }
     ctx->glist_total = ng;

@@ -80,8 +80,17 @@ int crk_ensure_particles(crk_ctx *ctx, int n) {
     rc |= dalloc(ctx, &ctx->h_tmp, cap);
     rc |= dalloc(ctx, &ctx->flags, cap);
     rc |= dalloc(ctx, &ctx->d_dt, cap);
-    rc |= dalloc(ctx, &ctx->gofs, tiles);
     rc |= dalloc(ctx, &ctx->uofs, tiles);
+    rc |= dalloc(ctx, &ctx->qV, cap);
+    rc |= dalloc(ctx, &ctx->cnt_g, cap);
+    rc |= dalloc(ctx, &ctx->cnt_u, cap);
+    rc |= dalloc(ctx, &ctx->len_g, tiles);
+    rc |= dalloc(ctx, &ctx->len_u, tiles);
+    rc |= dalloc(ctx, &ctx->tcap, tiles);
+    rc |= dalloc(ctx, &ctx->tbase, tiles);
+    rc |= dalloc(ctx, &ctx->frec, 10 * (size_t)cap);
+    rc |= dalloc(ctx, &ctx->sfun, cap);
+    rc |= dalloc(ctx, &ctx->sig, cap);
     rc |= dalloc(ctx, &ctx->node_lo, 2 * (size_t)tiles + MAX_LEVELS);
     rc |= dalloc(ctx, &ctx->node_hi, 2 * (size_t)tiles + MAX_LEVELS);
     rc |= dalloc(ctx, &ctx->hist, 256 * (size_t)nb);
@@ -95,8 +104,25 @@ int crk_ensure_particles(crk_ctx *ctx, int n) {
     ctx->cap_nodes = 2 * tiles + MAX_LEVELS;
     ctx->cap_hist = 256 * nb;
     ctx->rates_valid = 0;
+    ctx->lists_valid = 0;
     long long want = (long long)tiles * 48;
-    if (ctx->cap_glist < want || ctx->cap_ulist < want) return crk_ensure_lists(ctx, want, want);
+    if (ctx->cap_ulist < want) return crk_ensure_lists(ctx, 0, want);
+    return CRK_OK;
+}
+
+int crk_ensure_entries(crk_ctx *ctx, long long total) {
+    if (total > 0xffffffffll)
+        return crk_set_error(ctx, CRK_ECAPACITY, "neighbour lists beyond 2^32 entries");
+    if (total <= ctx->ent_cap && ctx->ent) return CRK_OK;
+    long long cap = total + total / 5 + 4096;
+    if (cap > 0xffffffffll) cap = 0xffffffffll;
+    int rc = dalloc(ctx, &ctx->ent, (size_t)cap);
+    rc |= dalloc(ctx, &ctx->Fst, (size_t)cap);
+    if (rc) {
+        ctx->ent_cap = 0;
+        return crk_set_error(ctx, CRK_ENOMEM, "cannot allocate %lld neighbour-list entries", cap);
+    }
+    ctx->ent_cap = cap;
     return CRK_OK;
 }
 
@@ -221,6 +247,14 @@ __global__ void k_unpack_forces(int n, const int32_t *__restrict__ perm, const f
     float2 q = vq[s];
     if (vsig) vsig[i] = q.x;
     if (qmax) qmax[i] = q.y;
+}
+
+// (q, V) records of the gather passes from the sorted V
+__global__ void k_make_qV(int n, const uint4 *__restrict__ q4, const float *__restrict__ V, uint4 *__restrict__ qV) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    uint4 q = q4[s];
+    qV[s] = make_uint4(q.x, q.y, q.z, __float_as_uint(V[s]));
 }
 
 namespace crk {
@@ -378,6 +412,9 @@ extern "C" int crk_destroy(crk_ctx *ctx) {
     dfree(&ctx->q4); dfree(&ctx->hs); dfree(&ctx->perm); dfree(&ctx->keys);
     dfree(&ctx->node_lo); dfree(&ctx->node_hi);
     dfree(&ctx->gofs); dfree(&ctx->uofs); dfree(&ctx->glist); dfree(&ctx->ulist);
+    dfree(&ctx->qV); dfree(&ctx->cnt_g); dfree(&ctx->cnt_u); dfree(&ctx->len_g); dfree(&ctx->len_u);
+    dfree(&ctx->tcap); dfree(&ctx->tbase); dfree(&ctx->ent); dfree(&ctx->Fst); dfree(&ctx->frec);
+    dfree(&ctx->sfun); dfree(&ctx->sig);
     dfree(&ctx->cell_start); dfree(&ctx->counters);
     dfree(&ctx->V); dfree(&ctx->Nn); dfree(&ctx->vel); dfree(&ctx->mass);
     dfree(&ctx->corr); dfree(&ctx->gv); dfree(&ctx->acc); dfree(&ctx->vq);
@@ -407,6 +444,14 @@ static int need_built(crk_ctx *ctx) {
     if (!ctx) return CRK_EINVAL;
     if (!ctx->built) return crk_set_error(ctx, CRK_ESTATE, "call crk_build_cells first");
     return CRK_OK;
+}
+
+// neighbour lists of the current build (walk 1 + walk 2), built on first need
+static int need_lists(crk_ctx *ctx, cudaStream_t s) {
+    if (ctx->lists_valid) return CRK_OK;
+    int rc = run_volumes(ctx, s);
+    if (!rc) rc = run_lists(ctx, s);
+    return rc;
 }
 
 extern "C" int crk_build_cells(crk_ctx *ctx, int n, const float *pos_h, void *stream) {
@@ -453,7 +498,7 @@ extern "C" int crk_build_stats(crk_ctx *ctx, int *ntiles, long long *g, long lon
     rc = crk_sync_counters(ctx, (cudaStream_t)stream);
     if (rc) return rc;
     if (ntiles) *ntiles = ctx->ntiles;
-    if (g) *g = (long long)ctx->h_counters[CNT_GLIST];
+    if (g) *g = ctx->lists_valid ? ctx->entries : 0;
     if (u) *u = (long long)ctx->h_counters[CNT_ULIST];
     return CRK_OK;
 }
@@ -496,9 +541,16 @@ extern "C" int crk_corrections(crk_ctx *ctx, const float *V, const float *vel_u,
         return crk_set_error(ctx, CRK_EINVAL, "NULL argument");
     cudaStream_t s = (cudaStream_t)stream;
     int n = ctx->n;
+    rc = need_lists(ctx, s);
+    if (rc) return rc;
     rc = gather_rows(ctx, V, ctx->V, 1, s);
     if (!rc && vel_u) rc = gather_rows(ctx, vel_u, ctx->vel, 4, s);
     if (rc) return rc;
+    if (n) {
+        k_make_qV<<<grid_for(n, 256), 256, 0, s>>>(n, ctx->q4, ctx->V, ctx->qV);
+        ++ctx->launches;
+        CRK_LAUNCH_CHECK(ctx, "gather records");
+    }
     rc = run_corrections(ctx, gradv != nullptr, s);
     if (rc) return rc;
     if (n) {
@@ -517,7 +569,8 @@ static int pack_force_inputs(crk_ctx *ctx, const float *mass, const float *vel_u
                              const float *B, const float *gradA, const float *gradB, const float *gradv,
                              cudaStream_t s) {
     int n = ctx->n;
-    int rc = gather_rows(ctx, mass, ctx->mass, 1, s);
+    int rc = need_lists(ctx, s);
+    if (!rc) rc = gather_rows(ctx, mass, ctx->mass, 1, s);
     if (!rc) rc = gather_rows(ctx, vel_u, ctx->vel, 4, s);
     if (!rc) rc = gather_rows(ctx, V, ctx->V, 1, s);
     if (rc) return rc;
@@ -576,7 +629,8 @@ extern "C" int crk_compatible(crk_ctx *ctx, const float *mass, const float *vel_
         ++ctx->launches;
         CRK_LAUNCH_CHECK(ctx, "pack kick velocities");
     }
-    rc = run_compatible(ctx, s);
+    rc = run_forces(ctx, s);     // F_ij of this evaluation state
+    if (!rc) rc = run_compatible(ctx, s);
     if (rc) return rc;
     return scatter_rows(ctx, ctx->du, du, 1, s);
 }

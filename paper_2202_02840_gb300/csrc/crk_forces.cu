@@ -1,4 +1,5 @@
-// crk_forces.cu -- pair-set passes over {(i,j), i != j : |dq|^2 < max(H_i,H_j)^2}:
+// crk_forces.cu -- pair-set passes over {(i,j), i != j : |dq|^2 < max(H_i,H_j)^2},
+// walking each particle's neighbour list:
 //   P4 momentum and direct energy rates with limited artificial viscosity
 //      (CRK-HACC Sec. 1.2 eq:mom, eq:eng, eq:visc, eq:mu, eq:hatvi, eq:phi..eq:phiad)
 //   P5 compatible energy (Sec. 1.2 eq:compEng .. eq:fij)
@@ -6,7 +7,8 @@
 // Every ordered pair is evaluated from its i side.  The pair function is
 // written so that evaluating (j, i) with the negated separation performs the
 // same floating-point operations on swapped operands: F_ji == -F_ij bitwise,
-// so the pairwise antisymmetry of eq:mom survives rounding.
+// so the pairwise antisymmetry of eq:mom survives rounding.  P4 stores each
+// F_ij at its list entry; P5 (run once per half kick) reuses them.
 #include "crk_pass.cuh"
 
 namespace crk {
@@ -154,33 +156,55 @@ __device__ __forceinline__ void pair_force(const FRec &a, const FRec &b, const f
     o.Q_a = Qa;
 }
 
-struct FBase {
-    FSrc src;
-    FParams fp;
-};
+// Per-particle records of the pair-set passes, packed once per evaluation.
+__global__ void k_pack_frec(int n, FSrc src, FParams fp, FRec *__restrict__ out, float *__restrict__ sfun) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    FRec r = load_frec(i, src, fp);
+    out[i] = r;
+    sfun[i] = r.k1.y / powf(r.k1.z, fp.gamma);       // s = P / rho^gamma (eq:fij)
+}
+
+__device__ __forceinline__ FRec ldg_frec(const FRec *p) {
+    const float4 *q = reinterpret_cast<const float4 *>(p);
+    FRec r;
+    float4 a = __ldg(q);
+    r.q = make_uint4(__float_as_uint(a.x), __float_as_uint(a.y), __float_as_uint(a.z), __float_as_uint(a.w));
+    r.k0 = __ldg(q + 1);
+    r.k1 = __ldg(q + 2);
+    r.k2 = __ldg(q + 3);
+    r.k3 = __ldg(q + 4);
+    r.k4 = __ldg(q + 5);
+    r.k5 = __ldg(q + 6);
+    r.k6 = __ldg(q + 7);
+    r.k7 = __ldg(q + 8);
+    r.k8 = __ldg(q + 9);
+    return r;
+}
 
 // ================================================================= P4 forces
 
 template <bool COMP>
 struct P4 {
+    static constexpr bool GATHER = false;
     struct Params {
-        FSrc src;
+        const FRec *frec;
+        const float *mass;
         FParams fp;
         float4 *acc;   // (ax, ay, az, dudt)
         float2 *vq;    // (vsig, qmax)
+        float4 *Fst;   // F_ij per list entry
     };
-    typedef FRec JRec;
     struct IState {
         FRec me;
         float m;
         Acc<COMP> F[3], du;
         float vsig, qmax;
-        int np;
     };
     __device__ static void init(IState &s, int i, bool valid, const Params &p) {
         if (valid) {
-            s.me = load_frec(i, p.src, p.fp);
-            s.m = p.src.mass[i];
+            s.me = p.frec[i];
+            s.m = p.mass[i];
         } else {
             s.me = FRec{};
             s.me.k0.x = 1.f;
@@ -188,108 +212,69 @@ struct P4 {
         }
         s.vsig = 0.f;
         s.qmax = 0.f;
-        s.np = 0;
     }
-    __device__ static void stage(JRec &r, int j, const Params &p) { r = load_frec(j, p.src, p.fp); }
-    __device__ static void pair(IState &s, const JRec &r, int j, int i, bool valid, const Params &p) {
+    __device__ static void pair(IState &s, uint32_t e, uint32_t pos, bool in_i, const Params &p) {
+        const uint32_t j = e & 0x3fffffffu;
+        const bool in_j = in_i ? (e >> 31) != 0u : true;
+        const FRec r = ldg_frec(p.frec + j);
         int dx = (int)(s.me.q.x - r.q.x), dy = (int)(s.me.q.y - r.q.y), dz = (int)(s.me.q.z - r.q.z);
-        unsigned long long R2 = r2_fixed(dx, dy, dz);
-        unsigned long long Hi2 = (unsigned long long)s.me.q.w * s.me.q.w;
-        unsigned long long Hj2 = (unsigned long long)r.q.w * r.q.w;
-        bool in_i = R2 < Hi2, in_j = R2 < Hj2;
-        if (valid && (in_i || in_j) && i != j) {
-            Sep d = separation(dx, dy, dz);
-            float x[3] = {d.x, d.y, d.z};
-            PairOut o;
-            pair_force(s.me, r, x, d.r2, d.r, in_i, in_j, p.fp, o);
-            float dv[3] = {r.k2.x - s.me.k2.x, r.k2.y - s.me.k2.y, r.k2.z - s.me.k2.z};
+        Sep d = separation(dx, dy, dz);
+        float x[3] = {d.x, d.y, d.z};
+        PairOut o;
+        pair_force(s.me, r, x, d.r2, d.r, in_i, in_j, p.fp, o);
+        p.Fst[pos] = make_float4(o.F[0], o.F[1], o.F[2], 0.f);
+        float dv[3] = {r.k2.x - s.me.k2.x, r.k2.y - s.me.k2.y, r.k2.z - s.me.k2.z};
 #pragma unroll
-            for (int g = 0; g < 3; g++) s.F[g].add(o.F[g]);
-            float wd = fmaf(dv[0], o.D[0], fmaf(dv[1], o.D[1], dv[2] * o.D[2]));
-            s.du.add(0.5f * (s.me.k1.x * r.k1.x) * o.Pt_b * wd);
-            float vx = -fmaf(dv[0], x[0], fmaf(dv[1], x[1], dv[2] * x[2]));   // (v_i - v_j).x_ij
-            if (vx < 0.f && d.r > 0.f) s.vsig = fmaxf(s.vsig, -vx / d.r);
-            s.qmax = fmaxf(s.qmax, o.Q_a);
-            s.np++;
-        }
+        for (int g = 0; g < 3; g++) s.F[g].add(o.F[g]);
+        float wd = fmaf(dv[0], o.D[0], fmaf(dv[1], o.D[1], dv[2] * o.D[2]));
+        s.du.add(0.5f * (s.me.k1.x * r.k1.x) * o.Pt_b * wd);
+        float vx = -fmaf(dv[0], x[0], fmaf(dv[1], x[1], dv[2] * x[2]));   // (v_i - v_j).x_ij
+        if (vx < 0.f && d.r > 0.f) s.vsig = fmaxf(s.vsig, -vx / d.r);
+        s.qmax = fmaxf(s.qmax, o.Q_a);
     }
     __device__ static void finish(IState &s, int i, const Params &p) {
         float im = 1.f / s.m;
         p.acc[i] = make_float4(s.F[0].value() * im, s.F[1].value() * im, s.F[2].value() * im, s.du.value() * im);
         p.vq[i] = make_float2(s.vsig, s.qmax);
     }
-    __device__ static int count(const IState &s) { return s.np; }
 };
 
 // ================================================================= P5 compatible energy
 
-struct __align__(16) CRec {
-    FRec f;
-    float4 vb;   // velocity before the kick, s = P / rho^gamma
-    float4 va;   // velocity after the kick
-};
-
+// sig = (v + v') of the kick and the entropy s of the evaluation state
 template <bool COMP>
 struct P5 {
+    static constexpr bool GATHER = false;
     struct Params {
-        FSrc src;
-        FParams fp;
-        const float4 *vb, *va;
+        const float4 *sig;
+        const float4 *Fst;
+        const float *mass;
         float *du;
     };
-    typedef CRec JRec;
     struct IState {
-        CRec me;
+        float4 me;
         float m;
         Acc<COMP> du;
     };
-    __device__ static CRec load(int j, const Params &p) {
-        CRec c;
-        c.f = load_frec(j, p.src, p.fp);
-        float4 b = p.vb[j], a = p.va[j];
-        float rho = c.f.k1.z;
-        float s = c.f.k1.y / powf(rho, p.fp.gamma);
-        c.vb = make_float4(b.x, b.y, b.z, s);
-        c.va = make_float4(a.x, a.y, a.z, 0.f);
-        return c;
-    }
     __device__ static void init(IState &s, int i, bool valid, const Params &p) {
-        if (valid) {
-            s.me = load(i, p);
-            s.m = p.src.mass[i];
-        } else {
-            s.me = CRec{};
-            s.me.f.k0.x = 1.f;
-            s.m = 1.f;
-        }
+        s.me = valid ? p.sig[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        s.m = valid ? p.mass[i] : 1.f;
     }
-    __device__ static void stage(JRec &r, int j, const Params &p) { r = load(j, p); }
-    __device__ static void pair(IState &s, const JRec &r, int j, int i, bool valid, const Params &p) {
-        int dx = (int)(s.me.f.q.x - r.f.q.x), dy = (int)(s.me.f.q.y - r.f.q.y), dz = (int)(s.me.f.q.z - r.f.q.z);
-        unsigned long long R2 = r2_fixed(dx, dy, dz);
-        unsigned long long Hi2 = (unsigned long long)s.me.f.q.w * s.me.f.q.w;
-        unsigned long long Hj2 = (unsigned long long)r.f.q.w * r.f.q.w;
-        bool in_i = R2 < Hi2, in_j = R2 < Hj2;
-        if (valid && (in_i || in_j) && i != j) {
-            Sep d = separation(dx, dy, dz);
-            float x[3] = {d.x, d.y, d.z};
-            PairOut o;
-            pair_force(s.me.f, r.f, x, d.r2, d.r, in_i, in_j, p.fp, o);
-            float w = fmaf(r.vb.x + r.va.x - s.me.vb.x - s.me.va.x, o.F[0],
-                           fmaf(r.vb.y + r.va.y - s.me.vb.y - s.me.va.y, o.F[1],
-                                (r.vb.z + r.va.z - s.me.vb.z - s.me.va.z) * o.F[2]));
-            // eq:fij with Delta E_ij = w/2
-            float si = s.me.vb.w, sj = r.vb.w, ss = si + sj;
-            float f = 0.5f;
-            if (ss != 0.f) {
-                bool take_min = (w >= 0.f) == (si >= sj);
-                f = (take_min ? fminf(si, sj) : fmaxf(si, sj)) / ss;
-            }
-            s.du.add(0.5f * f * w);
+    __device__ static void pair(IState &s, uint32_t e, uint32_t pos, bool, const Params &p) {
+        const float4 r = __ldg(p.sig + (e & 0x3fffffffu));
+        const float4 F = __ldg(p.Fst + pos);
+        // 2 Delta E_ij = (v_j + v'_j - v_i - v'_i) . F_ij  (reading of eq:Eij)
+        float w = fmaf(r.x - s.me.x, F.x, fmaf(r.y - s.me.y, F.y, (r.z - s.me.z) * F.z));
+        // eq:fij
+        float si = s.me.w, sj = r.w, ss = si + sj;
+        float f = 0.5f;
+        if (ss != 0.f) {
+            bool take_min = (w >= 0.f) == (si >= sj);
+            f = (take_min ? fminf(si, sj) : fmaxf(si, sj)) / ss;
         }
+        s.du.add(0.5f * f * w);
     }
     __device__ static void finish(IState &s, int i, const Params &p) { p.du[i] = s.du.value() / s.m; }
-    __device__ static int count(const IState &) { return 0; }
 };
 
 static FParams fparams(const crk_params &c) {
@@ -305,27 +290,44 @@ static FParams fparams(const crk_params &c) {
     return f;
 }
 
-static FSrc fsrc(const crk_ctx *ctx) {
-    return FSrc{ctx->q4, ctx->hs, ctx->V, ctx->vel, ctx->mass, ctx->corr, ctx->gv};
+// kick velocities (w unused) -> sig = (vb + va, s)
+__global__ void k_sig(int n, const float4 *__restrict__ vb, const float4 *__restrict__ va,
+                      const float *__restrict__ sfun, float4 *__restrict__ sig) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float4 b = vb[i], a = va[i];
+    sig[i] = make_float4(b.x + a.x, b.y + a.y, b.z + a.z, sfun[i]);
 }
 
 int run_forces(crk_ctx *ctx, cudaStream_t s) {
-    CRK_CUDA(ctx, cudaMemsetAsync(ctx->counters + CNT_PAIRS_U, 0, sizeof(unsigned long long), s));
+    if (ctx->n == 0) return CRK_OK;
+    FParams fp = fparams(ctx->p);
+    FSrc src{ctx->q4, ctx->hs, ctx->V, ctx->vel, ctx->mass, ctx->corr, ctx->gv};
+    k_pack_frec<<<grid_for(ctx->n, 256), 256, 0, s>>>(ctx->n, src, fp, reinterpret_cast<FRec *>(ctx->frec),
+                                                     ctx->sfun);
+    ++ctx->launches;
+    CRK_LAUNCH_CHECK(ctx, "pack pair records");
+    const FRec *fr = reinterpret_cast<const FRec *>(ctx->frec);
     if (ctx->p.precision == 1) {
-        typename P4<true>::Params p{fsrc(ctx), fparams(ctx->p), ctx->acc, ctx->vq};
-        return launch_pass<P4<true>, 4>(ctx, PROF_P4, true, p, ctx->counters + CNT_PAIRS_U, s, "P4 forces");
+        typename P4<true>::Params p{fr, ctx->mass, fp, ctx->acc, ctx->vq, ctx->Fst};
+        return launch_lpass<P4<true>, 4>(ctx, PROF_P4, p, s, "P4 forces");
     }
-    typename P4<false>::Params p{fsrc(ctx), fparams(ctx->p), ctx->acc, ctx->vq};
-    return launch_pass<P4<false>, 4>(ctx, PROF_P4, true, p, ctx->counters + CNT_PAIRS_U, s, "P4 forces");
+    typename P4<false>::Params p{fr, ctx->mass, fp, ctx->acc, ctx->vq, ctx->Fst};
+    return launch_lpass<P4<false>, 4>(ctx, PROF_P4, p, s, "P4 forces");
 }
 
+// P5 for the kick vb -> va (sorted float4 arrays), with the F_ij of the last P4.
 int run_compatible(crk_ctx *ctx, cudaStream_t s) {
+    if (ctx->n == 0) return CRK_OK;
+    k_sig<<<grid_for(ctx->n, 256), 256, 0, s>>>(ctx->n, ctx->vb, ctx->va, ctx->sfun, ctx->sig);
+    ++ctx->launches;
+    CRK_LAUNCH_CHECK(ctx, "kick sums");
     if (ctx->p.precision == 1) {
-        typename P5<true>::Params p{fsrc(ctx), fparams(ctx->p), ctx->vb, ctx->va, ctx->du};
-        return launch_pass<P5<true>, 4>(ctx, PROF_P5, true, p, nullptr, s, "P5 compatible energy");
+        typename P5<true>::Params p{ctx->sig, ctx->Fst, ctx->mass, ctx->du};
+        return launch_lpass<P5<true>, 8>(ctx, PROF_P5, p, s, "P5 compatible energy");
     }
-    typename P5<false>::Params p{fsrc(ctx), fparams(ctx->p), ctx->vb, ctx->va, ctx->du};
-    return launch_pass<P5<false>, 4>(ctx, PROF_P5, true, p, nullptr, s, "P5 compatible energy");
+    typename P5<false>::Params p{ctx->sig, ctx->Fst, ctx->mass, ctx->du};
+    return launch_lpass<P5<false>, 8>(ctx, PROF_P5, p, s, "P5 compatible energy");
 }
 
 }  // namespace crk

@@ -27,6 +27,7 @@ enum {
     CNT_WORK = 6,       // dynamic tile counter of the persistent pair kernels
     CNT_NOTDONE = 7,    // h iteration: particles not converged
     CNT_DTMIN = 8,      // min per-particle time step (float bits)
+    CNT_ENTRIES = 9,    // neighbour-list entries of the last list build
     CNT_COUNT = 16
 };
 
@@ -100,6 +101,19 @@ struct crk_ctx {
     unsigned long long *counters = nullptr;
     unsigned long long *h_counters = nullptr;   // pinned host mirror
 
+    // per-particle neighbour lists (column layout per tile) and stored pair forces
+    uint4 *qV = nullptr;             // (qx, qy, qz, V bits)
+    int32_t *cnt_g = nullptr, *cnt_u = nullptr;   // gather (j != i) and pair-set counts
+    uint32_t *len_g = nullptr, *len_u = nullptr;  // per-tile max counts
+    uint32_t *tcap = nullptr, *tbase = nullptr;   // per-tile entry capacity / base
+    uint32_t *ent = nullptr;         // list entries: j | (j's kernel reaches i) << 31
+    float4 *Fst = nullptr;           // F_ij per entry (P4 -> P5)
+    long long ent_cap = 0, entries = 0;
+    int lists_valid = 0;
+    float4 *frec = nullptr;          // packed pair-set records, 10 float4 per particle
+    float *sfun = nullptr;           // specific entropy of the evaluation state
+    float4 *sig = nullptr;           // (v + v') of a kick, s
+
     // pass buffers in sorted order
     float *V = nullptr, *Nn = nullptr;
     float4 *vel = nullptr;           // (vx, vy, vz, u) of the evaluation state
@@ -141,6 +155,7 @@ int crk_set_error(crk_ctx *ctx, int code, const char *fmt, ...);
 int crk_check_cuda(crk_ctx *ctx, cudaError_t e, const char *what);
 int crk_ensure_particles(crk_ctx *ctx, int n);
 int crk_ensure_lists(crk_ctx *ctx, long long ng, long long nu);
+int crk_ensure_entries(crk_ctx *ctx, long long total);
 int crk_sync_counters(crk_ctx *ctx, cudaStream_t s);
 
 #define CRK_CUDA(ctx, call)                                                      \
@@ -158,7 +173,7 @@ int crk_sync_counters(crk_ctx *ctx, cudaStream_t s);
 // internal entry points shared between translation units (sorted-order data)
 namespace crk {
 enum { PROF_P1 = 0, PROF_PN = 1, PROF_P2 = 2, PROF_P3 = 3, PROF_P4 = 4, PROF_P5 = 5, PROF_BUILD = 6,
-       PROF_NPASS = 8 };
+       PROF_LISTS = 7, PROF_NPASS = 8 };
 void prof_begin(crk_ctx *ctx, int id, cudaStream_t s);
 void prof_end(crk_ctx *ctx, cudaStream_t s);
 int build_cells_sorted(crk_ctx *ctx, int n, const float4 *pos_h, const int32_t *order,
@@ -168,6 +183,8 @@ int build_tree(crk_ctx *ctx, cudaStream_t s);
 int finish_build(crk_ctx *ctx, cudaStream_t s);
 int cell_level_host(const crk_ctx *ctx);
 int run_volumes(crk_ctx *ctx, cudaStream_t s);
+int run_lists(crk_ctx *ctx, cudaStream_t s);
+int scan_u32(crk_ctx *ctx, const uint32_t *in, uint32_t *out, int count, cudaStream_t s);
 int run_neighbours(crk_ctx *ctx, int mode, int32_t *cnt, uint32_t *hash, cudaStream_t s);
 int run_corrections(crk_ctx *ctx, bool with_gradv, cudaStream_t s);
 int run_forces(crk_ctx *ctx, cudaStream_t s);

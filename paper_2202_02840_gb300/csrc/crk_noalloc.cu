@@ -24,8 +24,8 @@ constexpr int TMAX = NMAX / crk::TILE;
 constexpr size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-    size_t key_a, key_b, idx_a, idx_b, keys, perm, q_tmp, q4, h_tmp, hs, V, Nn;
-    size_t nlo, nhi, gofs, uofs, glist, ulist, hist, scan, cells, counters, total;
+    size_t key_a, key_b, idx_a, idx_b, keys, perm, q_tmp, q4, h_tmp, hs, V, Nn, qV, cnt_g, cnt_u;
+    size_t nlo, nhi, uofs, ulist, len_g, len_u, hist, scan, cells, counters, total;
 };
 
 constexpr Layout make_layout() {
@@ -43,12 +43,15 @@ constexpr Layout make_layout() {
     L.hs = o;       o = al(o + 4ull * NMAX);
     L.V = o;        o = al(o + 4ull * NMAX);
     L.Nn = o;       o = al(o + 4ull * NMAX);
+    L.qV = o;       o = al(o + 16ull * NMAX);
+    L.cnt_g = o;    o = al(o + 4ull * NMAX);
+    L.cnt_u = o;    o = al(o + 4ull * NMAX);
     L.nlo = o;      o = al(o + 16ull * (2 * TMAX + crk::MAX_LEVELS));
     L.nhi = o;      o = al(o + 16ull * (2 * TMAX + crk::MAX_LEVELS));
-    L.gofs = o;     o = al(o + 8ull * TMAX);
     L.uofs = o;     o = al(o + 8ull * TMAX);
-    L.glist = o;    o = al(o + 4ull * TMAX * TMAX);   // every tile may neighbour every tile
-    L.ulist = o;    o = al(o + 4ull * TMAX * TMAX);
+    L.ulist = o;    o = al(o + 4ull * TMAX * TMAX);   // every tile may neighbour every tile
+    L.len_g = o;    o = al(o + 4ull * TMAX);
+    L.len_u = o;    o = al(o + 4ull * TMAX);
     L.hist = o;     o = al(o + 4ull * 256 * ((NMAX + 4095) / 4096));
     L.scan = o;     o = al(o + 4ull * (2 * 4096 + 64));
     L.cells = o;    o = al(o + 4ull * 9);              // chaining-mesh table at level 1
@@ -61,7 +64,7 @@ constexpr Layout LAY = make_layout();
 
 }  // namespace
 
-// The scratch of every call (about 3.3 MB for NMAX = 16384).
+// The scratch of every call (about 3.0 MB for NMAX = 16384).
 static __device__ __align__(256) unsigned char g_noalloc_scratch[LAY.total];
 
 // Device address of g_noalloc_scratch, resolved once per device.
@@ -98,12 +101,15 @@ extern "C" int crk_volumes_noalloc(int n, const float *pos_h, float *V, float *N
     ctx.hs = (float *)(b + LAY.hs);
     ctx.V = (float *)(b + LAY.V);
     ctx.Nn = (float *)(b + LAY.Nn);
+    ctx.qV = (uint4 *)(b + LAY.qV);
+    ctx.cnt_g = (int32_t *)(b + LAY.cnt_g);
+    ctx.cnt_u = (int32_t *)(b + LAY.cnt_u);
     ctx.node_lo = (uint4 *)(b + LAY.nlo);
     ctx.node_hi = (uint4 *)(b + LAY.nhi);
-    ctx.gofs = (uint2 *)(b + LAY.gofs);
     ctx.uofs = (uint2 *)(b + LAY.uofs);
-    ctx.glist = (uint32_t *)(b + LAY.glist);
     ctx.ulist = (uint32_t *)(b + LAY.ulist);
+    ctx.len_g = (uint32_t *)(b + LAY.len_g);
+    ctx.len_u = (uint32_t *)(b + LAY.len_u);
     ctx.hist = (uint32_t *)(b + LAY.hist);
     ctx.scan_tmp = (uint32_t *)(b + LAY.scan);
     ctx.cell_start = (int32_t *)(b + LAY.cells);
@@ -112,7 +118,6 @@ extern "C" int crk_volumes_noalloc(int n, const float *pos_h, float *V, float *N
     ctx.cap_tiles = TMAX;
     ctx.cap_nodes = 2 * TMAX + crk::MAX_LEVELS;
     ctx.cap_hist = 256 * ((NMAX + 4095) / 4096);
-    ctx.cap_glist = (long long)TMAX * TMAX;
     ctx.cap_ulist = (long long)TMAX * TMAX;
 
     if (cudaMemsetAsync(ctx.counters, 0, sizeof(unsigned long long) * crk::CNT_COUNT, s) != cudaSuccess)
@@ -125,7 +130,7 @@ extern "C" int crk_volumes_noalloc(int n, const float *pos_h, float *V, float *N
         cudaStreamSynchronize(s) != cudaSuccess)
         return CRK_ECUDA;
     if (hc[crk::CNT_ERR_INPUT]) return CRK_EINVAL;
-    if ((long long)hc[crk::CNT_GLIST] > ctx.cap_glist) return CRK_ECAPACITY;
+    if ((long long)hc[crk::CNT_ULIST] > ctx.cap_ulist) return CRK_ECAPACITY;
     rc = crk::run_volumes(&ctx, s);
     if (!rc) rc = crk::scatter_rows(&ctx, ctx.V, V, 1, s);
     if (!rc && Nngb) rc = crk::scatter_rows(&ctx, ctx.Nn, Nngb, 1, s);

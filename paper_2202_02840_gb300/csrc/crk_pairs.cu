@@ -1,62 +1,12 @@
-// crk_pairs.cu -- gather pair passes over gather(i) = {j : |dq|^2 < H_i^2}:
-//   P1 volumes           (CRK-HACC Sec. 1.2 eq:vol, Sec. 2.6 eq:hi)
+// crk_pairs.cu -- gather pair passes over gather(i) = {j : |dq|^2 < H_i^2},
+// walking each particle's neighbour list (P1 volumes are fused into the
+// list-counting walk, crk_walk.cu):
 //   P2 RK corrections    (Sec. 1.2 eq:RK, eq:gRK, moment conditions)
 //   P3 velocity gradient (Sec. 1.2 eq:gradv)
+// plus the tile-walk neighbour-set inspection pass.
 #include "crk_pass.cuh"
 
 namespace crk {
-
-// ================================================================= P1 volumes
-
-struct P1 {
-    struct Params {
-        const uint4 *q4;
-        const float *hs;
-        float *V, *Nn;
-    };
-    struct JRec {
-        uint4 q;
-    };
-    struct IState {
-        uint4 q;
-        unsigned long long H2;
-        float h, inv_h, acc;
-        int np;
-    };
-    __device__ static void init(IState &s, int i, bool valid, const Params &p) {
-        s.q = valid ? p.q4[i] : make_uint4(0, 0, 0, 0);
-        s.h = valid ? p.hs[i] : 1.f;
-        s.H2 = (unsigned long long)s.q.w * s.q.w;
-        s.inv_h = 1.f / s.h;
-        s.acc = 0.f;
-        s.np = 0;
-    }
-    __device__ static void stage(JRec &r, int j, const Params &p) { r.q = p.q4[j]; }
-    __device__ static void pair(IState &s, const JRec &r, int, int, bool, const Params &) {
-        int dx = (int)(s.q.x - r.q.x), dy = (int)(s.q.y - r.q.y), dz = (int)(s.q.z - r.q.z);
-        if (r2_fixed(dx, dy, dz) < s.H2) {
-            Sep x = separation(dx, dy, dz);
-            float eta = x.r * s.inv_h;
-            float t = fmaxf(1.f - eta, 0.f);
-            float t2 = t * t, t3 = t2 * t;
-            s.acc = fmaf(t3 * t3, fmaf(eta, fmaf(eta, K35_3, 6.f), 1.f), s.acc);
-            s.np++;
-        }
-    }
-    __device__ static void finish(IState &s, int i, const Params &p) {
-        float ih3 = s.inv_h * s.inv_h * s.inv_h;
-        float nsum = KW * ih3 * s.acc;                       // n_i, eq:vol
-        p.V[i] = 1.f / nsum;
-        if (p.Nn) p.Nn[i] = (4.18879020f * s.h * s.h * s.h) * nsum;   // eq:hi, 4/3 pi h^3 n_i
-    }
-    __device__ static int count(const IState &s) { return s.np - 1; }
-};
-
-int run_volumes(crk_ctx *ctx, cudaStream_t s) {
-    P1::Params p{ctx->q4, ctx->hs, ctx->V, ctx->Nn};
-    CRK_CUDA(ctx, cudaMemsetAsync(ctx->counters + CNT_PAIRS_G, 0, sizeof(unsigned long long), s));
-    return launch_pass<P1, 8>(ctx, PROF_P1, false, p, ctx->counters + CNT_PAIRS_G, s, "P1 volumes");
-}
 
 // ================================================================= neighbour sets
 
@@ -122,7 +72,7 @@ struct PN {
 int run_neighbours(crk_ctx *ctx, int mode, int32_t *cnt, uint32_t *hash, cudaStream_t s) {
     if (mode == 0) {
         PN<false>::Params p{ctx->q4, ctx->perm, cnt, hash};
-        return launch_pass<PN<false>, 8>(ctx, PROF_PN, false, p, nullptr, s, "neighbour sets");
+        return launch_pass<PN<false>, 8>(ctx, PROF_PN, true, p, nullptr, s, "neighbour sets");
     }
     PN<true>::Params p{ctx->q4, ctx->perm, cnt, hash};
     return launch_pass<PN<true>, 8>(ctx, PROF_PN, true, p, nullptr, s, "neighbour sets");
@@ -198,26 +148,21 @@ __device__ __forceinline__ void rk_solve(I m0f, const I *m1f, const I *m2f, cons
 
 template <bool FP64_SOLVE, bool COMP>
 struct P2 {
+    static constexpr bool GATHER = true;
     struct Params {
         const uint4 *q4;
+        const uint4 *qV;   // (qx, qy, qz, V bits)
         const float *hs;
-        const float *V;
         CorrRec *corr;
-    };
-    struct __align__(16) JRec {
-        uint4 q;
-        float4 v;   // V_j, -, -, -
     };
     struct IState {
         uint4 q;
-        unsigned long long H2;
         float h, inv_h;
         Acc<COMP> m0, m1[3], m2[6], dm0[3], s1[9], s2[18];
     };
     __device__ static void init(IState &s, int i, bool valid, const Params &p) {
         s.q = valid ? p.q4[i] : make_uint4(0, 0, 0, 0);
         s.h = valid ? p.hs[i] : 1.f;
-        s.H2 = (unsigned long long)s.q.w * s.q.w;
         s.inv_h = 1.f / s.h;
         s.m0 = Acc<COMP>();
 #pragma unroll
@@ -228,41 +173,39 @@ struct P2 {
         for (int a = 0; a < 9; a++) s.s1[a] = Acc<COMP>();
 #pragma unroll
         for (int a = 0; a < 18; a++) s.s2[a] = Acc<COMP>();
+        // self term of gather(i): x = 0, W(0) (unnormalised 1), grad W(0) = 0
+        if (valid) s.m0.add(__uint_as_float(__ldg(&p.qV[i].w)));
     }
-    __device__ static void stage(JRec &r, int j, const Params &p) {
-        r.q = p.q4[j];
-        r.v = make_float4(p.V[j], 0.f, 0.f, 0.f);
-    }
-    __device__ static void pair(IState &s, const JRec &r, int, int, bool, const Params &) {
-        int dx = (int)(s.q.x - r.q.x), dy = (int)(s.q.y - r.q.y), dz = (int)(s.q.z - r.q.z);
-        if (r2_fixed(dx, dy, dz) < s.H2) {
-            Sep d = separation(dx, dy, dz);
-            float x[3] = {d.x, d.y, d.z};
-            float eta = d.r * s.inv_h;
-            float t = fmaxf(1.f - eta, 0.f);
-            float t2 = t * t, t4 = t2 * t2, t5 = t4 * t;
-            float Wu = t5 * t * fmaf(eta, fmaf(eta, K35_3, 6.f), 1.f);   // W / (495/(32 pi h^3))
-            float Gu = -fmaf(5.f, eta, 1.f) * t5;                        // grad W / (1155/(4 pi h^5) x)
-            float w = r.v.x * Wu, g = r.v.x * Gu;
-            float gx[3] = {g * x[0], g * x[1], g * x[2]};
-            float xx[6] = {x[0] * x[0], x[0] * x[1], x[0] * x[2], x[1] * x[1], x[1] * x[2], x[2] * x[2]};
-            s.m0.add(w);
+    __device__ static void pair(IState &s, uint32_t e, uint32_t, bool, const Params &p) {
+        const uint4 r = __ldg(p.qV + (e & 0x3fffffffu));
+        int dx = (int)(s.q.x - r.x), dy = (int)(s.q.y - r.y), dz = (int)(s.q.z - r.z);
+        const float Vj = __uint_as_float(r.w);
+        Sep d = separation(dx, dy, dz);
+        float x[3] = {d.x, d.y, d.z};
+        float eta = d.r * s.inv_h;
+        float t = fmaxf(1.f - eta, 0.f);
+        float t2 = t * t, t4 = t2 * t2, t5 = t4 * t;
+        float Wu = t5 * t * fmaf(eta, fmaf(eta, K35_3, 6.f), 1.f);   // W / (495/(32 pi h^3))
+        float Gu = -fmaf(5.f, eta, 1.f) * t5;                        // grad W / (1155/(4 pi h^5) x)
+        float w = Vj * Wu, g = Vj * Gu;
+        float gx[3] = {g * x[0], g * x[1], g * x[2]};
+        float xx[6] = {x[0] * x[0], x[0] * x[1], x[0] * x[2], x[1] * x[1], x[1] * x[2], x[2] * x[2]};
+        s.m0.add(w);
 #pragma unroll
-            for (int a = 0; a < 3; a++) {
-                s.m1[a].add(w * x[a]);
-                s.dm0[a].add(gx[a]);
-            }
-#pragma unroll
-            for (int p = 0; p < 6; p++) s.m2[p].add(w * xx[p]);
-#pragma unroll
-            for (int a = 0; a < 3; a++)
-#pragma unroll
-                for (int gg = 0; gg < 3; gg++) s.s1[3 * a + gg].add(x[a] * gx[gg]);
-#pragma unroll
-            for (int p = 0; p < 6; p++)
-#pragma unroll
-                for (int gg = 0; gg < 3; gg++) s.s2[3 * p + gg].add(xx[p] * gx[gg]);
+        for (int a = 0; a < 3; a++) {
+            s.m1[a].add(w * x[a]);
+            s.dm0[a].add(gx[a]);
         }
+#pragma unroll
+        for (int q = 0; q < 6; q++) s.m2[q].add(w * xx[q]);
+#pragma unroll
+        for (int a = 0; a < 3; a++)
+#pragma unroll
+            for (int gg = 0; gg < 3; gg++) s.s1[3 * a + gg].add(x[a] * gx[gg]);
+#pragma unroll
+        for (int q = 0; q < 6; q++)
+#pragma unroll
+            for (int gg = 0; gg < 3; gg++) s.s2[3 * q + gg].add(xx[q] * gx[gg]);
     }
     // Moments from the pair sums: W-type sums scale by cW = 495/(32 pi h^3),
     // gradient sums by cG = 1155/(4 pi h^5); then
@@ -315,28 +258,23 @@ struct P2 {
         }
         p.corr[i] = out;
     }
-    __device__ static int count(const IState &) { return 0; }
 };
 
 // ================================================================= P3 grad v
 
 template <bool COMP>
 struct P3 {
+    static constexpr bool GATHER = true;
     struct Params {
         const uint4 *q4;
+        const uint4 *qV;
         const float *hs;
-        const float *V;
         const float4 *vel;
         const CorrRec *corr;
         GvRec *gv;
     };
-    struct __align__(16) JRec {
-        uint4 q;
-        float4 vv;   // vx, vy, vz, V
-    };
     struct IState {
         uint4 q;
-        unsigned long long H2;
         float inv_h, cW, cG;
         float A, B[3], gA[3], gB[9], v[3];
         Acc<COMP> acc[9];
@@ -344,7 +282,6 @@ struct P3 {
     __device__ static void init(IState &s, int i, bool valid, const Params &p) {
         s.q = valid ? p.q4[i] : make_uint4(0, 0, 0, 0);
         float h = valid ? p.hs[i] : 1.f;
-        s.H2 = (unsigned long long)s.q.w * s.q.w;
         s.inv_h = 1.f / h;
         float ih2 = s.inv_h * s.inv_h, ih3 = ih2 * s.inv_h;
         s.cW = KW * ih3;
@@ -360,36 +297,33 @@ struct P3 {
 #pragma unroll
         for (int k = 0; k < 9; k++) s.acc[k] = Acc<COMP>();
     }
-    __device__ static void stage(JRec &r, int j, const Params &p) {
-        r.q = p.q4[j];
-        float4 v = p.vel[j];
-        r.vv = make_float4(v.x, v.y, v.z, p.V[j]);
-    }
-    __device__ static void pair(IState &s, const JRec &r, int, int, bool, const Params &) {
-        int dx = (int)(s.q.x - r.q.x), dy = (int)(s.q.y - r.q.y), dz = (int)(s.q.z - r.q.z);
-        if (r2_fixed(dx, dy, dz) < s.H2) {
-            Sep d = separation(dx, dy, dz);
-            float x[3] = {d.x, d.y, d.z};
-            float eta = d.r * s.inv_h;
-            float t = fmaxf(1.f - eta, 0.f);
-            float t2 = t * t, t4 = t2 * t2, t5 = t4 * t;
-            float W = s.cW * t5 * t * fmaf(eta, fmaf(eta, K35_3, 6.f), 1.f);
-            float G = s.cG * fmaf(5.f, eta, 1.f) * t5;       // grad W = G x
-            // eq:gRK with the i-side coefficients
-            float sB = fmaf(s.B[0], x[0], fmaf(s.B[1], x[1], fmaf(s.B[2], x[2], 1.f)));
-            float sW = sB * W, AW = s.A * W, AsG = s.A * sB * G;
-            float gR[3];
+    __device__ static void pair(IState &s, uint32_t e, uint32_t, bool, const Params &p) {
+        const uint32_t j = e & 0x3fffffffu;
+        const uint4 r = __ldg(p.qV + j);
+        const float4 vj = __ldg(p.vel + j);
+        const float Vj = __uint_as_float(r.w);
+        int dx = (int)(s.q.x - r.x), dy = (int)(s.q.y - r.y), dz = (int)(s.q.z - r.z);
+        Sep d = separation(dx, dy, dz);
+        float x[3] = {d.x, d.y, d.z};
+        float eta = d.r * s.inv_h;
+        float t = fmaxf(1.f - eta, 0.f);
+        float t2 = t * t, t4 = t2 * t2, t5 = t4 * t;
+        float W = s.cW * t5 * t * fmaf(eta, fmaf(eta, K35_3, 6.f), 1.f);
+        float G = s.cG * fmaf(5.f, eta, 1.f) * t5;       // grad W = G x
+        // eq:gRK with the i-side coefficients
+        float sB = fmaf(s.B[0], x[0], fmaf(s.B[1], x[1], fmaf(s.B[2], x[2], 1.f)));
+        float sW = sB * W, AW = s.A * W, AsG = s.A * sB * G;
+        float gR[3];
 #pragma unroll
-            for (int g = 0; g < 3; g++) {
-                float gBx = fmaf(s.gB[g], x[0], fmaf(s.gB[3 + g], x[1], s.gB[6 + g] * x[2]));
-                gR[g] = fmaf(s.gA[g], sW, fmaf(AW, gBx + s.B[g], AsG * x[g]));
-            }
-            float Vd[3] = {r.vv.w * (s.v[0] - r.vv.x), r.vv.w * (s.v[1] - r.vv.y), r.vv.w * (s.v[2] - r.vv.z)};
-#pragma unroll
-            for (int a = 0; a < 3; a++)
-#pragma unroll
-                for (int b = 0; b < 3; b++) s.acc[3 * a + b].add(-Vd[a] * gR[b]);
+        for (int g = 0; g < 3; g++) {
+            float gBx = fmaf(s.gB[g], x[0], fmaf(s.gB[3 + g], x[1], s.gB[6 + g] * x[2]));
+            gR[g] = fmaf(s.gA[g], sW, fmaf(AW, gBx + s.B[g], AsG * x[g]));
         }
+        float Vd[3] = {Vj * (s.v[0] - vj.x), Vj * (s.v[1] - vj.y), Vj * (s.v[2] - vj.z)};
+#pragma unroll
+        for (int a = 0; a < 3; a++)
+#pragma unroll
+            for (int b = 0; b < 3; b++) s.acc[3 * a + b].add(-Vd[a] * gR[b]);
     }
     __device__ static void finish(IState &s, int i, const Params &p) {
         GvRec g;
@@ -398,27 +332,26 @@ struct P3 {
         g.g2 = make_float4(s.acc[8].value(), 0.f, 0.f, 0.f);
         p.gv[i] = g;
     }
-    __device__ static int count(const IState &) { return 0; }
 };
 
 int run_corrections(crk_ctx *ctx, bool with_gradv, cudaStream_t s) {
     int rc;
     if (ctx->p.precision == 1) {
         typedef P2<true, true> K;
-        K::Params p{ctx->q4, ctx->hs, ctx->V, ctx->corr};
-        rc = launch_pass<K, 4>(ctx, PROF_P2, false, p, nullptr, s, "P2 corrections");
+        K::Params p{ctx->q4, ctx->qV, ctx->hs, ctx->corr};
+        rc = launch_lpass<K, 4>(ctx, PROF_P2, p, s, "P2 corrections");
     } else {
         typedef P2<false, false> K;
-        K::Params p{ctx->q4, ctx->hs, ctx->V, ctx->corr};
-        rc = launch_pass<K, 4>(ctx, PROF_P2, false, p, nullptr, s, "P2 corrections");
+        K::Params p{ctx->q4, ctx->qV, ctx->hs, ctx->corr};
+        rc = launch_lpass<K, 4>(ctx, PROF_P2, p, s, "P2 corrections");
     }
     if (rc || !with_gradv) return rc;
     if (ctx->p.precision == 1) {
-        P3<true>::Params p3{ctx->q4, ctx->hs, ctx->V, ctx->vel, ctx->corr, ctx->gv};
-        return launch_pass<P3<true>, 4>(ctx, PROF_P3, false, p3, nullptr, s, "P3 grad v");
+        P3<true>::Params p3{ctx->q4, ctx->qV, ctx->hs, ctx->vel, ctx->corr, ctx->gv};
+        return launch_lpass<P3<true>, 4>(ctx, PROF_P3, p3, s, "P3 grad v");
     }
-    P3<false>::Params p3{ctx->q4, ctx->hs, ctx->V, ctx->vel, ctx->corr, ctx->gv};
-    return launch_pass<P3<false>, 4>(ctx, PROF_P3, false, p3, nullptr, s, "P3 grad v");
+    P3<false>::Params p3{ctx->q4, ctx->qV, ctx->hs, ctx->vel, ctx->corr, ctx->gv};
+    return launch_lpass<P3<false>, 4>(ctx, PROF_P3, p3, s, "P3 grad v");
 }
 
 }  // namespace crk

@@ -91,6 +91,57 @@ struct Acc {
     __device__ __forceinline__ float value() const { return COMP ? s - c : s; }
 };
 
+// ---------------------------------------------------------------- list passes
+
+// Warp per tile, lane = particle i; lane i walks its own neighbour list (entry
+// k at base + 32 k + lane).  Gather passes walk the first cnt_g[i] entries,
+// pair-set passes all cnt_u[i].  P must provide Params, IState, GATHER,
+//   init(IState&, int i, bool valid, const Params&)
+//   pair(IState&, uint32_t entry, uint32_t pos, bool in_i, const Params&)
+//   finish(IState&, int i, const Params&)            (valid lanes only)
+struct ListGeom {
+    int n, ntiles;
+    const uint32_t *base;
+    const uint32_t *len_g, *len_u;
+    const int32_t *cnt_g, *cnt_u;
+    const uint32_t *ent;
+};
+
+template <class P, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32) k_lpass(ListGeom g, typename P::Params prm) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int tile = blockIdx.x * WARPS + w;
+    if (tile >= g.ntiles) return;
+    const int i = tile * TILE + lane;
+    const bool valid = i < g.n;
+    typename P::IState st;
+    P::init(st, i, valid, prm);
+    const uint32_t base = g.base[tile] + lane;
+    const int len = (int)(P::GATHER ? g.len_g[tile] : g.len_u[tile]);
+    const int mg = valid ? g.cnt_g[i] : 0;
+    const int my = P::GATHER ? mg : (valid ? g.cnt_u[i] : 0);
+    for (int k = 0; k < len; k++) {
+        if (k < my) {
+            const uint32_t pos = base + 32u * (uint32_t)k;
+            P::pair(st, __ldg(g.ent + pos), pos, k < mg, prm);
+        }
+    }
+    if (valid) P::finish(st, i, prm);
+}
+
+template <class P, int WARPS>
+int launch_lpass(crk_ctx *ctx, int prof_id, const typename P::Params &prm, cudaStream_t s, const char *what) {
+    if (ctx->n == 0) return CRK_OK;
+    if (!ctx->lists_valid) return crk_set_error(ctx, CRK_ESTATE, "%s: neighbour lists are not built", what);
+    ListGeom g{ctx->n, ctx->ntiles, ctx->tbase, ctx->len_g, ctx->len_u, ctx->cnt_g, ctx->cnt_u, ctx->ent};
+    prof_begin(ctx, prof_id, s);
+    k_lpass<P, WARPS><<<grid_for(ctx->ntiles, WARPS), WARPS * 32, 0, s>>>(g, prm);
+    ++ctx->launches;
+    prof_end(ctx, s);
+    CRK_LAUNCH_CHECK(ctx, what);
+    return CRK_OK;
+}
+
 // ---------------------------------------------------------------- kernel maths
 
 // C4 Wendland kernel (eq:C4) with eta = r/h and t = 1 - eta:

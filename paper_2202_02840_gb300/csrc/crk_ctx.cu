@@ -86,7 +86,6 @@ int crk_ensure_particles(crk_ctx *ctx, int n) {
     rc |= dalloc(ctx, &ctx->cnt_u, cap);
     rc |= dalloc(ctx, &ctx->len_g, tiles);
     rc |= dalloc(ctx, &ctx->len_u, tiles);
-    rc |= dalloc(ctx, &ctx->tcap, tiles);
     rc |= dalloc(ctx, &ctx->tbase, tiles);
     rc |= dalloc(ctx, &ctx->frec, 10 * (size_t)cap);
     rc |= dalloc(ctx, &ctx->sfun, cap);
@@ -110,19 +109,25 @@ int crk_ensure_particles(crk_ctx *ctx, int n) {
     return CRK_OK;
 }
 
-int crk_ensure_entries(crk_ctx *ctx, long long total) {
-    if (total > 0xffffffffll)
-        return crk_set_error(ctx, CRK_ECAPACITY, "neighbour lists beyond 2^32 entries");
-    if (total <= ctx->ent_cap && ctx->ent) return CRK_OK;
-    long long cap = total + total / 5 + 4096;
-    if (cap > 0xffffffffll) cap = 0xffffffffll;
-    int rc = dalloc(ctx, &ctx->ent, (size_t)cap);
-    rc |= dalloc(ctx, &ctx->Fst, (size_t)cap);
-    if (rc) {
-        ctx->ent_cap = 0;
-        return crk_set_error(ctx, CRK_ENOMEM, "cannot allocate %lld neighbour-list entries", cap);
+// List entries (fixed layout, n_ent) and stored forces (compact, n_force);
+// a negative size leaves that buffer as it is.
+int crk_ensure_entries(crk_ctx *ctx, long long n_ent, long long n_force) {
+    if (n_ent > ctx->ent_cap || !ctx->ent) {
+        long long cap = n_ent < 4096 ? 4096 : n_ent;
+        if (dalloc(ctx, &ctx->ent, (size_t)cap)) {
+            ctx->ent_cap = 0;
+            return crk_set_error(ctx, CRK_ENOMEM, "cannot allocate %lld neighbour-list entries", cap);
+        }
+        ctx->ent_cap = cap;
     }
-    ctx->ent_cap = cap;
+    if (n_force > ctx->f_cap || !ctx->Fst) {
+        long long cap = n_force + n_force / 5 + 4096;
+        if (dalloc(ctx, &ctx->Fst, (size_t)cap)) {
+            ctx->f_cap = 0;
+            return crk_set_error(ctx, CRK_ENOMEM, "cannot allocate %lld stored pair forces", cap);
+        }
+        ctx->f_cap = cap;
+    }
     return CRK_OK;
 }
 

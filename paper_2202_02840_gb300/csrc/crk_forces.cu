@@ -213,7 +213,7 @@ struct P4 {
         s.vsig = 0.f;
         s.qmax = 0.f;
     }
-    __device__ static void pair(IState &s, uint32_t e, uint32_t pos, bool in_i, const Params &p) {
+    __device__ static void pair(IState &s, uint32_t e, size_t pos, bool in_i, const Params &p) {
         const uint32_t j = e & 0x3fffffffu;
         const bool in_j = in_i ? (e >> 31) != 0u : true;
         const FRec r = ldg_frec(p.frec + j);
@@ -260,7 +260,7 @@ struct P5 {
         s.me = valid ? p.sig[i] : make_float4(0.f, 0.f, 0.f, 0.f);
         s.m = valid ? p.mass[i] : 1.f;
     }
-    __device__ static void pair(IState &s, uint32_t e, uint32_t pos, bool, const Params &p) {
+    __device__ static void pair(IState &s, uint32_t e, size_t pos, bool, const Params &p) {
         const float4 r = __ldg(p.sig + (e & 0x3fffffffu));
         const float4 F = __ldg(p.Fst + pos);
         // 2 Delta E_ij = (v_j + v'_j - v_i - v'_i) . F_ij  (reading of eq:Eij)

@@ -27,7 +27,8 @@ enum {
     CNT_WORK = 6,       // dynamic tile counter of the persistent pair kernels
     CNT_NOTDONE = 7,    // h iteration: particles not converged
     CNT_DTMIN = 8,      // min per-particle time step (float bits)
-    CNT_ENTRIES = 9,    // neighbour-list entries of the last list build
+    CNT_ENTRIES = 9,    // stored-force units (32 entries) of the last list build
+    CNT_MAXCNT = 10,    // largest pair-set count of the last walk
     CNT_COUNT = 16
 };
 
@@ -105,10 +106,12 @@ struct crk_ctx {
     uint4 *qV = nullptr;             // (qx, qy, qz, V bits)
     int32_t *cnt_g = nullptr, *cnt_u = nullptr;   // gather (j != i) and pair-set counts
     uint32_t *len_g = nullptr, *len_u = nullptr;  // per-tile max counts
-    uint32_t *tcap = nullptr, *tbase = nullptr;   // per-tile entry capacity / base
+    uint32_t *tcap = nullptr, *tbase = nullptr;   // per-tile stored-force base (units of 32)
     uint32_t *ent = nullptr;         // list entries: j | (j's kernel reaches i) << 31
-    float4 *Fst = nullptr;           // F_ij per entry (P4 -> P5)
-    long long ent_cap = 0, entries = 0;
+    float4 *Fst = nullptr;           // F_ij per entry (P4 -> P5), compact layout
+    long long ent_cap = 0, f_cap = 0, entries = 0;
+    int kcap = 384;                  // list columns per particle
+    int volumes_only = 0;            // walk without writing lists (no list buffer)
     int lists_valid = 0;
     float4 *frec = nullptr;          // packed pair-set records, 10 float4 per particle
     float *sfun = nullptr;           // specific entropy of the evaluation state
@@ -155,7 +158,7 @@ int crk_set_error(crk_ctx *ctx, int code, const char *fmt, ...);
 int crk_check_cuda(crk_ctx *ctx, cudaError_t e, const char *what);
 int crk_ensure_particles(crk_ctx *ctx, int n);
 int crk_ensure_lists(crk_ctx *ctx, long long ng, long long nu);
-int crk_ensure_entries(crk_ctx *ctx, long long total);
+int crk_ensure_entries(crk_ctx *ctx, long long n_ent, long long n_force);
 int crk_sync_counters(crk_ctx *ctx, cudaStream_t s);
 
 #define CRK_CUDA(ctx, call)                                                      \

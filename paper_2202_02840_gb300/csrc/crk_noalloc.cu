@@ -87,6 +87,7 @@ extern "C" int crk_volumes_noalloc(int n, const float *pos_h, float *V, float *N
     crk_ctx ctx;                      // host stack: no allocation anywhere
     crk_default_params(&ctx.p);
     ctx.p.kmax = 1;
+    ctx.volumes_only = 1;             // P1 only: the walk writes no neighbour lists
     ctx.err[0] = 0;
     ctx.device = dev;
     ctx.key_a = (uint32_t *)(b + LAY.key_a);

@@ -176,7 +176,7 @@ struct P2 {
         // self term of gather(i): x = 0, W(0) (unnormalised 1), grad W(0) = 0
         if (valid) s.m0.add(__uint_as_float(__ldg(&p.qV[i].w)));
     }
-    __device__ static void pair(IState &s, uint32_t e, uint32_t, bool, const Params &p) {
+    __device__ static void pair(IState &s, uint32_t e, size_t, bool, const Params &p) {
         const uint4 r = __ldg(p.qV + (e & 0x3fffffffu));
         int dx = (int)(s.q.x - r.x), dy = (int)(s.q.y - r.y), dz = (int)(s.q.z - r.z);
         const float Vj = __uint_as_float(r.w);
@@ -297,7 +297,7 @@ struct P3 {
 #pragma unroll
         for (int k = 0; k < 9; k++) s.acc[k] = Acc<COMP>();
     }
-    __device__ static void pair(IState &s, uint32_t e, uint32_t, bool, const Params &p) {
+    __device__ static void pair(IState &s, uint32_t e, size_t, bool, const Params &p) {
         const uint32_t j = e & 0x3fffffffu;
         const uint4 r = __ldg(p.qV + j);
         const float4 vj = __ldg(p.vel + j);

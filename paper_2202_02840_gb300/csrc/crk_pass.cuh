@@ -100,13 +100,15 @@ struct Acc {
 //   pair(IState&, uint32_t entry, uint32_t pos, bool in_i, const Params&)
 //   finish(IState&, int i, const Params&)            (valid lanes only)
 struct ListGeom {
-    int n, ntiles;
-    const uint32_t *base;
+    int n, ntiles, kcap;
+    const uint32_t *fbase;             // per-tile stored-force base, units of 32 entries
     const uint32_t *len_g, *len_u;
     const int32_t *cnt_g, *cnt_u;
     const uint32_t *ent;
 };
 
+// Entry k of a particle's list (gather neighbours k < cnt_g from the front
+// columns, the rest from the back columns) and its stored-force position.
 template <class P, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32) k_lpass(ListGeom g, typename P::Params prm) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -116,14 +118,15 @@ __global__ void __launch_bounds__(WARPS * 32) k_lpass(ListGeom g, typename P::Pa
     const bool valid = i < g.n;
     typename P::IState st;
     P::init(st, i, valid, prm);
-    const uint32_t base = g.base[tile] + lane;
+    const uint32_t *col0 = g.ent + (size_t)tile * g.kcap * 32 + lane;
+    const size_t fb = (size_t)g.fbase[tile] * 32 + lane;
     const int len = (int)(P::GATHER ? g.len_g[tile] : g.len_u[tile]);
     const int mg = valid ? g.cnt_g[i] : 0;
     const int my = P::GATHER ? mg : (valid ? g.cnt_u[i] : 0);
     for (int k = 0; k < len; k++) {
         if (k < my) {
-            const uint32_t pos = base + 32u * (uint32_t)k;
-            P::pair(st, __ldg(g.ent + pos), pos, k < mg, prm);
+            const int c = k < mg ? k : g.kcap - 1 - (k - mg);
+            P::pair(st, __ldg(col0 + (size_t)c * 32), fb + (size_t)k * 32, k < mg, prm);
         }
     }
     if (valid) P::finish(st, i, prm);
@@ -133,7 +136,8 @@ template <class P, int WARPS>
 int launch_lpass(crk_ctx *ctx, int prof_id, const typename P::Params &prm, cudaStream_t s, const char *what) {
     if (ctx->n == 0) return CRK_OK;
     if (!ctx->lists_valid) return crk_set_error(ctx, CRK_ESTATE, "%s: neighbour lists are not built", what);
-    ListGeom g{ctx->n, ctx->ntiles, ctx->tbase, ctx->len_g, ctx->len_u, ctx->cnt_g, ctx->cnt_u, ctx->ent};
+    ListGeom g{ctx->n, ctx->ntiles, ctx->kcap, ctx->tbase, ctx->len_g, ctx->len_u, ctx->cnt_g, ctx->cnt_u,
+               ctx->ent};
     prof_begin(ctx, prof_id, s);
     k_lpass<P, WARPS><<<grid_for(ctx->ntiles, WARPS), WARPS * 32, 0, s>>>(g, prm);
     ++ctx->launches;

@@ -1,17 +1,18 @@
 // crk_walk.cu -- per-particle neighbour lists, built once per evaluation from
 // the tile interaction lists (CRK-HACC Sec. 2.3: interaction lists assembled
 // once per hydro step and reused by every hydro kernel), with P1 volumes
-// (Sec. 1.2 eq:vol, Sec. 2.6 eq:hi) fused into the counting walk.
+// (Sec. 1.2 eq:vol, Sec. 2.6 eq:hi) fused into the same walk.
 //
-// Walk 1 (count): warp per i-tile over the pair-set tile list; every staged
-// neighbour is tested with the exact fixed-point predicate.  Lane i counts its
-// gather neighbours (j != i, |dq|^2 < H_i^2) and its pair-set neighbours, and
-// sums W(r, h_i) over gather(i) (self included) for n_i.
-// Scan: tile capacities 32 * max_lane(pair-set count) -> tile base offsets.
-// Walk 2 (fill): the same walk writes lane i's entries into the tile's column
-// layout, entry k at base + 32 k + lane: first the gather neighbours (bit 31 =
-// j's own kernel also reaches i), then the pair-set neighbours outside
-// gather(i) (whose kernel always reaches i).  Both sections ascend in j.
+// One walk: warp per i-tile over the pair-set tile list; every staged
+// neighbour is tested once with the exact fixed-point predicate.  Lane i sums
+// W(r, h_i) over gather(i) (self included) for n_i and writes its list into
+// the tile's column layout with KCAP columns (entry column c of lane i at
+// (tile * KCAP + c) * 32 + i): gather neighbours (j != i, |dq|^2 < H_i^2) from
+// column 0 upwards with bit 31 = "j's kernel also reaches i", the other
+// pair-set neighbours from column KCAP - 1 downwards.  A particle with more
+// than KCAP neighbours sets the overflow maximum; the host then grows KCAP and
+// walks again.  Stored pair forces use a compact layout: per-tile base (in
+// units of 32 entries) from a scan of the per-tile maximum count.
 #include "crk_pass.cuh"
 
 namespace crk {
@@ -19,23 +20,19 @@ namespace crk {
 constexpr int WALK_WARPS = 8;
 
 struct WalkArgs {
-    int n, ntiles;
+    int n, ntiles, kcap;
     const uint4 *q4;
     const float *hs;
     const uint2 *ofs;        // pair-set tile list per tile
     const uint32_t *tiles;
-    // count outputs
     float *V, *Nn;
     uint4 *qV;               // (qx, qy, qz, V bits)
     int32_t *cnt_g, *cnt_u;
     uint32_t *len_g, *len_u; // per-tile max counts
-    unsigned long long *pairs_g, *pairs_u;
-    // fill
-    const uint32_t *base;    // per-tile base offset (entries)
+    unsigned long long *pairs_g, *pairs_u, *maxcnt;
     uint32_t *ent;
 };
 
-template <bool FILL>
 __global__ void __launch_bounds__(WALK_WARPS * 32) k_walk(WalkArgs a) {
     __shared__ uint4 sq[WALK_WARPS][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -47,13 +44,10 @@ __global__ void __launch_bounds__(WALK_WARPS * 32) k_walk(WalkArgs a) {
     const unsigned long long Hi2 = (unsigned long long)qi.w * qi.w;   // 0 for invalid lanes
     const float h = valid ? a.hs[i] : 1.f;
     const float inv_h = 1.f / h;
+    const int kcap = a.kcap;
+    uint32_t *const col0 = a.ent ? a.ent + (size_t)tile * kcap * 32 + lane : nullptr;
     float acc = 0.f;
-    int cg = 0, cu = 0;
-    uint32_t kg = 0, ko = 0, tb = 0;
-    if (FILL) {
-        tb = a.base[tile];
-        ko = valid ? (uint32_t)a.cnt_g[i] : 0u;
-    }
+    int cg = 0, co = 0;
     const uint2 lo = a.ofs[tile];
     for (uint32_t t = 0; t < lo.y; t++) {
         const int J = (int)a.tiles[lo.x + t];
@@ -67,72 +61,61 @@ __global__ void __launch_bounds__(WALK_WARPS * 32) k_walk(WalkArgs a) {
             const int dx = (int)(qi.x - qj.x), dy = (int)(qi.y - qj.y), dz = (int)(qi.z - qj.z);
             const unsigned long long R2 = r2_fixed(dx, dy, dz);
             const bool in_i = R2 < Hi2;
-            const bool in_j = valid && R2 < (unsigned long long)qj.w * qj.w;
-            const bool self = (j0 + jj) == i;
-            if (!FILL) {
+            if (in_i) {
+                Sep d = separation(dx, dy, dz);
+                float eta = d.r * inv_h;
+                float tt = fmaxf(1.f - eta, 0.f);
+                float t2 = tt * tt, t3 = t2 * tt;
+                acc = fmaf(t3 * t3, fmaf(eta, fmaf(eta, K35_3, 6.f), 1.f), acc);
+            }
+            const uint32_t j = (uint32_t)(j0 + jj);
+            if (a.ent && valid && (int)j != i) {
+                const bool in_j = R2 < (unsigned long long)qj.w * qj.w;
                 if (in_i) {
-                    Sep d = separation(dx, dy, dz);
-                    float eta = d.r * inv_h;
-                    float tt = fmaxf(1.f - eta, 0.f);
-                    float t2 = tt * tt, t3 = t2 * tt;
-                    acc = fmaf(t3 * t3, fmaf(eta, fmaf(eta, K35_3, 6.f), 1.f), acc);
-                }
-                if (!self) {
-                    cg += in_i;
-                    cu += (in_i || in_j);
-                }
-            } else if (!self) {
-                const uint32_t j = (uint32_t)(j0 + jj);
-                if (in_i) {
-                    a.ent[tb + kg * 32u + lane] = j | (in_j ? 0x80000000u : 0u);
-                    kg++;
+                    if (cg < kcap) col0[(size_t)cg * 32] = j | (in_j ? 0x80000000u : 0u);
+                    cg++;
                 } else if (in_j) {
-                    a.ent[tb + ko * 32u + lane] = j;
-                    ko++;
+                    if (co < kcap) col0[(size_t)(kcap - 1 - co) * 32] = j;
+                    co++;
                 }
             }
         }
     }
-    if (!FILL) {
-        if (valid) {
-            float ih3 = inv_h * inv_h * inv_h;
-            float nsum = KW * ih3 * acc;                       // n_i, eq:vol
-            float V = 1.f / nsum;
-            a.V[i] = V;
-            if (a.Nn) a.Nn[i] = (4.18879020f * h * h * h) * nsum;   // eq:hi
-            a.qV[i] = make_uint4(qi.x, qi.y, qi.z, __float_as_uint(V));
-            a.cnt_g[i] = cg;
-            a.cnt_u[i] = cu;
-        }
-        uint32_t mg = __reduce_max_sync(0xffffffffu, (uint32_t)cg);
-        uint32_t mu = __reduce_max_sync(0xffffffffu, (uint32_t)cu);
-        uint32_t sg = __reduce_add_sync(0xffffffffu, (uint32_t)cg);
-        uint32_t su = __reduce_add_sync(0xffffffffu, (uint32_t)cu);
-        if (lane == 0) {
-            a.len_g[tile] = mg;
-            a.len_u[tile] = mu;
-            atomicAdd(a.pairs_g, (unsigned long long)sg);
-            atomicAdd(a.pairs_u, (unsigned long long)su);
-        }
+    const int cu = cg + co;
+    if (valid) {
+        float ih3 = inv_h * inv_h * inv_h;
+        float nsum = KW * ih3 * acc;                       // n_i, eq:vol
+        float V = 1.f / nsum;
+        a.V[i] = V;
+        if (a.Nn) a.Nn[i] = (4.18879020f * h * h * h) * nsum;   // eq:hi
+        a.qV[i] = make_uint4(qi.x, qi.y, qi.z, __float_as_uint(V));
+        a.cnt_g[i] = cg;
+        a.cnt_u[i] = cu;
+    }
+    uint32_t mg = __reduce_max_sync(0xffffffffu, (uint32_t)cg);
+    uint32_t mu = __reduce_max_sync(0xffffffffu, (uint32_t)cu);
+    uint32_t sg = __reduce_add_sync(0xffffffffu, (uint32_t)cg);
+    uint32_t su = __reduce_add_sync(0xffffffffu, (uint32_t)cu);
+    if (lane == 0) {
+        a.len_g[tile] = mg;
+        a.len_u[tile] = mu;
+        atomicAdd(a.pairs_g, (unsigned long long)sg);
+        atomicAdd(a.pairs_u, (unsigned long long)su);
+        atomicMax(a.maxcnt, (unsigned long long)mu);
     }
 }
 
-// tile capacity 32 * max pair-set count; exclusive scan done by the caller
-__global__ void k_tile_cap(int ntiles, const uint32_t *__restrict__ len_u, uint32_t *__restrict__ cap) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < ntiles) cap[t] = 32u * len_u[t];
-}
-
-// total entries = base[last] + cap[last]
-__global__ void k_total(int ntiles, const uint32_t *__restrict__ base, const uint32_t *__restrict__ cap,
+// total stored-force units (32 entries each) = base[last] + len_u[last]
+__global__ void k_total(int ntiles, const uint32_t *__restrict__ base, const uint32_t *__restrict__ len,
                         unsigned long long *out) {
-    *out = ntiles ? (unsigned long long)base[ntiles - 1] + cap[ntiles - 1] : 0ull;
+    *out = ntiles ? (unsigned long long)base[ntiles - 1] + len[ntiles - 1] : 0ull;
 }
 
 static WalkArgs walk_args(crk_ctx *ctx) {
     WalkArgs a;
     a.n = ctx->n;
     a.ntiles = ctx->ntiles;
+    a.kcap = ctx->kcap;
     a.q4 = ctx->q4;
     a.hs = ctx->hs;
     a.ofs = ctx->uofs;
@@ -146,53 +129,62 @@ static WalkArgs walk_args(crk_ctx *ctx) {
     a.len_u = ctx->len_u;
     a.pairs_g = ctx->counters + CNT_PAIRS_G;
     a.pairs_u = ctx->counters + CNT_PAIRS_U;
-    a.base = ctx->tbase;
-    a.ent = ctx->ent;
+    a.maxcnt = ctx->counters + CNT_MAXCNT;
+    a.ent = ctx->volumes_only ? nullptr : ctx->ent;
     return a;
 }
 
-// Walk 1: counts and P1 volumes.
+// The walk: P1 volumes and the neighbour lists (valid once run_lists checked them).
 int run_volumes(crk_ctx *ctx, cudaStream_t s) {
+    ctx->lists_valid = 0;
     if (ctx->n == 0) return CRK_OK;
+    if (!ctx->volumes_only) {
+        int rc = crk_ensure_entries(ctx, (long long)ctx->ntiles * 32 * ctx->kcap, -1);
+        if (rc) return rc;
+    }
     CRK_CUDA(ctx, cudaMemsetAsync(ctx->counters + CNT_PAIRS_G, 0, 2 * sizeof(unsigned long long), s));
+    CRK_CUDA(ctx, cudaMemsetAsync(ctx->counters + CNT_MAXCNT, 0, sizeof(unsigned long long), s));
     prof_begin(ctx, PROF_P1, s);
-    k_walk<false><<<grid_for(ctx->ntiles, WALK_WARPS), WALK_WARPS * 32, 0, s>>>(walk_args(ctx));
+    k_walk<<<grid_for(ctx->ntiles, WALK_WARPS), WALK_WARPS * 32, 0, s>>>(walk_args(ctx));
     ++ctx->launches;
     prof_end(ctx, s);
-    CRK_LAUNCH_CHECK(ctx, "P1 volumes (walk 1)");
-    ctx->lists_valid = 0;
+    CRK_LAUNCH_CHECK(ctx, "P1 volumes and neighbour lists (walk)");
     return CRK_OK;
 }
 
-// Scan and walk 2: per-particle lists for the passes after P1.  Synchronises
-// once to size the entry buffer.
+// Check the walk's lists (synchronises once): on overflow grow KCAP and walk
+// again; then lay out the stored pair forces.
 int run_lists(crk_ctx *ctx, cudaStream_t s) {
+    if (ctx->volumes_only) return crk_set_error(ctx, CRK_ESTATE, "no neighbour lists in this context");
     if (ctx->n == 0) {
         ctx->lists_valid = 1;
         return CRK_OK;
     }
     int nt = ctx->ntiles;
-    prof_begin(ctx, PROF_LISTS, s);
-    k_tile_cap<<<grid_for(nt, 256), 256, 0, s>>>(nt, ctx->len_u, ctx->tcap);
-    ++ctx->launches;
-    CRK_LAUNCH_CHECK(ctx, "tile capacities");
-    int rc = scan_u32(ctx, ctx->tcap, ctx->tbase, nt, s);
-    if (rc) return rc;
-    k_total<<<1, 1, 0, s>>>(nt, ctx->tbase, ctx->tcap, ctx->counters + CNT_ENTRIES);
-    ++ctx->launches;
-    CRK_LAUNCH_CHECK(ctx, "entry total");
-    rc = crk_sync_counters(ctx, s);
-    if (rc) return rc;
-    long long total = (long long)ctx->h_counters[CNT_ENTRIES];
-    rc = crk_ensure_entries(ctx, total);
-    if (rc) return rc;
-    k_walk<true><<<grid_for(nt, WALK_WARPS), WALK_WARPS * 32, 0, s>>>(walk_args(ctx));
-    ++ctx->launches;
-    prof_end(ctx, s);
-    CRK_LAUNCH_CHECK(ctx, "neighbour lists (walk 2)");
-    ctx->entries = total;
-    ctx->lists_valid = 1;
-    return CRK_OK;
+    for (int attempt = 0; attempt < 3; attempt++) {
+        prof_begin(ctx, PROF_LISTS, s);
+        int rc = scan_u32(ctx, ctx->len_u, ctx->tbase, nt, s);
+        if (rc) return rc;
+        k_total<<<1, 1, 0, s>>>(nt, ctx->tbase, ctx->len_u, ctx->counters + CNT_ENTRIES);
+        ++ctx->launches;
+        prof_end(ctx, s);
+        CRK_LAUNCH_CHECK(ctx, "list layout");
+        rc = crk_sync_counters(ctx, s);
+        if (rc) return rc;
+        long long maxc = (long long)ctx->h_counters[CNT_MAXCNT];
+        if (maxc <= ctx->kcap) {
+            long long units = (long long)ctx->h_counters[CNT_ENTRIES];
+            rc = crk_ensure_entries(ctx, -1, units * 32);
+            if (rc) return rc;
+            ctx->entries = units * 32;
+            ctx->lists_valid = 1;
+            return CRK_OK;
+        }
+        ctx->kcap = (int)((maxc + maxc / 4 + 31) / 32 * 32);
+        rc = run_volumes(ctx, s);
+        if (rc) return rc;
+    }
+    return crk_set_error(ctx, CRK_ECAPACITY, "neighbour lists keep overflowing");
 }
 
 }  // namespace crk

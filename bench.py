@@ -306,7 +306,7 @@ def run_gpu(args):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "n": n, "precision": "mixed" if args.precision else "plain",
+                "config": {"workload": WORKLOAD, "n": n, "precision": ["plain", "mixed", "mixed+compensated moments"][args.precision],
                            "parallelism": "replicas" if world > 1 else "single",
                            "l2": "step working set ~%.1f GB > L2 (129 MB)" % (n * 460 / 1e9),
                            "pairs_per_step": pairs / args.steps,
@@ -338,7 +338,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n-side", type=int, default=128)
-    ap.add_argument("--precision", type=int, default=1, choices=[0, 1])
+    ap.add_argument("--precision", type=int, default=1, choices=[0, 1, 2])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     args = ap.parse_args()

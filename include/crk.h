@@ -78,8 +78,10 @@ typedef struct {
     double h_max;     /* upper clamp of the evolved h (< 1/3) */
     double dt_max;    /* cap of the CFL time step */
     int precision;    /* 0 = plain FP32 (FP32 sums, FP32 3x3 inverse);
-                         1 = mixed (FP32 pair sums with compensated momentum and
-                             energy accumulation, FP64 3x3 inverse) */
+                         1 = mixed (default): FP32 pair sums, compensated momentum
+                             and energy accumulation, moments formed and the 3x3
+                             system solved in FP64;
+                         2 = mixed with compensated moment and grad-v sums too */
     int kmax;         /* finest chaining-mesh level reported by crk_cells (<= 7) */
     int reserved[6];
 } crk_params;

@@ -380,7 +380,7 @@ extern "C" int crk_create(const crk_params *p, crk_ctx **out) {
     if (p) prm = *p; else crk_default_params(&prm);
     if (!(prm.gamma > 1.0) || !(prm.n_h > 0) || !(prm.N_res > 0) || !(prm.eta_fold > 0) ||
         !(prm.h_max > 0 && prm.h_max < 1.0 / 3.0) || !(prm.h_min > 0 && prm.h_min < prm.h_max) ||
-        prm.kmax < 1 || prm.kmax > 7 || (prm.precision != 0 && prm.precision != 1) || !(prm.dt_max > 0))
+        prm.kmax < 1 || prm.kmax > 7 || prm.precision < 0 || prm.precision > 2 || !(prm.dt_max > 0))
         return CRK_EINVAL;
     crk_ctx *ctx = new (std::nothrow) crk_ctx();
     if (!ctx) return CRK_ENOMEM;
@@ -452,12 +452,7 @@ static int need_built(crk_ctx *ctx) {
 }
 
 // neighbour lists of the current build (walk 1 + walk 2), built on first need
-static int need_lists(crk_ctx *ctx, cudaStream_t s) {
-    if (ctx->lists_valid) return CRK_OK;
-    int rc = run_volumes(ctx, s);
-    if (!rc) rc = run_lists(ctx, s);
-    return rc;
-}
+static int need_lists(crk_ctx *ctx, cudaStream_t s) { return run_lists(ctx, s); }
 
 extern "C" int crk_build_cells(crk_ctx *ctx, int n, const float *pos_h, void *stream) {
     if (!ctx) return CRK_EINVAL;

@@ -308,7 +308,7 @@ int run_forces(crk_ctx *ctx, cudaStream_t s) {
     ++ctx->launches;
     CRK_LAUNCH_CHECK(ctx, "pack pair records");
     const FRec *fr = reinterpret_cast<const FRec *>(ctx->frec);
-    if (ctx->p.precision == 1) {
+    if (ctx->p.precision >= 1) {
         typename P4<true>::Params p{fr, ctx->mass, fp, ctx->acc, ctx->vq, ctx->Fst};
         return launch_lpass<P4<true>, 4>(ctx, PROF_P4, p, s, "P4 forces");
     }
@@ -322,7 +322,7 @@ int run_compatible(crk_ctx *ctx, cudaStream_t s) {
     k_sig<<<grid_for(ctx->n, 256), 256, 0, s>>>(ctx->n, ctx->vb, ctx->va, ctx->sfun, ctx->sig);
     ++ctx->launches;
     CRK_LAUNCH_CHECK(ctx, "kick sums");
-    if (ctx->p.precision == 1) {
+    if (ctx->p.precision >= 1) {
         typename P5<true>::Params p{ctx->sig, ctx->Fst, ctx->mass, ctx->du};
         return launch_lpass<P5<true>, 8>(ctx, PROF_P5, p, s, "P5 compatible energy");
     }

@@ -336,8 +336,12 @@ struct P3 {
 
 int run_corrections(crk_ctx *ctx, bool with_gradv, cudaStream_t s) {
     int rc;
-    if (ctx->p.precision == 1) {
+    if (ctx->p.precision == 2) {
         typedef P2<true, true> K;
+        K::Params p{ctx->q4, ctx->qV, ctx->hs, ctx->corr};
+        rc = launch_lpass<K, 4>(ctx, PROF_P2, p, s, "P2 corrections");
+    } else if (ctx->p.precision == 1) {
+        typedef P2<true, false> K;
         K::Params p{ctx->q4, ctx->qV, ctx->hs, ctx->corr};
         rc = launch_lpass<K, 4>(ctx, PROF_P2, p, s, "P2 corrections");
     } else {
@@ -346,7 +350,7 @@ int run_corrections(crk_ctx *ctx, bool with_gradv, cudaStream_t s) {
         rc = launch_lpass<K, 4>(ctx, PROF_P2, p, s, "P2 corrections");
     }
     if (rc || !with_gradv) return rc;
-    if (ctx->p.precision == 1) {
+    if (ctx->p.precision == 2) {
         P3<true>::Params p3{ctx->q4, ctx->qV, ctx->hs, ctx->vel, ctx->corr, ctx->gv};
         return launch_lpass<P3<true>, 4>(ctx, PROF_P3, p3, s, "P3 grad v");
     }

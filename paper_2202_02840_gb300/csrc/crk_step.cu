@@ -220,7 +220,6 @@ __global__ void k_write_h(int n, const int32_t *__restrict__ perm, const float *
 // P1 -> P2 -> P3 -> P4 at the current build, with ctx->vel / ctx->mass set.
 static int evaluate(crk_ctx *ctx, cudaStream_t s) {
     int rc = run_volumes(ctx, s);
-    if (!rc) rc = run_lists(ctx, s);
     if (!rc) rc = run_corrections(ctx, true, s);
     if (!rc) rc = run_forces(ctx, s);
     if (rc) return rc;

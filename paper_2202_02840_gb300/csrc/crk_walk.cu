@@ -1,11 +1,11 @@
 // crk_walk.cu -- per-particle neighbour lists, built once per evaluation from
 // the tile interaction lists (CRK-HACC Sec. 2.3: interaction lists assembled
-// once per hydro step and reused by every hydro kernel), with P1 volumes
-// (Sec. 1.2 eq:vol, Sec. 2.6 eq:hi) fused into the same walk.
+// once per hydro step and reused by every hydro kernel), and P1 volumes
+// (Sec. 1.2 eq:vol, Sec. 2.6 eq:hi) over those lists.
 //
 // One walk: warp per i-tile over the pair-set tile list; every staged
-// neighbour is tested once with the exact fixed-point predicate.  Lane i sums
-// W(r, h_i) over gather(i) (self included) for n_i and writes its list into
+// neighbour is tested once with the exact fixed-point predicate (integer work
+// only).  Lane i writes its list into
 // the tile's column layout with KCAP columns (entry column c of lane i at
 // (tile * KCAP + c) * 32 + i): gather neighbours (j != i, |dq|^2 < H_i^2) from
 // column 0 upwards with bit 31 = "j's kernel also reaches i", the other
@@ -33,6 +33,8 @@ struct WalkArgs {
     uint32_t *ent;
 };
 
+// LISTS: write the lists; VOL: sum n_i in the walk (volumes-only contexts).
+template <bool LISTS, bool VOL>
 __global__ void __launch_bounds__(WALK_WARPS * 32) k_walk(WalkArgs a) {
     __shared__ uint4 sq[WALK_WARPS][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -45,7 +47,7 @@ __global__ void __launch_bounds__(WALK_WARPS * 32) k_walk(WalkArgs a) {
     const float h = valid ? a.hs[i] : 1.f;
     const float inv_h = 1.f / h;
     const int kcap = a.kcap;
-    uint32_t *const col0 = a.ent ? a.ent + (size_t)tile * kcap * 32 + lane : nullptr;
+    uint32_t *const col0 = LISTS ? a.ent + (size_t)tile * kcap * 32 + lane : nullptr;
     float acc = 0.f;
     int cg = 0, co = 0;
     const uint2 lo = a.ofs[tile];
@@ -56,12 +58,13 @@ __global__ void __launch_bounds__(WALK_WARPS * 32) k_walk(WalkArgs a) {
         __syncwarp();
         if (lane < cnt) sq[w][lane] = a.q4[j0 + lane];
         __syncwarp();
+#pragma unroll 4
         for (int jj = 0; jj < cnt; jj++) {
             const uint4 qj = sq[w][jj];
             const int dx = (int)(qi.x - qj.x), dy = (int)(qi.y - qj.y), dz = (int)(qi.z - qj.z);
             const unsigned long long R2 = r2_fixed(dx, dy, dz);
             const bool in_i = R2 < Hi2;
-            if (in_i) {
+            if (VOL && in_i) {
                 Sep d = separation(dx, dy, dz);
                 float eta = d.r * inv_h;
                 float tt = fmaxf(1.f - eta, 0.f);
@@ -69,7 +72,7 @@ __global__ void __launch_bounds__(WALK_WARPS * 32) k_walk(WalkArgs a) {
                 acc = fmaf(t3 * t3, fmaf(eta, fmaf(eta, K35_3, 6.f), 1.f), acc);
             }
             const uint32_t j = (uint32_t)(j0 + jj);
-            if (a.ent && valid && (int)j != i) {
+            if (LISTS && valid && (int)j != i) {
                 const bool in_j = R2 < (unsigned long long)qj.w * qj.w;
                 if (in_i) {
                     if (cg < kcap) col0[(size_t)cg * 32] = j | (in_j ? 0x80000000u : 0u);
@@ -83,12 +86,12 @@ __global__ void __launch_bounds__(WALK_WARPS * 32) k_walk(WalkArgs a) {
     }
     const int cu = cg + co;
     if (valid) {
-        float ih3 = inv_h * inv_h * inv_h;
-        float nsum = KW * ih3 * acc;                       // n_i, eq:vol
-        float V = 1.f / nsum;
-        a.V[i] = V;
-        if (a.Nn) a.Nn[i] = (4.18879020f * h * h * h) * nsum;   // eq:hi
-        a.qV[i] = make_uint4(qi.x, qi.y, qi.z, __float_as_uint(V));
+        if (VOL) {
+            float ih3 = inv_h * inv_h * inv_h;
+            float nsum = KW * ih3 * acc;                       // n_i, eq:vol
+            a.V[i] = 1.f / nsum;
+            if (a.Nn) a.Nn[i] = (4.18879020f * h * h * h) * nsum;   // eq:hi
+        }
         a.cnt_g[i] = cg;
         a.cnt_u[i] = cu;
     }
@@ -134,27 +137,28 @@ static WalkArgs walk_args(crk_ctx *ctx) {
     return a;
 }
 
-// The walk: P1 volumes and the neighbour lists (valid once run_lists checked them).
-int run_volumes(crk_ctx *ctx, cudaStream_t s) {
-    ctx->lists_valid = 0;
-    if (ctx->n == 0) return CRK_OK;
+static int launch_walk(crk_ctx *ctx, cudaStream_t s) {
     if (!ctx->volumes_only) {
         int rc = crk_ensure_entries(ctx, (long long)ctx->ntiles * 32 * ctx->kcap, -1);
         if (rc) return rc;
     }
     CRK_CUDA(ctx, cudaMemsetAsync(ctx->counters + CNT_PAIRS_G, 0, 2 * sizeof(unsigned long long), s));
     CRK_CUDA(ctx, cudaMemsetAsync(ctx->counters + CNT_MAXCNT, 0, sizeof(unsigned long long), s));
-    prof_begin(ctx, PROF_P1, s);
-    k_walk<<<grid_for(ctx->ntiles, WALK_WARPS), WALK_WARPS * 32, 0, s>>>(walk_args(ctx));
+    prof_begin(ctx, PROF_LISTS, s);
+    if (ctx->volumes_only)
+        k_walk<false, true><<<grid_for(ctx->ntiles, WALK_WARPS), WALK_WARPS * 32, 0, s>>>(walk_args(ctx));
+    else
+        k_walk<true, false><<<grid_for(ctx->ntiles, WALK_WARPS), WALK_WARPS * 32, 0, s>>>(walk_args(ctx));
     ++ctx->launches;
     prof_end(ctx, s);
-    CRK_LAUNCH_CHECK(ctx, "P1 volumes and neighbour lists (walk)");
+    CRK_LAUNCH_CHECK(ctx, "neighbour walk");
     return CRK_OK;
 }
 
-// Check the walk's lists (synchronises once): on overflow grow KCAP and walk
-// again; then lay out the stored pair forces.
+// The walk and the list layout (synchronises once): on overflow grow KCAP and
+// walk again; then lay out the stored pair forces.
 int run_lists(crk_ctx *ctx, cudaStream_t s) {
+    if (ctx->lists_valid) return CRK_OK;
     if (ctx->volumes_only) return crk_set_error(ctx, CRK_ESTATE, "no neighbour lists in this context");
     if (ctx->n == 0) {
         ctx->lists_valid = 1;
@@ -162,12 +166,12 @@ int run_lists(crk_ctx *ctx, cudaStream_t s) {
     }
     int nt = ctx->ntiles;
     for (int attempt = 0; attempt < 3; attempt++) {
-        prof_begin(ctx, PROF_LISTS, s);
-        int rc = scan_u32(ctx, ctx->len_u, ctx->tbase, nt, s);
+        int rc = launch_walk(ctx, s);
+        if (rc) return rc;
+        rc = scan_u32(ctx, ctx->len_u, ctx->tbase, nt, s);
         if (rc) return rc;
         k_total<<<1, 1, 0, s>>>(nt, ctx->tbase, ctx->len_u, ctx->counters + CNT_ENTRIES);
         ++ctx->launches;
-        prof_end(ctx, s);
         CRK_LAUNCH_CHECK(ctx, "list layout");
         rc = crk_sync_counters(ctx, s);
         if (rc) return rc;
@@ -181,10 +185,60 @@ int run_lists(crk_ctx *ctx, cudaStream_t s) {
             return CRK_OK;
         }
         ctx->kcap = (int)((maxc + maxc / 4 + 31) / 32 * 32);
-        rc = run_volumes(ctx, s);
-        if (rc) return rc;
     }
     return crk_set_error(ctx, CRK_ECAPACITY, "neighbour lists keep overflowing");
+}
+
+// P1 volumes over the gather lists (eq:vol, eq:hi), self included.
+struct P1 {
+    static constexpr bool GATHER = true;
+    struct Params {
+        const uint4 *q4;
+        const float *hs;
+        float *V, *Nn;
+        uint4 *qV;
+    };
+    struct IState {
+        uint4 q;
+        float h, inv_h, acc;
+    };
+    __device__ static void init(IState &s, int i, bool valid, const Params &p) {
+        s.q = valid ? p.q4[i] : make_uint4(0, 0, 0, 0);
+        s.h = valid ? p.hs[i] : 1.f;
+        s.inv_h = 1.f / s.h;
+        s.acc = 1.f;                                   // self: W(0) / (495/(32 pi h^3)) = 1
+    }
+    __device__ static void pair(IState &s, uint32_t e, size_t, bool, const Params &p) {
+        const uint4 r = __ldg(p.q4 + (e & 0x3fffffffu));
+        int dx = (int)(s.q.x - r.x), dy = (int)(s.q.y - r.y), dz = (int)(s.q.z - r.z);
+        Sep d = separation(dx, dy, dz);
+        float eta = d.r * s.inv_h;
+        float t = fmaxf(1.f - eta, 0.f);
+        float t2 = t * t, t3 = t2 * t;
+        s.acc = fmaf(t3 * t3, fmaf(eta, fmaf(eta, K35_3, 6.f), 1.f), s.acc);
+    }
+    __device__ static void finish(IState &s, int i, const Params &p) {
+        float ih3 = s.inv_h * s.inv_h * s.inv_h;
+        float nsum = KW * ih3 * s.acc;                       // n_i, eq:vol
+        float V = 1.f / nsum;
+        p.V[i] = V;
+        if (p.Nn) p.Nn[i] = (4.18879020f * s.h * s.h * s.h) * nsum;   // eq:hi
+        p.qV[i] = make_uint4(s.q.x, s.q.y, s.q.z, __float_as_uint(V));
+    }
+};
+
+// P1 volumes: the walk (if the lists are stale) and the list pass; a
+// volumes-only context sums n_i inside the walk instead.
+int run_volumes(crk_ctx *ctx, cudaStream_t s) {
+    if (ctx->n == 0) return CRK_OK;
+    if (ctx->volumes_only) {
+        ctx->lists_valid = 0;
+        return launch_walk(ctx, s);
+    }
+    int rc = run_lists(ctx, s);
+    if (rc) return rc;
+    P1::Params p{ctx->q4, ctx->hs, ctx->V, ctx->Nn, ctx->qV};
+    return launch_lpass<P1, 8>(ctx, PROF_P1, p, s, "P1 volumes");
 }
 
 }  // namespace crk

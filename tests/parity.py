@@ -14,10 +14,11 @@ TOL = 1e-5
 # sums (odd moments, grad m1 = delta m0 + sum V x grad W) cost it ~1e-4 on
 # lattice-like inputs.
 TOL_PLAIN = 2e-3
-# RMS-relative bar for the RK coefficients B, grad A, grad B of the mixed path:
-# their sums cancel to ~1e-4 of the terms on lattice-like inputs and FP32 pair
-# terms then leave ~1e-5..1e-4 of the field RMS (measured 1.1e-5 .. 1.2e-4).
-RMS_TOL = 3e-4
+# RMS-relative bars for the RK coefficients B, grad A, grad B: their sums
+# cancel to ~1e-4 of the terms on lattice-like inputs, so FP32 pair terms leave
+# ~1e-5..1e-4 of the field RMS with compensated moment sums (precision 2,
+# measured up to 1.2e-4) and ~3x that with plain FP32 moment sums (precision 1).
+RMS_TOL = {1: 1e-3, 2: 3e-4}
 
 
 def as_np(t, shape=None):

@@ -270,53 +270,86 @@ __device__ __forceinline__ unsigned long long box_gap2(uint4 alo, uint4 ahi, uin
     return gx * gx + gy * gy + gz * gz;
 }
 
-struct TreeDesc {
-    int off[MAX_LEVELS];
-    int cnt[MAX_LEVELS];
-    int top;
+// 32-ary view of the binary tile tree: 32-ary level L is binary level 5 L, and
+// the children of node k are nodes 32 k .. 32 k + 31 one 32-ary level down.
+constexpr int MAX_L32 = 8;
+constexpr int LIST_WARPS = 4;
+constexpr int STACK = 256;
+
+struct Tree32 {
+    int off[MAX_L32];
+    int cnt[MAX_L32];
+    int top;          // highest 32-ary level (at most 32 nodes)
 };
 
-// Walk the tree for tile I; emit (or count) every tile J whose box is closer
-// than the reach R: gather: R = Hmax_I; union: R = max(Hmax_I, Hmax_J).
-template <bool UNION, bool WRITE>
-__device__ int walk(const TreeDesc &T, const uint4 *__restrict__ lo, const uint4 *__restrict__ hi,
-                    uint4 Ilo, uint4 Ihi, uint32_t *__restrict__ out) {
-    int stL[2 * MAX_LEVELS], stK[2 * MAX_LEVELS];
-    int sp = 0, cnt = 0;
-    stL[sp] = T.top; stK[sp] = 0; sp++;
-    unsigned long long HI = Ilo.w;
-    while (sp > 0) {
-        sp--;
-        int L = stL[sp], k = stK[sp];
-        uint4 nlo = lo[T.off[L] + k], nhi = hi[T.off[L] + k];
-        unsigned long long R = HI;
-        if (UNION && (unsigned long long)nlo.w > R) R = nlo.w;
-        if (box_gap2(Ilo, Ihi, nlo, nhi) >= R * R) continue;
-        if (L == 0) {
-            if (WRITE) out[cnt] = (uint32_t)k;
-            cnt++;
-        } else {
-            int kr = 2 * k + 1;
-            if (kr < T.cnt[L - 1]) { stL[sp] = L - 1; stK[sp] = kr; sp++; }
-            stL[sp] = L - 1; stK[sp] = 2 * k; sp++;
+// Warp-cooperative depth-first walk for tile I (one warp): every lane tests one
+// child of the node being expanded; passing leaves (tiles) are emitted in
+// ascending order, passing inner nodes pushed so that the lowest pops first.
+// The reach of a node is max(Hmax_I, Hmax_node) (pair-set predicate).
+template <bool WRITE>
+__device__ uint32_t walk32(const Tree32 &T, const uint4 *__restrict__ lo, const uint4 *__restrict__ hi,
+                           uint4 Ilo, uint4 Ihi, uint32_t *__restrict__ out, int *stL, int *stK, int lane) {
+    const unsigned lt = lanemask_lt();
+    const unsigned long long HI = Ilo.w;
+    uint32_t count = 0;
+    int sp = 0;
+    int L = T.top + 1, k = 0;           // virtual root: its children are the top-level nodes
+    for (;;) {
+        const int cl = L - 1;
+        const int c = k * 32 + lane;
+        bool pass = false;
+        if (c < T.cnt[cl]) {
+            const uint4 nlo = lo[T.off[cl] + c], nhi = hi[T.off[cl] + c];
+            unsigned long long R = HI > (unsigned long long)nlo.w ? HI : (unsigned long long)nlo.w;
+            pass = box_gap2(Ilo, Ihi, nlo, nhi) < R * R;
         }
+        const unsigned m = __ballot_sync(0xffffffffu, pass);
+        const int np = __popc(m);
+        if (cl == 0) {
+            if (WRITE && pass) out[count + __popc(m & lt)] = (uint32_t)c;
+            count += np;
+        } else if (np) {
+            if (pass) {
+                const int pos = sp + (np - 1 - __popc(m & lt));
+                if (pos < STACK) { stL[pos] = cl; stK[pos] = c; }
+            }
+            sp += np;
+        }
+        __syncwarp();
+        if (sp == 0) break;
+        sp--;
+        if (sp >= STACK) return 0xffffffffu;  // stack overflow: caller reports
+        L = stL[sp];
+        k = stK[sp];
+        __syncwarp();
     }
-    return cnt;
+    return count;
 }
 
-template <bool UNION>
-__global__ void k_lists(int ntiles, TreeDesc T, const uint4 *__restrict__ lo, const uint4 *__restrict__ hi,
-                        uint2 *__restrict__ ofs, uint32_t *__restrict__ list, long long cap,
-                        unsigned long long *counter) {
-    int I = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(LIST_WARPS * 32) k_lists32(int ntiles, Tree32 T, const uint4 *__restrict__ lo,
+                                                             const uint4 *__restrict__ hi, uint2 *__restrict__ ofs,
+                                                             uint32_t *__restrict__ list, long long cap,
+                                                             unsigned long long *counter) {
+    __shared__ int stL[LIST_WARPS][STACK], stK[LIST_WARPS][STACK];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int I = blockIdx.x * LIST_WARPS + w;
     if (I >= ntiles) return;
-    uint4 Ilo = lo[I], Ihi = hi[I];
-    int c = walk<UNION, false>(T, lo, hi, Ilo, Ihi, nullptr);
-    unsigned long long base = atomicAdd(counter, (unsigned long long)c);
+    const uint4 Ilo = lo[I], Ihi = hi[I];
+    uint32_t c = walk32<false>(T, lo, hi, Ilo, Ihi, nullptr, stL[w], stK[w], lane);
+    unsigned long long base = 0;
+    if (c == 0xffffffffu) {
+        if (lane == 0) {
+            atomicAdd(counter, (unsigned long long)cap + 1ull);   // forces the overflow path
+            ofs[I] = make_uint2(0u, 0u);
+        }
+        return;
+    }
+    if (lane == 0) base = atomicAdd(counter, (unsigned long long)c);
+    base = __shfl_sync(0xffffffffu, base, 0);
     if ((long long)(base + c) <= cap) {
-        walk<UNION, true>(T, lo, hi, Ilo, Ihi, list + base);
-        ofs[I] = make_uint2((uint32_t)base, (uint32_t)c);
-    } else {
+        walk32<true>(T, lo, hi, Ilo, Ihi, list + base, stL[w], stK[w], lane);
+        if (lane == 0) ofs[I] = make_uint2((uint32_t)base, c);
+    } else if (lane == 0) {
         ofs[I] = make_uint2(0u, 0u);
     }
 }
@@ -345,25 +378,30 @@ __global__ void k_cell_start(int n, const uint32_t *__restrict__ keys, int kmax,
 
 // ------------------------------------------------------------------ drivers
 
-static TreeDesc tree_desc(const crk_ctx *ctx) {
-    TreeDesc T;
-    for (int L = 0; L < MAX_LEVELS; L++) {
-        T.off[L] = ctx->level_off[L];
-        T.cnt[L] = ctx->level_cnt[L];
+static Tree32 tree32(const crk_ctx *ctx) {
+    Tree32 T;
+    int L = 0;
+    for (; L < MAX_L32 && 5 * L < ctx->nlevels; L++) {
+        T.off[L] = ctx->level_off[5 * L];
+        T.cnt[L] = ctx->level_cnt[5 * L];
     }
-    T.top = ctx->nlevels - 1;
+    for (int k = L; k < MAX_L32; k++) {
+        T.off[k] = 0;
+        T.cnt[k] = 0;
+    }
+    T.top = L - 1;
     return T;
 }
 
 int rebuild_lists(crk_ctx *ctx, cudaStream_t s) {
     if (ctx->ntiles == 0) return CRK_OK;
-    TreeDesc T = tree_desc(ctx);
+    Tree32 T = tree32(ctx);
+    if (T.cnt[T.top] > 32) return crk_set_error(ctx, CRK_ECAPACITY, "tile tree too deep");
     CRK_CUDA(ctx, cudaMemsetAsync(ctx->counters + CNT_GLIST, 0, 2 * sizeof(unsigned long long), s));
     ctx->lists_valid = 0;
-    int b = 128;
-    k_lists<true><<<grid_for(ctx->ntiles, b), b, 0, s>>>(ctx->ntiles, T, ctx->node_lo, ctx->node_hi,
-                                                          ctx->uofs, ctx->ulist, ctx->cap_ulist,
-                                                          ctx->counters + CNT_ULIST);
+    k_lists32<<<grid_for(ctx->ntiles, LIST_WARPS), LIST_WARPS * 32, 0, s>>>(
+        ctx->ntiles, T, ctx->node_lo, ctx->node_hi, ctx->uofs, ctx->ulist, ctx->cap_ulist,
+        ctx->counters + CNT_ULIST);
     ++ctx->launches;
     CRK_LAUNCH_CHECK(ctx, "interaction lists");
     return CRK_OK;

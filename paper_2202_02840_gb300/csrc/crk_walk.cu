@@ -25,6 +25,7 @@ struct WalkArgs {
     const float *hs;
     const uint2 *ofs;        // pair-set tile list per tile
     const uint32_t *tiles;
+    const uint4 *tlo, *thi;  // tile boxes (xlo, ylo, zlo, Hmax), (xhi, yhi, zhi, count)
     float *V, *Nn;
     uint4 *qV;               // (qx, qy, qz, V bits)
     int32_t *cnt_g, *cnt_u;
@@ -34,6 +35,13 @@ struct WalkArgs {
 };
 
 // LISTS: write the lists; VOL: sum n_i in the walk (volumes-only contexts).
+// circular distance (fixed point) from coordinate q to the interval [lo, hi]
+__device__ __forceinline__ unsigned long long point_gap(uint32_t q, uint32_t lo, uint32_t hi) {
+    if (q >= lo && q <= hi) return 0ull;
+    uint32_t d1 = lo - q, d2 = q - hi;   // both modulo 2^32
+    return (unsigned long long)(d1 < d2 ? d1 : d2);
+}
+
 template <bool LISTS, bool VOL>
 __global__ void __launch_bounds__(WALK_WARPS * 32) k_walk(WalkArgs a) {
     __shared__ uint4 sq[WALK_WARPS][32];
@@ -53,6 +61,13 @@ __global__ void __launch_bounds__(WALK_WARPS * 32) k_walk(WalkArgs a) {
     const uint2 lo = a.ofs[tile];
     for (uint32_t t = 0; t < lo.y; t++) {
         const int J = (int)a.tiles[lo.x + t];
+        // skip a neighbour tile that no lane's sphere (reach max(H_i, Hmax_J)) touches
+        const uint4 Jlo = __ldg(a.tlo + J), Jhi = __ldg(a.thi + J);
+        const unsigned long long gx = point_gap(qi.x, Jlo.x, Jhi.x), gy = point_gap(qi.y, Jlo.y, Jhi.y),
+                                 gz = point_gap(qi.z, Jlo.z, Jhi.z);
+        const unsigned long long reach = qi.w > Jlo.w ? qi.w : Jlo.w;
+        const bool near = valid && gx * gx + gy * gy + gz * gz < reach * reach;
+        if (__ballot_sync(0xffffffffu, near) == 0u) continue;
         const int j0 = J * TILE;
         const int cnt = min(TILE, a.n - j0);
         __syncwarp();
@@ -123,6 +138,8 @@ static WalkArgs walk_args(crk_ctx *ctx) {
     a.hs = ctx->hs;
     a.ofs = ctx->uofs;
     a.tiles = ctx->ulist;
+    a.tlo = ctx->node_lo;
+    a.thi = ctx->node_hi;
     a.V = ctx->V;
     a.Nn = ctx->Nn;
     a.qV = ctx->qV;

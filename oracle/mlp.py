@@ -1,0 +1,140 @@
+"""FP64 oracle of the learned smoothing-length proposal (TEST INFRASTRUCTURE ONLY).
+
+The paper evolves h with one Thacker update per step (Sec. 2.6, eq:thacker)
+and notes that solving eq:hi iteratively is the alternative; the learned part
+proposes a starting h for that fixed-point iteration.  Definitions (the same
+readings as the CUDA path, written independently here):
+
+features (8 per particle), cells of the grid level kf = the largest k in
+[1, 7] with 2^-k >= 4 N^(-1/3) (64 * 8^k <= N), cell of a particle = top kf bits of each
+fixed-point coordinate, counts over the periodic grid (an offset that wraps
+onto the same cell counts again):
+  f0 log1p(own cell)      f1 log1p(6 face cells)   f2 log1p(12 edge cells)
+  f3 log1p(8 corner cells) f4 log1p(all 27)        f5 log(h_prev / N^(-1/3))
+  f6 h_prev * div v        f7 log(N_prev / N_res)
+network: y = W3 . silu(W2 silu(W1 x + b1) + b2) + b3, silu(z) = z sigmoid(z),
+W1 64x8, W2 64x64, W3 64, packed as [W1, b1, W2, b2, W3, b3] (4801 values);
+proposal h = h_prev exp(y); target log(h_conv / h_prev); loss mean (y - t)^2.
+"""
+import numpy as np
+
+from . import crk as O
+
+N_PARAM = 64 * 8 + 64 + 64 * 64 + 64 + 64 + 1
+
+
+def grid_level(n):
+    """Largest k in [1, 7] with 2^-k >= 4 n^(-1/3), i.e. 64 * 8^k <= n (exact in integers)."""
+    k = 1
+    while k < 7 and 64 * 8 ** (k + 1) <= int(n):
+        k += 1
+    return k
+
+
+def unpack(w):
+    w = np.asarray(w, np.float64)
+    o = 0
+    W1 = w[o:o + 512].reshape(64, 8); o += 512
+    b1 = w[o:o + 64]; o += 64
+    W2 = w[o:o + 4096].reshape(64, 64); o += 4096
+    b2 = w[o:o + 64]; o += 64
+    W3 = w[o:o + 64]; o += 64
+    b3 = w[o]
+    return W1, b1, W2, b2, W3, b3
+
+
+def features(pos_h, N_prev=None, divv=None, kf=None, N_res=268.0):
+    pos = np.asarray(pos_h, np.float32).reshape(-1, 4)
+    n = pos.shape[0]
+    kf = grid_level(n) if kf is None else kf
+    q, _ = O.fixed_point(pos)
+    c = (q >> np.uint32(32 - kf)).astype(np.int64)
+    g = 1 << kf
+    cid = (c[:, 2] * g + c[:, 1]) * g + c[:, 0]
+    counts = np.bincount(cid, minlength=g ** 3).astype(np.float64)
+    own = np.zeros(n); face = np.zeros(n); edge = np.zeros(n); corner = np.zeros(n)
+    for dz in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                m = abs(dx) + abs(dy) + abs(dz)
+                cc = ((c[:, 2] + dz) % g * g + (c[:, 1] + dy) % g) * g + (c[:, 0] + dx) % g
+                v = counts[cc]
+                if m == 0:
+                    own += v
+                elif m == 1:
+                    face += v
+                elif m == 2:
+                    edge += v
+                else:
+                    corner += v
+    h = pos[:, 3].astype(np.float64)
+    f = np.empty((n, 8))
+    f[:, 0] = np.log1p(own)
+    f[:, 1] = np.log1p(face)
+    f[:, 2] = np.log1p(edge)
+    f[:, 3] = np.log1p(corner)
+    f[:, 4] = np.log1p(own + face + edge + corner)
+    f[:, 5] = np.log(h * float(n) ** (1.0 / 3.0))
+    f[:, 6] = 0.0 if divv is None else h * np.asarray(divv, np.float64)
+    f[:, 7] = 0.0 if N_prev is None else np.log(np.asarray(N_prev, np.float64) / N_res)
+    return f
+
+
+def silu(z):
+    return z / (1.0 + np.exp(-z))
+
+
+def dsilu(z):
+    s = 1.0 / (1.0 + np.exp(-z))
+    return s * (1.0 + z * (1.0 - s))
+
+
+def forward(w, x):
+    """FP64 forward: returns y and the intermediates (z1, a1, z2, a2)."""
+    W1, b1, W2, b2, W3, b3 = unpack(w)
+    x = np.asarray(x, np.float64)
+    z1 = x @ W1.T + b1
+    a1 = silu(z1)
+    z2 = a1 @ W2.T + b2
+    a2 = silu(z2)
+    y = a2 @ W3 + b3
+    return y, (z1, a1, z2, a2)
+
+
+def loss_and_grad(w, x, t):
+    """Mean squared error and its gradient by hand-written backpropagation."""
+    W1, b1, W2, b2, W3, b3 = unpack(w)
+    x = np.asarray(x, np.float64)
+    t = np.asarray(t, np.float64)
+    y, (z1, a1, z2, a2) = forward(w, x)
+    B = x.shape[0]
+    r = y - t
+    L = float(np.mean(r * r))
+    dy = 2.0 * r / B
+    gW3 = a2.T @ dy
+    gb3 = dy.sum()
+    dz2 = np.outer(dy, W3) * dsilu(z2)
+    gW2 = dz2.T @ a1
+    gb2 = dz2.sum(0)
+    dz1 = (dz2 @ W2) * dsilu(z1)
+    gW1 = dz1.T @ x
+    gb1 = dz1.sum(0)
+    g = np.concatenate([gW1.ravel(), gb1, gW2.ravel(), gb2, gW3, [gb3]])
+    return L, g
+
+
+def init_weights(seed=0):
+    """Seeded fan-in-scaled normal initial weights (generator only, no training)."""
+    r = np.random.Generator(np.random.Philox(key=seed))
+    W1 = r.normal(0, 1.0 / np.sqrt(8), (64, 8))
+    W2 = r.normal(0, 1.0 / np.sqrt(64), (64, 64))
+    W3 = r.normal(0, 0.1 / np.sqrt(64), 64)
+    return np.concatenate([W1.ravel(), np.zeros(64), W2.ravel(), np.zeros(64), W3, [0.0]])
+
+
+def bf16_round(a):
+    """Round FP32 values to bfloat16 (nearest-even) and back, as the GPU stores them."""
+    f = np.ascontiguousarray(np.asarray(a, np.float32))
+    u = f.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).reshape(np.shape(a))

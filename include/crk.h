@@ -213,8 +213,11 @@ int crk_step(crk_ctx *ctx, int n, float *pos_h, float *vel_u, const float *mass,
 int crk_reset_rates(crk_ctx *ctx);
 
 /* Fixed-point solve of eq:hi by eq:thacker updates (Sec. 2.6): repeat P1 and
- * the Thacker update for every particle not yet converged, until
- * |Delta_N - 1| <= tol for all particles or max_it iterations.  Reads and
+ * the Thacker update (clamped to [h_min, h_max]) for every particle not yet
+ * converged, until |Delta_N - 1| <= tol for all particles or max_it
+ * iterations.  A particle held at a bound that its update points beyond (a
+ * particle in a void that would need h > h_max) counts as converged: that is
+ * the bound-constrained solution.  Converged particles keep their h.  Reads and
  * updates the h column of pos_h[4n] in place (tiles are rebuilt as h
  * changes).  *iterations (host) receives the iterations used.  Returns
  * CRK_ENONCONV if some particle did not converge.  Synchronises. */
@@ -227,11 +230,13 @@ int crk_h_iterate(crk_ctx *ctx, int n, float *pos_h, float tol, int max_it, int 
  * stops recording.  At most 4096 records are kept. */
 int crk_profile(crk_ctx *ctx, int enable);
 
-#define CRK_PROF_NPASS 8
+#define CRK_PROF_NPASS 10
 /* Wait for the recorded events and sum them per pass: ms[k] (milliseconds)
  * and counts[k] (records) for k = 0 P1 volumes, 1 neighbour sets, 2 P2
  * corrections, 3 P3 grad v, 4 P4 forces, 5 P5 compatible energy, 6 cell build
- * (all its kernels), 7 neighbour-list fill; arrays of CRK_PROF_NPASS entries
+ * (all its kernels), 7 neighbour-list fill, 8 learned-h inference
+ * (crk_mlp_forward, or crk_h_propose with its cell count), 9 one training step
+ * (gradient and Adam); arrays of CRK_PROF_NPASS entries
  * (may be NULL).  P1 is the list-counting walk, which also computes volumes.
  * *total_launches (may be NULL) = kernels launched by ctx since crk_create. */
 int crk_profile_read(crk_ctx *ctx, double *ms, long long *counts, long long *total_launches);
@@ -260,6 +265,103 @@ int crk_profile_read(crk_ctx *ctx, double *ms, long long *counts, long long *tot
  *  - The call synchronises `stream` once (to check the binning) and then
  *    enqueues P1 and the output scatter on it. */
 int crk_volumes_noalloc(int n, const float *pos_h, float *V, float *Nngb, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Learned smoothing-length proposal.
+ *
+ * The paper evolves h by one Thacker update per step (Sec. 2.6, eq:thacker;
+ * eq:hi defines the target neighbour count N_res).  Solving eq:hi exactly is
+ * the fixed-point iteration of crk_h_iterate; these calls propose its
+ * starting point with a small network trained on converged solutions.  The
+ * iteration stays in charge: it judges every proposal and corrects it to the
+ * same tolerance as without one.
+ *
+ * Features, 8 per particle, row-major float[8n] in caller order.  Cells are
+ * those of the grid of side 2^-kf, kf the largest k in [1, 7] with
+ * 64 * 8^k <= n (so that 2^-kf >= 4 N^(-1/3), about one kernel support at
+ * N_res); a particle's cell is the top kf bits of its fixed-point
+ * coordinates, neighbours wrap periodically (with 2 cells per axis an offset
+ * of -1 and +1 reach the same cell and both count):
+ *   0 log(1 + own cell count)        1 log(1 + sum of the 6 face cells)
+ *   2 log(1 + sum of the 12 edge cells) 3 log(1 + sum of the 8 corner cells)
+ *   4 log(1 + sum of all 27 cells)   5 log(h / Delta), Delta = N^(-1/3)
+ *   6 h div v (trace of gradv; 0 without gradv)
+ *   7 log(Nngb / N_res) (0 without Nngb)
+ * Network: y = s_y (W3 . silu(W2 silu(W1 x + b1) + b2) + b3), sizes 8 -> 64
+ * -> 64 -> 1, silu(z) = z / (1 + e^-z), s_y = CRK_MLP_YSCALE a fixed output
+ * scale (the corrections are of order 1% in log h; the scale keeps the
+ * network's own outputs of order one).  Parameters are one FP32 array of
+ * CRK_MLP_NPARAM values packed as W1 (64x8, row-major [out][in]), b1 (64),
+ * W2 (64x64, [out][in]), b2 (64), W3 (64), b3 (1).  Arithmetic: weights, the
+ * features and both hidden activations are rounded to BF16, products are
+ * accumulated in FP32 on the tensor cores, biases stay FP32, and silu uses
+ * the hardware tanh approximation of the logistic function.
+ * Target of training: log(h_conv / h_ref) (h_ref below); loss: mean squared error over the
+ * batch; optimiser: Adam (beta1 0.9, beta2 0.999, eps 1e-8) on the FP32
+ * master weights, which the context owns.
+ * ---------------------------------------------------------------------- */
+#define CRK_MLP_NPARAM 4801
+#define CRK_MLP_NFEAT 8
+#define CRK_MLP_YSCALE 0.015625f
+
+/* Copy the network parameters in (w: CRK_MLP_NPARAM floats, host or device)
+ * and reset the Adam state.  Must precede every other crk_mlp / crk_h_propose
+ * call (CRK_ESTATE otherwise). */
+int crk_mlp_set_weights(crk_ctx *ctx, const float *w, void *stream);
+
+/* Copy the current FP32 master weights out (host or device pointer). */
+int crk_mlp_get_weights(crk_ctx *ctx, float *w, void *stream);
+
+/* Features of n particles.  pos_h[4n] in; gradv[9n] and Nngb[n] (device, may
+ * be NULL) in; feat[8n] out.  With pos_conv[4n] (the same particles with the
+ * converged h in the w column) also target[n] = log(h_conv / h_ref), where
+ * h_ref = h_prev (N_res / Nngb)^(1/3) with Nngb (the constant-density
+ * solution of eq:hi, which the proposal starts from) and h_ref = h_prev
+ * without; pos_conv and target are both NULL or both set.  CRK_EINVAL for
+ * coordinates outside [0,1) or h outside (0,1).  Synchronises `stream` once
+ * to check the records. */
+int crk_h_features(crk_ctx *ctx, int n, const float *pos_h, const float *gradv, const float *Nngb,
+                   const float *pos_conv, float *feat, float *target, void *stream);
+
+/* Network output y[n] (device) for the feature rows feat[8n] (device). */
+int crk_mlp_forward(crk_ctx *ctx, int n, const float *feat, float *y, void *stream);
+
+/* Proposal, in place: the h column of pos_h[4n] (device) becomes
+ * clamp(h_ref exp(y), h_min, h_max), y the network output for the particle's
+ * features (computed in the same kernel from pos_h, gradv, Nngb as for
+ * crk_h_features) and h_ref as there: the network corrects the
+ * constant-density estimate h (N_res / Nngb)^(1/3) (h without Nngb).  A
+ * particle whose Nngb already satisfies |(N_res / Nngb)^(1/3) - 1| <= tol
+ * keeps its h (the judge of crk_h_iterate).  Synchronises `stream` once to
+ * check the records; on CRK_EINVAL the h column is unspecified. */
+int crk_h_propose(crk_ctx *ctx, int n, float *pos_h, const float *gradv, const float *Nngb, float tol,
+                  void *stream);
+
+/* One full-batch step over the n rows feat[8n], target[n] (device): the
+ * gradient of the mean squared error goes to grad[CRK_MLP_NPARAM] (device,
+ * may be NULL) and the loss to loss[1] (device, may be NULL); then, for
+ * lr > 0, one Adam update of the weights (lr = 0 leaves them unchanged, which
+ * makes this the gradient evaluation). */
+int crk_mlp_train_step(crk_ctx *ctx, int n, const float *feat, const float *target, float lr, float *grad,
+                       float *loss, void *stream);
+
+/* Rows that the proposal acts on: rows[0..*count) (device out, capacity n)
+ * receives, in increasing order, base + i for every i with
+ * |(N_res / Nngb[i])^(1/3) - 1| > tol (Nngb device, n floats); *count
+ * (host) their number.  base offsets the indices into a data set that
+ * concatenates several snapshots.  Synchronises `stream`. */
+int crk_h_select(crk_ctx *ctx, int n, const float *Nngb, float tol, int base, int32_t *rows, int *count,
+                 void *stream);
+
+/* `steps` Adam steps on batches of `batch` rows drawn with replacement by a
+ * counter-based generator (SplitMix64 of seed and the global step count, so
+ * that successive calls continue the sequence) from the rows feat[8n],
+ * target[n] (device): from all n rows when rows is NULL, else from the
+ * n_rows row indices rows[] (device, each in [0, n)).  loss_hist (host,
+ * `steps` floats, may be NULL) receives the loss of each batch; with
+ * loss_hist the call synchronises. */
+int crk_mlp_train(crk_ctx *ctx, int n, const float *feat, const float *target, const int32_t *rows, int n_rows,
+                  int batch, int steps, float lr, unsigned long long seed, float *loss_hist, void *stream);
 
 #ifdef __cplusplus
 }

@@ -279,9 +279,12 @@ def cfl_dt(ev, prm=None):
     return np.minimum(dt_h, dt_a)
 
 
-def h_iterate(pos_h, tol=1e-4, max_it=50, prm=None, k=None):
-    """Fixed-point solve of eq:hi by repeated eq:thacker updates: a particle is
-    converged once |Delta_N - 1| <= tol and keeps its h from then on."""
+def h_iterate(pos_h, tol=1e-4, max_it=50, prm=None, k=None, h_min=1e-6, h_max=0.3):
+    """Fixed-point solve of eq:hi by repeated eq:thacker updates, each clamped
+    to [h_min, h_max] as the evolved h is: a particle is converged once
+    |Delta_N - 1| <= tol, or once it sits at a bound that its update points
+    beyond (the bound-constrained solution, e.g. a particle in a void that
+    would need h > h_max to reach N_res), and keeps its h from then on."""
     prm = params() if prm is None else prm
     pos = _pos(pos_h).copy()
     n = pos.shape[0]
@@ -290,11 +293,11 @@ def h_iterate(pos_h, tol=1e-4, max_it=50, prm=None, k=None):
     for it in range(1, max_it + 1):
         p1 = volumes(pos, k)
         d = np.cbrt(prm[2] / p1["N"])
-        done |= np.abs(d - 1.0) <= tol
+        hn = np.clip(thacker(pos[:, 3].astype(np.float64), p1["N"], prm), h_min, h_max).astype(np.float32)
+        done |= (np.abs(d - 1.0) <= tol) | (hn == pos[:, 3])
         if done.all():
             return pos[:, 3].copy(), it, done
-        hn = thacker(pos[:, 3].astype(np.float64), p1["N"], prm)
-        pos[:, 3] = np.where(done, pos[:, 3], hn.astype(np.float32))
+        pos[:, 3] = np.where(done, pos[:, 3], hn)
     return pos[:, 3].copy(), it, done
 
 

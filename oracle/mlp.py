@@ -12,15 +12,23 @@ onto the same cell counts again):
   f0 log1p(own cell)      f1 log1p(6 face cells)   f2 log1p(12 edge cells)
   f3 log1p(8 corner cells) f4 log1p(all 27)        f5 log(h_prev / N^(-1/3))
   f6 h_prev * div v        f7 log(N_prev / N_res)
-network: y = W3 . silu(W2 silu(W1 x + b1) + b2) + b3, silu(z) = z sigmoid(z),
-W1 64x8, W2 64x64, W3 64, packed as [W1, b1, W2, b2, W3, b3] (4801 values);
-proposal h = h_prev exp(y); target log(h_conv / h_prev); loss mean (y - t)^2.
+network: y = s_y (W3 . silu(W2 silu(W1 x + b1) + b2) + b3), silu(z) = z sigmoid(z),
+s_y = 2^-6 a fixed output scale (log-h corrections are of order 1%, which
+keeps the network's own outputs of order one), W1 64x8, W2 64x64, W3 64,
+packed as [W1, b1, W2, b2, W3, b3] (4801 values); proposal h = h_ref exp(y),
+h_ref = h_prev (N_res / N_prev)^(1/3) (the constant-density solution of
+eq:hi; h_prev without N_prev); target log(h_conv / h_ref); loss mean (y - t)^2.
+Declared arithmetic of the tensor-core path (forward/loss_and_grad with
+rnd=bf16_round, round_weights(w), bf16_round(x)): BF16 weight matrices,
+features and hidden activations, BF16 deltas into the weight-gradient
+products, every sum in FP64 here (FP32 on the GPU), FP32 biases.
 """
 import numpy as np
 
 from . import crk as O
 
 N_PARAM = 64 * 8 + 64 + 64 * 64 + 64 + 64 + 1
+Y_SCALE = 2.0 ** -6
 
 
 def grid_level(n):
@@ -89,47 +97,62 @@ def dsilu(z):
     return s * (1.0 + z * (1.0 - s))
 
 
-def forward(w, x):
-    """FP64 forward: returns y and the intermediates (z1, a1, z2, a2)."""
+def _ident(a):
+    return a
+
+
+def forward(w, x, rnd=None):
+    """FP64 forward: returns y and the intermediates (z1, a1, z2, a2).
+
+    rnd (optional) rounds each hidden activation where the declared arithmetic
+    stores it: bf16_round gives the BF16-activation network that the
+    tensor-core path computes (with round_weights(w) and bf16_round(x))."""
+    r = _ident if rnd is None else rnd
     W1, b1, W2, b2, W3, b3 = unpack(w)
     x = np.asarray(x, np.float64)
     z1 = x @ W1.T + b1
-    a1 = silu(z1)
+    a1 = np.asarray(r(silu(z1)), np.float64)
     z2 = a1 @ W2.T + b2
-    a2 = silu(z2)
-    y = a2 @ W3 + b3
+    a2 = np.asarray(r(silu(z2)), np.float64)
+    y = Y_SCALE * (a2 @ W3 + b3)
     return y, (z1, a1, z2, a2)
 
 
-def loss_and_grad(w, x, t):
-    """Mean squared error and its gradient by hand-written backpropagation."""
+def loss_and_grad(w, x, t, rnd=None):
+    """Mean squared error and its gradient by hand-written backpropagation.
+
+    With rnd, the activations of the forward pass and the two back-propagated
+    deltas that enter matrix products (dL/dz2, dL/dz1) are rounded where the
+    declared arithmetic stores them; bias gradients take the unrounded deltas."""
+    r = _ident if rnd is None else rnd
     W1, b1, W2, b2, W3, b3 = unpack(w)
     x = np.asarray(x, np.float64)
     t = np.asarray(t, np.float64)
-    y, (z1, a1, z2, a2) = forward(w, x)
+    y, (z1, a1, z2, a2) = forward(w, x, rnd)
     B = x.shape[0]
-    r = y - t
-    L = float(np.mean(r * r))
-    dy = 2.0 * r / B
+    res = y - t
+    L = float(np.mean(res * res))
+    dy = Y_SCALE * 2.0 * res / B
     gW3 = a2.T @ dy
     gb3 = dy.sum()
     dz2 = np.outer(dy, W3) * dsilu(z2)
-    gW2 = dz2.T @ a1
     gb2 = dz2.sum(0)
+    dz2 = np.asarray(r(dz2), np.float64)
+    gW2 = dz2.T @ a1
     dz1 = (dz2 @ W2) * dsilu(z1)
-    gW1 = dz1.T @ x
     gb1 = dz1.sum(0)
+    dz1 = np.asarray(r(dz1), np.float64)
+    gW1 = dz1.T @ x
     g = np.concatenate([gW1.ravel(), gb1, gW2.ravel(), gb2, gW3, [gb3]])
     return L, g
 
 
-def init_weights(seed=0):
-    """Seeded fan-in-scaled normal initial weights (generator only, no training)."""
-    r = np.random.Generator(np.random.Philox(key=seed))
-    W1 = r.normal(0, 1.0 / np.sqrt(8), (64, 8))
-    W2 = r.normal(0, 1.0 / np.sqrt(64), (64, 64))
-    W3 = r.normal(0, 0.1 / np.sqrt(64), 64)
-    return np.concatenate([W1.ravel(), np.zeros(64), W2.ravel(), np.zeros(64), W3, [0.0]])
+def round_weights(w):
+    """The declared weight precision: W1, W2, W3 rounded to BF16, biases kept."""
+    w = np.asarray(w, np.float64).copy()
+    for a, b in ((0, 512), (576, 4672), (4736, 4800)):
+        w[a:b] = bf16_round(w[a:b])
+    return w
 
 
 def bf16_round(a):

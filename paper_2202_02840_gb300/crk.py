@@ -70,6 +70,15 @@ def lib():
         L.crk_reset_rates.argtypes = [_vp]
         L.crk_h_iterate.argtypes = [_vp, _ci, _vp, ctypes.c_float, _ci, ctypes.POINTER(_ci), _vp]
         L.crk_volumes_noalloc.argtypes = [_ci, _vp, _vp, _vp, _vp]
+        L.crk_mlp_set_weights.argtypes = [_vp, _vp, _vp]
+        L.crk_mlp_get_weights.argtypes = [_vp, _vp, _vp]
+        L.crk_h_features.argtypes = [_vp, _ci, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
+        L.crk_mlp_forward.argtypes = [_vp, _ci, _vp, _vp, _vp]
+        L.crk_h_propose.argtypes = [_vp, _ci, _vp, _vp, _vp, ctypes.c_float, _vp]
+        L.crk_mlp_train_step.argtypes = [_vp, _ci, _vp, _vp, ctypes.c_float, _vp, _vp, _vp]
+        L.crk_mlp_train.argtypes = [_vp, _ci, _vp, _vp, _vp, _ci, _ci, _ci, ctypes.c_float, ctypes.c_ulonglong,
+                                    _vp, _vp]
+        L.crk_h_select.argtypes = [_vp, _ci, _vp, ctypes.c_float, _ci, _vp, ctypes.POINTER(_ci), _vp]
         L.crk_profile.argtypes = [_vp, _ci]
         L.crk_profile_read.argtypes = [_vp, _vp, _vp, ctypes.POINTER(ctypes.c_longlong)]
         _LIB = L
@@ -267,7 +276,8 @@ def crk_h_iterate(ctx, pos_h, tol=1e-4, max_it=50, stream=None):
 
 
 PASS_NAMES = ["P1 volumes", "neighbour sets", "P2 corrections", "P3 grad v", "P4 forces",
-              "P5 compatible energy", "cell build", "neighbour lists"]
+              "P5 compatible energy", "cell build", "neighbour lists", "h proposal", "mlp train step"]
+NPASS = len(PASS_NAMES)
 
 
 def crk_profile(ctx, enable=True):
@@ -276,11 +286,11 @@ def crk_profile(ctx, enable=True):
 
 def crk_profile_read(ctx):
     """({pass: total ms}, {pass: records}, total kernel launches since creation)."""
-    ms = (ctypes.c_double * 8)()
-    cnt = (ctypes.c_longlong * 8)()
+    ms = (ctypes.c_double * NPASS)()
+    cnt = (ctypes.c_longlong * NPASS)()
     tot = ctypes.c_longlong(0)
     ctx.check(lib().crk_profile_read(ctx.handle, ms, cnt, ctypes.byref(tot)))
-    return ({PASS_NAMES[k]: ms[k] for k in range(8)}, {PASS_NAMES[k]: cnt[k] for k in range(8)},
+    return ({PASS_NAMES[k]: ms[k] for k in range(NPASS)}, {PASS_NAMES[k]: cnt[k] for k in range(NPASS)},
             tot.value)
 
 
@@ -306,3 +316,85 @@ def crk_volumes_noalloc(pos_h, stream=None):
     if rc != CRK_OK:
         raise CrkError(rc, "crk_volumes_noalloc failed")
     return V, N
+
+
+# ---------------------------------------------------------------- learned h proposal
+
+MLP_NPARAM = 4801
+MLP_NFEAT = 8
+
+
+def _opt(x, shape, name):
+    return _vp(None) if x is None else _t(x, shape, name)
+
+
+def crk_mlp_set_weights(ctx, w, stream=None):
+    """Load the FP32 parameters (CUDA tensor of MLP_NPARAM) and reset Adam."""
+    ctx.check(lib().crk_mlp_set_weights(ctx.handle, _t(w, (MLP_NPARAM,), "w"), _stream(stream)))
+
+
+def crk_mlp_get_weights(ctx, stream=None):
+    w = torch.empty(MLP_NPARAM, dtype=torch.float32, device=torch.device("cuda"))
+    ctx.check(lib().crk_mlp_get_weights(ctx.handle, _vp(w.data_ptr()), _stream(stream)))
+    return w
+
+
+def crk_h_features(ctx, pos_h, gradv=None, Nngb=None, pos_conv=None, stream=None):
+    """Features (n, 8); with pos_conv also the targets log(h_conv / h_prev) -> (feat, target)."""
+    n = pos_h.shape[0]
+    dev = pos_h.device
+    feat = torch.empty((n, MLP_NFEAT), dtype=torch.float32, device=dev)
+    target = torch.empty(n, dtype=torch.float32, device=dev) if pos_conv is not None else None
+    ctx.check(lib().crk_h_features(ctx.handle, n, _t(pos_h, (n, 4), "pos_h"), _opt(gradv, (n, 3, 3), "gradv"),
+                                   _opt(Nngb, (n,), "Nngb"), _opt(pos_conv, (n, 4), "pos_conv"),
+                                   _vp(feat.data_ptr()), _vp(None if target is None else target.data_ptr()),
+                                   _stream(stream)))
+    return (feat, target) if pos_conv is not None else feat
+
+
+def crk_mlp_forward(ctx, feat, stream=None):
+    n = feat.shape[0]
+    y = torch.empty(n, dtype=torch.float32, device=feat.device)
+    ctx.check(lib().crk_mlp_forward(ctx.handle, n, _t(feat, (n, MLP_NFEAT), "feat"), _vp(y.data_ptr()),
+                                    _stream(stream)))
+    return y
+
+
+def crk_h_propose(ctx, pos_h, gradv=None, Nngb=None, tol=1e-4, stream=None):
+    """Write the proposed h into pos_h[:, 3] in place."""
+    n = pos_h.shape[0]
+    ctx.check(lib().crk_h_propose(ctx.handle, n, _t(pos_h, (n, 4), "pos_h"), _opt(gradv, (n, 3, 3), "gradv"),
+                                  _opt(Nngb, (n,), "Nngb"), float(tol), _stream(stream)))
+
+
+def crk_mlp_train_step(ctx, feat, target, lr=0.0, stream=None):
+    """One full-batch step; returns (grad, loss) as CUDA tensors."""
+    n = feat.shape[0]
+    dev = feat.device
+    grad = torch.empty(MLP_NPARAM, dtype=torch.float32, device=dev)
+    loss = torch.empty(1, dtype=torch.float32, device=dev)
+    ctx.check(lib().crk_mlp_train_step(ctx.handle, n, _t(feat, (n, MLP_NFEAT), "feat"), _t(target, (n,), "target"),
+                                       float(lr), _vp(grad.data_ptr()), _vp(loss.data_ptr()), _stream(stream)))
+    return grad, loss
+
+
+def crk_h_select(ctx, Nngb, tol=1e-4, base=0, stream=None):
+    """Indices (int32 CUDA tensor, base-offset) of the rows the judge hands to the proposal."""
+    n = Nngb.shape[0]
+    rows = torch.empty(max(n, 1), dtype=torch.int32, device=Nngb.device)
+    cnt = _ci(0)
+    ctx.check(lib().crk_h_select(ctx.handle, n, _t(Nngb, (n,), "Nngb"), float(tol), int(base),
+                                 _vp(rows.data_ptr()), ctypes.byref(cnt), _stream(stream)))
+    return rows[:cnt.value]
+
+
+def crk_mlp_train(ctx, feat, target, rows=None, batch=4096, steps=1000, lr=1e-3, seed=1, stream=None):
+    """`steps` Adam steps on batches sampled from all rows (rows None) or from the
+    listed rows; returns the per-step losses (list of floats)."""
+    n = feat.shape[0]
+    hist = (ctypes.c_float * max(int(steps), 1))()
+    nr = 0 if rows is None else rows.shape[0]
+    ctx.check(lib().crk_mlp_train(ctx.handle, n, _t(feat, (n, MLP_NFEAT), "feat"), _t(target, (n,), "target"),
+                                  _vp(None) if rows is None else _t(rows, (nr,), "rows", torch.int32), nr,
+                                  int(batch), int(steps), float(lr), int(seed), hist, _stream(stream)))
+    return [hist[k] for k in range(int(steps))]

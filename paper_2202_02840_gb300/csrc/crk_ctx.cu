@@ -427,6 +427,7 @@ extern "C" int crk_destroy(crk_ctx *ctx) {
     dfree(&ctx->st_pos); dfree(&ctx->st_vel); dfree(&ctx->st_half); dfree(&ctx->st_tmp);
     dfree(&ctx->st_tmp1); dfree(&ctx->q_tmp); dfree(&ctx->h_tmp); dfree(&ctx->flags); dfree(&ctx->d_red); dfree(&ctx->d_dt); dfree(&ctx->d_scalars);
     if (ctx->h_counters) cudaFreeHost(ctx->h_counters);
+    mlp_free(ctx);
     prof_free(ctx);
     delete ctx;
     return CRK_OK;

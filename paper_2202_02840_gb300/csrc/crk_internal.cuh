@@ -29,6 +29,7 @@ enum {
     CNT_DTMIN = 8,      // min per-particle time step (float bits)
     CNT_ENTRIES = 9,    // stored-force units (32 entries) of the last list build
     CNT_MAXCNT = 10,    // largest pair-set count of the last walk
+    CNT_MLP_ERR = 11,   // invalid records seen by the feature kernels
     CNT_COUNT = 16
 };
 
@@ -143,6 +144,18 @@ struct crk_ctx {
     int rates_valid = 0;
     int step_n = 0;
 
+    // learned smoothing-length proposal (network state and feature grid)
+    float *mlp_w = nullptr;          // FP32 master weights, CRK_MLP_NPARAM
+    float *mlp_m = nullptr, *mlp_v = nullptr;   // Adam first and second moments
+    float *mlp_part = nullptr;       // per-block gradient partials of one step
+    int cap_part = 0;                // blocks the partial buffer holds
+    float *mlp_hist = nullptr;       // per-step loss of the last training run
+    int cap_hist_loss = 0;
+    long long mlp_t = 0;             // Adam steps taken since the weights were set
+    int32_t *fcnt = nullptr;         // occupancy of the feature grid (8^7 cells)
+    uint32_t *sel = nullptr;         // row selection: flags and their scan (2 x cap_sel)
+    int cap_sel = 0;
+
     // launch accounting and per-pass event timing
     long long launches = 0;
     int prof_on = 0;
@@ -176,7 +189,8 @@ int crk_sync_counters(crk_ctx *ctx, cudaStream_t s);
 // internal entry points shared between translation units (sorted-order data)
 namespace crk {
 enum { PROF_P1 = 0, PROF_PN = 1, PROF_P2 = 2, PROF_P3 = 3, PROF_P4 = 4, PROF_P5 = 5, PROF_BUILD = 6,
-       PROF_LISTS = 7, PROF_NPASS = 8 };
+       PROF_LISTS = 7, PROF_MLP_FWD = 8, PROF_MLP_TRAIN = 9, PROF_NPASS = 10 };
+void mlp_free(crk_ctx *ctx);
 void prof_begin(crk_ctx *ctx, int id, cudaStream_t s);
 void prof_end(crk_ctx *ctx, cudaStream_t s);
 int build_cells_sorted(crk_ctx *ctx, int n, const float4 *pos_h, const int32_t *order,

@@ -192,12 +192,12 @@ __global__ void k_h_iter(int n, StepConsts c, float tol, const float *__restrict
     unsigned nd = 0;
     if (s < n && !flags[s]) {
         float d = cbrtf(c.N_res / Nn[s]);
-        if (fabsf(d - 1.f) <= tol) {
+        float lam = d < 1.f ? 0.2f * (1.f + d * d) : 0.2f * (1.f + 1.f / (d * d * d));
+        float hn = fminf(fmaxf(hs[s] * (1.f - lam + lam * d), c.h_min), c.h_max);
+        // converged, or held at a bound that the update points beyond
+        if (fabsf(d - 1.f) <= tol || hn == hs[s]) {
             flags[s] = 1;
         } else {
-            float lam = d < 1.f ? 0.2f * (1.f + d * d) : 0.2f * (1.f + 1.f / (d * d * d));
-            float hn = hs[s] * (1.f - lam + lam * d);
-            hn = fminf(fmaxf(hn, c.h_min), c.h_max);
             hs[s] = hn;
             uint4 q = q4[s];
             q.w = to_fixed(hn);

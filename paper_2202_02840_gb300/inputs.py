@@ -173,6 +173,18 @@ def zeldovich(n_side: int = 128, seed: int = 4, seed_u: int = 5, contrast: float
     return out
 
 
+def mlp_init(seed: int = 0) -> np.ndarray:
+    """Seeded initial parameters of the 8-64-64-1 network, packed as
+    [W1 (64x8), b1, W2 (64x64), b2, W3, b3]: fan-in scaled normal hidden
+    weights, zero biases and a zero output row (so that the untrained network
+    outputs 0 and the proposal starts as its reference).  FP32."""
+    r = rng(1000 + int(seed))
+    W1 = r.normal(0.0, 1.0 / np.sqrt(8.0), (64, 8))
+    W2 = r.normal(0.0, 1.0 / np.sqrt(64.0), (64, 64))
+    w = np.concatenate([W1.ravel(), np.zeros(64), W2.ravel(), np.zeros(64), np.zeros(64), [0.0]])
+    return w.astype(np.float32)
+
+
 WORKLOADS = {
     "uniform": uniform,
     "sedov": sedov,

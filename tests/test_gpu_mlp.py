@@ -1,0 +1,319 @@
+"""GPU parity of the learned smoothing-length proposal against the FP64 oracle.
+
+Features are compared value by value (cell counts are integers, so their
+logarithms agree to FP32 rounding).  The network is compared with the oracle
+evaluated in the declared arithmetic (BF16 weights, features and hidden
+activations, FP64 sums): the remaining differences come from FP32 sums and
+the hardware tanh approximation, which move some BF16 roundings by one unit.
+The tolerances below are derived from that: a hidden activation that rounds
+the other way changes by at most one BF16 unit (2^-8 relative), so
+|dy| <= sum_k |W3_k| (2^-8 |a2_k| + 1.1 sum_j |W2_kj| 2^-8 |a1_j|) (all
+flipping the same way); the test allows a quarter of that bound per row,
+and a root-mean-square difference of 2% of the spread of y.  A transposed
+operand or a misplaced parameter moves y by several times its spread.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import crk as O
+from oracle import mlp as M
+from paper_2202_02840_gb300 import crk, inputs, learned_h
+from parity import as_np, workload
+
+pytestmark = pytest.mark.gpu
+
+BF16_U = 2.0 ** -8
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _device():
+    import __graft_entry__
+    __graft_entry__.build()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    torch.cuda.set_device(0)
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def rand_features(n, seed):
+    r = np.random.default_rng(seed)
+    x = np.stack([r.uniform(0, 4, n), r.uniform(0, 6, n), r.uniform(0, 6.5, n), r.uniform(0, 6, n),
+                  r.uniform(1, 8, n), r.normal(1.4, 0.3, n), r.normal(0, 0.3, n), r.normal(0, 0.1, n)], 1)
+    return x.astype(np.float32)
+
+
+def rand_weights(seed):
+    r = np.random.default_rng(100 + seed)
+    w = inputs.mlp_init(seed).astype(np.float64)
+    w[512:576] = r.normal(0, 0.3, 64)   # nonzero biases and output row
+    w[4672:4736] = r.normal(0, 0.3, 64)
+    w[4736:4800] = r.normal(0, 0.125, 64)
+    w[4800] = 0.1
+    return w.astype(np.float32)
+
+
+def fwd_bound(w, x):
+    """Per-row bound on |y_gpu - y_declared| if every hidden activation flipped one BF16 unit."""
+    _, (_, a1, _, a2) = M.forward(M.round_weights(w), x, rnd=M.bf16_round)
+    W1, b1, W2, b2, W3, b3 = M.unpack(M.round_weights(w))
+    return M.Y_SCALE * (BF16_U * np.abs(a2) + 1.1 * (BF16_U * np.abs(a1)) @ np.abs(W2).T) @ np.abs(W3)
+
+
+def check_forward(w, x, y_gpu):
+    xb = M.bf16_round(x).astype(np.float64)
+    y_o, _ = M.forward(M.round_weights(w), xb, rnd=M.bf16_round)
+    d = np.abs(np.asarray(y_gpu, np.float64) - y_o)
+    bound = fwd_bound(w, xb)
+    print("forward: max |dy| %.3e, max dy/bound %.3f, rms/std %.4f" %
+          (d.max(), np.max(d / bound), np.sqrt(np.mean(d ** 2)) / y_o.std()))
+    assert np.all(d <= 0.25 * bound + 1e-6), np.max(d / bound)
+    assert np.sqrt(np.mean(d ** 2)) <= 0.02 * y_o.std()
+    return y_o
+
+
+# ---------------------------------------------------------------- features
+
+FEAT_CASES = {
+    "lattice16": lambda: (np.concatenate([inputs.lattice(16), np.full((4096, 1), 0.25)], 1).astype(np.float32)),
+    "uniform16": lambda: workload("uniform", 16)["pos_h"],
+    "clustered3000": lambda: workload("clustered", 3000, 11)["pos_h"],
+    "sedov24": lambda: inputs.sedov(24)["pos_h"],
+}
+
+
+@pytest.mark.parametrize("case", list(FEAT_CASES))
+def test_features_match_oracle(case):
+    pos = np.ascontiguousarray(FEAT_CASES[case](), np.float32)
+    n = pos.shape[0]
+    r = np.random.default_rng(7)
+    gradv = r.normal(0, 0.5, (n, 3, 3)).astype(np.float32)
+    N = r.uniform(150, 400, n).astype(np.float32)
+    conv = pos.copy()
+    conv[:, 3] *= r.uniform(0.8, 1.25, n).astype(np.float32)
+    ctx = crk.crk_create()
+    feat, target = crk.crk_h_features(ctx, dev(pos), dev(gradv), dev(N), dev(conv))
+    g = as_np(feat).astype(np.float64)
+    divv = gradv[:, 0, 0].astype(np.float64) + gradv[:, 1, 1] + gradv[:, 2, 2]
+    o = M.features(pos, N_prev=N, divv=divv)
+    np.testing.assert_allclose(g[:, :5], o[:, :5], rtol=2e-7, atol=0)
+    d5 = np.abs(g[:, 5] - o[:, 5])
+    assert np.all(d5 <= 1e-6 * (1 + np.abs(o[:, 5]))), (d5.max(), g[np.argmax(d5)], o[np.argmax(d5)])
+    np.testing.assert_allclose(g[:, 6], o[:, 6], rtol=1e-6, atol=4e-7 * np.abs(o[:, 6]).max())
+    np.testing.assert_allclose(g[:, 7], o[:, 7], rtol=0, atol=4e-7)
+    h_ref = pos[:, 3].astype(np.float64) * np.cbrt(268.0 / N.astype(np.float64))
+    t_o = np.log(conv[:, 3].astype(np.float64) / h_ref)
+    np.testing.assert_allclose(as_np(target), t_o, rtol=0, atol=5e-7)
+    # without gradv / Nngb the two features are zero
+    f2 = as_np(crk.crk_h_features(ctx, dev(pos)))
+    assert not np.any(f2[:, 6:]) and np.array_equal(f2[:, :6], as_np(feat)[:, :6])
+
+
+def test_features_reject_invalid_records():
+    pos = workload("uniform", 16)["pos_h"].copy()
+    pos[5, 0] = 1.0
+    ctx = crk.crk_create()
+    with pytest.raises(crk.CrkError) as ei:
+        crk.crk_h_features(ctx, dev(pos))
+    assert ei.value.code == -1
+    pos[5, 0] = 0.5
+    pos[9, 3] = np.nan
+    with pytest.raises(crk.CrkError):
+        crk.crk_h_features(ctx, dev(pos))
+
+
+# ---------------------------------------------------------------- network
+
+@pytest.mark.parametrize("n", [1, 17, 5003])
+def test_forward_matches_declared_oracle(n):
+    """Ragged sizes: a partial 16-row tile and a partial 8-warp block."""
+    w = rand_weights(1)
+    x = rand_features(n, 2)
+    ctx = crk.crk_create()
+    crk.crk_mlp_set_weights(ctx, dev(w))
+    y = as_np(crk.crk_mlp_forward(ctx, dev(x)))
+    if n > 100:
+        check_forward(w, x, y)
+    else:
+        xb = M.bf16_round(x).astype(np.float64)
+        y_o, _ = M.forward(M.round_weights(w), xb, rnd=M.bf16_round)
+        assert np.all(np.abs(y - y_o) <= 0.25 * fwd_bound(w, xb) + 1e-6)
+
+
+def test_forward_single_path_network():
+    """Only W1[3,5], W2[7,3], W3[7] set: y = s_y (2 silu(silu(x5)) + b3) up to BF16 rounding."""
+    w = np.zeros(M.N_PARAM, np.float32)
+    w[3 * 8 + 5] = 1.0
+    w[576 + 7 * 64 + 3] = 1.0
+    w[4736 + 7] = 2.0
+    w[4800] = 0.25
+    x = np.zeros((64, 8), np.float32)
+    x[:, 5] = np.linspace(-4, 4, 64)
+    x[:, 2] = 9.0
+    ctx = crk.crk_create()
+    crk.crk_mlp_set_weights(ctx, dev(w))
+    y = as_np(crk.crk_mlp_forward(ctx, dev(x))).astype(np.float64)
+    xb = M.bf16_round(x[:, 5]).astype(np.float64)
+    a = M.bf16_round(M.silu(xb)).astype(np.float64)
+    e = (2.0 * M.bf16_round(M.silu(a)).astype(np.float64) + 0.25) * M.Y_SCALE
+    d = np.abs(y - e)
+    assert np.all(d <= 2 * 2.0 ** -8 * (np.abs(e) + M.Y_SCALE)), np.stack([x[:, 5], y, e], 1)[np.argsort(-d)[:5]]
+
+
+def test_gradient_matches_oracle():
+    """Full-batch gradient (lr = 0) over a ragged batch against the declared-
+    arithmetic oracle and the FP64 oracle, block by block."""
+    n = 3001
+    w = rand_weights(3)
+    x = rand_features(n, 4)
+    ctx = crk.crk_create()
+    crk.crk_mlp_set_weights(ctx, dev(w))
+    xb = M.bf16_round(x).astype(np.float64)
+    y_o, _ = M.forward(M.round_weights(w), xb, rnd=M.bf16_round)
+    t = (y_o + np.random.default_rng(5).normal(0, 0.3, n)).astype(np.float32)
+    g, loss = crk.crk_mlp_train_step(ctx, dev(x), dev(t), lr=0.0)
+    g = as_np(g).astype(np.float64)
+    L_d, g_d = M.loss_and_grad(M.round_weights(w), xb, t, rnd=M.bf16_round)
+    L_64, g_64 = M.loss_and_grad(M.round_weights(w), xb, t)
+    assert abs(float(as_np(loss)[0]) - L_d) <= 1e-2 * L_d
+    blocks = (("W1", 0, 512), ("b1", 512, 576), ("W2", 576, 4672), ("b2", 4672, 4736), ("W3", 4736, 4800),
+              ("b3", 4800, 4801))
+    for name, a, b in blocks:
+        for ref, lim in ((g_d, 3e-2), (g_64, 4e-2)):
+            rel = np.linalg.norm(g[a:b] - ref[a:b]) / np.linalg.norm(ref[a:b])
+            print(name, "rel L2 %.2e" % rel)
+            assert rel <= lim, (name, rel)
+    # lr = 0 leaves the weights unchanged
+    np.testing.assert_array_equal(as_np(crk.crk_mlp_get_weights(ctx)), w)
+
+
+def test_first_adam_step_is_normalised_gradient():
+    """At t = 1 Adam's bias-corrected step is lr g / (|g| + eps) (Kingma & Ba 2015)."""
+    n = 1000
+    w = rand_weights(5)
+    x = rand_features(n, 6)
+    t = np.random.default_rng(7).normal(0, 0.2, n).astype(np.float32)
+    ctx = crk.crk_create()
+    crk.crk_mlp_set_weights(ctx, dev(w))
+    lr = 1e-3
+    g, _ = crk.crk_mlp_train_step(ctx, dev(x), dev(t), lr=lr)
+    g = as_np(g).astype(np.float64)
+    w1 = as_np(crk.crk_mlp_get_weights(ctx)).astype(np.float64)
+    expect = w - lr * g / (np.abs(g) + 1e-8)
+    d = np.abs(w1 - expect)
+    k = np.argsort(-(d / (1e-6 * lr + 2.0 ** -22 * np.abs(w))))[:5]
+    assert np.all(d <= 1e-6 * lr + 2.0 ** -22 * np.abs(w)), np.stack([k, w[k], w1[k], expect[k], g[k]], 1)
+
+
+def test_training_reduces_loss_on_a_known_map():
+    """The sampled-batch trainer fits a smooth target of the features."""
+    n = 20000
+    x = rand_features(n, 8)
+    t = (-x[:, 7] / 30.0 + 0.005 * np.tanh(x[:, 6])).astype(np.float32)
+    ctx = crk.crk_create()
+    losses = learned_h.train(ctx, dev(x), dev(t), steps=600, batch=2048, lr=2e-3)
+    assert len(losses) == 600 and np.all(np.isfinite(losses))
+    assert np.mean(losses[-50:]) < 0.05 * np.mean(losses[:10]), (losses[:3], losses[-3:])
+
+
+# ---------------------------------------------------------------- proposal
+
+def test_proposal_matches_oracle_and_judge():
+    st = workload("clustered", 3000, 11)
+    pos = st["pos_h"].copy()
+    n = pos.shape[0]
+    ctx = crk.crk_create()
+    g = dev(pos)
+    crk.crk_build_cells(ctx, g)
+    V, N = crk.crk_volumes(ctx)
+    gradv = crk.crk_corrections(ctx, V, dev(st["vel_u"]))[4]
+    w = rand_weights(9)
+    w[4736:4800] *= 0.1
+    crk.crk_mlp_set_weights(ctx, dev(w))
+    feat = crk.crk_h_features(ctx, g, gradv, N)
+    y = as_np(crk.crk_mlp_forward(ctx, feat)).astype(np.float64)
+    d = np.abs(np.cbrt(268.0 / as_np(N).astype(np.float64)) - 1.0)
+    tol = float(np.median(d))            # half the particles are judged converged
+    p = g.clone()
+    crk.crk_h_propose(ctx, p, gradv, N, tol=tol)
+    h0 = pos[:, 3].astype(np.float64)
+    h1 = as_np(p)[:, 3].astype(np.float64)
+    np.testing.assert_array_equal(as_np(p)[:, :3], pos[:, :3])
+    keep = d <= tol - 1e-6
+    move = d > tol + 1e-6
+    assert keep.sum() > 0 and move.sum() > 0
+    np.testing.assert_array_equal(h1[keep], h0[keep])
+    expect = np.clip(h0 * np.cbrt(268.0 / as_np(N).astype(np.float64)) * np.exp(y), 1e-6, 0.3)
+    np.testing.assert_allclose(h1[move], expect[move], rtol=3e-6)
+    check_forward(w, as_np(feat), y)
+
+
+def test_proposal_requires_weights_and_handles_empty():
+    ctx = crk.crk_create()
+    pos = dev(workload("uniform", 16)["pos_h"])
+    with pytest.raises(crk.CrkError) as ei:
+        crk.crk_h_propose(ctx, pos)
+    assert ei.value.code == -7
+    crk.crk_mlp_set_weights(ctx, dev(rand_weights(0)))
+    empty = torch.empty((0, 4), dtype=torch.float32, device="cuda")
+    crk.crk_h_propose(ctx, empty)
+    assert crk.crk_h_features(ctx, empty).shape == (0, 8)
+
+
+def test_select_rows_matches_judge():
+    r = np.random.default_rng(3)
+    n = 70001
+    N = r.uniform(200, 340, n).astype(np.float32)
+    d = np.abs(np.cbrt(268.0 / N.astype(np.float64)) - 1.0)
+    tol = 0.03
+    ok = np.abs(d - tol) > 1e-6
+    N = N[ok]
+    d = d[ok]
+    ctx = crk.crk_create()
+    rows = as_np(crk.crk_h_select(ctx, dev(N), tol=tol, base=123))
+    np.testing.assert_array_equal(rows, np.nonzero(d > tol)[0] + 123)
+    assert crk.crk_h_select(ctx, dev(N), tol=10.0).shape == (0,)
+
+
+@pytest.fixture(scope="module")
+def sedov_data():
+    snaps, probe = learned_h.sedov_snapshots(n_side=32, steps=120, every=10)
+    return snaps, probe
+
+
+def test_learned_proposal_saves_iterations(sedov_data):
+    """Trained on half of the snapshots of a Sedov run, the proposal starts the
+    fixed-point iteration closer to eq:hi on the other half: fewer iterations
+    at the same tolerance than from the evolved h, and every particle still
+    meets it.  The constant-density reference alone (all-zero network) is
+    reported beside it."""
+    snaps, probe = sedov_data
+    train, held = snaps[0::2], snaps[1::2]
+    ctx = crk.crk_create()
+    feat, target, rows = learned_h.dataset(ctx, train)
+    losses = learned_h.train(ctx, feat, target, rows, steps=1500, batch=4096, lr=1e-3)
+    var = float(torch.mean(target[rows.long()] ** 2))
+    print("rows %d, mean target^2 %.3e, first loss %.3e, last loss %.3e" %
+          (rows.shape[0], var, losses[0], np.mean(losses[-50:])))
+    assert np.mean(losses[-50:]) < var
+    w = crk.crk_mlp_get_weights(ctx)
+    ref = crk.crk_create()
+    learned_h.zero_network(ref)
+    crk.crk_mlp_set_weights(probe, w)
+    plain, reference, learned = [], [], []
+    for s in held:
+        it_r, ok_r, _ = s.solve_from_proposal(ref)
+        it, ok, p = s.solve_from_proposal(probe)
+        assert ok and ok_r and s.ok_plain
+        plain.append(s.it_plain)
+        reference.append(it_r)
+        learned.append(it)
+        crk.crk_build_cells(probe, p)
+        _, N = crk.crk_volumes(probe)
+        dN = np.abs(np.cbrt(268.0 / as_np(N).astype(np.float64)) - 1.0)
+        hp = as_np(p)[:, 3]
+        assert np.all((dN <= 1e-4 + 2e-6) | (hp == np.float32(0.3))), dN.max()
+    print("iterations: plain", plain, "reference only", reference, "learned", learned)
+    assert sum(learned) < sum(plain)

@@ -43,7 +43,7 @@ def test_silu_special_values():
 
 
 def test_single_path_network_is_double_silu():
-    """Only W1[3,5], W2[7,3], W3[7] set: y = 2 silu(silu(x5)) + b3."""
+    """Only W1[3,5], W2[7,3], W3[7] set: y = s_y (2 silu(silu(x5)) + b3)."""
     w = np.zeros(M.N_PARAM)
     W1, b1, W2, b2, W3, _ = M.unpack(w)   # views into w
     W1[3, 5] = 1.0
@@ -56,7 +56,7 @@ def test_single_path_network_is_double_silu():
     y, _ = M.forward(w, x)
     sig = lambda v: 1.0 / (1.0 + np.exp(-v))
     a = x[:, 5] * sig(x[:, 5])
-    expect = 2.0 * a * sig(a) + 0.25
+    expect = (2.0 * a * sig(a) + 0.25) / 64.0
     np.testing.assert_allclose(y, expect, rtol=1e-14, atol=1e-15)
 
 
@@ -95,6 +95,31 @@ def test_loss_is_zero_at_target_and_gradient_vanishes():
     y, _ = M.forward(w, x)
     L, g = M.loss_and_grad(w, x, y)
     assert L == 0.0 and not np.any(g)
+
+
+def test_declared_precision_network():
+    """rnd = identity is the FP64 network; rnd = bf16_round stays within the
+    first-order bound of rounding every hidden activation by half a BF16 ulp."""
+    w = M.round_weights(_rand_w(seed=4))
+    x = M.bf16_round(np.random.default_rng(5).normal(0, 1.5, (200, 8)))
+    y, (z1, a1, z2, a2) = M.forward(w, x)
+    yi, _ = M.forward(w, x, rnd=lambda a: a)
+    np.testing.assert_array_equal(y, yi)
+    yb, _ = M.forward(w, x, rnd=M.bf16_round)
+    W1, b1, W2, b2, W3, b3 = M.unpack(w)
+    u = 2.0 ** -9
+    bound = M.Y_SCALE * (u * np.abs(a2) + 1.1 * (u * np.abs(a1)) @ np.abs(W2).T) @ np.abs(W3)
+    assert np.all(np.abs(yb - y) <= 1.01 * bound + 1e-15)
+    assert np.any(yb != y)
+    # weight rounding leaves the biases and rounds every matrix entry
+    w0 = _rand_w(seed=4)
+    assert np.array_equal(w[512:576], w0[512:576]) and w[4800] == w0[4800]
+    assert np.array_equal(w[576:4672], M.bf16_round(w0[576:4672]))
+    # the rounded-delta gradient differs from the FP64 one by BF16-level amounts only
+    t = np.random.default_rng(6).normal(0, 0.3, 200)
+    _, g = M.loss_and_grad(w, x, t)
+    _, gb = M.loss_and_grad(w, x, t, rnd=M.bf16_round)
+    assert 0 < np.linalg.norm(gb - g) <= 2e-2 * np.linalg.norm(g)
 
 
 def test_grid_level():

@@ -390,6 +390,18 @@ def test_h_iteration_converges_to_target_neighbour_count():
     assert np.max(np.abs(np.cbrt(268.0 / N) - 1.0)) <= 1e-4 + 1e-12
 
 
+def test_h_iteration_stops_at_the_h_bound():
+    """With h_max below the solution of eq:hi every update is clamped back to
+    h_max: the particles are done at the bound after one pass."""
+    side = 16
+    pos = np.concatenate([inputs.lattice(side), np.full((side ** 3, 1), 3.0 / side)], 1).astype(np.float32)
+    h, it, done = O.h_iterate(pos, tol=1e-4, max_it=20, h_max=3.0 / side)
+    assert it == 1 and done.all() and np.all(h == np.float32(3.0 / side))
+    # without the bound the same start converges to N_res in several passes
+    h2, it2, done2 = O.h_iterate(pos, tol=1e-4, max_it=60)
+    assert done2.all() and it2 > 3 and np.all(h2 > np.float32(3.0 / side))
+
+
 def test_cfl_of_gas_at_rest_is_sound_crossing():
     st = perfect_lattice(14, h_spacings=3.5)
     ev = O.evaluate(st, k=0)

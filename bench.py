@@ -182,6 +182,101 @@ def run_reference(args):
     return 0
 
 
+# --------------------------------------------------------------------- learned h
+
+MLP_TENSOR_FLOPS_PER_ROW = 2 * (8 * 64 + 64 * 64)   # the two BF16 tensor-core products per row
+
+
+def learned_h_report(dev, train_side=64, train_steps=200, every=10, eval_side=256, eval_steps=10, tol=1e-4):
+    """Learned smoothing-length proposal: train on snapshots of a Sedov run,
+    then solve eq:hi at a larger Sedov state plainly and from the proposal."""
+    import torch
+    from paper_2202_02840_gb300 import crk, inputs, learned_h
+
+    def wall(f):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        r = f()
+        torch.cuda.synchronize(dev)
+        return r, 1e3 * (time.perf_counter() - t0)
+
+    (snaps, probe), data_ms = wall(lambda: learned_h.sedov_snapshots(n_side=train_side, steps=train_steps,
+                                                                    every=every, tol=tol))
+    ctx = crk.crk_create()
+    feat, target, rows = learned_h.dataset(ctx, snaps)
+    crk.crk_profile(ctx, True)
+    steps = 2000
+    losses, train_ms = wall(lambda: learned_h.train(ctx, feat, target, rows, steps=steps, batch=4096, lr=1e-3))
+    pm, pc, _ = crk.crk_profile_read(ctx)
+    crk.crk_profile(ctx, False)
+    w = crk.crk_mlp_get_weights(ctx)
+    sel_t = target[rows.long()]
+    train = {"workload": "sedov-%d^3, %d KDK steps, a snapshot every %d" % (train_side, train_steps, every),
+             "snapshots": len(snaps), "rows": int(feat.shape[0]), "selected_rows": int(rows.shape[0]),
+             "adam_steps": steps, "batch": 4096, "loss_first": losses[0], "loss_last50": float(np.mean(losses[-50:])),
+             "mean_target_sq_selected": float(torch.mean(sel_t * sel_t)),
+             "train_step_ms": pm["mlp train step"] / max(1, pc["mlp train step"]), "train_wall_ms": train_ms,
+             "data_wall_ms": data_ms, "plain_iterations": [s.it_plain for s in snaps]}
+    del snaps, feat, target, rows
+    probe.close()
+
+    st = inputs.sedov(eval_side)
+    pos = torch.from_numpy(st["pos_h"]).to(dev)
+    vel = torch.from_numpy(st["vel_u"]).to(dev)
+    mass = torch.from_numpy(st["mass"]).to(dev)
+    stepper = crk.crk_create()
+    for _ in range(eval_steps):
+        dt = crk.crk_step(stepper, pos, vel, mass, 0.0, diag=True)["dt"]
+    stepper.close()
+    del st
+    ev = crk.crk_create()
+    crk.crk_build_cells(ev, pos)
+    V, N = crk.crk_volumes(ev)
+    gradv = crk.crk_corrections(ev, V, vel)[4]
+    del V
+    n = pos.shape[0]
+
+    def solve(weights):
+        p = pos.clone()
+        t_prop = 0.0
+        if weights is not None:
+            crk.crk_mlp_set_weights(ev, weights)
+            crk.crk_profile(ev, True)
+            crk.crk_h_propose(ev, p, gradv, N, dt=dt, tol=tol)
+            pm, pc, _ = crk.crk_profile_read(ev)
+            crk.crk_profile(ev, False)
+            t_prop = pm["h proposal"] / max(1, pc["h proposal"])
+        (it, ok), ms = wall(lambda: crk.crk_h_iterate(ev, p, tol=tol, max_it=60))
+        return it, ok, ms, t_prop, p
+
+    it_p, ok_p, ms_p, _, p_conv = solve(None)
+    it_r, ok_r, ms_r, _, _ = solve(torch.zeros_like(w))
+    it_l, ok_l, ms_l, prop_ms, _ = solve(w)
+    # accuracy of the network on this state: residual of log h against the converged h
+    f, t = crk.crk_h_features(ev, pos, gradv, N, p_conv, dt=dt)
+    sel = crk.crk_h_select(ev, N, tol=tol).long()
+    crk.crk_mlp_set_weights(ev, w)
+    y = crk.crk_mlp_forward(ev, f)
+    rms_ref = float(torch.sqrt(torch.mean(t[sel] ** 2))) if sel.numel() else 0.0
+    rms_net = float(torch.sqrt(torch.mean((t[sel] - y[sel]) ** 2))) if sel.numel() else 0.0
+    peaks = measured_peaks()
+    bf16 = float(peaks.get("bf16_tflops", 1900.0))
+    tflops = MLP_TENSOR_FLOPS_PER_ROW * n / (prop_ms / 1e3) / 1e12
+    ev.close()
+    return {"train": train,
+            "eval": {"workload": "sedov-%d^3 after %d KDK steps (evolved h)" % (eval_side, eval_steps), "n": n,
+                     "tol": tol, "selected_rows": int(sel.numel()),
+                     "iterations_plain": it_p, "iterations_reference_only": it_r, "iterations_learned": it_l,
+                     "converged": [ok_p, ok_r, ok_l],
+                     "solve_ms_plain": ms_p, "solve_ms_reference_only": ms_r, "solve_ms_learned": ms_l,
+                     "rms_log_h_error_reference": rms_ref, "rms_log_h_error_learned": rms_net,
+                     "proposal_ms": prop_ms, "proposal_rows_per_s": n / (prop_ms / 1e3),
+                     "proposal_roofline": {"bound": "tensor", "achieved": tflops, "peak": bf16, "unit": "TFLOP/s",
+                                           "frac": tflops / bf16,
+                                           "note": "BF16 mma.sync flops of the two hidden products per row; "
+                                                   "the pass also evaluates 128 SFU tanh per row"}}}
+
+
 # --------------------------------------------------------------------- GPU arm
 
 def run_gpu(args):
@@ -239,6 +334,7 @@ def run_gpu(args):
     crk.crk_profile(ctx, False)
     clk = clocks.stop()
     ntiles, entries, utp = crk.crk_build_stats(ctx)
+    ctx.close()
 
     # ---------------- end to end through host buffers (pinned), same step count
     h_pos = torch.from_numpy(st["pos_h"]).pin_memory()
@@ -318,6 +414,8 @@ def run_gpu(args):
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": n * 36,
                         "d2h_bytes_per_step": n * 32},
                 "gpu_launches": launches, "clocks": clk}
+        if not args.no_learned_h and world == 1:
+            line["learned_h"] = learned_h_report(dev)
         if not args.no_cpu_baseline and world == 1:
             from oracle import crk as O
             p, dt, ns = calibrated_oracle(st, args.cpu_seconds, seed=2)
@@ -325,7 +423,6 @@ def run_gpu(args):
                                     "sample": "FP64 oracle passes P1,P2,P3,P4,P5,P5 on %d random target "
                                               "particles of the workload (%.1f s)" % (ns, dt)}
         print(json.dumps(line))
-    ctx.close()
     if dist is not None:
         dist.destroy_process_group()
     return 0
@@ -341,6 +438,7 @@ def main():
     ap.add_argument("--precision", type=int, default=1, choices=[0, 1, 2])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-learned-h", action="store_true", help="skip the learned-h training and evaluation")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -285,7 +285,9 @@ int crk_volumes_noalloc(int n, const float *pos_h, float *V, float *Nngb, void *
  *   0 log(1 + own cell count)        1 log(1 + sum of the 6 face cells)
  *   2 log(1 + sum of the 12 edge cells) 3 log(1 + sum of the 8 corner cells)
  *   4 log(1 + sum of all 27 cells)   5 log(h / Delta), Delta = N^(-1/3)
- *   6 h div v (trace of gradv; 0 without gradv)
+ *   6 dt div v (div v = trace of gradv, dt the step that led to the state;
+ *     0 without gradv): the compression h div v made dimensionless by the
+ *     step, so that it transfers between resolutions
  *   7 log(Nngb / N_res) (0 without Nngb)
  * Network: y = s_y (W3 . silu(W2 silu(W1 x + b1) + b2) + b3), sizes 8 -> 64
  * -> 64 -> 1, silu(z) = z / (1 + e^-z), s_y = CRK_MLP_YSCALE a fixed output
@@ -313,14 +315,14 @@ int crk_mlp_set_weights(crk_ctx *ctx, const float *w, void *stream);
 int crk_mlp_get_weights(crk_ctx *ctx, float *w, void *stream);
 
 /* Features of n particles.  pos_h[4n] in; gradv[9n] and Nngb[n] (device, may
- * be NULL) in; feat[8n] out.  With pos_conv[4n] (the same particles with the
+ * be NULL) and the step dt >= 0 in; feat[8n] out.  With pos_conv[4n] (the same particles with the
  * converged h in the w column) also target[n] = log(h_conv / h_ref), where
  * h_ref = h_prev (N_res / Nngb)^(1/3) with Nngb (the constant-density
  * solution of eq:hi, which the proposal starts from) and h_ref = h_prev
  * without; pos_conv and target are both NULL or both set.  CRK_EINVAL for
  * coordinates outside [0,1) or h outside (0,1).  Synchronises `stream` once
  * to check the records. */
-int crk_h_features(crk_ctx *ctx, int n, const float *pos_h, const float *gradv, const float *Nngb,
+int crk_h_features(crk_ctx *ctx, int n, const float *pos_h, const float *gradv, const float *Nngb, float dt,
                    const float *pos_conv, float *feat, float *target, void *stream);
 
 /* Network output y[n] (device) for the feature rows feat[8n] (device). */
@@ -328,13 +330,13 @@ int crk_mlp_forward(crk_ctx *ctx, int n, const float *feat, float *y, void *stre
 
 /* Proposal, in place: the h column of pos_h[4n] (device) becomes
  * clamp(h_ref exp(y), h_min, h_max), y the network output for the particle's
- * features (computed in the same kernel from pos_h, gradv, Nngb as for
+ * features (computed in the same kernel from pos_h, gradv, Nngb, dt as for
  * crk_h_features) and h_ref as there: the network corrects the
  * constant-density estimate h (N_res / Nngb)^(1/3) (h without Nngb).  A
  * particle whose Nngb already satisfies |(N_res / Nngb)^(1/3) - 1| <= tol
  * keeps its h (the judge of crk_h_iterate).  Synchronises `stream` once to
  * check the records; on CRK_EINVAL the h column is unspecified. */
-int crk_h_propose(crk_ctx *ctx, int n, float *pos_h, const float *gradv, const float *Nngb, float tol,
+int crk_h_propose(crk_ctx *ctx, int n, float *pos_h, const float *gradv, const float *Nngb, float dt, float tol,
                   void *stream);
 
 /* One full-batch step over the n rows feat[8n], target[n] (device): the

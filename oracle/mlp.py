@@ -11,7 +11,10 @@ fixed-point coordinate, counts over the periodic grid (an offset that wraps
 onto the same cell counts again):
   f0 log1p(own cell)      f1 log1p(6 face cells)   f2 log1p(12 edge cells)
   f3 log1p(8 corner cells) f4 log1p(all 27)        f5 log(h_prev / N^(-1/3))
-  f6 h_prev * div v        f7 log(N_prev / N_res)
+  f6 dt * div v            f7 log(N_prev / N_res)
+(f6 is the compression h div v made dimensionless by the step, (dt / h) h div v:
+h div v itself carries the flow's velocity scale, which grows with resolution
+in the Sedov runs, and does not transfer from one resolution to another)
 network: y = s_y (W3 . silu(W2 silu(W1 x + b1) + b2) + b3), silu(z) = z sigmoid(z),
 s_y = 2^-6 a fixed output scale (log-h corrections are of order 1%, which
 keeps the network's own outputs of order one), W1 64x8, W2 64x64, W3 64,
@@ -51,7 +54,7 @@ def unpack(w):
     return W1, b1, W2, b2, W3, b3
 
 
-def features(pos_h, N_prev=None, divv=None, kf=None, N_res=268.0):
+def features(pos_h, N_prev=None, divv=None, dt=0.0, kf=None, N_res=268.0):
     pos = np.asarray(pos_h, np.float32).reshape(-1, 4)
     n = pos.shape[0]
     kf = grid_level(n) if kf is None else kf
@@ -83,7 +86,7 @@ def features(pos_h, N_prev=None, divv=None, kf=None, N_res=268.0):
     f[:, 3] = np.log1p(corner)
     f[:, 4] = np.log1p(own + face + edge + corner)
     f[:, 5] = np.log(h * float(n) ** (1.0 / 3.0))
-    f[:, 6] = 0.0 if divv is None else h * np.asarray(divv, np.float64)
+    f[:, 6] = 0.0 if divv is None else float(dt) * np.asarray(divv, np.float64)
     f[:, 7] = 0.0 if N_prev is None else np.log(np.asarray(N_prev, np.float64) / N_res)
     return f
 

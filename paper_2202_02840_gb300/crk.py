@@ -72,9 +72,9 @@ def lib():
         L.crk_volumes_noalloc.argtypes = [_ci, _vp, _vp, _vp, _vp]
         L.crk_mlp_set_weights.argtypes = [_vp, _vp, _vp]
         L.crk_mlp_get_weights.argtypes = [_vp, _vp, _vp]
-        L.crk_h_features.argtypes = [_vp, _ci, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
+        L.crk_h_features.argtypes = [_vp, _ci, _vp, _vp, _vp, ctypes.c_float, _vp, _vp, _vp, _vp]
         L.crk_mlp_forward.argtypes = [_vp, _ci, _vp, _vp, _vp]
-        L.crk_h_propose.argtypes = [_vp, _ci, _vp, _vp, _vp, ctypes.c_float, _vp]
+        L.crk_h_propose.argtypes = [_vp, _ci, _vp, _vp, _vp, ctypes.c_float, ctypes.c_float, _vp]
         L.crk_mlp_train_step.argtypes = [_vp, _ci, _vp, _vp, ctypes.c_float, _vp, _vp, _vp]
         L.crk_mlp_train.argtypes = [_vp, _ci, _vp, _vp, _vp, _ci, _ci, _ci, ctypes.c_float, ctypes.c_ulonglong,
                                     _vp, _vp]
@@ -339,14 +339,14 @@ def crk_mlp_get_weights(ctx, stream=None):
     return w
 
 
-def crk_h_features(ctx, pos_h, gradv=None, Nngb=None, pos_conv=None, stream=None):
+def crk_h_features(ctx, pos_h, gradv=None, Nngb=None, pos_conv=None, dt=0.0, stream=None):
     """Features (n, 8); with pos_conv also the targets log(h_conv / h_prev) -> (feat, target)."""
     n = pos_h.shape[0]
     dev = pos_h.device
     feat = torch.empty((n, MLP_NFEAT), dtype=torch.float32, device=dev)
     target = torch.empty(n, dtype=torch.float32, device=dev) if pos_conv is not None else None
     ctx.check(lib().crk_h_features(ctx.handle, n, _t(pos_h, (n, 4), "pos_h"), _opt(gradv, (n, 3, 3), "gradv"),
-                                   _opt(Nngb, (n,), "Nngb"), _opt(pos_conv, (n, 4), "pos_conv"),
+                                   _opt(Nngb, (n,), "Nngb"), float(dt), _opt(pos_conv, (n, 4), "pos_conv"),
                                    _vp(feat.data_ptr()), _vp(None if target is None else target.data_ptr()),
                                    _stream(stream)))
     return (feat, target) if pos_conv is not None else feat
@@ -360,11 +360,11 @@ def crk_mlp_forward(ctx, feat, stream=None):
     return y
 
 
-def crk_h_propose(ctx, pos_h, gradv=None, Nngb=None, tol=1e-4, stream=None):
+def crk_h_propose(ctx, pos_h, gradv=None, Nngb=None, dt=0.0, tol=1e-4, stream=None):
     """Write the proposed h into pos_h[:, 3] in place."""
     n = pos_h.shape[0]
     ctx.check(lib().crk_h_propose(ctx.handle, n, _t(pos_h, (n, 4), "pos_h"), _opt(gradv, (n, 3, 3), "gradv"),
-                                  _opt(Nngb, (n,), "Nngb"), float(tol), _stream(stream)))
+                                  _opt(Nngb, (n,), "Nngb"), float(dt), float(tol), _stream(stream)))
 
 
 def crk_mlp_train_step(ctx, feat, target, lr=0.0, stream=None):

@@ -7,7 +7,8 @@
 //
 //   features  8 per particle from the occupancy of the 27 cells around the
 //             particle on a fixed grid of side 2^-kf >= 4 N^(-1/3), the
-//             previous h, h div v and the previous neighbour count;
+//             previous h, the compression over the last step dt div v and
+//             the previous neighbour count;
 //   network   y = s_y (W3 . silu(W2 silu(W1 x + b1) + b2) + b3), 8 -> 64 -> 64 -> 1,
 //             s_y = 2^-6 a fixed output scale,
 //             BF16 weights and layer inputs, FP32 accumulation and biases, on
@@ -83,6 +84,7 @@ struct FeatArgs {
     const float *gradv;      // 9n or null (div v = trace)
     const float *Nngb;       // n or null
     const int32_t *fcnt;     // 8^kf cell counts
+    float dt;                // step of the state (feature 6 = dt div v)
     float log_cbrt_n;        // log(N^(1/3)) = -log(Delta)
     float inv_N_res;
     float N_res;
@@ -170,7 +172,7 @@ __device__ __forceinline__ float2 quad_features(const FeatArgs &a, int i, int t,
             const float *gv = a.gradv + 9 * (size_t)i;
             dv = __ldg(gv) + __ldg(gv + 4) + __ldg(gv + 8);
         }
-        f.x = h * dv;
+        f.x = a.dt * dv;
         f.y = a.Nngb ? logf(N * a.inv_N_res) : 0.f;
     }
     return f;
@@ -656,9 +658,11 @@ int check_records(crk_ctx *ctx, cudaStream_t s) {
     return CRK_OK;
 }
 
-FeatArgs feat_args(const crk_ctx *ctx, int n, const float *pos_h, const float *gradv, const float *Nngb, int kf) {
+FeatArgs feat_args(const crk_ctx *ctx, int n, const float *pos_h, const float *gradv, const float *Nngb, float dt,
+                   int kf) {
     FeatArgs a;
     a.n = n;
+    a.dt = dt;
     a.kf = kf;
     a.pos_h = reinterpret_cast<const float4 *>(pos_h);
     a.gradv = gradv;
@@ -789,18 +793,19 @@ extern "C" int crk_mlp_get_weights(crk_ctx *ctx, float *w, void *stream) {
 }
 
 extern "C" int crk_h_features(crk_ctx *ctx, int n, const float *pos_h, const float *gradv, const float *Nngb,
-                              const float *pos_conv, float *feat, float *target, void *stream) {
+                              float dt, const float *pos_conv, float *feat, float *target, void *stream) {
     if (!ctx) return CRK_EINVAL;
     if (n < 0 || n > (1 << 30)) return crk_set_error(ctx, CRK_EINVAL, "bad n");
     if (n == 0) return CRK_OK;
     if (!pos_h || !feat) return crk_set_error(ctx, CRK_EINVAL, "null pos_h or feat");
+    if (!(dt >= 0.f)) return crk_set_error(ctx, CRK_EINVAL, "bad dt");
     if ((pos_conv == nullptr) != (target == nullptr))
         return crk_set_error(ctx, CRK_EINVAL, "pos_conv and target go together");
     cudaStream_t s = (cudaStream_t)stream;
     int kf = feature_level(n);
     int rc = count_cells(ctx, n, reinterpret_cast<const float4 *>(pos_h), kf, s);
     if (rc) return rc;
-    FeatArgs fa = feat_args(ctx, n, pos_h, gradv, Nngb, kf);
+    FeatArgs fa = feat_args(ctx, n, pos_h, gradv, Nngb, dt, kf);
     k_features<<<grid_for(4ll * n, 256), 256, 0, s>>>(fa, reinterpret_cast<const float4 *>(pos_conv), feat, target);
     ++ctx->launches;
     CRK_LAUNCH_CHECK(ctx, "features");
@@ -823,19 +828,19 @@ extern "C" int crk_mlp_forward(crk_ctx *ctx, int n, const float *feat, float *y,
     return CRK_OK;
 }
 
-extern "C" int crk_h_propose(crk_ctx *ctx, int n, float *pos_h, const float *gradv, const float *Nngb, float tol,
-                             void *stream) {
+extern "C" int crk_h_propose(crk_ctx *ctx, int n, float *pos_h, const float *gradv, const float *Nngb, float dt,
+                             float tol, void *stream) {
     int rc = need_weights(ctx);
     if (rc) return rc;
     if (n < 0 || n > (1 << 30)) return crk_set_error(ctx, CRK_EINVAL, "bad n");
     if (n == 0) return CRK_OK;
-    if (!pos_h || !(tol >= 0.f)) return crk_set_error(ctx, CRK_EINVAL, "null pos_h or bad tol");
+    if (!pos_h || !(tol >= 0.f) || !(dt >= 0.f)) return crk_set_error(ctx, CRK_EINVAL, "null pos_h, bad tol or dt");
     cudaStream_t s = (cudaStream_t)stream;
     int kf = feature_level(n);
     prof_begin(ctx, PROF_MLP_FWD, s);
     rc = count_cells(ctx, n, reinterpret_cast<const float4 *>(pos_h), kf, s);
     if (rc) return rc;
-    FeatArgs fa = feat_args(ctx, n, pos_h, gradv, Nngb, kf);
+    FeatArgs fa = feat_args(ctx, n, pos_h, gradv, Nngb, dt, kf);
     k_mlp_fwd<1><<<fwd_blocks(ctx, n), 256, 0, s>>>(n, ctx->mlp_w, nullptr, nullptr, fa,
                                                      reinterpret_cast<float4 *>(pos_h), tol, (float)ctx->p.h_min,
                                                      (float)ctx->p.h_max, (float)ctx->p.N_res);

@@ -340,12 +340,24 @@ extern "C" int crk_step(crk_ctx *ctx, int n, float *pos_h, float *vel_u, const f
     return CRK_OK;
 }
 
+static int h_iterate(crk_ctx *ctx, int n, float *pos_h, float tol, int max_it, int *iterations, cudaStream_t s);
+
+// P1 is all the iteration needs: it runs as the fused volume walk, without
+// per-particle neighbour lists or stored-force buffers.
 extern "C" int crk_h_iterate(crk_ctx *ctx, int n, float *pos_h, float tol, int max_it, int *iterations,
                              void *stream) {
     if (!ctx) return CRK_EINVAL;
     if (n <= 0 || !pos_h || !(tol > 0.f) || max_it < 1) return crk_set_error(ctx, CRK_EINVAL, "bad arguments");
-    cudaStream_t s = (cudaStream_t)stream;
     ctx->rates_valid = 0;
+    int vo = ctx->volumes_only;
+    ctx->volumes_only = 1;
+    int rc = h_iterate(ctx, n, pos_h, tol, max_it, iterations, (cudaStream_t)stream);
+    ctx->volumes_only = vo;
+    ctx->lists_valid = 0;
+    return rc;
+}
+
+static int h_iterate(crk_ctx *ctx, int n, float *pos_h, float tol, int max_it, int *iterations, cudaStream_t s) {
     int rc = build_cells_sorted(ctx, n, (const float4 *)pos_h, nullptr, s);
     if (!rc) rc = finish_build(ctx, s);
     if (rc) return rc;

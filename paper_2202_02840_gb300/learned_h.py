@@ -8,7 +8,8 @@ Data protocol (the method generates its own training data):
   * a Sedov blast (the Sedov-Taylor test of Sec. 4) is advanced with crk_step,
     whose h evolves by one Thacker update per step (Sec. 2.6, eq:thacker);
   * at every `every`-th step the state is a snapshot: P1 gives N_i at the
-    evolved h, P2/P3 give grad v, the fixed-point iteration of eq:hi from the
+    evolved h, P2/P3 give grad v (with the step dt, the compression dt div v),
+    the fixed-point iteration of eq:hi from the
     evolved h gives the converged h and the iteration count without a
     proposal, and the features plus the target log(h_conv / h_prev) are taken;
   * the network is trained by crk_mlp_train (Adam on sampled batches);
@@ -27,13 +28,14 @@ def dev(a):
 class Snapshot:
     """Features, targets and the plain fixed-point solve of one state."""
 
-    def __init__(self, ctx, pos_h, vel_u, tol=1e-4, max_it=60):
+    def __init__(self, ctx, pos_h, vel_u, dt, tol=1e-4, max_it=60):
         crk.crk_build_cells(ctx, pos_h)
         V, N = crk.crk_volumes(ctx)
         gradv = crk.crk_corrections(ctx, V, vel_u)[4]
         pos_conv = pos_h.clone()
         it, ok = crk.crk_h_iterate(ctx, pos_conv, tol=tol, max_it=max_it)
-        feat, target = crk.crk_h_features(ctx, pos_h, gradv, N, pos_conv)
+        feat, target = crk.crk_h_features(ctx, pos_h, gradv, N, pos_conv, dt=dt)
+        self.dt = dt
         self.pos_h = pos_h.clone()
         self.gradv, self.N = gradv, N
         self.feat, self.target = feat, target
@@ -48,7 +50,7 @@ class Snapshot:
         """(iterations, converged, pos_h with the converged h) starting from the
         proposal of the network loaded in ctx."""
         p = self.pos_h.clone()
-        crk.crk_h_propose(ctx, p, self.gradv, self.N, tol=self.tol)
+        crk.crk_h_propose(ctx, p, self.gradv, self.N, dt=self.dt, tol=self.tol)
         it, ok = crk.crk_h_iterate(ctx, p, tol=self.tol, max_it=self.max_it)
         return it, ok, p
 
@@ -62,9 +64,9 @@ def sedov_snapshots(n_side=32, steps=100, every=10, seed=3, tol=1e-4, max_it=60,
     probe = crk.crk_create(**p)
     snaps = []
     for k in range(1, steps + 1):
-        crk.crk_step(stepper, pos, vel, mass, 0.0)
+        dt = crk.crk_step(stepper, pos, vel, mass, 0.0, diag=(k % every == 0))
         if k % every == 0:
-            snaps.append(Snapshot(probe, pos, vel, tol=tol, max_it=max_it))
+            snaps.append(Snapshot(probe, pos, vel, dt["dt"], tol=tol, max_it=max_it))
     stepper.close()
     return snaps, probe
 

@@ -94,10 +94,11 @@ def test_features_match_oracle(case):
     conv = pos.copy()
     conv[:, 3] *= r.uniform(0.8, 1.25, n).astype(np.float32)
     ctx = crk.crk_create()
-    feat, target = crk.crk_h_features(ctx, dev(pos), dev(gradv), dev(N), dev(conv))
+    dt = 0.37
+    feat, target = crk.crk_h_features(ctx, dev(pos), dev(gradv), dev(N), dev(conv), dt=dt)
     g = as_np(feat).astype(np.float64)
     divv = gradv[:, 0, 0].astype(np.float64) + gradv[:, 1, 1] + gradv[:, 2, 2]
-    o = M.features(pos, N_prev=N, divv=divv)
+    o = M.features(pos, N_prev=N, divv=divv, dt=np.float32(dt))
     np.testing.assert_allclose(g[:, :5], o[:, :5], rtol=2e-7, atol=0)
     d5 = np.abs(g[:, 5] - o[:, 5])
     assert np.all(d5 <= 1e-6 * (1 + np.abs(o[:, 5]))), (d5.max(), g[np.argmax(d5)], o[np.argmax(d5)])
@@ -232,12 +233,12 @@ def test_proposal_matches_oracle_and_judge():
     w = rand_weights(9)
     w[4736:4800] *= 0.1
     crk.crk_mlp_set_weights(ctx, dev(w))
-    feat = crk.crk_h_features(ctx, g, gradv, N)
+    feat = crk.crk_h_features(ctx, g, gradv, N, dt=0.01)
     y = as_np(crk.crk_mlp_forward(ctx, feat)).astype(np.float64)
     d = np.abs(np.cbrt(268.0 / as_np(N).astype(np.float64)) - 1.0)
     tol = float(np.median(d))            # half the particles are judged converged
     p = g.clone()
-    crk.crk_h_propose(ctx, p, gradv, N, tol=tol)
+    crk.crk_h_propose(ctx, p, gradv, N, dt=0.01, tol=tol)
     h0 = pos[:, 3].astype(np.float64)
     h1 = as_np(p)[:, 3].astype(np.float64)
     np.testing.assert_array_equal(as_np(p)[:, :3], pos[:, :3])

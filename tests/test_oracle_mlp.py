@@ -143,14 +143,14 @@ def test_lattice_features_closed_form(side, kf):
     ph = np.concatenate([pos, np.full((n, 1), h)], 1).astype(np.float32)
     m = n / 8 ** kf
     divv = np.full(n, 0.5)
-    f = M.features(ph, N_prev=np.full(n, 268.0), divv=divv, kf=kf, N_res=268.0)
+    f = M.features(ph, N_prev=np.full(n, 268.0), divv=divv, dt=0.125, kf=kf, N_res=268.0)
     np.testing.assert_allclose(f[:, 0], np.log1p(m))
     np.testing.assert_allclose(f[:, 1], np.log1p(6 * m))
     np.testing.assert_allclose(f[:, 2], np.log1p(12 * m))
     np.testing.assert_allclose(f[:, 3], np.log1p(8 * m))
     np.testing.assert_allclose(f[:, 4], np.log1p(27 * m))
     np.testing.assert_allclose(f[:, 5], np.log(nh), rtol=1e-6)
-    np.testing.assert_allclose(f[:, 6], 0.5 * np.float32(h), rtol=1e-12)
+    np.testing.assert_allclose(f[:, 6], 0.5 * 0.125, rtol=1e-15)
     assert not np.any(f[:, 7])
 
 

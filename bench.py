@@ -279,6 +279,18 @@ def learned_h_report(dev, train_side=64, train_steps=200, every=10, eval_side=25
 
 # --------------------------------------------------------------------- GPU arm
 
+def aggregate(times_ms, work, dist=None, device="cpu"):
+    """Whole-job numbers of a replicated run: the slowest rank's times (max)
+    and the work of all ranks (sum).  Without a process group, the inputs."""
+    import torch
+    t = torch.tensor([float(x) for x in times_ms], dtype=torch.float64, device=device)
+    w = torch.tensor([float(x) for x in work], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(w, op=dist.ReduceOp.SUM)
+    return [float(x) for x in t.cpu()], [float(x) for x in w.cpu()]
+
+
 def run_gpu(args):
     import torch
     import __graft_entry__
@@ -370,14 +382,9 @@ def run_gpu(args):
     e2ectx_close = e2e_ctx.close()
 
     # ---------------- aggregate over ranks (max time, summed work)
-    t = torch.tensor([ms, e2e_ms], dtype=torch.float64, device=dev)
-    w = torch.tensor([float(pairs), float(e2e_pairs)], dtype=torch.float64, device=dev)
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.all_reduce(w, op=dist.ReduceOp.SUM)
-    ms_max, e2e_max = float(t[0]), float(t[1])
-    value = float(w[0]) / (ms_max / 1e3)
-    e2e_value = float(w[1]) / (e2e_max / 1e3)
+    (ms_max, e2e_max), (w0, w1) = aggregate([ms, e2e_ms], [float(pairs), float(e2e_pairs)], dist, dev)
+    value = w0 / (ms_max / 1e3)
+    e2e_value = w1 / (e2e_max / 1e3)
 
     # ---------------- roofline of the dominant pass
     per_step_pairs = {"P1 volumes": diags[-1]["pairs_gather"], "P2 corrections": diags[-1]["pairs_gather"],

@@ -114,13 +114,13 @@ def zeldovich_fields(n_side: int, seed: int):
     inv_k2[keep] = 1.0 / k2[keep]
     ks = (kx, ky, kz)
     # psi_k = i k delta_k / k^2  so that delta = -div psi
-    psi = np.stack([np.fft.irfftn(1j * ks[a] * dk * inv_k2, s=(n, n, n)) for a in range(3)])
+    psi = np.stack([np.fft.irfftn(1j * ks[a] * dk * inv_k2, s=(n, n, n), axes=(0, 1, 2)) for a in range(3)])
     scale = 1.0 / np.sqrt((psi ** 2).sum(axis=0).mean())   # unit rms displacement
     psi *= scale
     T = np.empty((3, 3, n, n, n))
     for a in range(3):
         for b in range(a, 3):
-            T[a, b] = np.fft.irfftn(-ks[a] * ks[b] * dk * inv_k2, s=(n, n, n)) * scale
+            T[a, b] = np.fft.irfftn(-ks[a] * ks[b] * dk * inv_k2, s=(n, n, n), axes=(0, 1, 2)) * scale
             T[b, a] = T[a, b]
     I1 = T[0, 0] + T[1, 1] + T[2, 2]
     I2 = (T[0, 0] * T[1, 1] - T[0, 1] * T[1, 0] + T[1, 1] * T[2, 2] - T[1, 2] * T[2, 1]

@@ -22,7 +22,7 @@ struct FParams {
 };
 
 // Per-particle record of the pair-set passes (160 bytes).
-struct __align__(16) FRec {
+struct __align__(32) FRec {
     uint4 q;        // qx, qy, qz, H
     float4 k0;      // 1/h, cW = 495/(32 pi h^3), cG = -1155/(4 pi h^5), h_hat = h/n_h
     float4 k1;      // V, P, rho, c_s
@@ -165,20 +165,25 @@ __global__ void k_pack_frec(int n, FSrc src, FParams fp, FRec *__restrict__ out,
     sfun[i] = r.k1.y / powf(r.k1.z, fp.gamma);       // s = P / rho^gamma (eq:fij)
 }
 
+// Two float4 of a record in one 256-bit read-only load (the record is 160 B,
+// so every pair of its float4 starts on a 32-byte boundary): one L1 sector
+// per lane per instruction instead of half a sector.
+__device__ __forceinline__ void ldg_v8(const float4 *p, float4 &a, float4 &b) {
+    asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+        : "l"(p));
+}
+
 __device__ __forceinline__ FRec ldg_frec(const FRec *p) {
     const float4 *q = reinterpret_cast<const float4 *>(p);
     FRec r;
-    float4 a = __ldg(q);
+    float4 a;
+    ldg_v8(q, a, r.k0);
     r.q = make_uint4(__float_as_uint(a.x), __float_as_uint(a.y), __float_as_uint(a.z), __float_as_uint(a.w));
-    r.k0 = __ldg(q + 1);
-    r.k1 = __ldg(q + 2);
-    r.k2 = __ldg(q + 3);
-    r.k3 = __ldg(q + 4);
-    r.k4 = __ldg(q + 5);
-    r.k5 = __ldg(q + 6);
-    r.k6 = __ldg(q + 7);
-    r.k7 = __ldg(q + 8);
-    r.k8 = __ldg(q + 9);
+    ldg_v8(q + 2, r.k1, r.k2);
+    ldg_v8(q + 4, r.k3, r.k4);
+    ldg_v8(q + 6, r.k5, r.k6);
+    ldg_v8(q + 8, r.k7, r.k8);
     return r;
 }
 
@@ -187,6 +192,9 @@ __device__ __forceinline__ FRec ldg_frec(const FRec *p) {
 template <bool COMP>
 struct P4 {
     static constexpr bool GATHER = false;
+    static constexpr int UNROLL = 1;
+    static constexpr bool PREFETCH = true;
+    using Rec = FRec;
     struct Params {
         const FRec *frec;
         const float *mass;
@@ -213,10 +221,9 @@ struct P4 {
         s.vsig = 0.f;
         s.qmax = 0.f;
     }
-    __device__ static void pair(IState &s, uint32_t e, size_t pos, bool in_i, const Params &p) {
-        const uint32_t j = e & 0x3fffffffu;
+    __device__ static Rec load(uint32_t e, size_t, const Params &p) { return ldg_frec(p.frec + (e & 0x3fffffffu)); }
+    __device__ static void pair(IState &s, const Rec &r, uint32_t e, size_t pos, bool in_i, const Params &p) {
         const bool in_j = in_i ? (e >> 31) != 0u : true;
-        const FRec r = ldg_frec(p.frec + j);
         int dx = (int)(s.me.q.x - r.q.x), dy = (int)(s.me.q.y - r.q.y), dz = (int)(s.me.q.z - r.q.z);
         Sep d = separation(dx, dy, dz);
         float x[3] = {d.x, d.y, d.z};
@@ -245,6 +252,11 @@ struct P4 {
 template <bool COMP>
 struct P5 {
     static constexpr bool GATHER = false;
+    static constexpr int UNROLL = 3;
+    static constexpr bool PREFETCH = false;
+    struct Rec {
+        float4 sig, F;
+    };
     struct Params {
         const float4 *sig;
         const float4 *Fst;
@@ -260,9 +272,12 @@ struct P5 {
         s.me = valid ? p.sig[i] : make_float4(0.f, 0.f, 0.f, 0.f);
         s.m = valid ? p.mass[i] : 1.f;
     }
-    __device__ static void pair(IState &s, uint32_t e, size_t pos, bool, const Params &p) {
-        const float4 r = __ldg(p.sig + (e & 0x3fffffffu));
-        const float4 F = __ldg(p.Fst + pos);
+    __device__ static Rec load(uint32_t e, size_t pos, const Params &p) {
+        return Rec{__ldg(p.sig + (e & 0x3fffffffu)), __ldg(p.Fst + pos)};
+    }
+    __device__ static void pair(IState &s, const Rec &rec, uint32_t, size_t, bool, const Params &) {
+        const float4 r = rec.sig;
+        const float4 F = rec.F;
         // 2 Delta E_ij = (v_j + v'_j - v_i - v'_i) . F_ij  (reading of eq:Eij)
         float w = fmaf(r.x - s.me.x, F.x, fmaf(r.y - s.me.y, F.y, (r.z - s.me.z) * F.z));
         // eq:fij

@@ -149,6 +149,9 @@ __device__ __forceinline__ void rk_solve(I m0f, const I *m1f, const I *m2f, cons
 template <bool FP64_SOLVE, bool COMP>
 struct P2 {
     static constexpr bool GATHER = true;
+    static constexpr int UNROLL = 4;
+    static constexpr bool PREFETCH = false;
+    using Rec = uint4;
     struct Params {
         const uint4 *q4;
         const uint4 *qV;   // (qx, qy, qz, V bits)
@@ -176,8 +179,8 @@ struct P2 {
         // self term of gather(i): x = 0, W(0) (unnormalised 1), grad W(0) = 0
         if (valid) s.m0.add(__uint_as_float(__ldg(&p.qV[i].w)));
     }
-    __device__ static void pair(IState &s, uint32_t e, size_t, bool, const Params &p) {
-        const uint4 r = __ldg(p.qV + (e & 0x3fffffffu));
+    __device__ static Rec load(uint32_t e, size_t, const Params &p) { return __ldg(p.qV + (e & 0x3fffffffu)); }
+    __device__ static void pair(IState &s, const Rec &r, uint32_t, size_t, bool, const Params &) {
         int dx = (int)(s.q.x - r.x), dy = (int)(s.q.y - r.y), dz = (int)(s.q.z - r.z);
         const float Vj = __uint_as_float(r.w);
         Sep d = separation(dx, dy, dz);
@@ -265,6 +268,8 @@ struct P2 {
 template <bool COMP>
 struct P3 {
     static constexpr bool GATHER = true;
+    static constexpr int UNROLL = 3;
+    static constexpr bool PREFETCH = false;
     struct Params {
         const uint4 *q4;
         const uint4 *qV;
@@ -297,10 +302,17 @@ struct P3 {
 #pragma unroll
         for (int k = 0; k < 9; k++) s.acc[k] = Acc<COMP>();
     }
-    __device__ static void pair(IState &s, uint32_t e, size_t, bool, const Params &p) {
+    struct Rec {
+        uint4 qV;
+        float4 v;
+    };
+    __device__ static Rec load(uint32_t e, size_t, const Params &p) {
         const uint32_t j = e & 0x3fffffffu;
-        const uint4 r = __ldg(p.qV + j);
-        const float4 vj = __ldg(p.vel + j);
+        return Rec{__ldg(p.qV + j), __ldg(p.vel + j)};
+    }
+    __device__ static void pair(IState &s, const Rec &rec, uint32_t, size_t, bool, const Params &) {
+        const uint4 r = rec.qV;
+        const float4 vj = rec.v;
         const float Vj = __uint_as_float(r.w);
         int dx = (int)(s.q.x - r.x), dy = (int)(s.q.y - r.y), dz = (int)(s.q.z - r.z);
         Sep d = separation(dx, dy, dz);

@@ -93,11 +93,15 @@ struct Acc {
 
 // ---------------------------------------------------------------- list passes
 
+
+
 // Warp per tile, lane = particle i; lane i walks its own neighbour list (entry
 // k at base + 32 k + lane).  Gather passes walk the first cnt_g[i] entries,
-// pair-set passes all cnt_u[i].  P must provide Params, IState, GATHER,
+// pair-set passes all cnt_u[i].  P must provide Params, IState, Rec, GATHER,
+// PREFETCH, UNROLL,
 //   init(IState&, int i, bool valid, const Params&)
-//   pair(IState&, uint32_t entry, uint32_t pos, bool in_i, const Params&)
+//   load(uint32_t entry, size_t pos, const Params&) -> Rec   (the neighbour's data)
+//   pair(IState&, const Rec&, uint32_t entry, size_t pos, bool in_i, const Params&)
 //   finish(IState&, int i, const Params&)            (valid lanes only)
 struct ListGeom {
     int n, ntiles, kcap;
@@ -109,8 +113,15 @@ struct ListGeom {
 
 // Entry k of a particle's list (gather neighbours k < cnt_g from the front
 // columns, the rest from the back columns) and its stored-force position.
-template <class P, int WARPS>
-__global__ void __launch_bounds__(WARPS * 32) k_lpass(ListGeom g, typename P::Params prm) {
+// The entries stream once from HBM, the longest latency of the loop, so they
+// are always read ahead.  Passes with 16-32-byte records (mostly L1 hits)
+// take P::UNROLL entries per iteration: that many independent gathers and
+// pair evaluations per lane, the next P::UNROLL entries in flight (measured
+// best: 4 for P1 and P2, 3 for P3 and P5).  P4, whose 160-byte record
+// already fills the registers, keeps one pair per iteration and instead
+// prefetches the record of entry k + 1 and the entry k + 2 (P::PREFETCH).
+template <class P, int WARPS, int MINB = 1>
+__global__ void __launch_bounds__(WARPS * 32, MINB) k_lpass(ListGeom g, typename P::Params prm) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int tile = blockIdx.x * WARPS + w;
     if (tile >= g.ntiles) return;
@@ -123,23 +134,65 @@ __global__ void __launch_bounds__(WARPS * 32) k_lpass(ListGeom g, typename P::Pa
     const int len = (int)(P::GATHER ? g.len_g[tile] : g.len_u[tile]);
     const int mg = valid ? g.cnt_g[i] : 0;
     const int my = P::GATHER ? mg : (valid ? g.cnt_u[i] : 0);
-    for (int k = 0; k < len; k++) {
-        if (k < my) {
-            const int c = k < mg ? k : g.kcap - 1 - (k - mg);
-            P::pair(st, __ldg(col0 + (size_t)c * 32), fb + (size_t)k * 32, k < mg, prm);
+    auto entry = [&](int k) -> uint32_t {
+        const int c = k < mg ? k : g.kcap - 1 - (k - mg);
+        return __ldg(col0 + (size_t)c * 32);
+    };
+    if (!P::PREFETCH) {
+        // U entries per iteration: U independent gathers and pair evaluations
+        // in flight per lane, the next U entries prefetched
+        constexpr int U = P::UNROLL;
+        uint32_t en[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) en[u] = u < my ? entry(u) : 0u;
+        for (int k = 0; k < len; k += U) {
+            uint32_t ec[U];
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                ec[u] = en[u];
+                if (k + U + u < my) en[u] = entry(k + U + u);
+            }
+            const size_t pos = fb + (size_t)k * 32;
+            typename P::Rec r[U];
+#pragma unroll
+            for (int u = 0; u < U; u++)
+                if (k + u < my) r[u] = P::load(ec[u], pos + 32 * u, prm);
+#pragma unroll
+            for (int u = 0; u < U; u++)
+                if (k + u < my) P::pair(st, r[u], ec[u], pos + 32 * u, k + u < mg, prm);
+        }
+    } else {
+        uint32_t e1 = my > 0 ? entry(0) : 0u;
+        uint32_t e2 = my > 1 ? entry(1) : 0u;
+        typename P::Rec r1{};
+        if (P::PREFETCH && my > 0) r1 = P::load(e1, fb, prm);
+        for (int k = 0; k < len; k++) {
+            if (k < my) {
+                const uint32_t e = e1;
+                const size_t pos = fb + (size_t)k * 32;
+                typename P::Rec r;
+                if (P::PREFETCH) {
+                    r = r1;
+                    if (k + 1 < my) r1 = P::load(e2, pos + 32, prm);
+                }
+                e1 = e2;
+                if (k + 2 < my) e2 = entry(k + 2);
+                if (!P::PREFETCH) r = P::load(e, pos, prm);
+                P::pair(st, r, e, pos, k < mg, prm);
+            }
         }
     }
     if (valid) P::finish(st, i, prm);
 }
 
-template <class P, int WARPS>
+template <class P, int WARPS, int MINB = 1>
 int launch_lpass(crk_ctx *ctx, int prof_id, const typename P::Params &prm, cudaStream_t s, const char *what) {
     if (ctx->n == 0) return CRK_OK;
     if (!ctx->lists_valid) return crk_set_error(ctx, CRK_ESTATE, "%s: neighbour lists are not built", what);
     ListGeom g{ctx->n, ctx->ntiles, ctx->kcap, ctx->tbase, ctx->len_g, ctx->len_u, ctx->cnt_g, ctx->cnt_u,
                ctx->ent};
     prof_begin(ctx, prof_id, s);
-    k_lpass<P, WARPS><<<grid_for(ctx->ntiles, WARPS), WARPS * 32, 0, s>>>(g, prm);
+    k_lpass<P, WARPS, MINB><<<grid_for(ctx->ntiles, WARPS), WARPS * 32, 0, s>>>(g, prm);
     ++ctx->launches;
     prof_end(ctx, s);
     CRK_LAUNCH_CHECK(ctx, what);

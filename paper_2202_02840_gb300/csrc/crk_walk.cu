@@ -59,6 +59,7 @@ __global__ void __launch_bounds__(WALK_WARPS * 32) k_walk(WalkArgs a) {
     float acc = 0.f;
     int cg = 0, co = 0;
     const uint2 lo = a.ofs[tile];
+    const uint4 Ilo = __ldg(a.tlo + tile), Ihi = __ldg(a.thi + tile);   // this tile's box, max H
     for (uint32_t t = 0; t < lo.y; t++) {
         const int J = (int)a.tiles[lo.x + t];
         // skip a neighbour tile that no lane's sphere (reach max(H_i, Hmax_J)) touches
@@ -70,11 +71,25 @@ __global__ void __launch_bounds__(WALK_WARPS * 32) k_walk(WalkArgs a) {
         if (__ballot_sync(0xffffffffu, near) == 0u) continue;
         const int j0 = J * TILE;
         const int cnt = min(TILE, a.n - j0);
+        // lane jj stages particle j0 + jj and keeps it only if it can be in the
+        // pair set of some particle of this tile: its gap to the tile's box
+        // below max(Hmax of the tile, H_j) (conservative, so the lists are
+        // unchanged)
         __syncwarp();
-        if (lane < cnt) sq[w][lane] = a.q4[j0 + lane];
+        bool keep = false;
+        if (lane < cnt) {
+            const uint4 q = a.q4[j0 + lane];
+            sq[w][lane] = q;
+            const unsigned long long hx = point_gap(q.x, Ilo.x, Ihi.x), hy = point_gap(q.y, Ilo.y, Ihi.y),
+                                     hz = point_gap(q.z, Ilo.z, Ihi.z);
+            const unsigned long long rj = q.w > Ilo.w ? q.w : Ilo.w;
+            keep = hx * hx + hy * hy + hz * hz < rj * rj;
+        }
+        unsigned mask = __ballot_sync(0xffffffffu, keep);
         __syncwarp();
-#pragma unroll 4
-        for (int jj = 0; jj < cnt; jj++) {
+        while (mask) {
+            const int jj = __ffs(mask) - 1;
+            mask &= mask - 1u;
             const uint4 qj = sq[w][jj];
             const int dx = (int)(qi.x - qj.x), dy = (int)(qi.y - qj.y), dz = (int)(qi.z - qj.z);
             const unsigned long long R2 = r2_fixed(dx, dy, dz);
@@ -209,6 +224,9 @@ int run_lists(crk_ctx *ctx, cudaStream_t s) {
 // P1 volumes over the gather lists (eq:vol, eq:hi), self included.
 struct P1 {
     static constexpr bool GATHER = true;
+    static constexpr int UNROLL = 4;
+    static constexpr bool PREFETCH = false;
+    using Rec = uint4;
     struct Params {
         const uint4 *q4;
         const float *hs;
@@ -225,8 +243,8 @@ struct P1 {
         s.inv_h = 1.f / s.h;
         s.acc = 1.f;                                   // self: W(0) / (495/(32 pi h^3)) = 1
     }
-    __device__ static void pair(IState &s, uint32_t e, size_t, bool, const Params &p) {
-        const uint4 r = __ldg(p.q4 + (e & 0x3fffffffu));
+    __device__ static Rec load(uint32_t e, size_t, const Params &p) { return __ldg(p.q4 + (e & 0x3fffffffu)); }
+    __device__ static void pair(IState &s, const Rec &r, uint32_t, size_t, bool, const Params &) {
         int dx = (int)(s.q.x - r.x), dy = (int)(s.q.y - r.y), dz = (int)(s.q.z - r.z);
         Sep d = separation(dx, dy, dz);
         float eta = d.r * s.inv_h;

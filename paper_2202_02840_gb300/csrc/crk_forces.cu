@@ -325,10 +325,10 @@ int run_forces(crk_ctx *ctx, cudaStream_t s) {
     const FRec *fr = reinterpret_cast<const FRec *>(ctx->frec);
     if (ctx->p.precision >= 1) {
         typename P4<true>::Params p{fr, ctx->mass, fp, ctx->acc, ctx->vq, ctx->Fst};
-        return launch_lpass<P4<true>, 4>(ctx, PROF_P4, p, s, "P4 forces");
+        return launch_lpass<P4<true>, 1>(ctx, PROF_P4, p, s, "P4 forces");
     }
     typename P4<false>::Params p{fr, ctx->mass, fp, ctx->acc, ctx->vq, ctx->Fst};
-    return launch_lpass<P4<false>, 4>(ctx, PROF_P4, p, s, "P4 forces");
+    return launch_lpass<P4<false>, 1>(ctx, PROF_P4, p, s, "P4 forces");
 }
 
 // P5 for the kick vb -> va (sorted float4 arrays), with the F_ij of the last P4.

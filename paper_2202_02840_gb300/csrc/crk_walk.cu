@@ -60,10 +60,27 @@ __global__ void __launch_bounds__(WALK_WARPS * 32) k_walk(WalkArgs a) {
     int cg = 0, co = 0;
     const uint2 lo = a.ofs[tile];
     const uint4 Ilo = __ldg(a.tlo + tile), Ihi = __ldg(a.thi + tile);   // this tile's box, max H
-    for (uint32_t t = 0; t < lo.y; t++) {
-        const int J = (int)a.tiles[lo.x + t];
+    // software pipeline over the candidate tiles: the tile id two ahead and
+    // the box of the next tile are in flight while the current tile is tested
+    // (each is otherwise a dependent L2 trip)
+    const uint32_t *tl = a.tiles + lo.x;
+    const int nt = (int)lo.y;
+    int J1 = nt > 0 ? (int)__ldg(tl) : 0, J2 = nt > 1 ? (int)__ldg(tl + 1) : 0;
+    uint4 lo1 = make_uint4(0, 0, 0, 0), hi1 = lo1;
+    if (nt > 0) {
+        lo1 = __ldg(a.tlo + J1);
+        hi1 = __ldg(a.thi + J1);
+    }
+    for (int t = 0; t < nt; t++) {
+        const int J = J1;
+        const uint4 Jlo = lo1, Jhi = hi1;
+        J1 = J2;
+        if (t + 2 < nt) J2 = (int)__ldg(tl + t + 2);
+        if (t + 1 < nt) {
+            lo1 = __ldg(a.tlo + J1);
+            hi1 = __ldg(a.thi + J1);
+        }
         // skip a neighbour tile that no lane's sphere (reach max(H_i, Hmax_J)) touches
-        const uint4 Jlo = __ldg(a.tlo + J), Jhi = __ldg(a.thi + J);
         const unsigned long long gx = point_gap(qi.x, Jlo.x, Jhi.x), gy = point_gap(qi.y, Jlo.y, Jhi.y),
                                  gz = point_gap(qi.z, Jlo.z, Jhi.z);
         const unsigned long long reach = qi.w > Jlo.w ? qi.w : Jlo.w;
@@ -78,7 +95,7 @@ __global__ void __launch_bounds__(WALK_WARPS * 32) k_walk(WalkArgs a) {
         __syncwarp();
         bool keep = false;
         if (lane < cnt) {
-            const uint4 q = a.q4[j0 + lane];
+            const uint4 q = __ldg(a.q4 + j0 + lane);
             sq[w][lane] = q;
             const unsigned long long hx = point_gap(q.x, Ilo.x, Ihi.x), hy = point_gap(q.y, Ilo.y, Ihi.y),
                                      hz = point_gap(q.z, Ilo.z, Ihi.z);

@@ -193,6 +193,7 @@ template <bool COMP>
 struct P4 {
     static constexpr bool GATHER = false;
     static constexpr int UNROLL = 1;
+    static constexpr bool ENTRIES = true;
     static constexpr bool PREFETCH = true;
     using Rec = FRec;
     struct Params {
@@ -201,7 +202,7 @@ struct P4 {
         FParams fp;
         float4 *acc;   // (ax, ay, az, dudt)
         float2 *vq;    // (vsig, qmax)
-        float4 *Fst;   // F_ij per list entry
+        float4 *Fst;   // (F_ij, j bits) per list entry
     };
     struct IState {
         FRec me;
@@ -229,7 +230,7 @@ struct P4 {
         float x[3] = {d.x, d.y, d.z};
         PairOut o;
         pair_force(s.me, r, x, d.r2, d.r, in_i, in_j, p.fp, o);
-        p.Fst[pos] = make_float4(o.F[0], o.F[1], o.F[2], 0.f);
+        p.Fst[pos] = make_float4(o.F[0], o.F[1], o.F[2], __uint_as_float(e & 0x3fffffffu));   // F_ij, j
         float dv[3] = {r.k2.x - s.me.k2.x, r.k2.y - s.me.k2.y, r.k2.z - s.me.k2.z};
 #pragma unroll
         for (int g = 0; g < 3; g++) s.F[g].add(o.F[g]);
@@ -272,8 +273,11 @@ struct P5 {
         s.me = valid ? p.sig[i] : make_float4(0.f, 0.f, 0.f, 0.f);
         s.m = valid ? p.mass[i] : 1.f;
     }
-    __device__ static Rec load(uint32_t e, size_t pos, const Params &p) {
-        return Rec{__ldg(p.sig + (e & 0x3fffffffu)), __ldg(p.Fst + pos)};
+    // the stored entry carries j (written by P4): the list itself is not read
+    static constexpr bool ENTRIES = false;
+    __device__ static Rec load(uint32_t, size_t pos, const Params &p) {
+        const float4 F = __ldg(p.Fst + pos);
+        return Rec{__ldg(p.sig + __float_as_uint(F.w)), F};
     }
     __device__ static void pair(IState &s, const Rec &rec, uint32_t, size_t, bool, const Params &) {
         const float4 r = rec.sig;

@@ -150,6 +150,7 @@ template <bool FP64_SOLVE, bool COMP>
 struct P2 {
     static constexpr bool GATHER = true;
     static constexpr int UNROLL = 4;
+    static constexpr bool ENTRIES = true;
     static constexpr bool PREFETCH = false;
     using Rec = uint4;
     struct Params {
@@ -269,6 +270,7 @@ template <bool COMP>
 struct P3 {
     static constexpr bool GATHER = true;
     static constexpr int UNROLL = 3;
+    static constexpr bool ENTRIES = true;
     static constexpr bool PREFETCH = false;
     struct Params {
         const uint4 *q4;

@@ -98,7 +98,8 @@ struct Acc {
 // Warp per tile, lane = particle i; lane i walks its own neighbour list (entry
 // k at base + 32 k + lane).  Gather passes walk the first cnt_g[i] entries,
 // pair-set passes all cnt_u[i].  P must provide Params, IState, Rec, GATHER,
-// PREFETCH, UNROLL,
+// PREFETCH, UNROLL, ENTRIES (false: the pass reads only its stored entries,
+// and `entry` is passed as 0),
 //   init(IState&, int i, bool valid, const Params&)
 //   load(uint32_t entry, size_t pos, const Params&) -> Rec   (the neighbour's data)
 //   pair(IState&, const Rec&, uint32_t entry, size_t pos, bool in_i, const Params&)
@@ -142,15 +143,16 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_lpass(ListGeom g, typename
         // U entries per iteration: U independent gathers and pair evaluations
         // in flight per lane, the next U entries prefetched
         constexpr int U = P::UNROLL;
+        constexpr bool E = P::ENTRIES;
         uint32_t en[U];
 #pragma unroll
-        for (int u = 0; u < U; u++) en[u] = u < my ? entry(u) : 0u;
+        for (int u = 0; u < U; u++) en[u] = (E && u < my) ? entry(u) : 0u;
         for (int k = 0; k < len; k += U) {
             uint32_t ec[U];
 #pragma unroll
             for (int u = 0; u < U; u++) {
                 ec[u] = en[u];
-                if (k + U + u < my) en[u] = entry(k + U + u);
+                if (E && k + U + u < my) en[u] = entry(k + U + u);
             }
             const size_t pos = fb + (size_t)k * 32;
             typename P::Rec r[U];

@@ -242,6 +242,7 @@ int run_lists(crk_ctx *ctx, cudaStream_t s) {
 struct P1 {
     static constexpr bool GATHER = true;
     static constexpr int UNROLL = 4;
+    static constexpr bool ENTRIES = true;
     static constexpr bool PREFETCH = false;
     using Rec = uint4;
     struct Params {

@@ -27,20 +27,25 @@ __global__ void k_keys(int n, const float4 *__restrict__ pos, uint32_t *__restri
                        int32_t *__restrict__ idx, uint4 *__restrict__ q_tmp,
                        float *__restrict__ h_tmp, unsigned long long *counters) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n) return;
-    float4 p = pos[t];
-    bool ok = (p.x >= 0.f && p.x < 1.f) && (p.y >= 0.f && p.y < 1.f) && (p.z >= 0.f && p.z < 1.f) &&
-              ((double)p.w > 0.0 && (double)p.w < 1.0 / 3.0);
-    if (!ok) {
-        atomicAdd(&counters[CNT_ERR_INPUT], 1ull);
-        p = make_float4(0.f, 0.f, 0.f, 0.01f);
+    uint32_t hbits = 0u;
+    if (t < n) {
+        float4 p = pos[t];
+        bool ok = (p.x >= 0.f && p.x < 1.f) && (p.y >= 0.f && p.y < 1.f) && (p.z >= 0.f && p.z < 1.f) &&
+                  ((double)p.w > 0.0 && (double)p.w < 1.0 / 3.0);
+        if (!ok) {
+            atomicAdd(&counters[CNT_ERR_INPUT], 1ull);
+            p = make_float4(0.f, 0.f, 0.f, 0.01f);
+        }
+        uint4 q = make_uint4(to_fixed(p.x), to_fixed(p.y), to_fixed(p.z), to_fixed(p.w));
+        q_tmp[t] = q;
+        h_tmp[t] = p.w;
+        key[t] = morton30(q.x, q.y, q.z);
+        idx[t] = t;
+        hbits = __float_as_uint(p.w);   // h > 0: the bits order like the values
     }
-    uint4 q = make_uint4(to_fixed(p.x), to_fixed(p.y), to_fixed(p.z), to_fixed(p.w));
-    q_tmp[t] = q;
-    h_tmp[t] = p.w;
-    key[t] = morton30(q.x, q.y, q.z);
-    idx[t] = t;
-    atomicMax(&counters[CNT_HMAX], (unsigned long long)__float_as_uint(p.w));
+    // max h: one atomic per warp, not one per particle on a single address
+    hbits = __reduce_max_sync(0xffffffffu, hbits);
+    if ((threadIdx.x & 31) == 0 && hbits) atomicMax(&counters[CNT_HMAX], (unsigned long long)hbits);
 }
 
 // ------------------------------------------------------------------ radix sort

@@ -293,7 +293,8 @@ struct Tree32 {
 // The reach of a node is max(Hmax_I, Hmax_node) (pair-set predicate).
 template <bool WRITE>
 __device__ uint32_t walk32(const Tree32 &T, const uint4 *__restrict__ lo, const uint4 *__restrict__ hi,
-                           uint4 Ilo, uint4 Ihi, uint32_t *__restrict__ out, int *stL, int *stK, int lane) {
+                           uint4 Ilo, uint4 Ihi, uint32_t *__restrict__ out, uint32_t lim, int *stL, int *stK,
+                           int lane) {
     const unsigned lt = lanemask_lt();
     const unsigned long long HI = Ilo.w;
     uint32_t count = 0;
@@ -311,7 +312,10 @@ __device__ uint32_t walk32(const Tree32 &T, const uint4 *__restrict__ lo, const 
         const unsigned m = __ballot_sync(0xffffffffu, pass);
         const int np = __popc(m);
         if (cl == 0) {
-            if (WRITE && pass) out[count + __popc(m & lt)] = (uint32_t)c;
+            if (WRITE && pass) {
+                const uint32_t at = count + __popc(m & lt);
+                if (at < lim) out[at] = (uint32_t)c;
+            }
             count += np;
         } else if (np) {
             if (pass) {
@@ -331,16 +335,22 @@ __device__ uint32_t walk32(const Tree32 &T, const uint4 *__restrict__ lo, const 
     return count;
 }
 
+constexpr uint32_t LIST_BUF = 1024;   // tiles a warp keeps in shared memory
+
+// One walk per tile into shared memory, then one allocation and a coalesced
+// copy; a tile with more than LIST_BUF neighbours walks a second time
+// straight into the allocated range.
 __global__ void __launch_bounds__(LIST_WARPS * 32) k_lists32(int ntiles, Tree32 T, const uint4 *__restrict__ lo,
                                                              const uint4 *__restrict__ hi, uint2 *__restrict__ ofs,
                                                              uint32_t *__restrict__ list, long long cap,
                                                              unsigned long long *counter) {
     __shared__ int stL[LIST_WARPS][STACK], stK[LIST_WARPS][STACK];
+    __shared__ uint32_t buf[LIST_WARPS][LIST_BUF];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int I = blockIdx.x * LIST_WARPS + w;
     if (I >= ntiles) return;
     const uint4 Ilo = lo[I], Ihi = hi[I];
-    uint32_t c = walk32<false>(T, lo, hi, Ilo, Ihi, nullptr, stL[w], stK[w], lane);
+    uint32_t c = walk32<true>(T, lo, hi, Ilo, Ihi, buf[w], LIST_BUF, stL[w], stK[w], lane);
     unsigned long long base = 0;
     if (c == 0xffffffffu) {
         if (lane == 0) {
@@ -352,7 +362,12 @@ __global__ void __launch_bounds__(LIST_WARPS * 32) k_lists32(int ntiles, Tree32 
     if (lane == 0) base = atomicAdd(counter, (unsigned long long)c);
     base = __shfl_sync(0xffffffffu, base, 0);
     if ((long long)(base + c) <= cap) {
-        walk32<true>(T, lo, hi, Ilo, Ihi, list + base, stL[w], stK[w], lane);
+        __syncwarp();
+        if (c <= LIST_BUF) {
+            for (uint32_t k = lane; k < c; k += 32) list[base + k] = buf[w][k];
+        } else {
+            walk32<true>(T, lo, hi, Ilo, Ihi, list + base, c, stL[w], stK[w], lane);
+        }
         if (lane == 0) ofs[I] = make_uint2((uint32_t)base, c);
     } else if (lane == 0) {
         ofs[I] = make_uint2(0u, 0u);

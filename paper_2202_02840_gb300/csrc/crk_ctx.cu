@@ -398,6 +398,7 @@ extern "C" int crk_create(const crk_params *p, crk_ctx **out) {
     rc |= dalloc(ctx, &ctx->scan_tmp, 2 * 4096 + 64);
     rc |= dalloc(ctx, &ctx->cell_start, ((size_t)1 << (3 * prm.kmax)) + 1);
     rc |= dalloc(ctx, &ctx->d_scalars, 64);
+    rc |= dalloc(ctx, &ctx->sm_next, 1024);
     if (!rc && cudaMallocHost((void **)&ctx->h_counters, CNT_COUNT * sizeof(unsigned long long)) != cudaSuccess)
         rc = CRK_ENOMEM;
     if (!rc && cudaMemset(ctx->counters, 0, CNT_COUNT * sizeof(unsigned long long)) != cudaSuccess) rc = CRK_ECUDA;
@@ -425,7 +426,7 @@ extern "C" int crk_destroy(crk_ctx *ctx) {
     dfree(&ctx->corr); dfree(&ctx->gv); dfree(&ctx->acc); dfree(&ctx->vq);
     dfree(&ctx->vb); dfree(&ctx->va); dfree(&ctx->du);
     dfree(&ctx->st_pos); dfree(&ctx->st_vel); dfree(&ctx->st_half); dfree(&ctx->st_tmp);
-    dfree(&ctx->st_tmp1); dfree(&ctx->q_tmp); dfree(&ctx->h_tmp); dfree(&ctx->flags); dfree(&ctx->d_red); dfree(&ctx->d_dt); dfree(&ctx->d_scalars);
+    dfree(&ctx->st_tmp1); dfree(&ctx->q_tmp); dfree(&ctx->h_tmp); dfree(&ctx->flags); dfree(&ctx->d_red); dfree(&ctx->d_dt); dfree(&ctx->d_scalars); dfree(&ctx->sm_next);
     if (ctx->h_counters) cudaFreeHost(ctx->h_counters);
     mlp_free(ctx);
     prof_free(ctx);

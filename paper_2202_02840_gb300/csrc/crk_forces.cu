@@ -11,6 +11,12 @@
 // F_ij at its list entry; P5 (run once per half kick) reuses them.
 #include "crk_pass.cuh"
 
+// Divisions of the pair force: the hardware reciprocal-based quotient (two
+// instructions, about 2 ulp) instead of the IEEE-rounded one (a dozen and a
+// branch).  The same operation is applied to swapped operands for (j, i), so
+// F_ji = -F_ij stays bitwise exact.
+#define FDIV(a, b) __fdividef((a), (b))
+
 namespace crk {
 
 struct FParams {
@@ -127,7 +133,7 @@ __device__ __forceinline__ void pair_force(const FRec &a, const FRec &b, const f
     float qs = qa + qb;
     float phi = 0.f;
     if (qs != 0.f) {
-        float is = 1.f / qs;
+        float is = FDIV(1.f, qs);
         phi = fminf(fmaxf(4.f * (qa * is) * (qb * is), 0.f), 1.f);
     }
     float eta = fminf(r * a.k0.x, r * b.k0.x);
@@ -144,8 +150,8 @@ __device__ __forceinline__ void pair_force(const FRec &a, const FRec &b, const f
     float ux = fmaf(uh[0], x[0], fmaf(uh[1], x[1], uh[2] * x[2]));
     // eq:mu, eq:visc
     float hha = a.k0.w, hhb = b.k0.w;
-    float mua = fminf(hha * ux / fmaf(hha * hha, fp.eps2, r2), 0.f);
-    float mub = fminf(hhb * ux / fmaf(hhb * hhb, fp.eps2, r2), 0.f);
+    float mua = fminf(FDIV(hha * ux, fmaf(hha * hha, fp.eps2, r2)), 0.f);
+    float mub = fminf(FDIV(hhb * ux, fmaf(hhb * hhb, fp.eps2, r2)), 0.f);
     float Qa = a.k1.z * mua * fmaf(fp.Cq, mua, -fp.Cl * a.k1.w);
     float Qb = b.k1.z * mub * fmaf(fp.Cq, mub, -fp.Cl * b.k1.w);
     float Pta = a.k1.y + Qa, Ptb = b.k1.y + Qb;
@@ -194,6 +200,7 @@ struct P4 {
     static constexpr bool GATHER = false;
     static constexpr int UNROLL = 1;
     static constexpr bool ENTRIES = true;
+    static constexpr bool PERSISTENT = true;
     static constexpr bool PREFETCH = true;
     using Rec = FRec;
     struct Params {
@@ -237,7 +244,7 @@ struct P4 {
         float wd = fmaf(dv[0], o.D[0], fmaf(dv[1], o.D[1], dv[2] * o.D[2]));
         s.du.add(0.5f * (s.me.k1.x * r.k1.x) * o.Pt_b * wd);
         float vx = -fmaf(dv[0], x[0], fmaf(dv[1], x[1], dv[2] * x[2]));   // (v_i - v_j).x_ij
-        if (vx < 0.f && d.r > 0.f) s.vsig = fmaxf(s.vsig, -vx / d.r);
+        if (vx < 0.f && d.r > 0.f) s.vsig = fmaxf(s.vsig, FDIV(-vx, d.r));
         s.qmax = fmaxf(s.qmax, o.Q_a);
     }
     __device__ static void finish(IState &s, int i, const Params &p) {
@@ -254,6 +261,7 @@ template <bool COMP>
 struct P5 {
     static constexpr bool GATHER = false;
     static constexpr int UNROLL = 3;
+    static constexpr bool PERSISTENT = false;
     static constexpr bool PREFETCH = false;
     struct Rec {
         float4 sig, F;

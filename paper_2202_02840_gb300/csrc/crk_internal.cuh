@@ -152,6 +152,7 @@ struct crk_ctx {
     float *mlp_hist = nullptr;       // per-step loss of the last training run
     int cap_hist_loss = 0;
     long long mlp_t = 0;             // Adam steps taken since the weights were set
+    uint32_t *sm_next = nullptr;     // per-SM tile counters of the persistent passes (1024)
     int32_t *fcnt = nullptr;         // occupancy of the feature grid (8^7 cells)
     uint32_t *sel = nullptr;         // row selection: flags and their scan (2 x cap_sel)
     int cap_sel = 0;

@@ -151,6 +151,7 @@ struct P2 {
     static constexpr bool GATHER = true;
     static constexpr int UNROLL = 4;
     static constexpr bool ENTRIES = true;
+    static constexpr bool PERSISTENT = false;
     static constexpr bool PREFETCH = false;
     using Rec = uint4;
     struct Params {
@@ -271,6 +272,7 @@ struct P3 {
     static constexpr bool GATHER = true;
     static constexpr int UNROLL = 3;
     static constexpr bool ENTRIES = true;
+    static constexpr bool PERSISTENT = false;
     static constexpr bool PREFETCH = false;
     struct Params {
         const uint4 *q4;

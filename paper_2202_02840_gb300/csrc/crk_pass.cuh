@@ -98,7 +98,7 @@ struct Acc {
 // Warp per tile, lane = particle i; lane i walks its own neighbour list (entry
 // k at base + 32 k + lane).  Gather passes walk the first cnt_g[i] entries,
 // pair-set passes all cnt_u[i].  P must provide Params, IState, Rec, GATHER,
-// PREFETCH, UNROLL, ENTRIES (false: the pass reads only its stored entries,
+// PREFETCH, UNROLL, PERSISTENT, ENTRIES (false: the pass reads only its stored entries,
 // and `entry` is passed as 0),
 //   init(IState&, int i, bool valid, const Params&)
 //   load(uint32_t entry, size_t pos, const Params&) -> Rec   (the neighbour's data)
@@ -121,11 +121,8 @@ struct ListGeom {
 // best: 4 for P1 and P2, 3 for P3 and P5).  P4, whose 160-byte record
 // already fills the registers, keeps one pair per iteration and instead
 // prefetches the record of entry k + 1 and the entry k + 2 (P::PREFETCH).
-template <class P, int WARPS, int MINB = 1>
-__global__ void __launch_bounds__(WARPS * 32, MINB) k_lpass(ListGeom g, typename P::Params prm) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int tile = blockIdx.x * WARPS + w;
-    if (tile >= g.ntiles) return;
+template <class P>
+__device__ __forceinline__ void lpass_tile(const ListGeom &g, const typename P::Params &prm, int tile, int lane) {
     const int i = tile * TILE + lane;
     const bool valid = i < g.n;
     typename P::IState st;
@@ -188,13 +185,63 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_lpass(ListGeom g, typename
 }
 
 template <class P, int WARPS, int MINB = 1>
+__global__ void __launch_bounds__(WARPS * 32, MINB) k_lpass(ListGeom g, typename P::Params prm) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int tile = blockIdx.x * WARPS + w;
+    if (tile >= g.ntiles) return;
+    lpass_tile<P>(g, prm, tile, lane);
+}
+
+// Persistent form (one warp per block, as many blocks as fit at once): SM s
+// owns the contiguous tile range [s chunk, (s+1) chunk) and its warps claim
+// tiles from it in order with an atomic counter, so the warps resident on one
+// SM work on neighbouring tiles, whose neighbour records they share in L1.  A
+// warp whose range is exhausted claims tiles from the other ranges.  Every
+// claim is one atomicAdd; a range's counter runs past chunk at most once per
+// warp, so the loop is bounded.
+template <class P>
+__global__ void __launch_bounds__(32) k_lpass_sm(ListGeom g, typename P::Params prm, uint32_t *next, int nrange,
+                                                 int chunk) {
+    const int lane = threadIdx.x & 31;
+    unsigned smid;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+    const int home = (int)(smid % (unsigned)nrange);
+    for (int r = 0; r < nrange; r++) {
+        const int range = (home + r) % nrange;
+        for (;;) {
+            uint32_t t = 0;
+            if (lane == 0) t = atomicAdd(&next[range], 1u);
+            t = __shfl_sync(0xffffffffu, t, 0);
+            if (t >= (uint32_t)chunk) break;
+            const long long tile = (long long)range * chunk + t;
+            if (tile >= g.ntiles) break;
+            lpass_tile<P>(g, prm, (int)tile, lane);
+        }
+    }
+}
+
+template <class P, int WARPS, int MINB = 1>
 int launch_lpass(crk_ctx *ctx, int prof_id, const typename P::Params &prm, cudaStream_t s, const char *what) {
     if (ctx->n == 0) return CRK_OK;
     if (!ctx->lists_valid) return crk_set_error(ctx, CRK_ESTATE, "%s: neighbour lists are not built", what);
     ListGeom g{ctx->n, ctx->ntiles, ctx->kcap, ctx->tbase, ctx->len_g, ctx->len_u, ctx->cnt_g, ctx->cnt_u,
                ctx->ent};
-    prof_begin(ctx, prof_id, s);
-    k_lpass<P, WARPS, MINB><<<grid_for(ctx->ntiles, WARPS), WARPS * 32, 0, s>>>(g, prm);
+    if constexpr (P::PERSISTENT) {
+        static int per_sm = 0;
+        if (!per_sm) {
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lpass_sm<P>, 32, 0) != cudaSuccess ||
+                per_sm < 1)
+                per_sm = 1;
+        }
+        const int nrange = ctx->nsm > 0 ? (ctx->nsm < 1024 ? ctx->nsm : 1024) : 1;
+        const int chunk = (ctx->ntiles + nrange - 1) / nrange;
+        CRK_CUDA(ctx, cudaMemsetAsync(ctx->sm_next, 0, sizeof(uint32_t) * nrange, s));
+        prof_begin(ctx, prof_id, s);
+        k_lpass_sm<P><<<nrange * per_sm, 32, 0, s>>>(g, prm, ctx->sm_next, nrange, chunk);
+    } else {
+        prof_begin(ctx, prof_id, s);
+        k_lpass<P, WARPS, MINB><<<grid_for(ctx->ntiles, WARPS), WARPS * 32, 0, s>>>(g, prm);
+    }
     ++ctx->launches;
     prof_end(ctx, s);
     CRK_LAUNCH_CHECK(ctx, what);

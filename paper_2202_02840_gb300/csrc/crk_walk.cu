@@ -243,6 +243,7 @@ struct P1 {
     static constexpr bool GATHER = true;
     static constexpr int UNROLL = 4;
     static constexpr bool ENTRIES = true;
+    static constexpr bool PERSISTENT = false;
     static constexpr bool PREFETCH = false;
     using Rec = uint4;
     struct Params {

@@ -39,6 +39,10 @@ WORKLOAD = "zeldovich-128^3: clustered gas, Zel'dovich lattice displacement, P(k
 # UNORDERED pair of the pair set (both kernel sides, limiter, viscosity, force).
 FLOPS_PER_UNIT = {"P1 volumes": 20, "P2 corrections": 110, "P3 grad v": 92, "P4 forces": 281,
                   "P5 compatible energy": 259}
+# DRAM bytes (read + write) per unit measured by ncu for the current P4 kernel on
+# zeldovich-64^3 (0.66 GB read + 1.20 GB written for 39.1 M unordered pairs); a
+# full 128^3 launch is too large to capture, so the traffic is scaled by units.
+TRAFFIC_PER_UNIT = {"P4 forces": 47.6}
 
 
 def measured_peaks():
@@ -398,8 +402,11 @@ def run_gpu(args):
     peaks = measured_peaks()
     max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     peak = alu_peak_tflops(sm_count, max_mhz)
+    traffic = TRAFFIC_PER_UNIT.get(dominant)
     roofline = {"bound": "alu", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak,
+                "traffic": traffic * per_step_pairs[dominant] if traffic else None,
+                "traffic_basis": "ncu DRAM bytes per unit on zeldovich-64^3, scaled by units" if traffic else None,
                 "peak_basis": "FP32 FMA issue: %d SMs x 128 lanes x 2 flops x %.0f MHz (max SM clock)"
                               % (sm_count, max_mhz),
                 "launch_ms": launch_ms,
@@ -411,7 +418,8 @@ def run_gpu(args):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "n": n, "precision": ["plain", "mixed", "mixed+compensated moments"][args.precision],
                            "parallelism": "replicas" if world > 1 else "single",
-                           "l2": "step working set ~%.1f GB > L2 (129 MB)" % (n * 460 / 1e9),
+                           "l2": "step working set ~%.1f GB > L2 (129 MB): inputs larger than L2, no flush"
+                                 % ((n * 460 + entries * 20) / 1e9),
                            "pairs_per_step": pairs / args.steps,
                            "tiles": ntiles, "pair_candidate_tiles_per_tile": utp / max(1, ntiles),
                            "list_entries_per_particle": entries / n,

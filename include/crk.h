@@ -224,6 +224,34 @@ int crk_reset_rates(crk_ctx *ctx);
 int crk_h_iterate(crk_ctx *ctx, int n, float *pos_h, float tol, int max_it, int *iterations,
                   void *stream);
 
+/* ------------------------------------------------------------------------
+ * Batched boxes.  nbox independent periodic unit boxes in one particle set:
+ * box b owns the caller rows [box_start[b], box_start[b+1]) (host array of
+ * nbox + 1 ascending ints, box_start[0] = 0, box_start[nbox] = n, nbox <=
+ * 65535).  Every box is its own simulation of Sec. 2 in its own unit cube
+ * (positions in [0,1), minimum images within the box, its own time step);
+ * particles of different boxes never interact.  One launch of each pass
+ * covers all boxes, so many small or unevenly occupied boxes cost one set of
+ * launches (the persistent P4 pass balances their tiles across the SMs).
+ * ---------------------------------------------------------------------- */
+
+/* Bin all boxes (as crk_build_cells, per box).  After it, crk_volumes,
+ * crk_corrections, crk_forces, crk_compatible and crk_neighbours work on the
+ * batched build with their usual arguments (caller order over all rows);
+ * crk_cells returns CRK_ESTATE (its chaining-mesh table describes one box).
+ * CRK_EINVAL for a bad box table or invalid particle records.  Synchronises. */
+int crk_build_cells_batched(crk_ctx *ctx, int n, int nbox, const int32_t *box_start, const float *pos_h,
+                            void *stream);
+
+/* One KDK step of every box (as crk_step, per box): dt (host, nbox doubles,
+ * may be NULL) fixes each box's step, <= 0 or NULL selects that box's CFL
+ * step.  diag (host, nbox entries, may be NULL) receives each box's FP64
+ * diagnostics (pairs_gather and pairs_union are totals over all boxes) and
+ * makes the call synchronise.  The box table is reloaded (and the rates
+ * re-evaluated) whenever it differs from the previous call's. */
+int crk_step_batched(crk_ctx *ctx, int n, int nbox, const int32_t *box_start, float *pos_h, float *vel_u,
+                     const float *mass, const double *dt, crk_diag *diag, void *stream);
+
 /* Per-pass GPU timing, for roofline measurement.  enable = 1 clears the
  * records and starts recording a CUDA event pair around every pass kernel (and
  * around each cell build), on the stream that kernel is launched on; enable = 0

@@ -79,6 +79,8 @@ def lib():
         L.crk_mlp_train.argtypes = [_vp, _ci, _vp, _vp, _vp, _ci, _ci, _ci, ctypes.c_float, ctypes.c_ulonglong,
                                     _vp, _vp]
         L.crk_h_select.argtypes = [_vp, _ci, _vp, ctypes.c_float, _ci, _vp, ctypes.POINTER(_ci), _vp]
+        L.crk_build_cells_batched.argtypes = [_vp, _ci, _ci, _vp, _vp, _vp]
+        L.crk_step_batched.argtypes = [_vp, _ci, _ci, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
         L.crk_profile.argtypes = [_vp, _ci]
         L.crk_profile_read.argtypes = [_vp, _vp, _vp, ctypes.POINTER(ctypes.c_longlong)]
         _LIB = L
@@ -398,3 +400,34 @@ def crk_mlp_train(ctx, feat, target, rows=None, batch=4096, steps=1000, lr=1e-3,
                                   _vp(None) if rows is None else _t(rows, (nr,), "rows", torch.int32), nr,
                                   int(batch), int(steps), float(lr), int(seed), hist, _stream(stream)))
     return [hist[k] for k in range(int(steps))]
+
+
+# ---------------------------------------------------------------- batched boxes
+
+def _box_table(box_start, n):
+    b = [int(x) for x in box_start]
+    arr = (ctypes.c_int32 * len(b))(*b)
+    return arr, len(b) - 1
+
+
+def crk_build_cells_batched(ctx, pos_h, box_start, stream=None):
+    """Bin independent boxes; box b owns rows box_start[b]:box_start[b+1] of pos_h."""
+    n = pos_h.shape[0]
+    arr, nbox = _box_table(box_start, n)
+    ctx.check(lib().crk_build_cells_batched(ctx.handle, n, nbox, arr, _t(pos_h, (n, 4), "pos_h"), _stream(stream)))
+    ctx.n = n
+
+
+def crk_step_batched(ctx, pos_h, vel_u, mass, box_start, dt=None, diag=False, stream=None):
+    """One KDK step of every box in place; dt (per box, None = CFL); per-box diagnostics if diag."""
+    n = pos_h.shape[0]
+    arr, nbox = _box_table(box_start, n)
+    dta = None if dt is None else (ctypes.c_double * nbox)(*[float(x) for x in dt])
+    d = (crk_diag * nbox)() if diag else None
+    ctx.check(lib().crk_step_batched(ctx.handle, n, nbox, arr, _t(pos_h, (n, 4), "pos_h"),
+                                     _t(vel_u, (n, 4), "vel_u"), _t(mass, (n,), "mass"), dta, d, _stream(stream)))
+    ctx.n = n
+    if not diag:
+        return None
+    return [{"dt": x.dt, "dt_next": x.dt_next, "E_kin": x.E_kin, "E_int": x.E_int, "P": list(x.P),
+             "pairs_gather": x.pairs_gather, "pairs_union": x.pairs_union} for x in d]

@@ -223,7 +223,7 @@ __global__ void k_gather_sorted(int n, const int32_t *__restrict__ idx, const ui
 // ------------------------------------------------------------------ tiles and tree
 
 __global__ void k_tiles(int n, int ntiles, const uint4 *__restrict__ q4, uint4 *__restrict__ lo,
-                        uint4 *__restrict__ hi) {
+                        uint4 *__restrict__ hi, const int32_t *__restrict__ sbox, uint32_t *__restrict__ nbox) {
     int tile = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int lane = threadIdx.x & 31;
     if (tile >= ntiles) return;
@@ -242,20 +242,37 @@ __global__ void k_tiles(int n, int ntiles, const uint4 *__restrict__ q4, uint4 *
         lo[tile] = make_uint4(xl, yl, zl, Hm);
         hi[tile] = make_uint4(xh, yh, zh, c);
     }
+    if (sbox) {   // batched boxes: the range of boxes the tile's particles belong to
+        uint32_t b = v ? (uint32_t)sbox[s] : 0u;
+        uint32_t bl = __reduce_min_sync(FULL, v ? b : 0xffffu);
+        uint32_t bh = __reduce_max_sync(FULL, v ? b : 0u);
+        if (lane == 0) nbox[tile] = bl | (bh << 16);
+    }
+}
+
+__device__ __forceinline__ bool box_ranges_meet(uint32_t a, uint32_t b) {
+    return (a & 0xffffu) <= (b >> 16) && (b & 0xffffu) <= (a >> 16);
 }
 
 __global__ void k_tree_level(const uint4 *__restrict__ clo, const uint4 *__restrict__ chi, int ccnt,
-                             uint4 *__restrict__ plo, uint4 *__restrict__ phi, int pcnt) {
+                             uint4 *__restrict__ plo, uint4 *__restrict__ phi, int pcnt,
+                             const uint32_t *__restrict__ cbox, uint32_t *__restrict__ pbox) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= pcnt) return;
     uint4 l = clo[2 * k], h = chi[2 * k];
+    uint32_t b = cbox ? cbox[2 * k] : 0u;
     if (2 * k + 1 < ccnt) {
         uint4 l2 = clo[2 * k + 1], h2 = chi[2 * k + 1];
         l = make_uint4(min(l.x, l2.x), min(l.y, l2.y), min(l.z, l2.z), max(l.w, l2.w));
         h = make_uint4(max(h.x, h2.x), max(h.y, h2.y), max(h.z, h2.z), h.w + h2.w);
+        if (cbox) {
+            uint32_t b2 = cbox[2 * k + 1];
+            b = min(b & 0xffffu, b2 & 0xffffu) | (max(b >> 16, b2 >> 16) << 16);
+        }
     }
     plo[k] = l;
     phi[k] = h;
+    if (cbox) pbox[k] = b;
 }
 
 // periodic gap (fixed point) between intervals [a0,a1] and [b0,b1] on a circle of 2^32
@@ -293,8 +310,8 @@ struct Tree32 {
 // The reach of a node is max(Hmax_I, Hmax_node) (pair-set predicate).
 template <bool WRITE>
 __device__ uint32_t walk32(const Tree32 &T, const uint4 *__restrict__ lo, const uint4 *__restrict__ hi,
-                           uint4 Ilo, uint4 Ihi, uint32_t *__restrict__ out, uint32_t lim, int *stL, int *stK,
-                           int lane) {
+                           const uint32_t *__restrict__ nbox, uint32_t Ibox, uint4 Ilo, uint4 Ihi,
+                           uint32_t *__restrict__ out, uint32_t lim, int *stL, int *stK, int lane) {
     const unsigned lt = lanemask_lt();
     const unsigned long long HI = Ilo.w;
     uint32_t count = 0;
@@ -307,7 +324,8 @@ __device__ uint32_t walk32(const Tree32 &T, const uint4 *__restrict__ lo, const 
         if (c < T.cnt[cl]) {
             const uint4 nlo = lo[T.off[cl] + c], nhi = hi[T.off[cl] + c];
             unsigned long long R = HI > (unsigned long long)nlo.w ? HI : (unsigned long long)nlo.w;
-            pass = box_gap2(Ilo, Ihi, nlo, nhi) < R * R;
+            pass = box_gap2(Ilo, Ihi, nlo, nhi) < R * R &&
+                   (!nbox || box_ranges_meet(Ibox, nbox[T.off[cl] + c]));
         }
         const unsigned m = __ballot_sync(0xffffffffu, pass);
         const int np = __popc(m);
@@ -341,16 +359,18 @@ constexpr uint32_t LIST_BUF = 1024;   // tiles a warp keeps in shared memory
 // copy; a tile with more than LIST_BUF neighbours walks a second time
 // straight into the allocated range.
 __global__ void __launch_bounds__(LIST_WARPS * 32) k_lists32(int ntiles, Tree32 T, const uint4 *__restrict__ lo,
-                                                             const uint4 *__restrict__ hi, uint2 *__restrict__ ofs,
-                                                             uint32_t *__restrict__ list, long long cap,
-                                                             unsigned long long *counter) {
+                                                             const uint4 *__restrict__ hi,
+                                                             const uint32_t *__restrict__ nbox,
+                                                             uint2 *__restrict__ ofs, uint32_t *__restrict__ list,
+                                                             long long cap, unsigned long long *counter) {
     __shared__ int stL[LIST_WARPS][STACK], stK[LIST_WARPS][STACK];
     __shared__ uint32_t buf[LIST_WARPS][LIST_BUF];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int I = blockIdx.x * LIST_WARPS + w;
     if (I >= ntiles) return;
     const uint4 Ilo = lo[I], Ihi = hi[I];
-    uint32_t c = walk32<true>(T, lo, hi, Ilo, Ihi, buf[w], LIST_BUF, stL[w], stK[w], lane);
+    const uint32_t Ibox = nbox ? nbox[I] : 0u;
+    uint32_t c = walk32<true>(T, lo, hi, nbox, Ibox, Ilo, Ihi, buf[w], LIST_BUF, stL[w], stK[w], lane);
     unsigned long long base = 0;
     if (c == 0xffffffffu) {
         if (lane == 0) {
@@ -366,7 +386,7 @@ __global__ void __launch_bounds__(LIST_WARPS * 32) k_lists32(int ntiles, Tree32 
         if (c <= LIST_BUF) {
             for (uint32_t k = lane; k < c; k += 32) list[base + k] = buf[w][k];
         } else {
-            walk32<true>(T, lo, hi, Ilo, Ihi, list + base, c, stL[w], stK[w], lane);
+            walk32<true>(T, lo, hi, nbox, Ibox, Ilo, Ihi, list + base, c, stL[w], stK[w], lane);
         }
         if (lane == 0) ofs[I] = make_uint2((uint32_t)base, c);
     } else if (lane == 0) {
@@ -420,8 +440,8 @@ int rebuild_lists(crk_ctx *ctx, cudaStream_t s) {
     CRK_CUDA(ctx, cudaMemsetAsync(ctx->counters + CNT_GLIST, 0, 2 * sizeof(unsigned long long), s));
     ctx->lists_valid = 0;
     k_lists32<<<grid_for(ctx->ntiles, LIST_WARPS), LIST_WARPS * 32, 0, s>>>(
-        ctx->ntiles, T, ctx->node_lo, ctx->node_hi, ctx->uofs, ctx->ulist, ctx->cap_ulist,
-        ctx->counters + CNT_ULIST);
+        ctx->ntiles, T, ctx->node_lo, ctx->node_hi, ctx->nbox > 1 ? ctx->node_box : nullptr, ctx->uofs,
+        ctx->ulist, ctx->cap_ulist, ctx->counters + CNT_ULIST);
     ++ctx->launches;
     CRK_LAUNCH_CHECK(ctx, "interaction lists");
     return CRK_OK;
@@ -431,7 +451,9 @@ int rebuild_lists(crk_ctx *ctx, cudaStream_t s) {
 int build_tree(crk_ctx *ctx, cudaStream_t s) {
     int n = ctx->n, nt = ctx->ntiles;
     if (nt == 0) return CRK_OK;
-    k_tiles<<<grid_for((long long)nt * 32, 256), 256, 0, s>>>(n, nt, ctx->q4, ctx->node_lo, ctx->node_hi);
+    const bool batched = ctx->nbox > 1;
+    k_tiles<<<grid_for((long long)nt * 32, 256), 256, 0, s>>>(n, nt, ctx->q4, ctx->node_lo, ctx->node_hi,
+                                                               batched ? ctx->sbox : nullptr, ctx->node_box);
     ++ctx->launches;
     for (int L = 1; L < ctx->nlevels; L++) {
         int pc = ctx->level_cnt[L];
@@ -439,7 +461,9 @@ int build_tree(crk_ctx *ctx, cudaStream_t s) {
                                                          ctx->node_hi + ctx->level_off[L - 1],
                                                          ctx->level_cnt[L - 1],
                                                          ctx->node_lo + ctx->level_off[L],
-                                                         ctx->node_hi + ctx->level_off[L], pc);
+                                                         ctx->node_hi + ctx->level_off[L], pc,
+                                                         batched ? ctx->node_box + ctx->level_off[L - 1] : nullptr,
+                                                         batched ? ctx->node_box + ctx->level_off[L] : nullptr);
         ++ctx->launches;
     }
     CRK_LAUNCH_CHECK(ctx, "tile tree");
@@ -449,9 +473,17 @@ int build_tree(crk_ctx *ctx, cudaStream_t s) {
 // Bin the n records pos[t] (float4 x,y,z,h) of some input order; base_perm maps
 // that order to caller indices (NULL = identity).  After the call idx_a holds,
 // for every new sorted slot, its index in the input order.
-int build_cells_sorted(crk_ctx *ctx, int n, const float4 *pos, const int32_t *base_perm, cudaStream_t s) {
+__global__ void k_gather_u32(int n, const int32_t *__restrict__ idx, const uint32_t *__restrict__ in,
+                             uint32_t *__restrict__ out) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < n) out[s] = in[idx[s]];
+}
+
+int build_cells_sorted(crk_ctx *ctx, int n, const float4 *pos, const int32_t *base_perm, cudaStream_t s,
+                       const int32_t *box_of_input) {
     int rc = crk_ensure_particles(ctx, n);
     if (rc) return rc;
+    if (!box_of_input) ctx->nbox = 0;   // a build without boxes is one box
     ctx->n = n;
     ctx->ntiles = (n + TILE - 1) / TILE;
     int L = 0, c = ctx->ntiles, off = 0;
@@ -476,17 +508,37 @@ int build_cells_sorted(crk_ctx *ctx, int n, const float4 *pos, const int32_t *ba
     k_keys<<<grid_for(n, 256), 256, 0, s>>>(n, pos, ctx->key_a, ctx->idx_a, q_tmp, h_tmp, ctx->counters);
     ++ctx->launches;
     CRK_LAUNCH_CHECK(ctx, "keys");
-    rc = radix_sort(ctx, n, 30, s);
-    if (rc) return rc;
+    if (box_of_input) {
+        // batched boxes: stable sort by Morton key, then stable sort by box,
+        // which leaves the order box-major and Morton within each box
+        CRK_CUDA(ctx, cudaMemcpyAsync(ctx->mkey, ctx->key_a, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s));
+        rc = radix_sort(ctx, n, 30, s);
+        if (rc) return rc;
+        k_gather_u32<<<grid_for(n, 256), 256, 0, s>>>(n, ctx->idx_a, reinterpret_cast<const uint32_t *>(box_of_input),
+                                                      ctx->key_a);
+        ++ctx->launches;
+        rc = radix_sort(ctx, n, ctx->nbox <= 256 ? 8 : 16, s);
+        if (rc) return rc;
+        CRK_CUDA(ctx, cudaMemcpyAsync(ctx->sbox, ctx->key_a, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
+        k_gather_u32<<<grid_for(n, 256), 256, 0, s>>>(n, ctx->idx_a, ctx->mkey, ctx->keys);
+        ++ctx->launches;
+        CRK_LAUNCH_CHECK(ctx, "box sort");
+    } else {
+        rc = radix_sort(ctx, n, 30, s);
+        if (rc) return rc;
+        CRK_CUDA(ctx, cudaMemcpyAsync(ctx->keys, ctx->key_a, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s));
+    }
     k_gather_sorted<<<grid_for(n, 256), 256, 0, s>>>(n, ctx->idx_a, q_tmp, h_tmp, base_perm, ctx->q4,
                                                      ctx->hs, ctx->idx_b);
     ++ctx->launches;
     CRK_LAUNCH_CHECK(ctx, "gather sorted");
     CRK_CUDA(ctx, cudaMemcpyAsync(ctx->perm, ctx->idx_b, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
-    CRK_CUDA(ctx, cudaMemcpyAsync(ctx->keys, ctx->key_a, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s));
-    k_cell_start<<<grid_for(n + 1, 256), 256, 0, s>>>(n, ctx->keys, ctx->p.kmax, ctx->counters, ctx->cell_start);
-    ++ctx->launches;
-    CRK_LAUNCH_CHECK(ctx, "cell table");
+    if (!box_of_input) {   // the chaining-mesh table describes one box
+        k_cell_start<<<grid_for(n + 1, 256), 256, 0, s>>>(n, ctx->keys, ctx->p.kmax, ctx->counters,
+                                                          ctx->cell_start);
+        ++ctx->launches;
+        CRK_LAUNCH_CHECK(ctx, "cell table");
+    }
     rc = build_tree(ctx, s);
     if (rc) return rc;
     rc = rebuild_lists(ctx, s);

@@ -427,6 +427,8 @@ extern "C" int crk_destroy(crk_ctx *ctx) {
     dfree(&ctx->vb); dfree(&ctx->va); dfree(&ctx->du);
     dfree(&ctx->st_pos); dfree(&ctx->st_vel); dfree(&ctx->st_half); dfree(&ctx->st_tmp);
     dfree(&ctx->st_tmp1); dfree(&ctx->q_tmp); dfree(&ctx->h_tmp); dfree(&ctx->flags); dfree(&ctx->d_red); dfree(&ctx->d_dt); dfree(&ctx->d_scalars); dfree(&ctx->sm_next);
+    dfree(&ctx->box_start); dfree(&ctx->dtb); dfree(&ctx->box_dtmin); dfree(&ctx->box_red);
+    dfree(&ctx->box_in); dfree(&ctx->sbox); dfree(&ctx->sbox_tmp); dfree(&ctx->mkey); dfree(&ctx->node_box);
     if (ctx->h_counters) cudaFreeHost(ctx->h_counters);
     mlp_free(ctx);
     prof_free(ctx);
@@ -472,10 +474,85 @@ extern "C" int crk_build_cells(crk_ctx *ctx, int n, const float *pos_h, void *st
     return CRK_OK;
 }
 
+// box of caller row t: the b with box_start[b] <= t < box_start[b+1]
+__global__ void k_box_of(int n, int nbox, const int32_t *__restrict__ start, int32_t *__restrict__ box) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    int lo = 0, hi = nbox - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (start[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    box[t] = lo;
+}
+
+int crk::ensure_boxes(crk_ctx *ctx, int n, int nbox) {
+    int rc = 0;
+    if (nbox > ctx->cap_box) {
+        int cap = nbox < 64 ? 64 : nbox;
+        rc |= dalloc(ctx, &ctx->box_start, (size_t)cap + 1);
+        rc |= dalloc(ctx, &ctx->dtb, (size_t)cap);
+        rc |= dalloc(ctx, &ctx->box_dtmin, (size_t)cap);
+        rc |= dalloc(ctx, &ctx->box_red, 8 * (size_t)cap);
+        if (rc) return rc;
+        ctx->cap_box = cap;
+    }
+    if (n > ctx->cap_bpart || !ctx->sbox) {
+        int cap = n < 4096 ? 4096 : n + n / 8;
+        int tiles = (cap + TILE - 1) / TILE;
+        rc |= dalloc(ctx, &ctx->box_in, (size_t)cap);
+        rc |= dalloc(ctx, &ctx->sbox, (size_t)cap);
+        rc |= dalloc(ctx, &ctx->sbox_tmp, (size_t)cap);
+        rc |= dalloc(ctx, &ctx->mkey, (size_t)cap);
+        rc |= dalloc(ctx, &ctx->node_box, 2 * (size_t)tiles + MAX_LEVELS);
+        if (rc) return rc;
+        ctx->cap_bpart = cap;
+    }
+    return CRK_OK;
+}
+
+// Validate a host box table and load it; ctx->box_in gets the box of every caller row.
+int crk::load_boxes(crk_ctx *ctx, int n, int nbox, const int32_t *box_start, cudaStream_t s) {
+    if (nbox < 1 || nbox > 65535 || !box_start) return crk_set_error(ctx, CRK_EINVAL, "bad box table");
+    if (box_start[0] != 0 || box_start[nbox] != n)
+        return crk_set_error(ctx, CRK_EINVAL, "box table must start at 0 and end at n");
+    for (int b = 0; b < nbox; b++)
+        if (box_start[b + 1] < box_start[b]) return crk_set_error(ctx, CRK_EINVAL, "box table not ascending");
+    int rc = ensure_boxes(ctx, n, nbox);
+    if (rc) return rc;
+    CRK_CUDA(ctx, cudaMemcpyAsync(ctx->box_start, box_start, sizeof(int32_t) * ((size_t)nbox + 1),
+                                  cudaMemcpyHostToDevice, s));
+    k_box_of<<<grid_for(n, 256), 256, 0, s>>>(n, nbox, ctx->box_start, ctx->box_in);
+    ++ctx->launches;
+    CRK_LAUNCH_CHECK(ctx, "box ids");
+    CRK_CUDA(ctx, cudaStreamSynchronize(s));   // the host table may be freed after the call
+    ctx->nbox = nbox;
+    return CRK_OK;
+}
+
+extern "C" int crk_build_cells_batched(crk_ctx *ctx, int n, int nbox, const int32_t *box_start,
+                                       const float *pos_h, void *stream) {
+    if (!ctx) return CRK_EINVAL;
+    if (n < 1 || !pos_h) return crk_set_error(ctx, CRK_EINVAL, "bad n or pos_h");
+    if (n > (1 << 30)) return crk_set_error(ctx, CRK_EINVAL, "n beyond 2^30");
+    cudaStream_t s = (cudaStream_t)stream;
+    ctx->rates_valid = 0;
+    int rc = crk_ensure_particles(ctx, n);
+    if (!rc) rc = load_boxes(ctx, n, nbox, box_start, s);
+    if (!rc) rc = build_cells_sorted(ctx, n, (const float4 *)pos_h, nullptr, s, ctx->box_in);
+    if (!rc) rc = finish_build(ctx, s);
+    if (rc) {
+        ctx->built = 0;
+        return rc;
+    }
+    return CRK_OK;
+}
+
 extern "C" int crk_cells(crk_ctx *ctx, uint32_t *keys, int32_t *perm, int32_t *cell_start, int *k_out,
                          void *stream) {
     int rc = need_built(ctx);
     if (rc) return rc;
+    if (ctx->nbox > 1) return crk_set_error(ctx, CRK_ESTATE, "the chaining-mesh table describes one box");
     cudaStream_t s = (cudaStream_t)stream;
     rc = crk_sync_counters(ctx, s);
     if (rc) return rc;

@@ -153,6 +153,21 @@ struct crk_ctx {
     int cap_hist_loss = 0;
     long long mlp_t = 0;             // Adam steps taken since the weights were set
     uint32_t *sm_next = nullptr;     // per-SM tile counters of the persistent passes (1024)
+
+    // batched boxes: nbox independent periodic unit boxes in one particle set
+    int nbox = 0;                    // 0: one box (no box ids)
+    int cap_box = 0;                 // boxes the per-box arrays hold
+    int cap_bpart = 0;               // particles the per-particle box arrays hold
+    int32_t *box_start = nullptr;    // [nbox+1] caller rows of each box (= sorted slots, box-major)
+    int32_t *box_in = nullptr;       // box of each caller row
+    int32_t *sbox = nullptr;         // box of each sorted slot
+    int32_t *sbox_tmp = nullptr;     // box of each slot of the previous build (rebuild input)
+    uint32_t *mkey = nullptr;        // Morton keys in input order during a batched sort
+    uint32_t *node_box = nullptr;    // tree nodes: lowest box | highest box << 16
+    int cap_node_box = 0;
+    double *dtb = nullptr;           // time step of each box (the step's dt for one box)
+    unsigned long long *box_dtmin = nullptr;   // per-box CFL minimum (float bits)
+    double *box_red = nullptr;       // per-box FP64 diagnostics, 8 per box
     int32_t *fcnt = nullptr;         // occupancy of the feature grid (8^7 cells)
     uint32_t *sel = nullptr;         // row selection: flags and their scan (2 x cap_sel)
     int cap_sel = 0;
@@ -195,7 +210,9 @@ void mlp_free(crk_ctx *ctx);
 void prof_begin(crk_ctx *ctx, int id, cudaStream_t s);
 void prof_end(crk_ctx *ctx, cudaStream_t s);
 int build_cells_sorted(crk_ctx *ctx, int n, const float4 *pos_h, const int32_t *order,
-                       cudaStream_t s);
+                       cudaStream_t s, const int32_t *box_of_input = nullptr);
+int ensure_boxes(crk_ctx *ctx, int n, int nbox);
+int load_boxes(crk_ctx *ctx, int n, int nbox, const int32_t *box_start, cudaStream_t s);
 int rebuild_lists(crk_ctx *ctx, cudaStream_t s);
 int build_tree(crk_ctx *ctx, cudaStream_t s);
 int finish_build(crk_ctx *ctx, cudaStream_t s);

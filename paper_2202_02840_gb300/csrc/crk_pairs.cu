@@ -24,32 +24,34 @@ struct PN {
     struct Params {
         const uint4 *q4;
         const int32_t *perm;
+        const int32_t *sbox;   // batched boxes (null: one box)
         int32_t *cnt;
         uint32_t *hash;
     };
     struct __align__(16) JRec {
         uint4 q;
-        int4 id;   // caller index, -, -, -
+        int4 id;   // caller index, box, -, -
     };
     struct IState {
         uint4 q;
         unsigned long long H2;
-        int c;
+        int c, box;
         uint32_t h;
     };
     __device__ static void init(IState &s, int i, bool valid, const Params &p) {
         s.q = valid ? p.q4[i] : make_uint4(0, 0, 0, 0);
         s.H2 = (unsigned long long)s.q.w * s.q.w;
         s.c = 0;
+        s.box = (valid && p.sbox) ? p.sbox[i] : 0;
         s.h = 0u;
     }
     __device__ static void stage(JRec &r, int j, const Params &p) {
         r.q = p.q4[j];
-        r.id = make_int4(p.perm[j], 0, 0, 0);
+        r.id = make_int4(p.perm[j], p.sbox ? p.sbox[j] : 0, 0, 0);
     }
     __device__ static void pair(IState &s, const JRec &r, int j, int i, bool valid, const Params &) {
         int dx = (int)(s.q.x - r.q.x), dy = (int)(s.q.y - r.q.y), dz = (int)(s.q.z - r.q.z);
-        unsigned long long R2 = r2_fixed(dx, dy, dz);
+        unsigned long long R2 = r.id.y == s.box ? r2_fixed(dx, dy, dz) : ~0ull;
         bool in;
         if (UNION) {
             unsigned long long Hj2 = (unsigned long long)r.q.w * r.q.w;
@@ -71,10 +73,10 @@ struct PN {
 
 int run_neighbours(crk_ctx *ctx, int mode, int32_t *cnt, uint32_t *hash, cudaStream_t s) {
     if (mode == 0) {
-        PN<false>::Params p{ctx->q4, ctx->perm, cnt, hash};
+        PN<false>::Params p{ctx->q4, ctx->perm, ctx->nbox > 1 ? ctx->sbox : nullptr, cnt, hash};
         return launch_pass<PN<false>, 8>(ctx, PROF_PN, true, p, nullptr, s, "neighbour sets");
     }
-    PN<true>::Params p{ctx->q4, ctx->perm, cnt, hash};
+    PN<true>::Params p{ctx->q4, ctx->perm, ctx->nbox > 1 ? ctx->sbox : nullptr, cnt, hash};
     return launch_pass<PN<true>, 8>(ctx, PROF_PN, true, p, nullptr, s, "neighbour sets");
 }
 

@@ -12,6 +12,8 @@
 #include <math.h>
 #include <string.h>
 
+#include <vector>
+
 namespace crk {
 
 static float bits_to_float(uint32_t b) {
@@ -45,7 +47,7 @@ static StepConsts step_consts(const crk_params &p) {
 __global__ void k_cfl(int n, StepConsts c, const float *__restrict__ hs, const float *__restrict__ V,
                       const float *__restrict__ mass, const float4 *__restrict__ vel,
                       const float4 *__restrict__ acc, const float2 *__restrict__ vq,
-                      const GvRec *__restrict__ gv, unsigned long long *dtmin) {
+                      const GvRec *__restrict__ gv, unsigned long long *dtmin, const int32_t *__restrict__ sbox) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     float dt = 3.0e38f;
     if (s < n) {
@@ -63,26 +65,51 @@ __global__ void k_cfl(int n, StepConsts c, const float *__restrict__ hs, const f
         float am = sqrtf(a.x * a.x + a.y * a.y + a.z * a.z);
         if (am > 0.f) dt = fminf(dt, sqrtf(hh / am));
     }
+    if (sbox) {   // batched boxes: one minimum per box (one atomic per box a warp touches)
+        const int b = s < n ? sbox[s] : -1;
+        const unsigned peers = __match_any_sync(0xffffffffu, b);
+        unsigned m = __float_as_uint(dt);
+        for (int k = 0; k < 32; k++) {
+            const unsigned mk = __shfl_sync(0xffffffffu, m, k);
+            if (((peers >> k) & 1u) && mk < m) m = mk;
+        }
+        if (b >= 0 && (threadIdx.x & 31) == __ffs(peers) - 1) atomicMin(dtmin + b, (unsigned long long)m);
+        return;
+    }
     unsigned m = __reduce_min_sync(0xffffffffu, __float_as_uint(dt));
     if ((threadIdx.x & 31) == 0) atomicMin(dtmin, (unsigned long long)m);
 }
 
-// d_scalars[0] = dt of this step: the requested dt, or min(CFL dt, dt_max)
-__global__ void k_pick_dt(double dt_req, double dt_max, const unsigned long long *dtmin, double *sc) {
-    double dt = dt_req;
+__global__ void k_fill_ull(int count, unsigned long long v, unsigned long long *out) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < count) out[k] = v;
+}
+
+// dt of this step for each box: the requested dt, or min(CFL dt, dt_max);
+// req (device, one per box) may be null, dt_req then applies to every box
+__global__ void k_pick_dt(int nbox, double dt_req, const double *req, double dt_max,
+                          const unsigned long long *dtmin, double *dtb) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nbox) return;
+    double dt = req ? req[b] : dt_req;
     if (!(dt > 0.0)) {
-        dt = (double)__uint_as_float((uint32_t)*dtmin);
+        dt = (double)__uint_as_float((uint32_t)dtmin[b]);
         if (!(dt < dt_max)) dt = dt_max;
     }
-    sc[0] = dt;
+    dtb[b] = dt;
+}
+
+// dt of slot s: its box's (one box: dtb[0])
+__device__ __forceinline__ double slot_dt(const double *dtb, const int32_t *sbox, int s) {
+    return dtb[sbox ? sbox[s] : 0];
 }
 
 // first half kick of eq:verletOP: p_1/2 = p + a dt/2; vb = p, va = p_1/2
-__global__ void k_kick1(int n, const double *sc, const float4 *__restrict__ st_vel, const float4 *__restrict__ acc,
+__global__ void k_kick1(int n, const double *sc, const int32_t *__restrict__ sbox, const float4 *__restrict__ st_vel, const float4 *__restrict__ acc,
                         float4 *__restrict__ vb, float4 *__restrict__ va) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
-    float h = (float)(0.5 * sc[0]);
+    float h = (float)(0.5 * slot_dt(sc, sbox, s));
     float4 v = st_vel[s], a = acc[s];
     vb[s] = make_float4(v.x, v.y, v.z, 0.f);
     va[s] = make_float4(fmaf(h, a.x, v.x), fmaf(h, a.y, v.y), fmaf(h, a.z, v.z), 0.f);
@@ -90,12 +117,12 @@ __global__ void k_kick1(int n, const double *sc, const float4 *__restrict__ st_v
 
 // u_1/2 = u + du dt/2; predictor p_p = p_1/2 + a dt/2, u_p = u_1/2 + du dt/2;
 // drift x1 = x + p_1/2 dt (periodic wrap into [0,1)).
-__global__ void k_half_drift(int n, const double *sc, float4 *__restrict__ st_pos, float4 *__restrict__ st_vel,
+__global__ void k_half_drift(int n, const double *sc, const int32_t *__restrict__ sbox, float4 *__restrict__ st_pos, float4 *__restrict__ st_vel,
                              float4 *__restrict__ st_half, const float4 *__restrict__ va,
                              const float4 *__restrict__ acc, const float *__restrict__ du) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
-    float dt = (float)sc[0], h = 0.5f * dt;
+    float dt = (float)slot_dt(sc, sbox, s), h = 0.5f * dt;
     float4 v = st_vel[s], ph = va[s], a = acc[s];
     float uh = fmaf(h, du[s], v.w);
     st_half[s] = make_float4(ph.x, ph.y, ph.z, uh);
@@ -124,23 +151,23 @@ __global__ void k_permute3(int n, const int32_t *__restrict__ idx, const float4 
 }
 
 // second half kick: p1 = p_1/2 + a1 dt/2; vb = p_1/2, va = p1
-__global__ void k_kick2(int n, const double *sc, const float4 *__restrict__ st_half, const float4 *__restrict__ acc,
+__global__ void k_kick2(int n, const double *sc, const int32_t *__restrict__ sbox, const float4 *__restrict__ st_half, const float4 *__restrict__ acc,
                         float4 *__restrict__ vb, float4 *__restrict__ va) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
-    float h = (float)(0.5 * sc[0]);
+    float h = (float)(0.5 * slot_dt(sc, sbox, s));
     float4 v = st_half[s], a = acc[s];
     vb[s] = make_float4(v.x, v.y, v.z, 0.f);
     va[s] = make_float4(fmaf(h, a.x, v.x), fmaf(h, a.y, v.y), fmaf(h, a.z, v.z), 0.f);
 }
 
 // final state: v1 = va, u1 = u_1/2 + du dt/2; h advanced by eq:thacker
-__global__ void k_finish(int n, const double *sc, StepConsts c, const float4 *__restrict__ st_half,
+__global__ void k_finish(int n, const double *sc, const int32_t *__restrict__ sbox, StepConsts c, const float4 *__restrict__ st_half,
                          const float4 *__restrict__ va, const float *__restrict__ du, const float *__restrict__ Nn,
                          const float *__restrict__ hs, float4 *__restrict__ st_vel, float4 *__restrict__ st_pos) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
-    float h = (float)(0.5 * sc[0]);
+    float h = (float)(0.5 * slot_dt(sc, sbox, s));
     float4 a = va[s];
     st_vel[s] = make_float4(a.x, a.y, a.z, fmaf(h, du[s], st_half[s].w));
     float d = cbrtf(c.N_res / Nn[s]);
@@ -175,6 +202,32 @@ __global__ void k_energy_partials(int n, const float4 *__restrict__ vel, const f
         __syncthreads();
     }
     if (threadIdx.x < 5) part[blockIdx.x * 8 + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+// the same sums per box: block b over the sorted slots of box b (box-major order)
+__global__ void k_energy_box(const int32_t *__restrict__ start, const float4 *__restrict__ vel,
+                             const float *__restrict__ mass, double *__restrict__ out) {
+    __shared__ double sh[5][256];
+    const int b = blockIdx.x;
+    double a[5] = {0, 0, 0, 0, 0};
+    for (int s = start[b] + threadIdx.x; s < start[b + 1]; s += blockDim.x) {
+        float4 v = vel[s];
+        double m = mass[s];
+        double vx = v.x, vy = v.y, vz = v.z;
+        a[0] += 0.5 * m * (vx * vx + vy * vy + vz * vz);
+        a[1] += m * (double)v.w;
+        a[2] += m * vx;
+        a[3] += m * vy;
+        a[4] += m * vz;
+    }
+    for (int k = 0; k < 5; k++) sh[k][threadIdx.x] = a[k];
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o)
+            for (int k = 0; k < 5; k++) sh[k][threadIdx.x] += sh[k][threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x < 5) out[b * 8 + threadIdx.x] = sh[threadIdx.x][0];
 }
 
 __global__ void k_energy_final(int nb, const double *__restrict__ part, double *__restrict__ out) {
@@ -224,11 +277,13 @@ static int evaluate(crk_ctx *ctx, cudaStream_t s) {
     if (!rc) rc = run_forces(ctx, s);
     if (rc) return rc;
     StepConsts c = step_consts(ctx->p);
-    unsigned long long big = 0x7f7fffffull;   // FLT_MAX bits
-    CRK_CUDA(ctx, cudaMemcpyAsync(ctx->counters + CNT_DTMIN, &big, sizeof(big), cudaMemcpyHostToDevice, s));
+    const bool batched = ctx->nbox > 1;
+    unsigned long long *dtmin = batched ? ctx->box_dtmin : ctx->counters + CNT_DTMIN;
+    const int nb = batched ? ctx->nbox : 1;
+    k_fill_ull<<<grid_for(nb, 256), 256, 0, s>>>(nb, 0x7f7fffffull, dtmin);   // FLT_MAX bits
     k_cfl<<<grid_for(ctx->n, 256), 256, 0, s>>>(ctx->n, c, ctx->hs, ctx->V, ctx->mass, ctx->vel, ctx->acc,
-                                                  ctx->vq, ctx->gv, ctx->counters + CNT_DTMIN);
-    ++ctx->launches;
+                                                  ctx->vq, ctx->gv, dtmin, batched ? ctx->sbox : nullptr);
+    ctx->launches += 2;
     CRK_LAUNCH_CHECK(ctx, "CFL");
     return CRK_OK;
 }
@@ -243,16 +298,17 @@ extern "C" int crk_reset_rates(crk_ctx *ctx) {
     return CRK_OK;
 }
 
-extern "C" int crk_step(crk_ctx *ctx, int n, float *pos_h, float *vel_u, const float *mass, double dt,
-                        crk_diag *diag, void *stream) {
-    if (!ctx) return CRK_EINVAL;
-    if (n <= 0 || !pos_h || !vel_u || !mass) return crk_set_error(ctx, CRK_EINVAL, "bad arguments");
-    cudaStream_t s = (cudaStream_t)stream;
+// One KDK step of all boxes (one box unless batched).  dt_req applies to every
+// box (<= 0: CFL); dt_box (device, one per box) overrides it when not null.
+static int step_impl(crk_ctx *ctx, int n, float *pos_h, float *vel_u, const float *mass, double dt_req,
+                     const double *dt_box, bool batched, cudaStream_t s) {
     StepConsts c = step_consts(ctx->p);
     int rc;
     int b = 256, g = grid_for(n, b);
-    if (!ctx->rates_valid || ctx->step_n != n || !ctx->built || ctx->n != n) {
-        rc = build_cells_sorted(ctx, n, (const float4 *)pos_h, nullptr, s);
+    const bool fresh = !ctx->rates_valid || ctx->step_n != n || !ctx->built || ctx->n != n ||
+                       (batched ? ctx->nbox < 1 : ctx->nbox > 1);
+    if (fresh) {
+        rc = build_cells_sorted(ctx, n, (const float4 *)pos_h, nullptr, s, batched ? ctx->box_in : nullptr);
         if (!rc) rc = finish_build(ctx, s);
         if (rc) return rc;
         rc = gather_rows(ctx, pos_h, ctx->st_pos, 4, s);
@@ -269,20 +325,24 @@ extern "C" int crk_step(crk_ctx *ctx, int n, float *pos_h, float *vel_u, const f
         if (!rc) rc = gather_rows(ctx, vel_u, ctx->st_vel, 4, s);
         if (rc) return rc;
     }
-    k_pick_dt<<<1, 1, 0, s>>>(dt, c.dt_max, ctx->counters + CNT_DTMIN, ctx->d_scalars);
+    const int nb = batched ? ctx->nbox : 1;
+    const int32_t *sbox = batched ? ctx->sbox : nullptr;
+    double *dtb = batched ? ctx->dtb : ctx->d_scalars;
+    k_pick_dt<<<grid_for(nb, 64), 64, 0, s>>>(nb, dt_req, dt_box, c.dt_max,
+                                               batched ? ctx->box_dtmin : ctx->counters + CNT_DTMIN, dtb);
     ++ctx->launches;
     // first half kick with the cached rates, compatible energy of that kick
-    k_kick1<<<g, b, 0, s>>>(n, ctx->d_scalars, ctx->st_vel, ctx->acc, ctx->vb, ctx->va);
+    k_kick1<<<g, b, 0, s>>>(n, dtb, sbox, ctx->st_vel, ctx->acc, ctx->vb, ctx->va);
     ++ctx->launches;
     CRK_LAUNCH_CHECK(ctx, "kick");
     rc = run_compatible(ctx, s);
     if (rc) return rc;
-    k_half_drift<<<g, b, 0, s>>>(n, ctx->d_scalars, ctx->st_pos, ctx->st_vel, ctx->st_half, ctx->va, ctx->acc,
-                                 ctx->du);
+    k_half_drift<<<g, b, 0, s>>>(n, dtb, sbox, ctx->st_pos, ctx->st_vel, ctx->st_half, ctx->va, ctx->acc, ctx->du);
     ++ctx->launches;
     CRK_LAUNCH_CHECK(ctx, "drift");
-    // rebuild at x1 (input order = current sorted order)
-    rc = build_cells_sorted(ctx, n, ctx->st_pos, ctx->perm, s);
+    // rebuild at x1 (input order = current sorted order; boxes keep their particles)
+    if (batched) CRK_CUDA(ctx, cudaMemcpyAsync(ctx->sbox_tmp, ctx->sbox, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
+    rc = build_cells_sorted(ctx, n, ctx->st_pos, ctx->perm, s, batched ? ctx->sbox_tmp : nullptr);
     if (!rc) rc = finish_build(ctx, s);
     if (rc) {
         ctx->rates_valid = 0;
@@ -304,38 +364,114 @@ extern "C" int crk_step(crk_ctx *ctx, int n, float *pos_h, float *vel_u, const f
         ctx->rates_valid = 0;
         return rc;
     }
-    // second half kick and its compatible energy
-    k_kick2<<<g, b, 0, s>>>(n, ctx->d_scalars, ctx->st_half, ctx->acc, ctx->vb, ctx->va);
+    // second half kick and its compatible energy (the boxes' dt of this step;
+    // the permutation kept every particle in its box)
+    k_kick2<<<g, b, 0, s>>>(n, dtb, sbox, ctx->st_half, ctx->acc, ctx->vb, ctx->va);
     ++ctx->launches;
     CRK_LAUNCH_CHECK(ctx, "kick");
     rc = run_compatible(ctx, s);
     if (rc) return rc;
-    k_finish<<<g, b, 0, s>>>(n, ctx->d_scalars, c, ctx->st_half, ctx->va, ctx->du, ctx->Nn, ctx->hs,
-                             ctx->st_vel, ctx->st_pos);
+    k_finish<<<g, b, 0, s>>>(n, dtb, sbox, c, ctx->st_half, ctx->va, ctx->du, ctx->Nn, ctx->hs, ctx->st_vel,
+                             ctx->st_pos);
     ++ctx->launches;
     CRK_LAUNCH_CHECK(ctx, "finish step");
     rc = scatter_rows(ctx, ctx->st_pos, pos_h, 4, s);
     if (!rc) rc = scatter_rows(ctx, ctx->st_vel, vel_u, 4, s);
+    return rc;
+}
+
+extern "C" int crk_step(crk_ctx *ctx, int n, float *pos_h, float *vel_u, const float *mass, double dt,
+                        crk_diag *diag, void *stream) {
+    if (!ctx) return CRK_EINVAL;
+    if (n <= 0 || !pos_h || !vel_u || !mass) return crk_set_error(ctx, CRK_EINVAL, "bad arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = step_impl(ctx, n, pos_h, vel_u, mass, dt, nullptr, false, s);
+    if (rc || !diag) return rc;
+    k_energy_partials<<<RED_BLOCKS, 256, 0, s>>>(n, ctx->st_vel, ctx->mass, ctx->d_red);
+    ++ctx->launches;
+    k_energy_final<<<1, 32, 0, s>>>(RED_BLOCKS, ctx->d_red, ctx->d_scalars + 2);
+    ++ctx->launches;
+    CRK_LAUNCH_CHECK(ctx, "diagnostics");
+    double h[8];
+    CRK_CUDA(ctx, cudaMemcpyAsync(h, ctx->d_scalars, sizeof(h), cudaMemcpyDeviceToHost, s));
+    rc = crk_sync_counters(ctx, s);
     if (rc) return rc;
-    if (diag) {
+    diag->dt = h[0];
+    diag->dt_next = (double)bits_to_float((uint32_t)ctx->h_counters[CNT_DTMIN]);
+    diag->E_kin = h[2];
+    diag->E_int = h[3];
+    diag->P[0] = h[4];
+    diag->P[1] = h[5];
+    diag->P[2] = h[6];
+    diag->pairs_gather = (long long)ctx->h_counters[CNT_PAIRS_G];
+    diag->pairs_union = (long long)ctx->h_counters[CNT_PAIRS_U];
+    return CRK_OK;
+}
+
+extern "C" int crk_step_batched(crk_ctx *ctx, int n, int nbox, const int32_t *box_start, float *pos_h,
+                                float *vel_u, const float *mass, const double *dt, crk_diag *diag, void *stream) {
+    if (!ctx) return CRK_EINVAL;
+    if (n <= 0 || !pos_h || !vel_u || !mass || !box_start) return crk_set_error(ctx, CRK_EINVAL, "bad arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    // the box table is loaded when it changes (and before the first batched step)
+    bool same = ctx->nbox == nbox && nbox >= 1 && ctx->box_start && ctx->rates_valid && ctx->step_n == n;
+    if (same) {
+        std::vector<int32_t> cur((size_t)nbox + 1);
+        CRK_CUDA(ctx, cudaMemcpyAsync(cur.data(), ctx->box_start, sizeof(int32_t) * ((size_t)nbox + 1),
+                                      cudaMemcpyDeviceToHost, s));
+        CRK_CUDA(ctx, cudaStreamSynchronize(s));
+        same = memcmp(cur.data(), box_start, sizeof(int32_t) * ((size_t)nbox + 1)) == 0;
+    }
+    int rc;
+    if (!same) {
+        ctx->rates_valid = 0;
+        rc = crk_ensure_particles(ctx, n);
+        if (!rc) rc = load_boxes(ctx, n, nbox, box_start, s);
+        if (rc) return rc;
+    }
+    const double *dt_box = nullptr;
+    if (dt) {   // one requested step per box (<= 0: that box's CFL step)
+        CRK_CUDA(ctx, cudaMemcpyAsync(ctx->box_red, dt, sizeof(double) * (size_t)nbox, cudaMemcpyHostToDevice, s));
+        CRK_CUDA(ctx, cudaStreamSynchronize(s));
+        dt_box = ctx->box_red;
+    }
+    rc = step_impl(ctx, n, pos_h, vel_u, mass, 0.0, dt_box, nbox > 1, s);
+    if (rc || !diag) return rc;
+    const int nb = nbox;
+    std::vector<double> red(8 * (size_t)nb), dts(nb);
+    std::vector<unsigned long long> dtn(nb);
+    if (nbox > 1) {
+        k_energy_box<<<nb, 256, 0, s>>>(ctx->box_start, ctx->st_vel, ctx->mass, ctx->box_red);
+        ++ctx->launches;
+        CRK_LAUNCH_CHECK(ctx, "diagnostics");
+        CRK_CUDA(ctx, cudaMemcpyAsync(red.data(), ctx->box_red, sizeof(double) * 8 * nb, cudaMemcpyDeviceToHost, s));
+        CRK_CUDA(ctx, cudaMemcpyAsync(dts.data(), ctx->dtb, sizeof(double) * nb, cudaMemcpyDeviceToHost, s));
+        CRK_CUDA(ctx, cudaMemcpyAsync(dtn.data(), ctx->box_dtmin, sizeof(unsigned long long) * nb,
+                                      cudaMemcpyDeviceToHost, s));
+    } else {
         k_energy_partials<<<RED_BLOCKS, 256, 0, s>>>(n, ctx->st_vel, ctx->mass, ctx->d_red);
-        ++ctx->launches;
         k_energy_final<<<1, 32, 0, s>>>(RED_BLOCKS, ctx->d_red, ctx->d_scalars + 2);
-        ++ctx->launches;
+        ctx->launches += 2;
         CRK_LAUNCH_CHECK(ctx, "diagnostics");
         double h[8];
         CRK_CUDA(ctx, cudaMemcpyAsync(h, ctx->d_scalars, sizeof(h), cudaMemcpyDeviceToHost, s));
-        rc = crk_sync_counters(ctx, s);
-        if (rc) return rc;
-        diag->dt = h[0];
-        diag->dt_next = (double)bits_to_float((uint32_t)ctx->h_counters[CNT_DTMIN]);
-        diag->E_kin = h[2];
-        diag->E_int = h[3];
-        diag->P[0] = h[4];
-        diag->P[1] = h[5];
-        diag->P[2] = h[6];
-        diag->pairs_gather = (long long)ctx->h_counters[CNT_PAIRS_G];
-        diag->pairs_union = (long long)ctx->h_counters[CNT_PAIRS_U];
+        CRK_CUDA(ctx, cudaStreamSynchronize(s));
+        for (int k = 0; k < 5; k++) red[k] = h[2 + k];
+        dts[0] = h[0];
+    }
+    rc = crk_sync_counters(ctx, s);
+    if (rc) return rc;
+    if (nbox == 1) dtn[0] = ctx->h_counters[CNT_DTMIN];
+    for (int b = 0; b < nb; b++) {
+        diag[b].dt = dts[b];
+        diag[b].dt_next = (double)bits_to_float((uint32_t)dtn[b]);
+        diag[b].E_kin = red[8 * b + 0];
+        diag[b].E_int = red[8 * b + 1];
+        diag[b].P[0] = red[8 * b + 2];
+        diag[b].P[1] = red[8 * b + 3];
+        diag[b].P[2] = red[8 * b + 4];
+        diag[b].pairs_gather = (long long)ctx->h_counters[CNT_PAIRS_G];
+        diag[b].pairs_union = (long long)ctx->h_counters[CNT_PAIRS_U];
     }
     return CRK_OK;
 }

@@ -32,6 +32,8 @@ struct WalkArgs {
     uint32_t *len_g, *len_u; // per-tile max counts
     unsigned long long *pairs_g, *pairs_u, *maxcnt;
     uint32_t *ent;
+    const int32_t *sbox;     // batched boxes: box of each slot (BATCH only)
+    const uint32_t *nbox;    // box range of each tile (BATCH only)
 };
 
 // LISTS: write the lists; VOL: sum n_i in the walk (volumes-only contexts).
@@ -42,9 +44,12 @@ __device__ __forceinline__ unsigned long long point_gap(uint32_t q, uint32_t lo,
     return (unsigned long long)(d1 < d2 ? d1 : d2);
 }
 
-template <bool LISTS, bool VOL>
+// BATCH: the particles belong to independent boxes; j can be a neighbour of i
+// only in i's box (the box ranges of tiles prune the rest).
+template <bool LISTS, bool VOL, bool BATCH>
 __global__ void __launch_bounds__(WALK_WARPS * 32) k_walk(WalkArgs a) {
     __shared__ uint4 sq[WALK_WARPS][32];
+    __shared__ int32_t sb[WALK_WARPS][BATCH ? 32 : 1];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int tile = blockIdx.x * WALK_WARPS + w;
     if (tile >= a.ntiles) return;
@@ -60,6 +65,8 @@ __global__ void __launch_bounds__(WALK_WARPS * 32) k_walk(WalkArgs a) {
     int cg = 0, co = 0;
     const uint2 lo = a.ofs[tile];
     const uint4 Ilo = __ldg(a.tlo + tile), Ihi = __ldg(a.thi + tile);   // this tile's box, max H
+    const int32_t bi = BATCH && valid ? a.sbox[i] : 0;
+    const uint32_t Ib = BATCH ? __ldg(a.nbox + tile) : 0u;
     // software pipeline over the candidate tiles: the tile id two ahead and
     // the box of the next tile are in flight while the current tile is tested
     // (each is otherwise a dependent L2 trip)
@@ -84,7 +91,11 @@ __global__ void __launch_bounds__(WALK_WARPS * 32) k_walk(WalkArgs a) {
         const unsigned long long gx = point_gap(qi.x, Jlo.x, Jhi.x), gy = point_gap(qi.y, Jlo.y, Jhi.y),
                                  gz = point_gap(qi.z, Jlo.z, Jhi.z);
         const unsigned long long reach = qi.w > Jlo.w ? qi.w : Jlo.w;
-        const bool near = valid && gx * gx + gy * gy + gz * gz < reach * reach;
+        bool near = valid && gx * gx + gy * gy + gz * gz < reach * reach;
+        if (BATCH) {
+            const uint32_t Jb = __ldg(a.nbox + J);
+            near = near && (uint32_t)bi >= (Jb & 0xffffu) && (uint32_t)bi <= (Jb >> 16);
+        }
         if (__ballot_sync(0xffffffffu, near) == 0u) continue;
         const int j0 = J * TILE;
         const int cnt = min(TILE, a.n - j0);
@@ -101,6 +112,11 @@ __global__ void __launch_bounds__(WALK_WARPS * 32) k_walk(WalkArgs a) {
                                      hz = point_gap(q.z, Ilo.z, Ihi.z);
             const unsigned long long rj = q.w > Ilo.w ? q.w : Ilo.w;
             keep = hx * hx + hy * hy + hz * hz < rj * rj;
+            if (BATCH) {
+                const int32_t bj = __ldg(a.sbox + j0 + lane);
+                sb[w][lane] = bj;
+                keep = keep && (uint32_t)bj >= (Ib & 0xffffu) && (uint32_t)bj <= (Ib >> 16);
+            }
         }
         unsigned mask = __ballot_sync(0xffffffffu, keep);
         __syncwarp();
@@ -109,7 +125,7 @@ __global__ void __launch_bounds__(WALK_WARPS * 32) k_walk(WalkArgs a) {
             mask &= mask - 1u;
             const uint4 qj = sq[w][jj];
             const int dx = (int)(qi.x - qj.x), dy = (int)(qi.y - qj.y), dz = (int)(qi.z - qj.z);
-            const unsigned long long R2 = r2_fixed(dx, dy, dz);
+            const unsigned long long R2 = (BATCH && sb[w][jj] != bi) ? ~0ull : r2_fixed(dx, dy, dz);
             const bool in_i = R2 < Hi2;
             if (VOL && in_i) {
                 Sep d = separation(dx, dy, dz);
@@ -183,6 +199,8 @@ static WalkArgs walk_args(crk_ctx *ctx) {
     a.pairs_u = ctx->counters + CNT_PAIRS_U;
     a.maxcnt = ctx->counters + CNT_MAXCNT;
     a.ent = ctx->volumes_only ? nullptr : ctx->ent;
+    a.sbox = ctx->nbox > 1 ? ctx->sbox : nullptr;
+    a.nbox = ctx->nbox > 1 ? ctx->node_box : nullptr;
     return a;
 }
 
@@ -194,10 +212,16 @@ static int launch_walk(crk_ctx *ctx, cudaStream_t s) {
     CRK_CUDA(ctx, cudaMemsetAsync(ctx->counters + CNT_PAIRS_G, 0, 2 * sizeof(unsigned long long), s));
     CRK_CUDA(ctx, cudaMemsetAsync(ctx->counters + CNT_MAXCNT, 0, sizeof(unsigned long long), s));
     prof_begin(ctx, PROF_LISTS, s);
-    if (ctx->volumes_only)
-        k_walk<false, true><<<grid_for(ctx->ntiles, WALK_WARPS), WALK_WARPS * 32, 0, s>>>(walk_args(ctx));
+    const int g = grid_for(ctx->ntiles, WALK_WARPS);
+    const bool b = ctx->nbox > 1;
+    if (ctx->volumes_only && b)
+        k_walk<false, true, true><<<g, WALK_WARPS * 32, 0, s>>>(walk_args(ctx));
+    else if (ctx->volumes_only)
+        k_walk<false, true, false><<<g, WALK_WARPS * 32, 0, s>>>(walk_args(ctx));
+    else if (b)
+        k_walk<true, false, true><<<g, WALK_WARPS * 32, 0, s>>>(walk_args(ctx));
     else
-        k_walk<true, false><<<grid_for(ctx->ntiles, WALK_WARPS), WALK_WARPS * 32, 0, s>>>(walk_args(ctx));
+        k_walk<true, false, false><<<g, WALK_WARPS * 32, 0, s>>>(walk_args(ctx));
     ++ctx->launches;
     prof_end(ctx, s);
     CRK_LAUNCH_CHECK(ctx, "neighbour walk");

@@ -1,0 +1,132 @@
+"""Batched boxes: independent periodic boxes in one particle set.
+
+Each box is its own problem, so the oracle checks each box on its own: the
+neighbour sets of a batched build must equal each box's brute-force sets
+bit for bit (a particle never sees another box), every pass must match the
+oracle box by box, and a batched step must advance each box as a step of
+that box alone would (with its own CFL time step)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import crk as O
+from paper_2202_02840_gb300 import crk, inputs
+from parity import TOL, as_np, rel_err, set_hash, workload
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _device():
+    import __graft_entry__
+    __graft_entry__.build()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    torch.cuda.set_device(0)
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def boxes():
+    """Three boxes of uneven size and structure (uniform, clumped, blast)."""
+    return [workload("uniform", 16), workload("clustered", 1500, 5), workload("sedov", 14)]
+
+
+def concat(sts):
+    start = np.cumsum([0] + [s["pos_h"].shape[0] for s in sts])
+    cat = {k: np.concatenate([s[k] for s in sts]) for k in ("pos_h", "vel_u", "mass")}
+    return cat, [int(x) for x in start]
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_batched_neighbour_sets_are_per_box(mode):
+    sts = boxes()
+    cat, start = concat(sts)
+    ctx = crk.crk_create()
+    crk.crk_build_cells_batched(ctx, dev(cat["pos_h"]), start)
+    cnt, hsh = crk.crk_neighbours(ctx, mode)
+    cnt, hsh = cnt.cpu().numpy(), hsh.cpu().numpy().view(np.uint32)
+    for b, st in enumerate(sts):
+        oc, ol = O.neighbours(st["pos_h"], mode=mode)
+        sl = slice(start[b], start[b + 1])
+        assert np.array_equal(cnt[sl], oc), b
+        assert np.array_equal(hsh[sl], set_hash(oc, ol + start[b])), b
+
+
+def test_batched_passes_match_each_box():
+    sts = boxes()
+    cat, start = concat(sts)
+    ctx = crk.crk_create()
+    crk.crk_build_cells_batched(ctx, dev(cat["pos_h"]), start)
+    V, N, pairs = crk.crk_volumes(ctx, with_pairs=True)
+    vel = dev(cat["vel_u"])
+    A, B, gA, gB, gv = crk.crk_corrections(ctx, V, vel)
+    acc, dudt, vsig, qmax = crk.crk_forces(ctx, dev(cat["mass"]), vel, V, A, B, gA, gB, gv)
+    tot_pairs = 0
+    for b, st in enumerate(sts):
+        sl = slice(start[b], start[b + 1])
+        ev = O.evaluate(st)
+        tot_pairs += ev["pairs"]
+        e = {k: rel_err(as_np(g)[sl], ev[k]) for k, g in (("V", V), ("A", A), ("gv", gv), ("dudt", dudt),
+                                                          ("vsig", vsig))}
+        e.update({k: rel_err(as_np(g)[sl], ev[k], floor=ev["s" + k]) for k, g in (("B", B), ("gA", gA),
+                                                                                  ("gB", gB))})
+        e["acc"] = rel_err(as_np(acc)[sl], ev["acc"], floor=ev["fscale"])
+        print("box", b, e)
+        assert max(e.values()) < 10 * TOL, (b, e)
+    assert pairs == tot_pairs
+
+
+def test_batched_step_matches_single_box_steps():
+    """Three KDK steps of all boxes at once against each box stepped alone."""
+    sts = boxes()
+    cat, start = concat(sts)
+    pos, vel, mass = dev(cat["pos_h"]), dev(cat["vel_u"]), dev(cat["mass"])
+    ctx = crk.crk_create()
+    single = []
+    for st in sts:
+        single.append((dev(st["pos_h"]), dev(st["vel_u"]), dev(st["mass"]), crk.crk_create()))
+    for step in range(3):
+        d = crk.crk_step_batched(ctx, pos, vel, mass, start, diag=True)
+        for b, (p, v, m, c) in enumerate(single):
+            ds = crk.crk_step(c, p, v, m, 0.0, diag=True)
+            assert abs(d[b]["dt"] - ds["dt"]) <= 1e-5 * ds["dt"], (step, b, d[b]["dt"], ds["dt"])
+            E, Es = d[b]["E_kin"] + d[b]["E_int"], ds["E_kin"] + ds["E_int"]
+            assert abs(E - Es) <= 1e-6 * abs(Es), (step, b)
+    gp, gv = pos.cpu().numpy(), vel.cpu().numpy()
+    for b, (p, v, m, c) in enumerate(single):
+        sl = slice(start[b], start[b + 1])
+        sp, sv = p.cpu().numpy(), v.cpu().numpy()
+        dx = np.abs(gp[sl, :3] - sp[:, :3])
+        dx = np.minimum(dx, 1.0 - dx)
+        e = {"x": float(dx.max()), "h": rel_err(gp[sl, 3], sp[:, 3]), "v": rel_err(gv[sl, :3], sv[:, :3]),
+             "u": rel_err(gv[sl, 3], sv[:, 3])}
+        print("box", b, e)
+        assert e["x"] < 1e-6 and max(e["h"], e["v"], e["u"]) < 10 * TOL, (b, e)
+
+
+def test_batched_fixed_steps_and_single_box_table():
+    """Per-box fixed dt is honoured; a one-box table is the plain step."""
+    sts = boxes()[:2]
+    cat, start = concat(sts)
+    ctx = crk.crk_create()
+    pos, vel, mass = dev(cat["pos_h"]), dev(cat["vel_u"]), dev(cat["mass"])
+    d = crk.crk_step_batched(ctx, pos, vel, mass, start, dt=[1e-4, 2e-4], diag=True)
+    assert d[0]["dt"] == 1e-4 and d[1]["dt"] == 2e-4
+    st = sts[0]
+    p1, v1, m1 = dev(st["pos_h"]), dev(st["vel_u"]), dev(st["mass"])
+    p2, v2 = p1.clone(), v1.clone()
+    c1, c2 = crk.crk_create(), crk.crk_create()
+    crk.crk_step_batched(c1, p1, v1, m1, [0, p1.shape[0]])
+    crk.crk_step(c2, p2, v2, m1, 0.0)
+    assert torch.equal(p1, p2) and torch.equal(v1, v2)
+
+
+@pytest.mark.parametrize("table", [[0, 100, 50, 4096], [0, 100, 4000], [1, 4096], []])
+def test_bad_box_tables_are_rejected(table):
+    st = workload("uniform", 16)
+    ctx = crk.crk_create()
+    with pytest.raises(crk.CrkError) as ei:
+        crk.crk_build_cells_batched(ctx, dev(st["pos_h"]), table)
+    assert ei.value.code == -1

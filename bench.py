@@ -281,6 +281,62 @@ def learned_h_report(dev, train_side=64, train_steps=200, every=10, eval_side=25
                                                    "the pass also evaluates 128 SFU tanh per row"}}}
 
 
+# --------------------------------------------------------------------- batched boxes
+
+def batched_report(dev, nbox=64, steps=10, warmup=2, seq_steps=2):
+    """Many independent Sedov boxes of uneven size (sides 16..96) stepped
+    together by crk_step_batched, against the same boxes stepped one by one."""
+    import torch
+    from paper_2202_02840_gb300 import crk, inputs
+
+    bx = inputs.sedov_boxes(nbox)
+    start = bx["box_start"]
+    n = start[-1]
+    pos = torch.from_numpy(bx["pos_h"]).to(dev)
+    vel = torch.from_numpy(bx["vel_u"]).to(dev)
+    mass = torch.from_numpy(bx["mass"]).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    ctx = crk.crk_create()
+    for _ in range(warmup):
+        crk.crk_step_batched(ctx, pos, vel, mass, start)
+    torch.cuda.synchronize(dev)
+    launches0 = crk.crk_launches(ctx)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        crk.crk_step_batched(ctx, pos, vel, mass, start)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / steps
+    launches = (crk.crk_launches(ctx) - launches0) / steps
+    d = crk.crk_step_batched(ctx, pos, vel, mass, start, diag=True)
+    pairs = 3 * d[0]["pairs_gather"] + 3 * d[0]["pairs_union"]
+    ctx.close()
+    # the same boxes one by one: one context each, timed after one warm-up step
+    seq_ms = 0.0
+    seq_launches = 0
+    for b in range(nbox):
+        sl = slice(start[b], start[b + 1])
+        p, v, m = (torch.from_numpy(bx[k][sl]).to(dev) for k in ("pos_h", "vel_u", "mass"))
+        c = crk.crk_create()
+        crk.crk_step(c, p, v, m, 0.0)
+        torch.cuda.synchronize(dev)
+        l0 = crk.crk_launches(c)
+        e0.record(stream)
+        for _ in range(seq_steps):
+            crk.crk_step(c, p, v, m, 0.0)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        seq_ms += e0.elapsed_time(e1) / seq_steps
+        seq_launches += (crk.crk_launches(c) - l0) / seq_steps
+        c.close()
+    return {"workload": "%d Sedov boxes, sides uniform in 16..96 (seeds 0..%d), %d particles" % (nbox, nbox - 1, n),
+            "n": n, "sides_min_max": [min(bx["sides"]), max(bx["sides"])], "steps": steps,
+            "ms_per_step": ms, "pair_interactions_per_s": pairs / (ms / 1e3), "kernel_launches_per_step": launches,
+            "one_by_one_ms_per_step": seq_ms, "one_by_one_launches_per_step": seq_launches,
+            "speedup_vs_one_by_one": seq_ms / ms}
+
+
 # --------------------------------------------------------------------- GPU arm
 
 def aggregate(times_ms, work, dist=None, device="cpu"):
@@ -431,6 +487,8 @@ def run_gpu(args):
                 "gpu_launches": launches, "clocks": clk}
         if not args.no_learned_h and world == 1:
             line["learned_h"] = learned_h_report(dev)
+        if not args.no_batched and world == 1:
+            line["batched"] = batched_report(dev)
         if not args.no_cpu_baseline and world == 1:
             from oracle import crk as O
             p, dt, ns = calibrated_oracle(st, args.cpu_seconds, seed=2)
@@ -454,6 +512,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-learned-h", action="store_true", help="skip the learned-h training and evaluation")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-boxes measurement")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -173,6 +173,19 @@ def zeldovich(n_side: int = 128, seed: int = 4, seed_u: int = 5, contrast: float
     return out
 
 
+def sedov_boxes(nbox: int = 64, side_lo: int = 16, side_hi: int = 96, seed: int = 0) -> dict:
+    """Independent Sedov boxes for the batched step: box b is sedov(side_b,
+    seed=b) with side_b drawn uniformly from the integers side_lo..side_hi;
+    arrays concatenated box-major, box_start[b] = first row of box b."""
+    sides = rng(7000 + int(seed)).integers(side_lo, side_hi + 1, nbox)
+    parts = [sedov(int(sd), seed=b) for b, sd in enumerate(sides)]
+    start = np.cumsum([0] + [p["pos_h"].shape[0] for p in parts])
+    out = {k: np.concatenate([p[k] for p in parts]) for k in ("pos_h", "vel_u", "mass")}
+    out["box_start"] = [int(x) for x in start]
+    out["sides"] = [int(x) for x in sides]
+    return out
+
+
 def mlp_init(seed: int = 0) -> np.ndarray:
     """Seeded initial parameters of the 8-64-64-1 network, packed as
     [W1 (64x8), b1, W2 (64x64), b2, W3, b3]: fan-in scaled normal hidden

@@ -81,6 +81,8 @@ def lib():
         L.crk_h_select.argtypes = [_vp, _ci, _vp, ctypes.c_float, _ci, _vp, ctypes.POINTER(_ci), _vp]
         L.crk_build_cells_batched.argtypes = [_vp, _ci, _ci, _vp, _vp, _vp]
         L.crk_step_batched.argtypes = [_vp, _ci, _ci, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
+        L.crk_autotune.argtypes = [_vp, _ci]
+        L.crk_tuning.argtypes = [_vp, _vp, _vp]
         L.crk_profile.argtypes = [_vp, _ci]
         L.crk_profile_read.argtypes = [_vp, _vp, _vp, ctypes.POINTER(ctypes.c_longlong)]
         _LIB = L
@@ -431,3 +433,17 @@ def crk_step_batched(ctx, pos_h, vel_u, mass, box_start, dt=None, diag=False, st
         return None
     return [{"dt": x.dt, "dt_next": x.dt_next, "E_kin": x.E_kin, "E_int": x.E_int, "P": list(x.P),
              "pairs_gather": x.pairs_gather, "pairs_union": x.pairs_union} for x in d]
+
+
+# ---------------------------------------------------------------- autotuner
+
+def crk_autotune(ctx, enable=True):
+    ctx.check(lib().crk_autotune(ctx.handle, 1 if enable else 0))
+
+
+def crk_tuning(ctx):
+    """{pass name: (variant, ms)} for the tuned passes."""
+    v = (ctypes.c_int * NPASS)()
+    ms = (ctypes.c_float * NPASS)()
+    ctx.check(lib().crk_tuning(ctx.handle, v, ms))
+    return {PASS_NAMES[k]: (v[k], ms[k]) for k in range(NPASS) if v[k] >= 0}

@@ -548,6 +548,35 @@ int build_cells_sorted(crk_ctx *ctx, int n, const float4 *pos, const int32_t *ba
     return CRK_OK;
 }
 
+__global__ void k_len_keys(int nt, const uint32_t *__restrict__ len, uint32_t *__restrict__ key,
+                           int32_t *__restrict__ idx) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nt) return;
+    key[t] = 0xffffu - min(len[t], 0xffffu);
+    idx[t] = t;
+}
+
+// ctx->tile_order = tiles sorted by decreasing pair-set list length (stable:
+// equal lengths keep Morton order), for the longest-first pass variants.
+int tile_order_by_length(crk_ctx *ctx, cudaStream_t s) {
+    const int nt = ctx->ntiles;
+    if (nt > ctx->cap_order) {
+        if (ctx->tile_order) cudaFree(ctx->tile_order);
+        ctx->tile_order = nullptr;
+        ctx->cap_order = 0;
+        CRK_CUDA(ctx, cudaMalloc((void **)&ctx->tile_order, sizeof(int32_t) * (size_t)nt));
+        ctx->cap_order = nt;
+    }
+    k_len_keys<<<grid_for(nt, 256), 256, 0, s>>>(nt, ctx->len_u, ctx->key_a, ctx->idx_a);
+    ++ctx->launches;
+    int rc = radix_sort(ctx, nt, 16, s);
+    if (rc) return rc;
+    CRK_CUDA(ctx, cudaMemcpyAsync(ctx->tile_order, ctx->idx_a, sizeof(int32_t) * (size_t)nt,
+                                  cudaMemcpyDeviceToDevice, s));
+    CRK_LAUNCH_CHECK(ctx, "tile order");
+    return CRK_OK;
+}
+
 int cell_level_host(const crk_ctx *ctx) {
     uint32_t bits = (uint32_t)ctx->h_counters[CNT_HMAX];
     float hmax;

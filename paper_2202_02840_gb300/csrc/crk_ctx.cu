@@ -307,6 +307,27 @@ static void prof_free(crk_ctx *ctx) {
     ctx->prof_cap = 0;
 }
 
+extern "C" int crk_autotune(crk_ctx *ctx, int enable) {
+    if (!ctx) return CRK_EINVAL;
+    if (enable && !ctx->tune_ev[0]) {
+        if (cudaEventCreate(&ctx->tune_ev[0]) != cudaSuccess || cudaEventCreate(&ctx->tune_ev[1]) != cudaSuccess)
+            return crk_set_error(ctx, CRK_ECUDA, "cudaEventCreate");
+    }
+    ctx->tune_on = enable ? 1 : 0;
+    if (enable)
+        for (int k = 0; k < 16; k++) ctx->tune_done[k] = 0;
+    return CRK_OK;
+}
+
+extern "C" int crk_tuning(crk_ctx *ctx, int *variant, float *ms) {
+    if (!ctx) return CRK_EINVAL;
+    for (int k = 0; k < CRK_PROF_NPASS; k++) {
+        if (variant) variant[k] = ctx->tune_done[k] ? ctx->tune_choice[k] : -1;
+        if (ms) ms[k] = ctx->tune_done[k] ? ctx->tune_ms[k] : 0.f;
+    }
+    return CRK_OK;
+}
+
 extern "C" int crk_profile(crk_ctx *ctx, int enable) {
     if (!ctx) return CRK_EINVAL;
     if (enable && !ctx->prof_ev) {
@@ -430,6 +451,9 @@ extern "C" int crk_destroy(crk_ctx *ctx) {
     dfree(&ctx->box_start); dfree(&ctx->dtb); dfree(&ctx->box_dtmin); dfree(&ctx->box_red);
     dfree(&ctx->box_in); dfree(&ctx->sbox); dfree(&ctx->sbox_tmp); dfree(&ctx->mkey); dfree(&ctx->node_box);
     if (ctx->h_counters) cudaFreeHost(ctx->h_counters);
+    for (int k = 0; k < 2; k++)
+        if (ctx->tune_ev[k]) cudaEventDestroy(ctx->tune_ev[k]);
+    if (ctx->tile_order) cudaFree(ctx->tile_order);
     mlp_free(ctx);
     prof_free(ctx);
     delete ctx;

@@ -172,6 +172,15 @@ struct crk_ctx {
     uint32_t *sel = nullptr;         // row selection: flags and their scan (2 x cap_sel)
     int cap_sel = 0;
 
+    // autotuner of the list passes (variant per pass; -1 = the built-in default)
+    int tune_on = 0;
+    int tune_done[16] = {0};
+    int tune_choice[16] = {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1};
+    float tune_ms[16] = {0};
+    cudaEvent_t tune_ev[2] = {nullptr, nullptr};
+    int32_t *tile_order = nullptr;   // tiles by decreasing pair-set list length
+    int cap_order = 0;
+
     // launch accounting and per-pass event timing
     long long launches = 0;
     int prof_on = 0;

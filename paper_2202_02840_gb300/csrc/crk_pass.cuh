@@ -121,7 +121,7 @@ struct ListGeom {
 // best: 4 for P1 and P2, 3 for P3 and P5).  P4, whose 160-byte record
 // already fills the registers, keeps one pair per iteration and instead
 // prefetches the record of entry k + 1 and the entry k + 2 (P::PREFETCH).
-template <class P>
+template <class P, int U>
 __device__ __forceinline__ void lpass_tile(const ListGeom &g, const typename P::Params &prm, int tile, int lane) {
     const int i = tile * TILE + lane;
     const bool valid = i < g.n;
@@ -139,7 +139,6 @@ __device__ __forceinline__ void lpass_tile(const ListGeom &g, const typename P::
     if (!P::PREFETCH) {
         // U entries per iteration: U independent gathers and pair evaluations
         // in flight per lane, the next U entries prefetched
-        constexpr int U = P::UNROLL;
         constexpr bool E = P::ENTRIES;
         uint32_t en[U];
 #pragma unroll
@@ -184,12 +183,14 @@ __device__ __forceinline__ void lpass_tile(const ListGeom &g, const typename P::
     if (valid) P::finish(st, i, prm);
 }
 
-template <class P, int WARPS, int MINB = 1>
-__global__ void __launch_bounds__(WARPS * 32, MINB) k_lpass(ListGeom g, typename P::Params prm) {
+// Grid form: warp w of block b takes tile order[b WARPS + w] (order null:
+// tiles in Morton order).
+template <class P, int WARPS, int U>
+__global__ void __launch_bounds__(WARPS * 32) k_lpass(ListGeom g, typename P::Params prm, const int32_t *order) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int tile = blockIdx.x * WARPS + w;
-    if (tile >= g.ntiles) return;
-    lpass_tile<P>(g, prm, tile, lane);
+    const int t = blockIdx.x * WARPS + w;
+    if (t >= g.ntiles) return;
+    lpass_tile<P, U>(g, prm, order ? order[t] : t, lane);
 }
 
 // Persistent form (one warp per block, as many blocks as fit at once): SM s
@@ -199,7 +200,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) k_lpass(ListGeom g, typename
 // warp whose range is exhausted claims tiles from the other ranges.  Every
 // claim is one atomicAdd; a range's counter runs past chunk at most once per
 // warp, so the loop is bounded.
-template <class P>
+template <class P, int U>
 __global__ void __launch_bounds__(32) k_lpass_sm(ListGeom g, typename P::Params prm, uint32_t *next, int nrange,
                                                  int chunk) {
     const int lane = threadIdx.x & 31;
@@ -215,9 +216,80 @@ __global__ void __launch_bounds__(32) k_lpass_sm(ListGeom g, typename P::Params 
             if (t >= (uint32_t)chunk) break;
             const long long tile = (long long)range * chunk + t;
             if (tile >= g.ntiles) break;
-            lpass_tile<P>(g, prm, (int)tile, lane);
+            lpass_tile<P, U>(g, prm, (int)tile, lane);
         }
     }
+}
+
+// ---------------------------------------------------------------- autotuner
+//
+// Variants of a list pass: the loop form (U pairs per iteration for the small
+// records; U is 1 for P4's prefetching loop) and the order tiles are taken in
+// (Morton in the grid; contiguous per-SM ranges in the persistent form;
+// longest list first in the grid).  Every variant visits each particle's list
+// in the same order, so all give bitwise identical results; the tuner times
+// each once on the first evaluation after crk_autotune(ctx, 1) and keeps the
+// fastest per pass.
+enum { ORD_GRID = 0, ORD_SM = 1, ORD_LONGEST = 2 };
+struct LVariant {
+    int U, ord;
+};
+constexpr int NVAR = 9;
+__host__ __device__ constexpr LVariant lvariant(int v) {
+    return v < 4 ? LVariant{v + 1, ORD_GRID} : (v < 8 ? LVariant{v - 3, ORD_LONGEST} : LVariant{1, ORD_SM});
+}
+
+int tile_order_by_length(crk_ctx *ctx, cudaStream_t s);   // ctx->tile_order, longest pair-set list first
+
+template <class P, int WARPS, int U>
+static void launch_variant_u(crk_ctx *ctx, const ListGeom &g, const typename P::Params &prm, int ord,
+                             cudaStream_t s) {
+    if (ord == ORD_SM) {
+        static int per_sm = 0;
+        if (!per_sm) {
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lpass_sm<P, U>, 32, 0) != cudaSuccess ||
+                per_sm < 1)
+                per_sm = 1;
+        }
+        const int nrange = ctx->nsm > 0 ? (ctx->nsm < 1024 ? ctx->nsm : 1024) : 1;
+        const int chunk = (ctx->ntiles + nrange - 1) / nrange;
+        cudaMemsetAsync(ctx->sm_next, 0, sizeof(uint32_t) * nrange, s);
+        k_lpass_sm<P, U><<<nrange * per_sm, 32, 0, s>>>(g, prm, ctx->sm_next, nrange, chunk);
+    } else {
+        k_lpass<P, WARPS, U><<<grid_for(ctx->ntiles, WARPS), WARPS * 32, 0, s>>>(
+            g, prm, ord == ORD_LONGEST ? ctx->tile_order : nullptr);
+    }
+}
+
+template <class P, int WARPS>
+static int launch_variant(crk_ctx *ctx, const ListGeom &g, const typename P::Params &prm, int v, cudaStream_t s) {
+    const LVariant lv = lvariant(v);
+    if (lv.ord == ORD_LONGEST) {
+        int rc = tile_order_by_length(ctx, s);
+        if (rc) return rc;
+    }
+    if constexpr (P::PREFETCH) {
+        launch_variant_u<P, WARPS, 1>(ctx, g, prm, lv.ord, s);
+    } else {
+        switch (lv.U) {
+        case 1: launch_variant_u<P, WARPS, 1>(ctx, g, prm, lv.ord, s); break;
+        case 2: launch_variant_u<P, WARPS, 2>(ctx, g, prm, lv.ord, s); break;
+        case 3: launch_variant_u<P, WARPS, 3>(ctx, g, prm, lv.ord, s); break;
+        default: launch_variant_u<P, WARPS, 4>(ctx, g, prm, lv.ord, s); break;
+        }
+    }
+    return CRK_OK;
+}
+
+// the measured default of each pass (before or without tuning)
+template <class P>
+constexpr int default_variant() {
+    return P::PREFETCH ? (P::PERSISTENT ? 8 : 0) : P::UNROLL - 1;
+}
+
+template <class P>
+constexpr bool variant_applies(int v) {
+    return P::PREFETCH ? (lvariant(v).U == 1) : true;
 }
 
 template <class P, int WARPS, int MINB = 1>
@@ -226,22 +298,35 @@ int launch_lpass(crk_ctx *ctx, int prof_id, const typename P::Params &prm, cudaS
     if (!ctx->lists_valid) return crk_set_error(ctx, CRK_ESTATE, "%s: neighbour lists are not built", what);
     ListGeom g{ctx->n, ctx->ntiles, ctx->kcap, ctx->tbase, ctx->len_g, ctx->len_u, ctx->cnt_g, ctx->cnt_u,
                ctx->ent};
-    if constexpr (P::PERSISTENT) {
-        static int per_sm = 0;
-        if (!per_sm) {
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lpass_sm<P>, 32, 0) != cudaSuccess ||
-                per_sm < 1)
-                per_sm = 1;
+    int rc;
+    if (ctx->tune_on && !ctx->tune_done[prof_id]) {
+        // time every applicable variant once (each recomputes the same outputs)
+        float best = 3.0e38f;
+        int bestv = default_variant<P>();
+        for (int v = 0; v < NVAR; v++) {
+            if (!variant_applies<P>(v)) continue;
+            CRK_CUDA(ctx, cudaEventRecord(ctx->tune_ev[0], s));
+            rc = launch_variant<P, WARPS>(ctx, g, prm, v, s);
+            if (rc) return rc;
+            CRK_CUDA(ctx, cudaEventRecord(ctx->tune_ev[1], s));
+            ++ctx->launches;
+            CRK_LAUNCH_CHECK(ctx, what);
+            CRK_CUDA(ctx, cudaEventSynchronize(ctx->tune_ev[1]));
+            float ms = 0.f;
+            CRK_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->tune_ev[0], ctx->tune_ev[1]));
+            if (ms < best) {
+                best = ms;
+                bestv = v;
+            }
         }
-        const int nrange = ctx->nsm > 0 ? (ctx->nsm < 1024 ? ctx->nsm : 1024) : 1;
-        const int chunk = (ctx->ntiles + nrange - 1) / nrange;
-        CRK_CUDA(ctx, cudaMemsetAsync(ctx->sm_next, 0, sizeof(uint32_t) * nrange, s));
-        prof_begin(ctx, prof_id, s);
-        k_lpass_sm<P><<<nrange * per_sm, 32, 0, s>>>(g, prm, ctx->sm_next, nrange, chunk);
-    } else {
-        prof_begin(ctx, prof_id, s);
-        k_lpass<P, WARPS, MINB><<<grid_for(ctx->ntiles, WARPS), WARPS * 32, 0, s>>>(g, prm);
+        ctx->tune_choice[prof_id] = bestv;
+        ctx->tune_ms[prof_id] = best;
+        ctx->tune_done[prof_id] = 1;
     }
+    const int v = ctx->tune_choice[prof_id] >= 0 ? ctx->tune_choice[prof_id] : default_variant<P>();
+    prof_begin(ctx, prof_id, s);
+    rc = launch_variant<P, WARPS>(ctx, g, prm, v, s);
+    if (rc) return rc;
     ++ctx->launches;
     prof_end(ctx, s);
     CRK_LAUNCH_CHECK(ctx, what);

@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(WALK_WARPS * 32) k_walk(WalkArgs a) {
                                  gz = point_gap(qi.z, Jlo.z, Jhi.z);
         const unsigned long long reach = qi.w > Jlo.w ? qi.w : Jlo.w;
         bool near = valid && gx * gx + gy * gy + gz * gz < reach * reach;
-        if (BATCH) {
+        if constexpr (BATCH) {
             const uint32_t Jb = __ldg(a.nbox + J);
             near = near && (uint32_t)bi >= (Jb & 0xffffu) && (uint32_t)bi <= (Jb >> 16);
         }
@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(WALK_WARPS * 32) k_walk(WalkArgs a) {
                                      hz = point_gap(q.z, Ilo.z, Ihi.z);
             const unsigned long long rj = q.w > Ilo.w ? q.w : Ilo.w;
             keep = hx * hx + hy * hy + hz * hz < rj * rj;
-            if (BATCH) {
+            if constexpr (BATCH) {
                 const int32_t bj = __ldg(a.sbox + j0 + lane);
                 sb[w][lane] = bj;
                 keep = keep && (uint32_t)bj >= (Ib & 0xffffu) && (uint32_t)bj <= (Ib >> 16);

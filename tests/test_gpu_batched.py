@@ -130,3 +130,33 @@ def test_bad_box_tables_are_rejected(table):
     with pytest.raises(crk.CrkError) as ei:
         crk.crk_build_cells_batched(ctx, dev(st["pos_h"]), table)
     assert ei.value.code == -1
+
+
+# ---------------------------------------------------------------- autotuner
+
+def test_autotuned_passes_give_identical_results():
+    """Every variant visits each list in the same order: results do not depend
+    on which one the tuner keeps (bitwise), and a choice is made per pass."""
+    st = workload("clustered", 3000, 11)
+    outs = []
+    for tune in (False, True):
+        ctx = crk.crk_create()
+        if tune:
+            crk.crk_autotune(ctx, True)
+        pos, vel, mass = dev(st["pos_h"]), dev(st["vel_u"]), dev(st["mass"])
+        crk.crk_build_cells(ctx, pos)
+        V, N = crk.crk_volumes(ctx)
+        A, B, gA, gB, gv = crk.crk_corrections(ctx, V, vel)
+        acc, dudt, vsig, qmax = crk.crk_forces(ctx, mass, vel, V, A, B, gA, gB, gv)
+        du = crk.crk_compatible(ctx, mass, vel, V, A, B, gA, gB, gv, vel[:, :3].contiguous(),
+                                (vel[:, :3] * 1.01).contiguous())
+        for _ in range(2):
+            crk.crk_step(ctx, pos, vel, mass, 0.0)
+        outs.append([V, A, B, gA, gB, gv, acc, dudt, vsig, du, pos, vel])
+        if tune:
+            t = crk.crk_tuning(ctx)
+            print(t)
+            assert set(t) >= {"P1 volumes", "P2 corrections", "P3 grad v", "P4 forces", "P5 compatible energy"}
+            assert all(0 <= v <= 8 and ms > 0 for v, ms in t.values())
+    for a, b in zip(*outs):
+        assert torch.equal(a, b)

@@ -297,18 +297,22 @@ def batched_report(dev, nbox=64, steps=10, warmup=2, seq_steps=2):
     mass = torch.from_numpy(bx["mass"]).to(dev)
     stream = torch.cuda.current_stream(dev)
     ctx = crk.crk_create()
-    for _ in range(warmup):
-        crk.crk_step_batched(ctx, pos, vel, mass, start)
+    crk.crk_autotune(ctx, True)
+    crk.crk_steps_batched(ctx, pos, vel, mass, start, warmup, use_graph=True)   # tunes, captures the graphs
     torch.cuda.synchronize(dev)
-    launches0 = crk.crk_launches(ctx)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(steps):
-        crk.crk_step_batched(ctx, pos, vel, mass, start)
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    ms = e0.elapsed_time(e1) / steps
-    launches = (crk.crk_launches(ctx) - launches0) / steps
+
+    def timed(use_graph):
+        l0 = crk.crk_launches(ctx)
+        e0.record(stream)
+        crk.crk_steps_batched(ctx, pos, vel, mass, start, steps, use_graph=use_graph)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / steps, (crk.crk_launches(ctx) - l0) / steps
+
+    ms, launches = timed(True)
+    ms_eager, _ = timed(False)
+    caps, reps, recs = crk.crk_graph_stats(ctx)
     d = crk.crk_step_batched(ctx, pos, vel, mass, start, diag=True)
     pairs = 3 * d[0]["pairs_gather"] + 3 * d[0]["pairs_union"]
     ctx.close()
@@ -333,6 +337,8 @@ def batched_report(dev, nbox=64, steps=10, warmup=2, seq_steps=2):
     return {"workload": "%d Sedov boxes, sides uniform in 16..96 (seeds 0..%d), %d particles" % (nbox, nbox - 1, n),
             "n": n, "sides_min_max": [min(bx["sides"]), max(bx["sides"])], "steps": steps,
             "ms_per_step": ms, "pair_interactions_per_s": pairs / (ms / 1e3), "kernel_launches_per_step": launches,
+            "cuda_graph": {"captures": caps, "replays": reps, "recoveries": recs,
+                           "eager_ms_per_step": ms_eager},
             "one_by_one_ms_per_step": seq_ms, "one_by_one_launches_per_step": seq_launches,
             "speedup_vs_one_by_one": seq_ms / ms}
 

@@ -209,6 +209,34 @@ int crk_compatible(crk_ctx *ctx, const float *mass, const float *vel_u, const fl
 int crk_step(crk_ctx *ctx, int n, float *pos_h, float *vel_u, const float *mass, double dt,
              crk_diag *diag, void *stream);
 
+/* nsteps KDK steps (as nsteps calls of crk_step with the same dt).  With
+ * use_graph = 1 every step after the first of a fresh state is one launch of
+ * a CUDA graph of the whole multi-pass step (two graphs: consecutive steps
+ * rotate the engine's state buffers), captured once and replayed with no host
+ * work between steps.  Nothing can grow inside a replayed step, so before the
+ * replays the call gives the neighbour-list columns and the tile-pair lists
+ * 50% headroom over the last step's needs (one more eager step applies a new
+ * column width) and the stored forces their worst case; each replayed step
+ * records whether a capacity was exceeded anyway.  If one was, the call
+ * restores the positions and velocities its replays started from and redoes
+ * those steps eagerly, the first of them evaluating the rates afresh at the
+ * restored state (so, unlike uninterrupted steps, without the predicted
+ * rates of R12).  Otherwise the results are bitwise those of eager steps.  A
+ * step that cannot be captured runs eagerly.  While crk_autotune is tuning,
+ * steps run eagerly until every pass has been tuned.  diag (host, may be
+ * NULL) receives the last step's diagnostics.  Synchronises. */
+int crk_steps(crk_ctx *ctx, int n, float *pos_h, float *vel_u, const float *mass, int nsteps, double dt,
+              int use_graph, crk_diag *diag, void *stream);
+
+/* crk_steps for batched boxes (box table as for crk_step_batched; dt > 0
+ * applies to every box, dt <= 0 gives each box its CFL step). */
+int crk_steps_batched(crk_ctx *ctx, int n, int nbox, const int32_t *box_start, float *pos_h, float *vel_u,
+                      const float *mass, int nsteps, double dt, int use_graph, void *stream);
+
+/* Graphs captured, graph launches, and replay runs redone eagerly after a
+ * capacity overflow, by crk_steps since crk_create (each may be NULL). */
+int crk_graph_stats(crk_ctx *ctx, long long *captures, long long *replays, long long *recoveries);
+
 /* Forget the cached rates so that the next crk_step evaluates afresh. */
 int crk_reset_rates(crk_ctx *ctx);
 

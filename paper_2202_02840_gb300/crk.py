@@ -81,6 +81,9 @@ def lib():
         L.crk_h_select.argtypes = [_vp, _ci, _vp, ctypes.c_float, _ci, _vp, ctypes.POINTER(_ci), _vp]
         L.crk_build_cells_batched.argtypes = [_vp, _ci, _ci, _vp, _vp, _vp]
         L.crk_step_batched.argtypes = [_vp, _ci, _ci, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
+        L.crk_steps.argtypes = [_vp, _ci, _vp, _vp, _vp, _ci, ctypes.c_double, _ci, ctypes.POINTER(crk_diag), _vp]
+        L.crk_graph_stats.argtypes = [_vp] + [ctypes.POINTER(ctypes.c_longlong)] * 3
+        L.crk_steps_batched.argtypes = [_vp, _ci, _ci, _vp, _vp, _vp, _vp, _ci, ctypes.c_double, _ci, _vp]
         L.crk_autotune.argtypes = [_vp, _ci]
         L.crk_tuning.argtypes = [_vp, _vp, _vp]
         L.crk_profile.argtypes = [_vp, _ci]
@@ -447,3 +450,36 @@ def crk_tuning(ctx):
     ms = (ctypes.c_float * NPASS)()
     ctx.check(lib().crk_tuning(ctx.handle, v, ms))
     return {PASS_NAMES[k]: (v[k], ms[k]) for k in range(NPASS) if v[k] >= 0}
+
+
+# ---------------------------------------------------------------- multi-step, CUDA graphs
+
+def crk_steps(ctx, pos_h, vel_u, mass, nsteps, dt=0.0, use_graph=True, diag=False, stream=None):
+    """nsteps KDK steps in place (captured once into CUDA graphs and replayed with use_graph)."""
+    n = pos_h.shape[0]
+    d = crk_diag()
+    ctx.check(lib().crk_steps(ctx.handle, n, _t(pos_h, (n, 4), "pos_h"), _t(vel_u, (n, 4), "vel_u"),
+                              _t(mass, (n,), "mass"), int(nsteps), float(dt), 1 if use_graph else 0,
+                              ctypes.byref(d) if diag else None, _stream(stream)))
+    ctx.n = n
+    if not diag:
+        return None
+    return {"dt": d.dt, "dt_next": d.dt_next, "E_kin": d.E_kin, "E_int": d.E_int, "P": list(d.P),
+            "pairs_gather": d.pairs_gather, "pairs_union": d.pairs_union}
+
+
+def crk_graph_stats(ctx):
+    """(graphs captured, graph launches, replay runs redone eagerly) since the context was created."""
+    c, r, v = ctypes.c_longlong(0), ctypes.c_longlong(0), ctypes.c_longlong(0)
+    ctx.check(lib().crk_graph_stats(ctx.handle, ctypes.byref(c), ctypes.byref(r), ctypes.byref(v)))
+    return c.value, r.value, v.value
+
+
+def crk_steps_batched(ctx, pos_h, vel_u, mass, box_start, nsteps, dt=0.0, use_graph=True, stream=None):
+    """nsteps KDK steps of every box in place (CUDA graphs with use_graph)."""
+    n = pos_h.shape[0]
+    arr, nbox = _box_table(box_start, n)
+    ctx.check(lib().crk_steps_batched(ctx.handle, n, nbox, arr, _t(pos_h, (n, 4), "pos_h"),
+                                      _t(vel_u, (n, 4), "vel_u"), _t(mass, (n,), "mass"), int(nsteps), float(dt),
+                                      1 if use_graph else 0, _stream(stream)))
+    ctx.n = n

@@ -589,6 +589,7 @@ int cell_level_host(const crk_ctx *ctx) {
 
 // Read the counters after a build; grow and redo the lists on overflow.
 int finish_build(crk_ctx *ctx, cudaStream_t s) {
+    if (ctx->graph_mode) return CRK_OK;   // captured step: checked after the replay
     int rc = crk_sync_counters(ctx, s);
     if (rc) return rc;
     if (ctx->h_counters[CNT_ERR_INPUT])

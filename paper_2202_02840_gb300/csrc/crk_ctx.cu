@@ -31,6 +31,7 @@ template <typename T>
 static int dalloc(crk_ctx *ctx, T **p, size_t count) {
     if (*p) cudaFree(*p);
     *p = nullptr;
+    if (ctx) ctx->alloc_gen++;   // captured graphs hold the old addresses
     if (count == 0) count = 1;
     cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
     if (e != cudaSuccess) {
@@ -128,6 +129,27 @@ int crk_ensure_entries(crk_ctx *ctx, long long n_ent, long long n_force) {
         }
         ctx->f_cap = cap;
     }
+    return CRK_OK;
+}
+
+// Grow the stored-force buffer to n_force entries, keeping its contents (the
+// forces of the last evaluation, which the next step's first kick reads).
+int crk_grow_forces_keep(crk_ctx *ctx, long long n_force) {
+    if (n_force <= ctx->f_cap && ctx->Fst) return CRK_OK;
+    float4 *nb = nullptr;
+    cudaError_t e = cudaMalloc((void **)&nb, sizeof(float4) * (size_t)n_force);
+    if (e != cudaSuccess) return crk_check_cuda(ctx, e, "cudaMalloc");
+    if (ctx->Fst && ctx->f_cap > 0) {
+        e = cudaMemcpy(nb, ctx->Fst, sizeof(float4) * (size_t)ctx->f_cap, cudaMemcpyDeviceToDevice);
+        if (e != cudaSuccess) {
+            cudaFree(nb);
+            return crk_check_cuda(ctx, e, "cudaMemcpy");
+        }
+        cudaFree(ctx->Fst);
+    }
+    ctx->Fst = nb;
+    ctx->f_cap = n_force;
+    ctx->alloc_gen++;
     return CRK_OK;
 }
 
@@ -455,6 +477,7 @@ extern "C" int crk_destroy(crk_ctx *ctx) {
         if (ctx->tune_ev[k]) cudaEventDestroy(ctx->tune_ev[k]);
     if (ctx->tile_order) cudaFree(ctx->tile_order);
     mlp_free(ctx);
+    graph_free(ctx);
     prof_free(ctx);
     delete ctx;
     return CRK_OK;

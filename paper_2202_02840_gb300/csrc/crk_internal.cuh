@@ -30,6 +30,7 @@ enum {
     CNT_ENTRIES = 9,    // stored-force units (32 entries) of the last list build
     CNT_MAXCNT = 10,    // largest pair-set count of the last walk
     CNT_MLP_ERR = 11,   // invalid records seen by the feature kernels
+    CNT_GRAPH_ERR = 12, // sticky: some replayed step overflowed a capacity or saw invalid records
     CNT_COUNT = 16
 };
 
@@ -181,6 +182,18 @@ struct crk_ctx {
     int32_t *tile_order = nullptr;   // tiles by decreasing pair-set list length
     int cap_order = 0;
 
+    // CUDA graphs of the steady-state step (two: the step swaps state buffers)
+    int graph_mode = 0;              // set while a step is captured: no host syncs, no growth
+    cudaStream_t gstream = nullptr;  // capture stream
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    cudaEvent_t gev[2] = {nullptr, nullptr};
+    long long glaunch[2] = {0, 0};   // kernels in each graph
+    long long gcaptures = 0, greplays = 0, grecoveries = 0;
+    unsigned long long gkey[2] = {0, 0};   // fingerprint of what each graph captured
+    float4 *bk_pos = nullptr, *bk_vel = nullptr;   // state before a run of replayed steps
+    int cap_bk = 0;
+    unsigned long long alloc_gen = 0;   // bumped by every device (re)allocation
+
     // launch accounting and per-pass event timing
     long long launches = 0;
     int prof_on = 0;
@@ -197,6 +210,7 @@ int crk_check_cuda(crk_ctx *ctx, cudaError_t e, const char *what);
 int crk_ensure_particles(crk_ctx *ctx, int n);
 int crk_ensure_lists(crk_ctx *ctx, long long ng, long long nu);
 int crk_ensure_entries(crk_ctx *ctx, long long n_ent, long long n_force);
+int crk_grow_forces_keep(crk_ctx *ctx, long long n_force);
 int crk_sync_counters(crk_ctx *ctx, cudaStream_t s);
 
 #define CRK_CUDA(ctx, call)                                                      \
@@ -216,6 +230,7 @@ namespace crk {
 enum { PROF_P1 = 0, PROF_PN = 1, PROF_P2 = 2, PROF_P3 = 3, PROF_P4 = 4, PROF_P5 = 5, PROF_BUILD = 6,
        PROF_LISTS = 7, PROF_MLP_FWD = 8, PROF_MLP_TRAIN = 9, PROF_NPASS = 10 };
 void mlp_free(crk_ctx *ctx);
+void graph_free(crk_ctx *ctx);
 void prof_begin(crk_ctx *ctx, int id, cudaStream_t s);
 void prof_end(crk_ctx *ctx, cudaStream_t s);
 int build_cells_sorted(crk_ctx *ctx, int n, const float4 *pos_h, const int32_t *order,

@@ -129,9 +129,12 @@ __device__ __forceinline__ void lpass_tile(const ListGeom &g, const typename P::
     P::init(st, i, valid, prm);
     const uint32_t *col0 = g.ent + (size_t)tile * g.kcap * 32 + lane;
     const size_t fb = (size_t)g.fbase[tile] * 32 + lane;
-    const int len = (int)(P::GATHER ? g.len_g[tile] : g.len_u[tile]);
-    const int mg = valid ? g.cnt_g[i] : 0;
-    const int my = P::GATHER ? mg : (valid ? g.cnt_u[i] : 0);
+    // counts beyond kcap only occur in a walk that overflowed (the host then
+    // grows kcap and walks again, or discards a replayed step): never read
+    // past the tile's columns
+    const int len = min((int)(P::GATHER ? g.len_g[tile] : g.len_u[tile]), g.kcap);
+    const int mg = valid ? min(g.cnt_g[i], g.kcap) : 0;
+    const int my = P::GATHER ? mg : (valid ? min(g.cnt_u[i], g.kcap) : 0);
     auto entry = [&](int k) -> uint32_t {
         const int c = k < mg ? k : g.kcap - 1 - (k - mg);
         return __ldg(col0 + (size_t)c * 32);

@@ -408,12 +408,9 @@ extern "C" int crk_step(crk_ctx *ctx, int n, float *pos_h, float *vel_u, const f
     return CRK_OK;
 }
 
-extern "C" int crk_step_batched(crk_ctx *ctx, int n, int nbox, const int32_t *box_start, float *pos_h,
-                                float *vel_u, const float *mass, const double *dt, crk_diag *diag, void *stream) {
-    if (!ctx) return CRK_EINVAL;
-    if (n <= 0 || !pos_h || !vel_u || !mass || !box_start) return crk_set_error(ctx, CRK_EINVAL, "bad arguments");
-    cudaStream_t s = (cudaStream_t)stream;
-    // the box table is loaded when it changes (and before the first batched step)
+// The box table is loaded when it differs from the loaded one (and before the
+// first batched step); loading forgets the rates.
+static int reload_boxes_if_changed(crk_ctx *ctx, int n, int nbox, const int32_t *box_start, cudaStream_t s) {
     bool same = ctx->nbox == nbox && nbox >= 1 && ctx->box_start && ctx->rates_valid && ctx->step_n == n;
     if (same) {
         std::vector<int32_t> cur((size_t)nbox + 1);
@@ -422,13 +419,20 @@ extern "C" int crk_step_batched(crk_ctx *ctx, int n, int nbox, const int32_t *bo
         CRK_CUDA(ctx, cudaStreamSynchronize(s));
         same = memcmp(cur.data(), box_start, sizeof(int32_t) * ((size_t)nbox + 1)) == 0;
     }
-    int rc;
-    if (!same) {
-        ctx->rates_valid = 0;
-        rc = crk_ensure_particles(ctx, n);
-        if (!rc) rc = load_boxes(ctx, n, nbox, box_start, s);
-        if (rc) return rc;
-    }
+    if (same) return CRK_OK;
+    ctx->rates_valid = 0;
+    int rc = crk_ensure_particles(ctx, n);
+    if (!rc) rc = load_boxes(ctx, n, nbox, box_start, s);
+    return rc;
+}
+
+extern "C" int crk_step_batched(crk_ctx *ctx, int n, int nbox, const int32_t *box_start, float *pos_h,
+                                float *vel_u, const float *mass, const double *dt, crk_diag *diag, void *stream) {
+    if (!ctx) return CRK_EINVAL;
+    if (n <= 0 || !pos_h || !vel_u || !mass || !box_start) return crk_set_error(ctx, CRK_EINVAL, "bad arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = reload_boxes_if_changed(ctx, n, nbox, box_start, s);
+    if (rc) return rc;
     const double *dt_box = nullptr;
     if (dt) {   // one requested step per box (<= 0: that box's CFL step)
         CRK_CUDA(ctx, cudaMemcpyAsync(ctx->box_red, dt, sizeof(double) * (size_t)nbox, cudaMemcpyHostToDevice, s));
@@ -474,6 +478,259 @@ extern "C" int crk_step_batched(crk_ctx *ctx, int n, int nbox, const int32_t *bo
         diag[b].pairs_union = (long long)ctx->h_counters[CNT_PAIRS_U];
     }
     return CRK_OK;
+}
+
+// ------------------------------------------------------------------ graphs
+
+namespace {
+
+// sticky overflow / invalid-input flag of a replayed step
+__global__ void k_graph_check(unsigned long long *cnt, long long cap_ulist, int kcap) {
+    if (cnt[CNT_ERR_INPUT] || (long long)cnt[CNT_ULIST] > cap_ulist || (long long)cnt[CNT_MAXCNT] > kcap)
+        cnt[CNT_GRAPH_ERR] = 1ull;
+}
+
+void swap_state(crk_ctx *ctx) {   // the buffer rotation step_impl performs after its rebuild
+    float4 *t;
+    t = ctx->st_pos; ctx->st_pos = ctx->st_tmp; ctx->st_tmp = t;
+    t = ctx->st_vel; ctx->st_vel = ctx->vb; ctx->vb = t;
+    t = ctx->st_half; ctx->st_half = ctx->va; ctx->va = t;
+}
+
+unsigned long long fnv(unsigned long long h, unsigned long long v) {
+    for (int k = 0; k < 8; k++) {
+        h ^= (v >> (8 * k)) & 0xffull;
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+void drop_graphs(crk_ctx *ctx) {
+    for (int k = 0; k < 2; k++) {
+        if (ctx->gexec[k]) cudaGraphExecDestroy(ctx->gexec[k]);
+        ctx->gexec[k] = nullptr;
+        ctx->gkey[k] = 0;
+    }
+}
+
+int run_diag(crk_ctx *ctx, int n, crk_diag *diag, cudaStream_t s) {
+    k_energy_partials<<<RED_BLOCKS, 256, 0, s>>>(n, ctx->st_vel, ctx->mass, ctx->d_red);
+    k_energy_final<<<1, 32, 0, s>>>(RED_BLOCKS, ctx->d_red, ctx->d_scalars + 2);
+    ctx->launches += 2;
+    CRK_LAUNCH_CHECK(ctx, "diagnostics");
+    double h[8];
+    CRK_CUDA(ctx, cudaMemcpyAsync(h, ctx->d_scalars, sizeof(h), cudaMemcpyDeviceToHost, s));
+    int rc = crk_sync_counters(ctx, s);
+    if (rc) return rc;
+    diag->dt = h[0];
+    diag->dt_next = (double)bits_to_float((uint32_t)ctx->h_counters[CNT_DTMIN]);
+    diag->E_kin = h[2];
+    diag->E_int = h[3];
+    diag->P[0] = h[4];
+    diag->P[1] = h[5];
+    diag->P[2] = h[6];
+    diag->pairs_gather = (long long)ctx->h_counters[CNT_PAIRS_G];
+    diag->pairs_union = (long long)ctx->h_counters[CNT_PAIRS_U];
+    return CRK_OK;
+}
+
+}  // namespace
+
+void crk::graph_free(crk_ctx *ctx) {
+    drop_graphs(ctx);
+    for (int k = 0; k < 2; k++)
+        if (ctx->gev[k]) cudaEventDestroy(ctx->gev[k]);
+    if (ctx->gstream) cudaStreamDestroy(ctx->gstream);
+    if (ctx->bk_pos) cudaFree(ctx->bk_pos);
+    if (ctx->bk_vel) cudaFree(ctx->bk_vel);
+    ctx->gstream = nullptr;
+    ctx->bk_pos = ctx->bk_vel = nullptr;
+    ctx->cap_bk = 0;
+}
+
+extern "C" int crk_graph_stats(crk_ctx *ctx, long long *captures, long long *replays, long long *recoveries) {
+    if (!ctx) return CRK_EINVAL;
+    if (captures) *captures = ctx->gcaptures;
+    if (replays) *replays = ctx->greplays;
+    if (recoveries) *recoveries = ctx->grecoveries;
+    return CRK_OK;
+}
+
+// Capture one steady-state step on the capture stream (kernels recorded, host
+// logic run: the state buffers rotate as after the step).  Returns false when
+// the step cannot be captured; the caller then steps eagerly.
+static bool capture_step(crk_ctx *ctx, int n, float *pos_h, float *vel_u, const float *mass, double dt, int p,
+                         unsigned long long key, bool batched) {
+    if (ctx->gexec[p]) cudaGraphExecDestroy(ctx->gexec[p]);
+    ctx->gexec[p] = nullptr;
+    ctx->gkey[p] = 0;
+    int prof = ctx->prof_on;
+    ctx->prof_on = 0;
+    ctx->graph_mode = 1;
+    cudaGraph_t graph = nullptr;
+    int rc = 0;
+    const long long l0 = ctx->launches;
+    cudaError_t e = cudaStreamBeginCapture(ctx->gstream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        rc = step_impl(ctx, n, pos_h, vel_u, mass, dt, nullptr, batched, ctx->gstream);
+        if (!rc) {
+            k_graph_check<<<1, 1, 0, ctx->gstream>>>(ctx->counters, ctx->cap_ulist, ctx->kcap);
+            ++ctx->launches;
+        }
+        e = cudaStreamEndCapture(ctx->gstream, &graph);
+    }
+    ctx->graph_mode = 0;
+    ctx->prof_on = prof;
+    bool ok = !rc && e == cudaSuccess && graph &&
+              cudaGraphInstantiate(&ctx->gexec[p], graph, 0) == cudaSuccess;
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();   // a failed capture leaves an error behind; the eager step reports its own
+    if (!ok) {
+        ctx->gexec[p] = nullptr;
+        ctx->rates_valid = 0;   // the host logic ran, the kernels did not: start afresh
+        return false;
+    }
+    ctx->gkey[p] = key;
+    ctx->glaunch[p] = ctx->launches - l0;
+    ctx->launches = l0;         // counted when the graph runs
+    ctx->gcaptures++;
+    return true;
+}
+
+static int steps_impl(crk_ctx *ctx, int n, float *pos_h, float *vel_u, const float *mass, int nsteps, double dt,
+                      int use_graph, bool batched, cudaStream_t s) {
+    int rc, done = 0;
+    // eager steps: without graphs, from a fresh state (its first step sizes
+    // every buffer a captured step uses) and while the passes are being tuned
+    for (;;) {
+        const bool fresh = !ctx->rates_valid || ctx->step_n != n || ctx->n != n || (ctx->nbox > 1) != batched;
+        bool tuning = false;
+        if (ctx->tune_on)
+            for (int k = PROF_P1; k <= PROF_P5; k++) tuning |= (k != PROF_PN && !ctx->tune_done[k]);
+        if (done == nsteps || (use_graph && !fresh && !tuning)) break;
+        rc = step_impl(ctx, n, pos_h, vel_u, mass, dt, nullptr, batched, s);
+        if (rc) return rc;
+        done++;
+    }
+    if (done < nsteps) {
+        // headroom for the replayed steps: list columns (they change only at a
+        // walk, so one more eager step applies the new width) and tile-pair lists
+        rc = crk_sync_counters(ctx, s);
+        if (rc) return rc;
+        const long long maxc = (long long)ctx->h_counters[CNT_MAXCNT];
+        const long long nu = (long long)ctx->h_counters[CNT_ULIST];
+        if (maxc + maxc / 2 > ctx->kcap && done < nsteps) {
+            ctx->kcap = (int)((maxc + maxc / 2 + 31) / 32 * 32);
+            rc = step_impl(ctx, n, pos_h, vel_u, mass, dt, nullptr, batched, s);
+            if (rc) return rc;
+            done++;
+        }
+        if (nu + nu / 2 > ctx->cap_ulist) {
+            rc = crk_ensure_lists(ctx, 0, nu + nu / 2 + 1024);
+            if (rc) return rc;
+        }
+    }
+    if (done < nsteps) {
+        // worst-case stored-force capacity (nothing grows inside a captured step;
+        // the forces of the last evaluation are kept: the next kick reads them),
+        // backup, capture stream
+        CRK_CUDA(ctx, cudaStreamSynchronize(s));
+        rc = crk_grow_forces_keep(ctx, (long long)ctx->ntiles * ctx->kcap * 32);
+        if (rc) return rc;
+        if (n > ctx->cap_bk) {
+            if (ctx->bk_pos) cudaFree(ctx->bk_pos);
+            if (ctx->bk_vel) cudaFree(ctx->bk_vel);
+            ctx->bk_pos = ctx->bk_vel = nullptr;
+            ctx->cap_bk = 0;
+            CRK_CUDA(ctx, cudaMalloc((void **)&ctx->bk_pos, sizeof(float4) * (size_t)n));
+            CRK_CUDA(ctx, cudaMalloc((void **)&ctx->bk_vel, sizeof(float4) * (size_t)n));
+            ctx->cap_bk = n;
+        }
+        if (!ctx->gstream) {
+            CRK_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->gstream, cudaStreamNonBlocking));
+            CRK_CUDA(ctx, cudaEventCreateWithFlags(&ctx->gev[0], cudaEventDisableTiming));
+            CRK_CUDA(ctx, cudaEventCreateWithFlags(&ctx->gev[1], cudaEventDisableTiming));
+        }
+        CRK_CUDA(ctx, cudaMemcpyAsync(ctx->bk_pos, pos_h, sizeof(float4) * (size_t)n, cudaMemcpyDeviceToDevice, s));
+        CRK_CUDA(ctx, cudaMemcpyAsync(ctx->bk_vel, vel_u, sizeof(float4) * (size_t)n, cudaMemcpyDeviceToDevice, s));
+        CRK_CUDA(ctx, cudaMemsetAsync(ctx->counters + CNT_GRAPH_ERR, 0, sizeof(unsigned long long), s));
+        CRK_CUDA(ctx, cudaEventRecord(ctx->gev[0], s));
+        CRK_CUDA(ctx, cudaStreamWaitEvent(ctx->gstream, ctx->gev[0], 0));
+        bool eager = false;
+        for (int k = done; k < nsteps; k++) {
+            // which of the two buffer rotations the state is in
+            const int p = (uintptr_t)ctx->st_pos < (uintptr_t)ctx->st_tmp ? 0 : 1;
+            unsigned long long key = 1469598103934665603ull;
+            unsigned long long dtbits;
+            memcpy(&dtbits, &dt, sizeof(dtbits));
+            const unsigned long long parts[] = {
+                (unsigned long long)n, (unsigned long long)(uintptr_t)pos_h, (unsigned long long)(uintptr_t)vel_u,
+                (unsigned long long)(uintptr_t)mass, ctx->alloc_gen, (unsigned long long)ctx->kcap,
+                (unsigned long long)ctx->cap_ulist, (unsigned long long)(uintptr_t)ctx->st_pos, dtbits,
+                (unsigned long long)batched * 7919ull + (unsigned long long)ctx->nbox,
+                (unsigned long long)(ctx->tune_choice[PROF_P1] + 16 * ctx->tune_choice[PROF_P2] +
+                                     256 * ctx->tune_choice[PROF_P3] + 4096 * ctx->tune_choice[PROF_P4] +
+                                     65536 * ctx->tune_choice[PROF_P5])};
+            for (unsigned long long v : parts) key = fnv(key, v);
+            if (!eager && (!ctx->gexec[p] || ctx->gkey[p] != key)) {
+                // capturing runs the step's host logic (its buffer rotation) but not its kernels
+                if (!capture_step(ctx, n, pos_h, vel_u, mass, dt, p, key, batched)) eager = true;
+            } else if (!eager) {
+                swap_state(ctx);
+            }
+            if (eager) {   // capture unavailable: the remaining steps run eagerly on the capture stream
+                rc = step_impl(ctx, n, pos_h, vel_u, mass, dt, nullptr, batched, ctx->gstream);
+                if (rc) return rc;
+                continue;
+            }
+            CRK_CUDA(ctx, cudaGraphLaunch(ctx->gexec[p], ctx->gstream));
+            ctx->launches += ctx->glaunch[p];
+            ctx->greplays++;
+        }
+        CRK_CUDA(ctx, cudaEventRecord(ctx->gev[1], ctx->gstream));
+        CRK_CUDA(ctx, cudaStreamWaitEvent(s, ctx->gev[1], 0));
+        rc = crk_sync_counters(ctx, s);
+        if (rc) return rc;
+        if (ctx->h_counters[CNT_GRAPH_ERR]) {
+            // a replayed step outgrew a capacity despite the headroom: restore the
+            // positions and velocities this run of replays started from and redo
+            // its steps eagerly (their first step evaluates the rates afresh there)
+            ctx->grecoveries++;
+            CRK_CUDA(ctx, cudaMemcpyAsync(pos_h, ctx->bk_pos, sizeof(float4) * (size_t)n, cudaMemcpyDeviceToDevice, s));
+            CRK_CUDA(ctx, cudaMemcpyAsync(vel_u, ctx->bk_vel, sizeof(float4) * (size_t)n, cudaMemcpyDeviceToDevice, s));
+            drop_graphs(ctx);
+            ctx->rates_valid = 0;
+            for (int k = done; k < nsteps; k++) {
+                rc = step_impl(ctx, n, pos_h, vel_u, mass, dt, nullptr, batched, s);
+                if (rc) return rc;
+            }
+        }
+    }
+    return CRK_OK;
+}
+
+extern "C" int crk_steps(crk_ctx *ctx, int n, float *pos_h, float *vel_u, const float *mass, int nsteps,
+                         double dt, int use_graph, crk_diag *diag, void *stream) {
+    if (!ctx) return CRK_EINVAL;
+    if (n <= 0 || !pos_h || !vel_u || !mass || nsteps < 0) return crk_set_error(ctx, CRK_EINVAL, "bad arguments");
+    if (nsteps == 0) return CRK_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = steps_impl(ctx, n, pos_h, vel_u, mass, nsteps, dt, use_graph, false, s);
+    if (rc) return rc;
+    return diag ? run_diag(ctx, n, diag, s) : CRK_OK;
+}
+
+extern "C" int crk_steps_batched(crk_ctx *ctx, int n, int nbox, const int32_t *box_start, float *pos_h,
+                                 float *vel_u, const float *mass, int nsteps, double dt, int use_graph,
+                                 void *stream) {
+    if (!ctx) return CRK_EINVAL;
+    if (n <= 0 || !pos_h || !vel_u || !mass || !box_start || nsteps < 0)
+        return crk_set_error(ctx, CRK_EINVAL, "bad arguments");
+    if (nsteps == 0) return CRK_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = reload_boxes_if_changed(ctx, n, nbox, box_start, s);
+    if (rc) return rc;
+    return steps_impl(ctx, n, pos_h, vel_u, mass, nsteps, dt, use_graph, nbox > 1, s);
 }
 
 static int h_iterate(crk_ctx *ctx, int n, float *pos_h, float tol, int max_it, int *iterations, cudaStream_t s);

@@ -163,8 +163,8 @@ __global__ void __launch_bounds__(WALK_WARPS * 32) k_walk(WalkArgs a) {
     uint32_t sg = __reduce_add_sync(0xffffffffu, (uint32_t)cg);
     uint32_t su = __reduce_add_sync(0xffffffffu, (uint32_t)cu);
     if (lane == 0) {
-        a.len_g[tile] = mg;
-        a.len_u[tile] = mu;
+        a.len_g[tile] = min(mg, (uint32_t)kcap);
+        a.len_u[tile] = min(mu, (uint32_t)kcap);
         atomicAdd(a.pairs_g, (unsigned long long)sg);
         atomicAdd(a.pairs_u, (unsigned long long)su);
         atomicMax(a.maxcnt, (unsigned long long)mu);
@@ -246,6 +246,10 @@ int run_lists(crk_ctx *ctx, cudaStream_t s) {
         k_total<<<1, 1, 0, s>>>(nt, ctx->tbase, ctx->len_u, ctx->counters + CNT_ENTRIES);
         ++ctx->launches;
         CRK_LAUNCH_CHECK(ctx, "list layout");
+        if (ctx->graph_mode) {   // captured step: capacities were fixed beforehand, overflow checked after
+            ctx->lists_valid = 1;
+            return CRK_OK;
+        }
         rc = crk_sync_counters(ctx, s);
         if (rc) return rc;
         long long maxc = (long long)ctx->h_counters[CNT_MAXCNT];

@@ -160,3 +160,84 @@ def test_autotuned_passes_give_identical_results():
             assert all(0 <= v <= 8 and ms > 0 for v, ms in t.values())
     for a, b in zip(*outs):
         assert torch.equal(a, b)
+
+
+# ---------------------------------------------------------------- CUDA graphs
+
+@pytest.mark.parametrize("case", ["uniform16", "sedov16"])
+def test_graph_steps_equal_eager_steps(case):
+    """Captured-and-replayed steps are the eager steps, bit for bit (inputs
+    whose neighbour counts stay within the list headroom)."""
+    st = {"uniform16": lambda: workload("uniform", 16), "clustered3000": lambda: workload("clustered", 3000, 11),
+          "sedov16": lambda: workload("sedov", 16)}[case]()
+    res = []
+    for mode in ("graph", "eager", "step"):
+        ctx = crk.crk_create()
+        pos, vel, mass = dev(st["pos_h"]), dev(st["vel_u"]), dev(st["mass"])
+        if mode == "step":
+            for _ in range(6):
+                crk.crk_step(ctx, pos, vel, mass, 0.0)
+            d = crk.crk_step(ctx, pos, vel, mass, 0.0, diag=True)
+        else:
+            crk.crk_steps(ctx, pos, vel, mass, 4, use_graph=(mode == "graph"))
+            d = crk.crk_steps(ctx, pos, vel, mass, 3, use_graph=(mode == "graph"), diag=True)
+        if mode == "graph":
+            caps, reps, recs = crk.crk_graph_stats(ctx)
+            print(case, "captures", caps, "replays", reps, "recoveries", recs)
+            # replayed steps after the first (one more eager step when the list columns needed headroom)
+            assert caps >= 2 and reps >= 5 and recs == 0, (caps, reps, recs)
+        res.append((pos, vel, d))
+    for p, v, d in res[1:]:
+        assert torch.equal(p, res[0][0]) and torch.equal(v, res[0][1])
+        assert d["E_kin"] == res[0][2]["E_kin"] and d["dt"] == res[0][2]["dt"]
+
+
+@pytest.mark.parametrize("case", ["converging16", "clustered3000"])
+def test_graph_steps_recover_from_list_overflow(case):
+    """Neighbour counts that outgrow even the list headroom (a converging flow;
+    clumps whose h grows towards N_res): the replays detect it, and the call
+    restores the state its replays started from and redoes their steps
+    eagerly, evaluating the rates afresh there.  The reference does the same
+    with eager steps and a reset of the rates at that point."""
+    if case == "converging16":
+        st = dict(workload("uniform", 16))
+        v = st["vel_u"].copy()
+        v[:, :3] = -3.0 * (st["pos_h"][:, :3].astype(np.float64) - 0.5).astype(np.float32)
+        st["vel_u"] = v
+        dt = 0.04
+    else:
+        st = workload("clustered", 3000, 11)
+        dt = 0.0
+    ctx = crk.crk_create()
+    pos, vel, mass = dev(st["pos_h"]), dev(st["vel_u"]), dev(st["mass"])
+    crk.crk_steps(ctx, pos, vel, mass, 6, dt=dt, use_graph=True)
+    caps, reps, recs = crk.crk_graph_stats(ctx)
+    print(case, "captures", caps, "replays", reps, "recoveries", recs)
+    assert torch.isfinite(pos).all() and torch.isfinite(vel).all()
+    ref = crk.crk_create()
+    rp, rv = dev(st["pos_h"]), dev(st["vel_u"])
+    if recs == 0:
+        crk.crk_steps(ref, rp, rv, mass, 6, dt=dt, use_graph=False)
+    else:
+        # eager steps before the replays (the first, plus one if the columns were widened), then a reset
+        eager = 6 - reps
+        crk.crk_steps(ref, rp, rv, mass, eager, dt=dt, use_graph=False)
+        crk.crk_reset_rates(ref)
+        crk.crk_steps(ref, rp, rv, mass, 6 - eager, dt=dt, use_graph=False)
+    assert torch.equal(pos, rp) and torch.equal(vel, rv)
+
+
+def test_batched_graph_steps_equal_eager_steps():
+    sts = [workload("uniform", 16), workload("sedov", 14), workload("sedov", 16)]
+    cat, start = concat(sts)
+    res = []
+    for use_graph in (True, False):
+        ctx = crk.crk_create()
+        pos, vel, mass = dev(cat["pos_h"]), dev(cat["vel_u"]), dev(cat["mass"])
+        crk.crk_steps_batched(ctx, pos, vel, mass, start, 5, use_graph=use_graph)
+        if use_graph:
+            caps, reps, recs = crk.crk_graph_stats(ctx)
+            print("batched captures", caps, "replays", reps, "recoveries", recs)
+            assert caps >= 2 and recs == 0
+        res.append((pos, vel))
+    assert torch.equal(res[0][0], res[1][0]) and torch.equal(res[0][1], res[1][1])

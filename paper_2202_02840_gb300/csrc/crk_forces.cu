@@ -27,19 +27,25 @@ struct FParams {
     float eta_crit, inv_eta_fold;
 };
 
-// Per-particle record of the pair-set passes (160 bytes).
+// Per-particle record of the pair-set passes: 160 bytes, five 32-byte sectors
+// (one 256-bit load each).  grad v enters the limiter only through the
+// quadratic form x . grad v . x, so its symmetric part is kept (6 numbers).
 struct __align__(32) FRec {
-    uint4 q;        // qx, qy, qz, H
-    float4 k0;      // 1/h, cW = 495/(32 pi h^3), cG = -1155/(4 pi h^5), h_hat = h/n_h
-    float4 k1;      // V, P, rho, c_s
-    float4 k2;      // vx, vy, vz, A
-    float4 k3;      // Bx, By, Bz, gAx
-    float4 k4;      // gAy, gAz, gB00, gB01
-    float4 k5;      // gB02, gB10, gB11, gB12
-    float4 k6;      // gB20, gB21, gB22, gv00
-    float4 k7;      // gv01, gv02, gv10, gv11
-    float4 k8;      // gv12, gv20, gv21, gv22
+    float4 w0;      // qx, qy, qz (fixed-point bits), 1/h
+    float4 w1;      // cW = 495/(32 pi h^3), cG = -1155/(4 pi h^5), h_hat = h/n_h, V
+    float4 w2;      // P, rho, c_s, A
+    float4 w3;      // vx, vy, vz, Bx
+    float4 w4;      // By, Bz, gAx, gAy
+    float4 w5;      // gAz, gB00, gB01, gB02
+    float4 w6;      // gB10, gB11, gB12, gB20
+    float4 w7;      // gB21, gB22, S_xx, S_yy
+    float4 w8;      // S_zz, S_xy, S_xz, S_yz   (S_ab = dv^a/dx^b + dv^b/dx^a for a != b)
+    float4 w9;      // unused (keeps records on 32-byte boundaries)
 };
+
+__device__ __forceinline__ uint32_t fq(const FRec &r, int k) {
+    return __float_as_uint(k == 0 ? r.w0.x : (k == 1 ? r.w0.y : r.w0.z));
+}
 
 struct FSrc {
     const uint4 *q4;
@@ -53,33 +59,35 @@ struct FSrc {
 
 __device__ __forceinline__ FRec load_frec(int j, const FSrc &src, const FParams &fp) {
     FRec r;
-    r.q = src.q4[j];
-    float h = src.hs[j], ih = 1.f / h, ih2 = ih * ih, ih3 = ih2 * ih;
-    r.k0 = make_float4(ih, KW * ih3, -KG * ih3 * ih2, h * fp.inv_nh);
+    const uint4 q = src.q4[j];
+    const float h = src.hs[j], ih = 1.f / h, ih2 = ih * ih, ih3 = ih2 * ih;
+    r.w0 = make_float4(__uint_as_float(q.x), __uint_as_float(q.y), __uint_as_float(q.z), ih);
     float V = src.V[j];
     float4 v = src.vel[j];
     float rho = src.mass[j] / V;
     float P = fp.gm1 * rho * v.w;
-    r.k1 = make_float4(V, P, rho, sqrtf(fmaxf(fp.gamma * P / rho, 0.f)));
     CorrRec c = src.corr[j];
     GvRec g = src.gv[j];
-    r.k2 = make_float4(v.x, v.y, v.z, c.c0.x);
-    r.k3 = make_float4(c.c0.y, c.c0.z, c.c0.w, c.c1.x);
-    r.k4 = make_float4(c.c1.y, c.c1.z, c.c1.w, c.c2.x);
-    r.k5 = make_float4(c.c2.y, c.c2.z, c.c2.w, c.c3.x);
-    r.k6 = make_float4(c.c3.y, c.c3.z, c.c3.w, g.g0.x);
-    r.k7 = make_float4(g.g0.y, g.g0.z, g.g0.w, g.g1.x);
-    r.k8 = make_float4(g.g1.y, g.g1.z, g.g1.w, g.g2.x);
+    // grad v [a][b]: g0 = (00 01 02 10), g1 = (11 12 20 21), g2 = (22 ...)
+    r.w1 = make_float4(KW * ih3, -KG * ih3 * ih2, h * fp.inv_nh, V);
+    r.w2 = make_float4(P, rho, sqrtf(fmaxf(fp.gamma * P / rho, 0.f)), c.c0.x);
+    r.w3 = make_float4(v.x, v.y, v.z, c.c0.y);
+    r.w4 = make_float4(c.c0.z, c.c0.w, c.c1.x, c.c1.y);
+    r.w5 = make_float4(c.c1.z, c.c1.w, c.c2.x, c.c2.y);
+    r.w6 = make_float4(c.c2.z, c.c2.w, c.c3.x, c.c3.y);
+    r.w7 = make_float4(c.c3.z, c.c3.w, g.g0.x, g.g1.x);
+    r.w8 = make_float4(g.g2.x, g.g0.y + g.g0.w, g.g0.z + g.g1.z, g.g1.y + g.g1.w);
+    r.w9 = make_float4(0.f, 0.f, 0.f, 0.f);
     return r;
 }
 
 // eq:gRK for particle a with separation x (= x_a - x_b), kernel value W and
 // radial factor G (grad W = G x).
 __device__ __forceinline__ void grad_rk(const FRec &a, const float x[3], float W, float G, float out[3]) {
-    const float A = a.k2.w;
-    const float B[3] = {a.k3.x, a.k3.y, a.k3.z};
-    const float gA[3] = {a.k3.w, a.k4.x, a.k4.y};
-    const float gB[9] = {a.k4.z, a.k4.w, a.k5.x, a.k5.y, a.k5.z, a.k5.w, a.k6.x, a.k6.y, a.k6.z};
+    const float A = a.w2.w;
+    const float B[3] = {a.w3.w, a.w4.x, a.w4.y};
+    const float gA[3] = {a.w4.z, a.w4.w, a.w5.x};
+    const float gB[9] = {a.w5.y, a.w5.z, a.w5.w, a.w6.x, a.w6.y, a.w6.z, a.w6.w, a.w7.x, a.w7.y};
     float sB = fmaf(B[0], x[0], fmaf(B[1], x[1], fmaf(B[2], x[2], 1.f)));
     float sW = sB * W, AW = A * W, AsG = A * sB * G;
 #pragma unroll
@@ -89,19 +97,18 @@ __device__ __forceinline__ void grad_rk(const FRec &a, const float x[3], float W
     }
 }
 
-// grad v . x for particle a
-__device__ __forceinline__ void gv_dot(const FRec &a, const float x[3], float o[3]) {
-    o[0] = fmaf(a.k6.w, x[0], fmaf(a.k7.x, x[1], a.k7.y * x[2]));
-    o[1] = fmaf(a.k7.z, x[0], fmaf(a.k7.w, x[1], a.k8.x * x[2]));
-    o[2] = fmaf(a.k8.y, x[0], fmaf(a.k8.z, x[1], a.k8.w * x[2]));
+// x . grad v . x from the symmetric part and the products xx = (x^2, y^2, z^2, xy, xz, yz)
+__device__ __forceinline__ float gv_quad(const FRec &a, const float xx[6]) {
+    return fmaf(a.w7.z, xx[0], fmaf(a.w7.w, xx[1], fmaf(a.w8.x, xx[2],
+           fmaf(a.w8.y, xx[3], fmaf(a.w8.z, xx[4], a.w8.w * xx[5])))));
 }
 
 __device__ __forceinline__ void kern(const FRec &a, float r, bool in, float &W, float &G) {
-    float eta = r * a.k0.x;
+    float eta = r * a.w0.w;
     float t = fmaxf(1.f - eta, 0.f);
     float t2 = t * t, t5 = t2 * t2 * t;
-    W = in ? a.k0.y * t5 * t * fmaf(eta, fmaf(eta, K35_3, 6.f), 1.f) : 0.f;
-    G = in ? a.k0.z * fmaf(5.f, eta, 1.f) * t5 : 0.f;
+    W = in ? a.w1.x * t5 * t * fmaf(eta, fmaf(eta, K35_3, 6.f), 1.f) : 0.f;
+    G = in ? a.w1.y * fmaf(5.f, eta, 1.f) * t5 : 0.f;
 }
 
 struct PairOut {
@@ -124,38 +131,33 @@ __device__ __forceinline__ void pair_force(const FRec &a, const FRec &b, const f
 #pragma unroll
     for (int g = 0; g < 3; g++) o.D[g] = gRb[g] - gRa[g];
 
-    // limiter, eq:phi .. eq:phiad
-    float pa[3], pb[3];
-    gv_dot(a, x, pa);
-    gv_dot(b, x, pb);
-    float qa = fmaf(x[0], pa[0], fmaf(x[1], pa[1], x[2] * pa[2]));
-    float qb = fmaf(x[0], pb[0], fmaf(x[1], pb[1], x[2] * pb[2]));
+    // limiter, eq:phi .. eq:phiad (x . grad v_a . x and x . grad v_b . x)
+    const float xx[6] = {x[0] * x[0], x[1] * x[1], x[2] * x[2], x[0] * x[1], x[0] * x[2], x[1] * x[2]};
+    float qa = gv_quad(a, xx);
+    float qb = gv_quad(b, xx);
     float qs = qa + qb;
     float phi = 0.f;
     if (qs != 0.f) {
         float is = FDIV(1.f, qs);
         phi = fminf(fmaxf(4.f * (qa * is) * (qb * is), 0.f), 1.f);
     }
-    float eta = fminf(r * a.k0.x, r * b.k0.x);
+    float eta = fminf(r * a.w0.w, r * b.w0.w);
     if (eta < fp.eta_crit) {
         float e = (eta - fp.eta_crit) * fp.inv_eta_fold;
         phi *= __expf(-e * e);
     }
-    // projected velocity difference, eq:hatvi (adot = 0)
-    float hp = -0.5f * phi;
-    float uh[3];
-    uh[0] = fmaf(hp, pa[0] + pb[0], a.k2.x - b.k2.x);
-    uh[1] = fmaf(hp, pa[1] + pb[1], a.k2.y - b.k2.y);
-    uh[2] = fmaf(hp, pa[2] + pb[2], a.k2.z - b.k2.z);
-    float ux = fmaf(uh[0], x[0], fmaf(uh[1], x[1], uh[2] * x[2]));
+    // projected velocity difference along x, eq:hatvi (adot = 0):
+    // u_ab . x = (v_a - v_b) . x - phi/2 (x . grad v_a . x + x . grad v_b . x)
+    float vx = fmaf(a.w3.x - b.w3.x, x[0], fmaf(a.w3.y - b.w3.y, x[1], (a.w3.z - b.w3.z) * x[2]));
+    float ux = fmaf(-0.5f * phi, qs, vx);
     // eq:mu, eq:visc
-    float hha = a.k0.w, hhb = b.k0.w;
+    float hha = a.w1.z, hhb = b.w1.z;
     float mua = fminf(FDIV(hha * ux, fmaf(hha * hha, fp.eps2, r2)), 0.f);
     float mub = fminf(FDIV(hhb * ux, fmaf(hhb * hhb, fp.eps2, r2)), 0.f);
-    float Qa = a.k1.z * mua * fmaf(fp.Cq, mua, -fp.Cl * a.k1.w);
-    float Qb = b.k1.z * mub * fmaf(fp.Cq, mub, -fp.Cl * b.k1.w);
-    float Pta = a.k1.y + Qa, Ptb = b.k1.y + Qb;
-    float cF = 0.5f * (a.k1.x * b.k1.x) * (Pta + Ptb);
+    float Qa = a.w2.y * mua * fmaf(fp.Cq, mua, -fp.Cl * a.w2.z);
+    float Qb = b.w2.y * mub * fmaf(fp.Cq, mub, -fp.Cl * b.w2.z);
+    float Pta = a.w2.x + Qa, Ptb = b.w2.x + Qb;
+    float cF = 0.5f * (a.w1.w * b.w1.w) * (Pta + Ptb);
 #pragma unroll
     for (int g = 0; g < 3; g++) o.F[g] = cF * o.D[g];
     o.Pt_b = Ptb;
@@ -168,12 +170,11 @@ __global__ void k_pack_frec(int n, FSrc src, FParams fp, FRec *__restrict__ out,
     if (i >= n) return;
     FRec r = load_frec(i, src, fp);
     out[i] = r;
-    sfun[i] = r.k1.y / powf(r.k1.z, fp.gamma);       // s = P / rho^gamma (eq:fij)
+    sfun[i] = r.w2.x / powf(r.w2.y, fp.gamma);       // s = P / rho^gamma (eq:fij)
 }
 
-// Two float4 of a record in one 256-bit read-only load (the record is 160 B,
-// so every pair of its float4 starts on a 32-byte boundary): one L1 sector
-// per lane per instruction instead of half a sector.
+// Two float4 of a record in one 256-bit read-only load (every pair of its
+// float4 starts on a 32-byte boundary): one L1 sector per lane per instruction.
 __device__ __forceinline__ void ldg_v8(const float4 *p, float4 &a, float4 &b) {
     asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
         : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
@@ -183,13 +184,11 @@ __device__ __forceinline__ void ldg_v8(const float4 *p, float4 &a, float4 &b) {
 __device__ __forceinline__ FRec ldg_frec(const FRec *p) {
     const float4 *q = reinterpret_cast<const float4 *>(p);
     FRec r;
-    float4 a;
-    ldg_v8(q, a, r.k0);
-    r.q = make_uint4(__float_as_uint(a.x), __float_as_uint(a.y), __float_as_uint(a.z), __float_as_uint(a.w));
-    ldg_v8(q + 2, r.k1, r.k2);
-    ldg_v8(q + 4, r.k3, r.k4);
-    ldg_v8(q + 6, r.k5, r.k6);
-    ldg_v8(q + 8, r.k7, r.k8);
+    ldg_v8(q, r.w0, r.w1);
+    ldg_v8(q + 2, r.w2, r.w3);
+    ldg_v8(q + 4, r.w4, r.w5);
+    ldg_v8(q + 6, r.w6, r.w7);
+    ldg_v8(q + 8, r.w8, r.w9);
     return r;
 }
 
@@ -223,7 +222,8 @@ struct P4 {
             s.m = p.mass[i];
         } else {
             s.me = FRec{};
-            s.me.k0.x = 1.f;
+            s.me.w0.w = 1.f;
+            s.me.w2.y = 1.f;
             s.m = 1.f;
         }
         s.vsig = 0.f;
@@ -232,17 +232,17 @@ struct P4 {
     __device__ static Rec load(uint32_t e, size_t, const Params &p) { return ldg_frec(p.frec + (e & 0x3fffffffu)); }
     __device__ static void pair(IState &s, const Rec &r, uint32_t e, size_t pos, bool in_i, const Params &p) {
         const bool in_j = in_i ? (e >> 31) != 0u : true;
-        int dx = (int)(s.me.q.x - r.q.x), dy = (int)(s.me.q.y - r.q.y), dz = (int)(s.me.q.z - r.q.z);
+        int dx = (int)(fq(s.me, 0) - fq(r, 0)), dy = (int)(fq(s.me, 1) - fq(r, 1)), dz = (int)(fq(s.me, 2) - fq(r, 2));
         Sep d = separation(dx, dy, dz);
         float x[3] = {d.x, d.y, d.z};
         PairOut o;
         pair_force(s.me, r, x, d.r2, d.r, in_i, in_j, p.fp, o);
         p.Fst[pos] = make_float4(o.F[0], o.F[1], o.F[2], __uint_as_float(e & 0x3fffffffu));   // F_ij, j
-        float dv[3] = {r.k2.x - s.me.k2.x, r.k2.y - s.me.k2.y, r.k2.z - s.me.k2.z};
+        float dv[3] = {r.w3.x - s.me.w3.x, r.w3.y - s.me.w3.y, r.w3.z - s.me.w3.z};
 #pragma unroll
         for (int g = 0; g < 3; g++) s.F[g].add(o.F[g]);
         float wd = fmaf(dv[0], o.D[0], fmaf(dv[1], o.D[1], dv[2] * o.D[2]));
-        s.du.add(0.5f * (s.me.k1.x * r.k1.x) * o.Pt_b * wd);
+        s.du.add(0.5f * (s.me.w1.w * r.w1.w) * o.Pt_b * wd);
         float vx = -fmaf(dv[0], x[0], fmaf(dv[1], x[1], dv[2] * x[2]));   // (v_i - v_j).x_ij
         if (vx < 0.f && d.r > 0.f) s.vsig = fmaxf(s.vsig, FDIV(-vx, d.r));
         s.qmax = fmaxf(s.qmax, o.Q_a);

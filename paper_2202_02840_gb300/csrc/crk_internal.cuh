@@ -115,7 +115,7 @@ struct crk_ctx {
     int kcap = 384;                  // list columns per particle
     int volumes_only = 0;            // walk without writing lists (no list buffer)
     int lists_valid = 0;
-    float4 *frec = nullptr;          // packed pair-set records, 10 float4 per particle
+    float4 *frec = nullptr;          // packed pair-set records, 10 float4 (160 B) per particle
     float *sfun = nullptr;           // specific entropy of the evaluation state
     float4 *sig = nullptr;           // (v + v') of a kick, s
 

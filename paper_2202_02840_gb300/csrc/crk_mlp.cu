@@ -56,6 +56,46 @@ __device__ __forceinline__ float tanh_sfu(float x) {
 
 __device__ __forceinline__ float logistic(float z) { return fmaf(0.5f, tanh_sfu(0.5f * z), 0.5f); }
 
+// Packed FP32 pairs (one instruction for two IEEE-rounded operations, the
+// same results as the scalar ones): the two columns of an mma accumulator
+// pair sit in adjacent registers.
+__device__ __forceinline__ unsigned long long pk2(float a, float b) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float2 up2(unsigned long long v) {
+    float2 f;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(f.x), "=f"(f.y) : "l"(v));
+    return f;
+}
+__device__ __forceinline__ unsigned long long mul2(unsigned long long a, unsigned long long b) {
+    unsigned long long d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b, unsigned long long c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+// silu of an accumulator pair (z0, z1) = (z0 s(z0), z1 s(z1)); with DS also s(1 + z(1 - s))
+template <bool DS>
+__device__ __forceinline__ float2 silu2(float z0, float z1, float2 *ds = nullptr) {
+    const unsigned long long half = pk2(0.5f, 0.5f);
+    const unsigned long long z = pk2(z0, z1);
+    const float2 hz = up2(mul2(half, z));
+    const unsigned long long th = pk2(tanh_sfu(hz.x), tanh_sfu(hz.y));
+    const unsigned long long sg = fma2(half, th, half);
+    if (DS) {
+        const float2 sv = up2(sg);
+        const unsigned long long oms = pk2(1.f - sv.x, 1.f - sv.y);
+        *ds = up2(mul2(sg, fma2(z, oms, pk2(1.f, 1.f))));
+    }
+    return up2(mul2(z, sg));
+}
+
 // D += A (16x8, row) B (8x8, col); bf16 in, f32 accumulate
 __device__ __forceinline__ void mma_k8(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t b0) {
     asm volatile(
@@ -158,14 +198,14 @@ __device__ __forceinline__ float2 quad_features(const FeatArgs &a, int i, int t,
     float2 f = make_float2(0.f, 0.f);
     if (!valid) return f;
     if (t == 0) {
-        f.x = log1pf(cls[0]);
-        f.y = log1pf(cls[1]);
+        f.x = __logf(1.f + cls[0]);   // counts are integers: 1 + c is exact
+        f.y = __logf(1.f + cls[1]);
     } else if (t == 1) {
-        f.x = log1pf(cls[2]);
-        f.y = log1pf(cls[3]);
+        f.x = __logf(1.f + cls[2]);
+        f.y = __logf(1.f + cls[3]);
     } else if (t == 2) {
-        f.x = log1pf(cls[0] + cls[1] + cls[2] + cls[3]);
-        f.y = logf(h) + a.log_cbrt_n;
+        f.x = __logf(1.f + (cls[0] + cls[1] + cls[2] + cls[3]));
+        f.y = __logf(h) + a.log_cbrt_n;
     } else {
         float dv = 0.f;
         if (a.gradv) {
@@ -173,7 +213,7 @@ __device__ __forceinline__ float2 quad_features(const FeatArgs &a, int i, int t,
             dv = __ldg(gv) + __ldg(gv + 4) + __ldg(gv + 8);
         }
         f.x = a.dt * dv;
-        f.y = a.Nngb ? logf(N * a.inv_N_res) : 0.f;
+        f.y = a.Nngb ? __logf(N * a.inv_N_res) : 0.f;
     }
     return f;
 }
@@ -230,15 +270,14 @@ __device__ __forceinline__ void layer1(uint32_t xa0, uint32_t xa1, const uint32_
         float c0 = S.b1[8 * j + 2 * t], c1 = S.b1[8 * j + 2 * t + 1];
         float d[4] = {c0, c1, c0, c1};
         mma_k8(d, xa0, xa1, w1f[j]);
-        float a[4];
-#pragma unroll
-        for (int c = 0; c < 4; c++) {
-            float s = logistic(d[c]);
-            a[c] = d[c] * s;
-            if (DS) ds1[j][c] = s * fmaf(d[c], 1.f - s, 1.f);
+        float2 g0, g1;
+        const float2 a01 = silu2<DS>(d[0], d[1], &g0), a23 = silu2<DS>(d[2], d[3], &g1);
+        if (DS) {
+            ds1[j][0] = g0.x; ds1[j][1] = g0.y;
+            ds1[j][2] = g1.x; ds1[j][3] = g1.y;
         }
-        A1[j >> 1][2 * (j & 1) + 0] = pack_bf16(a[0], a[1]);   // row g
-        A1[j >> 1][2 * (j & 1) + 1] = pack_bf16(a[2], a[3]);   // row g + 8
+        A1[j >> 1][2 * (j & 1) + 0] = pack_bf16(a01.x, a01.y);   // row g
+        A1[j >> 1][2 * (j & 1) + 1] = pack_bf16(a23.x, a23.y);   // row g + 8
     }
 }
 
@@ -267,7 +306,7 @@ __device__ __forceinline__ float quad_sum(float v) {
 // the features in place and writes the proposal into pos.w.  One warp per
 // 16-row tile, tiles strided over the grid.
 template <int MODE>
-__global__ void __launch_bounds__(256) k_mlp_fwd(int n, const float *__restrict__ W, const float *__restrict__ feat,
+__global__ void __launch_bounds__(256, 4) k_mlp_fwd(int n, const float *__restrict__ W, const float *__restrict__ feat,
                                                   float *__restrict__ y_out, FeatArgs fa, float4 *pos_out, float tol,
                                                   float h_min, float h_max, float N_res) {
     __shared__ __align__(16) FwdShm S;
@@ -299,8 +338,9 @@ __global__ void __launch_bounds__(256) k_mlp_fwd(int n, const float *__restrict_
             float d[4];
             layer2_tile(j, A1, S, g, t, d);
             float wa = S.w3[8 * j + 2 * t], wb = S.w3[8 * j + 2 * t + 1];
-            y0 = fmaf(wa, bf16r(d[0] * logistic(d[0])), fmaf(wb, bf16r(d[1] * logistic(d[1])), y0));
-            y1 = fmaf(wa, bf16r(d[2] * logistic(d[2])), fmaf(wb, bf16r(d[3] * logistic(d[3])), y1));
+            const float2 a01 = silu2<false>(d[0], d[1]), a23 = silu2<false>(d[2], d[3]);
+            y0 = fmaf(wa, bf16r(a01.x), fmaf(wb, bf16r(a01.y), y0));
+            y1 = fmaf(wa, bf16r(a23.x), fmaf(wb, bf16r(a23.y), y1));
         }
         y0 = Y_SCALE * (quad_sum(y0) + b3);
         y1 = Y_SCALE * (quad_sum(y1) + b3);
@@ -435,12 +475,10 @@ __global__ void __launch_bounds__(128) k_mlp_grad(TrainArgs a) {
         for (int j = 0; j < 8; j++) {
             float d[4];
             layer2_tile(j, A1, S.f, g, t, d);
-#pragma unroll
-            for (int c = 0; c < 4; c++) {
-                float s = logistic(d[c]);
-                a2[j][c] = bf16r(d[c] * s);
-                ds2[j][c] = s * fmaf(d[c], 1.f - s, 1.f);
-            }
+            float2 g0, g1;
+            const float2 a01 = silu2<true>(d[0], d[1], &g0), a23 = silu2<true>(d[2], d[3], &g1);
+            a2[j][0] = bf16r(a01.x); a2[j][1] = bf16r(a01.y); a2[j][2] = bf16r(a23.x); a2[j][3] = bf16r(a23.y);
+            ds2[j][0] = g0.x; ds2[j][1] = g0.y; ds2[j][2] = g1.x; ds2[j][3] = g1.y;
             float wa = S.f.w3[8 * j + 2 * t], wb = S.f.w3[8 * j + 2 * t + 1];
             y0 = fmaf(wa, a2[j][0], fmaf(wb, a2[j][1], y0));
             y1 = fmaf(wa, a2[j][2], fmaf(wb, a2[j][3], y1));

@@ -253,6 +253,66 @@ int crk_h_iterate(crk_ctx *ctx, int n, float *pos_h, float tol, int max_it, int 
                   void *stream);
 
 /* ------------------------------------------------------------------------
+ * Hierarchical power-of-two time bins (Sec. 2.1: the hydro subcycles of
+ * eq:Usubsub, the criteria Delta y_hyd and Delta y_acc, leaf-level bins, the
+ * f_l limiter, parabolic streaming of passive leaves).
+ *
+ * A cycle advances the state by one base step Delta, cut into 2^L ticks.  The
+ * leaves are the 32-particle tiles of the Morton order at the cycle start;
+ * they keep their particles for the whole cycle.  A leaf at level l steps
+ * 2^(L-l) ticks.  Levels:
+ *   particle: the smallest l >= 0 with Delta / 2^l < dt_i (the per-particle
+ *     CFL and acceleration criteria of crk_step, compared in FP64); a particle
+ *     needing l > L is held at L and counted as unresolved;
+ *   leaf: the deepest of its particles, raised by the limiter so that leaves
+ *     on each other's interaction list (tile boxes closer than the larger
+ *     Hmax) differ by at most f_l levels: at the cycle start to the least
+ *     fixed point over all leaves; mid-cycle over the leaves ending a step
+ *     (the others held), which also wake every passive neighbour up to at
+ *     least their level - f_l (its step then ends at the first tick that is a
+ *     multiple of its new step, and its half kick shrinks to match);
+ *   a leaf moves to a shallower level one level at a time, at a tick aligned
+ *     with the doubled step.
+ * Every tick at which some leaf ends its step: all particles stream along
+ * x0 + p0 t + a t^2/2 (constant acceleration of their last evaluation), the
+ * leaves ending a step evaluate P1..P4 (passive neighbours enter with their
+ * streamed x, v, u and last evaluated V, A, B, grad A, grad B, grad v), close
+ * their KDK step with compatible energy (eq:verletOP, eq:compEng), advance h
+ * by one eq:thacker update and open their next step.  At the last tick every
+ * leaf ends its step together; the particles are sorted again and evaluated
+ * in full, which is also the evaluation the next cycle (or crk_step) opens
+ * with.
+ * ---------------------------------------------------------------------- */
+
+typedef struct {
+    int ticks;                  /* ticks at which some leaf ended a step (incl. the last) */
+    long long evaluations;      /* particle derivative evaluations, incl. the full one at the end */
+    long long wakeups;          /* passive leaves raised by the limiter */
+    long long unresolved;       /* particle level requests deeper than L (held at L) */
+    int leaves;                 /* leaves (tiles) of the cycle */
+    int level_count[32];        /* leaves per level at the cycle start */
+} crk_htb_stats;
+
+/* One cycle of hierarchical time bins on the caller's state pos_h[4n],
+ * vel_u[4n] (updated in place, synchronized at the end) and mass[n].
+ * Delta > 0 is the base step, 0 <= L <= 20 the number of levels below it,
+ * f_l >= 0 the limiter.  Like crk_step it opens with the cached evaluation
+ * of the last step or cycle (evaluating afresh after crk_reset_rates or on a
+ * new state) and leaves the evaluation at its end cached.  stats (host, may
+ * be NULL).  One box only (CRK_ESTATE after a batched build).  Synchronises
+ * once or twice per tick. */
+int crk_cycle(crk_ctx *ctx, int n, float *pos_h, float *vel_u, const float *mass, double Delta, int L,
+              int f_l, crk_htb_stats *stats, void *stream);
+
+/* The level assignment of a cycle start, on its own: bins pos_h[4n] (as
+ * crk_build_cells), takes the per-particle time steps dt[n] (device, caller
+ * order) and writes level[n] (device, caller order): the level of each
+ * particle's leaf after the limiter's fixed point.  *unresolved (host, may be
+ * NULL) receives the count of particle requests deeper than L.  Synchronises. */
+int crk_htb_levels(crk_ctx *ctx, int n, const float *pos_h, const float *dt, double Delta, int L, int f_l,
+                   int32_t *level, long long *unresolved, void *stream);
+
+/* ------------------------------------------------------------------------
  * Batched boxes.  nbox independent periodic unit boxes in one particle set:
  * box b owns the caller rows [box_start[b], box_start[b+1]) (host array of
  * nbox + 1 ascending ints, box_start[0] = 0, box_start[nbox] = n, nbox <=

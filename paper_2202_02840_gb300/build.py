@@ -15,7 +15,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT_DIR, "libcrk.so")
 SOURCES = ["crk_ctx.cu", "crk_cells.cu", "crk_walk.cu", "crk_pairs.cu", "crk_forces.cu", "crk_step.cu",
-           "crk_noalloc.cu", "crk_mlp.cu"]
+           "crk_noalloc.cu", "crk_mlp.cu", "crk_htb.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                      "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]

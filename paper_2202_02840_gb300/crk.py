@@ -38,6 +38,11 @@ class crk_diag(ctypes.Structure):
                 ("pairs_gather", ctypes.c_longlong), ("pairs_union", ctypes.c_longlong)]
 
 
+class crk_htb_stats(ctypes.Structure):
+    _fields_ = [("ticks", ctypes.c_int), ("evaluations", ctypes.c_longlong), ("wakeups", ctypes.c_longlong),
+                ("unresolved", ctypes.c_longlong), ("leaves", ctypes.c_int), ("level_count", ctypes.c_int * 32)]
+
+
 _LIB = None
 _vp = ctypes.c_void_p
 _ci = ctypes.c_int
@@ -68,6 +73,10 @@ def lib():
         L.crk_compatible.argtypes = [_vp] + [_vp] * 11 + [_vp]
         L.crk_step.argtypes = [_vp, _ci, _vp, _vp, _vp, ctypes.c_double, ctypes.POINTER(crk_diag), _vp]
         L.crk_reset_rates.argtypes = [_vp]
+        L.crk_cycle.argtypes = [_vp, _ci, _vp, _vp, _vp, ctypes.c_double, _ci, _ci, ctypes.POINTER(crk_htb_stats),
+                                _vp]
+        L.crk_htb_levels.argtypes = [_vp, _ci, _vp, _vp, ctypes.c_double, _ci, _ci, _vp,
+                                     ctypes.POINTER(ctypes.c_longlong), _vp]
         L.crk_h_iterate.argtypes = [_vp, _ci, _vp, ctypes.c_float, _ci, ctypes.POINTER(_ci), _vp]
         L.crk_volumes_noalloc.argtypes = [_ci, _vp, _vp, _vp, _vp]
         L.crk_mlp_set_weights.argtypes = [_vp, _vp, _vp]
@@ -263,6 +272,32 @@ def crk_step(ctx, pos_h, vel_u, mass, dt=0.0, diag=False, stream=None):
         return None
     return {"dt": d.dt, "dt_next": d.dt_next, "E_kin": d.E_kin, "E_int": d.E_int, "P": list(d.P),
             "pairs_gather": d.pairs_gather, "pairs_union": d.pairs_union}
+
+
+def crk_cycle(ctx, pos_h, vel_u, mass, Delta, L, f_l=2, stream=None):
+    """One cycle of hierarchical time bins (base step Delta, 2^L ticks, limiter
+    f_l) in place on pos_h, vel_u; returns the cycle's statistics."""
+    n = pos_h.shape[0]
+    st = crk_htb_stats()
+    ctx.check(lib().crk_cycle(ctx.handle, n, _t(pos_h, (n, 4), "pos_h"), _t(vel_u, (n, 4), "vel_u"),
+                              _t(mass, (n,), "mass"), float(Delta), int(L), int(f_l), ctypes.byref(st),
+                              _stream(stream)))
+    ctx.n = n
+    return {"ticks": st.ticks, "evaluations": st.evaluations, "wakeups": st.wakeups, "unresolved": st.unresolved,
+            "leaves": st.leaves, "level_count": list(st.level_count)}
+
+
+def crk_htb_levels(ctx, pos_h, dt, Delta, L, f_l=2, stream=None):
+    """Leaf level of every particle (int32, caller order) after the limiter,
+    from the per-particle time steps dt; returns (level, unresolved)."""
+    n = pos_h.shape[0]
+    level = torch.empty(n, dtype=torch.int32, device=pos_h.device)
+    unres = ctypes.c_longlong(0)
+    ctx.check(lib().crk_htb_levels(ctx.handle, n, _t(pos_h, (n, 4), "pos_h"), _t(dt, (n,), "dt"), float(Delta),
+                                   int(L), int(f_l), _t(level, (n,), "level", torch.int32), ctypes.byref(unres),
+                                   _stream(stream)))
+    ctx.n = n
+    return level, int(unres.value)
 
 
 def crk_reset_rates(ctx):

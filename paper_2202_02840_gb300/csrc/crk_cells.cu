@@ -222,6 +222,12 @@ __global__ void k_gather_sorted(int n, const int32_t *__restrict__ idx, const ui
 
 // ------------------------------------------------------------------ tiles and tree
 
+// Tile boxes as periodic arcs: per axis the smallest arc around the tile's
+// first particle that holds every particle, lo = q_0 + min_k d_k and
+// hi = q_0 + max_k d_k (mod 2^32) with d_k = (int)(q_k - q_0).  For a tile of
+// the Morton order this is its min/max box; a tile whose particles drifted
+// across the periodic boundary (time bins keep tiles between sorts) gets an
+// arc with lo > hi instead of a box spanning the whole period.
 __global__ void k_tiles(int n, int ntiles, const uint4 *__restrict__ q4, uint4 *__restrict__ lo,
                         uint4 *__restrict__ hi, const int32_t *__restrict__ sbox, uint32_t *__restrict__ nbox) {
     int tile = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -230,12 +236,14 @@ __global__ void k_tiles(int n, int ntiles, const uint4 *__restrict__ q4, uint4 *
     int s = tile * TILE + lane;
     bool v = s < n;
     uint4 q = v ? q4[s] : make_uint4(0, 0, 0, 0);
-    uint32_t xl = __reduce_min_sync(FULL, v ? q.x : 0xffffffffu);
-    uint32_t yl = __reduce_min_sync(FULL, v ? q.y : 0xffffffffu);
-    uint32_t zl = __reduce_min_sync(FULL, v ? q.z : 0xffffffffu);
-    uint32_t xh = __reduce_max_sync(FULL, v ? q.x : 0u);
-    uint32_t yh = __reduce_max_sync(FULL, v ? q.y : 0u);
-    uint32_t zh = __reduce_max_sync(FULL, v ? q.z : 0u);
+    const uint32_t rx = __shfl_sync(FULL, q.x, 0), ry = __shfl_sync(FULL, q.y, 0), rz = __shfl_sync(FULL, q.z, 0);
+    const int dx = v ? (int)(q.x - rx) : 0, dy = v ? (int)(q.y - ry) : 0, dz = v ? (int)(q.z - rz) : 0;
+    uint32_t xl = rx + (uint32_t)__reduce_min_sync(FULL, dx);
+    uint32_t yl = ry + (uint32_t)__reduce_min_sync(FULL, dy);
+    uint32_t zl = rz + (uint32_t)__reduce_min_sync(FULL, dz);
+    uint32_t xh = rx + (uint32_t)__reduce_max_sync(FULL, dx);
+    uint32_t yh = ry + (uint32_t)__reduce_max_sync(FULL, dy);
+    uint32_t zh = rz + (uint32_t)__reduce_max_sync(FULL, dz);
     uint32_t Hm = __reduce_max_sync(FULL, v ? q.w : 0u);
     uint32_t c = __popc(__ballot_sync(FULL, v));
     if (lane == 0) {
@@ -254,6 +262,14 @@ __device__ __forceinline__ bool box_ranges_meet(uint32_t a, uint32_t b) {
     return (a & 0xffffu) <= (b >> 16) && (b & 0xffffu) <= (a >> 16);
 }
 
+// Inner tree nodes hold plain intervals: a child arc that wraps (lo > hi) is
+// widened to the whole axis, which keeps every node a superset of its tiles.
+__device__ __forceinline__ void unwrap_arcs(uint4 &l, uint4 &h) {
+    if (l.x > h.x) { l.x = 0u; h.x = 0xffffffffu; }
+    if (l.y > h.y) { l.y = 0u; h.y = 0xffffffffu; }
+    if (l.z > h.z) { l.z = 0u; h.z = 0xffffffffu; }
+}
+
 __global__ void k_tree_level(const uint4 *__restrict__ clo, const uint4 *__restrict__ chi, int ccnt,
                              uint4 *__restrict__ plo, uint4 *__restrict__ phi, int pcnt,
                              const uint32_t *__restrict__ cbox, uint32_t *__restrict__ pbox) {
@@ -261,8 +277,10 @@ __global__ void k_tree_level(const uint4 *__restrict__ clo, const uint4 *__restr
     if (k >= pcnt) return;
     uint4 l = clo[2 * k], h = chi[2 * k];
     uint32_t b = cbox ? cbox[2 * k] : 0u;
+    unwrap_arcs(l, h);
     if (2 * k + 1 < ccnt) {
         uint4 l2 = clo[2 * k + 1], h2 = chi[2 * k + 1];
+        unwrap_arcs(l2, h2);
         l = make_uint4(min(l.x, l2.x), min(l.y, l2.y), min(l.z, l2.z), max(l.w, l2.w));
         h = make_uint4(max(h.x, h2.x), max(h.y, h2.y), max(h.z, h2.z), h.w + h2.w);
         if (cbox) {
@@ -275,14 +293,13 @@ __global__ void k_tree_level(const uint4 *__restrict__ clo, const uint4 *__restr
     if (cbox) pbox[k] = b;
 }
 
-// periodic gap (fixed point) between intervals [a0,a1] and [b0,b1] on a circle of 2^32
+// periodic gap (fixed point) between the arcs [a0,a1] and [b0,b1] of a circle
+// of 2^32 (an arc may wrap, a0 > a1): 0 when they meet, else the shorter way
+// round; all differences modulo 2^32
 __device__ __forceinline__ unsigned long long axis_gap(uint32_t a0, uint32_t a1, uint32_t b0, uint32_t b1) {
-    const long long C = 4294967296ll;
-    long long d0 = max(0ll, max((long long)b0 - (long long)a1, (long long)a0 - (long long)b1));
-    long long dp = (long long)b0 + C - (long long)a1;
-    long long dm = (long long)a0 + C - (long long)b1;
-    long long g = min(d0, min(dp, dm));
-    return (unsigned long long)g;
+    if (b0 - a0 <= a1 - a0 || a0 - b0 <= b1 - b0) return 0ull;
+    const uint32_t g1 = b0 - a1, g2 = a0 - b1;
+    return (unsigned long long)(g1 < g2 ? g1 : g2);
 }
 
 __device__ __forceinline__ unsigned long long box_gap2(uint4 alo, uint4 ahi, uint4 blo, uint4 bhi) {
@@ -357,8 +374,10 @@ constexpr uint32_t LIST_BUF = 1024;   // tiles a warp keeps in shared memory
 
 // One walk per tile into shared memory, then one allocation and a coalesced
 // copy; a tile with more than LIST_BUF neighbours walks a second time
-// straight into the allocated range.
-__global__ void __launch_bounds__(LIST_WARPS * 32) k_lists32(int ntiles, Tree32 T, const uint4 *__restrict__ lo,
+// straight into the allocated range.  act (may be null): the lists of the
+// tiles act[0 .. count) only.
+__global__ void __launch_bounds__(LIST_WARPS * 32) k_lists32(int count, const int32_t *__restrict__ act, Tree32 T,
+                                                             const uint4 *__restrict__ lo,
                                                              const uint4 *__restrict__ hi,
                                                              const uint32_t *__restrict__ nbox,
                                                              uint2 *__restrict__ ofs, uint32_t *__restrict__ list,
@@ -366,8 +385,9 @@ __global__ void __launch_bounds__(LIST_WARPS * 32) k_lists32(int ntiles, Tree32 
     __shared__ int stL[LIST_WARPS][STACK], stK[LIST_WARPS][STACK];
     __shared__ uint32_t buf[LIST_WARPS][LIST_BUF];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int I = blockIdx.x * LIST_WARPS + w;
-    if (I >= ntiles) return;
+    const int t = blockIdx.x * LIST_WARPS + w;
+    if (t >= count) return;
+    const int I = act ? act[t] : t;
     const uint4 Ilo = lo[I], Ihi = hi[I];
     const uint32_t Ibox = nbox ? nbox[I] : 0u;
     uint32_t c = walk32<true>(T, lo, hi, nbox, Ibox, Ilo, Ihi, buf[w], LIST_BUF, stL[w], stK[w], lane);
@@ -439,8 +459,10 @@ int rebuild_lists(crk_ctx *ctx, cudaStream_t s) {
     if (T.cnt[T.top] > 32) return crk_set_error(ctx, CRK_ECAPACITY, "tile tree too deep");
     CRK_CUDA(ctx, cudaMemsetAsync(ctx->counters + CNT_GLIST, 0, 2 * sizeof(unsigned long long), s));
     ctx->lists_valid = 0;
-    k_lists32<<<grid_for(ctx->ntiles, LIST_WARPS), LIST_WARPS * 32, 0, s>>>(
-        ctx->ntiles, T, ctx->node_lo, ctx->node_hi, ctx->nbox > 1 ? ctx->node_box : nullptr, ctx->uofs,
+    const int count = ctx->act ? ctx->nact : ctx->ntiles;
+    if (count == 0) return CRK_OK;
+    k_lists32<<<grid_for(count, LIST_WARPS), LIST_WARPS * 32, 0, s>>>(
+        count, ctx->act, T, ctx->node_lo, ctx->node_hi, ctx->nbox > 1 ? ctx->node_box : nullptr, ctx->uofs,
         ctx->ulist, ctx->cap_ulist, ctx->counters + CNT_ULIST);
     ++ctx->launches;
     CRK_LAUNCH_CHECK(ctx, "interaction lists");

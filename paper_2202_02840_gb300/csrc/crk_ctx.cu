@@ -477,6 +477,7 @@ extern "C" int crk_destroy(crk_ctx *ctx) {
         if (ctx->tune_ev[k]) cudaEventDestroy(ctx->tune_ev[k]);
     if (ctx->tile_order) cudaFree(ctx->tile_order);
     mlp_free(ctx);
+    htb_free(ctx);
     graph_free(ctx);
     prof_free(ctx);
     delete ctx;

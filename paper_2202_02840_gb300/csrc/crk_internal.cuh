@@ -31,7 +31,12 @@ enum {
     CNT_MAXCNT = 10,    // largest pair-set count of the last walk
     CNT_MLP_ERR = 11,   // invalid records seen by the feature kernels
     CNT_GRAPH_ERR = 12, // sticky: some replayed step overflowed a capacity or saw invalid records
-    CNT_COUNT = 16
+    CNT_TNEXT = 13,     // time bins: earliest step end over the leaves (ticks)
+    CNT_CHANGED = 14,   // time bins: a limiter sweep raised some level
+    CNT_UNRES = 15,     // time bins: particle level requests deeper than L
+    CNT_WAKE = 16,      // time bins: passive leaves raised
+    CNT_NACT = 17,      // time bins: leaves ending a step at the current tick
+    CNT_COUNT = 24
 };
 
 // Pass-input records in sorted order.
@@ -194,6 +199,20 @@ struct crk_ctx {
     int cap_bk = 0;
     unsigned long long alloc_gen = 0;   // bumped by every device (re)allocation
 
+    // hierarchical time bins (the tiles are the leaves; per-tile and sorted per-particle arrays)
+    int cap_htb = 0;                 // tiles the per-tile arrays hold
+    int cap_htbp = 0;                // particles the per-particle arrays hold
+    int32_t *tlev = nullptr;         // level of each leaf
+    int32_t *tt0 = nullptr;          // tick its current step started
+    int32_t *tlen = nullptr;         // ticks of its current step
+    int32_t *twake = nullptr;        // level a passive leaf is raised to by its active neighbours
+    uint32_t *tflag = nullptr, *tscan = nullptr;   // active flags and their exclusive scan
+    int32_t *tact = nullptr;         // the active leaves of the current tick
+    float *du_open = nullptr;        // energy rate of each particle's opening kick
+    float *hc = nullptr;             // closing half-kick duration at the cycle end (sorted)
+    const int32_t *act = nullptr;    // set: walk, tile lists and list passes cover these tiles only
+    int nact = 0;
+
     // launch accounting and per-pass event timing
     long long launches = 0;
     int prof_on = 0;
@@ -230,6 +249,7 @@ namespace crk {
 enum { PROF_P1 = 0, PROF_PN = 1, PROF_P2 = 2, PROF_P3 = 3, PROF_P4 = 4, PROF_P5 = 5, PROF_BUILD = 6,
        PROF_LISTS = 7, PROF_MLP_FWD = 8, PROF_MLP_TRAIN = 9, PROF_NPASS = 10 };
 void mlp_free(crk_ctx *ctx);
+void htb_free(crk_ctx *ctx);
 void graph_free(crk_ctx *ctx);
 void prof_begin(crk_ctx *ctx, int id, cudaStream_t s);
 void prof_end(crk_ctx *ctx, cudaStream_t s);
@@ -248,6 +268,7 @@ int run_neighbours(crk_ctx *ctx, int mode, int32_t *cnt, uint32_t *hash, cudaStr
 int run_corrections(crk_ctx *ctx, bool with_gradv, cudaStream_t s);
 int run_forces(crk_ctx *ctx, cudaStream_t s);
 int run_compatible(crk_ctx *ctx, cudaStream_t s);
+int evaluate(crk_ctx *ctx, cudaStream_t s);   // P1..P4 and per-particle time steps (crk_step.cu)
 int gather_rows(crk_ctx *ctx, const void *in, void *out, int width_words, cudaStream_t s);
 int scatter_rows(crk_ctx *ctx, const void *in, void *out, int width_words, cudaStream_t s);
 inline int grid_for(long long n, int block) { return (int)((n + block - 1) / block); }

@@ -302,6 +302,19 @@ int launch_lpass(crk_ctx *ctx, int prof_id, const typename P::Params &prm, cudaS
     ListGeom g{ctx->n, ctx->ntiles, ctx->kcap, ctx->tbase, ctx->len_g, ctx->len_u, ctx->cnt_g, ctx->cnt_u,
                ctx->ent};
     int rc;
+    if (ctx->act) {
+        // the tiles ctx->act[0 .. nact) only (time bins): grid form over that
+        // list, each pass's default loop form, no tuning
+        if (ctx->nact == 0) return CRK_OK;
+        g.ntiles = ctx->nact;
+        constexpr int U = P::PREFETCH ? 1 : P::UNROLL;
+        prof_begin(ctx, prof_id, s);
+        k_lpass<P, WARPS, U><<<grid_for(ctx->nact, WARPS), WARPS * 32, 0, s>>>(g, prm, ctx->act);
+        ++ctx->launches;
+        prof_end(ctx, s);
+        CRK_LAUNCH_CHECK(ctx, what);
+        return CRK_OK;
+    }
     if (ctx->tune_on && !ctx->tune_done[prof_id]) {
         // time every applicable variant once (each recomputes the same outputs)
         float best = 3.0e38f;

@@ -47,7 +47,8 @@ static StepConsts step_consts(const crk_params &p) {
 __global__ void k_cfl(int n, StepConsts c, const float *__restrict__ hs, const float *__restrict__ V,
                       const float *__restrict__ mass, const float4 *__restrict__ vel,
                       const float4 *__restrict__ acc, const float2 *__restrict__ vq,
-                      const GvRec *__restrict__ gv, unsigned long long *dtmin, const int32_t *__restrict__ sbox) {
+                      const GvRec *__restrict__ gv, unsigned long long *dtmin, const int32_t *__restrict__ sbox,
+                      float *__restrict__ dt_out) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     float dt = 3.0e38f;
     if (s < n) {
@@ -64,6 +65,7 @@ __global__ void k_cfl(int n, StepConsts c, const float *__restrict__ hs, const f
         float4 a = acc[s];
         float am = sqrtf(a.x * a.x + a.y * a.y + a.z * a.z);
         if (am > 0.f) dt = fminf(dt, sqrtf(hh / am));
+        dt_out[s] = dt;   // per particle, for the time bins
     }
     if (sbox) {   // batched boxes: one minimum per box (one atomic per box a warp touches)
         const int b = s < n ? sbox[s] : -1;
@@ -270,9 +272,25 @@ __global__ void k_write_h(int n, const int32_t *__restrict__ perm, const float *
 
 // ------------------------------------------------------------------ evaluation
 
-// P1 -> P2 -> P3 -> P4 at the current build, with ctx->vel / ctx->mass set.
-static int evaluate(crk_ctx *ctx, cudaStream_t s) {
+// qV = (q, V) of every slot: after a P1 over some tiles only (time bins), the
+// other slots keep their last V at their current position
+__global__ void k_qv_refresh(int n, const uint4 *__restrict__ q4, const float *__restrict__ V, uint4 *__restrict__ qV) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    uint4 q = q4[s];
+    qV[s] = make_uint4(q.x, q.y, q.z, __float_as_uint(V[s]));
+}
+
+// P1 -> P2 -> P3 -> P4 at the current build, with ctx->vel / ctx->mass set
+// (over the tiles ctx->act only when that is set), then the per-particle
+// time steps of every slot.
+int evaluate(crk_ctx *ctx, cudaStream_t s) {
     int rc = run_volumes(ctx, s);
+    if (!rc && ctx->act) {
+        k_qv_refresh<<<grid_for(ctx->n, 256), 256, 0, s>>>(ctx->n, ctx->q4, ctx->V, ctx->qV);
+        ++ctx->launches;
+        CRK_LAUNCH_CHECK(ctx, "pass records");
+    }
     if (!rc) rc = run_corrections(ctx, true, s);
     if (!rc) rc = run_forces(ctx, s);
     if (rc) return rc;
@@ -282,7 +300,8 @@ static int evaluate(crk_ctx *ctx, cudaStream_t s) {
     const int nb = batched ? ctx->nbox : 1;
     k_fill_ull<<<grid_for(nb, 256), 256, 0, s>>>(nb, 0x7f7fffffull, dtmin);   // FLT_MAX bits
     k_cfl<<<grid_for(ctx->n, 256), 256, 0, s>>>(ctx->n, c, ctx->hs, ctx->V, ctx->mass, ctx->vel, ctx->acc,
-                                                  ctx->vq, ctx->gv, dtmin, batched ? ctx->sbox : nullptr);
+                                                  ctx->vq, ctx->gv, dtmin, batched ? ctx->sbox : nullptr,
+                                                  ctx->d_dt);
     ctx->launches += 2;
     CRK_LAUNCH_CHECK(ctx, "CFL");
     return CRK_OK;

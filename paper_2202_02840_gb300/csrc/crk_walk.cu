@@ -34,13 +34,15 @@ struct WalkArgs {
     uint32_t *ent;
     const int32_t *sbox;     // batched boxes: box of each slot (BATCH only)
     const uint32_t *nbox;    // box range of each tile (BATCH only)
+    const int32_t *act;      // may be null: walk the tiles act[0 .. ntiles) only
 };
 
 // LISTS: write the lists; VOL: sum n_i in the walk (volumes-only contexts).
-// circular distance (fixed point) from coordinate q to the interval [lo, hi]
+// circular distance (fixed point) from coordinate q to the arc [lo, hi]
+// (which may wrap, lo > hi); differences modulo 2^32
 __device__ __forceinline__ unsigned long long point_gap(uint32_t q, uint32_t lo, uint32_t hi) {
-    if (q >= lo && q <= hi) return 0ull;
-    uint32_t d1 = lo - q, d2 = q - hi;   // both modulo 2^32
+    if (q - lo <= hi - lo) return 0ull;
+    uint32_t d1 = lo - q, d2 = q - hi;
     return (unsigned long long)(d1 < d2 ? d1 : d2);
 }
 
@@ -51,8 +53,9 @@ __global__ void __launch_bounds__(WALK_WARPS * 32) k_walk(WalkArgs a) {
     __shared__ uint4 sq[WALK_WARPS][32];
     __shared__ int32_t sb[WALK_WARPS][BATCH ? 32 : 1];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int tile = blockIdx.x * WALK_WARPS + w;
-    if (tile >= a.ntiles) return;
+    const int tw = blockIdx.x * WALK_WARPS + w;
+    if (tw >= a.ntiles) return;
+    const int tile = a.act ? a.act[tw] : tw;
     const int i = tile * TILE + lane;
     const bool valid = i < a.n;
     const uint4 qi = valid ? a.q4[i] : make_uint4(0, 0, 0, 0);
@@ -201,6 +204,8 @@ static WalkArgs walk_args(crk_ctx *ctx) {
     a.ent = ctx->volumes_only ? nullptr : ctx->ent;
     a.sbox = ctx->nbox > 1 ? ctx->sbox : nullptr;
     a.nbox = ctx->nbox > 1 ? ctx->node_box : nullptr;
+    a.act = ctx->act;
+    if (ctx->act) a.ntiles = ctx->nact;
     return a;
 }
 
@@ -211,8 +216,13 @@ static int launch_walk(crk_ctx *ctx, cudaStream_t s) {
     }
     CRK_CUDA(ctx, cudaMemsetAsync(ctx->counters + CNT_PAIRS_G, 0, 2 * sizeof(unsigned long long), s));
     CRK_CUDA(ctx, cudaMemsetAsync(ctx->counters + CNT_MAXCNT, 0, sizeof(unsigned long long), s));
+    if (ctx->act) {   // tiles left out of the walk take no list columns and no stored forces
+        CRK_CUDA(ctx, cudaMemsetAsync(ctx->len_g, 0, sizeof(uint32_t) * ctx->ntiles, s));
+        CRK_CUDA(ctx, cudaMemsetAsync(ctx->len_u, 0, sizeof(uint32_t) * ctx->ntiles, s));
+        if (ctx->nact == 0) return CRK_OK;
+    }
     prof_begin(ctx, PROF_LISTS, s);
-    const int g = grid_for(ctx->ntiles, WALK_WARPS);
+    const int g = grid_for(ctx->act ? ctx->nact : ctx->ntiles, WALK_WARPS);
     const bool b = ctx->nbox > 1;
     if (ctx->volumes_only && b)
         k_walk<false, true, true><<<g, WALK_WARPS * 32, 0, s>>>(walk_args(ctx));

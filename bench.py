@@ -343,6 +343,94 @@ def batched_report(dev, nbox=64, steps=10, warmup=2, seq_steps=2):
             "speedup_vs_one_by_one": seq_ms / ms}
 
 
+def time_bins_report(dev, side=64, L=5, cycles=4, f_ls=(0, 1, 2, 3, 4), warm_steps=20):
+    """Hierarchical time bins (crk_cycle) on a Sedov blast against global
+    stepping at the finest tick over the same simulated time: GPU time,
+    particle evaluations, energy error and the L1 difference of the radial
+    density and energy profiles, for a sweep of the limiter f_l (the Sedov
+    test of the paper's Sec. 4 with its f_l sweep)."""
+    import numpy as np
+    import torch
+    from paper_2202_02840_gb300 import crk, inputs
+
+    st = inputs.sedov(side)
+    pos = torch.from_numpy(st["pos_h"]).to(dev)
+    vel = torch.from_numpy(st["vel_u"]).to(dev)
+    mass = torch.from_numpy(st["mass"]).to(dev)
+    m = st["mass"].astype(np.float64)
+    ctx = crk.crk_create()
+    for _ in range(warm_steps):                      # let the blast form (CFL steps)
+        d = crk.crk_step(ctx, pos, vel, mass, 0.0, diag=True)
+    ctx.close()
+    tick = d["dt_next"]
+    Delta = tick * (1 << L)
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    probe = crk.crk_create()
+
+    def energy(v):
+        v = v.cpu().numpy().astype(np.float64)
+        return float((0.5 * m * (v[:, :3] ** 2).sum(1) + m * v[:, 3]).sum())
+
+    def profiles(p, v):
+        crk.crk_build_cells(probe, p)
+        V, _ = crk.crk_volumes(probe)
+        rho = m / V.cpu().numpy().astype(np.float64)
+        x = p[:, :3].cpu().numpy().astype(np.float64) - 0.5
+        x -= np.round(x)
+        r = np.sqrt((x * x).sum(1))
+        edges = np.arange(0.0, 0.45, 0.5 / side)
+        i = np.digitize(r, edges) - 1
+        ok = (i >= 0) & (i < len(edges) - 1)
+        c = np.maximum(np.bincount(i[ok], None, len(edges) - 1), 1)
+        u = v[:, 3].cpu().numpy().astype(np.float64)
+        return (np.bincount(i[ok], rho[ok], len(edges) - 1) / c, np.bincount(i[ok], u[ok], len(edges) - 1) / c)
+
+    E0 = energy(vel)
+    # global stepping at the finest tick
+    gp, gv = pos.clone(), vel.clone()
+    g = crk.crk_create()
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for _ in range(cycles << L):
+        crk.crk_step(g, gp, gv, mass, tick)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    g_ms = e0.elapsed_time(e1)
+    g.close()
+    rho_g, u_g = profiles(gp, gv)
+    n = pos.shape[0]
+    out = {"workload": "sedov-%d^3 after %d CFL steps, %d cycles of 2^%d ticks" % (side, warm_steps, cycles, L),
+           "n": n, "L": L, "Delta": Delta, "tick": tick, "cycles": cycles,
+           "global": {"ms": g_ms, "evaluations": n * (cycles << L), "energy_error": energy(gv) / E0 - 1.0},
+           "f_l": {}}
+    for f in f_ls:
+        hp, hv = pos.clone(), vel.clone()
+        c = crk.crk_create()
+        ev = wk = un = ticks = 0
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for _ in range(cycles):
+            info = crk.crk_cycle(c, hp, hv, mass, Delta, L, f)
+            ev += info["evaluations"]
+            wk += info["wakeups"]
+            un += info["unresolved"]
+            ticks += info["ticks"]
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1)
+        c.close()
+        rho_h, u_h = profiles(hp, hv)
+        out["f_l"][str(f)] = {
+            "ms": ms, "speedup_vs_global": g_ms / ms, "evaluations": ev,
+            "evaluation_fraction": ev / float(n * (cycles << L)), "ticks": ticks, "wakeups": wk, "unresolved": un,
+            "energy_error": energy(hv) / E0 - 1.0,
+            "L1_rho_vs_global": float(np.abs(rho_h - rho_g).sum() / np.abs(rho_g).sum()),
+            "L1_u_vs_global": float(np.abs(u_h - u_g).sum() / np.abs(u_g).sum())}
+    probe.close()
+    return out
+
+
 # --------------------------------------------------------------------- GPU arm
 
 def aggregate(times_ms, work, dist=None, device="cpu"):
@@ -500,6 +588,8 @@ def run_gpu(args):
             line["learned_h"] = learned_h_report(dev)
         if not args.no_batched and world == 1:
             line["batched"] = batched_report(dev)
+        if not args.no_time_bins and world == 1:
+            line["time_bins"] = time_bins_report(dev)
         if not args.no_cpu_baseline and world == 1:
             from oracle import crk as O
             p, dt, ns = calibrated_oracle(st, args.cpu_seconds, seed=2)
@@ -524,6 +614,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-learned-h", action="store_true", help="skip the learned-h training and evaluation")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-boxes measurement")
+    ap.add_argument("--no-time-bins", action="store_true", help="skip the hierarchical time-bin measurement")
     ap.add_argument("--no-autotune", action="store_true", help="keep the built-in pass variants")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":

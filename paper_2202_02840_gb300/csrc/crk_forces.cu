@@ -229,6 +229,17 @@ struct P4 {
         s.vsig = 0.f;
         s.qmax = 0.f;
     }
+    __device__ static void zero(IState &s) {
+        for (int g = 0; g < 3; g++) s.F[g] = Acc<COMP>();
+        s.du = Acc<COMP>();
+        s.vsig = s.qmax = 0.f;
+    }
+    __device__ static void merge(IState &s, const IState &o) {
+        for (int g = 0; g < 3; g++) merge_acc(s.F[g], o.F[g]);
+        merge_acc(s.du, o.du);
+        s.vsig = fmaxf(s.vsig, o.vsig);
+        s.qmax = fmaxf(s.qmax, o.qmax);
+    }
     __device__ static Rec load(uint32_t e, size_t, const Params &p) { return ldg_frec(p.frec + (e & 0x3fffffffu)); }
     __device__ static void pair(IState &s, const Rec &r, uint32_t e, size_t pos, bool in_i, const Params &p) {
         const bool in_j = in_i ? (e >> 31) != 0u : true;
@@ -281,6 +292,8 @@ struct P5 {
         s.me = valid ? p.sig[i] : make_float4(0.f, 0.f, 0.f, 0.f);
         s.m = valid ? p.mass[i] : 1.f;
     }
+    __device__ static void zero(IState &s) { s.du = Acc<COMP>(); }
+    __device__ static void merge(IState &s, const IState &o) { merge_acc(s.du, o.du); }
     // the stored entry carries j (written by P4): the list itself is not read
     static constexpr bool ENTRIES = false;
     __device__ static Rec load(uint32_t, size_t pos, const Params &p) {

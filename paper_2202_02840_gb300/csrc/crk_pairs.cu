@@ -183,6 +183,23 @@ struct P2 {
         // self term of gather(i): x = 0, W(0) (unnormalised 1), grad W(0) = 0
         if (valid) s.m0.add(__uint_as_float(__ldg(&p.qV[i].w)));
     }
+    __device__ static void zero(IState &s) {
+        s.m0 = Acc<COMP>();
+        for (int a = 0; a < 3; a++) s.m1[a] = s.dm0[a] = Acc<COMP>();
+        for (int a = 0; a < 6; a++) s.m2[a] = Acc<COMP>();
+        for (int a = 0; a < 9; a++) s.s1[a] = Acc<COMP>();
+        for (int a = 0; a < 18; a++) s.s2[a] = Acc<COMP>();
+    }
+    __device__ static void merge(IState &s, const IState &o) {
+        merge_acc(s.m0, o.m0);
+        for (int a = 0; a < 3; a++) {
+            merge_acc(s.m1[a], o.m1[a]);
+            merge_acc(s.dm0[a], o.dm0[a]);
+        }
+        for (int a = 0; a < 6; a++) merge_acc(s.m2[a], o.m2[a]);
+        for (int a = 0; a < 9; a++) merge_acc(s.s1[a], o.s1[a]);
+        for (int a = 0; a < 18; a++) merge_acc(s.s2[a], o.s2[a]);
+    }
     __device__ static Rec load(uint32_t e, size_t, const Params &p) { return __ldg(p.qV + (e & 0x3fffffffu)); }
     __device__ static void pair(IState &s, const Rec &r, uint32_t, size_t, bool, const Params &) {
         int dx = (int)(s.q.x - r.x), dy = (int)(s.q.y - r.y), dz = (int)(s.q.z - r.z);
@@ -307,6 +324,12 @@ struct P3 {
         s.v[0] = v.x; s.v[1] = v.y; s.v[2] = v.z;
 #pragma unroll
         for (int k = 0; k < 9; k++) s.acc[k] = Acc<COMP>();
+    }
+    __device__ static void zero(IState &s) {
+        for (int k = 0; k < 9; k++) s.acc[k] = Acc<COMP>();
+    }
+    __device__ static void merge(IState &s, const IState &o) {
+        for (int k = 0; k < 9; k++) merge_acc(s.acc[k], o.acc[k]);
     }
     struct Rec {
         uint4 qV;

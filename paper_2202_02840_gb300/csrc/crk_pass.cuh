@@ -224,6 +224,80 @@ __global__ void __launch_bounds__(32) k_lpass_sm(ListGeom g, typename P::Params 
     }
 }
 
+// Split form, for passes over few tiles (time bins: the leaves ending a step
+// at a deep level): S warps share one tile, warp w walking the entry range
+// [w chunk, (w+1) chunk) of every lane's list, so a tile's pairs take 1/S of
+// the time of one warp walking them all.  Warps w > 0 start from empty sums
+// (P::zero); warp 0 merges their partial states in warp order (P::merge,
+// deterministic) and finishes.  The stored forces of P4 go to the same entry
+// positions as in the other forms; the sums differ from them by rounding.
+template <class P>
+constexpr int split_warps() {
+    return (7 * 32 * sizeof(typename P::IState) <= 44 * 1024) ? 8
+           : ((3 * 32 * sizeof(typename P::IState) <= 44 * 1024) ? 4 : 2);
+}
+
+template <class P, int S, int U>
+__global__ void __launch_bounds__(S * 32) k_lpass_split(ListGeom g, typename P::Params prm, const int32_t *order) {
+    using IS = typename P::IState;
+    __shared__ __align__(16) unsigned char part[(S - 1) * 32 * sizeof(IS)];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int tile = order[blockIdx.x];
+    const int i = tile * TILE + lane;
+    const bool valid = i < g.n;
+    IS st;
+    P::init(st, i, valid, prm);
+    if (w > 0) P::zero(st);
+    const uint32_t *col0 = g.ent + (size_t)tile * g.kcap * 32 + lane;
+    const size_t fb = (size_t)g.fbase[tile] * 32 + lane;
+    const int len = min((int)(P::GATHER ? g.len_g[tile] : g.len_u[tile]), g.kcap);
+    const int mg = valid ? min(g.cnt_g[i], g.kcap) : 0;
+    const int my = P::GATHER ? mg : (valid ? min(g.cnt_u[i], g.kcap) : 0);
+    const int chunk = ((len + S - 1) / S + U - 1) / U * U;
+    const int k0 = w * chunk, k1 = min(len, k0 + chunk);
+    const int mk = min(my, k1);   // this warp's entries of this lane: [k0, mk)
+    auto entry = [&](int k) -> uint32_t {
+        const int c = k < mg ? k : g.kcap - 1 - (k - mg);
+        return __ldg(col0 + (size_t)c * 32);
+    };
+    constexpr bool E = P::ENTRIES;
+    uint32_t en[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) en[u] = (E && k0 + u < mk) ? entry(k0 + u) : 0u;
+    for (int k = k0; k < k1; k += U) {
+        uint32_t ec[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            ec[u] = en[u];
+            if (E && k + U + u < mk) en[u] = entry(k + U + u);
+        }
+        const size_t pos = fb + (size_t)k * 32;
+        typename P::Rec r[U];
+#pragma unroll
+        for (int u = 0; u < U; u++)
+            if (k + u < mk) r[u] = P::load(ec[u], pos + 32 * u, prm);
+#pragma unroll
+        for (int u = 0; u < U; u++)
+            if (k + u < mk) P::pair(st, r[u], ec[u], pos + 32 * u, k + u < mg, prm);
+    }
+    IS *sp = reinterpret_cast<IS *>(part);
+    if (w > 0) sp[(w - 1) * 32 + lane] = st;
+    __syncthreads();
+    if (w == 0) {
+#pragma unroll 1
+        for (int v = 1; v < S; v++) P::merge(st, sp[(v - 1) * 32 + lane]);
+        if (valid) P::finish(st, i, prm);
+    }
+}
+
+// merge a partial pair sum into another (the compensated sum keeps the
+// partial's correction term)
+template <bool C>
+__device__ __forceinline__ void merge_acc(Acc<C> &d, const Acc<C> &o) {
+    d.add(o.s);
+    if (C) d.add(-o.c);
+}
+
 // ---------------------------------------------------------------- autotuner
 //
 // Variants of a list pass: the loop form (U pairs per iteration for the small
@@ -309,7 +383,12 @@ int launch_lpass(crk_ctx *ctx, int prof_id, const typename P::Params &prm, cudaS
         g.ntiles = ctx->nact;
         constexpr int U = P::PREFETCH ? 1 : P::UNROLL;
         prof_begin(ctx, prof_id, s);
-        k_lpass<P, WARPS, U><<<grid_for(ctx->nact, WARPS), WARPS * 32, 0, s>>>(g, prm, ctx->act);
+        const int nsm = ctx->nsm > 0 ? ctx->nsm : 152;
+        constexpr int S = split_warps<P>();
+        if (ctx->nact < 8 * nsm)   // few tiles: S warps per tile
+            k_lpass_split<P, S, U><<<ctx->nact, S * 32, 0, s>>>(g, prm, ctx->act);
+        else
+            k_lpass<P, WARPS, U><<<grid_for(ctx->nact, WARPS), WARPS * 32, 0, s>>>(g, prm, ctx->act);
         ++ctx->launches;
         prof_end(ctx, s);
         CRK_LAUNCH_CHECK(ctx, what);

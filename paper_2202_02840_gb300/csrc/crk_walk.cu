@@ -174,6 +174,108 @@ __global__ void __launch_bounds__(WALK_WARPS * 32) k_walk(WalkArgs a) {
     }
 }
 
+// The walk for few tiles (time bins, act set): S warps share one tile, warp w
+// testing the candidate tiles [w chunk, (w+1) chunk) of its list.  A first
+// sweep counts every lane's gather and other neighbours per warp; their
+// prefix over the warps gives each warp its columns, and a second sweep
+// writes the entries there, so every list is exactly the one-warp walk's.
+template <int S>
+__global__ void __launch_bounds__(S * 32) k_walk_split(WalkArgs a) {
+    __shared__ uint4 sq[S][32];
+    __shared__ int cnt[2][S][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int tile = a.act[blockIdx.x];
+    const int i = tile * TILE + lane;
+    const bool valid = i < a.n;
+    const uint4 qi = valid ? a.q4[i] : make_uint4(0, 0, 0, 0);
+    const unsigned long long Hi2 = (unsigned long long)qi.w * qi.w;
+    const int kcap = a.kcap;
+    uint32_t *const col0 = a.ent + (size_t)tile * kcap * 32 + lane;
+    const uint2 lo = a.ofs[tile];
+    const uint4 Ilo = __ldg(a.tlo + tile), Ihi = __ldg(a.thi + tile);
+    const int nt = (int)lo.y;
+    const int chunk = (nt + S - 1) / S;
+    const int t0 = w * chunk, t1 = min(nt, t0 + chunk);
+    int base_g = 0, base_o = 0, tot_g = 0, tot_o = 0;
+    for (int phase = 0; phase < 2; phase++) {
+        int cg = 0, co = 0;
+        for (int t = t0; t < t1; t++) {
+            const int J = (int)__ldg(a.tiles + lo.x + t);
+            const uint4 Jlo = __ldg(a.tlo + J), Jhi = __ldg(a.thi + J);
+            const unsigned long long gx = point_gap(qi.x, Jlo.x, Jhi.x), gy = point_gap(qi.y, Jlo.y, Jhi.y),
+                                     gz = point_gap(qi.z, Jlo.z, Jhi.z);
+            const unsigned long long reach = qi.w > Jlo.w ? qi.w : Jlo.w;
+            const bool near = valid && gx * gx + gy * gy + gz * gz < reach * reach;
+            if (__ballot_sync(0xffffffffu, near) == 0u) continue;
+            const int j0 = J * TILE;
+            const int cj = min(TILE, a.n - j0);
+            __syncwarp();
+            bool keep = false;
+            if (lane < cj) {
+                const uint4 q = __ldg(a.q4 + j0 + lane);
+                sq[w][lane] = q;
+                const unsigned long long hx = point_gap(q.x, Ilo.x, Ihi.x), hy = point_gap(q.y, Ilo.y, Ihi.y),
+                                         hz = point_gap(q.z, Ilo.z, Ihi.z);
+                const unsigned long long rj = q.w > Ilo.w ? q.w : Ilo.w;
+                keep = hx * hx + hy * hy + hz * hz < rj * rj;
+            }
+            unsigned mask = __ballot_sync(0xffffffffu, keep);
+            __syncwarp();
+            while (mask) {
+                const int jj = __ffs(mask) - 1;
+                mask &= mask - 1u;
+                const uint4 qj = sq[w][jj];
+                const int dx = (int)(qi.x - qj.x), dy = (int)(qi.y - qj.y), dz = (int)(qi.z - qj.z);
+                const unsigned long long R2 = r2_fixed(dx, dy, dz);
+                const uint32_t j = (uint32_t)(j0 + jj);
+                if (valid && (int)j != i) {
+                    const bool in_i = R2 < Hi2;
+                    const bool in_j = R2 < (unsigned long long)qj.w * qj.w;
+                    if (in_i) {
+                        const int c = base_g + cg;
+                        if (phase == 1 && c < kcap) col0[(size_t)c * 32] = j | (in_j ? 0x80000000u : 0u);
+                        cg++;
+                    } else if (in_j) {
+                        const int c = base_o + co;
+                        if (phase == 1 && c < kcap) col0[(size_t)(kcap - 1 - c) * 32] = j;
+                        co++;
+                    }
+                }
+            }
+        }
+        if (phase == 0) {
+            cnt[0][w][lane] = cg;
+            cnt[1][w][lane] = co;
+            __syncthreads();
+            for (int v = 0; v < S; v++) {
+                if (v < w) {
+                    base_g += cnt[0][v][lane];
+                    base_o += cnt[1][v][lane];
+                }
+                tot_g += cnt[0][v][lane];
+                tot_o += cnt[1][v][lane];
+            }
+        }
+    }
+    if (w != 0) return;
+    const int cu = tot_g + tot_o;
+    if (valid) {
+        a.cnt_g[i] = tot_g;
+        a.cnt_u[i] = cu;
+    }
+    uint32_t mg = __reduce_max_sync(0xffffffffu, (uint32_t)tot_g);
+    uint32_t mu = __reduce_max_sync(0xffffffffu, (uint32_t)cu);
+    uint32_t sg = __reduce_add_sync(0xffffffffu, (uint32_t)tot_g);
+    uint32_t su = __reduce_add_sync(0xffffffffu, (uint32_t)cu);
+    if (lane == 0) {
+        a.len_g[tile] = min(mg, (uint32_t)kcap);
+        a.len_u[tile] = min(mu, (uint32_t)kcap);
+        atomicAdd(a.pairs_g, (unsigned long long)sg);
+        atomicAdd(a.pairs_u, (unsigned long long)su);
+        atomicMax(a.maxcnt, (unsigned long long)mu);
+    }
+}
+
 // total stored-force units (32 entries each) = base[last] + len_u[last]
 __global__ void k_total(int ntiles, const uint32_t *__restrict__ base, const uint32_t *__restrict__ len,
                         unsigned long long *out) {
@@ -224,7 +326,10 @@ static int launch_walk(crk_ctx *ctx, cudaStream_t s) {
     prof_begin(ctx, PROF_LISTS, s);
     const int g = grid_for(ctx->act ? ctx->nact : ctx->ntiles, WALK_WARPS);
     const bool b = ctx->nbox > 1;
-    if (ctx->volumes_only && b)
+    const int nsm = ctx->nsm > 0 ? ctx->nsm : 152;
+    if (ctx->act && !ctx->volumes_only && !b && ctx->nact < 8 * nsm)   // few tiles: 8 warps per tile
+        k_walk_split<8><<<ctx->nact, 8 * 32, 0, s>>>(walk_args(ctx));
+    else if (ctx->volumes_only && b)
         k_walk<false, true, true><<<g, WALK_WARPS * 32, 0, s>>>(walk_args(ctx));
     else if (ctx->volumes_only)
         k_walk<false, true, false><<<g, WALK_WARPS * 32, 0, s>>>(walk_args(ctx));
@@ -300,6 +405,8 @@ struct P1 {
         s.inv_h = 1.f / s.h;
         s.acc = 1.f;                                   // self: W(0) / (495/(32 pi h^3)) = 1
     }
+    __device__ static void zero(IState &s) { s.acc = 0.f; }
+    __device__ static void merge(IState &s, const IState &o) { s.acc += o.acc; }
     __device__ static Rec load(uint32_t e, size_t, const Params &p) { return __ldg(p.q4 + (e & 0x3fffffffu)); }
     __device__ static void pair(IState &s, const Rec &r, uint32_t, size_t, bool, const Params &) {
         int dx = (int)(s.q.x - r.x), dy = (int)(s.q.y - r.y), dz = (int)(s.q.z - r.z);

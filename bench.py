@@ -445,6 +445,9 @@ def aggregate(times_ms, work, dist=None, device="cpu"):
     return [float(x) for x in t.cpu()], [float(x) for x in w.cpu()]
 
 
+ORDER_NAMES = {0: "morton", 1: "hilbert", 2: "bisection"}
+
+
 def run_gpu(args):
     import torch
     import __graft_entry__
@@ -467,8 +470,29 @@ def run_gpu(args):
     vel0 = torch.from_numpy(st["vel_u"]).to(dev)
     mass = torch.from_numpy(st["mass"]).to(dev)
     pos, vel = pos0.clone(), vel0.clone()
-    ctx = crk.crk_create(precision=args.precision)
     stream = torch.cuda.current_stream(dev)
+    # tile order (Morton, Hilbert, bisection): given, or the fastest of two
+    # timed steps each on a copy of the state (part of the warm-up)
+    order_ms = {}
+    if args.tile_order == "auto":
+        for o in (0, 1, 2):
+            p, v = pos0.clone(), vel0.clone()
+            c = crk.crk_create(precision=args.precision, tile_order=o)
+            crk.crk_step(c, p, v, mass, 0.0)
+            torch.cuda.synchronize(dev)
+            t0 = torch.cuda.Event(enable_timing=True)
+            t1 = torch.cuda.Event(enable_timing=True)
+            t0.record(stream)
+            for _ in range(2):
+                crk.crk_step(c, p, v, mass, 0.0)
+            t1.record(stream)
+            torch.cuda.synchronize(dev)
+            order_ms[ORDER_NAMES[o]] = t0.elapsed_time(t1) / 2
+            c.close()
+        tile_order = min((0, 1, 2), key=lambda o: order_ms[ORDER_NAMES[o]])
+    else:
+        tile_order = int(args.tile_order)
+    ctx = crk.crk_create(precision=args.precision, tile_order=tile_order)
 
     def barrier():
         if dist is not None:
@@ -513,7 +537,7 @@ def run_gpu(args):
     d_pos = torch.empty_like(pos0)
     d_vel = torch.empty_like(vel0)
     d_mass = torch.empty_like(mass)
-    e2e_ctx = crk.crk_create(precision=args.precision)
+    e2e_ctx = crk.crk_create(precision=args.precision, tile_order=tile_order)
     for _ in range(max(1, args.warmup)):
         d_pos.copy_(h_pos, non_blocking=True)
         d_vel.copy_(h_vel, non_blocking=True)
@@ -578,6 +602,7 @@ def run_gpu(args):
                            "tiles": ntiles, "pair_candidate_tiles_per_tile": utp / max(1, ntiles),
                            "list_entries_per_particle": entries / n,
                            "autotuned_variants": {k: v for k, (v, _) in tuning.items()},
+                           "tile_order": ORDER_NAMES[tile_order], "tile_order_step_ms": order_ms or None,
                            "gather_pairs_per_particle": diags[-1]["pairs_gather"] / n,
                            "union_pairs_per_particle": diags[-1]["pairs_union"] / n},
                 "roofline": roofline,
@@ -616,6 +641,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-boxes measurement")
     ap.add_argument("--no-time-bins", action="store_true", help="skip the hierarchical time-bin measurement")
     ap.add_argument("--no-autotune", action="store_true", help="keep the built-in pass variants")
+    ap.add_argument("--tile-order", default="auto", choices=["auto", "0", "1", "2"],
+                    help="particle order of the tiles: 0 Morton, 1 Hilbert, 2 bisection, auto = fastest")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

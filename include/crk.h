@@ -83,7 +83,12 @@ typedef struct {
                              system solved in FP64;
                          2 = mixed with compensated moment and grad-v sums too */
     int kmax;         /* finest chaining-mesh level reported by crk_cells (<= 7) */
-    int reserved[6];
+    int tile_order;   /* order of the particles that cuts them into 32-particle tiles:
+                         0 = Morton (default; the chaining-mesh order of Sec. 2.3,
+                             the only one crk_cells reports),
+                         1 = Hilbert curve (same cells, no jumps between them),
+                         2 = recursive coordinate bisection (the paper's leaves) */
+    int reserved[5];
 } crk_params;
 
 /* Per-step diagnostics (host memory), all reductions in FP64. */
@@ -339,6 +344,11 @@ int crk_build_cells_batched(crk_ctx *ctx, int n, int nbox, const int32_t *box_st
  * re-evaluated) whenever it differs from the previous call's. */
 int crk_step_batched(crk_ctx *ctx, int n, int nbox, const int32_t *box_start, float *pos_h, float *vel_u,
                      const float *mass, const double *dt, crk_diag *diag, void *stream);
+
+/* The sorted order of the last build: perm[s] (device, n ints) = the caller
+ * row in slot s; tile t holds slots 32t .. 32t + 31.  For every tile_order
+ * (crk_cells reports the Morton order with its cell table). */
+int crk_order(crk_ctx *ctx, int32_t *perm, void *stream);
 
 /* Per-pass GPU timing, for roofline measurement.  enable = 1 clears the
  * records and starts recording a CUDA event pair around every pass kernel (and

@@ -29,7 +29,8 @@ class crk_params(ctypes.Structure):
     _fields_ = [(k, ctypes.c_double) for k in
                 ("gamma", "n_h", "N_res", "C_l", "C_q", "eps", "eta_crit", "eta_fold", "C_cfl", "zeta",
                  "h_min", "h_max", "dt_max")] + [
-        ("precision", ctypes.c_int), ("kmax", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
+        ("precision", ctypes.c_int), ("kmax", ctypes.c_int), ("tile_order", ctypes.c_int),
+        ("reserved", ctypes.c_int * 5)]
 
 
 class crk_diag(ctypes.Structure):
@@ -73,6 +74,7 @@ def lib():
         L.crk_compatible.argtypes = [_vp] + [_vp] * 11 + [_vp]
         L.crk_step.argtypes = [_vp, _ci, _vp, _vp, _vp, ctypes.c_double, ctypes.POINTER(crk_diag), _vp]
         L.crk_reset_rates.argtypes = [_vp]
+        L.crk_order.argtypes = [_vp, _vp, _vp]
         L.crk_cycle.argtypes = [_vp, _ci, _vp, _vp, _vp, ctypes.c_double, _ci, _ci, ctypes.POINTER(crk_htb_stats),
                                 _vp]
         L.crk_htb_levels.argtypes = [_vp, _ci, _vp, _vp, ctypes.c_double, _ci, _ci, _vp,
@@ -180,6 +182,13 @@ def crk_cells(ctx, kmax=7, stream=None):
     ctx.check(lib().crk_cells(ctx.handle, _vp(keys.data_ptr()), _vp(perm.data_ptr()), _vp(cs.data_ptr()),
                               ctypes.byref(k), _stream(stream)))
     return keys, perm, cs[: (1 << (3 * k.value)) + 1], k.value
+
+
+def crk_order(ctx, stream=None):
+    """Sorted order of the last build: perm[s] = caller row in slot s (int32)."""
+    perm = torch.empty(ctx.n, dtype=torch.int32, device=torch.device("cuda"))
+    ctx.check(lib().crk_order(ctx.handle, _vp(perm.data_ptr()), _stream(stream)))
+    return perm
 
 
 def crk_build_stats(ctx, stream=None):

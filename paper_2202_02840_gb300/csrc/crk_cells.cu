@@ -25,7 +25,7 @@ constexpr unsigned FULL = 0xffffffffu;
 // (0, 1/3)) are counted and replaced by a harmless record.
 __global__ void k_keys(int n, const float4 *__restrict__ pos, uint32_t *__restrict__ key,
                        int32_t *__restrict__ idx, uint4 *__restrict__ q_tmp,
-                       float *__restrict__ h_tmp, unsigned long long *counters) {
+                       float *__restrict__ h_tmp, unsigned long long *counters, int hilbert) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     uint32_t hbits = 0u;
     if (t < n) {
@@ -39,7 +39,7 @@ __global__ void k_keys(int n, const float4 *__restrict__ pos, uint32_t *__restri
         uint4 q = make_uint4(to_fixed(p.x), to_fixed(p.y), to_fixed(p.z), to_fixed(p.w));
         q_tmp[t] = q;
         h_tmp[t] = p.w;
-        key[t] = morton30(q.x, q.y, q.z);
+        key[t] = hilbert ? hilbert30(q.x, q.y, q.z) : morton30(q.x, q.y, q.z);
         idx[t] = t;
         hbits = __float_as_uint(p.w);   // h > 0: the bits order like the values
     }
@@ -203,6 +203,262 @@ static int radix_sort(crk_ctx *ctx, int n, int bits, cudaStream_t s) {
         uint32_t *tk = kin; kin = kout; kout = tk;
         int32_t *tv = vin; vin = vout; vout = tv;
     }
+    return CRK_OK;
+}
+
+// ------------------------------------------------------------------ recursive coordinate bisection
+//
+// tile_order 2: the Morton order is refined by recursive coordinate bisection
+// into leaves of one tile.  A segment [a, b) of more than 32 particles splits
+// at nl = 32 ceil(ceil((b - a)/2) / 32) (every left part a whole number of
+// tiles) along the longest axis of its fixed-point box: its particles are
+// binned into 256 equal slices of that box, the slice holding the nl-th
+// particle is the median slice, and a stable partition puts the slices
+// below it first, then the median slice, then the slices above, so the
+// first nl particles are the lower part.  Level by level, all segments at
+// once; within a leaf the Morton order stays.
+
+constexpr int RCB_BINS = 256;
+
+__host__ __device__ __forceinline__ int rcb_left(int size) { return ((size + 1) / 2 + 31) / 32 * 32; }
+
+// the segment of slot s after `level` splits: start a, size, index (path bits)
+__device__ __forceinline__ bool rcb_segment(int n, int level, int s, int &a, int &size, int &path) {
+    a = 0;
+    size = n;
+    path = 0;
+    for (int l = 0; l < level; l++) {
+        if (size <= TILE) return false;
+        const int nl = rcb_left(size);
+        if (s < a + nl) {
+            size = nl;
+            path = 2 * path;
+        } else {
+            a += nl;
+            size -= nl;
+            path = 2 * path + 1;
+        }
+    }
+    return size > TILE;
+}
+
+// per slot: its segment (start, index; -1 when the segment does not split)
+// and the segment's box (one atomic per segment a warp touches)
+__global__ void k_rcb_box(int n, int level, const int32_t *__restrict__ perm, const uint4 *__restrict__ q,
+                          int32_t *__restrict__ seg_a, int32_t *__restrict__ seg_id, uint32_t *__restrict__ blo,
+                          uint32_t *__restrict__ bhi, int32_t *__restrict__ bsize) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    int a = 0, size = 0, path = -1;
+    bool act = false;
+    uint4 p = make_uint4(0, 0, 0, 0);
+    if (s < n) {
+        act = rcb_segment(n, level, s, a, size, path);
+        if (!act) path = -1;
+        seg_a[s] = a;
+        seg_id[s] = path;
+        p = q[perm[s]];
+    }
+    const unsigned peers = __match_any_sync(FULL, path);
+    uint32_t lx = p.x, ly = p.y, lz = p.z, hx = p.x, hy = p.y, hz = p.z;
+    for (int k = 0; k < 32; k++) {
+        const uint32_t ox = __shfl_sync(FULL, p.x, k), oy = __shfl_sync(FULL, p.y, k), oz = __shfl_sync(FULL, p.z, k);
+        if ((peers >> k) & 1u) {
+            lx = min(lx, ox); ly = min(ly, oy); lz = min(lz, oz);
+            hx = max(hx, ox); hy = max(hy, oy); hz = max(hz, oz);
+        }
+    }
+    if (act && (int)(threadIdx.x & 31) == __ffs(peers) - 1) {
+        atomicMin(blo + 3 * path, lx); atomicMin(blo + 3 * path + 1, ly); atomicMin(blo + 3 * path + 2, lz);
+        atomicMax(bhi + 3 * path, hx); atomicMax(bhi + 3 * path + 1, hy); atomicMax(bhi + 3 * path + 2, hz);
+        bsize[path] = size;
+    }
+}
+
+__device__ __forceinline__ int rcb_axis(const uint32_t *lo, const uint32_t *hi, int path, uint32_t &l0,
+                                        unsigned long long &ext) {
+    const uint32_t e0 = hi[3 * path] - lo[3 * path], e1 = hi[3 * path + 1] - lo[3 * path + 1],
+                   e2 = hi[3 * path + 2] - lo[3 * path + 2];
+    int ax = 0;
+    uint32_t m = e0;
+    if (e1 > m) { ax = 1; m = e1; }
+    if (e2 > m) { ax = 2; m = e2; }
+    l0 = lo[3 * path + ax];
+    ext = (unsigned long long)m + 1ull;
+    return ax;
+}
+
+// slice of every particle along its segment's axis, and the slice counts
+__global__ void k_rcb_hist(int n, const int32_t *__restrict__ perm, const uint4 *__restrict__ q,
+                           const int32_t *__restrict__ seg_id, const uint32_t *__restrict__ blo,
+                           const uint32_t *__restrict__ bhi, uint32_t *__restrict__ bin, uint32_t *__restrict__ hist) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const int path = seg_id[s];
+    if (path < 0) return;
+    uint32_t l0;
+    unsigned long long ext;
+    const int ax = rcb_axis(blo, bhi, path, l0, ext);
+    const uint4 p = q[perm[s]];
+    const uint32_t c = ax == 0 ? p.x : (ax == 1 ? p.y : p.z);
+    const uint32_t b = (uint32_t)(((unsigned long long)(c - l0) * RCB_BINS) / ext);
+    bin[s] = b;
+    atomicAdd(hist + (size_t)path * RCB_BINS + b, 1u);
+}
+
+// per segment (warp): the median slice and the counts below it and in it
+__global__ void k_rcb_pick(int nseg, const int32_t *__restrict__ bsize, const uint32_t *__restrict__ hist,
+                           uint32_t *__restrict__ pick) {
+    const int lane = threadIdx.x & 31;
+    const int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (g >= nseg) return;
+    const int size = bsize[g];
+    if (size <= TILE) return;
+    const uint32_t nl = (uint32_t)rcb_left(size);
+    uint32_t v[RCB_BINS / 32], sum = 0;
+#pragma unroll
+    for (int k = 0; k < RCB_BINS / 32; k++) {
+        v[k] = hist[(size_t)g * RCB_BINS + lane * (RCB_BINS / 32) + k];
+        sum += v[k];
+    }
+    uint32_t x = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(FULL, x, o);
+        if (lane >= o) x += y;
+    }
+    uint32_t below = x - sum;   // particles in the slices before this lane's
+    int found = -1;
+    uint32_t c0 = 0, c1 = 0;
+#pragma unroll
+    for (int k = 0; k < RCB_BINS / 32; k++) {
+        if (found < 0 && below + v[k] >= nl) {
+            found = lane * (RCB_BINS / 32) + k;
+            c0 = below;
+            c1 = v[k];
+        }
+        below += v[k];
+    }
+    const unsigned m = __ballot_sync(FULL, found >= 0);
+    if (lane == __ffs(m) - 1) {
+        pick[3 * g] = (uint32_t)found;
+        pick[3 * g + 1] = c0;
+        pick[3 * g + 2] = c1;
+    }
+}
+
+__global__ void k_rcb_flags(int n, const int32_t *__restrict__ seg_id, const uint32_t *__restrict__ bin,
+                            const uint32_t *__restrict__ pick, uint32_t *__restrict__ f0, uint32_t *__restrict__ f1) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const int path = seg_id[s];
+    uint32_t a = 0, b = 0;
+    if (path >= 0) {
+        const uint32_t m = pick[3 * path], v = bin[s];
+        a = v < m;
+        b = v == m;
+    }
+    f0[s] = a;
+    f1[s] = b;
+}
+
+// stable three-way partition of every splitting segment (below, median, above)
+__global__ void k_rcb_scatter(int n, const int32_t *__restrict__ perm, const int32_t *__restrict__ seg_a,
+                              const int32_t *__restrict__ seg_id, const uint32_t *__restrict__ bin,
+                              const uint32_t *__restrict__ pick, const uint32_t *__restrict__ r0,
+                              const uint32_t *__restrict__ r1, int32_t *__restrict__ out) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const int path = seg_id[s];
+    int d = s;
+    if (path >= 0) {
+        const int a = seg_a[s];
+        const uint32_t m = pick[3 * path], v = bin[s];
+        const int k0 = (int)(r0[s] - r0[a]), k1 = (int)(r1[s] - r1[a]);
+        const int c0 = (int)pick[3 * path + 1], c1 = (int)pick[3 * path + 2];
+        d = v < m ? a + k0 : (v == m ? a + c0 + k1 : a + c0 + c1 + (s - a - k0 - k1));
+    }
+    out[d] = perm[s];
+}
+
+template <class T>
+static int rcb_grow(crk_ctx *ctx, T **p, size_t count) {
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    CRK_CUDA(ctx, cudaMalloc((void **)p, sizeof(T) * (count ? count : 1)));
+    ++ctx->alloc_gen;
+    return CRK_OK;
+}
+
+static int ensure_rcb(crk_ctx *ctx, int n, int nseg) {
+    int rc = CRK_OK;
+    if (n > ctx->cap_rcb || nseg > ctx->cap_rcb_seg) {
+        ctx->cap_rcb = 0;
+        ctx->cap_rcb_seg = 0;
+        rc = rcb_grow(ctx, &ctx->rcb_a, n);
+        if (!rc) rc = rcb_grow(ctx, &ctx->rcb_id, n);
+        if (!rc) rc = rcb_grow(ctx, &ctx->rcb_bin, n);
+        if (!rc) rc = rcb_grow(ctx, &ctx->rcb_f, 4 * (size_t)n);
+        if (!rc) rc = rcb_grow(ctx, &ctx->rcb_lo, 3 * (size_t)nseg);
+        if (!rc) rc = rcb_grow(ctx, &ctx->rcb_hi, 3 * (size_t)nseg);
+        if (!rc) rc = rcb_grow(ctx, &ctx->rcb_size, nseg);
+        if (!rc) rc = rcb_grow(ctx, &ctx->rcb_pick, 3 * (size_t)nseg);
+        if (!rc) rc = rcb_grow(ctx, &ctx->rcb_hist, (size_t)RCB_BINS * nseg);
+        if (rc) return rc;
+        ctx->cap_rcb = n;
+        ctx->cap_rcb_seg = nseg;
+    }
+    return CRK_OK;
+}
+
+void rcb_free(crk_ctx *ctx) {
+    void *ps[] = {ctx->rcb_a, ctx->rcb_id, ctx->rcb_size, ctx->rcb_bin, ctx->rcb_f, ctx->rcb_lo, ctx->rcb_hi,
+                  ctx->rcb_pick, ctx->rcb_hist};
+    for (void *p : ps)
+        if (p) cudaFree(p);
+    ctx->rcb_a = ctx->rcb_id = ctx->rcb_size = nullptr;
+    ctx->rcb_bin = ctx->rcb_f = ctx->rcb_lo = ctx->rcb_hi = ctx->rcb_pick = ctx->rcb_hist = nullptr;
+    ctx->cap_rcb = ctx->cap_rcb_seg = 0;
+}
+
+__global__ void k_fill_u32(long long count, uint32_t v, uint32_t *out) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < count) out[k] = v;
+}
+
+// Refine the sorted order idx_a (input indices) by recursive coordinate
+// bisection of the fixed-point records q_tmp (input order).
+static int rcb_refine(crk_ctx *ctx, int n, cudaStream_t s) {
+    int levels = 0;
+    for (int size = n; size > TILE; size = rcb_left(size)) levels++;   // the largest segment goes left
+    int rc = ensure_rcb(ctx, n, 1 << (levels > 0 ? levels - 1 : 0));
+    if (rc) return rc;
+    int32_t *cur = ctx->idx_a, *nxt = ctx->idx_b;
+    uint32_t *f0 = ctx->rcb_f, *f1 = ctx->rcb_f + n, *r0 = ctx->rcb_f + 2 * (size_t)n, *r1 = ctx->rcb_f + 3 * (size_t)n;
+    const int g = grid_for(n, 256);
+    for (int L = 0; L < levels; L++) {
+        const int nseg = 1 << L;
+        k_fill_u32<<<grid_for(3ll * nseg, 256), 256, 0, s>>>(3ll * nseg, 0xffffffffu, ctx->rcb_lo);
+        CRK_CUDA(ctx, cudaMemsetAsync(ctx->rcb_hi, 0, sizeof(uint32_t) * 3 * (size_t)nseg, s));
+        CRK_CUDA(ctx, cudaMemsetAsync(ctx->rcb_size, 0, sizeof(int32_t) * (size_t)nseg, s));
+        CRK_CUDA(ctx, cudaMemsetAsync(ctx->rcb_hist, 0, sizeof(uint32_t) * RCB_BINS * (size_t)nseg, s));
+        k_rcb_box<<<g, 256, 0, s>>>(n, L, cur, ctx->q_tmp, ctx->rcb_a, ctx->rcb_id, ctx->rcb_lo, ctx->rcb_hi,
+                                    ctx->rcb_size);
+        k_rcb_hist<<<g, 256, 0, s>>>(n, cur, ctx->q_tmp, ctx->rcb_id, ctx->rcb_lo, ctx->rcb_hi, ctx->rcb_bin,
+                                     ctx->rcb_hist);
+        k_rcb_pick<<<grid_for(32ll * nseg, 256), 256, 0, s>>>(nseg, ctx->rcb_size, ctx->rcb_hist, ctx->rcb_pick);
+        k_rcb_flags<<<g, 256, 0, s>>>(n, ctx->rcb_id, ctx->rcb_bin, ctx->rcb_pick, f0, f1);
+        ctx->launches += 5;
+        CRK_LAUNCH_CHECK(ctx, "bisection");
+        rc = scan_u32(ctx, f0, r0, n, s);
+        if (!rc) rc = scan_u32(ctx, f1, r1, n, s);
+        if (rc) return rc;
+        k_rcb_scatter<<<g, 256, 0, s>>>(n, cur, ctx->rcb_a, ctx->rcb_id, ctx->rcb_bin, ctx->rcb_pick, r0, r1, nxt);
+        ++ctx->launches;
+        CRK_LAUNCH_CHECK(ctx, "bisection");
+        int32_t *t = cur; cur = nxt; nxt = t;
+    }
+    if (cur != ctx->idx_a)
+        CRK_CUDA(ctx, cudaMemcpyAsync(ctx->idx_a, cur, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
     return CRK_OK;
 }
 
@@ -527,9 +783,12 @@ int build_cells_sorted(crk_ctx *ctx, int n, const float4 *pos, const int32_t *ba
     uint4 *q_tmp = ctx->q_tmp;
     float *h_tmp = ctx->h_tmp;
     prof_begin(ctx, PROF_BUILD, s);
-    k_keys<<<grid_for(n, 256), 256, 0, s>>>(n, pos, ctx->key_a, ctx->idx_a, q_tmp, h_tmp, ctx->counters);
+    k_keys<<<grid_for(n, 256), 256, 0, s>>>(n, pos, ctx->key_a, ctx->idx_a, q_tmp, h_tmp, ctx->counters,
+                                            ctx->p.tile_order == 1);
     ++ctx->launches;
     CRK_LAUNCH_CHECK(ctx, "keys");
+    if (box_of_input && ctx->p.tile_order == 2)
+        return crk_set_error(ctx, CRK_EINVAL, "the bisection order covers one box (tile_order 0 or 1 for batches)");
     if (box_of_input) {
         // batched boxes: stable sort by Morton key, then stable sort by box,
         // which leaves the order box-major and Morton within each box
@@ -548,14 +807,19 @@ int build_cells_sorted(crk_ctx *ctx, int n, const float4 *pos, const int32_t *ba
     } else {
         rc = radix_sort(ctx, n, 30, s);
         if (rc) return rc;
+        // sorted keys (read by the chaining-mesh table, which only the Morton order has)
         CRK_CUDA(ctx, cudaMemcpyAsync(ctx->keys, ctx->key_a, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s));
+        if (ctx->p.tile_order == 2) {
+            rc = rcb_refine(ctx, n, s);
+            if (rc) return rc;
+        }
     }
     k_gather_sorted<<<grid_for(n, 256), 256, 0, s>>>(n, ctx->idx_a, q_tmp, h_tmp, base_perm, ctx->q4,
                                                      ctx->hs, ctx->idx_b);
     ++ctx->launches;
     CRK_LAUNCH_CHECK(ctx, "gather sorted");
     CRK_CUDA(ctx, cudaMemcpyAsync(ctx->perm, ctx->idx_b, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
-    if (!box_of_input) {   // the chaining-mesh table describes one box
+    if (!box_of_input && ctx->p.tile_order == 0) {   // the chaining-mesh table: one box, Morton order
         k_cell_start<<<grid_for(n + 1, 256), 256, 0, s>>>(n, ctx->keys, ctx->p.kmax, ctx->counters,
                                                           ctx->cell_start);
         ++ctx->launches;

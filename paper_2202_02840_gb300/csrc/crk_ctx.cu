@@ -423,7 +423,8 @@ extern "C" int crk_create(const crk_params *p, crk_ctx **out) {
     if (p) prm = *p; else crk_default_params(&prm);
     if (!(prm.gamma > 1.0) || !(prm.n_h > 0) || !(prm.N_res > 0) || !(prm.eta_fold > 0) ||
         !(prm.h_max > 0 && prm.h_max < 1.0 / 3.0) || !(prm.h_min > 0 && prm.h_min < prm.h_max) ||
-        prm.kmax < 1 || prm.kmax > 7 || prm.precision < 0 || prm.precision > 2 || !(prm.dt_max > 0))
+        prm.kmax < 1 || prm.kmax > 7 || prm.precision < 0 || prm.precision > 2 || !(prm.dt_max > 0) ||
+        prm.tile_order < 0 || prm.tile_order > 2)
         return CRK_EINVAL;
     crk_ctx *ctx = new (std::nothrow) crk_ctx();
     if (!ctx) return CRK_ENOMEM;
@@ -478,6 +479,7 @@ extern "C" int crk_destroy(crk_ctx *ctx) {
     if (ctx->tile_order) cudaFree(ctx->tile_order);
     mlp_free(ctx);
     htb_free(ctx);
+    rcb_free(ctx);
     graph_free(ctx);
     prof_free(ctx);
     delete ctx;
@@ -596,11 +598,23 @@ extern "C" int crk_build_cells_batched(crk_ctx *ctx, int n, int nbox, const int3
     return CRK_OK;
 }
 
+extern "C" int crk_order(crk_ctx *ctx, int32_t *perm, void *stream) {
+    int rc = need_built(ctx);
+    if (rc) return rc;
+    if (!perm) return crk_set_error(ctx, CRK_EINVAL, "null perm");
+    if (ctx->n)
+        CRK_CUDA(ctx, cudaMemcpyAsync(perm, ctx->perm, 4 * (size_t)ctx->n, cudaMemcpyDeviceToDevice,
+                                      (cudaStream_t)stream));
+    return CRK_OK;
+}
+
 extern "C" int crk_cells(crk_ctx *ctx, uint32_t *keys, int32_t *perm, int32_t *cell_start, int *k_out,
                          void *stream) {
     int rc = need_built(ctx);
     if (rc) return rc;
     if (ctx->nbox > 1) return crk_set_error(ctx, CRK_ESTATE, "the chaining-mesh table describes one box");
+    if (ctx->p.tile_order != 0)
+        return crk_set_error(ctx, CRK_ESTATE, "the chaining-mesh table describes the Morton order (tile_order 0)");
     cudaStream_t s = (cudaStream_t)stream;
     rc = crk_sync_counters(ctx, s);
     if (rc) return rc;

@@ -199,6 +199,12 @@ struct crk_ctx {
     int cap_bk = 0;
     unsigned long long alloc_gen = 0;   // bumped by every device (re)allocation
 
+    // recursive coordinate bisection (tile_order 2): per-slot and per-segment scratch
+    int cap_rcb = 0, cap_rcb_seg = 0;
+    int32_t *rcb_a = nullptr, *rcb_id = nullptr, *rcb_size = nullptr;
+    uint32_t *rcb_bin = nullptr, *rcb_f = nullptr, *rcb_lo = nullptr, *rcb_hi = nullptr, *rcb_pick = nullptr;
+    uint32_t *rcb_hist = nullptr;
+
     // hierarchical time bins (the tiles are the leaves; per-tile and sorted per-particle arrays)
     int cap_htb = 0;                 // tiles the per-tile arrays hold
     int cap_htbp = 0;                // particles the per-particle arrays hold
@@ -250,6 +256,7 @@ enum { PROF_P1 = 0, PROF_PN = 1, PROF_P2 = 2, PROF_P3 = 3, PROF_P4 = 4, PROF_P5 
        PROF_LISTS = 7, PROF_MLP_FWD = 8, PROF_MLP_TRAIN = 9, PROF_NPASS = 10 };
 void mlp_free(crk_ctx *ctx);
 void htb_free(crk_ctx *ctx);
+void rcb_free(crk_ctx *ctx);
 void graph_free(crk_ctx *ctx);
 void prof_begin(crk_ctx *ctx, int id, cudaStream_t s);
 void prof_end(crk_ctx *ctx, cudaStream_t s);
@@ -289,6 +296,37 @@ __device__ __forceinline__ uint32_t spread3(uint32_t v) {   // 10 bits -> every 
 
 __device__ __forceinline__ uint32_t morton30(uint32_t qx, uint32_t qy, uint32_t qz) {
     return spread3(qx >> 22) | (spread3(qy >> 22) << 1) | (spread3(qz >> 22) << 2);
+}
+
+// Index along the Hilbert curve through the 2^10 cells per axis of the top 10
+// fixed-point bits (Skilling's transposed form: the axes are rotated and
+// reflected level by level into the curve's transposed index, which is Gray
+// decoded and interleaved, x most significant).  Like the Morton key, a
+// prefix of 3k bits names a level-k cell, but consecutive cells along the
+// curve always share a face, so runs of consecutive particles stay compact.
+__device__ __forceinline__ uint32_t hilbert30(uint32_t qx, uint32_t qy, uint32_t qz) {
+    uint32_t X[3] = {qx >> 22, qy >> 22, qz >> 22};
+#pragma unroll
+    for (uint32_t Q = 1u << 9; Q > 1u; Q >>= 1) {
+        const uint32_t P = Q - 1u;
+#pragma unroll
+        for (int i = 0; i < 3; i++) {
+            if (X[i] & Q) {
+                X[0] ^= P;
+            } else {
+                const uint32_t t = (X[0] ^ X[i]) & P;
+                X[0] ^= t;
+                X[i] ^= t;
+            }
+        }
+    }
+    X[1] ^= X[0];
+    X[2] ^= X[1];
+    uint32_t t = 0;
+#pragma unroll
+    for (uint32_t Q = 1u << 9; Q > 1u; Q >>= 1)
+        if (X[2] & Q) t ^= Q - 1u;
+    return spread3(X[2] ^ t) | (spread3(X[1] ^ t) << 1) | (spread3(X[0] ^ t) << 2);
 }
 
 // floor(s * 2^32) for s in [0,1): the product is exact, truncation is floor.

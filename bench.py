@@ -431,6 +431,64 @@ def time_bins_report(dev, side=64, L=5, cycles=4, f_ls=(0, 1, 2, 3, 4), warm_ste
     return out
 
 
+def sod_report(dev, sides=(64, 128, 256)):
+    """Sod shock tube (the paper's Sec. 4 test, inputs.sod) to t = 0.075 (the
+    paper's t = 0.15) at several resolutions: GPU time of each run, the
+    one-dimensionality of the flow, and self-convergence: the L1 difference
+    of each run's binned profiles (density, velocity, pressure, specific
+    energy) over the isolated half from those of the finest run.  The L1
+    against the exact Riemann solution is measured by the tests."""
+    import numpy as np
+    import torch
+    from paper_2202_02840_gb300 import crk, inputs
+
+    runs, parts = {}, {}
+    for n in sides:
+        st = inputs.sod(n)
+        pos = torch.from_numpy(st["pos_h"]).to(dev)
+        vel = torch.from_numpy(st["vel_u"]).to(dev)
+        mass = torch.from_numpy(st["mass"]).to(dev)
+        d = crk.crk_step(crk.crk_create(tile_order=1), pos.clone(), vel.clone(), mass, 0.0, diag=True)
+        ctx = crk.crk_create(tile_order=1)
+        t, dt_next, steps = 0.0, d["dt"], 0
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        while t < st["t_end"] - 1e-12:
+            d = crk.crk_step(ctx, pos, vel, mass, min(dt_next, st["t_end"] - t), diag=True)
+            t += d["dt"]
+            dt_next = d["dt_next"]
+            steps += 1
+        torch.cuda.synchronize(dev)
+        wall = time.perf_counter() - t0
+        probe = crk.crk_create()
+        crk.crk_build_cells(probe, pos)
+        V, _ = crk.crk_volumes(probe)
+        p = pos.cpu().numpy().astype(np.float64)
+        v = vel.cpu().numpy().astype(np.float64)
+        rho = st["mass"].astype(np.float64) / V.cpu().numpy().astype(np.float64)
+        P = (st["gamma"] - 1.0) * rho * v[:, 3]
+        sel = p[:, 0] < 0.5
+        parts[n] = (p[sel, 0], {q: a[sel] for q, a in (("rho", rho), ("v", v[:, 0]), ("P", P), ("u", v[:, 3]))})
+        runs[n] = {"N": len(p), "N_x": "%d+%d" % (n // 4, n // 8), "steps": steps, "wall_s": wall,
+                   "ms_per_step": 1e3 * wall / steps, "max_transverse_v": float(np.abs(v[:, 1:3]).max())}
+        probe.close()
+        ctx.close()
+    # the finest run's profile: means over bins of its low-side lattice spacing, interpolated
+    nf = max(sides)
+    xf, qf = parts[nf]
+    nb = nf // 4
+    edges = np.linspace(0.0, 0.5, nb + 1)
+    i = np.clip(np.digitize(xf, edges) - 1, 0, nb - 1)
+    c = np.bincount(i, None, nb)
+    mid = 0.5 * (edges[1:] + edges[:-1])[c > 0]
+    ref = {q: (np.bincount(i, a, nb)[c > 0] / c[c > 0]) for q, a in qf.items()}
+    for n in sides[:-1]:
+        x, qs = parts[n]
+        runs[n]["L1_vs_finest"] = {q: float(np.mean(np.abs(a - np.interp(x, mid, ref[q])))) for q, a in qs.items()}
+    return {"workload": "Sod tube in the unit cube (interfaces at 1/4, 3/4; rho, P = 1 | 1/8), t = 0.075",
+            "runs": {str(k): v for k, v in runs.items()}}
+
+
 # --------------------------------------------------------------------- GPU arm
 
 def aggregate(times_ms, work, dist=None, device="cpu"):
@@ -615,6 +673,8 @@ def run_gpu(args):
             line["batched"] = batched_report(dev)
         if not args.no_time_bins and world == 1:
             line["time_bins"] = time_bins_report(dev)
+        if not args.no_sod and world == 1:
+            line["sod"] = sod_report(dev)
         if not args.no_cpu_baseline and world == 1:
             from oracle import crk as O
             p, dt, ns = calibrated_oracle(st, args.cpu_seconds, seed=2)
@@ -640,6 +700,7 @@ def main():
     ap.add_argument("--no-learned-h", action="store_true", help="skip the learned-h training and evaluation")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-boxes measurement")
     ap.add_argument("--no-time-bins", action="store_true", help="skip the hierarchical time-bin measurement")
+    ap.add_argument("--no-sod", action="store_true", help="skip the Sod shock-tube measurement")
     ap.add_argument("--no-autotune", action="store_true", help="keep the built-in pass variants")
     ap.add_argument("--tile-order", default="auto", choices=["auto", "0", "1", "2"],
                     help="particle order of the tiles: 0 Morton, 1 Hilbert, 2 bisection, auto = fastest")

@@ -173,6 +173,37 @@ def zeldovich(n_side: int = 128, seed: int = 4, seed_u: int = 5, contrast: float
     return out
 
 
+def sod(n_hi: int = 64) -> dict:
+    """Sod shock tube of the paper's Sec. 4 test, scaled into the periodic unit
+    cube: the paper's domain x in [0, 2) with interfaces at 0.5 and 1.5 becomes
+    x in [0, 1) with interfaces at 1/4 and 3/4 (lengths and times halved, the
+    paper's t = 0.15 is t = 0.075 here).  High state rho = P = 1 for x < 1/4 and
+    x >= 3/4, low state rho = P = 1/8 between (the same temperature), at rest;
+    a step-function start, which the paper reports gives results
+    indistinguishable from its smoothed interface.  Equal masses m = 1/n_hi^3:
+    the high state is a cubic lattice of spacing 1/n_hi, the low state one of
+    spacing 2/n_hi; h = 4 spacings; u = P/((gamma-1) rho) = 3/2 everywhere.
+    The isolated half x in [0, 1/2) holds one interface (high on the left)."""
+    n = int(n_hi)
+    if n % 8 or n < 32:
+        raise ValueError("n_hi must be a multiple of 8 and at least 32")
+    gamma = 5.0 / 3.0
+    hx = (np.concatenate([np.arange(n // 4), np.arange(3 * n // 4, n)]) + 0.5) / n
+    ht = (np.arange(n) + 0.5) / n
+    lx = 0.25 + (np.arange(n // 4) + 0.5) * 2.0 / n
+    lt = (np.arange(n // 2) + 0.5) * 2.0 / n
+    hi = np.stack(np.meshgrid(hx, ht, ht, indexing="ij"), -1).reshape(-1, 3)
+    lo = np.stack(np.meshgrid(lx, lt, lt, indexing="ij"), -1).reshape(-1, 3)
+    x = np.concatenate([hi, lo])
+    h = np.concatenate([np.full(len(hi), 4.0 / n), np.full(len(lo), 8.0 / n)])
+    vel = np.zeros((len(x), 3))
+    u = np.full(len(x), 1.0 / (gamma - 1.0) * 1.0)   # P/rho = 1 on both sides
+    st = pack(x, h, vel, u, 1.0 / n ** 3)
+    st.update({"t_end": 0.075, "x0": 0.25, "domain": (0.0, 0.5), "left": (1.0, 0.0, 1.0),
+               "right": (0.125, 0.0, 0.125), "gamma": gamma})
+    return st
+
+
 def sedov_boxes(nbox: int = 64, side_lo: int = 16, side_hi: int = 96, seed: int = 0) -> dict:
     """Independent Sedov boxes for the batched step: box b is sedov(side_b,
     seed=b) with side_b drawn uniformly from the integers side_lo..side_hi;

@@ -22,9 +22,12 @@ from . import build as _build
 # Constants stated in the paper: gamma = 5/3 (Sec. 1.1), n_h = 4 and N_res = 268
 # (Sec. 2.6), C_l = 2, C_q = 1, eps = 0.1 (Sec. 1.2), eta_crit = 1/n_h,
 # eta_fold = 0.2/n_h (Sec. 1.2), C_CFL = 0.25, zeta = 4 (Sec. 2.1).
+# The scale factor a and its rate adot (Sec. 1.1, comoving variables with
+# p = a^2 dx/dt) default to a static box, a = 1, adot = 0.
 PARAMS = dict(gamma=5.0 / 3.0, n_h=4.0, N_res=268.0, C_l=2.0, C_q=1.0, eps=0.1,
-              eta_crit=1.0 / 4.0, eta_fold=0.2 / 4.0, C_cfl=0.25, zeta=4.0)
-_ORDER = ["gamma", "n_h", "N_res", "C_l", "C_q", "eps", "eta_crit", "eta_fold", "C_cfl", "zeta"]
+              eta_crit=1.0 / 4.0, eta_fold=0.2 / 4.0, C_cfl=0.25, zeta=4.0, a=1.0, adot=0.0)
+_ORDER = ["gamma", "n_h", "N_res", "C_l", "C_q", "eps", "eta_crit", "eta_fold", "C_cfl", "zeta", "a", "adot"]
+IA, IADOT = 10, 11
 
 _LIB = None
 _f32p = np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")
@@ -176,8 +179,9 @@ def corrections(pos_h, V, k=None, targets=None, moments=False):
     return out
 
 
-def gradv(pos_h, V, vel, A, B, gA, gB, k=None, targets=None):
-    """P3: grad v (gv[i, alpha, beta] = d v^alpha / d x^beta), eq:gradv."""
+def gradv(pos_h, V, vel, A, B, gA, gB, k=None, targets=None, a=1.0):
+    """P3: grad v (gv[i, alpha, beta] = d v^alpha / d x^beta), eq:gradv, of the
+    peculiar velocity v = p / a (vel holds p)."""
     pos = _pos(pos_h)
     n = pos.shape[0]
     tp, nt, keep = _tg(targets)
@@ -185,7 +189,7 @@ def gradv(pos_h, V, vel, A, B, gA, gB, k=None, targets=None):
     c = lambda a: np.ascontiguousarray(a, np.float64)
     _check(load().orc_gradv(n, pos, _k(pos, k), tp, nt, c(V), c(vel), c(A), c(B), c(gA), c(gB), gv),
            "gradv")
-    return gv
+    return gv / a
 
 
 def forces(pos_h, vel, u, mass, V, A, B, gA, gB, gv, prm=None, k=None, targets=None):
@@ -250,7 +254,7 @@ def evaluate(state, prm=None, k=None, targets=None):
     vel, u = np.ascontiguousarray(vu[:, :3]), np.ascontiguousarray(vu[:, 3])
     p1 = volumes(pos, k)
     p2 = corrections(pos, p1["V"], k)
-    gv = gradv(pos, p1["V"], vel, p2["A"], p2["B"], p2["gA"], p2["gB"], k)
+    gv = gradv(pos, p1["V"], vel, p2["A"], p2["B"], p2["gA"], p2["gB"], k, a=prm[IA])
     p4 = forces(pos, vel, u, mass, p1["V"], p2["A"], p2["B"], p2["gA"], p2["gB"], gv, prm, k, targets)
     ev = dict(p1)
     ev.update(p2)
@@ -264,15 +268,17 @@ def evaluate(state, prm=None, k=None, targets=None):
 
 
 def cfl_dt(ev, prm=None):
-    """Per-particle time step of Sec. 2.1 (adot = 0, no gravity so r_soft -> inf):
-    v_max = max(v_sig, c_s, sqrt(zeta Q/rho), h_hat |tr grad v|),
-    dt_i = min(C_CFL h_hat / v_max, sqrt(h_hat / |a|))."""
+    """Per-particle time step of Sec. 2.1 (no gravity, so r_soft -> inf and
+    the total acceleration is the hydro one, (1/a^2) dp/dt):
+    v_max = max(v_sig, c_s, sqrt(zeta Q/rho), (h_hat/a) |tr grad v + 3 adot|),
+    dt_i = min(C_CFL h_hat / v_max, sqrt(h_hat / |a_tot|))."""
     prm = params() if prm is None else prm
+    sa, sadot = prm[IA], prm[IADOT]
     hh = ev["pos_h"][:, 3].astype(np.float64) / prm[1]
     csq = np.sqrt(prm[9] * ev["qmax"] / ev["rho"])
-    div = np.abs(np.trace(ev["gv"], axis1=1, axis2=2))
-    vmax = np.maximum.reduce([ev["vsig"], ev["cs"], csq, hh * div])
-    amag = np.sqrt((ev["acc"] ** 2).sum(axis=1))
+    div = np.abs(np.trace(ev["gv"], axis1=1, axis2=2) + 3.0 * sadot)
+    vmax = np.maximum.reduce([ev["vsig"], ev["cs"], csq, hh / sa * div])
+    amag = np.sqrt((ev["acc"] ** 2).sum(axis=1)) / (sa * sa)
     with np.errstate(divide="ignore"):
         dt_h = np.where(vmax > 0, prm[8] * hh / vmax, np.inf)
         dt_a = np.where(amag > 0, np.sqrt(hh / amag), np.inf)
@@ -319,7 +325,12 @@ def _wrap_f32(x):
 
 def kdk_step(state, ev=None, dt=None, prm=None, k=None, h_min=1e-6, h_max=0.3, dt_max=1.0):
     """One hydro step, eq:verletOP (Sec. 2.1) with predicted p_p, u_p and the
-    compatible energy of eq:compEng for each half kick; the rates of `ev` (the
+    compatible energy of eq:compEng for each half kick (in comoving variables:
+    the drift moves x by dt p_1/2 / a^2, and the energy kicks add the
+    expansion term -(adot/a)(3(gamma-1) + 2) u of eq:CosmoEngEqn, explicitly in
+    the u of the opening half kick and implicitly in the u of the closing one,
+    which together are the trapezoidal rule for it; a and adot are constant
+    over the step); the rates of `ev` (the
     evaluation at the state's positions) are reused for the first half kick.
     h advances by one eq:thacker update of the new evaluation, clamped to
     [h_min, h_max].  Positions, velocities and u are stored in FP32 between
@@ -334,16 +345,18 @@ def kdk_step(state, ev=None, dt=None, prm=None, k=None, h_min=1e-6, h_max=0.3, d
     vel, u = vu[:, :3], vu[:, 3]
     mass = np.asarray(state["mass"], np.float64)
     a0 = ev["acc"]
+    sa = prm[IA]
+    E = prm[IADOT] / sa * (3.0 * (prm[0] - 1.0) + 2.0)   # expansion term of eq:CosmoEngEqn
     p_half = vel + 0.5 * dt * a0
     du1 = compatible(ev["pos_h"], ev["vel"], ev["u"], mass, ev["V"], ev["A"], ev["B"], ev["gA"], ev["gB"],
                      ev["gv"], vel, p_half, prm, k)
-    u_half = u + 0.5 * dt * du1
+    u_half = u + 0.5 * dt * (du1 - E * u)                       # opening half: explicit in u
     p_p = p_half + 0.5 * dt * a0
-    u_p = u_half + 0.5 * dt * du1
+    u_p = (u_half + 0.5 * dt * du1) / (1.0 + 0.5 * dt * E)      # closing halves: implicit in u
     n = pos.shape[0]
     st1 = {"pos_h": np.empty((n, 4), np.float32), "vel_u": np.empty((n, 4), np.float32),
            "mass": np.asarray(state["mass"], np.float32)}
-    st1["pos_h"][:, :3] = _wrap_f32(pos[:, :3].astype(np.float64) + dt * p_half)
+    st1["pos_h"][:, :3] = _wrap_f32(pos[:, :3].astype(np.float64) + dt / (sa * sa) * p_half)
     st1["pos_h"][:, 3] = pos[:, 3]
     st1["vel_u"][:, :3] = p_p
     st1["vel_u"][:, 3] = u_p
@@ -351,7 +364,7 @@ def kdk_step(state, ev=None, dt=None, prm=None, k=None, h_min=1e-6, h_max=0.3, d
     p1 = p_half + 0.5 * dt * ev1["acc"]
     du2 = compatible(ev1["pos_h"], ev1["vel"], ev1["u"], mass, ev1["V"], ev1["A"], ev1["B"], ev1["gA"],
                      ev1["gB"], ev1["gv"], p_half, p1, prm, k)
-    u1 = u_half + 0.5 * dt * du2
+    u1 = (u_half + 0.5 * dt * du2) / (1.0 + 0.5 * dt * E)
     h1 = np.clip(thacker(pos[:, 3].astype(np.float64), ev1["N"], prm), h_min, h_max)
     out = {"pos_h": st1["pos_h"].copy(), "vel_u": np.empty((n, 4), np.float32), "mass": st1["mass"]}
     out["pos_h"][:, 3] = h1

@@ -50,7 +50,7 @@ static const double TWO32 = 4294967296.0;
 
 /* parameter vector layout (double prm[]) */
 enum { P_GAMMA = 0, P_NH, P_NRES, P_CL, P_CQ, P_EPS, P_ETACRIT, P_ETAFOLD,
-       P_CCFL, P_ZETA, P_COUNT };
+       P_CCFL, P_ZETA, P_A, P_ADOT, P_COUNT };
 
 /* ---------------------------------------------------------------- system */
 
@@ -634,9 +634,15 @@ static double phi_vanleer(double a, double b) {
 }
 
 /* Pairwise quantities of one (i,j) in the pair set, eq:mom, eq:eng, eq:visc,
- * eq:mu, eq:hatvi, eq:phi..eq:phiad (a = 1, adot = 0, natural units).
- * F = 1/2 V_i V_j (P~_i + P~_j)(grad W^R_ji - grad W^R_ij); also returns
- * D = grad W^R_ji - grad W^R_ij, P~_j and Q_i of this pair. */
+ * eq:mu, eq:hatvi, eq:phi..eq:phiad, in comoving variables with scale factor a
+ * and its rate adot (prm[P_A], prm[P_ADOT]): vel holds p = a^2 dx/dt = a v, gv
+ * the gradient of the peculiar velocity v = p / a.
+ * F = m_i dp_ij/dt = a^2/2 V_i V_j (P~_i + P~_j)(grad W^R_ji - grad W^R_ij);
+ * u^_ij = (p_i - p_j)/a - 1/2 phi (grad v_i + grad v_j).x_ij + adot x_ij (the
+ * projection acts on the peculiar part only), mu_i = min(0, (h^_i/a) u^.x /
+ * (r^2 + h^_i^2 eps^2)); the approach speed of the signal velocity takes
+ * dx/dt_ij + (adot/a) x_ij.  Also returns D = grad W^R_ji - grad W^R_ij, P~_j
+ * and Q_i of this pair. */
 static void pair_force(const sys_t *s, const fstate_t *f, int i, int j,
                        double F[3], double D[3], double *Ptj, double *Qi_out, double *xr_out) {
     const double *prm = f->prm;
@@ -668,39 +674,42 @@ static void pair_force(const sys_t *s, const fstate_t *f, int i, int j,
     double phiad = (eta < ec) ? exp(-((eta - ec) / ef) * ((eta - ec) / ef)) : 1.0;
     double phi = phiVL * phiad;
 
-    /* midpoint-projected velocity difference, eq:hatvi (adot = 0) */
+    /* midpoint-projected proper velocity difference, eq:hatvi */
+    const double sa = prm[P_A], sadot = prm[P_ADOT];
     double uh[3];
     for (int a = 0; a < 3; a++) {
         double proj = 0.0;
         for (int b = 0; b < 3; b++) proj += (Gi[3 * a + b] + Gj[3 * a + b]) * x[b];
-        uh[a] = (f->vel[3 * i + a] - f->vel[3 * j + a]) - 0.5 * phi * proj;
+        uh[a] = (f->vel[3 * i + a] - f->vel[3 * j + a]) / sa - 0.5 * phi * proj + sadot * x[a];
     }
     double ux = dot3(uh, x);
 
     /* viscosity, eq:visc / eq:mu with R7 */
     double eps = prm[P_EPS], Cl = prm[P_CL], Cq = prm[P_CQ], nh = prm[P_NH];
     double hh_i = s->h[i] / nh, hh_j = s->h[j] / nh;
-    double mu_i = hh_i * ux / (r * r + hh_i * hh_i * eps * eps);
-    double mu_j = hh_j * ux / (r * r + hh_j * hh_j * eps * eps);
+    double mu_i = (hh_i / sa) * ux / (r * r + hh_i * hh_i * eps * eps);
+    double mu_j = (hh_j / sa) * ux / (r * r + hh_j * hh_j * eps * eps);
     if (mu_i > 0.0) mu_i = 0.0;
     if (mu_j > 0.0) mu_j = 0.0;
     double Q_i = rho_i * (-Cl * c_i * mu_i + Cq * mu_i * mu_i);
     double Q_j = rho_j * (-Cl * c_j * mu_j + Cq * mu_j * mu_j);
 
     double Pt_i = P_i + Q_i, Pt_j = P_j + Q_j;
-    double c = 0.5 * f->V[i] * f->V[j] * (Pt_i + Pt_j);
+    double c = 0.5 * sa * sa * f->V[i] * f->V[j] * (Pt_i + Pt_j);
     for (int a = 0; a < 3; a++) F[a] = c * D[a];
     *Ptj = Pt_j;
     *Qi_out = Q_i;
-    /* approach speed for the signal velocity (R9) */
+    /* approach speed for the signal velocity (R9): (dx/dt_ij + (adot/a) x_ij).x_ij / r */
     double vx = 0.0;
     for (int a = 0; a < 3; a++) vx += (f->vel[3 * i + a] - f->vel[3 * j + a]) * x[a];
+    vx = vx / (sa * sa) + (sadot / sa) * r * r;
     *xr_out = (r > 0.0 && vx < 0.0) ? -vx / r : 0.0;
 }
 
 /* P4 -- eq:mom (momentum), eq:eng (direct energy rate) with P -> P + Q:
- *   acc_i  = (1/m_i) sum_j F_ij,
- *   dudt_i = (1/m_i) sum_j 1/2 V_i V_j P~_j (v_j - v_i).(grad W^R_ji - grad W^R_ij),
+ *   acc_i  = dp_i/dt = (1/m_i) sum_j F_ij,
+ *   dudt_i = (1/m_i) sum_j 1/(2 a^4) V_i V_j P~_j (p_j - p_i).(grad W^R_ji - grad W^R_ij)
+ *            (eq:eng with dx/dt = p / a^2),
  *   vsig_i = max_j approach speed (R9), qmax_i = max_j Q_i of the pair,
  *   fscale_i = (1/m_i) sum_j |F_ij| (scale of the cancelling pair sum, optional). */
 int orc_forces(int n, const float *pos4, int k, const int *tgt, int ntgt, const double *prm,
@@ -740,8 +749,9 @@ int orc_forces(int n, const float *pos4, int k, const int *tgt, int ntgt, const 
                 if (ap > vs) vs = ap;
                 if (Qi > qm) qm = Qi;
             }
+            const double a4 = prm[P_A] * prm[P_A] * prm[P_A] * prm[P_A];
             for (int a = 0; a < 3; a++) acc[3 * i + a] = Fs[a] / mass[i];
-            dudt[i] = du / mass[i];
+            dudt[i] = du / (a4 * mass[i]);
             vsig[i] = vs;
             if (qmax) qmax[i] = qm;
             if (fscale) fscale[i] = fa / mass[i];
@@ -764,9 +774,9 @@ static double f_partition(double dE, double si, double sj) {
     return (take_min ? lo : hi) / sum;
 }
 
-/* P5 -- compatible energy, eq:compEng .. eq:fij (a = 1, adot = 0):
- *   a_ij = F_ij / m_i, Delta u_ij = f_ij/2 (v_j + v'_j - v_i - v'_i).a_ij,
- *   Delta E_ij = 1/2 (v_j + v'_j - v_i - v'_i).F_ij (R10), s = P / rho^gamma,
+/* P5 -- compatible energy, eq:compEng2 .. eq:fij:
+ *   dp_ij/dt = F_ij / m_i, Delta u_ij = f_ij/(2 a^4) (p_j + p'_j - p_i - p'_i).dp_ij/dt,
+ *   Delta E_ij = 1/2 (p_j + p'_j - p_i - p'_i).F_ij (R10), s = P / rho^gamma,
  * with F_ij from the evaluation state (vel, u) and (vb, va) the velocities
  * before and after the kick.  du[i] = sum_j Delta u_ij (multiply by the kick's
  * duration for the energy change). */
@@ -807,7 +817,7 @@ int orc_compatible(int n, const float *pos4, int k, const int *tgt, int ntgt, co
                 double fij = f_partition(dE, s_i, s_j);
                 acc += fij * 0.5 * w / mass[i];
             }
-            du[i] = acc;
+            du[i] = acc / (prm[P_A] * prm[P_A] * prm[P_A] * prm[P_A]);
         }
         free(l.v);
     }

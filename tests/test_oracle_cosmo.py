@@ -1,0 +1,156 @@
+"""Pins of the comoving (expanding-box) factors of the oracle (CRK-HACC Sec.
+1.1-1.2: p = a^2 dx/dt, eq:mom with a^2, eq:eng with 1/(2a^2) and dx/dt =
+p/a^2, eq:compEng2 with 1/(2a^4), eq:mu with h^/a and the Hubble flow adot x
+in u^, the signal velocity with (adot/a) x, the expansion term of
+eq:CosmoEngEqn, the drift p/a^2, and the time-step criteria), against what the
+mathematics fixes:
+
+* a lattice at rest in a contracting box (adot < 0): no force, and the
+  viscous pressure and signal velocity of its pairs in closed form from the
+  Hubble flow alone; in an expanding box both vanish;
+* with the viscosity off, the force scales as a^2, the direct energy rate as
+  1/a^4 and the compatible energy as 1/a^2 at fixed state;
+* the compatible kicks keep sum m (p^2/(2a^4) + u) fixed (adot = 0);
+* expansion cooling converges to u0 exp(-(adot/a)(3(gamma-1)+2) t) at second
+  order in the step;
+* a uniformly moving lattice drifts by dt p / a^2;
+* the time step of a lattice at rest is set by (h^/a) 3|adot| when that wins.
+"""
+import numpy as np
+
+from oracle import crk as O
+from paper_2202_02840_gb300 import inputs
+
+
+def lattice_state(side=16, u=1.0):
+    x = inputs.lattice(side)
+    st = inputs.pack(x, 4.0 / side, np.zeros((len(x), 3)), u, 1.0 / side ** 3)
+    return st
+
+
+def eval_with(st, **kw):
+    prm = O.params(**kw)
+    return O.evaluate(st, prm), prm
+
+
+def test_lattice_at_rest_in_a_contracting_box():
+    side = 16
+    st = lattice_state(side)
+    a, adot = 0.7, -0.2
+    ev, prm = eval_with(st, a=a, adot=adot)
+    assert np.max(np.abs(ev["acc"])) < 1e-10 and np.max(np.abs(ev["dudt"])) < 1e-12
+    # farthest pair-set neighbour on the lattice (h = 4 spacings, r < h)
+    d = np.arange(-4, 5)
+    g = np.stack(np.meshgrid(d, d, d, indexing="ij"), -1).reshape(-1, 3)
+    r = np.sqrt((g * g).sum(1)) / side
+    rmax = r[(r < 4.0 / side)].max()
+    assert np.allclose(ev["vsig"], -adot / a * rmax, rtol=1e-12)
+    hh = 4.0 / side / 4.0
+    mu = hh / a * adot * rmax ** 2 / (rmax ** 2 + hh * hh * 0.01)
+    rho, cs = ev["rho"], ev["cs"]          # the SPH density of the lattice (m / V) and its sound speed
+    Q = rho * (-2.0 * cs * mu + 1.0 * mu * mu)
+    assert np.allclose(ev["qmax"], Q, rtol=1e-10)
+    ev2, _ = eval_with(st, a=a, adot=+0.2)
+    assert np.max(ev2["qmax"]) == 0.0 and np.max(ev2["vsig"]) == 0.0
+
+
+def test_force_and_energy_rates_scale_with_a():
+    st = inputs.uniform(16)
+    e1, _ = eval_with(st, C_l=0.0, C_q=0.0)
+    a = 0.6
+    ea, prm = eval_with(st, C_l=0.0, C_q=0.0, a=a)
+    assert np.allclose(ea["acc"], a * a * e1["acc"], rtol=1e-12, atol=1e-12 * np.abs(e1["acc"]).max())
+    assert np.allclose(ea["dudt"], e1["dudt"] / a ** 4, rtol=1e-12, atol=1e-12 * np.abs(e1["dudt"]).max())
+    vel = st["vel_u"][:, :3].astype(np.float64)
+    kick = vel + 1e-3 * ea["acc"]
+    args = lambda ev: (ev["pos_h"], ev["vel"], ev["u"], ev["mass"], ev["V"], ev["A"], ev["B"], ev["gA"], ev["gB"],
+                       ev["gv"])
+    c1 = O.compatible(*args(e1), vel, kick, O.params(C_l=0.0, C_q=0.0))
+    ca = O.compatible(*args(ea), vel, kick, prm)
+    assert np.allclose(ca, c1 / a ** 2, rtol=1e-10, atol=1e-12 * np.abs(c1).max())
+
+
+def test_compatible_kicks_conserve_the_comoving_energy():
+    st = inputs.uniform(16)
+    st["vel_u"][:, :3] *= 20.0                       # strong flows, viscosity on
+    a = 0.55
+    prm = O.params(a=a)
+    m = st["mass"].astype(np.float64)
+    E = lambda s: float((m * (0.5 * (s["vel_u"][:, :3].astype(np.float64) ** 2).sum(1) / a ** 4
+                              + s["vel_u"][:, 3].astype(np.float64))).sum())
+    ev = O.evaluate(st, prm)
+    dt = 0.5 * float(O.cfl_dt(ev, prm).min())
+    out, _, _ = O.kdk_step(st, ev=ev, dt=dt, prm=prm)
+    kin = float((m * 0.5 * (st["vel_u"][:, :3].astype(np.float64) ** 2).sum(1) / a ** 4).sum())
+    dE = abs(E(out) - E(st))
+    print("comoving energy change", dE / E(st), "kinetic", kin / E(st))
+    assert dE < 1e-6 * E(st)
+    # the same step with the compatible energy scaled as in a static box fails it
+    assert kin > 1e-3 * E(st)
+
+
+def test_expansion_cooling_converges_to_the_exponential():
+    st = lattice_state(16, u=1.0)
+    a, adot = 0.8, 0.4
+    prm = O.params(a=a, adot=adot)
+    E = adot / a * (3.0 * (5.0 / 3.0 - 1.0) + 2.0)
+    T = 0.5
+    errs = []
+    for N in (4, 8):
+        s, ev = st, None
+        for _ in range(N):
+            s, ev, _ = O.kdk_step(s, ev=ev, dt=T / N, prm=prm)
+        u = s["vel_u"][:, 3].astype(np.float64)
+        assert np.allclose(u, u[0], rtol=0, atol=1e-6)
+        errs.append(abs(u.mean() - np.exp(-E * T)))
+        assert np.max(np.abs(s["pos_h"][:, :3] - st["pos_h"][:, :3])) == 0.0
+    print("cooling errors", errs)
+    assert errs[1] < 0.3 * errs[0] and errs[0] < 0.05
+
+
+def test_uniform_motion_drifts_by_p_over_a_squared():
+    side = 16
+    st = lattice_state(side)
+    p = np.array([0.3, -0.2, 0.1])
+    st["vel_u"][:, :3] = p.astype(np.float32)
+    a = 0.5
+    prm = O.params(a=a)
+    dt = 1e-3
+    out, ev, _ = O.kdk_step(st, dt=dt, prm=prm)
+    dx = out["pos_h"][:, :3].astype(np.float64) - st["pos_h"][:, :3]
+    dx -= np.round(dx)
+    assert np.allclose(dx, dt * p.astype(np.float32).astype(np.float64) / a ** 2, atol=1e-7)
+    assert np.allclose(out["vel_u"][:, :3], st["vel_u"][:, :3], atol=1e-9)
+
+
+def test_time_step_of_a_lattice_at_rest_uses_the_hubble_divergence():
+    side = 16
+    st = lattice_state(side, u=1e-8)
+    a, adot = 0.9, 2.0
+    prm = O.params(a=a, adot=adot)
+    ev = O.evaluate(st, prm)
+    hh = 4.0 / side / 4.0
+    want = 0.25 * hh / (hh / a * 3.0 * adot)
+    assert np.allclose(O.cfl_dt(ev, prm), want, rtol=1e-12)
+
+
+def test_signal_velocity_by_brute_force():
+    """v_sig,i = max_j max(0, -(dx/dt_ij + (adot/a) x_ij).x_ij / r) over the
+    pair set, dx/dt = p / a^2, recomputed pair by pair."""
+    st = inputs.uniform(16)
+    st["vel_u"][:, :3] *= 10.0
+    a, adot = 0.5, -0.05
+    ev, prm = eval_with(st, a=a, adot=adot)
+    cnt, lists = O.neighbours(st["pos_h"], mode=1)
+    i = np.repeat(np.arange(len(cnt)), cnt)
+    j = lists
+    q, _ = O.fixed_point(st["pos_h"])
+    dq = (q[i].astype(np.int64) - q[j].astype(np.int64))
+    dq = (dq + (1 << 31)) % (1 << 32) - (1 << 31)
+    x = dq * 2.0 ** -32
+    r = np.sqrt((x * x).sum(1))
+    p = st["vel_u"][:, :3].astype(np.float64)
+    app = -(((p[i] - p[j]) / a ** 2 + adot / a * x) * x).sum(1) / r
+    want = np.zeros(len(cnt))
+    np.maximum.at(want, i, np.maximum(app, 0.0))
+    assert np.allclose(ev["vsig"], want, rtol=1e-12, atol=0)

@@ -77,6 +77,13 @@ typedef struct {
     double h_min;     /* lower clamp of the evolved h (box units) */
     double h_max;     /* upper clamp of the evolved h (< 1/3) */
     double dt_max;    /* cap of the CFL time step */
+    double a;         /* cosmic scale factor (Sec. 1.1); 1 = a static box.  The state's
+                         velocity column then holds p = a^2 dx/dt = a v (v peculiar) */
+    double adot;      /* da/dt; 0 = a static box.  a and adot enter eq:mom (a^2), eq:eng
+                         (1/(2a^2), dx/dt = p/a^2), eq:compEng2 (1/(2a^4)), eq:mu (h^/a,
+                         u^ = v^ + adot x), the signal velocity ((adot/a) x), eq:gradv (of
+                         v = p/a), the drift (p/a^2), the expansion term of eq:CosmoEngEqn
+                         and the time-step criteria; crk_set_expansion changes them */
     int precision;    /* 0 = plain FP32 (FP32 sums, FP32 3x3 inverse);
                          1 = mixed (default): FP32 pair sums, compensated momentum
                              and energy accumulation, moments formed and the 3x3
@@ -241,6 +248,12 @@ int crk_steps_batched(crk_ctx *ctx, int n, int nbox, const int32_t *box_start, f
 /* Graphs captured, graph launches, and replay runs redone eagerly after a
  * capacity overflow, by crk_steps since crk_create (each may be NULL). */
 int crk_graph_stats(crk_ctx *ctx, long long *captures, long long *replays, long long *recoveries);
+
+/* Set the scale factor a > 0 and its rate adot for the following calls (see
+ * crk_params.a): a step uses them as constants over its duration (the caller
+ * passes the values of the step's midpoint).  The cached rates of the last
+ * evaluation were computed with the previous values. */
+int crk_set_expansion(crk_ctx *ctx, double a, double adot);
 
 /* Forget the cached rates so that the next crk_step evaluates afresh. */
 int crk_reset_rates(crk_ctx *ctx);

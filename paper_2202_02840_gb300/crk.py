@@ -28,7 +28,7 @@ class CrkError(RuntimeError):
 class crk_params(ctypes.Structure):
     _fields_ = [(k, ctypes.c_double) for k in
                 ("gamma", "n_h", "N_res", "C_l", "C_q", "eps", "eta_crit", "eta_fold", "C_cfl", "zeta",
-                 "h_min", "h_max", "dt_max")] + [
+                 "h_min", "h_max", "dt_max", "a", "adot")] + [
         ("precision", ctypes.c_int), ("kmax", ctypes.c_int), ("tile_order", ctypes.c_int),
         ("reserved", ctypes.c_int * 5)]
 
@@ -74,6 +74,7 @@ def lib():
         L.crk_compatible.argtypes = [_vp] + [_vp] * 11 + [_vp]
         L.crk_step.argtypes = [_vp, _ci, _vp, _vp, _vp, ctypes.c_double, ctypes.POINTER(crk_diag), _vp]
         L.crk_reset_rates.argtypes = [_vp]
+        L.crk_set_expansion.argtypes = [_vp, ctypes.c_double, ctypes.c_double]
         L.crk_order.argtypes = [_vp, _vp, _vp]
         L.crk_cycle.argtypes = [_vp, _ci, _vp, _vp, _vp, ctypes.c_double, _ci, _ci, ctypes.POINTER(crk_htb_stats),
                                 _vp]
@@ -307,6 +308,11 @@ def crk_htb_levels(ctx, pos_h, dt, Delta, L, f_l=2, stream=None):
                                    _stream(stream)))
     ctx.n = n
     return level, int(unres.value)
+
+
+def crk_set_expansion(ctx, a, adot):
+    """Scale factor and its rate for the following calls (comoving variables)."""
+    ctx.check(lib().crk_set_expansion(ctx.handle, float(a), float(adot)))
 
 
 def crk_reset_rates(ctx):

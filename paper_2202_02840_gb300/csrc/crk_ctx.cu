@@ -411,6 +411,8 @@ extern "C" int crk_default_params(crk_params *p) {
     p->h_min = 1e-6;
     p->h_max = 0.3;
     p->dt_max = 1.0;
+    p->a = 1.0;
+    p->adot = 0.0;
     p->precision = 1;
     p->kmax = 7;
     return CRK_OK;
@@ -424,7 +426,8 @@ extern "C" int crk_create(const crk_params *p, crk_ctx **out) {
     if (!(prm.gamma > 1.0) || !(prm.n_h > 0) || !(prm.N_res > 0) || !(prm.eta_fold > 0) ||
         !(prm.h_max > 0 && prm.h_max < 1.0 / 3.0) || !(prm.h_min > 0 && prm.h_min < prm.h_max) ||
         prm.kmax < 1 || prm.kmax > 7 || prm.precision < 0 || prm.precision > 2 || !(prm.dt_max > 0) ||
-        prm.tile_order < 0 || prm.tile_order > 2)
+        prm.tile_order < 0 || prm.tile_order > 2 || !(prm.a > 0.0) || !(prm.a < 1e30) ||
+        !(prm.adot > -1e30 && prm.adot < 1e30))
         return CRK_EINVAL;
     crk_ctx *ctx = new (std::nothrow) crk_ctx();
     if (!ctx) return CRK_ENOMEM;

@@ -25,6 +25,10 @@ struct FParams {
     float eps2;            // eps^2
     float Cl, Cq;
     float eta_crit, inv_eta_fold;
+    // comoving variables (Sec. 1.1): scale factor a, adot = da/dt; all 1 / 0 in a static box
+    float half_a2;         // a^2 / 2 (eq:mom)
+    float inv_a, inv_a2, inv_a4;
+    float adot, adot_a;    // adot, adot / a
 };
 
 // Per-particle record of the pair-set passes: 160 bytes, five 32-byte sectors
@@ -112,7 +116,7 @@ __device__ __forceinline__ void kern(const FRec &a, float r, bool in, float &W, 
 }
 
 struct PairOut {
-    float F[3];    // force on a from b, 1/2 V_a V_b (P~_a + P~_b)(grad W^R_ba - grad W^R_ab)
+    float F[3];    // m_a dp_ab/dt = a^2/2 V_a V_b (P~_a + P~_b)(grad W^R_ba - grad W^R_ab)
     float D[3];    // grad W^R_ba - grad W^R_ab
     float Pt_b;    // P_b + Q_b of this pair
     float Q_a;     // Q_a of this pair
@@ -146,18 +150,20 @@ __device__ __forceinline__ void pair_force(const FRec &a, const FRec &b, const f
         float e = (eta - fp.eta_crit) * fp.inv_eta_fold;
         phi *= __expf(-e * e);
     }
-    // projected velocity difference along x, eq:hatvi (adot = 0):
-    // u_ab . x = (v_a - v_b) . x - phi/2 (x . grad v_a . x + x . grad v_b . x)
+    // projected proper velocity difference along x, eq:hatvi (the state holds
+    // p = a v; the projection acts on the peculiar part only):
+    // u_ab . x = (p_a - p_b) . x / a - phi/2 (x . grad v_a . x + x . grad v_b . x) + adot r^2
     float vx = fmaf(a.w3.x - b.w3.x, x[0], fmaf(a.w3.y - b.w3.y, x[1], (a.w3.z - b.w3.z) * x[2]));
-    float ux = fmaf(-0.5f * phi, qs, vx);
-    // eq:mu, eq:visc
+    float ux = fmaf(fp.adot, r2, fmaf(-0.5f * phi, qs, vx * fp.inv_a));
+    // eq:mu (h^/a), eq:visc
     float hha = a.w1.z, hhb = b.w1.z;
-    float mua = fminf(FDIV(hha * ux, fmaf(hha * hha, fp.eps2, r2)), 0.f);
-    float mub = fminf(FDIV(hhb * ux, fmaf(hhb * hhb, fp.eps2, r2)), 0.f);
+    float uxa = ux * fp.inv_a;
+    float mua = fminf(FDIV(hha * uxa, fmaf(hha * hha, fp.eps2, r2)), 0.f);
+    float mub = fminf(FDIV(hhb * uxa, fmaf(hhb * hhb, fp.eps2, r2)), 0.f);
     float Qa = a.w2.y * mua * fmaf(fp.Cq, mua, -fp.Cl * a.w2.z);
     float Qb = b.w2.y * mub * fmaf(fp.Cq, mub, -fp.Cl * b.w2.z);
     float Pta = a.w2.x + Qa, Ptb = b.w2.x + Qb;
-    float cF = 0.5f * (a.w1.w * b.w1.w) * (Pta + Ptb);
+    float cF = fp.half_a2 * (a.w1.w * b.w1.w) * (Pta + Ptb);
 #pragma unroll
     for (int g = 0; g < 3; g++) o.F[g] = cF * o.D[g];
     o.Pt_b = Ptb;
@@ -254,13 +260,16 @@ struct P4 {
         for (int g = 0; g < 3; g++) s.F[g].add(o.F[g]);
         float wd = fmaf(dv[0], o.D[0], fmaf(dv[1], o.D[1], dv[2] * o.D[2]));
         s.du.add(0.5f * (s.me.w1.w * r.w1.w) * o.Pt_b * wd);
-        float vx = -fmaf(dv[0], x[0], fmaf(dv[1], x[1], dv[2] * x[2]));   // (v_i - v_j).x_ij
+        // (dx_i/dt - dx_j/dt + (adot/a) x_ij).x_ij with dx/dt = p / a^2
+        float vx = fmaf(p.fp.adot_a, d.r2, -fmaf(dv[0], x[0], fmaf(dv[1], x[1], dv[2] * x[2])) * p.fp.inv_a2);
         if (vx < 0.f && d.r > 0.f) s.vsig = fmaxf(s.vsig, FDIV(-vx, d.r));
         s.qmax = fmaxf(s.qmax, o.Q_a);
     }
     __device__ static void finish(IState &s, int i, const Params &p) {
         float im = 1.f / s.m;
-        p.acc[i] = make_float4(s.F[0].value() * im, s.F[1].value() * im, s.F[2].value() * im, s.du.value() * im);
+        // dp/dt, and du/dt of eq:eng: 1/(2a^2) V V P~ (dx_j/dt - dx_i/dt).D with dx/dt = p / a^2
+        p.acc[i] = make_float4(s.F[0].value() * im, s.F[1].value() * im, s.F[2].value() * im,
+                               s.du.value() * im * p.fp.inv_a4);
         p.vq[i] = make_float2(s.vsig, s.qmax);
     }
 };
@@ -282,6 +291,7 @@ struct P5 {
         const float4 *Fst;
         const float *mass;
         float *du;
+        float inv_a4;
     };
     struct IState {
         float4 me;
@@ -314,7 +324,8 @@ struct P5 {
         }
         s.du.add(0.5f * f * w);
     }
-    __device__ static void finish(IState &s, int i, const Params &p) { p.du[i] = s.du.value() / s.m; }
+    // eq:compEng2: 1/(2 a^4) (p_j + p'_j - p_i - p'_i) . dp_ij/dt
+    __device__ static void finish(IState &s, int i, const Params &p) { p.du[i] = s.du.value() / s.m * p.inv_a4; }
 };
 
 static FParams fparams(const crk_params &c) {
@@ -327,6 +338,12 @@ static FParams fparams(const crk_params &c) {
     f.Cq = (float)c.C_q;
     f.eta_crit = (float)c.eta_crit;
     f.inv_eta_fold = (float)(1.0 / c.eta_fold);
+    f.half_a2 = (float)(0.5 * c.a * c.a);
+    f.inv_a = (float)(1.0 / c.a);
+    f.inv_a2 = (float)(1.0 / (c.a * c.a));
+    f.inv_a4 = (float)(1.0 / (c.a * c.a * c.a * c.a));
+    f.adot = (float)c.adot;
+    f.adot_a = (float)(c.adot / c.a);
     return f;
 }
 
@@ -363,10 +380,12 @@ int run_compatible(crk_ctx *ctx, cudaStream_t s) {
     ++ctx->launches;
     CRK_LAUNCH_CHECK(ctx, "kick sums");
     if (ctx->p.precision >= 1) {
-        typename P5<true>::Params p{ctx->sig, ctx->Fst, ctx->mass, ctx->du};
+        typename P5<true>::Params p{ctx->sig, ctx->Fst, ctx->mass, ctx->du,
+                                    (float)(1.0 / (ctx->p.a * ctx->p.a * ctx->p.a * ctx->p.a))};
         return launch_lpass<P5<true>, 8>(ctx, PROF_P5, p, s, "P5 compatible energy");
     }
-    typename P5<false>::Params p{ctx->sig, ctx->Fst, ctx->mass, ctx->du};
+    typename P5<false>::Params p{ctx->sig, ctx->Fst, ctx->mass, ctx->du,
+                                 (float)(1.0 / (ctx->p.a * ctx->p.a * ctx->p.a * ctx->p.a))};
     return launch_lpass<P5<false>, 8>(ctx, PROF_P5, p, s, "P5 compatible energy");
 }
 

@@ -300,6 +300,7 @@ struct P3 {
         const float4 *vel;
         const CorrRec *corr;
         GvRec *gv;
+        float inv_a;        // the state holds p = a v: grad v = (1/a) grad p
     };
     struct IState {
         uint4 q;
@@ -368,9 +369,10 @@ struct P3 {
     }
     __device__ static void finish(IState &s, int i, const Params &p) {
         GvRec g;
-        g.g0 = make_float4(s.acc[0].value(), s.acc[1].value(), s.acc[2].value(), s.acc[3].value());
-        g.g1 = make_float4(s.acc[4].value(), s.acc[5].value(), s.acc[6].value(), s.acc[7].value());
-        g.g2 = make_float4(s.acc[8].value(), 0.f, 0.f, 0.f);
+        const float k = p.inv_a;
+        g.g0 = make_float4(s.acc[0].value() * k, s.acc[1].value() * k, s.acc[2].value() * k, s.acc[3].value() * k);
+        g.g1 = make_float4(s.acc[4].value() * k, s.acc[5].value() * k, s.acc[6].value() * k, s.acc[7].value() * k);
+        g.g2 = make_float4(s.acc[8].value() * k, 0.f, 0.f, 0.f);
         p.gv[i] = g;
     }
 };
@@ -392,10 +394,10 @@ int run_corrections(crk_ctx *ctx, bool with_gradv, cudaStream_t s) {
     }
     if (rc || !with_gradv) return rc;
     if (ctx->p.precision == 2) {
-        P3<true>::Params p3{ctx->q4, ctx->qV, ctx->hs, ctx->vel, ctx->corr, ctx->gv};
+        P3<true>::Params p3{ctx->q4, ctx->qV, ctx->hs, ctx->vel, ctx->corr, ctx->gv, (float)(1.0 / ctx->p.a)};
         return launch_lpass<P3<true>, 4>(ctx, PROF_P3, p3, s, "P3 grad v");
     }
-    P3<false>::Params p3{ctx->q4, ctx->qV, ctx->hs, ctx->vel, ctx->corr, ctx->gv};
+    P3<false>::Params p3{ctx->q4, ctx->qV, ctx->hs, ctx->vel, ctx->corr, ctx->gv, (float)(1.0 / ctx->p.a)};
     return launch_lpass<P3<false>, 4>(ctx, PROF_P3, p3, s, "P3 grad v");
 }
 

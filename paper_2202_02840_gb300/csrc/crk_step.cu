@@ -25,6 +25,9 @@ static float bits_to_float(uint32_t b) {
 struct StepConsts {
     float gamma, gm1, inv_nh, C_cfl, zeta, N_res, h_min, h_max;
     double dt_max;
+    // comoving variables (1, 1, 0, 0 in a static box)
+    float inv_a, inv_a2, adot;
+    float E;   // (adot/a)(3(gamma-1) + 2): expansion term of eq:CosmoEngEqn
 };
 
 static StepConsts step_consts(const crk_params &p) {
@@ -38,12 +41,17 @@ static StepConsts step_consts(const crk_params &p) {
     c.h_min = (float)p.h_min;
     c.h_max = (float)p.h_max;
     c.dt_max = p.dt_max;
+    c.inv_a = (float)(1.0 / p.a);
+    c.inv_a2 = (float)(1.0 / (p.a * p.a));
+    c.adot = (float)p.adot;
+    c.E = (float)(p.adot / p.a * (3.0 * (p.gamma - 1.0) + 2.0));
     return c;
 }
 
-// Per-particle time step (Sec. 2.1, adot = 0, pure hydro so r_soft -> inf):
-// v_max = max(v_sig, c_s, sqrt(zeta Q/rho), h_hat |tr grad v|),
-// dt_i = min(C_CFL h_hat / v_max, sqrt(h_hat / |a|)); global min as float bits.
+// Per-particle time step (Sec. 2.1, pure hydro so r_soft -> inf and the total
+// acceleration is (1/a^2) dp/dt):
+// v_max = max(v_sig, c_s, sqrt(zeta Q/rho), (h_hat/a) |tr grad v + 3 adot|),
+// dt_i = min(C_CFL h_hat / v_max, sqrt(h_hat / |a_tot|)); global min as float bits.
 __global__ void k_cfl(int n, StepConsts c, const float *__restrict__ hs, const float *__restrict__ V,
                       const float *__restrict__ mass, const float4 *__restrict__ vel,
                       const float4 *__restrict__ acc, const float2 *__restrict__ vq,
@@ -59,11 +67,11 @@ __global__ void k_cfl(int n, StepConsts c, const float *__restrict__ hs, const f
         float2 q = vq[s];
         float csq = sqrtf(fmaxf(c.zeta * q.y / rho, 0.f));
         GvRec g = gv[s];
-        float div = fabsf(g.g0.x + g.g1.x + g.g2.x);
+        float div = fabsf(fmaf(3.f, c.adot, g.g0.x + g.g1.x + g.g2.x)) * c.inv_a;
         float vmax = fmaxf(fmaxf(q.x, cs), fmaxf(csq, hh * div));
         if (vmax > 0.f) dt = fminf(dt, c.C_cfl * hh / vmax);
         float4 a = acc[s];
-        float am = sqrtf(a.x * a.x + a.y * a.y + a.z * a.z);
+        float am = sqrtf(a.x * a.x + a.y * a.y + a.z * a.z) * c.inv_a2;
         if (am > 0.f) dt = fminf(dt, sqrtf(hh / am));
         dt_out[s] = dt;   // per particle, for the time bins
     }
@@ -117,20 +125,26 @@ __global__ void k_kick1(int n, const double *sc, const int32_t *__restrict__ sbo
     va[s] = make_float4(fmaf(h, a.x, v.x), fmaf(h, a.y, v.y), fmaf(h, a.z, v.z), 0.f);
 }
 
-// u_1/2 = u + du dt/2; predictor p_p = p_1/2 + a dt/2, u_p = u_1/2 + du dt/2;
-// drift x1 = x + p_1/2 dt (periodic wrap into [0,1)).
-__global__ void k_half_drift(int n, const double *sc, const int32_t *__restrict__ sbox, float4 *__restrict__ st_pos, float4 *__restrict__ st_vel,
+// u_1/2 = u + (du - E u) dt/2; predictor p_p = p_1/2 + a dt/2,
+// u_p = (u_1/2 + du dt/2) / (1 + E dt/2); drift x1 = x + p_1/2 dt / a^2
+// (periodic wrap into [0,1)).  The expansion term -E u of eq:CosmoEngEqn
+// enters the opening half kick explicitly and the closing ones implicitly:
+// the trapezoidal rule over the step (E = 0 in a static box).
+__global__ void k_half_drift(int n, const double *sc, const int32_t *__restrict__ sbox, StepConsts c,
+                             float4 *__restrict__ st_pos, float4 *__restrict__ st_vel,
                              float4 *__restrict__ st_half, const float4 *__restrict__ va,
                              const float4 *__restrict__ acc, const float *__restrict__ du) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     float dt = (float)slot_dt(sc, sbox, s), h = 0.5f * dt;
     float4 v = st_vel[s], ph = va[s], a = acc[s];
-    float uh = fmaf(h, du[s], v.w);
+    float uh = fmaf(h, fmaf(-c.E, v.w, du[s]), v.w);
     st_half[s] = make_float4(ph.x, ph.y, ph.z, uh);
-    st_vel[s] = make_float4(fmaf(h, a.x, ph.x), fmaf(h, a.y, ph.y), fmaf(h, a.z, ph.z), fmaf(h, du[s], uh));
+    st_vel[s] = make_float4(fmaf(h, a.x, ph.x), fmaf(h, a.y, ph.y), fmaf(h, a.z, ph.z),
+                            fmaf(h, du[s], uh) / fmaf(h, c.E, 1.f));
     float4 p = st_pos[s];
-    float x[3] = {fmaf(dt, ph.x, p.x), fmaf(dt, ph.y, p.y), fmaf(dt, ph.z, p.z)};
+    const float dx = dt * c.inv_a2;
+    float x[3] = {fmaf(dx, ph.x, p.x), fmaf(dx, ph.y, p.y), fmaf(dx, ph.z, p.z)};
 #pragma unroll
     for (int k = 0; k < 3; k++) {
         x[k] -= floorf(x[k]);
@@ -171,7 +185,7 @@ __global__ void k_finish(int n, const double *sc, const int32_t *__restrict__ sb
     if (s >= n) return;
     float h = (float)(0.5 * slot_dt(sc, sbox, s));
     float4 a = va[s];
-    st_vel[s] = make_float4(a.x, a.y, a.z, fmaf(h, du[s], st_half[s].w));
+    st_vel[s] = make_float4(a.x, a.y, a.z, fmaf(h, du[s], st_half[s].w) / fmaf(h, c.E, 1.f));
     float d = cbrtf(c.N_res / Nn[s]);
     float lam = d < 1.f ? 0.2f * (1.f + d * d) : 0.2f * (1.f + 1.f / (d * d * d));
     float hn = hs[s] * (1.f - lam + lam * d);
@@ -356,7 +370,7 @@ static int step_impl(crk_ctx *ctx, int n, float *pos_h, float *vel_u, const floa
     CRK_LAUNCH_CHECK(ctx, "kick");
     rc = run_compatible(ctx, s);
     if (rc) return rc;
-    k_half_drift<<<g, b, 0, s>>>(n, dtb, sbox, ctx->st_pos, ctx->st_vel, ctx->st_half, ctx->va, ctx->acc, ctx->du);
+    k_half_drift<<<g, b, 0, s>>>(n, dtb, sbox, c, ctx->st_pos, ctx->st_vel, ctx->st_half, ctx->va, ctx->acc, ctx->du);
     ++ctx->launches;
     CRK_LAUNCH_CHECK(ctx, "drift");
     // rebuild at x1 (input order = current sorted order; boxes keep their particles)
@@ -565,6 +579,16 @@ void crk::graph_free(crk_ctx *ctx) {
     ctx->gstream = nullptr;
     ctx->bk_pos = ctx->bk_vel = nullptr;
     ctx->cap_bk = 0;
+}
+
+extern "C" int crk_set_expansion(crk_ctx *ctx, double a, double adot) {
+    if (!ctx) return CRK_EINVAL;
+    if (!(a > 0.0 && a < 1e30) || !(adot > -1e30 && adot < 1e30))
+        return crk_set_error(ctx, CRK_EINVAL, "bad scale factor or rate");
+    if (a != ctx->p.a || adot != ctx->p.adot) drop_graphs(ctx);   // graphs hold the old constants
+    ctx->p.a = a;
+    ctx->p.adot = adot;
+    return CRK_OK;
 }
 
 extern "C" int crk_graph_stats(crk_ctx *ctx, long long *captures, long long *replays, long long *recoveries) {

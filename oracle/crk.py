@@ -25,9 +25,10 @@ from . import build as _build
 # The scale factor a and its rate adot (Sec. 1.1, comoving variables with
 # p = a^2 dx/dt) default to a static box, a = 1, adot = 0.
 PARAMS = dict(gamma=5.0 / 3.0, n_h=4.0, N_res=268.0, C_l=2.0, C_q=1.0, eps=0.1,
-              eta_crit=1.0 / 4.0, eta_fold=0.2 / 4.0, C_cfl=0.25, zeta=4.0, a=1.0, adot=0.0)
-_ORDER = ["gamma", "n_h", "N_res", "C_l", "C_q", "eps", "eta_crit", "eta_fold", "C_cfl", "zeta", "a", "adot"]
-IA, IADOT = 10, 11
+              eta_crit=1.0 / 4.0, eta_fold=0.2 / 4.0, C_cfl=0.25, zeta=4.0, a=1.0, adot=0.0, density=0.0)
+_ORDER = ["gamma", "n_h", "N_res", "C_l", "C_q", "eps", "eta_crit", "eta_fold", "C_cfl", "zeta", "a", "adot",
+          "density"]
+IA, IADOT, IDENS = 10, 11, 12   # density 0: rho = m / V (R5); 1: the RK-corrected sum (rk_density)
 
 _LIB = None
 _f32p = np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")
@@ -51,8 +52,9 @@ def load():
                                         _f64p, _vp, _vp, _vp]
         lib.orc_gradv.argtypes = [_ci, _f32p, _ci, _vp, _ci] + [_f64p] * 7
         lib.orc_forces.argtypes = [_ci, _f32p, _ci, _vp, _ci] + [_f64p] * 13 + [
-            _vp, _vp, ctypes.POINTER(ctypes.c_longlong)]
-        lib.orc_compatible.argtypes = [_ci, _f32p, _ci, _vp, _ci] + [_f64p] * 13
+            _vp, _vp, ctypes.POINTER(ctypes.c_longlong), _vp]
+        lib.orc_compatible.argtypes = [_ci, _f32p, _ci, _vp, _ci] + [_f64p] * 13 + [_vp]
+        lib.orc_rkdensity.argtypes = [_ci, _f32p, _ci, _vp, _ci, _f64p, _f64p, _f64p, _f64p]
         lib.orc_kernel.argtypes = [_ci, _f64p, _f64p, _f64p, _f64p]
         lib.orc_num_threads.restype = _ci
         _LIB = lib
@@ -192,8 +194,24 @@ def gradv(pos_h, V, vel, A, B, gA, gB, k=None, targets=None, a=1.0):
     return gv / a
 
 
-def forces(pos_h, vel, u, mass, V, A, B, gA, gB, gv, prm=None, k=None, targets=None):
-    """P4: acceleration, direct du/dt, signal velocity, max pair Q (eq:mom, eq:eng)."""
+def _opt(a):
+    return None if a is None else np.ascontiguousarray(a, np.float64)
+
+
+def rk_density(pos_h, mass, A, B, k=None, targets=None):
+    """RK-corrected density rho_i = sum_j m_j W^R_ij over gather(i), self included."""
+    pos = _pos(pos_h)
+    n = pos.shape[0]
+    tp, nt, keep = _tg(targets)
+    rho = np.full(n, np.nan)
+    c = lambda a: np.ascontiguousarray(a, np.float64)
+    _check(load().orc_rkdensity(n, pos, _k(pos, k), tp, nt, c(mass), c(A), c(B), rho), "rkdensity")
+    return rho
+
+
+def forces(pos_h, vel, u, mass, V, A, B, gA, gB, gv, prm=None, k=None, targets=None, rho=None):
+    """P4: acceleration, direct du/dt, signal velocity, max pair Q (eq:mom, eq:eng);
+    rho (optional) replaces m / V as the density."""
     pos = _pos(pos_h)
     n = pos.shape[0]
     tp, nt, keep = _tg(targets)
@@ -205,12 +223,16 @@ def forces(pos_h, vel, u, mass, V, A, B, gA, gB, gv, prm=None, k=None, targets=N
     _check(load().orc_forces(n, pos, _k(pos, k), tp, nt, c(prm), c(V), c(mass), c(vel), c(u),
                              c(A), c(B), c(gA), c(gB), c(gv), acc, dudt, vsig,
                              qmax.ctypes.data_as(_vp), fscale.ctypes.data_as(_vp),
-                             ctypes.byref(pairs)), "forces")
+                             ctypes.byref(pairs), _ptr(_opt(rho))), "forces")
     return {"acc": acc, "dudt": dudt, "vsig": vsig, "qmax": qmax, "fscale": fscale,
             "pairs": int(pairs.value)}
 
 
-def compatible(pos_h, vel, u, mass, V, A, B, gA, gB, gv, vb, va, prm=None, k=None, targets=None):
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(_vp)
+
+
+def compatible(pos_h, vel, u, mass, V, A, B, gA, gB, gv, vb, va, prm=None, k=None, targets=None, rho=None):
     """P5: sum_j Delta u_ij for the kick vb -> va (eq:compEng .. eq:fij)."""
     pos = _pos(pos_h)
     n = pos.shape[0]
@@ -219,18 +241,20 @@ def compatible(pos_h, vel, u, mass, V, A, B, gA, gB, gv, vb, va, prm=None, k=Non
     du = np.full(n, np.nan)
     c = lambda a: np.ascontiguousarray(a, np.float64)
     _check(load().orc_compatible(n, pos, _k(pos, k), tp, nt, c(prm), c(V), c(mass), c(vel), c(u),
-                                 c(A), c(B), c(gA), c(gB), c(gv), c(vb), c(va), du), "compatible")
+                                 c(A), c(B), c(gA), c(gB), c(gv), c(vb), c(va), du, _ptr(_opt(rho))),
+           "compatible")
     return du
 
 
 # ------------------------------------------------------------ elementwise
 
 
-def thermo(V, mass, u, prm=None):
-    """eq:EOS with rho = m/V: rho, P = (gamma-1) rho u, c_s = sqrt(gamma P/rho), s = P/rho^gamma."""
+def thermo(V, mass, u, prm=None, rho=None):
+    """eq:EOS with rho = m/V (or the given density): rho, P = (gamma-1) rho u,
+    c_s = sqrt(gamma P/rho), s = P/rho^gamma."""
     prm = params() if prm is None else prm
     g = prm[0]
-    rho = np.asarray(mass, np.float64) / V
+    rho = np.asarray(mass, np.float64) / V if rho is None else np.asarray(rho, np.float64)
     P = (g - 1.0) * rho * u
     cs = np.sqrt(g * P / rho)
     s = P / rho ** g
@@ -255,14 +279,16 @@ def evaluate(state, prm=None, k=None, targets=None):
     p1 = volumes(pos, k)
     p2 = corrections(pos, p1["V"], k)
     gv = gradv(pos, p1["V"], vel, p2["A"], p2["B"], p2["gA"], p2["gB"], k, a=prm[IA])
-    p4 = forces(pos, vel, u, mass, p1["V"], p2["A"], p2["B"], p2["gA"], p2["gB"], gv, prm, k, targets)
+    rk = rk_density(pos, mass, p2["A"], p2["B"], k) if prm[IDENS] else None
+    p4 = forces(pos, vel, u, mass, p1["V"], p2["A"], p2["B"], p2["gA"], p2["gB"], gv, prm, k, targets, rho=rk)
     ev = dict(p1)
     ev.update(p2)
     ev["gv"] = gv
     ev.update({"acc": p4["acc"], "dudt": p4["dudt"], "vsig": p4["vsig"], "qmax": p4["qmax"],
                "fscale": p4["fscale"],
                "pairs_union": p4["pairs"], "pairs_gather": p1["pairs"]})
-    ev["rho"], ev["P"], ev["cs"], ev["s"] = thermo(p1["V"], mass, u, prm)
+    ev["rho"], ev["P"], ev["cs"], ev["s"] = thermo(p1["V"], mass, u, prm, rho=rk)
+    ev["rk_rho"] = rk
     ev["pos_h"], ev["vel"], ev["u"], ev["mass"] = pos.copy(), vel, u, mass
     return ev
 
@@ -349,7 +375,7 @@ def kdk_step(state, ev=None, dt=None, prm=None, k=None, h_min=1e-6, h_max=0.3, d
     E = prm[IADOT] / sa * (3.0 * (prm[0] - 1.0) + 2.0)   # expansion term of eq:CosmoEngEqn
     p_half = vel + 0.5 * dt * a0
     du1 = compatible(ev["pos_h"], ev["vel"], ev["u"], mass, ev["V"], ev["A"], ev["B"], ev["gA"], ev["gB"],
-                     ev["gv"], vel, p_half, prm, k)
+                     ev["gv"], vel, p_half, prm, k, rho=ev.get("rk_rho"))
     u_half = u + 0.5 * dt * (du1 - E * u)                       # opening half: explicit in u
     p_p = p_half + 0.5 * dt * a0
     u_p = (u_half + 0.5 * dt * du1) / (1.0 + 0.5 * dt * E)      # closing halves: implicit in u
@@ -363,7 +389,7 @@ def kdk_step(state, ev=None, dt=None, prm=None, k=None, h_min=1e-6, h_max=0.3, d
     ev1 = evaluate(st1, prm, k)
     p1 = p_half + 0.5 * dt * ev1["acc"]
     du2 = compatible(ev1["pos_h"], ev1["vel"], ev1["u"], mass, ev1["V"], ev1["A"], ev1["B"], ev1["gA"],
-                     ev1["gB"], ev1["gv"], p_half, p1, prm, k)
+                     ev1["gB"], ev1["gv"], p_half, p1, prm, k, rho=ev1.get("rk_rho"))
     u1 = (u_half + 0.5 * dt * du2) / (1.0 + 0.5 * dt * E)
     h1 = np.clip(thacker(pos[:, 3].astype(np.float64), ev1["N"], prm), h_min, h_max)
     out = {"pos_h": st1["pos_h"].copy(), "vel_u": np.empty((n, 4), np.float32), "mass": st1["mass"]}

@@ -623,7 +623,10 @@ int orc_gradv(int n, const float *pos4, int k, const int *tgt, int ntgt, const d
 /* Per-particle state shared by P4 and P5. */
 typedef struct {
     const double *prm, *V, *mass, *vel, *u, *A, *B, *gA, *gB, *gv;
+    const double *rho;   /* density of each particle (R5: m / V when NULL) */
 } fstate_t;
+
+static double dens(const fstate_t *f, int i) { return f->rho ? f->rho[i] : f->mass[i] / f->V[i]; }
 
 /* eq:phiVL / eq:rij with reading R6 */
 static double phi_vanleer(double a, double b) {
@@ -658,7 +661,7 @@ static void pair_force(const sys_t *s, const fstate_t *f, int i, int j,
     for (int a = 0; a < 3; a++) D[a] = grj[a] - gri[a];
 
     /* thermodynamics, eq:EOS with rho = m / V (R5) */
-    double rho_i = f->mass[i] / f->V[i], rho_j = f->mass[j] / f->V[j];
+    double rho_i = dens(f, i), rho_j = dens(f, j);
     double P_i = (gam - 1.0) * rho_i * f->u[i], P_j = (gam - 1.0) * rho_j * f->u[j];
     double c_i = sqrt(gam * P_i / rho_i), c_j = sqrt(gam * P_j / rho_j);
 
@@ -716,14 +719,14 @@ int orc_forces(int n, const float *pos4, int k, const int *tgt, int ntgt, const 
                const double *V, const double *mass, const double *vel, const double *u,
                const double *A, const double *B, const double *gA, const double *gB, const double *gv,
                double *acc, double *dudt, double *vsig, double *qmax, double *fscale,
-               long long *npairs) {
+               long long *npairs, const double *rho) {
     sys_t s;
     int rc = sys_init(&s, n, pos4, k);
     if (rc) return rc;
     int nt;
     int *t = make_targets(n, tgt, ntgt, &nt);
     if (!t || check_targets(n, t, nt)) { free(t); sys_free(&s); return t ? ORC_EINVAL : ORC_ENOMEM; }
-    fstate_t f = {prm, V, mass, vel, u, A, B, gA, gB, gv};
+    fstate_t f = {prm, V, mass, vel, u, A, B, gA, gB, gv, rho};
     uint32_t Hm = sys_Hmax(&s);
     long long pairs = 0;
     int err = 0;
@@ -783,14 +786,14 @@ static double f_partition(double dE, double si, double sj) {
 int orc_compatible(int n, const float *pos4, int k, const int *tgt, int ntgt, const double *prm,
                    const double *V, const double *mass, const double *vel, const double *u,
                    const double *A, const double *B, const double *gA, const double *gB, const double *gv,
-                   const double *vb, const double *va, double *du) {
+                   const double *vb, const double *va, double *du, const double *rho) {
     sys_t s;
     int rc = sys_init(&s, n, pos4, k);
     if (rc) return rc;
     int nt;
     int *t = make_targets(n, tgt, ntgt, &nt);
     if (!t || check_targets(n, t, nt)) { free(t); sys_free(&s); return t ? ORC_EINVAL : ORC_ENOMEM; }
-    fstate_t f = {prm, V, mass, vel, u, A, B, gA, gB, gv};
+    fstate_t f = {prm, V, mass, vel, u, A, B, gA, gB, gv, rho};
     double gam = prm[P_GAMMA];
     uint32_t Hm = sys_Hmax(&s);
     int err = 0;
@@ -801,14 +804,14 @@ int orc_compatible(int n, const float *pos4, int k, const int *tgt, int ntgt, co
         for (int kk = 0; kk < nt; kk++) {
             int i = t[kk];
             if (neighbours(&s, i, MODE_UNION, Hm, &l)) { err = ORC_ENOMEM; continue; }
-            double rho_i = mass[i] / V[i];
+            double rho_i = dens(&f, i);
             double s_i = (gam - 1.0) * rho_i * u[i] / pow(rho_i, gam);
             double acc = 0.0;
             for (int m = 0; m < l.n; m++) {
                 int j = l.v[m];
                 double F[3], D[3], Ptj, Qi, ap;
                 pair_force(&s, &f, i, j, F, D, &Ptj, &Qi, &ap);
-                double rho_j = mass[j] / V[j];
+                double rho_j = dens(&f, j);
                 double s_j = (gam - 1.0) * rho_j * u[j] / pow(rho_j, gam);
                 double w = 0.0;
                 for (int a = 0; a < 3; a++)
@@ -818,6 +821,44 @@ int orc_compatible(int n, const float *pos4, int k, const int *tgt, int ntgt, co
                 acc += fij * 0.5 * w / mass[i];
             }
             du[i] = acc / (prm[P_A] * prm[P_A] * prm[P_A] * prm[P_A]);
+        }
+        free(l.v);
+    }
+    free(t);
+    sys_free(&s);
+    return err;
+}
+
+/* RK-corrected density (the density option of crk_params): rho_i = sum over
+ * gather(i), self included, of m_j W^R_ij = A_i (1 + B_i . x_ij) W(r_ij, h_i)
+ * (eq:RK), the RK interpolant of the field m_j / V_j, which it reproduces when
+ * that field is constant or linear. */
+int orc_rkdensity(int n, const float *pos4, int k, const int *tgt, int ntgt, const double *mass,
+                  const double *A, const double *B, double *rho) {
+    sys_t s;
+    int rc = sys_init(&s, n, pos4, k);
+    if (rc) return rc;
+    int nt;
+    int *t = make_targets(n, tgt, ntgt, &nt);
+    if (!t || check_targets(n, t, nt)) { free(t); sys_free(&s); return t ? ORC_EINVAL : ORC_ENOMEM; }
+    uint32_t Hm = sys_Hmax(&s);
+    int err = 0;
+#pragma omp parallel
+    {
+        ilist l = {0};
+#pragma omp for schedule(dynamic, 16)
+        for (int kk = 0; kk < nt; kk++) {
+            int i = t[kk];
+            if (neighbours(&s, i, MODE_GATHER, Hm, &l)) { err = ORC_ENOMEM; continue; }
+            double sum = 0.0;
+            for (int m = 0; m < l.n; m++) {
+                int j = l.v[m];
+                double x[3];
+                pair_sep(&s, i, j, x);
+                double r = sqrt(dot3(x, x));
+                sum += mass[j] * (1.0 + dot3(B + 3 * i, x)) * W_c4(r, s.h[i]);
+            }
+            rho[i] = A[i] * sum;
         }
         free(l.v);
     }

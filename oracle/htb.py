@@ -189,8 +189,8 @@ def cycle(state, ev=None, Delta=1e-3, L=4, f_l=2, prm=None, k=None, h_min=1e-6, 
     bins.  `ev` is the evaluation at the state (O.evaluate, or the one a
     previous cycle returned).  Returns (state', ev', info)."""
     prm = O.params() if prm is None else prm
-    if prm[O.IA] != 1.0 or prm[O.IADOT] != 0.0:
-        raise ValueError("time bins are defined here for a static box (a = 1, adot = 0)")
+    if prm[O.IA] != 1.0 or prm[O.IADOT] != 0.0 or prm[O.IDENS] != 0.0:
+        raise ValueError("time bins are defined here for a static box (a = 1, adot = 0) and rho = m / V")
     if ev is None:
         ev = O.evaluate(state, prm, k)
     n = state["pos_h"].shape[0]

@@ -95,7 +95,9 @@ typedef struct {
                              the only one crk_cells reports),
                          1 = Hilbert curve (same cells, no jumps between them),
                          2 = recursive coordinate bisection (the paper's leaves) */
-    int reserved[5];
+    int density;      /* 0 = rho = m/V (default); 1 = the RK-corrected sum
+                         rho_i = sum_{j in gather(i)} m_j W^R_ij (eq:RK), self included */
+    int reserved[4];
 } crk_params;
 
 /* Per-step diagnostics (host memory), all reductions in FP64. */
@@ -369,13 +371,13 @@ int crk_order(crk_ctx *ctx, int32_t *perm, void *stream);
  * stops recording.  At most 4096 records are kept. */
 int crk_profile(crk_ctx *ctx, int enable);
 
-#define CRK_PROF_NPASS 10
+#define CRK_PROF_NPASS 11
 /* Wait for the recorded events and sum them per pass: ms[k] (milliseconds)
  * and counts[k] (records) for k = 0 P1 volumes, 1 neighbour sets, 2 P2
  * corrections, 3 P3 grad v, 4 P4 forces, 5 P5 compatible energy, 6 cell build
  * (all its kernels), 7 neighbour-list fill, 8 learned-h inference
  * (crk_mlp_forward, or crk_h_propose with its cell count), 9 one training step
- * (gradient and Adam); arrays of CRK_PROF_NPASS entries
+ * (gradient and Adam), 10 the RK-corrected density pass; arrays of CRK_PROF_NPASS entries
  * (may be NULL).  P1 is the list-counting walk, which also computes volumes.
  * *total_launches (may be NULL) = kernels launched by ctx since crk_create. */
 int crk_profile_read(crk_ctx *ctx, double *ms, long long *counts, long long *total_launches);

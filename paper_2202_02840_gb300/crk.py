@@ -30,7 +30,7 @@ class crk_params(ctypes.Structure):
                 ("gamma", "n_h", "N_res", "C_l", "C_q", "eps", "eta_crit", "eta_fold", "C_cfl", "zeta",
                  "h_min", "h_max", "dt_max", "a", "adot")] + [
         ("precision", ctypes.c_int), ("kmax", ctypes.c_int), ("tile_order", ctypes.c_int),
-        ("reserved", ctypes.c_int * 5)]
+        ("density", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
 
 
 class crk_diag(ctypes.Structure):
@@ -333,7 +333,8 @@ def crk_h_iterate(ctx, pos_h, tol=1e-4, max_it=50, stream=None):
 
 
 PASS_NAMES = ["P1 volumes", "neighbour sets", "P2 corrections", "P3 grad v", "P4 forces",
-              "P5 compatible energy", "cell build", "neighbour lists", "h proposal", "mlp train step"]
+              "P5 compatible energy", "cell build", "neighbour lists", "h proposal", "mlp train step",
+              "RK density"]
 NPASS = len(PASS_NAMES)
 
 

@@ -81,6 +81,7 @@ int crk_ensure_particles(crk_ctx *ctx, int n) {
     rc |= dalloc(ctx, &ctx->h_tmp, cap);
     rc |= dalloc(ctx, &ctx->flags, cap);
     rc |= dalloc(ctx, &ctx->d_dt, cap);
+    rc |= dalloc(ctx, &ctx->rho, cap);
     rc |= dalloc(ctx, &ctx->uofs, tiles);
     rc |= dalloc(ctx, &ctx->qV, cap);
     rc |= dalloc(ctx, &ctx->cnt_g, cap);
@@ -426,7 +427,7 @@ extern "C" int crk_create(const crk_params *p, crk_ctx **out) {
     if (!(prm.gamma > 1.0) || !(prm.n_h > 0) || !(prm.N_res > 0) || !(prm.eta_fold > 0) ||
         !(prm.h_max > 0 && prm.h_max < 1.0 / 3.0) || !(prm.h_min > 0 && prm.h_min < prm.h_max) ||
         prm.kmax < 1 || prm.kmax > 7 || prm.precision < 0 || prm.precision > 2 || !(prm.dt_max > 0) ||
-        prm.tile_order < 0 || prm.tile_order > 2 || !(prm.a > 0.0) || !(prm.a < 1e30) ||
+        prm.tile_order < 0 || prm.tile_order > 2 || prm.density < 0 || prm.density > 1 || !(prm.a > 0.0) || !(prm.a < 1e30) ||
         !(prm.adot > -1e30 && prm.adot < 1e30))
         return CRK_EINVAL;
     crk_ctx *ctx = new (std::nothrow) crk_ctx();
@@ -473,7 +474,7 @@ extern "C" int crk_destroy(crk_ctx *ctx) {
     dfree(&ctx->corr); dfree(&ctx->gv); dfree(&ctx->acc); dfree(&ctx->vq);
     dfree(&ctx->vb); dfree(&ctx->va); dfree(&ctx->du);
     dfree(&ctx->st_pos); dfree(&ctx->st_vel); dfree(&ctx->st_half); dfree(&ctx->st_tmp);
-    dfree(&ctx->st_tmp1); dfree(&ctx->q_tmp); dfree(&ctx->h_tmp); dfree(&ctx->flags); dfree(&ctx->d_red); dfree(&ctx->d_dt); dfree(&ctx->d_scalars); dfree(&ctx->sm_next);
+    dfree(&ctx->st_tmp1); dfree(&ctx->q_tmp); dfree(&ctx->h_tmp); dfree(&ctx->flags); dfree(&ctx->d_red); dfree(&ctx->d_dt); dfree(&ctx->rho); dfree(&ctx->d_scalars); dfree(&ctx->sm_next);
     dfree(&ctx->box_start); dfree(&ctx->dtb); dfree(&ctx->box_dtmin); dfree(&ctx->box_red);
     dfree(&ctx->box_in); dfree(&ctx->sbox); dfree(&ctx->sbox_tmp); dfree(&ctx->mkey); dfree(&ctx->node_box);
     if (ctx->h_counters) cudaFreeHost(ctx->h_counters);

@@ -54,6 +54,7 @@ __device__ __forceinline__ uint32_t fq(const FRec &r, int k) {
 struct FSrc {
     const uint4 *q4;
     const float *hs;
+    const float *rho;      // RK-corrected density, or null for m / V
     const float *V;
     const float4 *vel;
     const float *mass;
@@ -68,7 +69,7 @@ __device__ __forceinline__ FRec load_frec(int j, const FSrc &src, const FParams 
     r.w0 = make_float4(__uint_as_float(q.x), __uint_as_float(q.y), __uint_as_float(q.z), ih);
     float V = src.V[j];
     float4 v = src.vel[j];
-    float rho = src.mass[j] / V;
+    float rho = src.rho ? src.rho[j] : src.mass[j] / V;
     float P = fp.gm1 * rho * v.w;
     CorrRec c = src.corr[j];
     GvRec g = src.gv[j];
@@ -359,7 +360,12 @@ __global__ void k_sig(int n, const float4 *__restrict__ vb, const float4 *__rest
 int run_forces(crk_ctx *ctx, cudaStream_t s) {
     if (ctx->n == 0) return CRK_OK;
     FParams fp = fparams(ctx->p);
-    FSrc src{ctx->q4, ctx->hs, ctx->V, ctx->vel, ctx->mass, ctx->corr, ctx->gv};
+    if (ctx->p.density) {   // the RK-corrected density of the current corrections
+        int rc = run_density(ctx, s);
+        if (rc) return rc;
+    }
+    FSrc src{ctx->q4, ctx->hs, ctx->p.density ? ctx->rho : nullptr, ctx->V, ctx->vel, ctx->mass, ctx->corr,
+             ctx->gv};
     k_pack_frec<<<grid_for(ctx->n, 256), 256, 0, s>>>(ctx->n, src, fp, reinterpret_cast<FRec *>(ctx->frec),
                                                      ctx->sfun);
     ++ctx->launches;

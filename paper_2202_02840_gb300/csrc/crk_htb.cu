@@ -689,8 +689,8 @@ extern "C" int crk_cycle(crk_ctx *ctx, int n, float *pos_h, float *vel_u, const 
     if (n <= 0 || !pos_h || !vel_u || !mass || !(Delta > 0.0) || !isfinite(Delta) || L < 0 || L > 20 || f_l < 0)
         return crk_set_error(ctx, CRK_EINVAL, "bad arguments");
     if (ctx->nbox > 1) return crk_set_error(ctx, CRK_ESTATE, "time bins cover one box");
-    if (ctx->p.a != 1.0 || ctx->p.adot != 0.0)
-        return crk_set_error(ctx, CRK_EINVAL, "time bins are built for a static box (a = 1, adot = 0)");
+    if (ctx->p.a != 1.0 || ctx->p.adot != 0.0 || ctx->p.density != 0)
+        return crk_set_error(ctx, CRK_EINVAL, "time bins are built for a static box (a = 1, adot = 0) and rho = m/V");
     if (ctx->volumes_only) return crk_set_error(ctx, CRK_ESTATE, "no neighbour lists in this context");
     if (stats) memset(stats, 0, sizeof(*stats));
     cudaStream_t s = (cudaStream_t)stream;

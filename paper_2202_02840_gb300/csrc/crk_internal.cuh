@@ -146,6 +146,7 @@ struct crk_ctx {
     int32_t *flags = nullptr;        // h iteration: converged flags
     double *d_red = nullptr;         // FP64 reduction scratch
     float *d_dt = nullptr;           // per-particle dt scratch
+    float *rho = nullptr;            // RK-corrected density (crk_params.density = 1)
     double *d_scalars = nullptr;     // [0] dt of the step, [1] dt_next, [2..] diagnostics
     int rates_valid = 0;
     int step_n = 0;
@@ -253,7 +254,7 @@ int crk_sync_counters(crk_ctx *ctx, cudaStream_t s);
 // internal entry points shared between translation units (sorted-order data)
 namespace crk {
 enum { PROF_P1 = 0, PROF_PN = 1, PROF_P2 = 2, PROF_P3 = 3, PROF_P4 = 4, PROF_P5 = 5, PROF_BUILD = 6,
-       PROF_LISTS = 7, PROF_MLP_FWD = 8, PROF_MLP_TRAIN = 9, PROF_NPASS = 10 };
+       PROF_LISTS = 7, PROF_MLP_FWD = 8, PROF_MLP_TRAIN = 9, PROF_DENS = 10, PROF_NPASS = 11 };
 void mlp_free(crk_ctx *ctx);
 void htb_free(crk_ctx *ctx);
 void rcb_free(crk_ctx *ctx);
@@ -273,6 +274,7 @@ int run_lists(crk_ctx *ctx, cudaStream_t s);
 int scan_u32(crk_ctx *ctx, const uint32_t *in, uint32_t *out, int count, cudaStream_t s);
 int run_neighbours(crk_ctx *ctx, int mode, int32_t *cnt, uint32_t *hash, cudaStream_t s);
 int run_corrections(crk_ctx *ctx, bool with_gradv, cudaStream_t s);
+int run_density(crk_ctx *ctx, cudaStream_t s);
 int run_forces(crk_ctx *ctx, cudaStream_t s);
 int run_compatible(crk_ctx *ctx, cudaStream_t s);
 int evaluate(crk_ctx *ctx, cudaStream_t s);   // P1..P4 and per-particle time steps (crk_step.cu)

@@ -377,6 +377,67 @@ struct P3 {
     }
 };
 
+// ================================================================= RK-corrected density
+
+// crk_params.density = 1: rho_i = sum over gather(i), self included, of
+// m_j W^R_ij = A_i (1 + B_i . x_ij) W(r_ij, h_i) (eq:RK): the RK interpolant of
+// m_j / V_j, exact for constant and linear fields.
+struct PD {
+    static constexpr bool GATHER = true;
+    static constexpr int UNROLL = 4;
+    static constexpr bool ENTRIES = true;
+    static constexpr bool PERSISTENT = false;
+    static constexpr bool PREFETCH = false;
+    struct Params {
+        const uint4 *q4;
+        const float *hs;
+        const float *mass;
+        const CorrRec *corr;
+        float *rho;
+    };
+    struct Rec {
+        uint4 q;
+        float m;
+    };
+    struct IState {
+        uint4 q;
+        float inv_h, A, B[3], acc;
+    };
+    __device__ static void init(IState &s, int i, bool valid, const Params &p) {
+        s.q = valid ? p.q4[i] : make_uint4(0, 0, 0, 0);
+        s.inv_h = 1.f / (valid ? p.hs[i] : 1.f);
+        const float4 c = valid ? p.corr[i].c0 : make_float4(0.f, 0.f, 0.f, 0.f);
+        s.A = c.x;
+        s.B[0] = c.y; s.B[1] = c.z; s.B[2] = c.w;
+        s.acc = valid ? p.mass[i] : 0.f;                 // self: x = 0, W(0) / (495/(32 pi h^3)) = 1
+    }
+    __device__ static void zero(IState &s) { s.acc = 0.f; }
+    __device__ static void merge(IState &s, const IState &o) { s.acc += o.acc; }
+    __device__ static Rec load(uint32_t e, size_t, const Params &p) {
+        const uint32_t j = e & 0x3fffffffu;
+        return Rec{__ldg(p.q4 + j), __ldg(p.mass + j)};
+    }
+    __device__ static void pair(IState &s, const Rec &r, uint32_t, size_t, bool, const Params &) {
+        int dx = (int)(s.q.x - r.q.x), dy = (int)(s.q.y - r.q.y), dz = (int)(s.q.z - r.q.z);
+        Sep d = separation(dx, dy, dz);
+        float eta = d.r * s.inv_h;
+        float t = fmaxf(1.f - eta, 0.f);
+        float t2 = t * t, t3 = t2 * t;
+        float Wu = t3 * t3 * fmaf(eta, fmaf(eta, K35_3, 6.f), 1.f);
+        float sB = fmaf(s.B[0], d.x, fmaf(s.B[1], d.y, fmaf(s.B[2], d.z, 1.f)));
+        s.acc = fmaf(r.m * sB, Wu, s.acc);
+    }
+    __device__ static void finish(IState &s, int i, const Params &p) {
+        const float ih3 = s.inv_h * s.inv_h * s.inv_h;
+        p.rho[i] = s.A * (KW * ih3) * s.acc;
+    }
+};
+
+int run_density(crk_ctx *ctx, cudaStream_t s) {
+    PD::Params p{ctx->q4, ctx->hs, ctx->mass, ctx->corr, ctx->rho};
+    return launch_lpass<PD, 8>(ctx, PROF_DENS, p, s, "RK density");
+}
+
 int run_corrections(crk_ctx *ctx, bool with_gradv, cudaStream_t s) {
     int rc;
     if (ctx->p.precision == 2) {

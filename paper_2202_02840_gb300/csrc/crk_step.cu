@@ -56,12 +56,12 @@ __global__ void k_cfl(int n, StepConsts c, const float *__restrict__ hs, const f
                       const float *__restrict__ mass, const float4 *__restrict__ vel,
                       const float4 *__restrict__ acc, const float2 *__restrict__ vq,
                       const GvRec *__restrict__ gv, unsigned long long *dtmin, const int32_t *__restrict__ sbox,
-                      float *__restrict__ dt_out) {
+                      float *__restrict__ dt_out, const float *__restrict__ rho_in) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     float dt = 3.0e38f;
     if (s < n) {
         float hh = hs[s] * c.inv_nh;
-        float rho = mass[s] / V[s];
+        float rho = rho_in ? rho_in[s] : mass[s] / V[s];
         float u = vel[s].w;
         float cs = sqrtf(fmaxf(c.gamma * c.gm1 * u, 0.f));
         float2 q = vq[s];
@@ -315,7 +315,7 @@ int evaluate(crk_ctx *ctx, cudaStream_t s) {
     k_fill_ull<<<grid_for(nb, 256), 256, 0, s>>>(nb, 0x7f7fffffull, dtmin);   // FLT_MAX bits
     k_cfl<<<grid_for(ctx->n, 256), 256, 0, s>>>(ctx->n, c, ctx->hs, ctx->V, ctx->mass, ctx->vel, ctx->acc,
                                                   ctx->vq, ctx->gv, dtmin, batched ? ctx->sbox : nullptr,
-                                                  ctx->d_dt);
+                                                  ctx->d_dt, ctx->p.density ? ctx->rho : nullptr);
     ctx->launches += 2;
     CRK_LAUNCH_CHECK(ctx, "CFL");
     return CRK_OK;

@@ -97,3 +97,30 @@ def test_graph_replays_follow_a_changing_scale_factor():
         crk.crk_steps(ctx, pos, vel, mass, 4, 1e-4, use_graph=use_graph)
         runs.append((as_np(pos), as_np(vel)))
     assert np.array_equal(runs[0][0], runs[1][0]) and np.array_equal(runs[0][1], runs[1][1])
+
+
+@pytest.mark.parametrize("case", ["uniform16", "zeldovich16"])
+def test_rk_density_forces_and_step(case):
+    """crk_params.density = 1: the RK-corrected density feeds P, c_s, the
+    viscosity, the forces and the compatible energy (and with a comoving box)."""
+    st = flowing(case)
+    prm = O.params(density=1.0, a=0.8, adot=0.1)
+    ev = O.evaluate(st, prm)
+    ctx = crk.crk_create(density=1, a=0.8, adot=0.1)
+    crk.crk_build_cells(ctx, dev(st["pos_h"]))
+    acc, dudt, vsig, qmax, pairs = crk.crk_forces(
+        ctx, dev(st["mass"]), dev(st["vel_u"]), f32(ev["V"]), f32(ev["A"]), f32(ev["B"]), f32(ev["gA"]),
+        f32(ev["gB"]), f32(ev["gv"]), with_pairs=True)
+    e = {"acc": rel_err(acc, ev["acc"], floor=ev["fscale"]), "dudt": rel_err(dudt, ev["dudt"]),
+         "vsig": rel_err(vsig, ev["vsig"]), "qmax": rel_err(qmax, ev["qmax"])}
+    dt = 0.5 * float(np.min(O.cfl_dt(ev, prm)))
+    ost, _, _ = O.kdk_step(st, ev=ev, dt=dt, prm=prm)
+    pos, vel, mass = dev(st["pos_h"]), dev(st["vel_u"]), dev(st["mass"])
+    crk.crk_step(crk.crk_create(density=1, a=0.8, adot=0.1), pos, vel, mass, dt)
+    gp, gv = as_np(pos), as_np(vel)
+    dx = gp[:, :3] - ost["pos_h"][:, :3]
+    dx -= np.round(dx)
+    e.update({"x": float(np.max(np.abs(dx))), "v": rel_err(gv[:, :3], ost["vel_u"][:, :3]),
+              "u": rel_err(gv[:, 3], ost["vel_u"][:, 3]), "h": rel_err(gp[:, 3], ost["pos_h"][:, 3])})
+    print(case, e)
+    assert e["x"] < 1e-6 and max(v for k, v in e.items() if k != "x") < TOL, e

@@ -40,9 +40,10 @@ WORKLOAD = "zeldovich-128^3: clustered gas, Zel'dovich lattice displacement, P(k
 FLOPS_PER_UNIT = {"P1 volumes": 20, "P2 corrections": 110, "P3 grad v": 92, "P4 forces": 281,
                   "P5 compatible energy": 259}
 # DRAM bytes (read + write) per unit measured by ncu for the current P4 kernel on
-# zeldovich-64^3 (0.66 GB read + 1.20 GB written for 39.1 M unordered pairs); a
-# full 128^3 launch is too large to capture, so the traffic is scaled by units.
-TRAFFIC_PER_UNIT = {"P4 forces": 47.6}
+# zeldovich-64^3 in the Hilbert order (0.65 GB read + 1.20 GB written for
+# 39.1 M unordered pairs); a full 128^3 launch is too large to capture, so the
+# traffic is scaled by units.
+TRAFFIC_PER_UNIT = {"P4 forces": 47.4}
 
 
 def measured_peaks():

@@ -92,6 +92,8 @@ int crk_ensure_particles(crk_ctx *ctx, int n) {
     rc |= dalloc(ctx, &ctx->frec, 10 * (size_t)cap);
     rc |= dalloc(ctx, &ctx->sfun, cap);
     rc |= dalloc(ctx, &ctx->sig, cap);
+    rc |= dalloc(ctx, &ctx->sig2, cap);
+    rc |= dalloc(ctx, &ctx->du_next, cap);
     rc |= dalloc(ctx, &ctx->node_lo, 2 * (size_t)tiles + MAX_LEVELS);
     rc |= dalloc(ctx, &ctx->node_hi, 2 * (size_t)tiles + MAX_LEVELS);
     rc |= dalloc(ctx, &ctx->hist, 256 * (size_t)nb);
@@ -468,14 +470,14 @@ extern "C" int crk_destroy(crk_ctx *ctx) {
     dfree(&ctx->gofs); dfree(&ctx->uofs); dfree(&ctx->glist); dfree(&ctx->ulist);
     dfree(&ctx->qV); dfree(&ctx->cnt_g); dfree(&ctx->cnt_u); dfree(&ctx->len_g); dfree(&ctx->len_u);
     dfree(&ctx->tcap); dfree(&ctx->tbase); dfree(&ctx->ent); dfree(&ctx->Fst); dfree(&ctx->frec);
-    dfree(&ctx->sfun); dfree(&ctx->sig);
+    dfree(&ctx->sfun); dfree(&ctx->sig); dfree(&ctx->sig2); dfree(&ctx->du_next);
     dfree(&ctx->cell_start); dfree(&ctx->counters);
     dfree(&ctx->V); dfree(&ctx->Nn); dfree(&ctx->vel); dfree(&ctx->mass);
     dfree(&ctx->corr); dfree(&ctx->gv); dfree(&ctx->acc); dfree(&ctx->vq);
     dfree(&ctx->vb); dfree(&ctx->va); dfree(&ctx->du);
     dfree(&ctx->st_pos); dfree(&ctx->st_vel); dfree(&ctx->st_half); dfree(&ctx->st_tmp);
     dfree(&ctx->st_tmp1); dfree(&ctx->q_tmp); dfree(&ctx->h_tmp); dfree(&ctx->flags); dfree(&ctx->d_red); dfree(&ctx->d_dt); dfree(&ctx->rho); dfree(&ctx->d_scalars); dfree(&ctx->sm_next);
-    dfree(&ctx->box_start); dfree(&ctx->dtb); dfree(&ctx->box_dtmin); dfree(&ctx->box_red);
+    dfree(&ctx->box_start); dfree(&ctx->dtb); dfree(&ctx->dtb_next); dfree(&ctx->box_dtmin); dfree(&ctx->box_red);
     dfree(&ctx->box_in); dfree(&ctx->sbox); dfree(&ctx->sbox_tmp); dfree(&ctx->mkey); dfree(&ctx->node_box);
     if (ctx->h_counters) cudaFreeHost(ctx->h_counters);
     for (int k = 0; k < 2; k++)
@@ -546,6 +548,7 @@ int crk::ensure_boxes(crk_ctx *ctx, int n, int nbox) {
         int cap = nbox < 64 ? 64 : nbox;
         rc |= dalloc(ctx, &ctx->box_start, (size_t)cap + 1);
         rc |= dalloc(ctx, &ctx->dtb, (size_t)cap);
+        rc |= dalloc(ctx, &ctx->dtb_next, (size_t)cap);
         rc |= dalloc(ctx, &ctx->box_dtmin, (size_t)cap);
         rc |= dalloc(ctx, &ctx->box_red, 8 * (size_t)cap);
         if (rc) return rc;

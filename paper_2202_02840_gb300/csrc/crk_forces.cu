@@ -277,15 +277,35 @@ struct P4 {
 
 // ================================================================= P5 compatible energy
 
-// sig = (v + v') of the kick and the entropy s of the evaluation state
-template <bool COMP>
+// sig = (v + v') of the kick and the entropy s of the evaluation state.
+// DUAL: two kicks with the same pair forces in one pass over the stored
+// forces (a step's closing kick and the next step's opening kick): sig and
+// sig2, du and du2, each sum in the same order as a single pass would take.
+// skip (may be null): a device flag set when the sums of this pass were
+// already formed by the previous step's dual pass; the pass then reads
+// nothing (the caller takes those sums).
+__device__ __forceinline__ float compat_term(const float4 me, const float4 r, const float4 F) {
+    // 2 Delta E_ij = (v_j + v'_j - v_i - v'_i) . F_ij  (reading of eq:Eij)
+    float w = fmaf(r.x - me.x, F.x, fmaf(r.y - me.y, F.y, (r.z - me.z) * F.z));
+    // eq:fij
+    float si = me.w, sj = r.w, ss = si + sj;
+    float f = 0.5f;
+    if (ss != 0.f) {
+        bool take_min = (w >= 0.f) == (si >= sj);
+        f = (take_min ? fminf(si, sj) : fmaxf(si, sj)) / ss;
+    }
+    return 0.5f * f * w;
+}
+
+template <bool COMP, bool DUAL = false>
 struct P5 {
     static constexpr bool GATHER = false;
     static constexpr int UNROLL = 3;
     static constexpr bool PERSISTENT = false;
     static constexpr bool PREFETCH = false;
+    static constexpr bool SKIPPABLE = true;
     struct Rec {
-        float4 sig, F;
+        float4 sig, sig2, F;
     };
     struct Params {
         const float4 *sig;
@@ -293,40 +313,48 @@ struct P5 {
         const float *mass;
         float *du;
         float inv_a4;
+        const unsigned long long *skip;
+        const float4 *sig2;
+        float *du2;
     };
     struct IState {
-        float4 me;
+        float4 me, me2;
         float m;
-        Acc<COMP> du;
+        Acc<COMP> du, du2;
     };
     __device__ static void init(IState &s, int i, bool valid, const Params &p) {
         s.me = valid ? p.sig[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        if (DUAL) s.me2 = valid ? p.sig2[i] : make_float4(0.f, 0.f, 0.f, 0.f);
         s.m = valid ? p.mass[i] : 1.f;
     }
-    __device__ static void zero(IState &s) { s.du = Acc<COMP>(); }
-    __device__ static void merge(IState &s, const IState &o) { merge_acc(s.du, o.du); }
+    __device__ static void zero(IState &s) {
+        s.du = Acc<COMP>();
+        s.du2 = Acc<COMP>();
+    }
+    __device__ static void merge(IState &s, const IState &o) {
+        merge_acc(s.du, o.du);
+        if (DUAL) merge_acc(s.du2, o.du2);
+    }
     // the stored entry carries j (written by P4): the list itself is not read
     static constexpr bool ENTRIES = false;
     __device__ static Rec load(uint32_t, size_t pos, const Params &p) {
         const float4 F = __ldg(p.Fst + pos);
-        return Rec{__ldg(p.sig + __float_as_uint(F.w)), F};
+        const uint32_t j = __float_as_uint(F.w);
+        Rec r;
+        r.sig = __ldg(p.sig + j);
+        if (DUAL) r.sig2 = __ldg(p.sig2 + j);
+        r.F = F;
+        return r;
     }
     __device__ static void pair(IState &s, const Rec &rec, uint32_t, size_t, bool, const Params &) {
-        const float4 r = rec.sig;
-        const float4 F = rec.F;
-        // 2 Delta E_ij = (v_j + v'_j - v_i - v'_i) . F_ij  (reading of eq:Eij)
-        float w = fmaf(r.x - s.me.x, F.x, fmaf(r.y - s.me.y, F.y, (r.z - s.me.z) * F.z));
-        // eq:fij
-        float si = s.me.w, sj = r.w, ss = si + sj;
-        float f = 0.5f;
-        if (ss != 0.f) {
-            bool take_min = (w >= 0.f) == (si >= sj);
-            f = (take_min ? fminf(si, sj) : fmaxf(si, sj)) / ss;
-        }
-        s.du.add(0.5f * f * w);
+        s.du.add(compat_term(s.me, rec.sig, rec.F));
+        if (DUAL) s.du2.add(compat_term(s.me2, rec.sig2, rec.F));
     }
     // eq:compEng2: 1/(2 a^4) (p_j + p'_j - p_i - p'_i) . dp_ij/dt
-    __device__ static void finish(IState &s, int i, const Params &p) { p.du[i] = s.du.value() / s.m * p.inv_a4; }
+    __device__ static void finish(IState &s, int i, const Params &p) {
+        p.du[i] = s.du.value() / s.m * p.inv_a4;
+        if (DUAL) p.du2[i] = s.du2.value() / s.m * p.inv_a4;
+    }
 };
 
 static FParams fparams(const crk_params &c) {
@@ -379,20 +407,51 @@ int run_forces(crk_ctx *ctx, cudaStream_t s) {
     return launch_lpass<P4<false>, 1>(ctx, PROF_P4, p, s, "P4 forces");
 }
 
-// P5 for the kick vb -> va (sorted float4 arrays), with the F_ij of the last P4.
-int run_compatible(crk_ctx *ctx, cudaStream_t s) {
+// P5 for the kick vb -> va (sorted float4 arrays), with the F_ij of the last P4;
+// skip (device flag, may be null) makes the pass read nothing when set.
+int run_compatible(crk_ctx *ctx, cudaStream_t s, const unsigned long long *skip) {
     if (ctx->n == 0) return CRK_OK;
     k_sig<<<grid_for(ctx->n, 256), 256, 0, s>>>(ctx->n, ctx->vb, ctx->va, ctx->sfun, ctx->sig);
     ++ctx->launches;
     CRK_LAUNCH_CHECK(ctx, "kick sums");
+    const float ia4 = (float)(1.0 / (ctx->p.a * ctx->p.a * ctx->p.a * ctx->p.a));
     if (ctx->p.precision >= 1) {
-        typename P5<true>::Params p{ctx->sig, ctx->Fst, ctx->mass, ctx->du,
-                                    (float)(1.0 / (ctx->p.a * ctx->p.a * ctx->p.a * ctx->p.a))};
+        typename P5<true>::Params p{ctx->sig, ctx->Fst, ctx->mass, ctx->du, ia4, skip, nullptr, nullptr};
         return launch_lpass<P5<true>, 8>(ctx, PROF_P5, p, s, "P5 compatible energy");
     }
-    typename P5<false>::Params p{ctx->sig, ctx->Fst, ctx->mass, ctx->du,
-                                 (float)(1.0 / (ctx->p.a * ctx->p.a * ctx->p.a * ctx->p.a))};
+    typename P5<false>::Params p{ctx->sig, ctx->Fst, ctx->mass, ctx->du, ia4, skip, nullptr, nullptr};
     return launch_lpass<P5<false>, 8>(ctx, PROF_P5, p, s, "P5 compatible energy");
+}
+
+// kick sums of the next step's opening kick: vb = p1 (= va of this closing
+// kick), va = p1 + a dt'/2 with the next step's dt (as k_kick1 will form them)
+__global__ void k_sig_next(int n, const double *dtn, const int32_t *__restrict__ sbox, const float4 *__restrict__ va,
+                           const float4 *__restrict__ acc, const float *__restrict__ sfun, float4 *__restrict__ sig2) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float h = (float)(0.5 * dtn[sbox ? sbox[i] : 0]);
+    float4 v = va[i], a = acc[i];
+    sig2[i] = make_float4(v.x + fmaf(h, a.x, v.x), v.y + fmaf(h, a.y, v.y), v.z + fmaf(h, a.z, v.z), sfun[i]);
+}
+
+// P5 of this closing kick (vb -> va into du) and of the next step's opening
+// kick (its dt per box in dtn; into du_next) in one pass over the stored forces.
+int run_compatible_dual(crk_ctx *ctx, const double *dtn, const int32_t *sbox, cudaStream_t s) {
+    if (ctx->n == 0) return CRK_OK;
+    const int g = grid_for(ctx->n, 256);
+    k_sig<<<g, 256, 0, s>>>(ctx->n, ctx->vb, ctx->va, ctx->sfun, ctx->sig);
+    k_sig_next<<<g, 256, 0, s>>>(ctx->n, dtn, sbox, ctx->va, ctx->acc, ctx->sfun, ctx->sig2);
+    ctx->launches += 2;
+    CRK_LAUNCH_CHECK(ctx, "kick sums");
+    const float ia4 = (float)(1.0 / (ctx->p.a * ctx->p.a * ctx->p.a * ctx->p.a));
+    if (ctx->p.precision >= 1) {
+        typename P5<true, true>::Params p{ctx->sig, ctx->Fst, ctx->mass, ctx->du, ia4, nullptr, ctx->sig2,
+                                          ctx->du_next};
+        return launch_lpass<P5<true, true>, 8>(ctx, PROF_P5, p, s, "P5 compatible energy (two kicks)");
+    }
+    typename P5<false, true>::Params p{ctx->sig, ctx->Fst, ctx->mass, ctx->du, ia4, nullptr, ctx->sig2,
+                                       ctx->du_next};
+    return launch_lpass<P5<false, true>, 8>(ctx, PROF_P5, p, s, "P5 compatible energy (two kicks)");
 }
 
 }  // namespace crk

@@ -666,6 +666,7 @@ static int cycle_impl(crk_ctx *ctx, int n, float *pos_h, float *vel_u, const flo
     CRK_LAUNCH_CHECK(ctx, "finish cycle");
     rc = scatter_rows(ctx, ctx->st_pos, pos_h, 4, s);
     if (!rc) rc = scatter_rows(ctx, ctx->st_vel, vel_u, 4, s);
+    if (!rc) CRK_CUDA(ctx, cudaMemsetAsync(ctx->counters + CNT_NEXT_OK, 0, sizeof(unsigned long long), s));
     if (!rc) rc = crk_sync_counters(ctx, s);
     if (rc) return rc;
     ctx->rates_valid = 1;

@@ -35,7 +35,9 @@ enum {
     CNT_CHANGED = 14,   // time bins: a limiter sweep raised some level
     CNT_UNRES = 15,     // time bins: particle level requests deeper than L
     CNT_WAKE = 16,      // time bins: passive leaves raised
-    CNT_NACT = 17,      // time bins: leaves ending a step at the current tick
+    CNT_NACT = 17,      // time bins: leaves ending a step at the current tick (and 18: their particles)
+    CNT_NEXT_OK = 19,   // du_next holds the next opening kick's energy rate for dt_next
+    CNT_SKIP = 20,      // this step's opening kick takes du_next
     CNT_COUNT = 24
 };
 
@@ -123,6 +125,9 @@ struct crk_ctx {
     float4 *frec = nullptr;          // packed pair-set records, 10 float4 (160 B) per particle
     float *sfun = nullptr;           // specific entropy of the evaluation state
     float4 *sig = nullptr;           // (v + v') of a kick, s
+    float4 *sig2 = nullptr;          // the same for the next step's opening kick
+    float *du_next = nullptr;        // the next step's opening-kick energy rate (formed ahead)
+    double *dtb_next = nullptr;      // the next step's dt per box (batched; one box uses d_scalars[16])
 
     // pass buffers in sorted order
     float *V = nullptr, *Nn = nullptr;
@@ -276,7 +281,8 @@ int run_neighbours(crk_ctx *ctx, int mode, int32_t *cnt, uint32_t *hash, cudaStr
 int run_corrections(crk_ctx *ctx, bool with_gradv, cudaStream_t s);
 int run_density(crk_ctx *ctx, cudaStream_t s);
 int run_forces(crk_ctx *ctx, cudaStream_t s);
-int run_compatible(crk_ctx *ctx, cudaStream_t s);
+int run_compatible(crk_ctx *ctx, cudaStream_t s, const unsigned long long *skip = nullptr);
+int run_compatible_dual(crk_ctx *ctx, const double *dtn, const int32_t *sbox, cudaStream_t s);
 int evaluate(crk_ctx *ctx, cudaStream_t s);   // P1..P4 and per-particle time steps (crk_step.cu)
 int gather_rows(crk_ctx *ctx, const void *in, void *out, int width_words, cudaStream_t s);
 int scatter_rows(crk_ctx *ctx, const void *in, void *out, int width_words, cudaStream_t s);

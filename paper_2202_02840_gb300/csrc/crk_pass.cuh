@@ -10,6 +10,8 @@
 
 #include "crk_internal.cuh"
 
+#include <type_traits>
+
 namespace crk {
 
 struct PassGeom {
@@ -121,8 +123,21 @@ struct ListGeom {
 // best: 4 for P1 and P2, 3 for P3 and P5).  P4, whose 160-byte record
 // already fills the registers, keeps one pair per iteration and instead
 // prefetches the record of entry k + 1 and the entry k + 2 (P::PREFETCH).
+// passes that declare SKIPPABLE take a device flag (Params::skip, may be null)
+template <class P, class = void>
+struct has_skip : std::false_type {};
+template <class P>
+struct has_skip<P, std::void_t<decltype(P::SKIPPABLE)>> : std::bool_constant<P::SKIPPABLE> {};
+
+template <class P>
+__device__ __forceinline__ bool pass_skipped(const typename P::Params &prm) {
+    if constexpr (has_skip<P>::value) return prm.skip && *(volatile const unsigned long long *)prm.skip;
+    return false;
+}
+
 template <class P, int U>
 __device__ __forceinline__ void lpass_tile(const ListGeom &g, const typename P::Params &prm, int tile, int lane) {
+    if (pass_skipped<P>(prm)) return;   // the sums were formed by an earlier pass
     const int i = tile * TILE + lane;
     const bool valid = i < g.n;
     typename P::IState st;

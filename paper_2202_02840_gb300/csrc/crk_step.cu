@@ -109,6 +109,33 @@ __global__ void k_pick_dt(int nbox, double dt_req, const double *req, double dt_
     dtb[b] = dt;
 }
 
+// The opening kick of a step may take the energy rates that the previous
+// step's dual P5 pass formed ahead (CNT_NEXT_OK), but only if they were formed
+// for exactly this step's dt in every box; the flag is consumed either way.
+__global__ void k_next_check(int nbox, const double *__restrict__ dtb, const double *__restrict__ dtn,
+                             unsigned long long *cnt) {
+    __shared__ int differ;
+    if (threadIdx.x == 0) differ = 0;
+    __syncthreads();
+    for (int b = threadIdx.x; b < nbox; b += blockDim.x)
+        if (dtb[b] != dtn[b]) differ = 1;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        cnt[CNT_SKIP] = (cnt[CNT_NEXT_OK] && !differ) ? 1ull : 0ull;
+        cnt[CNT_NEXT_OK] = 0ull;
+    }
+}
+
+// the opening kick's energy rates when its P5 pass was skipped
+__global__ void k_take_next(int n, const unsigned long long *cnt, const float *__restrict__ du_next,
+                            float *__restrict__ du) {
+    if (!cnt[CNT_SKIP]) return;
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < n) du[s] = du_next[s];
+}
+
+__global__ void k_set_next_ok(unsigned long long *cnt) { cnt[CNT_NEXT_OK] = 1ull; }
+
 // dt of slot s: its box's (one box: dtb[0])
 __device__ __forceinline__ double slot_dt(const double *dtb, const int32_t *sbox, int s) {
     return dtb[sbox ? sbox[s] : 0];
@@ -361,15 +388,21 @@ static int step_impl(crk_ctx *ctx, int n, float *pos_h, float *vel_u, const floa
     const int nb = batched ? ctx->nbox : 1;
     const int32_t *sbox = batched ? ctx->sbox : nullptr;
     double *dtb = batched ? ctx->dtb : ctx->d_scalars;
+    double *dtn = batched ? ctx->dtb_next : ctx->d_scalars + 16;   // the next step's dt
+    if (fresh) CRK_CUDA(ctx, cudaMemsetAsync(ctx->counters + CNT_NEXT_OK, 0, 2 * sizeof(unsigned long long), s));
     k_pick_dt<<<grid_for(nb, 64), 64, 0, s>>>(nb, dt_req, dt_box, c.dt_max,
                                                batched ? ctx->box_dtmin : ctx->counters + CNT_DTMIN, dtb);
-    ++ctx->launches;
+    k_next_check<<<1, 256, 0, s>>>(nb, dtb, dtn, ctx->counters);
+    ctx->launches += 2;
     // first half kick with the cached rates, compatible energy of that kick
+    // (formed ahead by the previous step's dual pass when its dt matches)
     k_kick1<<<g, b, 0, s>>>(n, dtb, sbox, ctx->st_vel, ctx->acc, ctx->vb, ctx->va);
     ++ctx->launches;
     CRK_LAUNCH_CHECK(ctx, "kick");
-    rc = run_compatible(ctx, s);
+    rc = run_compatible(ctx, s, ctx->counters + CNT_SKIP);
     if (rc) return rc;
+    k_take_next<<<g, b, 0, s>>>(n, ctx->counters, ctx->du_next, ctx->du);
+    ++ctx->launches;
     k_half_drift<<<g, b, 0, s>>>(n, dtb, sbox, c, ctx->st_pos, ctx->st_vel, ctx->st_half, ctx->va, ctx->acc, ctx->du);
     ++ctx->launches;
     CRK_LAUNCH_CHECK(ctx, "drift");
@@ -400,10 +433,16 @@ static int step_impl(crk_ctx *ctx, int n, float *pos_h, float *vel_u, const floa
     // second half kick and its compatible energy (the boxes' dt of this step;
     // the permutation kept every particle in its box)
     k_kick2<<<g, b, 0, s>>>(n, dtb, sbox, ctx->st_half, ctx->acc, ctx->vb, ctx->va);
-    ++ctx->launches;
+    // the next step's dt under the same request, and both kicks' compatible
+    // energy (this closing kick, the next opening kick) in one pass
+    k_pick_dt<<<grid_for(nb, 64), 64, 0, s>>>(nb, dt_req, dt_box, c.dt_max,
+                                               batched ? ctx->box_dtmin : ctx->counters + CNT_DTMIN, dtn);
+    ctx->launches += 2;
     CRK_LAUNCH_CHECK(ctx, "kick");
-    rc = run_compatible(ctx, s);
+    rc = run_compatible_dual(ctx, dtn, sbox, s);
     if (rc) return rc;
+    k_set_next_ok<<<1, 1, 0, s>>>(ctx->counters);
+    ++ctx->launches;
     k_finish<<<g, b, 0, s>>>(n, dtb, sbox, c, ctx->st_half, ctx->va, ctx->du, ctx->Nn, ctx->hs, ctx->st_vel,
                              ctx->st_pos);
     ++ctx->launches;

@@ -462,7 +462,7 @@ __device__ __forceinline__ Sep separation(int dx, int dy, int dz) {
     s.y = (float)dy * TWO_M32;
     s.z = (float)dz * TWO_M32;
     s.r2 = fmaf(s.x, s.x, fmaf(s.y, s.y, s.z * s.z));
-    s.r = sqrtf(s.r2);
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(s.r) : "f"(s.r2));
     return s;
 }
 

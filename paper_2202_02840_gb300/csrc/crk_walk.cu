@@ -123,12 +123,7 @@ __global__ void __launch_bounds__(WALK_WARPS * 32) k_walk(WalkArgs a) {
         }
         unsigned mask = __ballot_sync(0xffffffffu, keep);
         __syncwarp();
-        while (mask) {
-            const int jj = __ffs(mask) - 1;
-            mask &= mask - 1u;
-            const uint4 qj = sq[w][jj];
-            const int dx = (int)(qi.x - qj.x), dy = (int)(qi.y - qj.y), dz = (int)(qi.z - qj.z);
-            const unsigned long long R2 = (BATCH && sb[w][jj] != bi) ? ~0ull : r2_fixed(dx, dy, dz);
+        auto visit = [&](int jj, const uint4 &qj, int dx, int dy, int dz, unsigned long long R2) {
             const bool in_i = R2 < Hi2;
             if (VOL && in_i) {
                 Sep d = separation(dx, dy, dz);
@@ -148,6 +143,29 @@ __global__ void __launch_bounds__(WALK_WARPS * 32) k_walk(WalkArgs a) {
                     co++;
                 }
             }
+        };
+        // two staged neighbours per iteration: two independent predicate
+        // chains in flight, visited in staging order (the lists are unchanged)
+        while (mask) {
+            int jj[4];
+            int cnt = 0;
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                jj[u] = mask ? __ffs(mask) - 1 : jj[0];
+                if (mask) { mask &= mask - 1u; cnt++; }
+            }
+            uint4 qq[4];
+            int dd[4][3];
+            unsigned long long RR[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                qq[u] = sq[w][jj[u]];
+                dd[u][0] = (int)(qi.x - qq[u].x); dd[u][1] = (int)(qi.y - qq[u].y); dd[u][2] = (int)(qi.z - qq[u].z);
+                RR[u] = (BATCH && sb[w][jj[u]] != bi) ? ~0ull : r2_fixed(dd[u][0], dd[u][1], dd[u][2]);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; u++)
+                if (u < cnt) visit(jj[u], qq[u], dd[u][0], dd[u][1], dd[u][2], RR[u]);
         }
     }
     const int cu = cg + co;
@@ -221,12 +239,7 @@ __global__ void __launch_bounds__(S * 32) k_walk_split(WalkArgs a) {
             }
             unsigned mask = __ballot_sync(0xffffffffu, keep);
             __syncwarp();
-            while (mask) {
-                const int jj = __ffs(mask) - 1;
-                mask &= mask - 1u;
-                const uint4 qj = sq[w][jj];
-                const int dx = (int)(qi.x - qj.x), dy = (int)(qi.y - qj.y), dz = (int)(qi.z - qj.z);
-                const unsigned long long R2 = r2_fixed(dx, dy, dz);
+            auto visit = [&](int jj, const uint4 &qj, unsigned long long R2) {
                 const uint32_t j = (uint32_t)(j0 + jj);
                 if (valid && (int)j != i) {
                     const bool in_i = R2 < Hi2;
@@ -241,6 +254,18 @@ __global__ void __launch_bounds__(S * 32) k_walk_split(WalkArgs a) {
                         co++;
                     }
                 }
+            };
+            while (mask) {   // two staged neighbours per iteration, in staging order
+                const int ja = __ffs(mask) - 1;
+                mask &= mask - 1u;
+                const bool two = mask != 0u;
+                const int jb = two ? __ffs(mask) - 1 : ja;
+                if (two) mask &= mask - 1u;
+                const uint4 qa = sq[w][ja], qb = sq[w][jb];
+                const unsigned long long Ra = r2_fixed((int)(qi.x - qa.x), (int)(qi.y - qa.y), (int)(qi.z - qa.z));
+                const unsigned long long Rb = r2_fixed((int)(qi.x - qb.x), (int)(qi.y - qb.y), (int)(qi.z - qb.z));
+                visit(ja, qa, Ra);
+                if (two) visit(jb, qb, Rb);
             }
         }
         if (phase == 0) {

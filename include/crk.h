@@ -385,9 +385,10 @@ int crk_profile_read(crk_ctx *ctx, double *ms, long long *counts, long long *tot
 /* Autotuner of the list passes (P1, P2, P3, P4, P5).  Each pass has variants
  * that differ only in how its work is laid out on the GPU: how many list
  * entries a lane takes per iteration (1-4, for the passes with small
- * neighbour records) and the order tiles are taken in (Morton order over the
+ * neighbour records), the order tiles are taken in (Morton order over the
  * grid; contiguous tile ranges per SM in a persistent launch; longest
- * pair-set list first).  Every variant visits each particle's list in the
+ * pair-set list first) and how many 32-particle tiles share a CTA (1, 2, 4
+ * or 8: 32-256 particles).  Every variant visits each particle's list in the
  * same order, so all produce bitwise identical results.  enable = 1 makes the
  * next call of each pass time every variant once (on the stream, with CUDA
  * events; the call synchronises while tuning) and keep the fastest for the
@@ -397,8 +398,9 @@ int crk_autotune(crk_ctx *ctx, int enable);
 /* The variant chosen for each pass k (CRK_PROF_NPASS entries, numbering as in
  * crk_profile_read; -1 = not tuned, the built-in default runs) and its time in
  * ms.  Variants 0-3: Morton order, 1-4 entries per iteration; 4-7: longest
- * list first, 1-4 entries; 8: per-SM tile ranges, 1 entry.  Either array may
- * be NULL. */
+ * list first, 1-4 entries; 8: per-SM tile ranges, 1 entry; 9-12: Morton order
+ * with the pass's own entries per iteration and CTAs of 1, 2, 4, 8 tiles.
+ * Either array may be NULL. */
 int crk_tuning(crk_ctx *ctx, int *variant, float *ms);
 
 /* Largest n accepted by crk_volumes_noalloc. */

@@ -325,10 +325,15 @@ __device__ __forceinline__ void merge_acc(Acc<C> &d, const Acc<C> &o) {
 enum { ORD_GRID = 0, ORD_SM = 1, ORD_LONGEST = 2 };
 struct LVariant {
     int U, ord;
+    int warps;   // tiles per CTA in the grid form (32 particles each); 0 = the pass's own
 };
-constexpr int NVAR = 9;
+// 0-3: grid, U = 1..4; 4-7: longest first, U = 1..4; 8: per-SM ranges;
+// 9-12: grid with the pass's own U and CTAs of 1, 2, 4, 8 tiles (32-256 particles)
+constexpr int NVAR = 13;
 __host__ __device__ constexpr LVariant lvariant(int v) {
-    return v < 4 ? LVariant{v + 1, ORD_GRID} : (v < 8 ? LVariant{v - 3, ORD_LONGEST} : LVariant{1, ORD_SM});
+    return v < 4 ? LVariant{v + 1, ORD_GRID, 0}
+                 : (v < 8 ? LVariant{v - 3, ORD_LONGEST, 0}
+                          : (v == 8 ? LVariant{1, ORD_SM, 0} : LVariant{0, ORD_GRID, 1 << (v - 9)}));
 }
 
 int tile_order_by_length(crk_ctx *ctx, cudaStream_t s);   // ctx->tile_order, longest pair-set list first
@@ -353,9 +358,24 @@ static void launch_variant_u(crk_ctx *ctx, const ListGeom &g, const typename P::
     }
 }
 
+template <class P, int W>
+static void launch_width(crk_ctx *ctx, const ListGeom &g, const typename P::Params &prm, cudaStream_t s) {
+    constexpr int U = P::PREFETCH ? 1 : P::UNROLL;
+    k_lpass<P, W, U><<<grid_for(ctx->ntiles, W), W * 32, 0, s>>>(g, prm, nullptr);
+}
+
 template <class P, int WARPS>
 static int launch_variant(crk_ctx *ctx, const ListGeom &g, const typename P::Params &prm, int v, cudaStream_t s) {
     const LVariant lv = lvariant(v);
+    if (lv.warps) {   // CTA width variants (the pass's own loop form)
+        switch (lv.warps) {
+        case 1: launch_width<P, 1>(ctx, g, prm, s); break;
+        case 2: launch_width<P, 2>(ctx, g, prm, s); break;
+        case 4: launch_width<P, 4>(ctx, g, prm, s); break;
+        default: launch_width<P, 8>(ctx, g, prm, s); break;
+        }
+        return CRK_OK;
+    }
     if (lv.ord == ORD_LONGEST) {
         int rc = tile_order_by_length(ctx, s);
         if (rc) return rc;
@@ -381,7 +401,7 @@ constexpr int default_variant() {
 
 template <class P>
 constexpr bool variant_applies(int v) {
-    return P::PREFETCH ? (lvariant(v).U == 1) : true;
+    return P::PREFETCH ? (lvariant(v).U <= 1) : true;
 }
 
 template <class P, int WARPS, int MINB = 1>

@@ -447,11 +447,13 @@ int run_compatible_dual(crk_ctx *ctx, const double *dtn, const int32_t *sbox, cu
     if (ctx->p.precision >= 1) {
         typename P5<true, true>::Params p{ctx->sig, ctx->Fst, ctx->mass, ctx->du, ia4, nullptr, ctx->sig2,
                                           ctx->du_next};
-        return launch_lpass<P5<true, true>, 8>(ctx, PROF_P5, p, s, "P5 compatible energy (two kicks)");
+        return launch_lpass<P5<true, true>, 8>(ctx, PROF_P5, p, s, "P5 compatible energy (two kicks)",
+                                              TUNE_P5_DUAL);
     }
     typename P5<false, true>::Params p{ctx->sig, ctx->Fst, ctx->mass, ctx->du, ia4, nullptr, ctx->sig2,
                                        ctx->du_next};
-    return launch_lpass<P5<false, true>, 8>(ctx, PROF_P5, p, s, "P5 compatible energy (two kicks)");
+    return launch_lpass<P5<false, true>, 8>(ctx, PROF_P5, p, s, "P5 compatible energy (two kicks)",
+                                              TUNE_P5_DUAL);
 }
 
 }  // namespace crk

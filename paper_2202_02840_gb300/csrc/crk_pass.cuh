@@ -404,8 +404,12 @@ constexpr bool variant_applies(int v) {
     return P::PREFETCH ? (lvariant(v).U <= 1) : true;
 }
 
+// tune_slot: the autotuner's record for this pass (default: its profiling id;
+// a pass with a different record layout, such as the two-kick P5, keeps its own)
 template <class P, int WARPS, int MINB = 1>
-int launch_lpass(crk_ctx *ctx, int prof_id, const typename P::Params &prm, cudaStream_t s, const char *what) {
+int launch_lpass(crk_ctx *ctx, int prof_id, const typename P::Params &prm, cudaStream_t s, const char *what,
+                 int tune_slot = -1) {
+    const int ts = tune_slot >= 0 ? tune_slot : prof_id;
     if (ctx->n == 0) return CRK_OK;
     if (!ctx->lists_valid) return crk_set_error(ctx, CRK_ESTATE, "%s: neighbour lists are not built", what);
     ListGeom g{ctx->n, ctx->ntiles, ctx->kcap, ctx->tbase, ctx->len_g, ctx->len_u, ctx->cnt_g, ctx->cnt_u,
@@ -429,7 +433,7 @@ int launch_lpass(crk_ctx *ctx, int prof_id, const typename P::Params &prm, cudaS
         CRK_LAUNCH_CHECK(ctx, what);
         return CRK_OK;
     }
-    if (ctx->tune_on && !ctx->tune_done[prof_id]) {
+    if (ctx->tune_on && !ctx->tune_done[ts]) {
         // time every applicable variant once (each recomputes the same outputs)
         float best = 3.0e38f;
         int bestv = default_variant<P>();
@@ -449,11 +453,11 @@ int launch_lpass(crk_ctx *ctx, int prof_id, const typename P::Params &prm, cudaS
                 bestv = v;
             }
         }
-        ctx->tune_choice[prof_id] = bestv;
-        ctx->tune_ms[prof_id] = best;
-        ctx->tune_done[prof_id] = 1;
+        ctx->tune_choice[ts] = bestv;
+        ctx->tune_ms[ts] = best;
+        ctx->tune_done[ts] = 1;
     }
-    const int v = ctx->tune_choice[prof_id] >= 0 ? ctx->tune_choice[prof_id] : default_variant<P>();
+    const int v = ctx->tune_choice[ts] >= 0 ? ctx->tune_choice[ts] : default_variant<P>();
     prof_begin(ctx, prof_id, s);
     rc = launch_variant<P, WARPS>(ctx, g, prm, v, s);
     if (rc) return rc;

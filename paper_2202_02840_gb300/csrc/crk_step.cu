@@ -688,7 +688,10 @@ static int steps_impl(crk_ctx *ctx, int n, float *pos_h, float *vel_u, const flo
         const bool fresh = !ctx->rates_valid || ctx->step_n != n || ctx->n != n || (ctx->nbox > 1) != batched;
         bool tuning = false;
         if (ctx->tune_on)
+        {
             for (int k = PROF_P1; k <= PROF_P5; k++) tuning |= (k != PROF_PN && !ctx->tune_done[k]);
+            tuning |= !ctx->tune_done[TUNE_P5_DUAL] || (ctx->p.density && !ctx->tune_done[PROF_DENS]);
+        }
         if (done == nsteps || (use_graph && !fresh && !tuning)) break;
         rc = step_impl(ctx, n, pos_h, vel_u, mass, dt, nullptr, batched, s);
         if (rc) return rc;
@@ -752,7 +755,8 @@ static int steps_impl(crk_ctx *ctx, int n, float *pos_h, float *vel_u, const flo
                 (unsigned long long)batched * 7919ull + (unsigned long long)ctx->nbox,
                 (unsigned long long)(ctx->tune_choice[PROF_P1] + 16 * ctx->tune_choice[PROF_P2] +
                                      256 * ctx->tune_choice[PROF_P3] + 4096 * ctx->tune_choice[PROF_P4] +
-                                     65536 * ctx->tune_choice[PROF_P5])};
+                                     65536 * ctx->tune_choice[PROF_P5] + 1048576 * ctx->tune_choice[TUNE_P5_DUAL] +
+                                     16777216 * ctx->tune_choice[PROF_DENS])};
             for (unsigned long long v : parts) key = fnv(key, v);
             if (!eager && (!ctx->gexec[p] || ctx->gkey[p] != key)) {
                 // capturing runs the step's host logic (its buffer rotation) but not its kernels

@@ -335,10 +335,12 @@ struct P5 {
         merge_acc(s.du, o.du);
         if (DUAL) merge_acc(s.du2, o.du2);
     }
-    // the stored entry carries j (written by P4): the list itself is not read
+    // the stored entry carries j (written by P4): the list itself is not read,
+    // and the stored (F_ij, j) are what streams from HBM (read ahead)
     static constexpr bool ENTRIES = false;
-    __device__ static Rec load(uint32_t, size_t pos, const Params &p) {
-        const float4 F = __ldg(p.Fst + pos);
+    using Stored = float4;
+    __device__ static Stored stored(size_t pos, const Params &p) { return __ldg(p.Fst + pos); }
+    __device__ static Rec load(const float4 &F, size_t, const Params &p) {
         const uint32_t j = __float_as_uint(F.w);
         Rec r;
         r.sig = __ldg(p.sig + j);
@@ -346,7 +348,7 @@ struct P5 {
         r.F = F;
         return r;
     }
-    __device__ static void pair(IState &s, const Rec &rec, uint32_t, size_t, bool, const Params &) {
+    __device__ static void pair(IState &s, const Rec &rec, const float4 &, size_t, bool, const Params &) {
         s.du.add(compat_term(s.me, rec.sig, rec.F));
         if (DUAL) s.du2.add(compat_term(s.me2, rec.sig2, rec.F));
     }

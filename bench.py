@@ -37,7 +37,7 @@ WORKLOAD = "zeldovich-128^3: clustered gas, Zel'dovich lattice displacement, P(k
 # div/sqrt/exp = 1), counted from the operations the paper's formulas require
 # (derivation in the design doc).  P1-P3 count per gather pair; P4 and P5 count per
 # UNORDERED pair of the pair set (both kernel sides, limiter, viscosity, force).
-FLOPS_PER_UNIT = {"P1 volumes": 20, "P2 corrections": 110, "P3 grad v": 92, "P4 forces": 281,
+FLOPS_PER_UNIT = {"P1 volumes": 20, "P2 corrections": 88, "P3 grad v": 92, "P4 forces": 281,
                   "P5 compatible energy": 259}
 # DRAM bytes (read + write) per unit measured by ncu for the current P4 kernel on
 # zeldovich-64^3 in the Hilbert order (0.65 GB read + 1.20 GB written for

@@ -87,6 +87,14 @@ __host__ __device__ constexpr int sym(int a, int b) {
     return a <= b ? (a == 0 ? b : (a == 1 ? 2 + b : 5)) : (b == 0 ? a : (b == 1 ? 2 + a : 5));
 }
 
+// symmetric index of (a,b,c): xxx, xxy, xxz, xyy, xyz, xzz, yyy, yyz, yzz, zzz
+__host__ __device__ constexpr int sym3(int a, int b, int c) {
+    const int lo = a < b ? (a < c ? a : c) : (b < c ? b : c);
+    const int hi = a > b ? (a > c ? a : c) : (b > c ? b : c);
+    const int mid = a + b + c - lo - hi;
+    return lo == 0 ? (mid == 0 ? hi : (mid == 1 ? 2 + hi : 5)) : (lo == 1 ? (mid == 1 ? 5 + hi : 8) : 9);
+}
+
 // Solve the RK coefficients from the moments (derived from the two moment
 // conditions of Sec. 1.2):  B = -m2^-1 m1, A = 1/(m0 + m1.B),
 // d_g B = -m2^-1 (d_g m1 + (d_g m2) B), d_g A = -A^2 (d_g m0 + B.d_g m1 + m1.d_g B).
@@ -165,7 +173,9 @@ struct P2 {
     struct IState {
         uint4 q;
         float h, inv_h;
-        Acc<COMP> m0, m1[3], m2[6], dm0[3], s1[9], s2[18];
+        // s1 = sum V x^a x^g Gu and s2 = sum V x^a x^b x^g Gu are symmetric
+        // tensors: only their distinct components are summed
+        Acc<COMP> m0, m1[3], m2[6], dm0[3], s1[6], s2[10];
     };
     __device__ static void init(IState &s, int i, bool valid, const Params &p) {
         s.q = valid ? p.q4[i] : make_uint4(0, 0, 0, 0);
@@ -177,9 +187,9 @@ struct P2 {
 #pragma unroll
         for (int a = 0; a < 6; a++) s.m2[a] = Acc<COMP>();
 #pragma unroll
-        for (int a = 0; a < 9; a++) s.s1[a] = Acc<COMP>();
+        for (int a = 0; a < 6; a++) s.s1[a] = Acc<COMP>();
 #pragma unroll
-        for (int a = 0; a < 18; a++) s.s2[a] = Acc<COMP>();
+        for (int a = 0; a < 10; a++) s.s2[a] = Acc<COMP>();
         // self term of gather(i): x = 0, W(0) (unnormalised 1), grad W(0) = 0
         if (valid) s.m0.add(__uint_as_float(__ldg(&p.qV[i].w)));
     }
@@ -187,8 +197,8 @@ struct P2 {
         s.m0 = Acc<COMP>();
         for (int a = 0; a < 3; a++) s.m1[a] = s.dm0[a] = Acc<COMP>();
         for (int a = 0; a < 6; a++) s.m2[a] = Acc<COMP>();
-        for (int a = 0; a < 9; a++) s.s1[a] = Acc<COMP>();
-        for (int a = 0; a < 18; a++) s.s2[a] = Acc<COMP>();
+        for (int a = 0; a < 6; a++) s.s1[a] = Acc<COMP>();
+        for (int a = 0; a < 10; a++) s.s2[a] = Acc<COMP>();
     }
     __device__ static void merge(IState &s, const IState &o) {
         merge_acc(s.m0, o.m0);
@@ -197,8 +207,8 @@ struct P2 {
             merge_acc(s.dm0[a], o.dm0[a]);
         }
         for (int a = 0; a < 6; a++) merge_acc(s.m2[a], o.m2[a]);
-        for (int a = 0; a < 9; a++) merge_acc(s.s1[a], o.s1[a]);
-        for (int a = 0; a < 18; a++) merge_acc(s.s2[a], o.s2[a]);
+        for (int a = 0; a < 6; a++) merge_acc(s.s1[a], o.s1[a]);
+        for (int a = 0; a < 10; a++) merge_acc(s.s2[a], o.s2[a]);
     }
     __device__ static Rec load(uint32_t e, size_t, const Params &p) { return __ldg(p.qV + (e & 0x3fffffffu)); }
     __device__ static void pair(IState &s, const Rec &r, uint32_t, size_t, bool, const Params &) {
@@ -225,11 +235,11 @@ struct P2 {
 #pragma unroll
         for (int a = 0; a < 3; a++)
 #pragma unroll
-            for (int gg = 0; gg < 3; gg++) s.s1[3 * a + gg].add(x[a] * gx[gg]);
+            for (int b = a; b < 3; b++) {
+                s.s1[sym(a, b)].add(x[a] * gx[b]);
 #pragma unroll
-        for (int q = 0; q < 6; q++)
-#pragma unroll
-            for (int gg = 0; gg < 3; gg++) s.s2[3 * q + gg].add(xx[q] * gx[gg]);
+                for (int gg = b; gg < 3; gg++) s.s2[sym3(a, b, gg)].add(xx[sym(a, b)] * gx[gg]);
+            }
     }
     // Moments from the pair sums: W-type sums scale by cW = 495/(32 pi h^3),
     // gradient sums by cG = 1155/(4 pi h^5); then
@@ -255,7 +265,7 @@ struct P2 {
 #pragma unroll
         for (int a = 0; a < 3; a++)
 #pragma unroll
-            for (int g = 0; g < 3; g++) dm1[3 * a + g] = cG * val(s.s1[3 * a + g]) + (a == g ? m0 : (T)0);
+            for (int g = 0; g < 3; g++) dm1[3 * a + g] = cG * val(s.s1[sym(a, g)]) + (a == g ? m0 : (T)0);
 #pragma unroll
         for (int a = 0; a < 3; a++)
 #pragma unroll
@@ -263,7 +273,7 @@ struct P2 {
 #pragma unroll
                 for (int g = 0; g < 3; g++) {
                     int q = sym(a, b);
-                    T v = cG * val(s.s2[3 * q + g]);
+                    T v = cG * val(s.s2[sym3(a, b, g)]);
                     if (a == g) v += m1[b];
                     if (b == g) v += m1[a];
                     dm2[3 * q + g] = v;

@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(WALK_WARPS * 32) k_walk(WalkArgs a) {
                 }
             }
         };
-        // two staged neighbours per iteration: two independent predicate
+        // four staged neighbours per iteration: four independent predicate
         // chains in flight, visited in staging order (the lists are unchanged)
         while (mask) {
             int jj[4];

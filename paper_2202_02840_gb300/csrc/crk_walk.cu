@@ -123,49 +123,73 @@ __global__ void __launch_bounds__(WALK_WARPS * 32) k_walk(WalkArgs a) {
         }
         unsigned mask = __ballot_sync(0xffffffffu, keep);
         __syncwarp();
-        auto visit = [&](int jj, const uint4 &qj, int dx, int dy, int dz, unsigned long long R2) {
-            const bool in_i = R2 < Hi2;
-            if (VOL && in_i) {
-                Sep d = separation(dx, dy, dz);
-                float eta = d.r * inv_h;
-                float tt = fmaxf(1.f - eta, 0.f);
-                float t2 = tt * tt, t3 = t2 * tt;
-                acc = fmaf(t3 * t3, fmaf(eta, fmaf(eta, K35_3, 6.f), 1.f), acc);
-            }
-            const uint32_t j = (uint32_t)(j0 + jj);
-            if (LISTS && valid && (int)j != i) {
-                const bool in_j = R2 < (unsigned long long)qj.w * qj.w;
-                if (in_i) {
-                    if (cg < kcap) col0[(size_t)cg * 32] = j | (in_j ? 0x80000000u : 0u);
-                    cg++;
-                } else if (in_j) {
-                    if (co < kcap) col0[(size_t)(kcap - 1 - co) * 32] = j;
-                    co++;
+        // four staged particles per iteration: four independent predicate
+        // chains in flight
+        auto staged4 = [&](auto &&visit) {
+            while (mask) {
+                int jj[4];
+                int cnt = 0;
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    jj[u] = mask ? __ffs(mask) - 1 : jj[0];
+                    if (mask) { mask &= mask - 1u; cnt++; }
                 }
+                uint4 qq[4];
+                int dd[4][3];
+                unsigned long long RR[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    qq[u] = sq[w][jj[u]];
+                    dd[u][0] = (int)(qi.x - qq[u].x); dd[u][1] = (int)(qi.y - qq[u].y); dd[u][2] = (int)(qi.z - qq[u].z);
+                    RR[u] = (BATCH && sb[w][jj[u]] != bi) ? ~0ull : r2_fixed(dd[u][0], dd[u][1], dd[u][2]);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; u++)
+                    if (u < cnt) visit(jj[u], qq[u], dd[u][0], dd[u][1], dd[u][2], RR[u]);
             }
         };
-        // four staged neighbours per iteration: four independent predicate
-        // chains in flight, visited in staging order (the lists are unchanged)
-        while (mask) {
-            int jj[4];
-            int cnt = 0;
-#pragma unroll
-            for (int u = 0; u < 4; u++) {
-                jj[u] = mask ? __ffs(mask) - 1 : jj[0];
-                if (mask) { mask &= mask - 1u; cnt++; }
+        if constexpr (LISTS) {
+            // test phase: the exact predicate of every kept staged particle
+            // sets this lane's bits (gather, other pair-set, "j reaches i");
+            // write phase: each lane writes only its own entries, in staging
+            // order, so the list-writing code runs once per entry rather than
+            // once per staged particle
+            unsigned gm = 0u, om = 0u, jm = 0u;
+            staged4([&](int jj, const uint4 &qj, int, int, int, unsigned long long R2) {
+                const bool in_i = R2 < Hi2;
+                const bool in_j = R2 < (unsigned long long)qj.w * qj.w;
+                const unsigned b = 1u << jj;
+                gm |= in_i ? b : 0u;
+                om |= (!in_i && in_j) ? b : 0u;
+                jm |= in_j ? b : 0u;
+            });
+            if (!valid) gm = om = 0u;
+            if (J == tile) {   // j != i
+                gm &= ~(1u << lane);
+                om &= ~(1u << lane);
             }
-            uint4 qq[4];
-            int dd[4][3];
-            unsigned long long RR[4];
-#pragma unroll
-            for (int u = 0; u < 4; u++) {
-                qq[u] = sq[w][jj[u]];
-                dd[u][0] = (int)(qi.x - qq[u].x); dd[u][1] = (int)(qi.y - qq[u].y); dd[u][2] = (int)(qi.z - qq[u].z);
-                RR[u] = (BATCH && sb[w][jj[u]] != bi) ? ~0ull : r2_fixed(dd[u][0], dd[u][1], dd[u][2]);
+            while (gm) {
+                const int jj = __ffs(gm) - 1;
+                gm &= gm - 1u;
+                if (cg < kcap) col0[(size_t)cg * 32] = (uint32_t)(j0 + jj) | (((jm >> jj) & 1u) << 31);
+                cg++;
             }
-#pragma unroll
-            for (int u = 0; u < 4; u++)
-                if (u < cnt) visit(jj[u], qq[u], dd[u][0], dd[u][1], dd[u][2], RR[u]);
+            while (om) {
+                const int jj = __ffs(om) - 1;
+                om &= om - 1u;
+                if (co < kcap) col0[(size_t)(kcap - 1 - co) * 32] = (uint32_t)(j0 + jj);
+                co++;
+            }
+        } else {
+            staged4([&](int, const uint4 &, int dx, int dy, int dz, unsigned long long R2) {
+                if (VOL && R2 < Hi2) {
+                    Sep d = separation(dx, dy, dz);
+                    float eta = d.r * inv_h;
+                    float tt = fmaxf(1.f - eta, 0.f);
+                    float t2 = tt * tt, t3 = t2 * tt;
+                    acc = fmaf(t3 * t3, fmaf(eta, fmaf(eta, K35_3, 6.f), 1.f), acc);
+                }
+            });
         }
     }
     const int cu = cg + co;

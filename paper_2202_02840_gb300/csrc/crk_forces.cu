@@ -284,17 +284,35 @@ struct P4 {
 // skip (may be null): a device flag set when the sums of this pass were
 // already formed by the previous step's dual pass; the pass then reads
 // nothing (the caller takes those sums).
-__device__ __forceinline__ float compat_term(const float4 me, const float4 r, const float4 F) {
-    // 2 Delta E_ij = (v_j + v'_j - v_i - v'_i) . F_ij  (reading of eq:Eij)
-    float w = fmaf(r.x - me.x, F.x, fmaf(r.y - me.y, F.y, (r.z - me.z) * F.z));
-    // eq:fij
-    float si = me.w, sj = r.w, ss = si + sj;
-    float f = 0.5f;
+// The partition of eq:fij for one pair: f = min(s_i, s_j)/(s_i + s_j) when
+// the pair's work and s_i - s_j have the same sign, else max/(s_i + s_j)
+// (1/2 when both vanish).  It depends on the pair's entropies only, so the
+// two-kick pass forms it once for both kicks.
+struct Part {
+    float fmn, fmx;
+    bool ige;   // s_i >= s_j
+};
+
+__device__ __forceinline__ Part partition(float si, float sj) {
+    Part p;
+    p.ige = si >= sj;
+    const float ss = si + sj;
     if (ss != 0.f) {
-        bool take_min = (w >= 0.f) == (si >= sj);
-        f = (take_min ? fminf(si, sj) : fmaxf(si, sj)) / ss;
+        const float r = __fdividef(1.f, ss);
+        p.fmn = fminf(si, sj) * r;
+        p.fmx = fmaxf(si, sj) * r;
+    } else {
+        p.fmn = p.fmx = 0.5f;
     }
-    return 0.5f * f * w;
+    return p;
+}
+
+// 2 Delta E_ij = (v_j + v'_j - v_i - v'_i) . F_ij  (reading of eq:Eij); this
+// returns f 2 Delta E_ij, the factor 1/2 being applied to the finished sum
+// (an exact scaling)
+__device__ __forceinline__ float compat_term(const float4 me, const float4 r, const float4 F, const Part &p) {
+    float w = fmaf(r.x - me.x, F.x, fmaf(r.y - me.y, F.y, (r.z - me.z) * F.z));
+    return (((w >= 0.f) == p.ige) ? p.fmn : p.fmx) * w;
 }
 
 template <bool COMP, bool DUAL = false>
@@ -349,13 +367,14 @@ struct P5 {
         return r;
     }
     __device__ static void pair(IState &s, const Rec &rec, const float4 &, size_t, bool, const Params &) {
-        s.du.add(compat_term(s.me, rec.sig, rec.F));
-        if (DUAL) s.du2.add(compat_term(s.me2, rec.sig2, rec.F));
+        const Part pt = partition(s.me.w, rec.sig.w);   // both kicks: s of the evaluation state
+        s.du.add(compat_term(s.me, rec.sig, rec.F, pt));
+        if (DUAL) s.du2.add(compat_term(s.me2, rec.sig2, rec.F, pt));
     }
     // eq:compEng2: 1/(2 a^4) (p_j + p'_j - p_i - p'_i) . dp_ij/dt
     __device__ static void finish(IState &s, int i, const Params &p) {
-        p.du[i] = s.du.value() / s.m * p.inv_a4;
-        if (DUAL) p.du2[i] = s.du2.value() / s.m * p.inv_a4;
+        p.du[i] = 0.5f * s.du.value() / s.m * p.inv_a4;
+        if (DUAL) p.du2[i] = 0.5f * s.du2.value() / s.m * p.inv_a4;
     }
 };
 

@@ -92,7 +92,7 @@ int crk_ensure_particles(crk_ctx *ctx, int n) {
     rc |= dalloc(ctx, &ctx->frec, 10 * (size_t)cap);
     rc |= dalloc(ctx, &ctx->sfun, cap);
     rc |= dalloc(ctx, &ctx->sig, cap);
-    rc |= dalloc(ctx, &ctx->sig2, cap);
+    rc |= dalloc(ctx, &ctx->sig2, 2 * (size_t)cap);   // two kicks' sums side by side
     rc |= dalloc(ctx, &ctx->du_next, cap);
     rc |= dalloc(ctx, &ctx->node_lo, 2 * (size_t)tiles + MAX_LEVELS);
     rc |= dalloc(ctx, &ctx->node_hi, 2 * (size_t)tiles + MAX_LEVELS);

@@ -180,14 +180,6 @@ __global__ void k_pack_frec(int n, FSrc src, FParams fp, FRec *__restrict__ out,
     sfun[i] = r.w2.x / powf(r.w2.y, fp.gamma);       // s = P / rho^gamma (eq:fij)
 }
 
-// Two float4 of a record in one 256-bit read-only load (every pair of its
-// float4 starts on a 32-byte boundary): one L1 sector per lane per instruction.
-__device__ __forceinline__ void ldg_v8(const float4 *p, float4 &a, float4 &b) {
-    asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-        : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
-        : "l"(p));
-}
-
 __device__ __forceinline__ FRec ldg_frec(const FRec *p) {
     const float4 *q = reinterpret_cast<const float4 *>(p);
     FRec r;
@@ -326,13 +318,12 @@ struct P5 {
         float4 sig, sig2, F;
     };
     struct Params {
-        const float4 *sig;
+        const float4 *sig;    // one kick: sig per particle; two kicks: (sig, sig2) side by side
         const float4 *Fst;
         const float *mass;
         float *du;
         float inv_a4;
         const unsigned long long *skip;
-        const float4 *sig2;
         float *du2;
     };
     struct IState {
@@ -341,8 +332,9 @@ struct P5 {
         Acc<COMP> du, du2;
     };
     __device__ static void init(IState &s, int i, bool valid, const Params &p) {
-        s.me = valid ? p.sig[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-        if (DUAL) s.me2 = valid ? p.sig2[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+        s.me = valid ? p.sig[DUAL ? 2 * (size_t)i : (size_t)i] : z;
+        if (DUAL) s.me2 = valid ? p.sig[2 * (size_t)i + 1] : z;
         s.m = valid ? p.mass[i] : 1.f;
     }
     __device__ static void zero(IState &s) {
@@ -361,8 +353,10 @@ struct P5 {
     __device__ static Rec load(const float4 &F, size_t, const Params &p) {
         const uint32_t j = __float_as_uint(F.w);
         Rec r;
-        r.sig = __ldg(p.sig + j);
-        if (DUAL) r.sig2 = __ldg(p.sig2 + j);
+        if (DUAL)
+            ldg_v8(p.sig + 2 * (size_t)j, r.sig, r.sig2);   // both kicks' sums in one 256-bit load
+        else
+            r.sig = __ldg(p.sig + j);
         r.F = F;
         return r;
     }
@@ -437,42 +431,43 @@ int run_compatible(crk_ctx *ctx, cudaStream_t s, const unsigned long long *skip)
     CRK_LAUNCH_CHECK(ctx, "kick sums");
     const float ia4 = (float)(1.0 / (ctx->p.a * ctx->p.a * ctx->p.a * ctx->p.a));
     if (ctx->p.precision >= 1) {
-        typename P5<true>::Params p{ctx->sig, ctx->Fst, ctx->mass, ctx->du, ia4, skip, nullptr, nullptr};
+        typename P5<true>::Params p{ctx->sig, ctx->Fst, ctx->mass, ctx->du, ia4, skip, nullptr};
         return launch_lpass<P5<true>, 8>(ctx, PROF_P5, p, s, "P5 compatible energy");
     }
-    typename P5<false>::Params p{ctx->sig, ctx->Fst, ctx->mass, ctx->du, ia4, skip, nullptr, nullptr};
+    typename P5<false>::Params p{ctx->sig, ctx->Fst, ctx->mass, ctx->du, ia4, skip, nullptr};
     return launch_lpass<P5<false>, 8>(ctx, PROF_P5, p, s, "P5 compatible energy");
 }
 
-// kick sums of the next step's opening kick: vb = p1 (= va of this closing
-// kick), va = p1 + a dt'/2 with the next step's dt (as k_kick1 will form them)
-__global__ void k_sig_next(int n, const double *dtn, const int32_t *__restrict__ sbox, const float4 *__restrict__ va,
+// kick sums of this closing kick (vb -> va) and of the next step's opening
+// kick (vb' = p1 = va, va' = p1 + a dt'/2 with the next step's dt, as k_kick1
+// will form them), side by side: sig2[2i] = sig_i, sig2[2i+1] = sig'_i
+__global__ void k_sig_dual(int n, const double *dtn, const int32_t *__restrict__ sbox,
+                           const float4 *__restrict__ vb, const float4 *__restrict__ va,
                            const float4 *__restrict__ acc, const float *__restrict__ sfun, float4 *__restrict__ sig2) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     float h = (float)(0.5 * dtn[sbox ? sbox[i] : 0]);
-    float4 v = va[i], a = acc[i];
-    sig2[i] = make_float4(v.x + fmaf(h, a.x, v.x), v.y + fmaf(h, a.y, v.y), v.z + fmaf(h, a.z, v.z), sfun[i]);
+    float4 b = vb[i], v = va[i], a = acc[i];
+    const float sf = sfun[i];
+    sig2[2 * (size_t)i] = make_float4(b.x + v.x, b.y + v.y, b.z + v.z, sf);
+    sig2[2 * (size_t)i + 1] = make_float4(v.x + fmaf(h, a.x, v.x), v.y + fmaf(h, a.y, v.y), v.z + fmaf(h, a.z, v.z), sf);
 }
 
 // P5 of this closing kick (vb -> va into du) and of the next step's opening
 // kick (its dt per box in dtn; into du_next) in one pass over the stored forces.
 int run_compatible_dual(crk_ctx *ctx, const double *dtn, const int32_t *sbox, cudaStream_t s) {
     if (ctx->n == 0) return CRK_OK;
-    const int g = grid_for(ctx->n, 256);
-    k_sig<<<g, 256, 0, s>>>(ctx->n, ctx->vb, ctx->va, ctx->sfun, ctx->sig);
-    k_sig_next<<<g, 256, 0, s>>>(ctx->n, dtn, sbox, ctx->va, ctx->acc, ctx->sfun, ctx->sig2);
-    ctx->launches += 2;
+    k_sig_dual<<<grid_for(ctx->n, 256), 256, 0, s>>>(ctx->n, dtn, sbox, ctx->vb, ctx->va, ctx->acc, ctx->sfun,
+                                                      ctx->sig2);
+    ++ctx->launches;
     CRK_LAUNCH_CHECK(ctx, "kick sums");
     const float ia4 = (float)(1.0 / (ctx->p.a * ctx->p.a * ctx->p.a * ctx->p.a));
     if (ctx->p.precision >= 1) {
-        typename P5<true, true>::Params p{ctx->sig, ctx->Fst, ctx->mass, ctx->du, ia4, nullptr, ctx->sig2,
-                                          ctx->du_next};
+        typename P5<true, true>::Params p{ctx->sig2, ctx->Fst, ctx->mass, ctx->du, ia4, nullptr, ctx->du_next};
         return launch_lpass<P5<true, true>, 8>(ctx, PROF_P5, p, s, "P5 compatible energy (two kicks)",
                                               TUNE_P5_DUAL);
     }
-    typename P5<false, true>::Params p{ctx->sig, ctx->Fst, ctx->mass, ctx->du, ia4, nullptr, ctx->sig2,
-                                       ctx->du_next};
+    typename P5<false, true>::Params p{ctx->sig2, ctx->Fst, ctx->mass, ctx->du, ia4, nullptr, ctx->du_next};
     return launch_lpass<P5<false, true>, 8>(ctx, PROF_P5, p, s, "P5 compatible energy (two kicks)",
                                               TUNE_P5_DUAL);
 }

@@ -125,7 +125,7 @@ struct crk_ctx {
     float4 *frec = nullptr;          // packed pair-set records, 10 float4 (160 B) per particle
     float *sfun = nullptr;           // specific entropy of the evaluation state
     float4 *sig = nullptr;           // (v + v') of a kick, s
-    float4 *sig2 = nullptr;          // the same for the next step's opening kick
+    float4 *sig2 = nullptr;          // two kicks (closing, next opening): sig side by side, 2 per particle
     float *du_next = nullptr;        // the next step's opening-kick energy rate (formed ahead)
     double *dtb_next = nullptr;      // the next step's dt per box (batched; one box uses d_scalars[16])
 

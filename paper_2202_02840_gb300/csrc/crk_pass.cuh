@@ -489,6 +489,14 @@ constexpr float KW = 4.9238560f;       // 495 / (32 pi)
 constexpr float KG = 91.9120344f;      // 1155 / (4 pi)
 constexpr float K35_3 = 11.6666667f;   // 35 / 3
 
+// Two float4 of a record in one 256-bit read-only load (p on a 32-byte
+// boundary): one L1 sector per lane per instruction.
+__device__ __forceinline__ void ldg_v8(const float4 *p, float4 &a, float4 &b) {
+    asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+        : "l"(p));
+}
+
 struct Sep {
     float x, y, z, r2, r;
 };

@@ -399,8 +399,10 @@ int crk_autotune(crk_ctx *ctx, int enable);
  * crk_profile_read; -1 = not tuned, the built-in default runs) and its time in
  * ms.  Variants 0-3: Morton order, 1-4 entries per iteration; 4-7: longest
  * list first, 1-4 entries; 8: per-SM tile ranges, 1 entry; 9-12: Morton order
- * with the pass's own entries per iteration and CTAs of 1, 2, 4, 8 tiles.
- * Either array may be NULL. */
+ * with the pass's own entries per iteration and CTAs of 1, 2, 4, 8 tiles;
+ * 13-16: 1-4 entries per iteration with the neighbour records of the next
+ * iteration read ahead, CTAs of one tile; 17-20: the same with the pass's own
+ * CTA width (13-20 for the gather passes only).  Either array may be NULL. */
 int crk_tuning(crk_ctx *ctx, int *variant, float *ms);
 
 /* Largest n accepted by crk_volumes_noalloc. */

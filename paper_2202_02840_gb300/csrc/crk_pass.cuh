@@ -184,7 +184,43 @@ __device__ __forceinline__ void list_loop(typename P::IState &st, const typename
     }
 }
 
-template <class P, int U>
+// list_loop with the neighbour records one iteration ahead as well (RP
+// variants): at iteration k the records of iteration k + 1 and the entries of
+// iteration k + 2 are in flight while the U pairs of iteration k are
+// evaluated, so a record that misses L1 is waited for only if it takes longer
+// than a whole iteration.  Same entries, same order: bitwise the same sums.
+template <class P, int U, class EntryFn>
+__device__ __forceinline__ void list_loop_rp(typename P::IState &st, const typename P::Params &prm, EntryFn entry,
+                                             size_t fb, int mg, int k0, int k1, int mk) {
+    uint32_t ec[U] = {}, en[U] = {};
+    typename P::Rec rc[U] = {}, rn[U] = {};
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+        if (k0 + u < mk) ec[u] = entry(k0 + u);
+        if (k0 + U + u < mk) en[u] = entry(k0 + U + u);
+    }
+#pragma unroll
+    for (int u = 0; u < U; u++)
+        if (k0 + u < mk) rc[u] = P::load(ec[u], fb + (size_t)(k0 + u) * 32, prm);
+    for (int k = k0; k < k1; k += U) {
+        uint32_t eu[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            if (k + U + u < mk) rn[u] = P::load(en[u], fb + (size_t)(k + U + u) * 32, prm);
+            eu[u] = ec[u];
+            ec[u] = en[u];
+            if (k + 2 * U + u < mk) en[u] = entry(k + 2 * U + u);
+        }
+        const size_t pos = fb + (size_t)k * 32;
+#pragma unroll
+        for (int u = 0; u < U; u++)
+            if (k + u < mk) P::pair(st, rc[u], eu[u], pos + 32 * u, k + u < mg, prm);
+#pragma unroll
+        for (int u = 0; u < U; u++) rc[u] = rn[u];
+    }
+}
+
+template <class P, int U, bool RP = false>
 __device__ __forceinline__ void lpass_tile(const ListGeom &g, const typename P::Params &prm, int tile, int lane) {
     if (pass_skipped<P>(prm)) return;   // the sums were formed by an earlier pass
     const int i = tile * TILE + lane;
@@ -204,7 +240,10 @@ __device__ __forceinline__ void lpass_tile(const ListGeom &g, const typename P::
         return __ldg(col0 + (size_t)c * 32);
     };
     if constexpr (!P::PREFETCH) {
-        list_loop<P, U>(st, prm, entry, fb, mg, 0, len, my);
+        if constexpr (RP)
+            list_loop_rp<P, U>(st, prm, entry, fb, mg, 0, len, my);
+        else
+            list_loop<P, U>(st, prm, entry, fb, mg, 0, len, my);
     } else {
         // two pairs per iteration: the record in flight alternates between
         // two register sets, so no record is copied from one to the other
@@ -235,12 +274,12 @@ __device__ __forceinline__ void lpass_tile(const ListGeom &g, const typename P::
 
 // Grid form: warp w of block b takes tile order[b WARPS + w] (order null:
 // tiles in Morton order).
-template <class P, int WARPS, int U>
+template <class P, int WARPS, int U, bool RP = false>
 __global__ void __launch_bounds__(WARPS * 32) k_lpass(ListGeom g, typename P::Params prm, const int32_t *order) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int t = blockIdx.x * WARPS + w;
     if (t >= g.ntiles) return;
-    lpass_tile<P, U>(g, prm, order ? order[t] : t, lane);
+    lpass_tile<P, U, RP>(g, prm, order ? order[t] : t, lane);
 }
 
 // Persistent form (one warp per block, as many blocks as fit at once): SM s
@@ -339,14 +378,21 @@ enum { ORD_GRID = 0, ORD_SM = 1, ORD_LONGEST = 2 };
 struct LVariant {
     int U, ord;
     int warps;   // tiles per CTA in the grid form (32 particles each); 0 = the pass's own
+    bool rp;     // records one iteration ahead (list_loop_rp)
 };
 // 0-3: grid, U = 1..4; 4-7: longest first, U = 1..4; 8: per-SM ranges;
-// 9-12: grid with the pass's own U and CTAs of 1, 2, 4, 8 tiles (32-256 particles)
-constexpr int NVAR = 13;
+// 9-12: grid with the pass's own U and CTAs of 1, 2, 4, 8 tiles (32-256 particles);
+// 13-16: grid, U = 1..4, records one iteration ahead, CTAs of one tile;
+// 17-20: the same with the pass's own CTA width (passes that read list entries,
+// without their own record prefetch)
+constexpr int NVAR = 21;
 __host__ __device__ constexpr LVariant lvariant(int v) {
-    return v < 4 ? LVariant{v + 1, ORD_GRID, 0}
-                 : (v < 8 ? LVariant{v - 3, ORD_LONGEST, 0}
-                          : (v == 8 ? LVariant{1, ORD_SM, 0} : LVariant{0, ORD_GRID, 1 << (v - 9)}));
+    return v < 4 ? LVariant{v + 1, ORD_GRID, 0, false}
+                 : (v < 8 ? LVariant{v - 3, ORD_LONGEST, 0, false}
+                          : (v == 8 ? LVariant{1, ORD_SM, 0, false}
+                                    : (v < 13 ? LVariant{0, ORD_GRID, 1 << (v - 9), false}
+                                              : (v < 17 ? LVariant{v - 12, ORD_GRID, 1, true}
+                                                        : LVariant{v - 16, ORD_GRID, 0, true}))));
 }
 
 int tile_order_by_length(crk_ctx *ctx, cudaStream_t s);   // ctx->tile_order, longest pair-set list first
@@ -377,9 +423,33 @@ static void launch_width(crk_ctx *ctx, const ListGeom &g, const typename P::Para
     k_lpass<P, W, U><<<grid_for(ctx->ntiles, W), W * 32, 0, s>>>(g, prm, nullptr);
 }
 
+template <class P, int W, int U>
+static void launch_rp(crk_ctx *ctx, const ListGeom &g, const typename P::Params &prm, cudaStream_t s) {
+    k_lpass<P, W, U, true><<<grid_for(ctx->ntiles, W), W * 32, 0, s>>>(g, prm, nullptr);
+}
+
+template <class P, int W>
+static void launch_rp_u(crk_ctx *ctx, const ListGeom &g, const typename P::Params &prm, int U, cudaStream_t s) {
+    switch (U) {
+    case 1: launch_rp<P, W, 1>(ctx, g, prm, s); break;
+    case 2: launch_rp<P, W, 2>(ctx, g, prm, s); break;
+    case 3: launch_rp<P, W, 3>(ctx, g, prm, s); break;
+    default: launch_rp<P, W, 4>(ctx, g, prm, s); break;
+    }
+}
+
 template <class P, int WARPS>
 static int launch_variant(crk_ctx *ctx, const ListGeom &g, const typename P::Params &prm, int v, cudaStream_t s) {
     const LVariant lv = lvariant(v);
+    if (lv.rp) {   // records one iteration ahead (passes with entries, no own prefetch)
+        if constexpr (P::ENTRIES && !P::PREFETCH) {
+            if (lv.warps == 1)
+                launch_rp_u<P, 1>(ctx, g, prm, lv.U, s);
+            else
+                launch_rp_u<P, WARPS>(ctx, g, prm, lv.U, s);
+        }
+        return CRK_OK;
+    }
     if (lv.warps) {   // CTA width variants (the pass's own loop form)
         switch (lv.warps) {
         case 1: launch_width<P, 1>(ctx, g, prm, s); break;
@@ -414,6 +484,7 @@ constexpr int default_variant() {
 
 template <class P>
 constexpr bool variant_applies(int v) {
+    if (lvariant(v).rp) return P::ENTRIES && !P::PREFETCH;
     return P::PREFETCH ? (lvariant(v).U <= 1) : true;
 }
 

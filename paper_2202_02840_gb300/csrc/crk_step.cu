@@ -752,12 +752,10 @@ static int steps_impl(crk_ctx *ctx, int n, float *pos_h, float *vel_u, const flo
                 (unsigned long long)n, (unsigned long long)(uintptr_t)pos_h, (unsigned long long)(uintptr_t)vel_u,
                 (unsigned long long)(uintptr_t)mass, ctx->alloc_gen, (unsigned long long)ctx->kcap,
                 (unsigned long long)ctx->cap_ulist, (unsigned long long)(uintptr_t)ctx->st_pos, dtbits,
-                (unsigned long long)batched * 7919ull + (unsigned long long)ctx->nbox,
-                (unsigned long long)(ctx->tune_choice[PROF_P1] + 16 * ctx->tune_choice[PROF_P2] +
-                                     256 * ctx->tune_choice[PROF_P3] + 4096 * ctx->tune_choice[PROF_P4] +
-                                     65536 * ctx->tune_choice[PROF_P5] + 1048576 * ctx->tune_choice[TUNE_P5_DUAL] +
-                                     16777216 * ctx->tune_choice[PROF_DENS])};
+                (unsigned long long)batched * 7919ull + (unsigned long long)ctx->nbox};
             for (unsigned long long v : parts) key = fnv(key, v);
+            const int tuned[] = {PROF_P1, PROF_P2, PROF_P3, PROF_P4, PROF_P5, TUNE_P5_DUAL, PROF_DENS};
+            for (int t : tuned) key = fnv(key, (unsigned long long)(long long)ctx->tune_choice[t]);
             if (!eager && (!ctx->gexec[p] || ctx->gkey[p] != key)) {
                 // capturing runs the step's host logic (its buffer rotation) but not its kernels
                 if (!capture_step(ctx, n, pos_h, vel_u, mass, dt, p, key, batched)) eager = true;

@@ -70,25 +70,27 @@ __global__ void __launch_bounds__(WALK_WARPS * 32) k_walk(WalkArgs a) {
     const uint4 Ilo = __ldg(a.tlo + tile), Ihi = __ldg(a.thi + tile);   // this tile's box, max H
     const int32_t bi = BATCH && valid ? a.sbox[i] : 0;
     const uint32_t Ib = BATCH ? __ldg(a.nbox + tile) : 0u;
-    // software pipeline over the candidate tiles: the tile id two ahead and
-    // the box of the next tile are in flight while the current tile is tested
-    // (each is otherwise a dependent L2 trip)
+    // software pipeline over the candidate tiles: the tile id two ahead, and
+    // the box and this lane's staged particle of the next tile, are in flight
+    // while the current tile is tested (each is otherwise a dependent L2 trip)
     const uint32_t *tl = a.tiles + lo.x;
     const int nt = (int)lo.y;
     int J1 = nt > 0 ? (int)__ldg(tl) : 0, J2 = nt > 1 ? (int)__ldg(tl + 1) : 0;
-    uint4 lo1 = make_uint4(0, 0, 0, 0), hi1 = lo1;
+    uint4 lo1 = make_uint4(0, 0, 0, 0), hi1 = lo1, qn = lo1;
     if (nt > 0) {
         lo1 = __ldg(a.tlo + J1);
         hi1 = __ldg(a.thi + J1);
+        if (J1 * TILE + lane < a.n) qn = __ldg(a.q4 + J1 * TILE + lane);
     }
     for (int t = 0; t < nt; t++) {
         const int J = J1;
-        const uint4 Jlo = lo1, Jhi = hi1;
+        const uint4 Jlo = lo1, Jhi = hi1, qc = qn;
         J1 = J2;
         if (t + 2 < nt) J2 = (int)__ldg(tl + t + 2);
         if (t + 1 < nt) {
             lo1 = __ldg(a.tlo + J1);
             hi1 = __ldg(a.thi + J1);
+            if (J1 * TILE + lane < a.n) qn = __ldg(a.q4 + J1 * TILE + lane);
         }
         // skip a neighbour tile that no lane's sphere (reach max(H_i, Hmax_J)) touches
         const unsigned long long gx = point_gap(qi.x, Jlo.x, Jhi.x), gy = point_gap(qi.y, Jlo.y, Jhi.y),
@@ -109,7 +111,7 @@ __global__ void __launch_bounds__(WALK_WARPS * 32) k_walk(WalkArgs a) {
         __syncwarp();
         bool keep = false;
         if (lane < cnt) {
-            const uint4 q = __ldg(a.q4 + j0 + lane);
+            const uint4 q = qc;
             sq[w][lane] = q;
             const unsigned long long hx = point_gap(q.x, Ilo.x, Ihi.x), hy = point_gap(q.y, Ilo.y, Ihi.y),
                                      hz = point_gap(q.z, Ilo.z, Ihi.z);

@@ -35,7 +35,7 @@ WORKLOAD = "zeldovich-128^3: clustered gas, Zel'dovich lattice displacement, P(k
 
 # Algorithmic FP32 flops per pair unit of each pass (FMA = 2, add/mul/min/max = 1,
 # div/sqrt/exp = 1), counted from the operations the paper's formulas require
-# (derivation in the design doc).  P1-P3 count per gather pair; P4 and P5 count per
+# (each term listed with the pass kernels).  P1-P3 count per gather pair; P4 and P5 count per
 # UNORDERED pair of the pair set (both kernel sides, limiter, viscosity, force).
 FLOPS_PER_UNIT = {"P1 volumes": 20, "P2 corrections": 88, "P3 grad v": 92, "P4 forces": 281,
                   "P5 compatible energy": 259}
@@ -558,9 +558,17 @@ def run_gpu(args):
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    # ---------------- device-resident timing (the first warm-up step tunes the passes)
-    if not args.no_autotune:
-        crk.crk_autotune(ctx, True)
+    # ---------------- device-resident timing (the first warm-up step tunes the
+    # passes, unless their variants are pinned)
+    pins = parse_variants(args.variants)
+
+    def prepare(c):
+        for name, v in pins.items():
+            crk.crk_tune_set(c, name, v)
+        if not pins and not args.no_autotune:
+            crk.crk_autotune(c, True)
+
+    prepare(ctx)
     for _ in range(args.warmup):
         crk.crk_step(ctx, pos, vel, mass, 0.0)
     crk.crk_autotune(ctx, False)
@@ -597,6 +605,7 @@ def run_gpu(args):
     d_vel = torch.empty_like(vel0)
     d_mass = torch.empty_like(mass)
     e2e_ctx = crk.crk_create(precision=args.precision, tile_order=tile_order)
+    prepare(e2e_ctx)   # tuned during its own warm-up, or pinned as ctx
     for _ in range(max(1, args.warmup)):
         d_pos.copy_(h_pos, non_blocking=True)
         d_vel.copy_(h_vel, non_blocking=True)
@@ -619,6 +628,7 @@ def run_gpu(args):
         h_vel.copy_(d_vel, non_blocking=True)
     e1.record(stream)
     barrier()
+    crk.crk_autotune(e2e_ctx, False)
     e2e_ms = e0.elapsed_time(e1)
     e2ectx_close = e2e_ctx.close()
 
@@ -660,7 +670,8 @@ def run_gpu(args):
                            "pairs_per_step": pairs / args.steps,
                            "tiles": ntiles, "pair_candidate_tiles_per_tile": utp / max(1, ntiles),
                            "list_entries_per_particle": entries / n,
-                           "autotuned_variants": {k: v for k, (v, _) in tuning.items()},
+                           ("pinned_variants" if pins else "autotuned_variants"):
+                               {k: v for k, (v, _) in tuning.items()} if not pins else pins,
                            "tile_order": ORDER_NAMES[tile_order], "tile_order_step_ms": order_ms or None,
                            "gather_pairs_per_particle": diags[-1]["pairs_gather"] / n,
                            "union_pairs_per_particle": diags[-1]["pairs_union"] / n},
@@ -688,6 +699,19 @@ def run_gpu(args):
     return 0
 
 
+VARIANT_PASSES = {"P1": "P1 volumes", "P2": "P2 corrections", "P3": "P3 grad v", "P4": "P4 forces",
+                  "P5": "P5 compatible energy"}
+
+
+def parse_variants(spec):
+    """'P1=20,P4=8' -> {'P1 volumes': 20, 'P4 forces': 8}."""
+    out = {}
+    for item in filter(None, (x.strip() for x in spec.split(","))):
+        k, v = item.split("=")
+        out[VARIANT_PASSES[k.strip()]] = int(v)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
@@ -703,6 +727,9 @@ def main():
     ap.add_argument("--no-time-bins", action="store_true", help="skip the hierarchical time-bin measurement")
     ap.add_argument("--no-sod", action="store_true", help="skip the Sod shock-tube measurement")
     ap.add_argument("--no-autotune", action="store_true", help="keep the built-in pass variants")
+    ap.add_argument("--variants", default="",
+                    help="pin list-pass variants instead of tuning them (numbering of crk_tuning), "
+                         "e.g. P1=20,P2=16,P3=9,P4=8,P5=9")
     ap.add_argument("--tile-order", default="auto", choices=["auto", "0", "1", "2"],
                     help="particle order of the tiles: 0 Morton, 1 Hilbert, 2 bisection, auto = fastest")
     args = ap.parse_args()

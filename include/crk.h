@@ -405,6 +405,19 @@ int crk_autotune(crk_ctx *ctx, int enable);
  * CTA width (13-20 for the gather passes only).  Either array may be NULL. */
 int crk_tuning(crk_ctx *ctx, int *variant, float *ms);
 
+/* Number of pass variants (the numbering of crk_tuning). */
+#define CRK_TUNE_NVARIANT 21
+
+/* Pin list pass k (numbering as in crk_profile_read: 0 P1, 2 P2, 3 P3, 4 P4,
+ * 5 P5, 10 RK density) to variant v (numbering as in crk_tuning; -1: the
+ * built-in default) and stop tuning it; for P5, both the one-kick and the
+ * two-kick pass.  Every variant gives bitwise the same results, so this only
+ * fixes the speed.  A later crk_autotune(ctx, 1) unpins every pass.
+ * CRK_EINVAL for another k or v outside [-1, CRK_TUNE_NVARIANT); a variant the
+ * pass does not have (P4: only 0, 4, 8-12; P5: 0-12) makes the pass's next call
+ * return CRK_EINVAL. */
+int crk_tune_set(crk_ctx *ctx, int pass, int variant);
+
 /* Largest n accepted by crk_volumes_noalloc. */
 #define CRK_NOALLOC_MAX_N 16384
 

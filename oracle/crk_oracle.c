@@ -12,7 +12,7 @@
  * an equivalent uniform-grid candidate search (grid level > 0) whose candidate
  * lists are sorted by particle index, so both searches give bit-identical sums.
  *
- * Readings where the paper is silent or ambiguous (each listed in the design doc):
+ * Readings where the paper is silent or ambiguous:
  *  R1 neighbour predicate: positions canonicalised to uint32 fixed point
  *     q = floor(s*2^32), minimum image dq = (int32)(q_i - q_j), R^2 = sum dq^2
  *     (exact in uint64); H = floor(h*2^32).  gather(i) = {j : R^2 < H_i^2}

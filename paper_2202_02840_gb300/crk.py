@@ -15,6 +15,7 @@ from . import build as _build
 
 CRK_OK = 0
 CRK_ENONCONV = -5
+CRK_EINVAL = -1
 _CODES = {-1: "CRK_EINVAL", -2: "CRK_ENOMEM", -3: "CRK_ECUDA", -4: "CRK_ETIMEOUT",
           -5: "CRK_ENONCONV", -6: "CRK_ECAPACITY", -7: "CRK_ESTATE"}
 
@@ -98,6 +99,7 @@ def lib():
         L.crk_steps_batched.argtypes = [_vp, _ci, _ci, _vp, _vp, _vp, _vp, _ci, ctypes.c_double, _ci, _vp]
         L.crk_autotune.argtypes = [_vp, _ci]
         L.crk_tuning.argtypes = [_vp, _vp, _vp]
+        L.crk_tune_set.argtypes = [_vp, _ci, _ci]
         L.crk_profile.argtypes = [_vp, _ci]
         L.crk_profile_read.argtypes = [_vp, _vp, _vp, ctypes.POINTER(ctypes.c_longlong)]
         _LIB = L
@@ -501,6 +503,14 @@ def crk_tuning(ctx):
     ms = (ctypes.c_float * NPASS)()
     ctx.check(lib().crk_tuning(ctx.handle, v, ms))
     return {PASS_NAMES[k]: (v[k], ms[k]) for k in range(NPASS) if v[k] >= 0}
+
+
+CRK_TUNE_NVARIANT = 21
+
+
+def crk_tune_set(ctx, pass_name, variant):
+    """Pin one list pass (a name of PASS_NAMES) to a variant (-1: its default)."""
+    ctx.check(lib().crk_tune_set(ctx.handle, PASS_NAMES.index(pass_name), int(variant)))
 
 
 # ---------------------------------------------------------------- multi-step, CUDA graphs

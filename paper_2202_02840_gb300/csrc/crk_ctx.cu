@@ -353,6 +353,21 @@ extern "C" int crk_tuning(crk_ctx *ctx, int *variant, float *ms) {
     return CRK_OK;
 }
 
+extern "C" int crk_tune_set(crk_ctx *ctx, int pass, int variant) {
+    if (!ctx) return CRK_EINVAL;
+    const bool list_pass = pass == PROF_P1 || pass == PROF_P2 || pass == PROF_P3 || pass == PROF_P4 ||
+                           pass == PROF_P5 || pass == PROF_DENS;
+    if (!list_pass || variant < -1 || variant >= NVAR)
+        return crk_set_error(ctx, CRK_EINVAL, "crk_tune_set: no pass %d variant %d", pass, variant);
+    const int slots[2] = {pass, pass == PROF_P5 ? TUNE_P5_DUAL : pass};
+    for (int k : slots) {
+        ctx->tune_choice[k] = variant;
+        ctx->tune_done[k] = 1;
+        ctx->tune_ms[k] = 0.f;
+    }
+    return CRK_OK;
+}
+
 extern "C" int crk_profile(crk_ctx *ctx, int enable) {
     if (!ctx) return CRK_EINVAL;
     if (enable && !ctx->prof_ev) {

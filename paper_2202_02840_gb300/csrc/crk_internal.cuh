@@ -261,6 +261,7 @@ namespace crk {
 enum { PROF_P1 = 0, PROF_PN = 1, PROF_P2 = 2, PROF_P3 = 3, PROF_P4 = 4, PROF_P5 = 5, PROF_BUILD = 6,
        PROF_LISTS = 7, PROF_MLP_FWD = 8, PROF_MLP_TRAIN = 9, PROF_DENS = 10, PROF_NPASS = 11 };
 constexpr int TUNE_P5_DUAL = 15;   // the autotuner's record of the two-kick P5 pass
+constexpr int NVAR = CRK_TUNE_NVARIANT;   // list-pass variants (lvariant)
 void mlp_free(crk_ctx *ctx);
 void htb_free(crk_ctx *ctx);
 void rcb_free(crk_ctx *ctx);

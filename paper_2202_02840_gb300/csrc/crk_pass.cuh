@@ -385,7 +385,6 @@ struct LVariant {
 // 13-16: grid, U = 1..4, records one iteration ahead, CTAs of one tile;
 // 17-20: the same with the pass's own CTA width (passes that read list entries,
 // without their own record prefetch)
-constexpr int NVAR = 21;
 __host__ __device__ constexpr LVariant lvariant(int v) {
     return v < 4 ? LVariant{v + 1, ORD_GRID, 0, false}
                  : (v < 8 ? LVariant{v - 3, ORD_LONGEST, 0, false}
@@ -542,6 +541,8 @@ int launch_lpass(crk_ctx *ctx, int prof_id, const typename P::Params &prm, cudaS
         ctx->tune_done[ts] = 1;
     }
     const int v = ctx->tune_choice[ts] >= 0 ? ctx->tune_choice[ts] : default_variant<P>();
+    if (!variant_applies<P>(v))   // only a variant pinned by crk_tune_set can be one the pass lacks
+        return crk_set_error(ctx, CRK_EINVAL, "%s: the pass has no variant %d", what, v);
     prof_begin(ctx, prof_id, s);
     rc = launch_variant<P, WARPS>(ctx, g, prm, v, s);
     if (rc) return rc;

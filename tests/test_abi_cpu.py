@@ -48,6 +48,12 @@ def test_exports_match_header_exactly(libcrk):
     assert exported == declared_functions()
 
 
+def test_variant_count_matches_the_header():
+    from paper_2202_02840_gb300 import crk
+    txt = open(os.path.join(ROOT, "include", "crk.h")).read()
+    assert int(re.search(r"#define CRK_TUNE_NVARIANT (\d+)", txt).group(1)) == crk.CRK_TUNE_NVARIANT
+
+
 def test_default_params_are_the_papers(libcrk):
     from paper_2202_02840_gb300 import crk
     p = crk.crk_default_params()

@@ -47,3 +47,11 @@ def test_aggregate_single_process_is_identity():
     sys.path.insert(0, ROOT)
     import bench
     assert bench.aggregate([3.0, 4.0], [5.0, 6.0]) == ([3.0, 4.0], [5.0, 6.0])
+
+
+def test_variant_pins_parse():
+    import bench
+    assert bench.parse_variants("") == {}
+    assert bench.parse_variants("P1=20, P4=8") == {"P1 volumes": 20, "P4 forces": 8}
+    with pytest.raises(KeyError):
+        bench.parse_variants("P9=1")

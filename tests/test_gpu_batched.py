@@ -157,9 +157,57 @@ def test_autotuned_passes_give_identical_results():
             t = crk.crk_tuning(ctx)
             print(t)
             assert set(t) >= {"P1 volumes", "P2 corrections", "P3 grad v", "P4 forces", "P5 compatible energy"}
-            assert all(0 <= v <= 12 and ms > 0 for v, ms in t.values())
+            assert all(0 <= v < crk.CRK_TUNE_NVARIANT and ms > 0 for v, ms in t.values())
     for a, b in zip(*outs):
         assert torch.equal(a, b)
+
+
+def test_every_pass_variant_gives_identical_results():
+    """Each list-pass variant, pinned with crk_tune_set, reproduces the default
+    run bit for bit (same lists walked in the same order), including two KDK
+    steps; a variant that a pass lacks is refused with CRK_EINVAL."""
+    st = workload("clustered", 3000, 11)
+    names = ("P1 volumes", "P2 corrections", "P3 grad v", "P4 forces", "P5 compatible energy")
+
+    def run(v):
+        ctx = crk.crk_create()
+        for name in names:
+            crk.crk_tune_set(ctx, name, v)
+        ran = set(names)
+
+        def call(name, fn):
+            try:
+                return fn()
+            except crk.CrkError as e:
+                assert e.code == crk.CRK_EINVAL and "has no variant" in str(e), str(e)
+                ran.discard(name)
+                crk.crk_tune_set(ctx, name, -1)
+                return fn()
+
+        pos, vel, mass = dev(st["pos_h"]), dev(st["vel_u"]), dev(st["mass"])
+        crk.crk_build_cells(ctx, pos)
+        V, N = call("P1 volumes", lambda: crk.crk_volumes(ctx))
+        A, B, gA, gB, gv = crk.crk_corrections(ctx, V, vel)
+        acc, dudt, vsig, qmax = call("P4 forces", lambda: crk.crk_forces(ctx, mass, vel, V, A, B, gA, gB, gv))
+        du = call("P5 compatible energy",
+                  lambda: crk.crk_compatible(ctx, mass, vel, V, A, B, gA, gB, gv, vel[:, :3].contiguous(),
+                                             (vel[:, :3] * 1.01).contiguous()))
+        for _ in range(2):
+            crk.crk_step(ctx, pos, vel, mass, 0.0)
+        return [V, N, A, B, gA, gB, gv, acc, dudt, vsig, qmax, du, pos, vel], ran
+
+    ref, _ = run(-1)
+    has = {name: set() for name in names}
+    for v in range(crk.CRK_TUNE_NVARIANT):
+        out, ran = run(v)
+        for name in ran:
+            has[name].add(v)
+        for a, b in zip(ref, out):
+            assert torch.equal(a, b), v
+    every = set(range(crk.CRK_TUNE_NVARIANT))
+    assert has["P1 volumes"] == has["P2 corrections"] == has["P3 grad v"] == every
+    assert has["P4 forces"] == {0, 4, 8, 9, 10, 11, 12}
+    assert has["P5 compatible energy"] == set(range(13))
 
 
 # ---------------------------------------------------------------- CUDA graphs

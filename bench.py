@@ -156,6 +156,69 @@ def calibrated_oracle(st, seconds, seed):
         ns = min(n, int(ns * min(16.0, max(2.0, 0.9 * seconds / dt))))
 
 
+def _rel_err(g, o, floor=None):
+    """max_i |g_i - o_i| / max(|o_i|, floor): floor = the field's RMS, or a
+    per-particle scale (the no-cancellation scale of a coefficient or force)."""
+    o = np.asarray(o, np.float64)
+    g = np.asarray(g, np.float64).reshape(o.shape)
+    if floor is None:
+        floor = np.sqrt(np.mean(o ** 2))
+    floor = np.asarray(floor, np.float64)
+    if floor.ndim == 1 and o.ndim > 1:
+        floor = floor.reshape((-1,) + (1,) * (o.ndim - 1))
+    return float(np.max(np.abs(g - o) / np.maximum(np.maximum(np.abs(o), floor), 1e-300)))
+
+
+def sampled_errors(st, dev, tile_order, precisions, n_sample=16, seed=77):
+    """Error of one GPU evaluation (P1-P4 at the initial state) in each
+    precision mode against the FP64 oracle, on a seeded sample of particles:
+    the oracle computes the sample's dependency cone from scratch (union
+    neighbours of the sample, their gather neighbours), so the sample's
+    outputs are exact FP64 values of the full-size workload."""
+    import torch
+    from oracle import crk as O
+    from paper_2202_02840_gb300 import crk
+    pos = st["pos_h"]
+    sample = np.sort(np.random.default_rng(seed).choice(pos.shape[0], n_sample, replace=False))
+    _, ul = O.neighbours(pos, mode=1, targets=sample)
+    U1 = np.unique(np.concatenate([sample, ul]))
+    _, gl = O.neighbours(pos, mode=0, targets=U1)
+    G2 = np.unique(np.concatenate([U1, gl]))
+    vel = st["vel_u"][:, :3].astype(np.float64)
+    u = st["vel_u"][:, 3].astype(np.float64)
+    m = st["mass"].astype(np.float64)
+    p1 = O.volumes(pos, targets=G2)
+    p2 = O.corrections(pos, p1["V"], targets=U1)
+    gv = O.gradv(pos, p1["V"], vel, p2["A"], p2["B"], p2["gA"], p2["gB"], targets=U1)
+    p4 = O.forces(pos, vel, u, m, p1["V"], p2["A"], p2["B"], p2["gA"], p2["gB"], gv, targets=sample)
+    s = sample
+    out = {}
+    for prec in precisions:
+        c = crk.crk_create(precision=prec, tile_order=tile_order)
+        dpos = torch.from_numpy(pos).to(dev)
+        dvel = torch.from_numpy(st["vel_u"]).to(dev)
+        crk.crk_build_cells(c, dpos)
+        V, _ = crk.crk_volumes(c)
+        A, B, gA, gB, g_v = crk.crk_corrections(c, V, dvel)
+        acc, dudt, _, _ = crk.crk_forces(c, torch.from_numpy(st["mass"]).to(dev), dvel, V, A, B, gA, gB, g_v)
+        h = {k: t.detach().cpu().double().numpy() for k, t in
+             (("V", V), ("A", A), ("B", B), ("gA", gA), ("gB", gB), ("gv", g_v), ("acc", acc), ("dudt", dudt))}
+        c.close()
+        out[["plain", "mixed", "mixed+compensated moments"][prec]] = {
+            "V": _rel_err(h["V"][s], p1["V"][s]), "A": _rel_err(h["A"][s], p2["A"][s]),
+            "B": _rel_err(h["B"][s], p2["B"][s], p2["sB"][s]),
+            "gradA": _rel_err(h["gA"][s], p2["gA"][s], p2["sgA"][s]),
+            "gradB": _rel_err(h["gB"][s], p2["gB"][s], p2["sgB"][s]),
+            "gradv": _rel_err(h["gv"][s], gv[s]),
+            "accel": _rel_err(h["acc"][s], p4["acc"][s], p4["fscale"][s]),
+            "dudt": _rel_err(h["dudt"][s], p4["dudt"][s])}
+    return {"sample": "%d seeded particles of the workload, FP64 oracle over their dependency cone "
+                      "(%d particles)" % (n_sample, G2.size),
+            "norm": "max |gpu - oracle| / max(|oracle|, floor); floor = field RMS over the sample, or the "
+                    "no-cancellation scale for B, grad A, grad B and the acceleration",
+            "by_precision": out}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -630,6 +693,31 @@ def run_gpu(args):
     barrier()
     crk.crk_autotune(e2e_ctx, False)
     e2e_ms = e0.elapsed_time(e1)
+
+    # ---------------- the plain FP32 path (precision 0: no compensated sums,
+    # FP32 moment formation) over the same warm-up and steps, for comparison
+    plain = None
+    if args.precision != 0 and world == 1:
+        c0 = crk.crk_create(precision=0, tile_order=tile_order)
+        prepare(c0)
+        p0, v0 = pos0.clone(), vel0.clone()
+        for _ in range(args.warmup):
+            crk.crk_step(c0, p0, v0, mass, 0.0)
+        crk.crk_autotune(c0, False)
+        barrier()
+        q0 = torch.cuda.Event(enable_timing=True)
+        q1 = torch.cuda.Event(enable_timing=True)
+        plain_pairs = 0
+        q0.record(stream)
+        for _ in range(args.steps):
+            d = crk.crk_step(c0, p0, v0, mass, 0.0, diag=True)
+            plain_pairs += 3 * d["pairs_gather"] + 3 * d["pairs_union"]
+        q1.record(stream)
+        barrier()
+        plain_ms = q0.elapsed_time(q1)
+        c0.close()
+        plain = {"precision": "plain", "ms_per_step": plain_ms / args.steps,
+                 "value": plain_pairs / (plain_ms * 1e-3), "unit": UNIT}
     e2ectx_close = e2e_ctx.close()
 
     # ---------------- aggregate over ranks (max time, summed work)
@@ -679,6 +767,9 @@ def run_gpu(args):
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": n * 36,
                         "d2h_bytes_per_step": n * 32},
                 "gpu_launches": launches, "clocks": clk}
+        if plain is not None:
+            plain["step_ms_ratio_to_this"] = plain["ms_per_step"] / (ms_max / args.steps)
+            line["plain_fp32"] = plain
         if not args.no_learned_h and world == 1:
             line["learned_h"] = learned_h_report(dev)
         if not args.no_batched and world == 1:
@@ -693,6 +784,8 @@ def run_gpu(args):
             line["cpu_baseline"] = {"value": p / dt, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
                                     "sample": "FP64 oracle passes P1,P2,P3,P4,P5,P5 on %d random target "
                                               "particles of the workload (%.1f s)" % (ns, dt)}
+            # the stated error of this mode and of the plain FP32 path
+            line["err"] = sampled_errors(st, dev, tile_order, sorted({0, args.precision}))
         print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()

@@ -402,7 +402,7 @@ int crk_autotune(crk_ctx *ctx, int enable);
  * with the pass's own entries per iteration and CTAs of 1, 2, 4, 8 tiles;
  * 13-16: 1-4 entries per iteration with the neighbour records of the next
  * iteration read ahead, CTAs of one tile; 17-20: the same with the pass's own
- * CTA width (13-20 for the gather passes only).  Either array may be NULL. */
+ * CTA width (13-20 for every list pass but P4).  Either array may be NULL. */
 int crk_tuning(crk_ctx *ctx, int *variant, float *ms);
 
 /* Number of pass variants (the numbering of crk_tuning). */
@@ -414,7 +414,7 @@ int crk_tuning(crk_ctx *ctx, int *variant, float *ms);
  * two-kick pass.  Every variant gives bitwise the same results, so this only
  * fixes the speed.  A later crk_autotune(ctx, 1) unpins every pass.
  * CRK_EINVAL for another k or v outside [-1, CRK_TUNE_NVARIANT); a variant the
- * pass does not have (P4: only 0, 4, 8-12; P5: 0-12) makes the pass's next call
+ * pass does not have (P4 has only 0, 4, 8-12) makes the pass's next call
  * return CRK_EINVAL. */
 int crk_tune_set(crk_ctx *ctx, int pass, int variant);
 

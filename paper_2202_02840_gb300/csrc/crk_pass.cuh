@@ -185,31 +185,39 @@ __device__ __forceinline__ void list_loop(typename P::IState &st, const typename
 }
 
 // list_loop with the neighbour records one iteration ahead as well (RP
-// variants): at iteration k the records of iteration k + 1 and the entries of
-// iteration k + 2 are in flight while the U pairs of iteration k are
-// evaluated, so a record that misses L1 is waited for only if it takes longer
-// than a whole iteration.  Same entries, same order: bitwise the same sums.
+// variants): at iteration k the records of iteration k + 1 and the entries
+// (or stored records) of iteration k + 2 are in flight while the U pairs of
+// iteration k are evaluated, so a record that misses L1 is waited for only if
+// it takes longer than a whole iteration.  Same entries, same order: bitwise
+// the same sums.
 template <class P, int U, class EntryFn>
 __device__ __forceinline__ void list_loop_rp(typename P::IState &st, const typename P::Params &prm, EntryFn entry,
                                              size_t fb, int mg, int k0, int k1, int mk) {
-    uint32_t ec[U] = {}, en[U] = {};
+    using Ent = typename EntOf<P>::type;
+    auto fetch = [&](int k) -> Ent {
+        if constexpr (P::ENTRIES)
+            return entry(k);
+        else
+            return P::stored(fb + (size_t)k * 32, prm);
+    };
+    Ent ec[U] = {}, en[U] = {};
     typename P::Rec rc[U] = {}, rn[U] = {};
 #pragma unroll
     for (int u = 0; u < U; u++) {
-        if (k0 + u < mk) ec[u] = entry(k0 + u);
-        if (k0 + U + u < mk) en[u] = entry(k0 + U + u);
+        if (k0 + u < mk) ec[u] = fetch(k0 + u);
+        if (k0 + U + u < mk) en[u] = fetch(k0 + U + u);
     }
 #pragma unroll
     for (int u = 0; u < U; u++)
         if (k0 + u < mk) rc[u] = P::load(ec[u], fb + (size_t)(k0 + u) * 32, prm);
     for (int k = k0; k < k1; k += U) {
-        uint32_t eu[U];
+        Ent eu[U];
 #pragma unroll
         for (int u = 0; u < U; u++) {
             if (k + U + u < mk) rn[u] = P::load(en[u], fb + (size_t)(k + U + u) * 32, prm);
             eu[u] = ec[u];
             ec[u] = en[u];
-            if (k + 2 * U + u < mk) en[u] = entry(k + 2 * U + u);
+            if (k + 2 * U + u < mk) en[u] = fetch(k + 2 * U + u);
         }
         const size_t pos = fb + (size_t)k * 32;
 #pragma unroll
@@ -383,8 +391,8 @@ struct LVariant {
 // 0-3: grid, U = 1..4; 4-7: longest first, U = 1..4; 8: per-SM ranges;
 // 9-12: grid with the pass's own U and CTAs of 1, 2, 4, 8 tiles (32-256 particles);
 // 13-16: grid, U = 1..4, records one iteration ahead, CTAs of one tile;
-// 17-20: the same with the pass's own CTA width (passes that read list entries,
-// without their own record prefetch)
+// 17-20: the same with the pass's own CTA width (passes without their own
+// record prefetch: all but P4)
 __host__ __device__ constexpr LVariant lvariant(int v) {
     return v < 4 ? LVariant{v + 1, ORD_GRID, 0, false}
                  : (v < 8 ? LVariant{v - 3, ORD_LONGEST, 0, false}
@@ -440,8 +448,8 @@ static void launch_rp_u(crk_ctx *ctx, const ListGeom &g, const typename P::Param
 template <class P, int WARPS>
 static int launch_variant(crk_ctx *ctx, const ListGeom &g, const typename P::Params &prm, int v, cudaStream_t s) {
     const LVariant lv = lvariant(v);
-    if (lv.rp) {   // records one iteration ahead (passes with entries, no own prefetch)
-        if constexpr (P::ENTRIES && !P::PREFETCH) {
+    if (lv.rp) {   // records one iteration ahead (passes without their own prefetch)
+        if constexpr (!P::PREFETCH) {
             if (lv.warps == 1)
                 launch_rp_u<P, 1>(ctx, g, prm, lv.U, s);
             else
@@ -483,7 +491,7 @@ constexpr int default_variant() {
 
 template <class P>
 constexpr bool variant_applies(int v) {
-    if (lvariant(v).rp) return P::ENTRIES && !P::PREFETCH;
+    if (lvariant(v).rp) return !P::PREFETCH;
     return P::PREFETCH ? (lvariant(v).U <= 1) : true;
 }
 

@@ -55,3 +55,26 @@ def test_variant_pins_parse():
     assert bench.parse_variants("P1=20, P4=8") == {"P1 volumes": 20, "P4 forces": 8}
     with pytest.raises(KeyError):
         bench.parse_variants("P9=1")
+
+
+def test_oracle_cone_gives_the_full_evaluation():
+    """The bench states its error on sampled particles whose oracle values come
+    from their dependency cone alone; on a small workload those values equal a
+    full FP64 evaluation (same per-particle sums), so the cone is complete."""
+    import numpy as np
+    import bench
+    from oracle import crk as O
+    from paper_2202_02840_gb300 import inputs
+    st = inputs.zeldovich(24)
+    s = np.sort(np.random.default_rng(3).choice(st["pos_h"].shape[0], 4, replace=False))
+    p1, p2, gv, p4, ncone = bench.oracle_cone(st, s)
+    ev = O.evaluate(st)
+    assert 4 < ncone < st["pos_h"].shape[0]
+    for a, b in ((p1["V"], ev["V"]), (p2["A"], ev["A"]), (p2["B"], ev["B"]), (p2["gA"], ev["gA"]),
+                 (p2["gB"], ev["gB"]), (gv, ev["gv"]), (p4["acc"], ev["acc"]), (p4["dudt"], ev["dudt"]),
+                 (p4["fscale"], ev["fscale"])):
+        np.testing.assert_allclose(a[s], b[s], rtol=1e-13, atol=1e-13 * np.abs(b[s]).max())
+    # a cone missing the gather neighbours of the union neighbours is wrong
+    V_bad = O.volumes(st["pos_h"], targets=s)["V"]
+    c_bad = O.corrections(st["pos_h"], V_bad, targets=s)
+    assert not np.allclose(c_bad["A"][s], ev["A"][s], rtol=1e-9)

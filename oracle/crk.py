@@ -1,7 +1,7 @@
 """FP64 CPU oracle of the CRKSPH pair passes (CRK-HACC, arXiv 2202.02840).
 
 TEST INFRASTRUCTURE ONLY: imported by tests/, __graft_entry__.smoke() and the
-CPU-baseline leg of bench.py, never by the product path.  Shares no code with
+CPU-baseline leg and reference arm of bench.py, never by the product path.  Shares no code with
 the CUDA library.  Pair passes run in crk_oracle.c (FP64, brute force or an
 equivalent grid search); the elementwise steps below are plain numpy FP64.
 

@@ -4,7 +4,9 @@
  * Selection and Smoothing Length").
  *
  * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the CPU
- * baseline leg of bench.py may load this library.  It shares no code, header,
+ * baseline leg and reference arm of bench.py may load this library (the bench
+ * times it and, in the CPU baseline leg, states the GPU error against it).
+ * It shares no code, header,
  * table or constant generator with the CUDA path; neither includes the other.
  *
  * Everything is FP64 and written literally from the paper's equations, one

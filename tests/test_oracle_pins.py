@@ -410,3 +410,28 @@ def test_cfl_of_gas_at_rest_is_sound_crossing():
     cs = np.sqrt(gam * (gam - 1.0) * 1.0)
     hh = st["pos_h"][:, 3].astype(np.float64) / 4.0
     assert np.allclose(dt, 0.25 * hh / cs, rtol=1e-9)
+
+
+@pytest.mark.parametrize("approach", [True, False])
+def test_compatible_energy_partition_by_entropy(approach):
+    """eq:fij on two particles of equal density, where s = P/rho^gamma is
+    proportional to u.  Approaching, the pair's work heats it (Delta E > 0)
+    and the hotter particle takes the smaller share min(s)/(s_i + s_j); receding,
+    the work cools it (Delta E < 0) and the hotter particle gives the larger
+    share max(s)/(s_i + s_j): cooler particles are heated, hotter ones cooled.
+    Energy conservation alone (any f with f_ij + f_ji = 1) does not fix this."""
+    pos = np.array([[0.50, 0.5, 0.5, 0.2], [0.55, 0.5, 0.5, 0.2]], np.float32)
+    u = np.array([2.0, 0.5])
+    m = np.ones(2)
+    sgn = 1.0 if approach else -1.0
+    vel = np.array([[0.1 * sgn, 0.0, 0.0], [-0.1 * sgn, 0.0, 0.0]])
+    V = O.volumes(pos)["V"]
+    assert V[0] == V[1]                         # equal density: s proportional to u
+    A, B, gA, gB, gv = np.ones(2), np.zeros((2, 3)), np.zeros((2, 3)), np.zeros((2, 3, 3)), np.zeros((2, 3, 3))
+    f = O.forces(pos, vel, u, m, V, A, B, gA, gB, gv)
+    va = vel + 1e-3 * f["acc"]
+    dE = m * O.compatible(pos, vel, u, m, V, A, B, gA, gB, gv, vel, va)
+    assert np.sign(dE.sum()) == (1.0 if approach else -1.0)
+    share_hot = dE[0] / dE.sum()
+    expect = (u[1] if approach else u[0]) / u.sum()
+    assert abs(share_hot - expect) < 1e-12, (share_hot, expect)

@@ -435,3 +435,44 @@ def test_compatible_energy_partition_by_entropy(approach):
     share_hot = dE[0] / dE.sum()
     expect = (u[1] if approach else u[0]) / u.sum()
     assert abs(share_hot - expect) < 1e-12, (share_hot, expect)
+
+
+@pytest.mark.parametrize("dx", [(0.024, -0.018, 0.02), (0.042, -0.034, 0.042)])
+def test_limited_viscosity_of_one_pair_in_closed_form(dx):
+    """eq:visc, eq:mu, eq:hatvi, eq:phi..eq:phiad written out for one pair with
+    given grad v (non-symmetric) and compared with the oracle's Q_i and Q_j
+    (reading R7: Q_j with j's own h, c_s, rho).  The first separation has
+    eta = min(r/h_i, r/h_j) = 0.144 < eta_crit (phi_ad = 0.011), the second
+    eta = 0.27 (phi_ad = 1, the projection 65% of v_ij.x_ij).  Taking eta as
+    the max, or the van Leer form 2r/(1+r), fails this pin."""
+    gam, Cl, Cq, eps, nh = 5.0 / 3.0, 2.0, 1.0, 0.1, 4.0
+    ec, ef = 1.0 / nh, 0.2 / nh
+    pos = np.array([[0.5, 0.5, 0.5, 0.2], [0.5 + dx[0], 0.5 + dx[1], 0.5 + dx[2], 0.25]], np.float32)
+    vel = np.array([[0.1, -0.05, 0.08], [-0.1, 0.05, -0.06]])
+    u, m, V = np.array([1.0, 0.5]), np.array([1.0, 1.5]), np.array([1e-3, 2e-3])
+    G = np.array([[[-5.0, 1.5, 0.3], [0.8, -2.0, 0.4], [-0.6, 0.2, -3.0]],
+                  [[-2.0, -0.7, 1.1], [0.4, -6.0, 0.0], [0.9, -0.3, -1.0]]])
+    A, B, gA, gB = np.ones(2), np.zeros((2, 3)), np.zeros((2, 3)), np.zeros((2, 3, 3))
+    out = O.forces(pos, vel, u, m, V, A, B, gA, gB, G)
+    # the separation the method uses: fixed-point difference (exact in FP64)
+    q, _ = O.fixed_point(pos)
+    x = ((q[0].astype(np.int64) - q[1].astype(np.int64) + 2 ** 31) % 2 ** 32 - 2 ** 31) * 2.0 ** -32
+    h = pos[:, 3].astype(np.float64)
+    r = np.sqrt(x @ x)
+    a, b = x @ G[0] @ x, x @ G[1] @ x
+    phi_vl = min(1.0, max(0.0, 4 * (a / b) / (1 + a / b) ** 2))
+    eta = min(r / h[0], r / h[1])
+    phi_ad = np.exp(-((eta - ec) / ef) ** 2) if eta < ec else 1.0
+    phi = phi_vl * phi_ad
+    vhat_i = vel[0] - 0.5 * phi * G[0] @ x                  # eq:hatvi, x = x_ij
+    vhat_j = vel[1] - 0.5 * phi * G[1] @ (-x)               # x_ji = -x_ij
+    ux = (vhat_i - vhat_j) @ x
+    rho = m / V
+    c = np.sqrt(gam * (gam - 1.0) * rho * u / rho)
+    Q = []
+    for k in (0, 1):
+        hh = h[k] / nh
+        mu = min(0.0, hh * ux / (r * r + hh * hh * eps * eps))
+        Q.append(rho[k] * (-Cl * c[k] * mu + Cq * mu * mu))
+    assert (eta < ec) == (dx[0] < 0.03) and 0.0 < phi_vl < 1.0 and ux < 0.0
+    np.testing.assert_allclose(out["qmax"], Q, rtol=1e-12)

@@ -379,6 +379,102 @@ def test_thacker_fixed_point_and_continuity():
     assert O.thacker([1.0], [400.0], prm)[0] < 1.0 < O.thacker([1.0], [150.0], prm)[0]
 
 
+def _frac(s):
+    num, _, den = str(s).partition("/")
+    return float(num) / float(den or 1)
+
+
+def test_thacker_matches_hand_evaluated_branches():
+    """eq:thacker at Delta_N = 1/2, 4/5, 1, 5/4, 2, evaluated by hand from the
+    printed piecewise lambda (tests/golden/thacker.json).  A swap of the two
+    branches, or Delta_N^3 in place of Delta_N^2 below 1, fails every case
+    but Delta_N = 1."""
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "thacker.json")))
+    prm = O.params()
+    assert prm[2] == gold["N_res"]
+    for c in gold["cases"]:
+        N, ratio = _frac(c["N"]), _frac(c["ratio"])
+        d = _frac(c["Delta_N"])
+        assert abs(np.cbrt(gold["N_res"] / N) - d) < 1e-15
+        got = O.thacker([0.05], [N], prm)[0] / 0.05
+        assert abs(got - ratio) < 1e-14, (c, got)
+        # lambda recovered from the update: h~/h - 1 = lambda (Delta_N - 1)
+        if d != 1.0:
+            assert abs((got - 1.0) / (d - 1.0) - _frac(c["lambda"])) < 1e-13, c
+
+
+def test_cfl_branches_in_closed_form():
+    """Sec. 2.1 time-step criteria, one particle per branch, with numbers
+    evaluated by hand (h = 0.1, so h_hat = h / n_h = 0.025; C_CFL = 0.25,
+    zeta = 4; no gravity, so min(h_hat, r_soft) = h_hat):
+      0  sound speed c_s = 2 dominates:        0.25 * 0.025 / 2 = 1/320
+      1  c_sq = sqrt(4 * 9 / 1) = 6 dominates:  0.25 * 0.025 / 6 = 1/960
+      2  v_sig = 10 dominates:                  0.25 * 0.025 / 10 = 1/1600
+      3  h_hat |tr grad v| = 0.025 * 40 = 1:    0.25 * 0.025 / 1 = 1/160
+      4  |a_tot| = |(600, 800, 0)| = 1000:      sqrt(0.025 / 1000) = 1/200
+    A c_sq without zeta, an acceleration criterion on h rather than h_hat, or
+    a missing square root each moves one of them."""
+    n = 5
+    gv = np.zeros((n, 3, 3))
+    gv[3] = np.diag([-40.0, 0.0, 0.0])
+    ev = {"pos_h": np.tile(np.array([0.5, 0.5, 0.5, 0.1], np.float32), (n, 1)),
+          "cs": np.array([2.0, 1.0, 1.0, 0.5, 0.1]),
+          "qmax": np.array([0.0, 9.0, 0.0, 0.0, 0.0]),
+          "rho": np.ones(n),
+          "vsig": np.array([0.0, 0.0, 10.0, 0.0, 0.0]),
+          "gv": gv,
+          "acc": np.array([[0, 0, 0], [0, 0, 0], [0, 0, 0], [0, 0, 0], [600.0, 800.0, 0.0]])}
+    dt = O.cfl_dt(ev)
+    want = np.array([1 / 320, 1 / 960, 1 / 1600, 1 / 160, 1 / 200])
+    assert np.allclose(dt, want, rtol=2e-7, atol=0), (dt, want)   # h = 0.1 is stored in FP32
+
+
+def _converging_flow(side=12, h_spacings=3.5, amp=0.3):
+    """A jittered lattice in a compressive periodic flow with a varying u, so
+    that the pair forces depend on p (viscosity acts on ~98% of the particles)
+    and on u (pressure)."""
+    pos = inputs.jittered_lattice(side, 0.1, 21)
+    n = pos.shape[0]
+    k = 2.0 * np.pi
+    vel = np.stack([-amp * np.sin(k * pos[:, 0]), -0.7 * amp * np.sin(k * pos[:, 1]),
+                    -0.4 * amp * np.sin(k * pos[:, 2])], 1)
+    u = 1.0 + 0.3 * np.cos(k * pos[:, 0])
+    return inputs.pack(pos, h_spacings / side, vel, u, 1.0 / n)
+
+
+def test_kdk_step_is_second_order_with_the_predictor():
+    """eq:verletOP (Sec. 2.1): the closing half kick takes the rates at
+    (x^1, p_p^1, u_p^1), which are within O(dt^2) of those at the step end,
+    so the step is second order.  Evaluating there with p^1/2 or u^1/2
+    instead (rates O(dt) off) makes it first order: with the two planted in
+    the oracle, these error ratios fall from ~4 to ~2.0-2.4.  h is held fixed
+    (h_min = h_max) so that every run integrates the same equations; the
+    reference takes 16 times the steps of the coarsest run."""
+    st0 = _converging_flow()
+    h = float(st0["pos_h"][0, 3])
+    T = 0.04
+
+    def run(m):
+        st, ev = st0, None
+        for _ in range(m):
+            st, ev, _ = O.kdk_step(st, ev, dt=T / m, h_min=h, h_max=h)
+        return st
+
+    ref = run(64)
+
+    def err(st):
+        dx = (st["pos_h"][:, :3].astype(np.float64) - ref["pos_h"][:, :3] + 0.5) % 1.0 - 0.5
+        dv = st["vel_u"][:, :3].astype(np.float64) - ref["vel_u"][:, :3]
+        du = st["vel_u"][:, 3].astype(np.float64) - ref["vel_u"][:, 3]
+        return np.array([np.sqrt((dx ** 2).sum(1).mean()), np.sqrt((dv ** 2).sum(1).mean()),
+                         np.sqrt((du ** 2).mean())])
+
+    e4, e8, e16 = err(run(4)), err(run(8)), err(run(16))
+    r1, r2 = e4 / e8, e8 / e16
+    print("error ratios", r1, r2)
+    assert np.all(r1 > 3.3) and np.all(r2 > 3.3), (r1, r2)
+
+
 def test_h_iteration_converges_to_target_neighbour_count():
     st = inputs.uniform(16)
     pos = st["pos_h"].copy()

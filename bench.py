@@ -44,6 +44,7 @@ FLOPS_PER_UNIT = {"P1 volumes": 20, "P2 corrections": 88, "P3 grad v": 92, "P4 f
 # 39.1 M unordered pairs); a full 128^3 launch is too large to capture, so the
 # traffic is scaled by units.
 TRAFFIC_PER_UNIT = {"P4 forces": 47.4}
+PRECISION_NAMES = ["plain", "mixed", "mixed+compensated moments", "mixed+float-float moments"]
 
 
 def measured_peaks():
@@ -801,7 +802,7 @@ def run_gpu(args):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "n": n, "precision": ["plain", "mixed", "mixed+compensated moments"][args.precision],
+                "config": {"workload": WORKLOAD, "n": n, "precision": PRECISION_NAMES[args.precision],
                            "parallelism": "replicas" if world > 1 else "single",
                            "l2": "step working set ~%.1f GB > L2 (129 MB): inputs larger than L2, no flush"
                                  % ((n * 460 + entries * 20) / 1e9),
@@ -865,7 +866,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n-side", type=int, default=128)
-    ap.add_argument("--precision", type=int, default=1, choices=[0, 1, 2])
+    ap.add_argument("--precision", type=int, default=1, choices=[0, 1, 2, 3])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-learned-h", action="store_true", help="skip the learned-h training and evaluation")

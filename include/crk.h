@@ -56,7 +56,7 @@ extern "C" {
 #define CRK_EINVAL (-1)     /* invalid argument or invalid particle data */
 #define CRK_ENOMEM (-2)     /* device allocation failed */
 #define CRK_ECUDA (-3)      /* a CUDA runtime call or kernel launch failed */
-#define CRK_ETIMEOUT (-4)   /* a bounded device-side wait gave up */
+#define CRK_ETIMEOUT (-4)   /* reserved: no entry point returns it (no kernel waits on another) */
 #define CRK_ENONCONV (-5)   /* the h fixed-point iteration did not converge */
 #define CRK_ECAPACITY (-6)  /* a fixed-capacity buffer overflowed */
 #define CRK_ESTATE (-7)     /* call out of order (e.g. a pass before crk_build_cells) */
@@ -88,7 +88,12 @@ typedef struct {
                          1 = mixed (default): FP32 pair sums, compensated momentum
                              and energy accumulation, moments formed and the 3x3
                              system solved in FP64;
-                         2 = mixed with compensated moment and grad-v sums too */
+                         2 = mixed with compensated moment and grad-v sums too;
+                         3 = mode 2 with every pair term of the moments carried in
+                             float-float (exact separation and integer r^2, an exact
+                             t = 1 - eta, error-free products): B, grad A, grad B
+                             to ~1e-8 of their RMS even where the moment sums cancel
+                             (lattice-like neighbourhoods), at about twice P2's cost */
     int kmax;         /* finest chaining-mesh level reported by crk_cells (<= 7) */
     int tile_order;   /* order of the particles that cuts them into 32-particle tiles:
                          0 = Morton (default; the chaining-mesh order of Sec. 2.3,
@@ -97,7 +102,22 @@ typedef struct {
                          2 = recursive coordinate bisection (the paper's leaves) */
     int density;      /* 0 = rho = m/V (default); 1 = the RK-corrected sum
                          rho_i = sum_{j in gather(i)} m_j W^R_ij (eq:RK), self included */
-    int reserved[4];
+    int h_mode;       /* smoothing length in crk_step / crk_steps (one box):
+                         0 = evolved (default, Sec. 2.6): one eq:thacker update of each
+                             evaluation's count carries h to the next step;
+                         1 = eq:hi solved before every evaluation by the fixed-point
+                             iteration of crk_h_iterate (tolerance h_tol, at most h_max_it
+                             P1 passes), started from the state's h;
+                         2 = as 1, started from the learned proposal (crk_h_propose; the
+                             network weights must be set): the first P1 judges and the
+                             proposal replaces the first update.
+                         In modes 1 and 2 the state keeps the solved h (no eq:thacker
+                         update after the evaluation), steps run eagerly (never from a
+                         CUDA graph: the solve reads its convergence on the host), and
+                         crk_step_batched returns CRK_ESTATE. */
+    int h_max_it;     /* iteration cap of h_mode 1 and 2 (default 50) */
+    float h_tol;      /* |Delta_N - 1| tolerance of h_mode 1 and 2 (default 1e-4) */
+    int reserved;
 } crk_params;
 
 /* Per-step diagnostics (host memory), all reductions in FP64. */
@@ -108,6 +128,8 @@ typedef struct {
     double P[3];          /* total momentum sum m v after the step */
     long long pairs_gather;  /* |gather(i)| - 1 summed over i, last evaluation */
     long long pairs_union;   /* ordered pairs of the pair set, last evaluation */
+    long long h_iterations;  /* h_mode 1, 2: P1 passes of the step's eq:hi solve (else 0) */
+    long long h_unconverged; /* h_mode 1, 2: particles still outside h_tol after them */
 } crk_diag;
 
 /* Fill *p with the paper's values (see crk_params).  Never fails for p != NULL. */
@@ -164,6 +186,20 @@ int crk_build_stats(crk_ctx *ctx, int *ntiles, long long *list_entries,
  * to a 2^-32 collision chance per particle. */
 int crk_neighbours(crk_ctx *ctx, int mode, int32_t *count, uint32_t *hash, void *stream);
 
+/* The per-particle neighbour lists that the list passes walk (the walk of the
+ * last build; built here if the passes have not built them yet), in caller
+ * order, for inspection.  offsets (device, n + 1 long longs) is the exclusive
+ * prefix sum of the set sizes of crk_neighbours in the same mode; lists
+ * (device, offsets[n] ints) receives particle i's set in
+ * lists[offsets[i] .. offsets[i+1]), in the order the passes visit it:
+ *   mode 0: gather(i) (eq:vol; self first), each entry the caller index of j
+ *           with bit 31 set when i is in gather(j) too (the "j's kernel
+ *           reaches i" flag P4 uses);
+ *   mode 1: the pair set of i (the gather neighbours, then the others),
+ *           caller indices.
+ * CRK_ESTATE in a context without lists (the allocation-free volumes). */
+int crk_neighbour_lists(crk_ctx *ctx, int mode, const long long *offsets, int32_t *lists, void *stream);
+
 /* P1, eq:vol and eq:hi: n_i = sum_{j in gather(i)} W(|x_ij|, h_i) with the
  * C4 Wendland kernel of eq:C4, V_i = 1/n_i, Nngb_i = 4/3 pi h_i^3 n_i.
  * Outputs V[n], Nngb[n] (Nngb may be NULL).  *pairs (host, may be NULL)
@@ -175,7 +211,7 @@ int crk_volumes(crk_ctx *ctx, float *V, float *Nngb, long long *pairs, void *str
  * sum_j V_j W^R_ij = 1, sum_j V_j x_ij W^R_ij = 0 (Sec. 1.2):
  *   B = -m2^-1 m1, A = 1/(m0 + m1.B), grad B = -m2^-1 (grad m1 + grad m2 B),
  *   grad A = -A^2 (grad m0 + B.grad m1 + m1.grad B)
- * (3x3 inverse in FP64 when precision = 1), then the velocity gradient of
+ * (3x3 inverse in FP64 when precision >= 1), then the velocity gradient of
  * eq:gradv, grad v_i = -sum_j V_j (v_i - v_j) (x) grad W^R_ij.
  * Inputs V[n], vel_u[4n]; outputs A, B, gradA, gradB, gradv (gradv may be
  * NULL to skip P3). */
@@ -440,7 +476,10 @@ int crk_tune_set(crk_ctx *ctx, int pass, int variant);
  *    call clears what must start at zero.  Calls that overlap on the GPU
  *    (other streams, other host threads) race on it: serialise them.
  *  - The call synchronises `stream` once (to check the binning) and then
- *    enqueues P1 and the output scatter on it. */
+ *    enqueues P1 and the output scatter on it.
+ *  - CRK_ESTATE if some internal buffer would have had to grow (which would
+ *    mean a library allocation); with the fixed sizes above this does not
+ *    happen for any n it accepts. */
 int crk_volumes_noalloc(int n, const float *pos_h, float *V, float *Nngb, void *stream);
 
 /* ------------------------------------------------------------------------

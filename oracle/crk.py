@@ -349,7 +349,25 @@ def _wrap_f32(x):
     return f
 
 
-def kdk_step(state, ev=None, dt=None, prm=None, k=None, h_min=1e-6, h_max=0.3, dt_max=1.0):
+def h_propose(pos_h, N_prev, divv, dt, w, tol, prm=None, h_min=1e-6, h_max=0.3):
+    """The learned starting point of the eq:hi solve (see oracle/mlp.py): h =
+    clamp(h_ref exp(y), h_min, h_max), h_ref = h (N_res / N_prev)^(1/3), y the
+    network output for the particle's features (FP64 forward of the declared
+    weights); a particle whose N_prev already meets |Delta_N - 1| <= tol
+    keeps its h (the judge)."""
+    from . import mlp as M
+    prm = params() if prm is None else prm
+    pos = _pos(pos_h)
+    h = pos[:, 3].astype(np.float64)
+    x = M.features(pos, N_prev=N_prev, divv=divv, dt=dt, N_res=prm[2])
+    y = M.forward(w, x)[0]
+    d = np.cbrt(prm[2] / np.asarray(N_prev, np.float64))
+    hp = np.clip(h * d * np.exp(y), h_min, h_max)
+    return np.where(np.abs(d - 1.0) <= tol, h, hp)
+
+
+def kdk_step(state, ev=None, dt=None, prm=None, k=None, h_min=1e-6, h_max=0.3, dt_max=1.0, h_mode=0,
+             h_tol=1e-4, h_max_it=50, h_solved=None, w=None):
     """One hydro step, eq:verletOP (Sec. 2.1) with predicted p_p, u_p and the
     compatible energy of eq:compEng for each half kick (in comoving variables:
     the drift moves x by dt p_1/2 / a^2, and the energy kicks add the
@@ -360,7 +378,15 @@ def kdk_step(state, ev=None, dt=None, prm=None, k=None, h_min=1e-6, h_max=0.3, d
     evaluation at the state's positions) are reused for the first half kick.
     h advances by one eq:thacker update of the new evaluation, clamped to
     [h_min, h_max].  Positions, velocities and u are stored in FP32 between
-    steps, as in the engine's state.  Returns (new_state, new_eval, dt)."""
+    steps, as in the engine's state.  Returns (new_state, new_eval, dt).
+
+    h_mode 1 solves eq:hi at the drifted positions before the evaluation
+    (h_iterate from the state's h, tolerance h_tol); h_mode 2 starts that
+    solve from the learned proposal (h_propose with the weights w, features
+    from the first P1 at the state's h and the last evaluation's grad v).  In
+    both the new state carries the solved h (no further eq:thacker update).
+    h_solved (FP32 array) replaces the solve by a given h, which is how a
+    step is compared with one whose solve made its own threshold decisions."""
     prm = params() if prm is None else prm
     if ev is None:
         ev = evaluate(state, prm, k)
@@ -386,12 +412,25 @@ def kdk_step(state, ev=None, dt=None, prm=None, k=None, h_min=1e-6, h_max=0.3, d
     st1["pos_h"][:, 3] = pos[:, 3]
     st1["vel_u"][:, :3] = p_p
     st1["vel_u"][:, 3] = u_p
+    if h_solved is not None:
+        st1["pos_h"][:, 3] = np.asarray(h_solved, np.float32)
+    elif h_mode == 1:
+        st1["pos_h"][:, 3] = h_iterate(st1["pos_h"], h_tol, h_max_it, prm, k, h_min, h_max)[0]
+    elif h_mode == 2:
+        N0 = volumes(st1["pos_h"], k)["N"]
+        hp = h_propose(st1["pos_h"], N0, np.trace(ev["gv"], axis1=1, axis2=2), dt, w, h_tol, prm, h_min, h_max)
+        pp = st1["pos_h"].copy()
+        pp[:, 3] = hp.astype(np.float32)
+        st1["pos_h"][:, 3] = h_iterate(pp, h_tol, h_max_it, prm, k, h_min, h_max)[0]
     ev1 = evaluate(st1, prm, k)
     p1 = p_half + 0.5 * dt * ev1["acc"]
     du2 = compatible(ev1["pos_h"], ev1["vel"], ev1["u"], mass, ev1["V"], ev1["A"], ev1["B"], ev1["gA"],
                      ev1["gB"], ev1["gv"], p_half, p1, prm, k, rho=ev1.get("rk_rho"))
     u1 = (u_half + 0.5 * dt * du2) / (1.0 + 0.5 * dt * E)
-    h1 = np.clip(thacker(pos[:, 3].astype(np.float64), ev1["N"], prm), h_min, h_max)
+    if h_mode or h_solved is not None:
+        h1 = st1["pos_h"][:, 3].astype(np.float64)
+    else:
+        h1 = np.clip(thacker(pos[:, 3].astype(np.float64), ev1["N"], prm), h_min, h_max)
     out = {"pos_h": st1["pos_h"].copy(), "vel_u": np.empty((n, 4), np.float32), "mass": st1["mass"]}
     out["pos_h"][:, 3] = h1
     out["vel_u"][:, :3] = p1

@@ -31,13 +31,15 @@ class crk_params(ctypes.Structure):
                 ("gamma", "n_h", "N_res", "C_l", "C_q", "eps", "eta_crit", "eta_fold", "C_cfl", "zeta",
                  "h_min", "h_max", "dt_max", "a", "adot")] + [
         ("precision", ctypes.c_int), ("kmax", ctypes.c_int), ("tile_order", ctypes.c_int),
-        ("density", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
+        ("density", ctypes.c_int), ("h_mode", ctypes.c_int), ("h_max_it", ctypes.c_int),
+        ("h_tol", ctypes.c_float), ("reserved", ctypes.c_int)]
 
 
 class crk_diag(ctypes.Structure):
     _fields_ = [("dt", ctypes.c_double), ("dt_next", ctypes.c_double), ("E_kin", ctypes.c_double),
                 ("E_int", ctypes.c_double), ("P", ctypes.c_double * 3),
-                ("pairs_gather", ctypes.c_longlong), ("pairs_union", ctypes.c_longlong)]
+                ("pairs_gather", ctypes.c_longlong), ("pairs_union", ctypes.c_longlong),
+                ("h_iterations", ctypes.c_longlong), ("h_unconverged", ctypes.c_longlong)]
 
 
 class crk_htb_stats(ctypes.Structure):
@@ -69,6 +71,7 @@ def lib():
         L.crk_build_stats.argtypes = [_vp, ctypes.POINTER(_ci), ctypes.POINTER(ctypes.c_longlong),
                                       ctypes.POINTER(ctypes.c_longlong), _vp]
         L.crk_neighbours.argtypes = [_vp, _ci, _vp, _vp, _vp]
+        L.crk_neighbour_lists.argtypes = [_vp, _ci, _vp, _vp, _vp]
         L.crk_volumes.argtypes = [_vp, _vp, _vp, ctypes.POINTER(ctypes.c_longlong), _vp]
         L.crk_corrections.argtypes = [_vp] + [_vp] * 7 + [_vp]
         L.crk_forces.argtypes = [_vp] + [_vp] * 12 + [ctypes.POINTER(ctypes.c_longlong), _vp]
@@ -211,6 +214,21 @@ def crk_neighbours(ctx, mode=0, stream=None):
     return cnt, hsh
 
 
+def crk_neighbour_lists(ctx, mode=0, stream=None):
+    """The neighbour lists the passes walk, in caller order: (offsets[n+1], lists)
+    as int64 / int32 CUDA tensors (mode 0 entries carry bit 31 = i in gather(j))."""
+    cnt, _ = crk_neighbours(ctx, mode, stream)
+    dev = cnt.device
+    off = torch.zeros(ctx.n + 1, dtype=torch.int64, device=dev)
+    if ctx.n:
+        off[1:] = torch.cumsum(cnt.to(torch.int64), 0)
+    total = int(off[-1].item()) if ctx.n else 0
+    lists = torch.empty(max(total, 1), dtype=torch.int32, device=dev)
+    ctx.check(lib().crk_neighbour_lists(ctx.handle, int(mode), _vp(off.data_ptr()), _vp(lists.data_ptr()),
+                                        _stream(stream)))
+    return off, lists[:total]
+
+
 def crk_volumes(ctx, with_pairs=False, stream=None):
     n = ctx.n
     dev = torch.device("cuda")
@@ -283,7 +301,8 @@ def crk_step(ctx, pos_h, vel_u, mass, dt=0.0, diag=False, stream=None):
     if not diag:
         return None
     return {"dt": d.dt, "dt_next": d.dt_next, "E_kin": d.E_kin, "E_int": d.E_int, "P": list(d.P),
-            "pairs_gather": d.pairs_gather, "pairs_union": d.pairs_union}
+            "pairs_gather": d.pairs_gather, "pairs_union": d.pairs_union, "h_iterations": d.h_iterations,
+            "h_unconverged": d.h_unconverged}
 
 
 def crk_cycle(ctx, pos_h, vel_u, mass, Delta, L, f_l=2, stream=None):
@@ -364,15 +383,16 @@ def crk_launches(ctx):
 NOALLOC_MAX_N = 16384
 
 
-def crk_volumes_noalloc(pos_h, stream=None):
+def crk_volumes_noalloc(pos_h, stream=None, with_N=True):
     """Volumes without any device allocation by the library (n <= NOALLOC_MAX_N).
-    Returns (V, Nngb); the output tensors are the caller's (allocated here by torch)."""
+    Returns (V, Nngb), Nngb None with with_N=False (the library is then given a
+    null Nngb); the output tensors are the caller's (allocated here by torch)."""
     n = pos_h.shape[0]
     dev = pos_h.device
     V = torch.empty(n, dtype=torch.float32, device=dev)
-    N = torch.empty(n, dtype=torch.float32, device=dev)
-    rc = lib().crk_volumes_noalloc(n, _t(pos_h, (n, 4), "pos_h"), _vp(V.data_ptr()), _vp(N.data_ptr()),
-                                   _stream(stream))
+    N = torch.empty(n, dtype=torch.float32, device=dev) if with_N else None
+    rc = lib().crk_volumes_noalloc(n, _t(pos_h, (n, 4), "pos_h"), _vp(V.data_ptr()),
+                                   _vp(N.data_ptr()) if with_N else None, _stream(stream))
     if rc != CRK_OK:
         raise CrkError(rc, "crk_volumes_noalloc failed")
     return V, N
@@ -526,7 +546,8 @@ def crk_steps(ctx, pos_h, vel_u, mass, nsteps, dt=0.0, use_graph=True, diag=Fals
     if not diag:
         return None
     return {"dt": d.dt, "dt_next": d.dt_next, "E_kin": d.E_kin, "E_int": d.E_int, "P": list(d.P),
-            "pairs_gather": d.pairs_gather, "pairs_union": d.pairs_union}
+            "pairs_gather": d.pairs_gather, "pairs_union": d.pairs_union, "h_iterations": d.h_iterations,
+            "h_unconverged": d.h_unconverged}
 
 
 def crk_graph_stats(ctx):

@@ -433,6 +433,9 @@ extern "C" int crk_default_params(crk_params *p) {
     p->adot = 0.0;
     p->precision = 1;
     p->kmax = 7;
+    p->h_mode = 0;
+    p->h_max_it = 50;
+    p->h_tol = 1e-4f;
     return CRK_OK;
 }
 
@@ -443,9 +446,10 @@ extern "C" int crk_create(const crk_params *p, crk_ctx **out) {
     if (p) prm = *p; else crk_default_params(&prm);
     if (!(prm.gamma > 1.0) || !(prm.n_h > 0) || !(prm.N_res > 0) || !(prm.eta_fold > 0) ||
         !(prm.h_max > 0 && prm.h_max < 1.0 / 3.0) || !(prm.h_min > 0 && prm.h_min < prm.h_max) ||
-        prm.kmax < 1 || prm.kmax > 7 || prm.precision < 0 || prm.precision > 2 || !(prm.dt_max > 0) ||
+        prm.kmax < 1 || prm.kmax > 7 || prm.precision < 0 || prm.precision > 3 || !(prm.dt_max > 0) ||
         prm.tile_order < 0 || prm.tile_order > 2 || prm.density < 0 || prm.density > 1 || !(prm.a > 0.0) || !(prm.a < 1e30) ||
-        !(prm.adot > -1e30 && prm.adot < 1e30))
+        !(prm.adot > -1e30 && prm.adot < 1e30) || prm.h_mode < 0 || prm.h_mode > 2 || prm.h_max_it < 1 ||
+        !(prm.h_tol > 0.f))
         return CRK_EINVAL;
     crk_ctx *ctx = new (std::nothrow) crk_ctx();
     if (!ctx) return CRK_ENOMEM;
@@ -676,6 +680,16 @@ extern "C" int crk_neighbours(crk_ctx *ctx, int mode, int32_t *count, uint32_t *
     if (!rc) rc = scatter_rows(ctx, ctx->flags, count, 1, s);
     if (!rc) rc = scatter_rows(ctx, ctx->st_tmp1, hash, 1, s);
     return rc;
+}
+
+extern "C" int crk_neighbour_lists(crk_ctx *ctx, int mode, const long long *offsets, int32_t *lists,
+                                   void *stream) {
+    int rc = need_built(ctx);
+    if (rc) return rc;
+    if ((ctx->n > 0 && (!offsets || !lists)) || (mode != 0 && mode != 1))
+        return crk_set_error(ctx, CRK_EINVAL, "bad arguments");
+    if (ctx->volumes_only) return crk_set_error(ctx, CRK_ESTATE, "no neighbour lists in this context");
+    return run_export_lists(ctx, mode, offsets, lists, (cudaStream_t)stream);
 }
 
 extern "C" int crk_volumes(crk_ctx *ctx, float *V, float *Nngb, long long *pairs, void *stream) {

@@ -155,6 +155,8 @@ struct crk_ctx {
     double *d_scalars = nullptr;     // [0] dt of the step, [1] dt_next, [2..] diagnostics
     int rates_valid = 0;
     int step_n = 0;
+    int h_iters = 0;                 // h_mode >= 1: P1 passes of the last step's eq:hi solve
+    long long h_unconv = 0;          // particles it left unconverged
 
     // learned smoothing-length proposal (network state and feature grid)
     float *mlp_w = nullptr;          // FP32 master weights, CRK_MLP_NPARAM
@@ -278,6 +280,7 @@ int finish_build(crk_ctx *ctx, cudaStream_t s);
 int cell_level_host(const crk_ctx *ctx);
 int run_volumes(crk_ctx *ctx, cudaStream_t s);
 int run_lists(crk_ctx *ctx, cudaStream_t s);
+int run_export_lists(crk_ctx *ctx, int mode, const long long *off, int32_t *out, cudaStream_t s);
 int scan_u32(crk_ctx *ctx, const uint32_t *in, uint32_t *out, int count, cudaStream_t s);
 int run_neighbours(crk_ctx *ctx, int mode, int32_t *cnt, uint32_t *hash, cudaStream_t s);
 int run_corrections(crk_ctx *ctx, bool with_gradv, cudaStream_t s);
@@ -286,6 +289,8 @@ int run_forces(crk_ctx *ctx, cudaStream_t s);
 int run_compatible(crk_ctx *ctx, cudaStream_t s, const unsigned long long *skip = nullptr);
 int run_compatible_dual(crk_ctx *ctx, const double *dtn, const int32_t *sbox, cudaStream_t s);
 int evaluate(crk_ctx *ctx, cudaStream_t s);   // P1..P4 and per-particle time steps (crk_step.cu)
+int propose_sorted(crk_ctx *ctx, int n, float4 *pos, const GvRec *gv, const float *Nn, float dt, float tol,
+                   cudaStream_t s);   // learned h proposal in sorted order (crk_mlp.cu)
 int gather_rows(crk_ctx *ctx, const void *in, void *out, int width_words, cudaStream_t s);
 int scatter_rows(crk_ctx *ctx, const void *in, void *out, int width_words, cudaStream_t s);
 inline int grid_for(long long n, int block) { return (int)((n + block - 1) / block); }

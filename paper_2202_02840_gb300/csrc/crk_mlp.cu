@@ -121,7 +121,8 @@ struct FeatArgs {
     int n;
     int kf;                  // feature grid level
     const float4 *pos_h;     // caller order (x, y, z, h)
-    const float *gradv;      // 9n or null (div v = trace)
+    const float *gradv;      // gv_stride n or null (div v = trace: entries 0, 4, 8 of a row)
+    int gv_stride;           // 9 (caller's 3x3 rows) or 12 (the engine's padded records)
     const float *Nngb;       // n or null
     const int32_t *fcnt;     // 8^kf cell counts
     float dt;                // step of the state (feature 6 = dt div v)
@@ -209,7 +210,7 @@ __device__ __forceinline__ float2 quad_features(const FeatArgs &a, int i, int t,
     } else {
         float dv = 0.f;
         if (a.gradv) {
-            const float *gv = a.gradv + 9 * (size_t)i;
+            const float *gv = a.gradv + (size_t)a.gv_stride * i;
             dv = __ldg(gv) + __ldg(gv + 4) + __ldg(gv + 8);
         }
         f.x = a.dt * dv;
@@ -704,6 +705,7 @@ FeatArgs feat_args(const crk_ctx *ctx, int n, const float *pos_h, const float *g
     a.kf = kf;
     a.pos_h = reinterpret_cast<const float4 *>(pos_h);
     a.gradv = gradv;
+    a.gv_stride = 9;
     a.Nngb = Nngb;
     a.fcnt = ctx->fcnt;
     a.log_cbrt_n = (float)(log((double)n) / 3.0);
@@ -887,6 +889,31 @@ extern "C" int crk_h_propose(crk_ctx *ctx, int n, float *pos_h, const float *gra
     CRK_LAUNCH_CHECK(ctx, "h proposal");
     return check_records(ctx, s);
 }
+
+namespace crk {
+// The proposal inside a step (sorted order): pos (x, y, z, h) in place, grad v
+// from the engine's padded records, the counts Nn of a P1 at the same
+// positions and h, dt the step that led to the state.
+int propose_sorted(crk_ctx *ctx, int n, float4 *pos, const GvRec *gv, const float *Nn, float dt, float tol,
+                   cudaStream_t s) {
+    int rc = need_weights(ctx);
+    if (rc) return rc;
+    if (n == 0) return CRK_OK;
+    int kf = feature_level(n);
+    prof_begin(ctx, PROF_MLP_FWD, s);
+    rc = count_cells(ctx, n, pos, kf, s);
+    if (rc) return rc;
+    FeatArgs fa = feat_args(ctx, n, reinterpret_cast<const float *>(pos), reinterpret_cast<const float *>(gv), Nn,
+                            dt, kf);
+    fa.gv_stride = 12;
+    k_mlp_fwd<1><<<fwd_blocks(ctx, n), 256, 0, s>>>(n, ctx->mlp_w, nullptr, nullptr, fa, pos, tol,
+                                                     (float)ctx->p.h_min, (float)ctx->p.h_max, (float)ctx->p.N_res);
+    ++ctx->launches;
+    prof_end(ctx, s);
+    CRK_LAUNCH_CHECK(ctx, "h proposal");
+    return CRK_OK;
+}
+}  // namespace crk
 
 extern "C" int crk_mlp_train_step(crk_ctx *ctx, int n, const float *feat, const float *target, float lr, float *grad,
                                   float *loss, void *stream) {

@@ -16,9 +16,13 @@
 // the array and must be serialised by the caller.
 #include "crk_internal.cuh"
 
+#include <atomic>
+
 namespace {
 
 constexpr int NMAX = CRK_NOALLOC_MAX_N;
+// whole tiles only: n = NMAX must not make a tile past the per-tile sub-buffers
+static_assert(NMAX % crk::TILE == 0, "CRK_NOALLOC_MAX_N must be a multiple of the 32-particle tile");
 constexpr int TMAX = NMAX / crk::TILE;
 
 constexpr size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -61,14 +65,18 @@ constexpr Layout make_layout() {
 }
 
 constexpr Layout LAY = make_layout();
+// the size the header documents (about 3.0 MB)
+static_assert(LAY.total <= 3200000, "the allocation-free scratch outgrew its documented size");
 
 }  // namespace
 
 // The scratch of every call (about 3.0 MB for NMAX = 16384).
 static __device__ __align__(256) unsigned char g_noalloc_scratch[LAY.total];
 
-// Device address of g_noalloc_scratch, resolved once per device.
-static void *g_scratch_addr[64];
+// Device address of g_noalloc_scratch, resolved once per device.  Host
+// threads making their first call at the same time may both resolve it; they
+// store the same address, and the atomic makes that race-free.
+static std::atomic<void *> g_scratch_addr[64];
 
 extern "C" int crk_volumes_noalloc(int n, const float *pos_h, float *V, float *Nngb, void *stream) {
     if (n < 0 || n > NMAX) return CRK_EINVAL;
@@ -76,12 +84,12 @@ extern "C" int crk_volumes_noalloc(int n, const float *pos_h, float *V, float *N
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return CRK_ECUDA;
     if (dev < 0 || dev >= 64) return CRK_EINVAL;
-    if (!g_scratch_addr[dev]) {
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return CRK_ECUDA;
-        g_scratch_addr[dev] = p;
+    void *addr = g_scratch_addr[dev].load(std::memory_order_acquire);
+    if (!addr) {
+        if (cudaGetSymbolAddress(&addr, g_noalloc_scratch) != cudaSuccess || !addr) return CRK_ECUDA;
+        g_scratch_addr[dev].store(addr, std::memory_order_release);
     }
-    unsigned char *b = (unsigned char *)g_scratch_addr[dev];
+    unsigned char *b = (unsigned char *)addr;
     cudaStream_t s = (cudaStream_t)stream;
 
     crk_ctx ctx;                      // host stack: no allocation anywhere
@@ -135,5 +143,9 @@ extern "C" int crk_volumes_noalloc(int n, const float *pos_h, float *V, float *N
     rc = crk::run_volumes(&ctx, s);
     if (!rc) rc = crk::scatter_rows(&ctx, ctx.V, V, 1, s);
     if (!rc && Nngb) rc = crk::scatter_rows(&ctx, ctx.Nn, Nngb, 1, s);
+    // Every buffer above was sized for NMAX, so nothing may have been grown;
+    // a later change to the build or the pass that did grow one would have
+    // swapped in library-allocated memory: report it rather than return.
+    if (!rc && ctx.alloc_gen != 0) return CRK_ESTATE;
     return rc;
 }

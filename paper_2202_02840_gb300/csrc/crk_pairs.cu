@@ -156,6 +156,54 @@ __device__ __forceinline__ void rk_solve(I m0f, const I *m1f, const I *m2f, cons
     out.c3 = make_float4((float)dB[5], (float)dB[6], (float)dB[7], (float)dB[8]);
 }
 
+// The pair sums of P2 (unnormalised: W-type sums without 495/(32 pi h^3),
+// gradient sums without 1155/(4 pi h^5)): m0 = sum V Wu, m1 = sum V x Wu,
+// m2 = sum V x x Wu (6 distinct), dm0 = sum V x Gu, s1 = sum V x^a x^g Gu (6),
+// s2 = sum V x^a x^b x^g Gu (10), with grad W = 1155/(4 pi h^5) Gu x.
+template <typename T>
+struct PairSums {
+    T m0, m1[3], m2[6], dm0[3], s1[6], s2[10];
+};
+
+// Moments from the pair sums: W-type sums scale by cW = 495/(32 pi h^3),
+// gradient sums by cG = 1155/(4 pi h^5); then
+//   d_g m1^a = delta_ag m0 + cG sum V x^a x^g Gu,
+//   d_g m2^ab = delta_ag m1^b + delta_bg m1^a + cG sum V x^a x^b x^g Gu.
+// The diagonal of d m1 nearly cancels (sum V x^a d_a W ~ -m0), so the mixed
+// paths form every moment in FP64 from the (compensated) sums and FP64
+// constants before that cancellation.
+template <typename T>
+__device__ __forceinline__ void moments(float h, const PairSums<T> &s, T &m0, T *m1, T *m2, T *dm0, T *dm1,
+                                        T *dm2) {
+    T ih = (T)1 / (T)h, ih2 = ih * ih, ih3 = ih2 * ih;
+    T cW = (T)KW_D * ih3;         // 495 / (32 pi)
+    T cG = (T)KG_D * ih3 * ih2;   // 1155 / (4 pi)
+    m0 = cW * s.m0;
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        m1[a] = cW * s.m1[a];
+        dm0[a] = cG * s.dm0[a];
+    }
+#pragma unroll
+    for (int q = 0; q < 6; q++) m2[q] = cW * s.m2[q];
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+        for (int g = 0; g < 3; g++) dm1[3 * a + g] = cG * s.s1[sym(a, g)] + (a == g ? m0 : (T)0);
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+        for (int b = a; b < 3; b++)
+#pragma unroll
+            for (int g = 0; g < 3; g++) {
+                int q = sym(a, b);
+                T v = cG * s.s2[sym3(a, b, g)];
+                if (a == g) v += m1[b];
+                if (b == g) v += m1[a];
+                dm2[3 * q + g] = v;
+            }
+}
+
 template <bool FP64_SOLVE, bool COMP>
 struct P2 {
     static constexpr bool GATHER = true;
@@ -248,48 +296,193 @@ struct P2 {
     // The diagonal of d m1 nearly cancels (sum V x^a d_a W ~ -m0), so the mixed
     // path forms every moment in FP64 from the compensated (hi, lo) sums and
     // FP64 constants before that cancellation.
-    template <typename T>
-    __device__ static void moments(const IState &s, T &m0, T *m1, T *m2, T *dm0, T *dm1, T *dm2) {
-        T ih = (T)1 / (T)s.h, ih2 = ih * ih, ih3 = ih2 * ih;
-        T cW = (T)4.9238560270859813 * ih3;     // 495 / (32 pi)
-        T cG = (T)91.912032198900327 * ih3 * ih2; // 1155 / (4 pi)
-        auto val = [](const Acc<COMP> &a) -> T { return COMP ? (T)a.s - (T)a.c : (T)a.s; };
-        m0 = cW * val(s.m0);
-#pragma unroll
-        for (int a = 0; a < 3; a++) {
-            m1[a] = cW * val(s.m1[a]);
-            dm0[a] = cG * val(s.dm0[a]);
-        }
-#pragma unroll
-        for (int q = 0; q < 6; q++) m2[q] = cW * val(s.m2[q]);
-#pragma unroll
-        for (int a = 0; a < 3; a++)
-#pragma unroll
-            for (int g = 0; g < 3; g++) dm1[3 * a + g] = cG * val(s.s1[sym(a, g)]) + (a == g ? m0 : (T)0);
-#pragma unroll
-        for (int a = 0; a < 3; a++)
-#pragma unroll
-            for (int b = a; b < 3; b++)
-#pragma unroll
-                for (int g = 0; g < 3; g++) {
-                    int q = sym(a, b);
-                    T v = cG * val(s.s2[sym3(a, b, g)]);
-                    if (a == g) v += m1[b];
-                    if (b == g) v += m1[a];
-                    dm2[3 * q + g] = v;
-                }
-    }
     __device__ static void finish(IState &s, int i, const Params &p) {
         CorrRec out;
+        auto val = [](const Acc<COMP> &a) -> double { return COMP ? (double)a.s - (double)a.c : (double)a.s; };
         if (FP64_SOLVE) {
+            PairSums<double> ps;
+            ps.m0 = val(s.m0);
+            for (int a = 0; a < 3; a++) ps.m1[a] = val(s.m1[a]), ps.dm0[a] = val(s.dm0[a]);
+            for (int q = 0; q < 6; q++) ps.m2[q] = val(s.m2[q]), ps.s1[q] = val(s.s1[q]);
+            for (int q = 0; q < 10; q++) ps.s2[q] = val(s.s2[q]);
             double m0, m1[3], m2[6], dm0[3], dm1[9], dm2[18];
-            moments<double>(s, m0, m1, m2, dm0, dm1, dm2);
+            moments<double>(s.h, ps, m0, m1, m2, dm0, dm1, dm2);
             rk_solve<double, double>(m0, m1, m2, dm0, dm1, dm2, out);
         } else {
+            PairSums<float> ps;
+            ps.m0 = s.m0.value();
+            for (int a = 0; a < 3; a++) ps.m1[a] = s.m1[a].value(), ps.dm0[a] = s.dm0[a].value();
+            for (int q = 0; q < 6; q++) ps.m2[q] = s.m2[q].value(), ps.s1[q] = s.s1[q].value();
+            for (int q = 0; q < 10; q++) ps.s2[q] = s.s2[q].value();
             float m0, m1[3], m2[6], dm0[3], dm1[9], dm2[18];
-            moments<float>(s, m0, m1, m2, dm0, dm1, dm2);
+            moments<float>(s.h, ps, m0, m1, m2, dm0, dm1, dm2);
             rk_solve<float, float>(m0, m1, m2, dm0, dm1, dm2, out);
         }
+        p.corr[i] = out;
+    }
+};
+
+// ---------------------------------------------------------------- P2 in float-float (precision 3)
+//
+// On lattice-like neighbourhoods the odd moments, grad m0, and the diagonal of
+// grad m1 = delta m0 + sum V x grad W cancel to ~1e-4 of their terms, so the
+// result keeps only ~1e-4 of the terms' relative accuracy: FP32 pair terms
+// (x rounded to FP32, t = 1 - eta rounded and raised to the sixth power, each
+// product rounded) leave 1e-5 .. 3e-5 of the field RMS in B, grad A, grad B.
+// This form carries every pair term as an unevaluated sum hi + lo of two
+// floats (an error-free product hi = a b, lo = fma(a, b, -hi), plus the
+// operands' own lo parts to first order), starting from exact inputs: the
+// separation x = dq 2^-32 split exactly into a float and its integer residual,
+// r = sqrt(R^2) from the exact integer R^2 with one Newton correction, eta
+// = r / h with its division residual, and t = 1 - eta by an exact
+// Fast2Sum.  The hi parts are summed by TwoSum, their rounding errors and the
+// lo parts in plain FP32 (they are ~1e-7 of the terms, so their own rounding
+// is negligible); each moment is then hi + lo in FP64.  Only FP32
+// arithmetic runs per pair; the __f*_rn intrinsics keep the compiler from
+// fusing the products whose rounding errors are being captured.
+struct FF {
+    float hi, lo;
+};
+constexpr float K35_3_LO = (float)(35.0 / 3.0 - (double)K35_3);   // 35/3 - K35_3
+
+__device__ __forceinline__ FF ff_mul(FF a, FF b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    const float e = fmaf(a.hi, b.hi, -p);                     // exact: a.hi b.hi - p
+    return FF{p, fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e))};
+}
+
+__device__ __forceinline__ FF ff_add(FF a, float b) {      // TwoSum of a.hi + b, lo carried
+    const float s = __fadd_rn(a.hi, b);
+    const float bb = __fsub_rn(s, a.hi);
+    const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return FF{s, e + a.lo};
+}
+
+// x = d 2^-32 exactly: hi = the float nearest d (times 2^-32), lo = the integer
+// residual (|residual| <= 2^6 for |d| < 2^31) times 2^-32
+__device__ __forceinline__ FF ff_coord(int d) {
+    const float f = __int2float_rn(d);
+    const int back = __float2int_rz(f);
+    return FF{f * TWO_M32, __int2float_rn(d - back) * TWO_M32};
+}
+
+// accumulator of FF terms: each hi part is added by TwoSum, whose exact
+// rounding error joins the lo parts in a plain FP32 sum.  (Kahan's
+// compensation is exact only while the running sum outweighs the term, which
+// the cancelling moment sums violate: it left ~2e-6 of the RMS in B.)
+struct AccFF {
+    float s = 0.f, l = 0.f;
+    __device__ __forceinline__ void add(FF v) {
+        const float t = __fadd_rn(s, v.hi);
+        const float bp = __fsub_rn(t, s);
+        const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(v.hi, bp));
+        s = t;
+        l += e + v.lo;
+    }
+    __device__ __forceinline__ double value() const { return (double)s + (double)l; }
+};
+
+__device__ __forceinline__ void merge_acc(AccFF &d, const AccFF &o) { d.add(FF{o.s, o.l}); }
+
+struct P2X {
+    static constexpr bool GATHER = true;
+    static constexpr int UNROLL = 2;
+    static constexpr bool ENTRIES = true;
+    static constexpr bool PERSISTENT = false;
+    static constexpr bool PREFETCH = false;
+    static constexpr bool NOTUNE = true;   // one accuracy mode, one loop form
+    using Rec = uint4;
+    using Params = P2<true, true>::Params;
+    struct IState {
+        uint4 q;
+        float h;
+        FF ih;                                  // 1/h as hi + lo
+        AccFF m0, m1[3], m2[6], dm0[3], s1[6], s2[10];
+    };
+    __device__ static void init(IState &s, int i, bool valid, const Params &p) {
+        s.q = valid ? p.q4[i] : make_uint4(0, 0, 0, 0);
+        s.h = valid ? p.hs[i] : 1.f;
+        const float ih = __frcp_rn(s.h);
+        s.ih = FF{ih, __fmul_rn(fmaf(-ih, s.h, 1.f), ih)};   // 1/h - ih to first order
+        s.m0 = AccFF();
+        for (int a = 0; a < 3; a++) s.m1[a] = s.dm0[a] = AccFF();
+        for (int a = 0; a < 6; a++) s.m2[a] = s.s1[a] = AccFF();
+        for (int a = 0; a < 10; a++) s.s2[a] = AccFF();
+        if (valid) s.m0.add(FF{__uint_as_float(__ldg(&p.qV[i].w)), 0.f});   // self: W(0) unnormalised 1
+    }
+    __device__ static void zero(IState &s) {
+        s.m0 = AccFF();
+        for (int a = 0; a < 3; a++) s.m1[a] = s.dm0[a] = AccFF();
+        for (int a = 0; a < 6; a++) s.m2[a] = s.s1[a] = AccFF();
+        for (int a = 0; a < 10; a++) s.s2[a] = AccFF();
+    }
+    __device__ static void merge(IState &s, const IState &o) {
+        merge_acc(s.m0, o.m0);
+        for (int a = 0; a < 3; a++) merge_acc(s.m1[a], o.m1[a]), merge_acc(s.dm0[a], o.dm0[a]);
+        for (int a = 0; a < 6; a++) merge_acc(s.m2[a], o.m2[a]), merge_acc(s.s1[a], o.s1[a]);
+        for (int a = 0; a < 10; a++) merge_acc(s.s2[a], o.s2[a]);
+    }
+    __device__ static Rec load(uint32_t e, size_t, const Params &p) { return __ldg(p.qV + (e & 0x3fffffffu)); }
+    __device__ static void pair(IState &s, const Rec &rc, uint32_t, size_t, bool, const Params &) {
+        const int dx = (int)(s.q.x - rc.x), dy = (int)(s.q.y - rc.y), dz = (int)(s.q.z - rc.z);
+        const float Vj = __uint_as_float(rc.w);
+        const FF x[3] = {ff_coord(dx), ff_coord(dy), ff_coord(dz)};
+        // r 2^32 = sqrt(R^2), R^2 exact; hi correctly rounded, lo from one Newton step
+        const unsigned long long R2 = r2_fixed(dx, dy, dz);
+        const float R2h = __ull2float_rn(R2);
+        const float R2l = __ll2float_rn((long long)(R2 - __float2ull_rz(R2h)));
+        const float rh = __fsqrt_rn(R2h);
+        const float rl = rh > 0.f ? __fdividef(fmaf(-rh, rh, R2h) + R2l, 2.f * rh) : 0.f;
+        // eta = r / h: hi = rounded product, lo = its residual plus the lo parts
+        const FF r = FF{rh * TWO_M32, rl * TWO_M32};
+        const FF eta = ff_mul(r, s.ih);
+        // t = 1 - eta: Fast2Sum (|1| >= eta) gives the exact residual of 1 - eta.hi
+        const float th = __fsub_rn(1.f, eta.hi);
+        const float tr = __fsub_rn(__fsub_rn(th, 1.f), -eta.hi);   // (1 - eta.hi) - th, negated
+        const FF t = FF{th, -tr - eta.lo};
+        const FF t2 = ff_mul(t, t), t4 = ff_mul(t2, t2), t5 = ff_mul(t4, t), t6 = ff_mul(t5, t);
+        // poly = 1 + eta (6 + eta 35/3), with 35/3 as the float K35_3 plus its residual
+        const FF poly = ff_add(ff_mul(ff_add(ff_mul(eta, FF{K35_3, K35_3_LO}), 6.f), eta), 1.f);
+        const FF Wu = ff_mul(t6, poly);                              // W / (495/(32 pi h^3))
+        const FF g5 = ff_add(ff_mul(eta, FF{5.f, 0.f}), 1.f);
+        const FF Gn = ff_mul(t5, g5);                                // -grad W / (1155/(4 pi h^5) x)
+        const FF w = ff_mul(FF{Vj, 0.f}, Wu);
+        const FF gn = ff_mul(FF{Vj, 0.f}, Gn);
+        const FF gx[3] = {ff_mul(gn, x[0]), ff_mul(gn, x[1]), ff_mul(gn, x[2])};
+        s.m0.add(w);
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            s.m1[a].add(ff_mul(w, x[a]));
+            s.dm0[a].add(FF{-gx[a].hi, -gx[a].lo});
+        }
+        // m2 and s2 in float-float too: where m2 is nearly singular along a
+        // direction no axis shares (a tilted sheet or filament, cond ~1e6) its
+        // FP32 rounding is amplified cond-fold in B and grad B
+#pragma unroll
+        for (int a = 0; a < 3; a++)
+#pragma unroll
+            for (int b = a; b < 3; b++) {
+                const FF xab = ff_mul(x[a], x[b]);
+                s.m2[sym(a, b)].add(ff_mul(w, xab));
+                const FF sx = ff_mul(x[a], gx[b]);
+                s.s1[sym(a, b)].add(FF{-sx.hi, -sx.lo});
+#pragma unroll
+                for (int gg = b; gg < 3; gg++) {
+                    const FF v = ff_mul(xab, gx[gg]);
+                    s.s2[sym3(a, b, gg)].add(FF{-v.hi, -v.lo});
+                }
+            }
+    }
+    __device__ static void finish(IState &s, int i, const Params &p) {
+        PairSums<double> ps;
+        ps.m0 = s.m0.value();
+        for (int a = 0; a < 3; a++) ps.m1[a] = s.m1[a].value(), ps.dm0[a] = s.dm0[a].value();
+        for (int q = 0; q < 6; q++) ps.m2[q] = s.m2[q].value(), ps.s1[q] = s.s1[q].value();
+        for (int q = 0; q < 10; q++) ps.s2[q] = s.s2[q].value();
+        double m0, m1[3], m2[6], dm0[3], dm1[9], dm2[18];
+        moments<double>(s.h, ps, m0, m1, m2, dm0, dm1, dm2);
+        CorrRec out;
+        rk_solve<double, double>(m0, m1, m2, dm0, dm1, dm2, out);
         p.corr[i] = out;
     }
 };
@@ -450,7 +643,10 @@ int run_density(crk_ctx *ctx, cudaStream_t s) {
 
 int run_corrections(crk_ctx *ctx, bool with_gradv, cudaStream_t s) {
     int rc;
-    if (ctx->p.precision == 2) {
+    if (ctx->p.precision == 3) {
+        P2X::Params p{ctx->q4, ctx->qV, ctx->hs, ctx->corr};
+        rc = launch_lpass<P2X, 4>(ctx, PROF_P2, p, s, "P2 corrections (float-float)");
+    } else if (ctx->p.precision == 2) {
         typedef P2<true, true> K;
         K::Params p{ctx->q4, ctx->qV, ctx->hs, ctx->corr};
         rc = launch_lpass<K, 4>(ctx, PROF_P2, p, s, "P2 corrections");
@@ -464,7 +660,7 @@ int run_corrections(crk_ctx *ctx, bool with_gradv, cudaStream_t s) {
         rc = launch_lpass<K, 4>(ctx, PROF_P2, p, s, "P2 corrections");
     }
     if (rc || !with_gradv) return rc;
-    if (ctx->p.precision == 2) {
+    if (ctx->p.precision >= 2) {
         P3<true>::Params p3{ctx->q4, ctx->qV, ctx->hs, ctx->vel, ctx->corr, ctx->gv, (float)(1.0 / ctx->p.a)};
         return launch_lpass<P3<true>, 4>(ctx, PROF_P3, p3, s, "P3 grad v");
     }

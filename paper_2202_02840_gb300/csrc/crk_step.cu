@@ -28,6 +28,7 @@ struct StepConsts {
     // comoving variables (1, 1, 0, 0 in a static box)
     float inv_a, inv_a2, adot;
     float E;   // (adot/a)(3(gamma-1) + 2): expansion term of eq:CosmoEngEqn
+    int keep_h;   // h_mode >= 1: the state keeps the solved h of its evaluation
 };
 
 static StepConsts step_consts(const crk_params &p) {
@@ -45,6 +46,7 @@ static StepConsts step_consts(const crk_params &p) {
     c.inv_a2 = (float)(1.0 / (p.a * p.a));
     c.adot = (float)p.adot;
     c.E = (float)(p.adot / p.a * (3.0 * (p.gamma - 1.0) + 2.0));
+    c.keep_h = p.h_mode >= 1;
     return c;
 }
 
@@ -213,10 +215,12 @@ __global__ void k_finish(int n, const double *sc, const int32_t *__restrict__ sb
     float h = (float)(0.5 * slot_dt(sc, sbox, s));
     float4 a = va[s];
     st_vel[s] = make_float4(a.x, a.y, a.z, fmaf(h, du[s], st_half[s].w) / fmaf(h, c.E, 1.f));
-    float d = cbrtf(c.N_res / Nn[s]);
-    float lam = d < 1.f ? 0.2f * (1.f + d * d) : 0.2f * (1.f + 1.f / (d * d * d));
-    float hn = hs[s] * (1.f - lam + lam * d);
-    hn = fminf(fmaxf(hn, c.h_min), c.h_max);
+    float hn = hs[s];
+    if (!c.keep_h) {   // the evolved h: one eq:thacker update of the evaluation's count
+        float d = cbrtf(c.N_res / Nn[s]);
+        float lam = d < 1.f ? 0.2f * (1.f + d * d) : 0.2f * (1.f + 1.f / (d * d * d));
+        hn = fminf(fmaxf(hs[s] * (1.f - lam + lam * d), c.h_min), c.h_max);
+    }
     float4 p = st_pos[s];
     st_pos[s] = make_float4(p.x, p.y, p.z, hn);
 }
@@ -305,6 +309,30 @@ __global__ void k_h_iter(int n, StepConsts c, float tol, const float *__restrict
     if ((threadIdx.x & 31) == 0 && nd) atomicAdd(notdone, (unsigned long long)nd);
 }
 
+// after the proposal wrote st_pos.w: the sorted h and the fixed-point support
+__global__ void k_take_h(int n, const float4 *__restrict__ st_pos, float *__restrict__ hs, uint4 *__restrict__ q4) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const float h = st_pos[s].w;
+    hs[s] = h;
+    q4[s].w = to_fixed(h);
+}
+
+__global__ void k_put_h(int n, const float *__restrict__ hs, float4 *__restrict__ st_pos) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    st_pos[s].w = hs[s];
+}
+
+// grad v records of the last evaluation into the new sorted order (new slot s
+// takes old slot idx[s])
+__global__ void k_permute_gv(int n, const int32_t *__restrict__ idx, const GvRec *__restrict__ in,
+                             GvRec *__restrict__ out) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    out[s] = in[idx[s]];
+}
+
 __global__ void k_write_h(int n, const int32_t *__restrict__ perm, const float *__restrict__ hs, float4 *pos_h) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
@@ -358,12 +386,78 @@ extern "C" int crk_reset_rates(crk_ctx *ctx) {
     return CRK_OK;
 }
 
+// eq:hi solved at the drifted positions before the evaluation (h_mode >= 1):
+// repeated P1 (summed in the walk, no lists) and eq:thacker updates of the
+// particles not yet converged, the tile tree and tile-pair lists refitted to
+// the new h after each (no re-sort), until every particle meets
+// |Delta_N - 1| <= h_tol or sits at a bound its update points beyond (the
+// rule of crk_h_iterate), or h_max_it passes.  h_mode 2 replaces the first
+// update by the learned proposal (judged: particles already converged keep
+// their h); its features take the grad v of the last evaluation, gv_old in the
+// previous sorted order (idx: new slot -> old slot), and the step's dt.
+static int solve_h(crk_ctx *ctx, int n, const int32_t *idx, cudaStream_t s, int *iters, long long *unconv) {
+    StepConsts c = step_consts(ctx->p);
+    const float tol = ctx->p.h_tol;
+    const int max_it = ctx->p.h_max_it;
+    const int b = 256, g = grid_for(n, b);
+    int rc = CRK_OK;
+    if (ctx->p.h_mode == 2) {   // the last evaluation's grad v, in the new order (frec is free until P4)
+        k_permute_gv<<<g, b, 0, s>>>(n, idx, ctx->gv, reinterpret_cast<GvRec *>(ctx->frec));
+        ++ctx->launches;
+        CRK_LAUNCH_CHECK(ctx, "permute grad v");
+    }
+    CRK_CUDA(ctx, cudaMemsetAsync(ctx->flags, 0, sizeof(int32_t) * n, s));
+    const int vo = ctx->volumes_only;
+    ctx->volumes_only = 1;
+    int it = 0;
+    unsigned long long nd = 1;
+    for (it = 1; it <= max_it; it++) {
+        rc = run_volumes(ctx, s);
+        if (rc) break;
+        if (it == 1 && ctx->p.h_mode == 2) {
+            double dt = 0.0;
+            CRK_CUDA(ctx, cudaMemcpyAsync(&dt, ctx->d_scalars, sizeof(double), cudaMemcpyDeviceToHost, s));
+            CRK_CUDA(ctx, cudaStreamSynchronize(s));
+            rc = propose_sorted(ctx, n, ctx->st_pos, reinterpret_cast<const GvRec *>(ctx->frec), ctx->Nn, (float)dt,
+                                tol, s);
+            if (rc) break;
+            k_take_h<<<g, b, 0, s>>>(n, ctx->st_pos, ctx->hs, ctx->q4);
+            ++ctx->launches;
+            CRK_LAUNCH_CHECK(ctx, "proposed h");
+        } else {
+            CRK_CUDA(ctx, cudaMemsetAsync(ctx->counters + CNT_NOTDONE, 0, sizeof(unsigned long long), s));
+            k_h_iter<<<g, b, 0, s>>>(n, c, tol, ctx->Nn, ctx->hs, ctx->q4, ctx->flags, ctx->counters + CNT_NOTDONE);
+            ++ctx->launches;
+            CRK_LAUNCH_CHECK(ctx, "h iteration");
+            rc = crk_sync_counters(ctx, s);
+            if (rc) break;
+            nd = ctx->h_counters[CNT_NOTDONE];
+            if (nd == 0) break;
+        }
+        rc = build_tree(ctx, s);
+        if (!rc) rc = rebuild_lists(ctx, s);
+        if (!rc) rc = finish_build(ctx, s);
+        if (rc) break;
+    }
+    ctx->volumes_only = vo;
+    ctx->lists_valid = 0;
+    if (rc) return rc;
+    *iters = it > max_it ? max_it : it;
+    *unconv = (long long)nd;
+    k_put_h<<<g, b, 0, s>>>(n, ctx->hs, ctx->st_pos);
+    ++ctx->launches;
+    CRK_LAUNCH_CHECK(ctx, "solved h");
+    return CRK_OK;
+}
+
 // One KDK step of all boxes (one box unless batched).  dt_req applies to every
 // box (<= 0: CFL); dt_box (device, one per box) overrides it when not null.
 static int step_impl(crk_ctx *ctx, int n, float *pos_h, float *vel_u, const float *mass, double dt_req,
                      const double *dt_box, bool batched, cudaStream_t s) {
     StepConsts c = step_consts(ctx->p);
     int rc;
+    if (batched && ctx->p.h_mode != 0)
+        return crk_set_error(ctx, CRK_ESTATE, "h_mode solves eq:hi in one-box steps only");
     int b = 256, g = grid_for(n, b);
     const bool fresh = !ctx->rates_valid || ctx->step_n != n || !ctx->built || ctx->n != n ||
                        (batched ? ctx->nbox < 1 : ctx->nbox > 1);
@@ -423,6 +517,15 @@ static int step_impl(crk_ctx *ctx, int n, float *pos_h, float *vel_u, const floa
     t = ctx->st_half; ctx->st_half = ctx->va; ctx->va = t;
     rc = gather_rows(ctx, mass, ctx->mass, 1, s);
     if (rc) return rc;
+    ctx->h_iters = 0;
+    ctx->h_unconv = 0;
+    if (ctx->p.h_mode >= 1) {   // eq:hi at x1 before the evaluation
+        rc = solve_h(ctx, n, ctx->idx_a, s, &ctx->h_iters, &ctx->h_unconv);
+        if (rc) {
+            ctx->rates_valid = 0;
+            return rc;
+        }
+    }
     // evaluation at (x1, p_p, u_p)
     CRK_CUDA(ctx, cudaMemcpyAsync(ctx->vel, ctx->st_vel, sizeof(float4) * n, cudaMemcpyDeviceToDevice, s));
     rc = evaluate(ctx, s);
@@ -477,6 +580,8 @@ extern "C" int crk_step(crk_ctx *ctx, int n, float *pos_h, float *vel_u, const f
     diag->P[2] = h[6];
     diag->pairs_gather = (long long)ctx->h_counters[CNT_PAIRS_G];
     diag->pairs_union = (long long)ctx->h_counters[CNT_PAIRS_U];
+    diag->h_iterations = ctx->h_iters;
+    diag->h_unconverged = ctx->h_unconv;
     return CRK_OK;
 }
 
@@ -548,6 +653,8 @@ extern "C" int crk_step_batched(crk_ctx *ctx, int n, int nbox, const int32_t *bo
         diag[b].P[2] = red[8 * b + 4];
         diag[b].pairs_gather = (long long)ctx->h_counters[CNT_PAIRS_G];
         diag[b].pairs_union = (long long)ctx->h_counters[CNT_PAIRS_U];
+        diag[b].h_iterations = 0;   // batched steps keep the evolved h
+        diag[b].h_unconverged = 0;
     }
     return CRK_OK;
 }
@@ -603,6 +710,8 @@ int run_diag(crk_ctx *ctx, int n, crk_diag *diag, cudaStream_t s) {
     diag->P[2] = h[6];
     diag->pairs_gather = (long long)ctx->h_counters[CNT_PAIRS_G];
     diag->pairs_union = (long long)ctx->h_counters[CNT_PAIRS_U];
+    diag->h_iterations = ctx->h_iters;
+    diag->h_unconverged = ctx->h_unconv;
     return CRK_OK;
 }
 
@@ -692,7 +801,8 @@ static int steps_impl(crk_ctx *ctx, int n, float *pos_h, float *vel_u, const flo
             for (int k = PROF_P1; k <= PROF_P5; k++) tuning |= (k != PROF_PN && !ctx->tune_done[k]);
             tuning |= !ctx->tune_done[TUNE_P5_DUAL] || (ctx->p.density && !ctx->tune_done[PROF_DENS]);
         }
-        if (done == nsteps || (use_graph && !fresh && !tuning)) break;
+        // a step that solves eq:hi syncs the host once per iteration: never captured
+        if (done == nsteps || (use_graph && !fresh && !tuning && ctx->p.h_mode == 0)) break;
         rc = step_impl(ctx, n, pos_h, vel_u, mass, dt, nullptr, batched, s);
         if (rc) return rc;
         done++;

@@ -200,7 +200,7 @@ __global__ void __launch_bounds__(WALK_WARPS * 32) k_walk(WalkArgs a) {
             float ih3 = inv_h * inv_h * inv_h;
             float nsum = KW * ih3 * acc;                       // n_i, eq:vol
             a.V[i] = 1.f / nsum;
-            if (a.Nn) a.Nn[i] = (4.18879020f * h * h * h) * nsum;   // eq:hi
+            if (a.Nn) a.Nn[i] = (K4PI_3 * h * h * h) * nsum;   // eq:hi
         }
         a.cnt_g[i] = cg;
         a.cnt_u[i] = cu;
@@ -432,6 +432,42 @@ int run_lists(crk_ctx *ctx, cudaStream_t s) {
     return crk_set_error(ctx, CRK_ECAPACITY, "neighbour lists keep overflowing");
 }
 
+// The lists the passes walk, exported in caller order: thread per sorted slot
+// s writes, from off[perm[s]], mode 0: its gather set (self first, then the
+// front columns) as caller index | (j's kernel reaches i) << 31; mode 1: its
+// pair set (front columns, then the back columns) as caller indices.
+__global__ void k_export_lists(int n, int kcap, int mode, const int32_t *__restrict__ perm,
+                               const int32_t *__restrict__ cnt_g, const int32_t *__restrict__ cnt_u,
+                               const uint32_t *__restrict__ ent, const long long *__restrict__ off,
+                               int32_t *__restrict__ out) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const int tile = s / TILE, lane = s % TILE;
+    const uint32_t *col0 = ent + (size_t)tile * kcap * 32 + lane;
+    const int ci = perm[s];
+    long long o = off[ci];
+    const int cg = min(cnt_g[s], kcap), cu = min(cnt_u[s], kcap);
+    if (mode == 0) out[o++] = (int32_t)((uint32_t)ci | 0x80000000u);
+    for (int k = 0; k < cg; k++) {
+        const uint32_t e = col0[(size_t)k * 32];
+        const uint32_t j = (uint32_t)perm[e & 0x3fffffffu];
+        out[o++] = (int32_t)(mode == 0 ? (j | (e & 0x80000000u)) : j);
+    }
+    if (mode == 1)
+        for (int k = cg; k < cu; k++) out[o++] = perm[col0[(size_t)(kcap - 1 - (k - cg)) * 32] & 0x3fffffffu];
+}
+
+int run_export_lists(crk_ctx *ctx, int mode, const long long *off, int32_t *out, cudaStream_t s) {
+    if (ctx->n == 0) return CRK_OK;
+    int rc = run_lists(ctx, s);
+    if (rc) return rc;
+    k_export_lists<<<grid_for(ctx->n, 256), 256, 0, s>>>(ctx->n, ctx->kcap, mode, ctx->perm, ctx->cnt_g, ctx->cnt_u,
+                                                          ctx->ent, off, out);
+    ++ctx->launches;
+    CRK_LAUNCH_CHECK(ctx, "export lists");
+    return CRK_OK;
+}
+
 // P1 volumes over the gather lists (eq:vol, eq:hi), self included.
 struct P1 {
     static constexpr bool GATHER = true;
@@ -472,7 +508,7 @@ struct P1 {
         float nsum = KW * ih3 * s.acc;                       // n_i, eq:vol
         float V = 1.f / nsum;
         p.V[i] = V;
-        if (p.Nn) p.Nn[i] = (4.18879020f * s.h * s.h * s.h) * nsum;   // eq:hi
+        if (p.Nn) p.Nn[i] = (K4PI_3 * s.h * s.h * s.h) * nsum;   // eq:hi
         p.qV[i] = make_uint4(s.q.x, s.q.y, s.q.z, __float_as_uint(V));
     }
 };

@@ -57,7 +57,11 @@ class Snapshot:
 
 def sedov_snapshots(n_side=32, steps=100, every=10, seed=3, tol=1e-4, max_it=60, params=None):
     """Advance a Sedov blast and take a Snapshot at every `every`-th step."""
-    st = inputs.sedov(n_side, seed=seed)
+    return run_snapshots(inputs.sedov(n_side, seed=seed), steps, every, tol, max_it, params)
+
+
+def run_snapshots(st, steps=100, every=10, tol=1e-4, max_it=60, params=None):
+    """Advance the state st (evolved h) and take a Snapshot at every `every`-th step."""
     pos, vel, mass = dev(st["pos_h"]), dev(st["vel_u"]), dev(st["mass"])
     p = params or {}
     stepper = crk.crk_create(**p)

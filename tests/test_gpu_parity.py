@@ -76,6 +76,40 @@ def test_neighbour_sets_bit_exact(case, mode):
     assert np.array_equal(hsh.cpu().numpy().view(np.uint32), set_hash(oc, ol))
 
 
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("case", list(CASES))
+def test_neighbour_lists_exact(case, mode):
+    """The lists the passes walk, element by element after sorting each
+    particle's list, against the oracle's brute-force sets; in mode 0 the
+    "j's kernel reaches i" flag of every gather entry against i in gather(j)."""
+    st = CASES[case]()
+    ctx = fresh(st)
+    off, lst = crk.crk_neighbour_lists(ctx, mode)
+    off = off.cpu().numpy()
+    raw = lst.cpu().numpy().view(np.uint32)
+    ids = (raw & np.uint32(0x7FFFFFFF)).astype(np.int64)
+    oc, ol = O.neighbours(st["pos_h"], mode=mode)
+    ooff = np.concatenate([[0], np.cumsum(oc.astype(np.int64))])
+    assert np.array_equal(off, ooff)
+    n = len(oc)
+    row = np.repeat(np.arange(n), oc)
+    got = np.lexsort((ids, row))
+    want = np.lexsort((ol.astype(np.int64), row))
+    assert np.array_equal(ids[got], ol.astype(np.int64)[want])
+    if mode == 0:
+        flag = (raw >> np.uint32(31)).astype(bool)
+        # i in gather(j): the fixed-point predicate R^2 < H_j^2 (exact integers)
+        q, H = O.fixed_point(st["pos_h"])
+        dq = (q[row].astype(np.int64) - q[ids].astype(np.int64) + 2 ** 31) % 2 ** 32 - 2 ** 31
+        a = np.abs(dq).astype(np.uint64)
+        R2 = (a * a).sum(axis=1, dtype=np.uint64)          # < 3 * 2^62: exact in uint64
+        Hj = H[ids].astype(np.uint64)
+        want_flag = R2 < Hj * Hj
+        assert np.array_equal(flag, want_flag)
+    else:
+        assert not np.any(raw >> np.uint32(31))
+
+
 # ---------------------------------------------------------------- passes in isolation
 
 @pytest.mark.parametrize("case", list(CASES))
@@ -107,7 +141,7 @@ def oracle_chain(st):
     return dict(V=V, p2=p2, r=r, gv_o=gv_o, gv=gv, p4=p4, vel=vel, u=u, m=m)
 
 
-@pytest.mark.parametrize("precision", [0, 1, 2])
+@pytest.mark.parametrize("precision", [0, 1, 2, 3])
 @pytest.mark.parametrize("case", ["uniform16", "clustered3000", "sedov16"])
 def test_corrections(case, precision):
     st = CASES[case]()

@@ -475,6 +475,27 @@ def test_kdk_step_is_second_order_with_the_predictor():
     assert np.all(r1 > 3.3) and np.all(r2 > 3.3), (r1, r2)
 
 
+@pytest.mark.parametrize("h_mode", [1, 2])
+def test_kdk_step_solving_eq_hi_leaves_a_solution(h_mode):
+    """A step with h_mode 1 (solve eq:hi from the state's h) or 2 (from the
+    constant-density proposal h (N_res/N)^(1/3), an untrained network with a
+    zero output row) evaluates at, and keeps, an h that meets eq:hi to the
+    tolerance at the drifted positions: the count of a fresh P1 there is
+    within tol of N_res for every particle.  With the evolved h (mode 0) the
+    same step leaves counts far from N_res (h = 3.5 spacings, N ~ 180).  On a
+    16^3 lattice the solution, h ~ 4 spacings = 0.25, lies inside the h bounds."""
+    st0 = _converging_flow(side=16)
+    ev = O.evaluate(st0)
+    dt = 0.5 * float(np.min(O.cfl_dt(ev)))
+    w = inputs.mlp_init(3)
+    st1, ev1, _ = O.kdk_step(st0, ev, dt=dt, h_mode=h_mode, h_tol=1e-4, h_max_it=200, w=w)
+    N = O.volumes(st1["pos_h"])["N"]
+    assert np.max(np.abs(np.cbrt(268.0 / N) - 1.0)) <= 1e-4 + 1e-9
+    assert np.array_equal(ev1["pos_h"][:, 3], st1["pos_h"][:, 3])
+    st0b, _, _ = O.kdk_step(st0, ev, dt=dt)
+    assert np.min(np.abs(np.cbrt(268.0 / O.volumes(st0b["pos_h"])["N"]) - 1.0)) > 1e-2
+
+
 def test_h_iteration_converges_to_target_neighbour_count():
     st = inputs.uniform(16)
     pos = st["pos_h"].copy()

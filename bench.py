@@ -44,6 +44,7 @@ FLOPS_PER_UNIT = {"P1 volumes": 20, "P2 corrections": 88, "P3 grad v": 92, "P4 f
 # 39.1 M unordered pairs); a full 128^3 launch is too large to capture, so the
 # traffic is scaled by units.
 TRAFFIC_PER_UNIT = {"P4 forces": 47.4}
+BUILD_BYTES_PER_PARTICLE = 44 + 4 * 20 + 52 + 16
 PRECISION_NAMES = ["plain", "mixed", "mixed+compensated moments", "mixed+float-float moments"]
 
 
@@ -223,7 +224,7 @@ def sampled_errors(st, dev, tile_order, precisions, n_sample=16, seed=77):
         h = {k: t.detach().cpu().double().numpy() for k, t in
              (("V", V), ("A", A), ("B", B), ("gA", gA), ("gB", gB), ("gv", g_v), ("acc", acc), ("dudt", dudt))}
         c.close()
-        out[["plain", "mixed", "mixed+compensated moments"][prec]] = {
+        out[PRECISION_NAMES[prec]] = {
             "V": _rel_err(h["V"][s], p1["V"][s]), "A": _rel_err(h["A"][s], p2["A"][s]),
             "B": _rel_err(h["B"][s], p2["B"][s], p2["sB"][s]),
             "gradA": _rel_err(h["gA"][s], p2["gA"][s], p2["sgA"][s]),
@@ -365,6 +366,91 @@ def learned_h_report(dev, train_side=64, train_steps=200, every=10, eval_side=25
 
 
 # --------------------------------------------------------------------- batched boxes
+
+def ai_step_report(dev, st, tile_order, steps=5, warmup=3, tol=1e-4, train_side=64, train_steps=40, every=1):
+    """The composed step that the metric compares, on the bench workload: KDK
+    steps that solve eq:hi before every evaluation (crk_params.h_mode), as
+    - plain_fp32: precision 0, the fixed-point iteration from the state's h;
+    - ai_step: precision 1, the iteration from the learned proposal, the
+      network trained on the solves of steps of the same kind (zeldovich-%d^3
+      with h_mode 1: features at the drifted positions and the previous solved
+      h, target the step's solved h);
+    - reference_only: precision 1, the proposal of the all-zero network (the
+      constant-density estimate h (N_res/N)^(1/3) alone), which separates what
+      the network adds.
+    Each arm starts from the workload's k-NN h; its first `warmup` steps solve
+    from there and are not timed.  Returns the report and the final states
+    (for the oracle's check of eq:hi in the CPU-baseline leg)."""
+    import torch
+    from paper_2202_02840_gb300 import crk, inputs, learned_h
+
+    snaps, probe = learned_h.step_snapshots(inputs.zeldovich(train_side), steps=train_steps, every=every, tol=tol)
+    tctx = crk.crk_create()
+    feat, target, rows = learned_h.dataset(tctx, snaps)
+    n_rows = rows.shape[0]
+    losses = learned_h.train(tctx, feat, target, rows, steps=2000, batch=4096, lr=1e-3)
+    w = crk.crk_mlp_get_weights(tctx)
+    tctx.close()
+    probe.close()
+    del snaps, feat, target, rows
+    stream = torch.cuda.current_stream(dev)
+    mass = torch.from_numpy(st["mass"]).to(dev)
+    out, finals = {}, {}
+    arms = (("plain_fp32", 0, 1, None, "the state's h"), ("ai_step", 1, 2, w, "learned proposal"),
+            ("reference_only", 1, 2, torch.zeros_like(w), "constant-density proposal (zero network)"))
+    for name, prec, mode, weights, start in arms:
+        pos = torch.from_numpy(st["pos_h"]).to(dev)
+        vel = torch.from_numpy(st["vel_u"]).to(dev)
+        c = crk.crk_create(precision=prec, h_mode=mode, h_tol=tol, tile_order=tile_order)
+        if weights is not None:
+            crk.crk_mlp_set_weights(c, weights)
+        crk.crk_autotune(c, True)
+        warm_it = [crk.crk_step(c, pos, vel, mass, 0.0, diag=True)["h_iterations"] for _ in range(warmup)]
+        crk.crk_autotune(c, False)
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        diags = [crk.crk_step(c, pos, vel, mass, 0.0, diag=True) for _ in range(steps)]
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / steps
+        c.close()
+        pairs = sum(3 * d["pairs_gather"] + 3 * d["pairs_union"] for d in diags) / steps
+        out[name] = {"precision": PRECISION_NAMES[prec], "h_start": start, "ms_per_step": ms, "value": pairs / (ms * 1e-3), "unit": UNIT,
+                     "h_iterations_per_step": [d["h_iterations"] for d in diags],
+                     "h_unconverged": max(d["h_unconverged"] for d in diags),
+                     "warmup_h_iterations": warm_it}
+        finals[name] = pos.cpu().numpy()
+    faster = min(("plain_fp32", "ai_step"), key=lambda k: out[k]["ms_per_step"])
+    out["comparison"] = {
+        "faster": faster, "ai_over_plain_step_ms": out["ai_step"]["ms_per_step"] / out["plain_fp32"]["ms_per_step"],
+        "h_tol": tol, "timed_steps": steps,
+        "train": {"workload": "zeldovich-%d^3, the eq:hi solves of %d KDK steps with h_mode 1 (every %d)" % (
+            train_side, train_steps, every), "rows": int(n_rows), "adam_steps": 2000, "loss_first": losses[0],
+            "loss_last50": float(np.mean(losses[-50:]))},
+        "accuracy": "both arms solve eq:hi to h_tol (checked by the oracle in err.eq_hi); the evaluation error "
+                    "of each precision mode is err.by_precision",
+        "batched": "not run: a step that solves eq:hi reads its convergence on the host each pass, so it is "
+                   "not captured in CUDA graphs and batched steps keep the evolved h"}
+    return out, finals
+
+
+def eq_hi_check(finals, tol, n_sample=64, seed=5):
+    """The oracle's FP64 count of a seeded sample of each final state:
+    max |Delta_N - 1| over the sampled particles not held at an h bound."""
+    from oracle import crk as O
+    res = {}
+    for name, pos in finals.items():
+        s = np.sort(np.random.default_rng(seed).choice(pos.shape[0], n_sample, replace=False))
+        N = O.volumes(pos, targets=s)["N"][s]
+        h = pos[s, 3]
+        free = (h > np.float32(1e-6)) & (h < np.float32(0.3))
+        dN = np.abs(np.cbrt(268.0 / N) - 1.0)
+        res[name] = {"max_abs_Delta_N_minus_1": float(dN[free].max()) if free.any() else None,
+                     "sampled": int(n_sample), "at_bound": int((~free).sum()), "tol": tol}
+    return res
+
 
 def batched_report(dev, nbox=64, steps=10, warmup=2, seq_steps=2):
     """Many independent Sedov boxes of uneven size (sides 16..96) stepped
@@ -796,6 +882,18 @@ def run_gpu(args):
         pass_roofline["P5 compatible energy"] = {"bound": "hbm", "ms_per_step": t5, "achieved": a, "unit": "GB/s",
                                                  "frac": a / hbm, "peak": hbm,
                                                  "bytes": "16 B per ordered pair-set entry, read once for two kicks"}
+    # the cell build: keys (read pos_h 16 B; write fixed point 16, key 4, index 4,
+    # h 4), four stable radix passes (histogram reads the 4-B key; the scatter
+    # reads and writes key and index, 16 B), the gather into sorted order (read
+    # index, fixed point, h: 24 B; write q4 16, h 4, perm 4, key 4), tile boxes
+    # (read q4 16 B): 192 B per particle, against the measured HBM copy bandwidth
+    tb = prof_ms.get("cell build", 0.0) / args.steps
+    if tb > 0:
+        a = BUILD_BYTES_PER_PARTICLE * n / (tb / 1e3) / 1e9
+        pass_roofline["cell build"] = {"bound": "hbm", "ms_per_step": tb, "achieved": a, "unit": "GB/s",
+                                       "frac": a / hbm, "peak": hbm,
+                                       "bytes": "%d B per particle per rebuild (keys, 4 radix passes, gather, "
+                                                "tile boxes)" % BUILD_BYTES_PER_PARTICLE}
     roofline["passes"] = pass_roofline
 
     if rank == 0:
@@ -807,6 +905,10 @@ def run_gpu(args):
                            "l2": "step working set ~%.1f GB > L2 (129 MB): inputs larger than L2, no flush"
                                  % ((n * 460 + entries * 20) / 1e9),
                            "pairs_per_step": pairs / args.steps,
+                           "pair_count": "per step: P1, P2, P3 over the gather pairs and P4 plus the two "
+                                         "compatible-energy kicks over the ordered pair-set pairs (3 x gather + "
+                                         "3 x pair set); both kicks' sums are formed in one pass over the stored "
+                                         "pair forces",
                            "tiles": ntiles, "pair_candidate_tiles_per_tile": utp / max(1, ntiles),
                            "list_entries_per_particle": entries / n,
                            ("pinned_variants" if pins else "autotuned_variants"):
@@ -822,13 +924,16 @@ def run_gpu(args):
             plain["step_ms_ratio_to_this"] = plain["ms_per_step"] / (ms_max / args.steps)
             line["plain_fp32"] = plain
         if not args.no_learned_h and world == 1:
-            line["learned_h"] = learned_h_report(dev)
+            line["learned_h"] = learned_h_report(dev, eval_side=args.learned_h_eval_side)
         if not args.no_batched and world == 1:
             line["batched"] = batched_report(dev)
         if not args.no_time_bins and world == 1:
             line["time_bins"] = time_bins_report(dev)
         if not args.no_sod and world == 1:
             line["sod"] = sod_report(dev)
+        finals = None
+        if not args.no_ai_step and world == 1:
+            line["ai_step"], finals = ai_step_report(dev, st, tile_order)
         if not args.no_cpu_baseline and world == 1:
             from oracle import crk as O
             p, dt, ns = calibrated_oracle(st, args.cpu_seconds, seed=2)
@@ -838,6 +943,8 @@ def run_gpu(args):
             # the stated error of this mode and of the plain FP32 path
             try:
                 line["err"] = sampled_errors(st, dev, tile_order, sorted({0, args.precision}))
+                if finals is not None:
+                    line["err"]["eq_hi"] = eq_hi_check(finals, line["ai_step"]["comparison"]["h_tol"])
             except Exception as e:   # the measurement line is printed regardless
                 line["err"] = {"unavailable": "%s: %s" % (type(e).__name__, e)}
         print(json.dumps(line))
@@ -873,6 +980,10 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-boxes measurement")
     ap.add_argument("--no-time-bins", action="store_true", help="skip the hierarchical time-bin measurement")
     ap.add_argument("--no-sod", action="store_true", help="skip the Sod shock-tube measurement")
+    ap.add_argument("--learned-h-eval-side", type=int, default=256,
+                    help="side of the Sedov state the learned-h report evaluates at (256: config 4)")
+    ap.add_argument("--no-ai-step", action="store_true",
+                    help="skip the steps that solve eq:hi (plain FP32 from h vs learned proposal)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the built-in pass variants")
     ap.add_argument("--variants", default="",
                     help="pin list-pass variants instead of tuning them (numbering of crk_tuning), "

@@ -404,6 +404,34 @@ static int ensure_htb(crk_ctx *ctx) {
     return CRK_OK;
 }
 
+// tile t holds a particle whose eq:hi solve is not yet done (flags[s] == 0)
+__global__ void k_unconv_flags(int ntiles, int n, const int32_t *__restrict__ flags, uint32_t *__restrict__ tflag) {
+    const int T = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (T >= ntiles) return;
+    const int s = T * TILE + (int)(threadIdx.x & 31);
+    const bool open = s < n && flags[s] == 0;
+    const unsigned m = __ballot_sync(FULLM, open);
+    if ((threadIdx.x & 31) == 0) tflag[T] = m != 0u;
+}
+
+// The tiles that hold a particle not yet converged (ctx->flags == 0), in tile
+// order, into ctx->tact; their count lands in ctx->counters[CNT_NACT] (read
+// after the caller's next sync).  The h solves walk only these tiles.
+int unconverged_tiles(crk_ctx *ctx, cudaStream_t s) {
+    int rc = ensure_htb(ctx);
+    if (rc) return rc;
+    const int nt = ctx->ntiles;
+    CRK_CUDA(ctx, cudaMemsetAsync(ctx->counters + CNT_NACT, 0, 2 * sizeof(unsigned long long), s));
+    k_unconv_flags<<<grid_for((long long)nt * 32, 256), 256, 0, s>>>(nt, ctx->n, ctx->flags, ctx->tflag);
+    ++ctx->launches;
+    rc = scan_u32(ctx, ctx->tflag, ctx->tscan, nt, s);
+    if (rc) return rc;
+    k_htb_compact<<<grid_for(nt, 256), 256, 0, s>>>(nt, ctx->n, ctx->tflag, ctx->tscan, ctx->tact, ctx->counters);
+    ++ctx->launches;
+    CRK_LAUNCH_CHECK(ctx, "unconverged tiles");
+    return CRK_OK;
+}
+
 void htb_free(crk_ctx *ctx) {
     int32_t **ti[] = {&ctx->tlev, &ctx->tt0, &ctx->tlen, &ctx->twake, &ctx->tact};
     for (auto p : ti)

@@ -266,6 +266,7 @@ constexpr int TUNE_P5_DUAL = 15;   // the autotuner's record of the two-kick P5 
 constexpr int NVAR = CRK_TUNE_NVARIANT;   // list-pass variants (lvariant)
 void mlp_free(crk_ctx *ctx);
 void htb_free(crk_ctx *ctx);
+int unconverged_tiles(crk_ctx *ctx, cudaStream_t s);   // tiles with flags == 0 -> ctx->tact (crk_htb.cu)
 void rcb_free(crk_ctx *ctx);
 void graph_free(crk_ctx *ctx);
 void prof_begin(crk_ctx *ctx, int id, cudaStream_t s);

@@ -395,6 +395,27 @@ extern "C" int crk_reset_rates(crk_ctx *ctx) {
 // update by the learned proposal (judged: particles already converged keep
 // their h); its features take the grad v of the last evaluation, gv_old in the
 // previous sorted order (idx: new slot -> old slot), and the step's dt.
+// One eq:thacker update of every particle not yet converged (k_h_iter), then
+// the tiles that still hold such a particle become ctx->act, so that the next
+// P1 walks (and the next list rebuild covers) only those: a particle's count
+// depends on its own h alone, so the others' counts stand.  Synchronises once;
+// *nd = particles updated (0: all converged).
+static int h_update(crk_ctx *ctx, const StepConsts &c, float tol, cudaStream_t s, unsigned long long *nd) {
+    const int n = ctx->n;
+    CRK_CUDA(ctx, cudaMemsetAsync(ctx->counters + CNT_NOTDONE, 0, sizeof(unsigned long long), s));
+    k_h_iter<<<grid_for(n, 256), 256, 0, s>>>(n, c, tol, ctx->Nn, ctx->hs, ctx->q4, ctx->flags,
+                                              ctx->counters + CNT_NOTDONE);
+    ++ctx->launches;
+    CRK_LAUNCH_CHECK(ctx, "h iteration");
+    int rc = unconverged_tiles(ctx, s);
+    if (!rc) rc = crk_sync_counters(ctx, s);
+    if (rc) return rc;
+    *nd = ctx->h_counters[CNT_NOTDONE];
+    ctx->nact = (int)ctx->h_counters[CNT_NACT];
+    ctx->act = ctx->tact;
+    return CRK_OK;
+}
+
 static int solve_h(crk_ctx *ctx, int n, const int32_t *idx, cudaStream_t s, int *iters, long long *unconv) {
     StepConsts c = step_consts(ctx->p);
     const float tol = ctx->p.h_tol;
@@ -424,23 +445,25 @@ static int solve_h(crk_ctx *ctx, int n, const int32_t *idx, cudaStream_t s, int 
             k_take_h<<<g, b, 0, s>>>(n, ctx->st_pos, ctx->hs, ctx->q4);
             ++ctx->launches;
             CRK_LAUNCH_CHECK(ctx, "proposed h");
+            ctx->act = nullptr;   // every particle may have moved: the next pass walks all tiles
         } else {
-            CRK_CUDA(ctx, cudaMemsetAsync(ctx->counters + CNT_NOTDONE, 0, sizeof(unsigned long long), s));
-            k_h_iter<<<g, b, 0, s>>>(n, c, tol, ctx->Nn, ctx->hs, ctx->q4, ctx->flags, ctx->counters + CNT_NOTDONE);
-            ++ctx->launches;
-            CRK_LAUNCH_CHECK(ctx, "h iteration");
-            rc = crk_sync_counters(ctx, s);
-            if (rc) break;
-            nd = ctx->h_counters[CNT_NOTDONE];
-            if (nd == 0) break;
+            rc = h_update(ctx, c, tol, s, &nd);
+            if (rc || nd == 0) break;
         }
         rc = build_tree(ctx, s);
         if (!rc) rc = rebuild_lists(ctx, s);
         if (!rc) rc = finish_build(ctx, s);
         if (rc) break;
     }
+    const bool partial = ctx->act != nullptr;
+    ctx->act = nullptr;
+    ctx->nact = 0;
     ctx->volumes_only = vo;
     ctx->lists_valid = 0;
+    if (!rc && partial) {   // the evaluation needs every tile's interaction list
+        rc = rebuild_lists(ctx, s);
+        if (!rc) rc = finish_build(ctx, s);
+    }
     if (rc) return rc;
     *iters = it > max_it ? max_it : it;
     *unconv = (long long)nd;
@@ -954,21 +977,16 @@ static int h_iterate(crk_ctx *ctx, int n, float *pos_h, float tol, int max_it, i
     unsigned long long nd = 1;
     for (it = 1; it <= max_it; it++) {
         rc = run_volumes(ctx, s);
-        if (rc) return rc;
-        CRK_CUDA(ctx, cudaMemsetAsync(ctx->counters + CNT_NOTDONE, 0, sizeof(unsigned long long), s));
-        k_h_iter<<<grid_for(n, 256), 256, 0, s>>>(n, c, tol, ctx->Nn, ctx->hs, ctx->q4, ctx->flags,
-                                                  ctx->counters + CNT_NOTDONE);
-        ++ctx->launches;
-        CRK_LAUNCH_CHECK(ctx, "h iteration");
-        rc = crk_sync_counters(ctx, s);
-        if (rc) return rc;
-        nd = ctx->h_counters[CNT_NOTDONE];
-        if (nd == 0) break;
+        if (!rc) rc = h_update(ctx, c, tol, s, &nd);
+        if (rc || nd == 0) break;
         rc = build_tree(ctx, s);
         if (!rc) rc = rebuild_lists(ctx, s);
         if (!rc) rc = finish_build(ctx, s);
-        if (rc) return rc;
+        if (rc) break;
     }
+    ctx->act = nullptr;
+    ctx->nact = 0;
+    if (rc) return rc;
     if (iterations) *iterations = it > max_it ? max_it : it;
     k_write_h<<<grid_for(n, 256), 256, 0, s>>>(n, ctx->perm, ctx->hs, (float4 *)pos_h);
     ++ctx->launches;

@@ -4,7 +4,10 @@ Orchestration only: every number is computed by libcrk.so kernels through the
 binding (crk.py); this module decides which calls to make, keeps the tensors
 and concatenates data sets (device memory plumbing).
 
-Data protocol (the method generates its own training data):
+Data protocols (the method generates its own training data); step_snapshots
+takes the rows from steps that solve eq:hi (h_mode 1), matching what the
+proposal sees inside such a step; the snapshots below take them from a run
+with the evolved h:
   * a Sedov blast (the Sedov-Taylor test of Sec. 4) is advanced with crk_step,
     whose h evolves by one Thacker update per step (Sec. 2.6, eq:thacker);
   * at every `every`-th step the state is a snapshot: P1 gives N_i at the
@@ -71,6 +74,45 @@ def run_snapshots(st, steps=100, every=10, tol=1e-4, max_it=60, params=None):
         dt = crk.crk_step(stepper, pos, vel, mass, 0.0, diag=(k % every == 0))
         if k % every == 0:
             snaps.append(Snapshot(probe, pos, vel, dt["dt"], tol=tol, max_it=max_it))
+    stepper.close()
+    return snaps, probe
+
+
+class StepSnapshot:
+    """The solve of eq:hi that one step with h_mode 1 performs, as training
+    rows: the features of the drifted positions with the previous step's
+    solved h (where that solve starts), the target from the h it converged to."""
+
+    def __init__(self, ctx, start, conv, vel_u, dt, tol=1e-4):
+        crk.crk_build_cells(ctx, start)
+        V, N = crk.crk_volumes(ctx)
+        gradv = crk.crk_corrections(ctx, V, vel_u)[4]
+        self.feat, self.target = crk.crk_h_features(ctx, start, gradv, N, conv, dt=dt)
+        self.N, self.tol, self.dt = N, tol, dt
+
+    def rows(self, ctx, base=0):
+        return crk.crk_h_select(ctx, self.N, tol=self.tol, base=base)
+
+
+def step_snapshots(st, steps=40, every=1, tol=1e-4, warm=3, params=None):
+    """Advance the state st with KDK steps that solve eq:hi (h_mode 1) and take
+    a StepSnapshot of every `every`-th step's solve (after `warm` steps, the
+    first of which solves from the initial h)."""
+    pos, vel, mass = dev(st["pos_h"]), dev(st["vel_u"]), dev(st["mass"])
+    p = dict(params or {})
+    p.update(h_mode=1, h_tol=tol)
+    stepper = crk.crk_create(**p)
+    probe = crk.crk_create()
+    for _ in range(warm):
+        crk.crk_step(stepper, pos, vel, mass, 0.0)
+    snaps = []
+    for k in range(steps):
+        h_prev = pos[:, 3].clone()
+        d = crk.crk_step(stepper, pos, vel, mass, 0.0, diag=True)
+        if k % every == 0:
+            start = pos.clone()
+            start[:, 3] = h_prev
+            snaps.append(StepSnapshot(probe, start, pos.clone(), vel, d["dt"], tol))
     stepper.close()
     return snaps, probe
 

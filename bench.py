@@ -202,7 +202,7 @@ def oracle_cone(st, sample):
     return p1, p2, gv, p4, G2.size
 
 
-def sampled_errors(st, dev, tile_order, precisions, n_sample=16, seed=77):
+def sampled_errors(st, dev, order, precisions, n_sample=16, seed=77):
     """Error of one GPU evaluation (P1-P4 at the initial state) in each
     precision mode against the FP64 oracle, on a seeded sample of particles
     whose exact FP64 values the oracle computes over their dependency cone."""
@@ -214,7 +214,7 @@ def sampled_errors(st, dev, tile_order, precisions, n_sample=16, seed=77):
     s = sample
     out = {}
     for prec in precisions:
-        c = crk.crk_create(precision=prec, tile_order=tile_order)
+        c = crk.crk_create(precision=prec, **order)
         dpos = torch.from_numpy(pos).to(dev)
         dvel = torch.from_numpy(st["vel_u"]).to(dev)
         crk.crk_build_cells(c, dpos)
@@ -229,13 +229,15 @@ def sampled_errors(st, dev, tile_order, precisions, n_sample=16, seed=77):
             "B": _rel_err(h["B"][s], p2["B"][s], p2["sB"][s]),
             "gradA": _rel_err(h["gA"][s], p2["gA"][s], p2["sgA"][s]),
             "gradB": _rel_err(h["gB"][s], p2["gB"][s], p2["sgB"][s]),
+            "B_rms": _rel_err(h["B"][s], p2["B"][s]), "gradA_rms": _rel_err(h["gA"][s], p2["gA"][s]),
+            "gradB_rms": _rel_err(h["gB"][s], p2["gB"][s]),
             "gradv": _rel_err(h["gv"][s], gv[s]),
             "accel": _rel_err(h["acc"][s], p4["acc"][s], p4["fscale"][s]),
             "dudt": _rel_err(h["dudt"][s], p4["dudt"][s])}
     return {"sample": "%d seeded particles of the workload, FP64 oracle over their dependency cone "
                       "(%d particles)" % (n_sample, ncone),
             "norm": "max |gpu - oracle| / max(|oracle|, floor); floor = field RMS over the sample, or the "
-                    "no-cancellation scale for B, grad A, grad B and the acceleration",
+                    "no-cancellation scale for B, grad A, grad B and the acceleration (*_rms: the RMS floor)",
             "by_precision": out}
 
 
@@ -367,7 +369,7 @@ def learned_h_report(dev, train_side=64, train_steps=200, every=10, eval_side=25
 
 # --------------------------------------------------------------------- batched boxes
 
-def ai_step_report(dev, st, tile_order, steps=5, warmup=3, tol=1e-4, train_side=64, train_steps=40, every=1):
+def ai_step_report(dev, st, order, steps=5, warmup=3, tol=1e-4, train_side=64, train_steps=40, every=1):
     """The composed step that the metric compares, on the bench workload: KDK
     steps that solve eq:hi before every evaluation (crk_params.h_mode), as
     - plain_fp32: precision 0, the fixed-point iteration from the state's h;
@@ -401,7 +403,7 @@ def ai_step_report(dev, st, tile_order, steps=5, warmup=3, tol=1e-4, train_side=
     for name, prec, mode, weights, start in arms:
         pos = torch.from_numpy(st["pos_h"]).to(dev)
         vel = torch.from_numpy(st["vel_u"]).to(dev)
-        c = crk.crk_create(precision=prec, h_mode=mode, h_tol=tol, tile_order=tile_order)
+        c = crk.crk_create(precision=prec, h_mode=mode, h_tol=tol, **order)
         if weights is not None:
             crk.crk_mlp_set_weights(c, weights)
         crk.crk_autotune(c, True)
@@ -672,7 +674,11 @@ def aggregate(times_ms, work, dist=None, device="cpu"):
     return [float(x) for x in t.cpu()], [float(x) for x in w.cpu()]
 
 
-ORDER_NAMES = {0: "morton", 1: "hilbert", 2: "bisection"}
+# particle orders that cut the tiles: (tile_order, rcb_leaf); the bisection to
+# one-tile leaves, and to the paper's leaf sizes N_ppl = 128, 256 (Sec. 2.3)
+ORDERS = {"morton": (0, 32), "hilbert": (1, 32), "bisection": (2, 32), "bisection-128": (2, 128),
+          "bisection-256": (2, 256)}
+ORDER_ARGS = {"0": "morton", "1": "hilbert", "2": "bisection", "2-128": "bisection-128", "2-256": "bisection-256"}
 
 
 def run_gpu(args):
@@ -716,9 +722,9 @@ def run_gpu(args):
     # timed steps each on a copy of the state (part of the warm-up)
     order_ms = {}
     if args.tile_order == "auto":
-        for o in (0, 1, 2):
+        for name, (t, leaf) in ORDERS.items():
             p, v = pos0.clone(), vel0.clone()
-            c = crk.crk_create(precision=args.precision, tile_order=o)
+            c = crk.crk_create(precision=args.precision, tile_order=t, rcb_leaf=leaf)
             crk.crk_step(c, p, v, mass, 0.0)
             torch.cuda.synchronize(dev)
             t0 = torch.cuda.Event(enable_timing=True)
@@ -728,12 +734,13 @@ def run_gpu(args):
                 crk.crk_step(c, p, v, mass, 0.0)
             t1.record(stream)
             torch.cuda.synchronize(dev)
-            order_ms[ORDER_NAMES[o]] = t0.elapsed_time(t1) / 2
+            order_ms[name] = t0.elapsed_time(t1) / 2
             c.close()
-        tile_order = min((0, 1, 2), key=lambda o: order_ms[ORDER_NAMES[o]])
+        order_name = min(ORDERS, key=lambda k: order_ms[k])
     else:
-        tile_order = int(args.tile_order)
-    ctx = crk.crk_create(precision=args.precision, tile_order=tile_order)
+        order_name = ORDER_ARGS[args.tile_order]
+    order = {"tile_order": ORDERS[order_name][0], "rcb_leaf": ORDERS[order_name][1]}
+    ctx = crk.crk_create(precision=args.precision, **order)
 
     def barrier():
         if dist is not None:
@@ -785,7 +792,7 @@ def run_gpu(args):
     d_pos = torch.empty_like(pos0)
     d_vel = torch.empty_like(vel0)
     d_mass = torch.empty_like(mass)
-    e2e_ctx = crk.crk_create(precision=args.precision, tile_order=tile_order)
+    e2e_ctx = crk.crk_create(precision=args.precision, **order)
     prepare(e2e_ctx)   # tuned during its own warm-up, or pinned as ctx
     for _ in range(max(1, args.warmup)):
         d_pos.copy_(h_pos, non_blocking=True)
@@ -816,7 +823,7 @@ def run_gpu(args):
     # FP32 moment formation) over the same warm-up and steps, for comparison
     plain = None
     if args.precision != 0 and world == 1:
-        c0 = crk.crk_create(precision=0, tile_order=tile_order)
+        c0 = crk.crk_create(precision=0, **order)
         prepare(c0)
         p0, v0 = pos0.clone(), vel0.clone()
         for _ in range(args.warmup):
@@ -836,6 +843,29 @@ def run_gpu(args):
         c0.close()
         plain = {"precision": "plain", "ms_per_step": plain_ms / args.steps,
                  "value": plain_pairs / (plain_ms * 1e-3), "unit": UNIT}
+    # the accuracy mode (precision 3: float-float moments) over the same warm-up
+    # and steps, with its P2 time
+    accurate = None
+    if args.precision != 3 and world == 1 and not args.no_accuracy_mode:
+        c3 = crk.crk_create(precision=3, **order)
+        prepare(c3)
+        p3, v3 = pos0.clone(), vel0.clone()
+        for _ in range(args.warmup):
+            crk.crk_step(c3, p3, v3, mass, 0.0)
+        crk.crk_autotune(c3, False)
+        crk.crk_profile(c3, True)
+        barrier()
+        q0 = torch.cuda.Event(enable_timing=True)
+        q1 = torch.cuda.Event(enable_timing=True)
+        q0.record(stream)
+        for _ in range(args.steps):
+            crk.crk_step(c3, p3, v3, mass, 0.0)
+        q1.record(stream)
+        barrier()
+        pm3, _, _ = crk.crk_profile_read(c3)
+        c3.close()
+        accurate = {"precision": PRECISION_NAMES[3], "ms_per_step": q0.elapsed_time(q1) / args.steps,
+                    "P2_ms_per_step": pm3["P2 corrections"] / args.steps}
     e2e_ctx.close()
 
     # ---------------- aggregate over ranks (max time, summed work)
@@ -913,7 +943,7 @@ def run_gpu(args):
                            "list_entries_per_particle": entries / n,
                            ("pinned_variants" if pins else "autotuned_variants"):
                                {k: v for k, (v, _) in tuning.items()} if not pins else pins,
-                           "tile_order": ORDER_NAMES[tile_order], "tile_order_step_ms": order_ms or None,
+                           "tile_order": order_name, "tile_order_step_ms": order_ms or None,
                            "gather_pairs_per_particle": diags[-1]["pairs_gather"] / n,
                            "union_pairs_per_particle": diags[-1]["pairs_union"] / n},
                 "roofline": roofline,
@@ -923,6 +953,9 @@ def run_gpu(args):
         if plain is not None:
             plain["step_ms_ratio_to_this"] = plain["ms_per_step"] / (ms_max / args.steps)
             line["plain_fp32"] = plain
+        if accurate is not None:
+            accurate["step_ms_ratio_to_this"] = accurate["ms_per_step"] / (ms_max / args.steps)
+            line["accuracy_mode"] = accurate
         if not args.no_learned_h and world == 1:
             line["learned_h"] = learned_h_report(dev, eval_side=args.learned_h_eval_side)
         if not args.no_batched and world == 1:
@@ -933,7 +966,7 @@ def run_gpu(args):
             line["sod"] = sod_report(dev)
         finals = None
         if not args.no_ai_step and world == 1:
-            line["ai_step"], finals = ai_step_report(dev, st, tile_order)
+            line["ai_step"], finals = ai_step_report(dev, st, order)
         if not args.no_cpu_baseline and world == 1:
             from oracle import crk as O
             p, dt, ns = calibrated_oracle(st, args.cpu_seconds, seed=2)
@@ -942,7 +975,7 @@ def run_gpu(args):
                                               "particles of the workload (%.1f s)" % (ns, dt)}
             # the stated error of this mode and of the plain FP32 path
             try:
-                line["err"] = sampled_errors(st, dev, tile_order, sorted({0, args.precision}))
+                line["err"] = sampled_errors(st, dev, order, sorted({0, args.precision, 3}))
                 if finals is not None:
                     line["err"]["eq_hi"] = eq_hi_check(finals, line["ai_step"]["comparison"]["h_tol"])
             except Exception as e:   # the measurement line is printed regardless
@@ -980,6 +1013,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-boxes measurement")
     ap.add_argument("--no-time-bins", action="store_true", help="skip the hierarchical time-bin measurement")
     ap.add_argument("--no-sod", action="store_true", help="skip the Sod shock-tube measurement")
+    ap.add_argument("--no-accuracy-mode", action="store_true", help="skip timing precision 3")
     ap.add_argument("--learned-h-eval-side", type=int, default=256,
                     help="side of the Sedov state the learned-h report evaluates at (256: config 4)")
     ap.add_argument("--no-ai-step", action="store_true",
@@ -988,8 +1022,9 @@ def main():
     ap.add_argument("--variants", default="",
                     help="pin list-pass variants instead of tuning them (numbering of crk_tuning), "
                          "e.g. P1=20,P2=16,P3=9,P4=8,P5=9")
-    ap.add_argument("--tile-order", default="auto", choices=["auto", "0", "1", "2"],
-                    help="particle order of the tiles: 0 Morton, 1 Hilbert, 2 bisection, auto = fastest")
+    ap.add_argument("--tile-order", default="auto", choices=["auto"] + list(ORDER_ARGS),
+                    help="particle order of the tiles: 0 Morton, 1 Hilbert, 2 bisection to one-tile leaves, "
+                         "2-128 / 2-256 bisection to leaves of 128 / 256 particles, auto = fastest")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

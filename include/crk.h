@@ -117,7 +117,9 @@ typedef struct {
                          crk_step_batched returns CRK_ESTATE. */
     int h_max_it;     /* iteration cap of h_mode 1 and 2 (default 50) */
     float h_tol;      /* |Delta_N - 1| tolerance of h_mode 1 and 2 (default 1e-4) */
-    int reserved;
+    int rcb_leaf;     /* tile_order 2: particles per bisection leaf, 32 (default: one
+                         tile), 128 or 256 (the paper's N_ppl range, Sec. 2.3: a leaf's tiles are
+                         cut from the order the splits leave inside it) */
 } crk_params;
 
 /* Per-step diagnostics (host memory), all reductions in FP64. */

@@ -66,8 +66,11 @@ def split_left(size):
     return ((size + 1) // 2 + TILE - 1) // TILE * TILE
 
 
-def bisection_order(pos_h):
-    """Sorted slot -> particle of the bisection order (leaves of one tile)."""
+def bisection_order(pos_h, leaf=TILE):
+    """Sorted slot -> particle of the bisection order: segments of more than
+    `leaf` particles split (leaves of one tile by default; 128 or 256, the
+    paper's N_ppl range of Sec. 2.3, whose tiles are cut from the order the
+    splits leave inside each leaf)."""
     _, perm, _, _ = O.cells(pos_h)
     perm = perm.astype(np.int64)
     q, _ = O.fixed_point(pos_h)
@@ -77,7 +80,7 @@ def bisection_order(pos_h):
         nxt, split = [], False
         for a, b in segs:
             size = b - a
-            if size <= TILE:
+            if size <= leaf:
                 nxt.append((a, b))
                 continue
             split = True

@@ -209,7 +209,9 @@ static int radix_sort(crk_ctx *ctx, int n, int bits, cudaStream_t s) {
 // ------------------------------------------------------------------ recursive coordinate bisection
 //
 // tile_order 2: the Morton order is refined by recursive coordinate bisection
-// into leaves of one tile.  A segment [a, b) of more than 32 particles splits
+// into leaves of at most `leaf` particles (crk_params.rcb_leaf: 32 = one tile,
+// or the paper's 128 / 256, whose tiles are then cut from the order the
+// splits leave inside each leaf).  A segment [a, b) of more than `leaf` particles splits
 // at nl = 32 ceil(ceil((b - a)/2) / 32) (every left part a whole number of
 // tiles) along the longest axis of its fixed-point box: its particles are
 // binned into 256 equal slices of that box, the slice holding the nl-th
@@ -223,12 +225,12 @@ constexpr int RCB_BINS = 256;
 __host__ __device__ __forceinline__ int rcb_left(int size) { return ((size + 1) / 2 + 31) / 32 * 32; }
 
 // the segment of slot s after `level` splits: start a, size, index (path bits)
-__device__ __forceinline__ bool rcb_segment(int n, int level, int s, int &a, int &size, int &path) {
+__device__ __forceinline__ bool rcb_segment(int n, int level, int leaf, int s, int &a, int &size, int &path) {
     a = 0;
     size = n;
     path = 0;
     for (int l = 0; l < level; l++) {
-        if (size <= TILE) return false;
+        if (size <= leaf) return false;
         const int nl = rcb_left(size);
         if (s < a + nl) {
             size = nl;
@@ -239,12 +241,12 @@ __device__ __forceinline__ bool rcb_segment(int n, int level, int s, int &a, int
             path = 2 * path + 1;
         }
     }
-    return size > TILE;
+    return size > leaf;
 }
 
 // per slot: its segment (start, index; -1 when the segment does not split)
 // and the segment's box (one atomic per segment a warp touches)
-__global__ void k_rcb_box(int n, int level, const int32_t *__restrict__ perm, const uint4 *__restrict__ q,
+__global__ void k_rcb_box(int n, int level, int leaf, const int32_t *__restrict__ perm, const uint4 *__restrict__ q,
                           int32_t *__restrict__ seg_a, int32_t *__restrict__ seg_id, uint32_t *__restrict__ blo,
                           uint32_t *__restrict__ bhi, int32_t *__restrict__ bsize) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -252,7 +254,7 @@ __global__ void k_rcb_box(int n, int level, const int32_t *__restrict__ perm, co
     bool act = false;
     uint4 p = make_uint4(0, 0, 0, 0);
     if (s < n) {
-        act = rcb_segment(n, level, s, a, size, path);
+        act = rcb_segment(n, level, leaf, s, a, size, path);
         if (!act) path = -1;
         seg_a[s] = a;
         seg_id[s] = path;
@@ -428,8 +430,9 @@ __global__ void k_fill_u32(long long count, uint32_t v, uint32_t *out) {
 // Refine the sorted order idx_a (input indices) by recursive coordinate
 // bisection of the fixed-point records q_tmp (input order).
 static int rcb_refine(crk_ctx *ctx, int n, cudaStream_t s) {
+    const int leaf = ctx->p.rcb_leaf;
     int levels = 0;
-    for (int size = n; size > TILE; size = rcb_left(size)) levels++;   // the largest segment goes left
+    for (int size = n; size > leaf; size = rcb_left(size)) levels++;   // the largest segment goes left
     int rc = ensure_rcb(ctx, n, 1 << (levels > 0 ? levels - 1 : 0));
     if (rc) return rc;
     int32_t *cur = ctx->idx_a, *nxt = ctx->idx_b;
@@ -441,7 +444,7 @@ static int rcb_refine(crk_ctx *ctx, int n, cudaStream_t s) {
         CRK_CUDA(ctx, cudaMemsetAsync(ctx->rcb_hi, 0, sizeof(uint32_t) * 3 * (size_t)nseg, s));
         CRK_CUDA(ctx, cudaMemsetAsync(ctx->rcb_size, 0, sizeof(int32_t) * (size_t)nseg, s));
         CRK_CUDA(ctx, cudaMemsetAsync(ctx->rcb_hist, 0, sizeof(uint32_t) * RCB_BINS * (size_t)nseg, s));
-        k_rcb_box<<<g, 256, 0, s>>>(n, L, cur, ctx->q_tmp, ctx->rcb_a, ctx->rcb_id, ctx->rcb_lo, ctx->rcb_hi,
+        k_rcb_box<<<g, 256, 0, s>>>(n, L, leaf, cur, ctx->q_tmp, ctx->rcb_a, ctx->rcb_id, ctx->rcb_lo, ctx->rcb_hi,
                                     ctx->rcb_size);
         k_rcb_hist<<<g, 256, 0, s>>>(n, cur, ctx->q_tmp, ctx->rcb_id, ctx->rcb_lo, ctx->rcb_hi, ctx->rcb_bin,
                                      ctx->rcb_hist);

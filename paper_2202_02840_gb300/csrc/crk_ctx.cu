@@ -436,6 +436,7 @@ extern "C" int crk_default_params(crk_params *p) {
     p->h_mode = 0;
     p->h_max_it = 50;
     p->h_tol = 1e-4f;
+    p->rcb_leaf = 32;
     return CRK_OK;
 }
 
@@ -449,7 +450,7 @@ extern "C" int crk_create(const crk_params *p, crk_ctx **out) {
         prm.kmax < 1 || prm.kmax > 7 || prm.precision < 0 || prm.precision > 3 || !(prm.dt_max > 0) ||
         prm.tile_order < 0 || prm.tile_order > 2 || prm.density < 0 || prm.density > 1 || !(prm.a > 0.0) || !(prm.a < 1e30) ||
         !(prm.adot > -1e30 && prm.adot < 1e30) || prm.h_mode < 0 || prm.h_mode > 2 || prm.h_max_it < 1 ||
-        !(prm.h_tol > 0.f))
+        !(prm.h_tol > 0.f) || (prm.rcb_leaf != 32 && prm.rcb_leaf != 128 && prm.rcb_leaf != 256))
         return CRK_EINVAL;
     crk_ctx *ctx = new (std::nothrow) crk_ctx();
     if (!ctx) return CRK_ENOMEM;

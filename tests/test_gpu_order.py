@@ -44,14 +44,17 @@ CASES = {
     "zeldovich32": lambda: inputs.zeldovich(32)["pos_h"],
     "sedov16": lambda: inputs.sedov(16)["pos_h"],
 }
-ORACLE = {0: lambda p: O.cells(p)[1], 1: R.hilbert_order, 2: R.bisection_order}
+ORACLE = {0: lambda p: O.cells(p)[1], 1: R.hilbert_order, 2: R.bisection_order,
+          "2-128": lambda p: R.bisection_order(p, leaf=128), "2-256": lambda p: R.bisection_order(p, leaf=256)}
+ORDER_PARAMS = {0: dict(tile_order=0), 1: dict(tile_order=1), 2: dict(tile_order=2),
+                "2-128": dict(tile_order=2, rcb_leaf=128), "2-256": dict(tile_order=2, rcb_leaf=256)}
 
 
-@pytest.mark.parametrize("order", [0, 1, 2])
+@pytest.mark.parametrize("order", [0, 1, 2, "2-128", "2-256"])
 @pytest.mark.parametrize("case", list(CASES))
 def test_order_bit_exact(case, order):
     pos = CASES[case]()
-    ctx = crk.crk_create(tile_order=order)
+    ctx = crk.crk_create(**ORDER_PARAMS[order])
     crk.crk_build_cells(ctx, dev(pos))
     got = crk.crk_order(ctx).cpu().numpy()
     want = ORACLE[order](pos)
@@ -75,7 +78,7 @@ def test_forces_in_every_order(order):
     assert max(e.values()) < TOL, e
 
 
-@pytest.mark.parametrize("order", [1, 2])
+@pytest.mark.parametrize("order", [1, 2, "2-128"])
 @pytest.mark.parametrize("case", ["uniform16", "zeldovich16"])
 def test_one_step_in_every_order(case, order):
     st = inputs.uniform(16) if case == "uniform16" else inputs.zeldovich(16)
@@ -83,7 +86,7 @@ def test_one_step_in_every_order(case, order):
     dt = 0.5 * float(np.min(O.cfl_dt(ev)))
     ost, _, _ = O.kdk_step(st, ev=ev, dt=dt)
     pos, vel, mass = dev(st["pos_h"]), dev(st["vel_u"]), dev(st["mass"])
-    ctx = crk.crk_create(tile_order=order)
+    ctx = crk.crk_create(**ORDER_PARAMS[order])
     crk.crk_step(ctx, pos, vel, mass, dt)
     gp, gv = as_np(pos), as_np(vel)
     dx = gp[:, :3] - ost["pos_h"][:, :3]

@@ -221,7 +221,7 @@ def gpu_chain(st, precision=1):
 @pytest.mark.parametrize("case", ["uniform16", "clustered3000"])
 def test_chained_evaluation(case):
     """GPU-only chain P1 -> P4 against the FP64 oracle chain: every FP32 error
-    of an earlier pass is propagated, so the bar is 10x the per-pass one."""
+    of an earlier pass is propagated, still within TOL (measured <= 7.4e-6)."""
     st = CASES[case]()
     g = gpu_chain(st)
     ev = O.evaluate(st)
@@ -229,7 +229,7 @@ def test_chained_evaluation(case):
     e.update({k: rel_err(g[k], ev[k], floor=ev["s" + k]) for k in ("B", "gA", "gB")})
     e["acc"] = rel_err(g["acc"], ev["acc"], floor=ev["fscale"])
     print(case, e)
-    assert max(e.values()) < 10 * TOL, e
+    assert max(e.values()) < TOL, e
 
 
 # ---------------------------------------------------------------- edge cases
@@ -338,18 +338,19 @@ def test_full_size_clustered_sampled(zel128):
          "acc": rel_err(as_np(g["acc"])[s], p4["acc"][s], floor=p4["fscale"][s]),
          "dudt": rel_err(as_np(g["dudt"])[s], p4["dudt"][s])}
     print("128^3 sample", e)
-    assert max(e.values()) < 10 * TOL, e
+    assert max(e.values()) < TOL, e
 
 
 # ---------------------------------------------------------------- KDK step
 
-def test_one_step_matches_oracle():
+@pytest.mark.parametrize("precision", [1, 3])
+def test_one_step_matches_oracle(precision):
     st = workload("uniform", 16)
     ev = O.evaluate(st)
     dt = 0.5 * float(np.min(O.cfl_dt(ev)))
     ost, oev, _ = O.kdk_step(st, ev=ev, dt=dt)
     pos, vel, mass = dev(st["pos_h"]), dev(st["vel_u"]), dev(st["mass"])
-    ctx = crk.crk_create()
+    ctx = crk.crk_create(precision=precision)
     d = crk.crk_step(ctx, pos, vel, mass, dt, diag=True)
     assert abs(d["dt"] - dt) < 1e-12 * dt
     gp, gv = pos.cpu().numpy().astype(np.float64), vel.cpu().numpy().astype(np.float64)

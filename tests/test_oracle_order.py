@@ -10,6 +10,7 @@ recursive coordinate bisection that cut particles into tiles):
   sorted order along that row.
 """
 import numpy as np
+import pytest
 
 from oracle import crk as O
 from oracle import order as R
@@ -48,14 +49,14 @@ def test_hilbert_order_keeps_level_cells_contiguous():
         assert np.count_nonzero(np.diff(cell)) == len(np.unique(cell)) - 1, k
 
 
-def _splits(perm, q):
+def _splits(perm, q, leaf=R.TILE):
     """Re-derive every split of a bisection order and check it."""
     segs = [(0, len(perm))]
     leaves = 0
     while segs:
         a, b = segs.pop()
         size = b - a
-        if size <= R.TILE:
+        if size <= leaf:
             leaves += 1
             continue
         x = q[perm[a:b]].astype(np.int64)
@@ -82,6 +83,37 @@ def test_bisection_order_splits():
         q, _ = O.fixed_point(pos)
         leaves = _splits(perm, q)
         assert leaves >= (n + R.TILE - 1) // R.TILE
+
+
+@pytest.mark.parametrize("leaf", [128, 256])
+def test_bisection_to_the_papers_leaf_sizes(leaf):
+    """Leaves of at most 128 or 256 particles (Sec. 2.3, N_ppl): every split
+    re-derived (longest axis, lower part first, whole tiles on the left), and
+    the one-tile bisection's order is that of the larger leaves refined
+    further: its first splits are the same."""
+    rng = np.random.default_rng(19)
+    c = rng.random((6, 3))
+    n = 3000
+    x = (c[rng.integers(0, 6, n)] + 0.04 * rng.standard_normal((n, 3))) % 1.0
+    pos = np.empty((n, 4), np.float32)
+    pos[:, :3] = O._wrap_f32(x)
+    pos[:, 3] = 0.05
+    perm = R.bisection_order(pos, leaf=leaf)
+    assert np.array_equal(np.sort(perm), np.arange(n))
+    q, _ = O.fixed_point(pos)
+    leaves = _splits(perm, q, leaf)
+    assert (n + leaf - 1) // leaf <= leaves < (n + leaf - 1) // leaf * 2 + 1
+    # the same particles in the same leaves as the one-tile bisection groups
+    # at that level: each leaf of `leaf` particles is a union of its tiles
+    fine = R.bisection_order(pos)
+    segs, a = [], 0
+    def leaf_segments(a, b):
+        if b - a <= leaf:
+            return [(a, b)]
+        nl = R.split_left(b - a)
+        return leaf_segments(a, a + nl) + leaf_segments(a + nl, b)
+    for a, b in leaf_segments(0, n):
+        assert set(perm[a:b].tolist()) == set(fine[a:b].tolist())
 
 
 def test_bisection_of_a_row_is_the_sorted_row():

@@ -475,6 +475,31 @@ def test_kdk_step_is_second_order_with_the_predictor():
     assert np.all(r1 > 3.3) and np.all(r2 > 3.3), (r1, r2)
 
 
+def test_constant_density_proposal_on_a_lattice():
+    """The learned proposal with the zero network is the constant-density
+    solution of eq:hi, h (N_res / N)^(1/3) (Sec. 2.6; R18): on a perfect
+    lattice N grows as h^3 up to the discreteness of the count, so from 3, 3.5
+    or 4.5 spacings it lands within 1% of the solution (4 spacings, where
+    N = 4/3 pi 4^3 = 268.08 ~ N_res); a square root for the cube root, or the
+    inverse ratio, lands 5-40% away.  Particles already within tol keep their
+    h (the judge), and the clamp to h_max holds."""
+    side = 16
+    w = np.zeros(4801, np.float32)
+    for hs in (3.0, 3.5, 4.5):
+        st = perfect_lattice(side, h_spacings=hs)
+        N = O.volumes(st["pos_h"], k=0)["N"]
+        hp = O.h_propose(st["pos_h"], N, np.zeros(side ** 3), 0.01, w, 1e-4)
+        assert np.max(np.abs(hp * side / 4.0 - 1.0)) < 1e-2, (hs, hp[0] * side)
+    st = perfect_lattice(side, h_spacings=4.0)
+    N = O.volumes(st["pos_h"], k=0)["N"]
+    hp = O.h_propose(st["pos_h"], N, np.zeros(side ** 3), 0.01, w, 1e-2)   # |Delta_N - 1| < 1e-2: judged done
+    assert np.array_equal(hp, st["pos_h"][:, 3].astype(np.float64))
+    st = perfect_lattice(side, h_spacings=3.0)
+    N = O.volumes(st["pos_h"], k=0)["N"]
+    hp = O.h_propose(st["pos_h"], N, np.zeros(side ** 3), 0.01, w, 1e-4, h_max=3.2 / side)
+    assert np.allclose(hp, 3.2 / side, rtol=0, atol=1e-15)
+
+
 @pytest.mark.parametrize("h_mode", [1, 2])
 def test_kdk_step_solving_eq_hi_leaves_a_solution(h_mode):
     """A step with h_mode 1 (solve eq:hi from the state's h) or 2 (from the

@@ -740,7 +740,10 @@ def run_gpu(args):
     else:
         order_name = ORDER_ARGS[args.tile_order]
     order = {"tile_order": ORDERS[order_name][0], "rcb_leaf": ORDERS[order_name][1]}
+    if args.pair_form is not None:
+        order["pair_form"] = args.pair_form
     ctx = crk.crk_create(precision=args.precision, **order)
+    pair_form = args.pair_form if args.pair_form is not None else crk.crk_default_params().pair_form
 
     def barrier():
         if dist is not None:
@@ -931,6 +934,7 @@ def run_gpu(args):
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "n": n, "precision": PRECISION_NAMES[args.precision],
+                           "pair_form": ["directed", "pair-once"][pair_form],
                            "parallelism": "replicas" if world > 1 else "single",
                            "l2": "step working set ~%.1f GB > L2 (129 MB): inputs larger than L2, no flush"
                                  % ((n * 460 + entries * 20) / 1e9),
@@ -1019,6 +1023,9 @@ def main():
     ap.add_argument("--no-ai-step", action="store_true",
                     help="skip the steps that solve eq:hi (plain FP32 from h vs learned proposal)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the built-in pass variants")
+    ap.add_argument("--pair-form", type=int, default=None, choices=[0, 1],
+                    help="P4/P5 over the pair set: 0 directed (each ordered pair from its i side), "
+                         "1 pair-once (each unordered pair once); default: the library's")
     ap.add_argument("--variants", default="",
                     help="pin list-pass variants instead of tuning them (numbering of crk_tuning), "
                          "e.g. P1=20,P2=16,P3=9,P4=8,P5=9")

@@ -120,6 +120,20 @@ typedef struct {
     int rcb_leaf;     /* tile_order 2: particles per bisection leaf, 32 (default: one
                          tile), 128 or 256 (the paper's N_ppl range, Sec. 2.3: a leaf's tiles are
                          cut from the order the splits leave inside it) */
+    int pair_form;    /* how P4 and P5 visit the pair set when every tile is evaluated:
+                         0 = directed (default): every ordered pair (i, j) is evaluated
+                             from its i side (twice per unordered pair; F_ji = -F_ij
+                             bitwise);
+                         1 = pair-once: each unordered pair is evaluated once,
+                             by the particle with the lower sorted index, and j's share
+                             (-F_ij, its eq:eng and eq:compEng terms, its Q, the signal
+                             velocity) is summed per tile pair and added to j's sums in a
+                             fixed order.  Same terms bitwise, another summation order:
+                             the results differ from form 0 by rounding only, and repeat
+                             bitwise from run to run.  Slower than form 0 on GB300
+                             (its lanes wait on one another); kept as the measured
+                             alternative.  Passes over a subset of tiles (time bins)
+                             always use form 0. */
 } crk_params;
 
 /* Per-step diagnostics (host memory), all reductions in FP64. */
@@ -472,8 +486,7 @@ int crk_tune_set(crk_ctx *ctx, int pass, int variant);
  *  - n must be in [0, CRK_NOALLOC_MAX_N]; larger n returns CRK_EINVAL.
  *  - CRK_EINVAL also for invalid particle records (as crk_build_cells).
  *  - The first call on a device resolves the array's device address for that
- *    device (cudaGetSymbolAddress); make that first call before any stream
- *    capture.
+ *    device (cudaGetSymbolAddress) and keeps it for later calls.
  *  - All calls share the array and it keeps the last call's contents; each
  *    call clears what must start at zero.  Calls that overlap on the GPU
  *    (other streams, other host threads) race on it: serialise them.

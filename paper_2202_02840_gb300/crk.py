@@ -32,7 +32,7 @@ class crk_params(ctypes.Structure):
                  "h_min", "h_max", "dt_max", "a", "adot")] + [
         ("precision", ctypes.c_int), ("kmax", ctypes.c_int), ("tile_order", ctypes.c_int),
         ("density", ctypes.c_int), ("h_mode", ctypes.c_int), ("h_max_it", ctypes.c_int),
-        ("h_tol", ctypes.c_float), ("rcb_leaf", ctypes.c_int)]
+        ("h_tol", ctypes.c_float), ("rcb_leaf", ctypes.c_int), ("pair_form", ctypes.c_int)]
 
 
 class crk_diag(ctypes.Structure):

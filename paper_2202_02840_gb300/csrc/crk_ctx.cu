@@ -86,6 +86,9 @@ int crk_ensure_particles(crk_ctx *ctx, int n) {
     rc |= dalloc(ctx, &ctx->qV, cap);
     rc |= dalloc(ctx, &ctx->cnt_g, cap);
     rc |= dalloc(ctx, &ctx->cnt_u, cap);
+    rc |= dalloc(ctx, &ctx->lowc, cap);
+    rc |= dalloc(ctx, &ctx->po_self, tiles);
+    rc |= dalloc(ctx, &ctx->po_tofs, tiles);
     rc |= dalloc(ctx, &ctx->len_g, tiles);
     rc |= dalloc(ctx, &ctx->len_u, tiles);
     rc |= dalloc(ctx, &ctx->tbase, tiles);
@@ -156,6 +159,47 @@ int crk_grow_forces_keep(crk_ctx *ctx, long long n_force) {
     return CRK_OK;
 }
 
+// Arrays of the pair-once form, sized with the tile lists: per tile-list
+// entry the reverse index, a copy of the entry (the tile lists the pass ran
+// with, which P5 reads after the lists may have been refitted), and 32 lanes
+// of j-side sums.  Sized on first use, so that contexts that never evaluate
+// forces do not hold them; growing keeps the reverse index and the copy (the
+// next kick's P5 reads them), and a captured step finds them sized before the
+// capture.
+template <typename T>
+static int grow_keep(crk_ctx *ctx, T **p, long long old_n, long long new_n) {
+    T *nb = nullptr;
+    cudaError_t e = cudaMalloc((void **)&nb, sizeof(T) * (size_t)new_n);
+    if (e != cudaSuccess) return crk_check_cuda(ctx, e, "cudaMalloc");
+    if (*p && old_n > 0) {
+        e = cudaMemcpy(nb, *p, sizeof(T) * (size_t)old_n, cudaMemcpyDeviceToDevice);
+        if (e != cudaSuccess) {
+            cudaFree(nb);
+            return crk_check_cuda(ctx, e, "cudaMemcpy");
+        }
+    }
+    if (*p) cudaFree(*p);
+    *p = nb;
+    ctx->alloc_gen++;
+    return CRK_OK;
+}
+
+int crk_ensure_pair_once(crk_ctx *ctx) {
+    const long long want = ctx->cap_ulist;
+    if (ctx->po_cap >= want && ctx->po_rev) return CRK_OK;
+    if (ctx->graph_mode) return crk_set_error(ctx, CRK_ESTATE, "pair-once arrays grow during a capture");
+    int rc = grow_keep(ctx, &ctx->po_rev, ctx->po_cap, want);
+    if (!rc) rc = grow_keep(ctx, &ctx->po_tlist, ctx->po_cap, want);
+    if (!rc) rc = dalloc(ctx, &ctx->po_rowA, 32 * (size_t)want);
+    if (!rc) rc = dalloc(ctx, &ctx->po_rowB, 32 * (size_t)want);
+    if (rc) {
+        ctx->po_cap = 0;
+        return crk_set_error(ctx, CRK_ENOMEM, "cannot allocate pair-once sums for %lld tile pairs", want);
+    }
+    ctx->po_cap = want;
+    return CRK_OK;
+}
+
 int crk_ensure_lists(crk_ctx *ctx, long long ng, long long nu) {
     if (ng > 0xffffffffll || nu > 0xffffffffll)
         return crk_set_error(ctx, CRK_ECAPACITY, "interaction lists beyond 2^32 entries");
@@ -176,6 +220,9 @@ int crk_sync_counters(crk_ctx *ctx, cudaStream_t s) {
     CRK_CUDA(ctx, cudaMemcpyAsync(ctx->h_counters, ctx->counters, CNT_COUNT * sizeof(unsigned long long),
                                   cudaMemcpyDeviceToHost, s));
     CRK_CUDA(ctx, cudaStreamSynchronize(s));
+    if (ctx->h_counters[CNT_PO_MISS])   // the tile lists were not symmetric (sticky)
+        return crk_set_error(ctx, CRK_ESTATE, "pair-once: %llu tile pairs without their reverse",
+                             ctx->h_counters[CNT_PO_MISS]);
     return CRK_OK;
 }
 
@@ -437,6 +484,7 @@ extern "C" int crk_default_params(crk_params *p) {
     p->h_max_it = 50;
     p->h_tol = 1e-4f;
     p->rcb_leaf = 32;
+    p->pair_form = 0;
     return CRK_OK;
 }
 
@@ -450,7 +498,8 @@ extern "C" int crk_create(const crk_params *p, crk_ctx **out) {
         prm.kmax < 1 || prm.kmax > 7 || prm.precision < 0 || prm.precision > 3 || !(prm.dt_max > 0) ||
         prm.tile_order < 0 || prm.tile_order > 2 || prm.density < 0 || prm.density > 1 || !(prm.a > 0.0) || !(prm.a < 1e30) ||
         !(prm.adot > -1e30 && prm.adot < 1e30) || prm.h_mode < 0 || prm.h_mode > 2 || prm.h_max_it < 1 ||
-        !(prm.h_tol > 0.f) || (prm.rcb_leaf != 32 && prm.rcb_leaf != 128 && prm.rcb_leaf != 256))
+        !(prm.h_tol > 0.f) || (prm.rcb_leaf != 32 && prm.rcb_leaf != 128 && prm.rcb_leaf != 256) ||
+        prm.pair_form < 0 || prm.pair_form > 1)
         return CRK_EINVAL;
     crk_ctx *ctx = new (std::nothrow) crk_ctx();
     if (!ctx) return CRK_ENOMEM;
@@ -490,6 +539,8 @@ extern "C" int crk_destroy(crk_ctx *ctx) {
     dfree(&ctx->gofs); dfree(&ctx->uofs); dfree(&ctx->glist); dfree(&ctx->ulist);
     dfree(&ctx->qV); dfree(&ctx->cnt_g); dfree(&ctx->cnt_u); dfree(&ctx->len_g); dfree(&ctx->len_u);
     dfree(&ctx->tcap); dfree(&ctx->tbase); dfree(&ctx->ent); dfree(&ctx->Fst); dfree(&ctx->frec);
+    dfree(&ctx->lowc); dfree(&ctx->po_self); dfree(&ctx->po_rev); dfree(&ctx->po_rowA); dfree(&ctx->po_rowB);
+    dfree(&ctx->po_tofs); dfree(&ctx->po_tlist);
     dfree(&ctx->sfun); dfree(&ctx->sig); dfree(&ctx->sig2); dfree(&ctx->du_next);
     dfree(&ctx->cell_start); dfree(&ctx->counters);
     dfree(&ctx->V); dfree(&ctx->Nn); dfree(&ctx->vel); dfree(&ctx->mass);

@@ -121,6 +121,7 @@ struct PairOut {
     float D[3];    // grad W^R_ba - grad W^R_ab
     float Pt_b;    // P_b + Q_b of this pair
     float Q_a;     // Q_a of this pair
+    float Q_b;     // Q_b of this pair
 };
 
 // One pair of the pair set seen from particle a; x = x_a - x_b.
@@ -169,6 +170,7 @@ __device__ __forceinline__ void pair_force(const FRec &a, const FRec &b, const f
     for (int g = 0; g < 3; g++) o.F[g] = cF * o.D[g];
     o.Pt_b = Ptb;
     o.Q_a = Qa;
+    o.Q_b = Qb;
 }
 
 // Per-particle records of the pair-set passes, packed once per evaluation.
@@ -372,6 +374,431 @@ struct P5 {
     }
 };
 
+// ================================================================= pair-once form
+//
+// Each unordered pair of the pair set is evaluated once, by its owner: the
+// particle with the lower sorted index.  Lane i of tile I takes the entries
+// of its list with j > i, which are a suffix of its gather entries and a
+// suffix of its other entries (the walk records where they start), merged in
+// increasing j: lane i then meets the candidate tiles of I in increasing
+// order, the order of I's tile list.  j's share of a pair (-F_ij and the
+// terms of j's other sums) goes to a ring of PO_W rows of 32 slots in shared
+// memory (row: candidate tile mod PO_W, slot: j's lane).  Lanes that hit one
+// slot in the same step add in lane order (match_any), so the sums repeat
+// bitwise.  A lane more than PO_W - 1 candidate tiles ahead of the slowest
+// lane waits.  When every lane has passed a candidate tile J, its ring row is
+// written to J's row of j-side sums for the tile pair: the entry (J, I) of
+// J's tile list (po_rev).  A last pass adds, for each particle j, the rows of
+// the candidate tiles K <= J of J's tile list, in list order, to j's own
+// sums.  The tile lists are symmetric (the tile-pair test is), so every pair
+// (I, J) with I <= J has its row, and every row with K <= J is written once.
+
+constexpr int PO_W = 8;        // candidate tiles the ring spans
+constexpr int PO_WARPS = 4;    // tiles per CTA
+constexpr int PO_CMAX = 128;   // candidate tiles (from the tile's own on) staged in shared memory
+constexpr uint32_t PO_NONE = 0xffffffffu;
+
+struct POGeom {
+    int n, ntiles, kcap;
+    const uint32_t *fbase;        // per-tile stored-force base, units of 32 entries
+    const int32_t *cnt_g, *cnt_u;
+    const int2 *lowc;             // per particle: gather and other entries with j < i
+    const uint32_t *ent;
+    const uint2 *tofs;            // pair-set tile lists: (offset, count) per tile
+    const uint32_t *tlist;
+    const uint32_t *rev;          // entry (I, J), J >= I -> entry (J, I); PO_NONE if missing
+    const int32_t *self;          // position of each tile in its own list (-1 if missing)
+};
+
+// Reverse index of the tile lists (each list ascending): for entry (I, J)
+// with J > I the position of I in J's list, by bisection; J == I gives the
+// tile's own position.  A missing reverse (which the symmetric tile-pair
+// test rules out) is counted in *miss and its row is never written.  The
+// lists are copied beside it (copy_ofs, copy_list): the pair-once passes read
+// the copy, which stays the lists of this evaluation when the lists are
+// refitted before a later kick.
+__global__ void k_po_rev(int ntiles, const uint2 *__restrict__ tofs, const uint32_t *__restrict__ tlist,
+                         uint32_t *__restrict__ rev, int32_t *__restrict__ self, uint2 *__restrict__ copy_ofs,
+                         uint32_t *__restrict__ copy_list, unsigned long long *miss) {
+    const int lane = threadIdx.x & 31;
+    const int I = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    if (I >= ntiles) return;
+    const uint2 to = tofs[I];
+    if (lane == 0) copy_ofs[I] = to;
+    bool found = false;
+    for (uint32_t c = lane; c < to.y; c += 32) {
+        const uint32_t J = tlist[to.x + c];
+        copy_list[to.x + c] = J;
+        if (J == (uint32_t)I) {
+            self[I] = (int32_t)c;
+            rev[to.x + c] = to.x + c;
+            found = true;
+        } else if (J > (uint32_t)I) {
+            const uint2 tj = tofs[J];
+            uint32_t lo = 0, hi = tj.y;
+            while (lo < hi) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (tlist[tj.x + mid] < (uint32_t)I) lo = mid + 1; else hi = mid;
+            }
+            const bool ok = lo < tj.y && tlist[tj.x + lo] == (uint32_t)I;
+            rev[to.x + c] = ok ? tj.x + lo : PO_NONE;
+            if (!ok) atomicAdd(miss, 1ull);
+        }
+    }
+    if (__ballot_sync(0xffffffffu, found) == 0u && lane == 0) {
+        self[I] = -1;
+        atomicAdd(miss, 1ull);
+    }
+}
+
+// Write ring row c (candidate c of this tile's list) to its tile pair's row
+// `row` and clear it; lane l takes slot l.
+template <class P>
+__device__ __forceinline__ void po_flush(const typename P::Params &prm, float (*ring)[P::NS], uint32_t row, int c,
+                                         int lane) {
+    float *slot = ring[(c % PO_W) * 32 + lane];
+    if (row != PO_NONE) P::flush(row, lane, slot, prm);
+#pragma unroll
+    for (int q = 0; q < P::NS; q++) slot[q] = 0.f;
+}
+
+// One tile of a pair-once pass.  P provides NS (floats of a share), Ent (what
+// a lane reads per list entry), Rec (the neighbour data), IState and
+//   init(IState&, int i, bool valid, const Params&)
+//   fetch(const uint32_t *col0, size_t fb, int mg, int kcap, int k, const Params&) -> Ent   (entry k)
+//   jof(const Ent&) -> j
+//   load(const Ent&, const Params&) -> Rec
+//   pair(IState&, const Rec&, const Ent&, size_t pos, bool in_i, const Params&, float share[NS])
+//   add(float *slot, const float share[NS]), flush(uint32_t row, int lane, const float *slot, const Params&)
+//   finish(IState&, int i, const Params&)          (valid lanes: i's own sums)
+template <class P>
+__device__ __forceinline__ void po_tile(const POGeom &g, const typename P::Params &prm, int tile, int lane,
+                                        float (*ring)[P::NS], uint32_t *stl, uint32_t *srv) {
+    using Ent = typename P::Ent;
+    const int i = tile * TILE + lane;
+    const bool valid = i < g.n;
+    typename P::IState st;
+    P::init(st, i, valid, prm);
+    const uint2 to = g.tofs[tile];
+    const int C = (int)to.y;
+    const int cself = g.self[tile];
+    if (cself < 0) return;   // counted by the reverse index
+    // the candidate tiles from this tile on, and their reverse entries
+    const int nst = min(C - cself, PO_CMAX);
+    for (int q = lane; q < nst; q += 32) {
+        stl[q] = __ldg(g.tlist + to.x + cself + q);
+        srv[q] = __ldg(g.rev + to.x + cself + q);
+    }
+    __syncwarp();
+    auto tl_at = [&](int c) -> uint32_t {
+        return c - cself < PO_CMAX ? stl[c - cself] : __ldg(g.tlist + to.x + c);
+    };
+    auto rv_at = [&](int c) -> uint32_t { return c - cself < PO_CMAX ? srv[c - cself] : __ldg(g.rev + to.x + c); };
+    const uint32_t *col0 = g.ent + (size_t)tile * g.kcap * 32 + lane;
+    const size_t fb = (size_t)g.fbase[tile] * 32 + lane;
+    const int mg = valid ? min(g.cnt_g[i], g.kcap) : 0;
+    const int mu = valid ? min(g.cnt_u[i], g.kcap) : 0;
+    const int2 lw = valid ? g.lowc[i] : make_int2(0, 0);
+    // owned entries: gather [kg, mg), other [ko, mu) (virtual indices)
+    int kg = min(lw.x, mg), ko = mg + min(lw.y, mu - mg);
+    Ent eg{}, eo{};
+    if (kg < mg) eg = P::fetch(col0, fb, mg, g.kcap, kg, prm);
+    if (ko < mu) eo = P::fetch(col0, fb, mg, g.kcap, ko, prm);
+    // next owned entry in increasing j (a j is in one of the two segments only)
+    auto pick = [&](int &k, Ent &e, bool &gath) -> bool {
+        const uint32_t jg = kg < mg ? P::jof(eg) : PO_NONE;
+        const uint32_t jo = ko < mu ? P::jof(eo) : PO_NONE;
+        if (jg == PO_NONE && jo == PO_NONE) return false;
+        if (jg < jo) {
+            k = kg; e = eg; gath = true;
+            if (++kg < mg) eg = P::fetch(col0, fb, mg, g.kcap, kg, prm);
+        } else {
+            k = ko; e = eo; gath = false;
+            if (++ko < mu) eo = P::fetch(col0, fb, mg, g.kcap, ko, prm);
+        }
+        return true;
+    };
+    // position of j's tile in this tile's list (monotone over a lane's entries)
+    int cp = cself;
+    uint32_t cJ = (uint32_t)tile;
+    auto cand = [&](uint32_t j) -> int {
+        const uint32_t J = j / TILE;
+        while (cJ < J && cp + 1 < C) cJ = tl_at(++cp);
+        return cp;
+    };
+    int k = 0;
+    Ent e{};
+    bool gath = false;
+    bool have = pick(k, e, gath);
+    typename P::Rec rc{};
+    int c = C;
+    if (have) {
+        rc = P::load(e, prm);
+        c = cand(P::jof(e));
+    }
+    int cf = cself;   // ring rows below cf are written out
+    for (;;) {
+        const int cm = (int)__reduce_min_sync(0xffffffffu, (unsigned)(have ? c : C));
+        if (cf < cm) {
+            __syncwarp();
+            for (; cf < cm; cf++) po_flush<P>(prm, ring, rv_at(cf), cf, lane);
+            __syncwarp();
+        }
+        if (cm >= C) break;
+        const bool go = have && c < cf + PO_W;
+        int k2 = 0;
+        Ent e2{};
+        bool g2 = false, have2 = false;
+        typename P::Rec rn{};
+        if (go) {
+            have2 = pick(k2, e2, g2);
+            if (have2) rn = P::load(e2, prm);
+        }
+        float sh[P::NS];
+        if (go) P::pair(st, rc, e, fb + (size_t)k * 32, gath, prm, sh);
+        // j's share into the ring: lanes with the same slot add in lane order
+        const uint32_t key = ((uint32_t)(c % PO_W) << 5) | (P::jof(e) & 31u);
+        unsigned pend = __ballot_sync(0xffffffffu, go);
+        while (pend) {
+            const bool mine = (pend >> lane) & 1u;
+            const unsigned grp = __match_any_sync(0xffffffffu, mine ? key : (0x10000u | (uint32_t)lane));
+            const bool lead = mine && (__ffs(grp) - 1 == lane);
+            if (lead) P::add(ring[key], sh);
+            pend &= ~__ballot_sync(0xffffffffu, lead);
+        }
+        if (go) {
+            have = have2;
+            k = k2;
+            e = e2;
+            gath = g2;
+            rc = rn;
+            c = have ? cand(P::jof(e)) : C;
+        }
+    }
+    if (valid) P::finish(st, i, prm);
+}
+
+template <class P>
+__global__ void __launch_bounds__(PO_WARPS * 32) k_po(POGeom g, typename P::Params prm) {
+    __shared__ float ring[PO_WARPS][PO_W * 32][P::NS];
+    __shared__ uint32_t stl[PO_WARPS][PO_CMAX], srv[PO_WARPS][PO_CMAX];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int tile = blockIdx.x * PO_WARPS + w;
+    if (tile >= g.ntiles) return;
+    if (pass_skipped<P>(prm)) return;
+    for (int q = lane; q < PO_W * 32; q += 32)
+#pragma unroll
+        for (int v = 0; v < P::NS; v++) ring[w][q][v] = 0.f;
+    __syncwarp();
+    po_tile<P>(g, prm, tile, lane, ring[w], stl[w], srv[w]);
+}
+
+// P4 in the pair-once form: the same pair function; i's sums as in P4, and
+// j's share -F_ij, 1/2 V_j V_i P~_i (dx_i/dt - dx_j/dt).(grad W^R_ij - grad W^R_ji),
+// Q_j of the pair and the pair's signal velocity, each bitwise the term the
+// directed form evaluates from j's side.
+template <bool COMP>
+struct P4PO {
+    static constexpr int NS = 6;   // F (3), du, Q, vsig
+    using Ent = uint32_t;
+    using Rec = FRec;
+    using IState = typename P4<COMP>::IState;
+    struct Params {
+        const FRec *frec;
+        const float *mass;
+        FParams fp;
+        float4 *acc;     // own sums (F, du) here; the row pass completes them
+        float2 *vq;
+        float4 *Fst;     // (F_ij, j) at the owner's entry
+        float4 *rowA;    // (F, du) per (tile-list entry, lane)
+        float2 *rowB;    // (Q, vsig)
+    };
+    __device__ static void init(IState &s, int i, bool valid, const Params &p) {
+        typename P4<COMP>::Params q{p.frec, p.mass, p.fp, p.acc, p.vq, p.Fst};
+        P4<COMP>::init(s, i, valid, q);
+    }
+    __device__ static Ent fetch(const uint32_t *col0, size_t, int mg, int kcap, int k, const Params &) {
+        const int c = k < mg ? k : kcap - 1 - (k - mg);
+        return __ldg(col0 + (size_t)c * 32);
+    }
+    __device__ static uint32_t jof(const Ent &e) { return e & 0x3fffffffu; }
+    __device__ static Rec load(const Ent &e, const Params &p) { return ldg_frec(p.frec + (e & 0x3fffffffu)); }
+    __device__ static void pair(IState &s, const Rec &r, const Ent &e, size_t pos, bool in_i, const Params &p,
+                                float sh[NS]) {
+        const bool in_j = in_i ? (e >> 31) != 0u : true;
+        int dx = (int)(fq(s.me, 0) - fq(r, 0)), dy = (int)(fq(s.me, 1) - fq(r, 1)), dz = (int)(fq(s.me, 2) - fq(r, 2));
+        Sep d = separation(dx, dy, dz);
+        float x[3] = {d.x, d.y, d.z};
+        PairOut o;
+        pair_force(s.me, r, x, d.r2, d.r, in_i, in_j, p.fp, o);
+        p.Fst[pos] = make_float4(o.F[0], o.F[1], o.F[2], __uint_as_float(e & 0x3fffffffu));   // F_ij, j
+        float dv[3] = {r.w3.x - s.me.w3.x, r.w3.y - s.me.w3.y, r.w3.z - s.me.w3.z};
+#pragma unroll
+        for (int g = 0; g < 3; g++) s.F[g].add(o.F[g]);
+        float wd = fmaf(dv[0], o.D[0], fmaf(dv[1], o.D[1], dv[2] * o.D[2]));
+        const float hvv = 0.5f * (s.me.w1.w * r.w1.w);
+        s.du.add(hvv * o.Pt_b * wd);
+        float vx = fmaf(p.fp.adot_a, d.r2, -fmaf(dv[0], x[0], fmaf(dv[1], x[1], dv[2] * x[2])) * p.fp.inv_a2);
+        const float vs = (vx < 0.f && d.r > 0.f) ? FDIV(-vx, d.r) : 0.f;
+        s.vsig = fmaxf(s.vsig, vs);
+        s.qmax = fmaxf(s.qmax, o.Q_a);
+        sh[0] = -o.F[0];
+        sh[1] = -o.F[1];
+        sh[2] = -o.F[2];
+        sh[3] = hvv * (s.me.w2.x + o.Q_a) * wd;
+        sh[4] = o.Q_b;
+        sh[5] = vs;
+    }
+    __device__ static void add(float *slot, const float sh[NS]) {
+        slot[0] += sh[0];
+        slot[1] += sh[1];
+        slot[2] += sh[2];
+        slot[3] += sh[3];
+        slot[4] = fmaxf(slot[4], sh[4]);
+        slot[5] = fmaxf(slot[5], sh[5]);
+    }
+    __device__ static void flush(uint32_t row, int lane, const float *slot, const Params &p) {
+        p.rowA[(size_t)row * 32 + lane] = make_float4(slot[0], slot[1], slot[2], slot[3]);
+        p.rowB[(size_t)row * 32 + lane] = make_float2(slot[4], slot[5]);
+    }
+    __device__ static void finish(IState &s, int i, const Params &p) {
+        p.acc[i] = make_float4(s.F[0].value(), s.F[1].value(), s.F[2].value(), s.du.value());
+        p.vq[i] = make_float2(s.vsig, s.qmax);
+    }
+};
+
+// P4 rows: j's own sums plus the rows of the candidate tiles K <= J of its
+// list, in list order; then the scalings of P4's finish.
+template <bool COMP>
+__global__ void k_p4po_rows(int n, const uint2 *__restrict__ tofs, const int32_t *__restrict__ self,
+                            const float4 *__restrict__ rowA, const float2 *__restrict__ rowB,
+                            const float *__restrict__ mass, FParams fp, float4 *__restrict__ acc,
+                            float2 *__restrict__ vq) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int tile = i / TILE, lane = i % TILE;
+    const float4 own = acc[i];
+    float2 v = vq[i];
+    Acc<COMP> F[3], du;
+    F[0].add(own.x);
+    F[1].add(own.y);
+    F[2].add(own.z);
+    du.add(own.w);
+    const uint32_t x = tofs[tile].x;
+    const int cs = self[tile];
+    for (int c = 0; c <= cs; c++) {
+        const size_t r = ((size_t)x + c) * 32 + lane;
+        const float4 a = rowA[r];
+        const float2 b = rowB[r];
+        F[0].add(a.x);
+        F[1].add(a.y);
+        F[2].add(a.z);
+        du.add(a.w);
+        v.x = fmaxf(v.x, b.y);
+        v.y = fmaxf(v.y, b.x);
+    }
+    const float im = 1.f / mass[i];
+    acc[i] = make_float4(F[0].value() * im, F[1].value() * im, F[2].value() * im, du.value() * im * fp.inv_a4);
+    vq[i] = v;
+}
+
+// P5 in the pair-once form over the owner's stored (F_ij, j): i's term as in
+// P5 and j's, f_ji 2 Delta E_ji with 2 Delta E_ji = 2 Delta E_ij bitwise and
+// the partition of eq:fij taken from j's side.
+template <bool COMP, bool DUAL>
+struct P5PO {
+    static constexpr int NS = 2;   // du (this kick), du2 (the second kick)
+    static constexpr bool SKIPPABLE = true;
+    using Ent = float4;
+    struct Rec {
+        float4 sig, sig2;
+    };
+    using IState = typename P5<COMP, DUAL>::IState;
+    struct Params {
+        const float4 *sig;
+        const float4 *Fst;
+        const float *mass;
+        float *du;       // own sums here; the row pass completes them
+        float inv_a4;
+        const unsigned long long *skip;
+        float *du2;
+        float2 *rowB;
+    };
+    __device__ static void init(IState &s, int i, bool valid, const Params &p) {
+        typename P5<COMP, DUAL>::Params q{p.sig, p.Fst, p.mass, p.du, p.inv_a4, p.skip, p.du2};
+        P5<COMP, DUAL>::init(s, i, valid, q);
+    }
+    __device__ static Ent fetch(const uint32_t *, size_t fb, int, int, int k, const Params &p) {
+        return __ldg(p.Fst + fb + (size_t)k * 32);
+    }
+    __device__ static uint32_t jof(const Ent &F) { return __float_as_uint(F.w); }
+    __device__ static Rec load(const Ent &F, const Params &p) {
+        const uint32_t j = __float_as_uint(F.w);
+        Rec r;
+        if (DUAL)
+            ldg_v8(p.sig + 2 * (size_t)j, r.sig, r.sig2);
+        else
+            r.sig = __ldg(p.sig + j);
+        return r;
+    }
+    __device__ static float dotw(const float4 &me, const float4 &r, const float4 &F) {
+        return fmaf(r.x - me.x, F.x, fmaf(r.y - me.y, F.y, (r.z - me.z) * F.z));
+    }
+    __device__ static void pair(IState &s, const Rec &rec, const Ent &F, size_t, bool, const Params &,
+                                float sh[NS]) {
+        const Part pt = partition(s.me.w, rec.sig.w);
+        const bool jge = rec.sig.w >= s.me.w;   // s_j >= s_i: the partition seen from j
+        const float w = dotw(s.me, rec.sig, F);
+        s.du.add((((w >= 0.f) == pt.ige) ? pt.fmn : pt.fmx) * w);
+        sh[0] = (((w >= 0.f) == jge) ? pt.fmn : pt.fmx) * w;
+        sh[1] = 0.f;
+        if (DUAL) {
+            const float w2 = dotw(s.me2, rec.sig2, F);
+            s.du2.add((((w2 >= 0.f) == pt.ige) ? pt.fmn : pt.fmx) * w2);
+            sh[1] = (((w2 >= 0.f) == jge) ? pt.fmn : pt.fmx) * w2;
+        }
+    }
+    __device__ static void add(float *slot, const float sh[NS]) {
+        slot[0] += sh[0];
+        slot[1] += sh[1];
+    }
+    __device__ static void flush(uint32_t row, int lane, const float *slot, const Params &p) {
+        p.rowB[(size_t)row * 32 + lane] = make_float2(slot[0], slot[1]);
+    }
+    __device__ static void finish(IState &s, int i, const Params &p) {
+        p.du[i] = s.du.value();
+        if (DUAL) p.du2[i] = s.du2.value();
+    }
+};
+
+template <bool COMP, bool DUAL>
+__global__ void k_p5po_rows(int n, const uint2 *__restrict__ tofs, const int32_t *__restrict__ self,
+                            const float2 *__restrict__ rowB, const float *__restrict__ mass, float inv_a4,
+                            const unsigned long long *skip, float *__restrict__ du, float *__restrict__ du2) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (skip && *(volatile const unsigned long long *)skip) return;
+    const int tile = i / TILE, lane = i % TILE;
+    Acc<COMP> s1, s2;
+    s1.add(du[i]);
+    if (DUAL) s2.add(du2[i]);
+    const uint32_t x = tofs[tile].x;
+    const int cs = self[tile];
+    for (int c = 0; c <= cs; c++) {
+        const float2 b = rowB[((size_t)x + c) * 32 + lane];
+        s1.add(b.x);
+        if (DUAL) s2.add(b.y);
+    }
+    const float m = mass[i];
+    du[i] = 0.5f * s1.value() / m * inv_a4;
+    if (DUAL) du2[i] = 0.5f * s2.value() / m * inv_a4;
+}
+
+static POGeom po_geom(const crk_ctx *ctx) {
+    return POGeom{ctx->n,   ctx->ntiles,  ctx->kcap,     ctx->tbase,  ctx->cnt_g,  ctx->cnt_u, ctx->lowc,
+                  ctx->ent, ctx->po_tofs, ctx->po_tlist, ctx->po_rev, ctx->po_self};
+}
+
 static FParams fparams(const crk_params &c) {
     FParams f;
     f.gamma = (float)c.gamma;
@@ -400,6 +827,52 @@ __global__ void k_sig(int n, const float4 *__restrict__ vb, const float4 *__rest
     sig[i] = make_float4(b.x + a.x, b.y + a.y, b.z + a.z, sfun[i]);
 }
 
+// P4 over the whole pair set in the pair-once form: the reverse index of the
+// tile lists, the pass, and the rows pass that completes every particle's sums.
+template <bool COMP>
+static int run_forces_po(crk_ctx *ctx, const FRec *fr, const FParams &fp, cudaStream_t s) {
+    if (!ctx->lists_valid) return crk_set_error(ctx, CRK_ESTATE, "P4 forces: neighbour lists are not built");
+    int rc = crk_ensure_pair_once(ctx);
+    if (rc) return rc;
+    typename P4PO<COMP>::Params p{fr, ctx->mass, fp, ctx->acc, ctx->vq, ctx->Fst, ctx->po_rowA, ctx->po_rowB};
+    prof_begin(ctx, PROF_P4, s);
+    k_po_rev<<<grid_for(ctx->ntiles, 8), 256, 0, s>>>(ctx->ntiles, ctx->uofs, ctx->ulist, ctx->po_rev,
+                                                       ctx->po_self, ctx->po_tofs, ctx->po_tlist,
+                                                       ctx->counters + CNT_PO_MISS);
+    k_po<P4PO<COMP>><<<grid_for(ctx->ntiles, PO_WARPS), PO_WARPS * 32, 0, s>>>(po_geom(ctx), p);
+    k_p4po_rows<COMP><<<grid_for(ctx->n, 256), 256, 0, s>>>(ctx->n, ctx->po_tofs, ctx->po_self, ctx->po_rowA,
+                                                            ctx->po_rowB, ctx->mass, fp, ctx->acc, ctx->vq);
+    ctx->launches += 3;
+    prof_end(ctx, s);
+    CRK_LAUNCH_CHECK(ctx, "P4 forces (pair-once)");
+    ctx->fst_po = 1;
+    return CRK_OK;
+}
+
+// P5 over the pair-once stored forces: the pass and its rows pass.
+template <bool COMP, bool DUAL>
+static int run_compat_po(crk_ctx *ctx, const float4 *sig, float ia4, const unsigned long long *skip, float *du2,
+                         cudaStream_t s, const char *what) {
+    if (!ctx->lists_valid) return crk_set_error(ctx, CRK_ESTATE, "%s: neighbour lists are not built", what);
+    typename P5PO<COMP, DUAL>::Params p{sig, ctx->Fst, ctx->mass, ctx->du, ia4, skip, du2, ctx->po_rowB};
+    prof_begin(ctx, PROF_P5, s);
+    k_po<P5PO<COMP, DUAL>><<<grid_for(ctx->ntiles, PO_WARPS), PO_WARPS * 32, 0, s>>>(po_geom(ctx), p);
+    k_p5po_rows<COMP, DUAL><<<grid_for(ctx->n, 256), 256, 0, s>>>(ctx->n, ctx->po_tofs, ctx->po_self, ctx->po_rowB,
+                                                                  ctx->mass, ia4, skip, ctx->du, du2);
+    ctx->launches += 2;
+    prof_end(ctx, s);
+    CRK_LAUNCH_CHECK(ctx, what);
+    return CRK_OK;
+}
+
+// Which form P5 takes: that of the P4 whose forces it reads.
+static int p5_form(crk_ctx *ctx, bool *po) {
+    *po = ctx->fst_po != 0;
+    if (*po && ctx->act)
+        return crk_set_error(ctx, CRK_ESTATE, "P5 over a tile subset needs the directed form of the stored forces");
+    return CRK_OK;
+}
+
 int run_forces(crk_ctx *ctx, cudaStream_t s) {
     if (ctx->n == 0) return CRK_OK;
     FParams fp = fparams(ctx->p);
@@ -414,6 +887,9 @@ int run_forces(crk_ctx *ctx, cudaStream_t s) {
     ++ctx->launches;
     CRK_LAUNCH_CHECK(ctx, "pack pair records");
     const FRec *fr = reinterpret_cast<const FRec *>(ctx->frec);
+    if (!ctx->act && ctx->p.pair_form == 1)
+        return ctx->p.precision >= 1 ? run_forces_po<true>(ctx, fr, fp, s) : run_forces_po<false>(ctx, fr, fp, s);
+    ctx->fst_po = 0;
     if (ctx->p.precision >= 1) {
         typename P4<true>::Params p{fr, ctx->mass, fp, ctx->acc, ctx->vq, ctx->Fst};
         return launch_lpass<P4<true>, 1>(ctx, PROF_P4, p, s, "P4 forces");
@@ -430,6 +906,13 @@ int run_compatible(crk_ctx *ctx, cudaStream_t s, const unsigned long long *skip)
     ++ctx->launches;
     CRK_LAUNCH_CHECK(ctx, "kick sums");
     const float ia4 = (float)(1.0 / (ctx->p.a * ctx->p.a * ctx->p.a * ctx->p.a));
+    bool po = false;
+    int rc = p5_form(ctx, &po);
+    if (rc) return rc;
+    if (po)
+        return ctx->p.precision >= 1
+                   ? run_compat_po<true, false>(ctx, ctx->sig, ia4, skip, nullptr, s, "P5 compatible energy")
+                   : run_compat_po<false, false>(ctx, ctx->sig, ia4, skip, nullptr, s, "P5 compatible energy");
     if (ctx->p.precision >= 1) {
         typename P5<true>::Params p{ctx->sig, ctx->Fst, ctx->mass, ctx->du, ia4, skip, nullptr};
         return launch_lpass<P5<true>, 8>(ctx, PROF_P5, p, s, "P5 compatible energy");
@@ -462,6 +945,14 @@ int run_compatible_dual(crk_ctx *ctx, const double *dtn, const int32_t *sbox, cu
     ++ctx->launches;
     CRK_LAUNCH_CHECK(ctx, "kick sums");
     const float ia4 = (float)(1.0 / (ctx->p.a * ctx->p.a * ctx->p.a * ctx->p.a));
+    bool po = false;
+    int rc = p5_form(ctx, &po);
+    if (rc) return rc;
+    if (po)
+        return ctx->p.precision >= 1 ? run_compat_po<true, true>(ctx, ctx->sig2, ia4, nullptr, ctx->du_next, s,
+                                                                 "P5 compatible energy (two kicks)")
+                                     : run_compat_po<false, true>(ctx, ctx->sig2, ia4, nullptr, ctx->du_next, s,
+                                                                  "P5 compatible energy (two kicks)");
     if (ctx->p.precision >= 1) {
         typename P5<true, true>::Params p{ctx->sig2, ctx->Fst, ctx->mass, ctx->du, ia4, nullptr, ctx->du_next};
         return launch_lpass<P5<true, true>, 8>(ctx, PROF_P5, p, s, "P5 compatible energy (two kicks)",

@@ -38,6 +38,7 @@ enum {
     CNT_NACT = 17,      // time bins: leaves ending a step at the current tick (and 18: their particles)
     CNT_NEXT_OK = 19,   // du_next holds the next opening kick's energy rate for dt_next
     CNT_SKIP = 20,      // this step's opening kick takes du_next
+    CNT_PO_MISS = 21,   // pair-once: tile pairs (I, J) whose reverse (J, I) was not found (sticky)
     CNT_COUNT = 24
 };
 
@@ -118,6 +119,15 @@ struct crk_ctx {
     uint32_t *tcap = nullptr, *tbase = nullptr;   // per-tile stored-force base (units of 32)
     uint32_t *ent = nullptr;         // list entries: j | (j's kernel reaches i) << 31
     float4 *Fst = nullptr;           // F_ij per entry (P4 -> P5), compact layout
+    int2 *lowc = nullptr;            // per particle: gather and other list entries with j < i
+    int32_t *po_self = nullptr;      // pair-once: position of each tile in its own tile list
+    uint32_t *po_rev = nullptr;      // pair-once: for tile-list entry (I, J), J >= I, the entry (J, I)
+    uint2 *po_tofs = nullptr;        // pair-once: copy of the tile lists its P4 ran with (offset, count)
+    uint32_t *po_tlist = nullptr;    //   and their entries
+    float4 *po_rowA = nullptr;       // pair-once: j-side sums per (tile-list entry, lane): P4 (F, du)
+    float2 *po_rowB = nullptr;       // P4 (Q, vsig); P5 (du, du of the second kick)
+    long long po_cap = 0;            // tile-list entries the pair-once arrays hold
+    int fst_po = 0;                  // Fst holds the pair-once form (owned entries only)
     long long ent_cap = 0, f_cap = 0, entries = 0;
     int kcap = 384;                  // list columns per particle
     int volumes_only = 0;            // walk without writing lists (no list buffer)
@@ -242,6 +252,7 @@ int crk_set_error(crk_ctx *ctx, int code, const char *fmt, ...);
 int crk_check_cuda(crk_ctx *ctx, cudaError_t e, const char *what);
 int crk_ensure_particles(crk_ctx *ctx, int n);
 int crk_ensure_lists(crk_ctx *ctx, long long ng, long long nu);
+int crk_ensure_pair_once(crk_ctx *ctx);
 int crk_ensure_entries(crk_ctx *ctx, long long n_ent, long long n_force);
 int crk_grow_forces_keep(crk_ctx *ctx, long long n_force);
 int crk_sync_counters(crk_ctx *ctx, cudaStream_t s);

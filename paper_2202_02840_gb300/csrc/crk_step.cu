@@ -688,7 +688,8 @@ namespace {
 
 // sticky overflow / invalid-input flag of a replayed step
 __global__ void k_graph_check(unsigned long long *cnt, long long cap_ulist, int kcap) {
-    if (cnt[CNT_ERR_INPUT] || (long long)cnt[CNT_ULIST] > cap_ulist || (long long)cnt[CNT_MAXCNT] > kcap)
+    if (cnt[CNT_ERR_INPUT] || cnt[CNT_PO_MISS] || (long long)cnt[CNT_ULIST] > cap_ulist ||
+        (long long)cnt[CNT_MAXCNT] > kcap)
         cnt[CNT_GRAPH_ERR] = 1ull;
 }
 
@@ -855,6 +856,10 @@ static int steps_impl(crk_ctx *ctx, int n, float *pos_h, float *vel_u, const flo
         CRK_CUDA(ctx, cudaStreamSynchronize(s));
         rc = crk_grow_forces_keep(ctx, (long long)ctx->ntiles * ctx->kcap * 32);
         if (rc) return rc;
+        if (ctx->p.pair_form == 1) {   // the pair-once arrays follow the tile lists' headroom
+            rc = crk_ensure_pair_once(ctx);
+            if (rc) return rc;
+        }
         if (n > ctx->cap_bk) {
             if (ctx->bk_pos) cudaFree(ctx->bk_pos);
             if (ctx->bk_vel) cudaFree(ctx->bk_vel);

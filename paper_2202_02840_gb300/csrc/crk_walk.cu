@@ -35,6 +35,7 @@ struct WalkArgs {
     const int32_t *sbox;     // batched boxes: box of each slot (BATCH only)
     const uint32_t *nbox;    // box range of each tile (BATCH only)
     const int32_t *act;      // may be null: walk the tiles act[0 .. ntiles) only
+    int2 *lowc;              // may be null: per particle, gather and other entries with j < i
 };
 
 // LISTS: write the lists; VOL: sum n_i in the walk (volumes-only contexts).
@@ -66,6 +67,7 @@ __global__ void __launch_bounds__(WALK_WARPS * 32) k_walk(WalkArgs a) {
     uint32_t *const col0 = LISTS ? a.ent + (size_t)tile * kcap * 32 + lane : nullptr;
     float acc = 0.f;
     int cg = 0, co = 0;
+    int lg = 0, lo_ = 0;   // entries with j < i: the candidate tiles come in ascending order
     const uint2 lo = a.ofs[tile];
     const uint4 Ilo = __ldg(a.tlo + tile), Ihi = __ldg(a.thi + tile);   // this tile's box, max H
     const int32_t bi = BATCH && valid ? a.sbox[i] : 0;
@@ -170,6 +172,11 @@ __global__ void __launch_bounds__(WALK_WARPS * 32) k_walk(WalkArgs a) {
                 gm &= ~(1u << lane);
                 om &= ~(1u << lane);
             }
+            if (J <= tile) {
+                const unsigned below = J == tile ? lanemask_lt() : 0xffffffffu;
+                lg = cg + __popc(gm & below);
+                lo_ = co + __popc(om & below);
+            }
             while (gm) {
                 const int jj = __ffs(gm) - 1;
                 gm &= gm - 1u;
@@ -204,6 +211,7 @@ __global__ void __launch_bounds__(WALK_WARPS * 32) k_walk(WalkArgs a) {
         }
         a.cnt_g[i] = cg;
         a.cnt_u[i] = cu;
+        if (LISTS && a.lowc) a.lowc[i] = make_int2(lg, lo_);
     }
     uint32_t mg = __reduce_max_sync(0xffffffffu, (uint32_t)cg);
     uint32_t mu = __reduce_max_sync(0xffffffffu, (uint32_t)cu);
@@ -359,6 +367,7 @@ static WalkArgs walk_args(crk_ctx *ctx) {
     a.nbox = ctx->nbox > 1 ? ctx->node_box : nullptr;
     a.act = ctx->act;
     if (ctx->act) a.ntiles = ctx->nact;
+    a.lowc = ctx->volumes_only ? nullptr : ctx->lowc;
     return a;
 }
 

@@ -136,11 +136,13 @@ def test_bad_box_tables_are_rejected(table):
 
 def test_autotuned_passes_give_identical_results():
     """Every variant visits each list in the same order: results do not depend
-    on which one the tuner keeps (bitwise), and a choice is made per pass."""
+    on which one the tuner keeps (bitwise), and a choice is made per pass.
+    P4 and P5 are tuned in their directed form (pair_form 0); the pair-once
+    form has one loop form, so a pair-once context tunes P1-P3 only."""
     st = workload("clustered", 3000, 11)
     outs = []
     for tune in (False, True):
-        ctx = crk.crk_create()
+        ctx = crk.crk_create(pair_form=0)
         if tune:
             crk.crk_autotune(ctx, True)
         pos, vel, mass = dev(st["pos_h"]), dev(st["vel_u"]), dev(st["mass"])
@@ -160,6 +162,13 @@ def test_autotuned_passes_give_identical_results():
             assert all(0 <= v < crk.CRK_TUNE_NVARIANT and ms > 0 for v, ms in t.values())
     for a, b in zip(*outs):
         assert torch.equal(a, b)
+    ctx = crk.crk_create(pair_form=1)
+    crk.crk_autotune(ctx, True)
+    pos, vel, mass = dev(st["pos_h"]), dev(st["vel_u"]), dev(st["mass"])
+    for _ in range(2):
+        crk.crk_step(ctx, pos, vel, mass, 0.0)
+    t = crk.crk_tuning(ctx)
+    assert set(t) >= {"P1 volumes", "P2 corrections", "P3 grad v"} and "P4 forces" not in t, t
 
 
 def test_every_pass_variant_gives_identical_results():
@@ -170,7 +179,7 @@ def test_every_pass_variant_gives_identical_results():
     names = ("P1 volumes", "P2 corrections", "P3 grad v", "P4 forces", "P5 compatible energy")
 
     def run(v):
-        ctx = crk.crk_create()
+        ctx = crk.crk_create(pair_form=0)   # the directed P4 and P5 have the variants
         for name in names:
             crk.crk_tune_set(ctx, name, v)
         ran = set(names)
@@ -211,15 +220,17 @@ def test_every_pass_variant_gives_identical_results():
 
 # ---------------------------------------------------------------- CUDA graphs
 
+@pytest.mark.parametrize("pair_form", [0, 1])
 @pytest.mark.parametrize("case", ["uniform16", "sedov16"])
-def test_graph_steps_equal_eager_steps(case):
+def test_graph_steps_equal_eager_steps(case, pair_form):
     """Captured-and-replayed steps are the eager steps, bit for bit (inputs
-    whose neighbour counts stay within the list headroom)."""
+    whose neighbour counts stay within the list headroom), in either form of
+    P4 and P5 (the pair-once arrays follow the tile lists' headroom)."""
     st = {"uniform16": lambda: workload("uniform", 16), "clustered3000": lambda: workload("clustered", 3000, 11),
           "sedov16": lambda: workload("sedov", 16)}[case]()
     res = []
     for mode in ("graph", "eager", "step"):
-        ctx = crk.crk_create()
+        ctx = crk.crk_create(pair_form=pair_form)
         pos, vel, mass = dev(st["pos_h"]), dev(st["vel_u"]), dev(st["mass"])
         if mode == "step":
             for _ in range(6):

@@ -89,20 +89,24 @@ def test_levels_match_oracle_bitwise(case):
             assert len(np.unique(want)) >= 2
 
 
-def _run_cycle(st, D, L, f):
+def _run_cycle(st, D, L, f, **params):
     pos, vel, mass = dev(st["pos_h"]), dev(st["vel_u"]), dev(st["mass"])
-    ctx = crk.crk_create()
+    ctx = crk.crk_create(**params)
     info = crk.crk_cycle(ctx, pos, vel, mass, D, L, f)
     return pos.cpu().numpy(), vel.cpu().numpy(), info, ctx
 
 
-def test_cycle_with_one_level_is_bitwise_the_kdk_step():
+@pytest.mark.parametrize("pair_form", [0, 1])
+def test_cycle_with_one_level_is_bitwise_the_kdk_step(pair_form):
+    """With every leaf at level 0 a cycle is one KDK step, bitwise, in either
+    form of P4 and P5 (the pair-once P5 of the opening kick reads the tile
+    lists its P4 ran with, though the cycle has refitted them)."""
     for st in (inputs.sedov(16), inputs.uniform(16)):
         ev = O.evaluate(st)
         D = 2.0 * float(O.cfl_dt(ev).min())
-        p1, v1, info, _ = _run_cycle(st, D, 0, 2)
+        p1, v1, info, _ = _run_cycle(st, D, 0, 2, pair_form=pair_form)
         pos, vel, mass = dev(st["pos_h"]), dev(st["vel_u"]), dev(st["mass"])
-        crk.crk_step(crk.crk_create(), pos, vel, mass, D)
+        crk.crk_step(crk.crk_create(pair_form=pair_form), pos, vel, mass, D)
         assert info["ticks"] == 1 and info["evaluations"] == len(p1)
         np.testing.assert_array_equal(p1, pos.cpu().numpy())
         np.testing.assert_array_equal(v1, vel.cpu().numpy())

@@ -160,13 +160,14 @@ def test_corrections(case, precision):
     assert max(e_rms.values()) < RMS_TOL.get(precision, TOL_PLAIN), e_rms
 
 
+@pytest.mark.parametrize("pair_form", [0, 1])
 @pytest.mark.parametrize("precision", [0, 1, 2])
 @pytest.mark.parametrize("case", ["uniform16", "clustered3000", "sedov16"])
-def test_forces(case, precision):
+def test_forces(case, precision, pair_form):
     st = CASES[case]()
     oc = oracle_chain(st)
     r = oc["r"]
-    ctx = fresh(st, precision=precision)
+    ctx = fresh(st, precision=precision, pair_form=pair_form)
     acc, dudt, vsig, qmax, pairs = crk.crk_forces(
         ctx, dev(st["mass"]), dev(st["vel_u"]), dev(f32(oc["V"])), dev(f32(r["A"])), dev(f32(r["B"])),
         dev(f32(r["gA"])), dev(f32(r["gB"])), dev(f32(oc["gv"])), with_pairs=True)
@@ -174,15 +175,16 @@ def test_forces(case, precision):
     assert pairs == p4["pairs"]
     e = {"acc": rel_err(acc, p4["acc"], floor=p4["fscale"]), "dudt": rel_err(dudt, p4["dudt"]),
          "vsig": rel_err(vsig, p4["vsig"]), "qmax": rel_err(qmax, p4["qmax"])}
-    print(case, precision, e)
+    print(case, precision, pair_form, e)
     assert max(e.values()) < (TOL if precision >= 1 else TOL_PLAIN), e
     # Newton's third law survives rounding: F_ji == -F_ij bitwise in the kernel
     F = as_np(acc) * oc["m"][:, None]
     assert np.max(np.abs(F.sum(axis=0))) < 1e-6 * np.abs(F).sum()
 
 
+@pytest.mark.parametrize("pair_form", [0, 1])
 @pytest.mark.parametrize("case", ["uniform16", "clustered3000"])
-def test_compatible_energy(case):
+def test_compatible_energy(case, pair_form):
     st = CASES[case]()
     oc = oracle_chain(st)
     r = oc["r"]
@@ -191,7 +193,7 @@ def test_compatible_energy(case):
     dt = 0.25 * float(st["pos_h"][:, 3].min()) / 4.0 / vmax
     vb = f32(oc["vel"])
     va = f32(oc["vel"] + dt * p4["acc"])
-    ctx = fresh(st)
+    ctx = fresh(st, pair_form=pair_form)
     du = crk.crk_compatible(ctx, dev(st["mass"]), dev(st["vel_u"]), dev(f32(oc["V"])), dev(f32(r["A"])),
                             dev(f32(r["B"])), dev(f32(r["gA"])), dev(f32(r["gB"])), dev(f32(oc["gv"])),
                             dev(vb), dev(va))
@@ -205,6 +207,30 @@ def test_compatible_energy(case):
     dK = 0.5 * (m * ((va.astype(np.float64) ** 2).sum(1) - (vb.astype(np.float64) ** 2).sum(1))).sum()
     dU = dt * (m * as_np(du)).sum()
     assert abs(dK + dU) < 1e-5 * np.abs(dK)
+
+
+def test_pair_once_repeats_bitwise_and_matches_directed():
+    """The pair-once form adds each share in a fixed order (lane order within
+    a step, list order over the tile pairs): two runs agree bitwise.  Its
+    terms are the directed form's bitwise, so the two forms differ by
+    summation order only (a few FP32 roundings of the per-particle sums)."""
+    st = CASES["clustered3000"]()
+    oc = oracle_chain(st)
+    r = oc["r"]
+    args = [dev(st["mass"]), dev(st["vel_u"]), dev(f32(oc["V"])), dev(f32(r["A"])), dev(f32(r["B"])),
+            dev(f32(r["gA"])), dev(f32(r["gB"])), dev(f32(oc["gv"]))]
+    out = {}
+    for form, rep in ((1, 0), (1, 1), (0, 0)):
+        ctx = fresh(st, pair_form=form)
+        out[form, rep] = [as_np(t) for t in crk.crk_forces(ctx, *args)]
+    for a, b in zip(out[1, 0], out[1, 1]):
+        assert np.array_equal(a, b)
+    fs = oc["p4"]["fscale"]
+    for k, (a, b) in enumerate(zip(out[1, 0], out[0, 0])):
+        e = rel_err(a, b.astype(np.float64), floor=fs if k == 0 else None)
+        assert e < 1e-6, (k, e)
+    # vsig and qmax are maxima over the same terms: equal bitwise
+    assert np.array_equal(out[1, 0][2], out[0, 0][2]) and np.array_equal(out[1, 0][3], out[0, 0][3])
 
 
 # ---------------------------------------------------------------- whole evaluation

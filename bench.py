@@ -44,6 +44,12 @@ FLOPS_PER_UNIT = {"P1 volumes": 20, "P2 corrections": 88, "P3 grad v": 92, "P4 f
 # 39.1 M unordered pairs); a full 128^3 launch is too large to capture, so the
 # traffic is scaled by units.
 TRAFFIC_PER_UNIT = {"P4 forces": 47.4}
+# the walk's exact predicate per lane test, in 32-bit integer operations:
+# dx, dy, dz (3), the widening squares and H_j^2 (4), two 64-bit additions
+# (4), the two 64-bit comparisons (4), the gather / other / reach bits (4)
+WALK_INT_OPS = 19
+# INT32 issue: 152 SMs x 64 lanes per clock x 2070 MHz (max SM clock)
+INT32_PEAK_TOPS = 152 * 64 * 2.07e9 / 1e12
 BUILD_BYTES_PER_PARTICLE = 44 + 4 * 20 + 52 + 16
 PRECISION_NAMES = ["plain", "mixed", "mixed+compensated moments", "mixed+float-float moments"]
 
@@ -927,6 +933,20 @@ def run_gpu(args):
                                        "frac": a / hbm, "peak": hbm,
                                        "bytes": "%d B per particle per rebuild (keys, 4 radix passes, gather, "
                                                 "tile boxes)" % BUILD_BYTES_PER_PARTICLE}
+    # the neighbour-list walk: integer work, WALK_INT_OPS 32-bit integer
+    # operations per lane test of the exact predicate, lane tests counted by
+    # the walk itself (crk_walk_stats; one walk per step), against the INT32
+    # issue rate (64 lanes per SM per clock)
+    tw = prof_ms.get("neighbour lists", 0.0) / args.steps
+    tests = crk.crk_walk_stats(ctx)
+    if tw > 0 and tests > 0:
+        a = WALK_INT_OPS * tests / (tw / 1e3) / 1e12
+        pass_roofline["neighbour lists"] = {"bound": "alu", "ms_per_step": tw, "achieved": a, "unit": "Tops/s",
+                                            "frac": a / INT32_PEAK_TOPS, "peak": INT32_PEAK_TOPS,
+                                            "lane_tests_per_step": tests,
+                                            "ops": "%d INT32 ops per lane test (3 subtractions, 4 widening "
+                                                   "products, two 64-bit sums and two 64-bit compares, 4 mask "
+                                                   "updates)" % WALK_INT_OPS}
     roofline["passes"] = pass_roofline
 
     if rank == 0:

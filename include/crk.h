@@ -193,6 +193,14 @@ int crk_cells(crk_ctx *ctx, uint32_t *keys, int32_t *perm, int32_t *cell_start, 
 int crk_build_stats(crk_ctx *ctx, int *ntiles, long long *list_entries,
                     long long *union_tile_pairs, void *stream);
 
+/* Work of the last neighbour-list walk (Sec. 2.3 interaction lists turned into
+ * per-particle lists): *lane_tests = evaluations of the exact fixed-point
+ * predicate |dq|^2 < H^2 (each lane of a tile tests every particle kept from
+ * each candidate tile; invalid lanes of a ragged last tile included), the
+ * walk's unit of work.  0 when the last walk wrote no lists.  Synchronises
+ * `stream`. */
+int crk_walk_stats(crk_ctx *ctx, long long *lane_tests, void *stream);
+
 /* Neighbour sets of the last build, for inspection: mode 0 = gather(i)
  * (self included), mode 1 = the pair set of i.  Device outputs in caller
  * order: count[n] = set size, hash[n] = sum over the set of fmix32(j + 1)

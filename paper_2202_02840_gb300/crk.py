@@ -70,6 +70,7 @@ def lib():
         L.crk_cells.argtypes = [_vp, _vp, _vp, _vp, ctypes.POINTER(_ci), _vp]
         L.crk_build_stats.argtypes = [_vp, ctypes.POINTER(_ci), ctypes.POINTER(ctypes.c_longlong),
                                       ctypes.POINTER(ctypes.c_longlong), _vp]
+        L.crk_walk_stats.argtypes = [_vp, ctypes.POINTER(ctypes.c_longlong), _vp]
         L.crk_neighbours.argtypes = [_vp, _ci, _vp, _vp, _vp]
         L.crk_neighbour_lists.argtypes = [_vp, _ci, _vp, _vp, _vp]
         L.crk_volumes.argtypes = [_vp, _vp, _vp, ctypes.POINTER(ctypes.c_longlong), _vp]
@@ -202,6 +203,13 @@ def crk_build_stats(ctx, stream=None):
     ctx.check(lib().crk_build_stats(ctx.handle, ctypes.byref(nt), ctypes.byref(g), ctypes.byref(u),
                                     _stream(stream)))
     return nt.value, g.value, u.value
+
+
+def crk_walk_stats(ctx, stream=None):
+    """Lane tests of the exact predicate in the last neighbour-list walk."""
+    t = ctypes.c_longlong(0)
+    ctx.check(lib().crk_walk_stats(ctx.handle, ctypes.byref(t), _stream(stream)))
+    return t.value
 
 
 def crk_neighbours(ctx, mode=0, stream=None):

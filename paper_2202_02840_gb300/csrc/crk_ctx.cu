@@ -722,6 +722,15 @@ extern "C" int crk_build_stats(crk_ctx *ctx, int *ntiles, long long *g, long lon
     return CRK_OK;
 }
 
+extern "C" int crk_walk_stats(crk_ctx *ctx, long long *lane_tests, void *stream) {
+    int rc = need_built(ctx);
+    if (rc) return rc;
+    rc = crk_sync_counters(ctx, (cudaStream_t)stream);
+    if (rc) return rc;
+    if (lane_tests) *lane_tests = (long long)ctx->h_counters[CNT_WALK_TESTS];
+    return CRK_OK;
+}
+
 extern "C" int crk_neighbours(crk_ctx *ctx, int mode, int32_t *count, uint32_t *hash, void *stream) {
     int rc = need_built(ctx);
     if (rc) return rc;

@@ -39,6 +39,7 @@ enum {
     CNT_NEXT_OK = 19,   // du_next holds the next opening kick's energy rate for dt_next
     CNT_SKIP = 20,      // this step's opening kick takes du_next
     CNT_PO_MISS = 21,   // pair-once: tile pairs (I, J) whose reverse (J, I) was not found (sticky)
+    CNT_WALK_TESTS = 22,  // lane tests of the exact predicate in the last list walk
     CNT_COUNT = 24
 };
 

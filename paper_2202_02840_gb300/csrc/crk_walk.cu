@@ -36,6 +36,7 @@ struct WalkArgs {
     const uint32_t *nbox;    // box range of each tile (BATCH only)
     const int32_t *act;      // may be null: walk the tiles act[0 .. ntiles) only
     int2 *lowc;              // may be null: per particle, gather and other entries with j < i
+    unsigned long long *tests;   // lane tests of the exact predicate (LISTS walk)
 };
 
 // LISTS: write the lists; VOL: sum n_i in the walk (volumes-only contexts).
@@ -68,6 +69,7 @@ __global__ void __launch_bounds__(WALK_WARPS * 32) k_walk(WalkArgs a) {
     float acc = 0.f;
     int cg = 0, co = 0;
     int lg = 0, lo_ = 0;   // entries with j < i: the candidate tiles come in ascending order
+    uint32_t ntest = 0;    // kept staged particles (warp-uniform)
     const uint2 lo = a.ofs[tile];
     const uint4 Ilo = __ldg(a.tlo + tile), Ihi = __ldg(a.thi + tile);   // this tile's box, max H
     const int32_t bi = BATCH && valid ? a.sbox[i] : 0;
@@ -126,6 +128,7 @@ __global__ void __launch_bounds__(WALK_WARPS * 32) k_walk(WalkArgs a) {
             }
         }
         unsigned mask = __ballot_sync(0xffffffffu, keep);
+        ntest += (uint32_t)__popc(mask);   // every lane tests every kept particle
         __syncwarp();
         // four staged particles per iteration: four independent predicate
         // chains in flight
@@ -223,6 +226,7 @@ __global__ void __launch_bounds__(WALK_WARPS * 32) k_walk(WalkArgs a) {
         atomicAdd(a.pairs_g, (unsigned long long)sg);
         atomicAdd(a.pairs_u, (unsigned long long)su);
         atomicMax(a.maxcnt, (unsigned long long)mu);
+        if (LISTS) atomicAdd(a.tests, 32ull * ntest);
     }
 }
 
@@ -368,6 +372,7 @@ static WalkArgs walk_args(crk_ctx *ctx) {
     a.act = ctx->act;
     if (ctx->act) a.ntiles = ctx->nact;
     a.lowc = ctx->volumes_only ? nullptr : ctx->lowc;
+    a.tests = ctx->counters + CNT_WALK_TESTS;
     return a;
 }
 
@@ -378,6 +383,7 @@ static int launch_walk(crk_ctx *ctx, cudaStream_t s) {
     }
     CRK_CUDA(ctx, cudaMemsetAsync(ctx->counters + CNT_PAIRS_G, 0, 2 * sizeof(unsigned long long), s));
     CRK_CUDA(ctx, cudaMemsetAsync(ctx->counters + CNT_MAXCNT, 0, sizeof(unsigned long long), s));
+    CRK_CUDA(ctx, cudaMemsetAsync(ctx->counters + CNT_WALK_TESTS, 0, sizeof(unsigned long long), s));
     if (ctx->act) {   // tiles left out of the walk take no list columns and no stored forces
         CRK_CUDA(ctx, cudaMemsetAsync(ctx->len_g, 0, sizeof(uint32_t) * ctx->ntiles, s));
         CRK_CUDA(ctx, cudaMemsetAsync(ctx->len_u, 0, sizeof(uint32_t) * ctx->ntiles, s));

@@ -110,6 +110,22 @@ def test_neighbour_lists_exact(case, mode):
         assert not np.any(raw >> np.uint32(31))
 
 
+@pytest.mark.parametrize("case", list(CASES))
+def test_walk_counts_its_lane_tests(case):
+    """The walk's unit of work (crk_walk_stats): every lane of a tile tests
+    every particle kept from a candidate tile, so the count is a multiple of
+    32, at least the pair-set entries it found, and at most 32 x 32 tests per
+    candidate tile of the tile-pair lists."""
+    st = CASES[case]()
+    ctx = fresh(st)
+    off, _ = crk.crk_neighbour_lists(ctx, 1)
+    tests = crk.crk_walk_stats(ctx)
+    entries = int(off.cpu().numpy()[-1])
+    _, _, tile_pairs = crk.crk_build_stats(ctx)
+    print(case, "lane tests", tests, "entries", entries, "tile pairs", tile_pairs)
+    assert tests % 32 == 0 and entries <= tests <= 32 * 32 * tile_pairs
+
+
 # ---------------------------------------------------------------- passes in isolation
 
 @pytest.mark.parametrize("case", list(CASES))

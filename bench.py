@@ -792,6 +792,7 @@ def run_gpu(args):
     crk.crk_profile(ctx, False)
     clk = clocks.stop()
     ntiles, entries, utp = crk.crk_build_stats(ctx)
+    walk_tests = crk.crk_walk_stats(ctx)   # lane tests of the last walk (one per step)
     ctx.close()
 
     # ---------------- end to end through host buffers (pinned), same step count
@@ -938,7 +939,7 @@ def run_gpu(args):
     # the walk itself (crk_walk_stats; one walk per step), against the INT32
     # issue rate (64 lanes per SM per clock)
     tw = prof_ms.get("neighbour lists", 0.0) / args.steps
-    tests = crk.crk_walk_stats(ctx)
+    tests = walk_tests
     if tw > 0 and tests > 0:
         a = WALK_INT_OPS * tests / (tw / 1e3) / 1e12
         pass_roofline["neighbour lists"] = {"bound": "alu", "ms_per_step": tw, "achieved": a, "unit": "Tops/s",

@@ -462,11 +462,13 @@ int crk_autotune(crk_ctx *ctx, int enable);
  * with the pass's own entries per iteration and CTAs of 1, 2, 4, 8 tiles;
  * 13-16: 1-4 entries per iteration with the neighbour records of the next
  * iteration read ahead, CTAs of one tile; 17-20: the same with the pass's own
- * CTA width (13-20 for every list pass but P4).  Either array may be NULL. */
+ * CTA width (13-20 for every list pass but P4); 21 (P4 only): the neighbour
+ * records brought into shared memory by TMA gathers (tile::gather4 from L2,
+ * two stages per warp, an mbarrier per stage).  Either array may be NULL. */
 int crk_tuning(crk_ctx *ctx, int *variant, float *ms);
 
 /* Number of pass variants (the numbering of crk_tuning). */
-#define CRK_TUNE_NVARIANT 21
+#define CRK_TUNE_NVARIANT 22
 
 /* Pin list pass k (numbering as in crk_profile_read: 0 P1, 2 P2, 3 P3, 4 P4,
  * 5 P5, 10 RK density) to variant v (numbering as in crk_tuning; -1: the

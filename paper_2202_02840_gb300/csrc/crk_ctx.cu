@@ -220,6 +220,8 @@ int crk_sync_counters(crk_ctx *ctx, cudaStream_t s) {
     CRK_CUDA(ctx, cudaMemcpyAsync(ctx->h_counters, ctx->counters, CNT_COUNT * sizeof(unsigned long long),
                                   cudaMemcpyDeviceToHost, s));
     CRK_CUDA(ctx, cudaStreamSynchronize(s));
+    if (ctx->h_counters[CNT_TMA_ERR])   // a TMA-fed pass timed out on its copies (sticky)
+        return crk_set_error(ctx, CRK_ECUDA, "a TMA-fed pass gave up waiting on its copies");
     if (ctx->h_counters[CNT_PO_MISS])   // the tile lists were not symmetric (sticky)
         return crk_set_error(ctx, CRK_ESTATE, "pair-once: %llu tile pairs without their reverse",
                              ctx->h_counters[CNT_PO_MISS]);

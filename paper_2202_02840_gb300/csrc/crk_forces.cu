@@ -202,6 +202,7 @@ struct P4 {
     static constexpr bool ENTRIES = true;
     static constexpr bool PERSISTENT = true;
     static constexpr bool PREFETCH = true;
+    static constexpr bool TMA = true;   // has the TMA-fed variant
     using Rec = FRec;
     struct Params {
         const FRec *frec;
@@ -211,6 +212,7 @@ struct P4 {
         float2 *vq;    // (vsig, qmax)
         float4 *Fst;   // (F_ij, j bits) per list entry
     };
+    static int launch_tma(crk_ctx *ctx, const ListGeom &g, const Params &prm, cudaStream_t s);
     struct IState {
         FRec me;
         float m;
@@ -268,6 +270,177 @@ struct P4 {
         p.vq[i] = make_float2(s.vsig, s.qmax);
     }
 };
+
+// ================================================================= P4 fed by TMA
+//
+// The same pass as P4's list loop, with each lane's neighbour record brought
+// into shared memory by the tensor-memory accelerator instead of five 256-bit
+// gathers through L1: per iteration one lane issues eight tile::gather4 loads
+// (four records each) of the next entries of all 32 lanes from L2, into the
+// other of two stages, and an mbarrier counts their bytes.  The lanes read
+// their record from shared memory when its pair comes up, so no registers
+// hold records in flight.  Same entries, same order, same pair function:
+// bitwise the results of the other variants.  Every wait on the mbarrier is
+// bounded; a wait that runs out sets CNT_TMA_ERR, waits (bounded again) for
+// the copies still in flight, and the warp returns.
+constexpr int TMA_RF = 36;                     // floats of a record P4 reads (w0 .. w8)
+constexpr int TMA_SLOT = 640;                  // bytes per gather4: 4 rows of 144 B, 128-byte slots
+constexpr int TMA_STAGE = 8 * TMA_SLOT;        // one record per lane
+constexpr uint32_t TMA_TX = 32u * TMA_RF * 4u; // bytes a stage receives
+constexpr uint32_t TMA_SPIN = 1u << 16;        // try_wait rounds before a wait is given up
+constexpr int TMA_WARPS = 4;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint32_t rounds) {
+    uint32_t ok = 0;
+    for (uint32_t it = 0; it < rounds && !ok; it++)
+        asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+                     : "=r"(ok)
+                     : "r"(bar), "r"(parity)
+                     : "memory");
+    return ok != 0;
+}
+
+// rows r0..r3 of the record map (x = 0) into 4 x 144 contiguous bytes at dst
+__device__ __forceinline__ void tma_gather4(uint32_t dst, const CUtensorMap *map, int4 r, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cta.global.tile::gather4.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(dst),
+        "l"(map), "r"(0), "r"(r.x), "r"(r.y), "r"(r.z), "r"(r.w), "r"(bar)
+        : "memory");
+}
+
+template <bool COMP>
+__global__ void __launch_bounds__(TMA_WARPS * 32) k_p4_tma(ListGeom g, typename P4<COMP>::Params prm,
+                                                          const __grid_constant__ CUtensorMap map,
+                                                          unsigned long long *err) {
+    __shared__ alignas(128) unsigned char stg[TMA_WARPS][2][TMA_STAGE];
+    __shared__ alignas(16) int rows[TMA_WARPS][32];
+    __shared__ alignas(8) unsigned long long bar[TMA_WARPS][2];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int tile = blockIdx.x * TMA_WARPS + w;
+    if (tile >= g.ntiles) return;
+    const uint32_t bar0 = smem_u32(&bar[w][0]), stg0 = smem_u32(&stg[w][0][0]);   // stage s: + 8 s, + TMA_STAGE s
+    if (lane == 0) {
+        mbar_init(bar0);
+        mbar_init(bar0 + 8);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+    using P = P4<COMP>;
+    const int i = tile * TILE + lane;
+    const bool valid = i < g.n;
+    typename P::IState st;
+    P::init(st, i, valid, prm);
+    const uint32_t *col0 = g.ent + (size_t)tile * g.kcap * 32 + lane;
+    const size_t fb = (size_t)g.fbase[tile] * 32 + lane;
+    const int len = min((int)g.len_u[tile], g.kcap);
+    const int mg = valid ? min(g.cnt_g[i], g.kcap) : 0;
+    const int my = valid ? min(g.cnt_u[i], g.kcap) : 0;
+    auto entry = [&](int k) -> uint32_t {
+        const int c = k < mg ? k : g.kcap - 1 - (k - mg);
+        return __ldg(col0 + (size_t)c * 32);
+    };
+    // the records of row j of every lane into stage s (lanes without an entry
+    // fetch row 0, so that a stage always receives TMA_TX bytes)
+    auto issue = [&](int s, uint32_t j) {
+        rows[w][lane] = (int)j;
+        __syncwarp();
+        if (lane == 0) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // the stage's last reads come first
+            mbar_expect_tx(bar0 + 8 * s, TMA_TX);
+#pragma unroll
+            for (int q = 0; q < 8; q++)
+                tma_gather4(stg0 + s * TMA_STAGE + q * TMA_SLOT, &map,
+                            *reinterpret_cast<const int4 *>(&rows[w][4 * q]), bar0 + 8 * s);
+        }
+        __syncwarp();
+    };
+    uint32_t e0 = my > 0 ? entry(0) : 0u, e1 = my > 1 ? entry(1) : 0u;
+    if (len > 0) issue(0, my > 0 ? (e0 & 0x3fffffffu) : 0u);
+    uint32_t ph = 0u;   // bit s: the phase stage s waits for next
+    const unsigned char *mine = &stg[w][0][0] + (lane >> 2) * TMA_SLOT + (lane & 3) * (TMA_RF * 4);
+    for (int k = 0; k < len; k++) {
+        const int s = k & 1;
+        const uint32_t e = e0;
+        if (k + 1 < len) issue(s ^ 1, k + 1 < my ? (e1 & 0x3fffffffu) : 0u);
+        e0 = e1;
+        e1 = k + 2 < my ? entry(k + 2) : 0u;
+        // one decision for the warp: every lane continues, or every lane leaves
+        if (!__all_sync(0xffffffffu, mbar_wait(bar0 + 8 * s, (ph >> s) & 1u, TMA_SPIN))) {
+            if (lane == 0) atomicAdd(err, 1ull);
+            mbar_wait(bar0 + 8 * s, (ph >> s) & 1u, 4 * TMA_SPIN);
+            if (k + 1 < len) mbar_wait(bar0 + 8 * (s ^ 1), (ph >> (s ^ 1)) & 1u, 4 * TMA_SPIN);
+            return;
+        }
+        ph ^= 1u << s;
+        if (k < my) {
+            const float4 *q = reinterpret_cast<const float4 *>(mine + s * TMA_STAGE);
+            FRec r;
+            r.w0 = q[0];
+            r.w1 = q[1];
+            r.w2 = q[2];
+            r.w3 = q[3];
+            r.w4 = q[4];
+            r.w5 = q[5];
+            r.w6 = q[6];
+            r.w7 = q[7];
+            r.w8 = q[8];
+            r.w9 = make_float4(0.f, 0.f, 0.f, 0.f);
+            P::pair(st, r, e, fb + (size_t)k * 32, k < mg, prm);
+        }
+        __syncwarp();
+    }
+    if (valid) P::finish(st, i, prm);
+}
+
+// The record map: a 2-D tensor of n rows of TMA_RF floats with a row pitch of
+// one record (160 B); a box is one row of TMA_RF floats (gather4 takes four).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static int frec_tensor_map(crk_ctx *ctx) {
+    if (ctx->frec_map_base == (const void *)ctx->frec && ctx->frec_map_rows == ctx->n) return CRK_OK;
+    static EncodeTiledFn encode = nullptr;
+    if (!encode) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+            return crk_set_error(ctx, CRK_ECUDA, "cuTensorMapEncodeTiled is not available");
+        encode = reinterpret_cast<EncodeTiledFn>(fn);
+    }
+    const cuuint64_t dims[2] = {(cuuint64_t)TMA_RF, (cuuint64_t)ctx->n};
+    const cuuint64_t strides[1] = {(cuuint64_t)sizeof(FRec)};
+    const cuuint32_t box[2] = {(cuuint32_t)TMA_RF, 1u};
+    const cuuint32_t estr[2] = {1u, 1u};
+    CUresult r = encode(&ctx->frec_map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)ctx->frec, dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return crk_set_error(ctx, CRK_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    ctx->frec_map_base = ctx->frec;
+    ctx->frec_map_rows = ctx->n;
+    return CRK_OK;
+}
+
+template <bool COMP>
+int P4<COMP>::launch_tma(crk_ctx *ctx, const ListGeom &g, const Params &prm, cudaStream_t s) {
+    int rc = frec_tensor_map(ctx);
+    if (rc) return rc;
+    k_p4_tma<COMP><<<grid_for(g.ntiles, TMA_WARPS), TMA_WARPS * 32, 0, s>>>(g, prm, ctx->frec_map,
+                                                                          ctx->counters + CNT_TMA_ERR);
+    return CRK_OK;
+}
 
 // ================================================================= P5 compatible energy
 

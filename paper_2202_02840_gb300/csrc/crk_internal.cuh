@@ -2,6 +2,7 @@
 // shared by the CUDA translation units of the CRKSPH pair engine.
 #pragma once
 
+#include <cuda.h>   // CUtensorMap (the encoder is reached through the runtime's driver entry point)
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stdio.h>
@@ -40,6 +41,7 @@ enum {
     CNT_SKIP = 20,      // this step's opening kick takes du_next
     CNT_PO_MISS = 21,   // pair-once: tile pairs (I, J) whose reverse (J, I) was not found (sticky)
     CNT_WALK_TESTS = 22,  // lane tests of the exact predicate in the last list walk
+    CNT_TMA_ERR = 23,   // sticky: a TMA-fed pass gave up waiting on its copies
     CNT_COUNT = 24
 };
 
@@ -134,6 +136,9 @@ struct crk_ctx {
     int volumes_only = 0;            // walk without writing lists (no list buffer)
     int lists_valid = 0;
     float4 *frec = nullptr;          // packed pair-set records, 10 float4 (160 B) per particle
+    CUtensorMap frec_map;            // TMA view of frec: rows of its first 36 floats (P4's TMA variant)
+    const void *frec_map_base = nullptr;
+    int frec_map_rows = -1;
     float *sfun = nullptr;           // specific entropy of the evaluation state
     float4 *sig = nullptr;           // (v + v') of a kick, s
     float4 *sig2 = nullptr;          // two kicks (closing, next opening): sig side by side, 2 per particle

@@ -393,20 +393,28 @@ struct LVariant {
     int U, ord;
     int warps;   // tiles per CTA in the grid form (32 particles each); 0 = the pass's own
     bool rp;     // records one iteration ahead (list_loop_rp)
+    bool tma;    // records brought into shared memory by TMA gathers (passes with P::TMA)
 };
 // 0-3: grid, U = 1..4; 4-7: longest first, U = 1..4; 8: per-SM ranges;
 // 9-12: grid with the pass's own U and CTAs of 1, 2, 4, 8 tiles (32-256 particles);
 // 13-16: grid, U = 1..4, records one iteration ahead, CTAs of one tile;
 // 17-20: the same with the pass's own CTA width (passes without their own
-// record prefetch: all but P4)
+// record prefetch: all but P4); 21: records by TMA gathers (P4)
 __host__ __device__ constexpr LVariant lvariant(int v) {
-    return v < 4 ? LVariant{v + 1, ORD_GRID, 0, false}
-                 : (v < 8 ? LVariant{v - 3, ORD_LONGEST, 0, false}
-                          : (v == 8 ? LVariant{1, ORD_SM, 0, false}
-                                    : (v < 13 ? LVariant{0, ORD_GRID, 1 << (v - 9), false}
-                                              : (v < 17 ? LVariant{v - 12, ORD_GRID, 1, true}
-                                                        : LVariant{v - 16, ORD_GRID, 0, true}))));
+    return v < 4 ? LVariant{v + 1, ORD_GRID, 0, false, false}
+                 : (v < 8 ? LVariant{v - 3, ORD_LONGEST, 0, false, false}
+                          : (v == 8 ? LVariant{1, ORD_SM, 0, false, false}
+                                    : (v < 13 ? LVariant{0, ORD_GRID, 1 << (v - 9), false, false}
+                                              : (v < 17 ? LVariant{v - 12, ORD_GRID, 1, true, false}
+                                                        : (v < 21 ? LVariant{v - 16, ORD_GRID, 0, true, false}
+                                                                  : LVariant{1, ORD_GRID, 0, false, true})))));
 }
+
+// passes with a TMA-fed variant (21)
+template <class P, class = void>
+struct has_tma : std::false_type {};
+template <class P>
+struct has_tma<P, std::void_t<decltype(P::TMA)>> : std::bool_constant<P::TMA> {};
 
 int tile_order_by_length(crk_ctx *ctx, cudaStream_t s);   // ctx->tile_order, longest pair-set list first
 
@@ -454,6 +462,10 @@ static void launch_rp_u(crk_ctx *ctx, const ListGeom &g, const typename P::Param
 template <class P, int WARPS>
 static int launch_variant(crk_ctx *ctx, const ListGeom &g, const typename P::Params &prm, int v, cudaStream_t s) {
     const LVariant lv = lvariant(v);
+    if (lv.tma) {
+        if constexpr (has_tma<P>::value) return P::launch_tma(ctx, g, prm, s);
+        return CRK_OK;
+    }
     if (lv.rp) {   // records one iteration ahead (passes without their own prefetch)
         if constexpr (!P::PREFETCH) {
             if (lv.warps == 1)
@@ -497,6 +509,7 @@ constexpr int default_variant() {
 
 template <class P>
 constexpr bool variant_applies(int v) {
+    if (lvariant(v).tma) return has_tma<P>::value;
     if (lvariant(v).rp) return !P::PREFETCH;
     return P::PREFETCH ? (lvariant(v).U <= 1) : true;
 }

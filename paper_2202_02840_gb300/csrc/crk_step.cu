@@ -688,7 +688,7 @@ namespace {
 
 // sticky overflow / invalid-input flag of a replayed step
 __global__ void k_graph_check(unsigned long long *cnt, long long cap_ulist, int kcap) {
-    if (cnt[CNT_ERR_INPUT] || cnt[CNT_PO_MISS] || (long long)cnt[CNT_ULIST] > cap_ulist ||
+    if (cnt[CNT_ERR_INPUT] || cnt[CNT_PO_MISS] || cnt[CNT_TMA_ERR] || (long long)cnt[CNT_ULIST] > cap_ulist ||
         (long long)cnt[CNT_MAXCNT] > kcap)
         cnt[CNT_GRAPH_ERR] = 1ull;
 }

@@ -184,24 +184,27 @@ def test_every_pass_variant_gives_identical_results():
             crk.crk_tune_set(ctx, name, v)
         ran = set(names)
 
-        def call(name, fn):
-            try:
-                return fn()
-            except crk.CrkError as e:
-                assert e.code == crk.CRK_EINVAL and "has no variant" in str(e), str(e)
-                ran.discard(name)
-                crk.crk_tune_set(ctx, name, -1)
-                return fn()
+        def call(fn):
+            # a pass pinned to a variant it lacks refuses it (CRK_EINVAL, naming
+            # itself): unpin that pass and call again
+            for _ in range(len(names) + 1):
+                try:
+                    return fn()
+                except crk.CrkError as e:
+                    assert e.code == crk.CRK_EINVAL and "has no variant" in str(e), str(e)
+                    name = next(k for k in names if str(e).split(": ", 1)[1].startswith(k))
+                    ran.discard(name)
+                    crk.crk_tune_set(ctx, name, -1)
+            raise AssertionError("variant %d refused repeatedly" % v)
 
         pos, vel, mass = dev(st["pos_h"]), dev(st["vel_u"]), dev(st["mass"])
         crk.crk_build_cells(ctx, pos)
-        V, N = call("P1 volumes", lambda: crk.crk_volumes(ctx))
-        A, B, gA, gB, gv = crk.crk_corrections(ctx, V, vel)
-        acc, dudt, vsig, qmax = call("P4 forces", lambda: crk.crk_forces(ctx, mass, vel, V, A, B, gA, gB, gv))
-        du = call("P5 compatible energy",
-                  lambda: crk.crk_compatible(ctx, mass, vel, V, A, B, gA, gB, gv, vel[:, :3].contiguous(),
+        V, N = call(lambda: crk.crk_volumes(ctx))
+        A, B, gA, gB, gv = call(lambda: crk.crk_corrections(ctx, V, vel))
+        acc, dudt, vsig, qmax = call(lambda: crk.crk_forces(ctx, mass, vel, V, A, B, gA, gB, gv))
+        du = call(lambda: crk.crk_compatible(ctx, mass, vel, V, A, B, gA, gB, gv, vel[:, :3].contiguous(),
                                              (vel[:, :3] * 1.01).contiguous()))
-        for _ in range(2):
+        for _ in range(2):   # every pass lacking v is unpinned by now
             crk.crk_step(ctx, pos, vel, mass, 0.0)
         return [V, N, A, B, gA, gB, gv, acc, dudt, vsig, qmax, du, pos, vel], ran
 
@@ -213,9 +216,9 @@ def test_every_pass_variant_gives_identical_results():
             has[name].add(v)
         for a, b in zip(ref, out):
             assert torch.equal(a, b), v
-    every = set(range(crk.CRK_TUNE_NVARIANT))
+    every = set(range(crk.CRK_TUNE_NVARIANT)) - {21}   # 21: records by TMA gathers, P4 only
     assert has["P1 volumes"] == has["P2 corrections"] == has["P3 grad v"] == has["P5 compatible energy"] == every
-    assert has["P4 forces"] == {0, 4, 8, 9, 10, 11, 12}
+    assert has["P4 forces"] == {0, 4, 8, 9, 10, 11, 12, 21}
 
 
 # ---------------------------------------------------------------- CUDA graphs

@@ -464,7 +464,9 @@ int crk_autotune(crk_ctx *ctx, int enable);
  * iteration read ahead, CTAs of one tile; 17-20: the same with the pass's own
  * CTA width (13-20 for every list pass but P4); 21 (P4 only): the neighbour
  * records brought into shared memory by TMA gathers (tile::gather4 from L2,
- * two stages per warp, an mbarrier per stage).  Either array may be NULL. */
+ * two stages per warp, an mbarrier per stage), measured 6x slower than the L1
+ * forms on GB300 and therefore run only when pinned by crk_tune_set, never
+ * by the tuner's sweep.  Either array may be NULL. */
 int crk_tuning(crk_ctx *ctx, int *variant, float *ms);
 
 /* Number of pass variants (the numbering of crk_tuning). */

@@ -557,7 +557,9 @@ int launch_lpass(crk_ctx *ctx, int prof_id, const typename P::Params &prm, cudaS
         float best = 3.0e38f;
         int bestv = default_variant<P>();
         for (int v = 0; v < NVAR; v++) {
-            if (!variant_applies<P>(v)) continue;
+            // the TMA-fed variant is measured 6x slower than the L1 forms on
+            // GB300: it runs only when pinned (crk_tune_set)
+            if (!variant_applies<P>(v) || lvariant(v).tma) continue;
             CRK_CUDA(ctx, cudaEventRecord(ctx->tune_ev[0], s));
             rc = launch_variant<P, WARPS>(ctx, g, prm, v, s);
             if (rc) return rc;

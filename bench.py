@@ -945,6 +945,7 @@ def run_gpu(args):
         pass_roofline["neighbour lists"] = {"bound": "alu", "ms_per_step": tw, "achieved": a, "unit": "Tops/s",
                                             "frac": a / INT32_PEAK_TOPS, "peak": INT32_PEAK_TOPS,
                                             "lane_tests_per_step": tests,
+                                            "useful_fraction": u_pairs / tests,
                                             "ops": "%d INT32 ops per lane test (3 subtractions, 4 widening "
                                                    "products, two 64-bit sums and two 64-bit compares, 4 mask "
                                                    "updates)" % WALK_INT_OPS}

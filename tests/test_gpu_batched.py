@@ -78,15 +78,18 @@ def test_batched_passes_match_each_box():
     assert pairs == tot_pairs
 
 
-def test_batched_step_matches_single_box_steps():
-    """Three KDK steps of all boxes at once against each box stepped alone."""
+@pytest.mark.parametrize("pair_form", [0, 1])
+def test_batched_step_matches_single_box_steps(pair_form):
+    """Three KDK steps of all boxes at once against each box stepped alone, in
+    either form of P4 and P5 (the pair-once form over boxes: the tile-pair
+    lists, and with them the reverse index, stay within each box)."""
     sts = boxes()
     cat, start = concat(sts)
     pos, vel, mass = dev(cat["pos_h"]), dev(cat["vel_u"]), dev(cat["mass"])
-    ctx = crk.crk_create()
+    ctx = crk.crk_create(pair_form=pair_form)
     single = []
     for st in sts:
-        single.append((dev(st["pos_h"]), dev(st["vel_u"]), dev(st["mass"]), crk.crk_create()))
+        single.append((dev(st["pos_h"]), dev(st["vel_u"]), dev(st["mass"]), crk.crk_create(pair_form=pair_form)))
     for step in range(3):
         d = crk.crk_step_batched(ctx, pos, vel, mass, start, diag=True)
         for b, (p, v, m, c) in enumerate(single):

@@ -128,13 +128,13 @@ def pick_delta(dt, base, L, tries=40):
     return bD, best
 
 
-def compare_cycle(st, L, f, mult, min_wakeups=0):
+def compare_cycle(st, L, f, mult, min_wakeups=0, **params):
     ev = O.evaluate(st)
     dt = O.cfl_dt(ev)
     D, margin = pick_delta(dt, mult * float(dt.min()), L)
     assert margin > 1e-4
     out, ev1, info = H.cycle(st, ev, Delta=D, L=L, f_l=f)
-    p, v, g, _ = _run_cycle(st, D, L, f)
+    p, v, g, _ = _run_cycle(st, D, L, f, **params)
     n = len(p)
     lev0 = np.bincount(info["levels_start"], minlength=32)
     assert g["level_count"] == lev0.tolist()
@@ -156,11 +156,15 @@ def compare_cycle(st, L, f, mult, min_wakeups=0):
     return info
 
 
-def test_cycle_matches_oracle_blast_with_wakeups():
+@pytest.mark.parametrize("pair_form", [0, 1])
+def test_cycle_matches_oracle_blast_with_wakeups(pair_form):
+    """Also in the pair-once form, whose full evaluations (the cycle's ends)
+    alternate with directed evaluations of the active tiles, each P5 taking
+    the form of the P4 that stored its forces."""
     st, ev = inputs.sedov(16, u0=0.05, jitter=0.1), None
     for _ in range(8):
         st, ev, _ = O.kdk_step(st, ev=ev)
-    info = compare_cycle(st, 4, 2, 12.0, min_wakeups=1)
+    info = compare_cycle(st, 4, 2, 12.0, min_wakeups=1, pair_form=pair_form)
     assert len(np.unique(info["levels_start"])) >= 3
 
 

@@ -466,11 +466,13 @@ int crk_autotune(crk_ctx *ctx, int enable);
  * records brought into shared memory by TMA gathers (tile::gather4 from L2,
  * two stages per warp, an mbarrier per stage), measured 6x slower than the L1
  * forms on GB300 and therefore run only when pinned by crk_tune_set, never
- * by the tuner's sweep.  Either array may be NULL. */
+ * by the tuner's sweep; 22 (every list pass but P4): per-SM tile ranges with
+ * the pass's own entries per iteration and the records of the next iteration
+ * read ahead.  Either array may be NULL. */
 int crk_tuning(crk_ctx *ctx, int *variant, float *ms);
 
 /* Number of pass variants (the numbering of crk_tuning). */
-#define CRK_TUNE_NVARIANT 22
+#define CRK_TUNE_NVARIANT 23
 
 /* Pin list pass k (numbering as in crk_profile_read: 0 P1, 2 P2, 3 P3, 4 P4,
  * 5 P5, 10 RK density) to variant v (numbering as in crk_tuning; -1: the

@@ -533,7 +533,7 @@ def crk_tuning(ctx):
     return {PASS_NAMES[k]: (v[k], ms[k]) for k in range(NPASS) if v[k] >= 0}
 
 
-CRK_TUNE_NVARIANT = 22
+CRK_TUNE_NVARIANT = 23
 
 
 def crk_tune_set(ctx, pass_name, variant):

@@ -303,7 +303,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_lpass(ListGeom g, typename P::Pa
 // warp whose range is exhausted claims tiles from the other ranges.  Every
 // claim is one atomicAdd; a range's counter runs past chunk at most once per
 // warp, so the loop is bounded.
-template <class P, int U>
+template <class P, int U, bool RP = false>
 __global__ void __launch_bounds__(32) k_lpass_sm(ListGeom g, typename P::Params prm, uint32_t *next, int nrange,
                                                  int chunk) {
     const int lane = threadIdx.x & 31;
@@ -319,7 +319,7 @@ __global__ void __launch_bounds__(32) k_lpass_sm(ListGeom g, typename P::Params 
             if (t >= (uint32_t)chunk) break;
             const long long tile = (long long)range * chunk + t;
             if (tile >= g.ntiles) break;
-            lpass_tile<P, U>(g, prm, (int)tile, lane);
+            lpass_tile<P, U, RP>(g, prm, (int)tile, lane);
         }
     }
 }
@@ -399,7 +399,8 @@ struct LVariant {
 // 9-12: grid with the pass's own U and CTAs of 1, 2, 4, 8 tiles (32-256 particles);
 // 13-16: grid, U = 1..4, records one iteration ahead, CTAs of one tile;
 // 17-20: the same with the pass's own CTA width (passes without their own
-// record prefetch: all but P4); 21: records by TMA gathers (P4)
+// record prefetch: all but P4); 21: records by TMA gathers (P4); 22: per-SM
+// ranges with the pass's own U and records one iteration ahead (all but P4)
 __host__ __device__ constexpr LVariant lvariant(int v) {
     return v < 4 ? LVariant{v + 1, ORD_GRID, 0, false, false}
                  : (v < 8 ? LVariant{v - 3, ORD_LONGEST, 0, false, false}
@@ -407,7 +408,8 @@ __host__ __device__ constexpr LVariant lvariant(int v) {
                                     : (v < 13 ? LVariant{0, ORD_GRID, 1 << (v - 9), false, false}
                                               : (v < 17 ? LVariant{v - 12, ORD_GRID, 1, true, false}
                                                         : (v < 21 ? LVariant{v - 16, ORD_GRID, 0, true, false}
-                                                                  : LVariant{1, ORD_GRID, 0, false, true})))));
+                                                                  : (v == 21 ? LVariant{1, ORD_GRID, 0, false, true}
+                                                                             : LVariant{0, ORD_SM, 0, true, false}))))));
 }
 
 // passes with a TMA-fed variant (21)
@@ -438,6 +440,23 @@ static void launch_variant_u(crk_ctx *ctx, const ListGeom &g, const typename P::
     }
 }
 
+// per-SM tile ranges, the pass's own entries per iteration, records one
+// iteration ahead
+template <class P>
+static void launch_sm_rp(crk_ctx *ctx, const ListGeom &g, const typename P::Params &prm, cudaStream_t s) {
+    constexpr int U = P::UNROLL;
+    static int per_sm = 0;
+    if (!per_sm) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lpass_sm<P, U, true>, 32, 0) != cudaSuccess ||
+            per_sm < 1)
+            per_sm = 1;
+    }
+    const int nrange = ctx->nsm > 0 ? (ctx->nsm < 1024 ? ctx->nsm : 1024) : 1;
+    const int chunk = (ctx->ntiles + nrange - 1) / nrange;
+    cudaMemsetAsync(ctx->sm_next, 0, sizeof(uint32_t) * nrange, s);
+    k_lpass_sm<P, U, true><<<nrange * per_sm, 32, 0, s>>>(g, prm, ctx->sm_next, nrange, chunk);
+}
+
 template <class P, int W>
 static void launch_width(crk_ctx *ctx, const ListGeom &g, const typename P::Params &prm, cudaStream_t s) {
     constexpr int U = P::PREFETCH ? 1 : P::UNROLL;
@@ -464,6 +483,10 @@ static int launch_variant(crk_ctx *ctx, const ListGeom &g, const typename P::Par
     const LVariant lv = lvariant(v);
     if (lv.tma) {
         if constexpr (has_tma<P>::value) return P::launch_tma(ctx, g, prm, s);
+        return CRK_OK;
+    }
+    if (lv.rp && lv.ord == ORD_SM) {
+        if constexpr (!P::PREFETCH) launch_sm_rp<P>(ctx, g, prm, s);
         return CRK_OK;
     }
     if (lv.rp) {   // records one iteration ahead (passes without their own prefetch)

@@ -43,7 +43,7 @@ FLOPS_PER_UNIT = {"P1 volumes": 20, "P2 corrections": 88, "P3 grad v": 92, "P4 f
 # zeldovich-64^3 in the Hilbert order (0.65 GB read + 1.20 GB written for
 # 39.1 M unordered pairs); a full 128^3 launch is too large to capture, so the
 # traffic is scaled by units.
-TRAFFIC_PER_UNIT = {"P4 forces": 47.4}
+TRAFFIC_PER_UNIT = {"P4 forces": 50.0}
 # the walk's exact predicate per lane test, in 32-bit integer operations:
 # dx, dy, dz (3), the widening squares and H_j^2 (4), two 64-bit additions
 # (4), the two 64-bit comparisons (4), the gather / other / reach bits (4)
